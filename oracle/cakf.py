@@ -1,0 +1,333 @@
+"""Plain FP64 reference of the computation-aware Kalman filter (CAKF) and smoother (CAKS).
+
+TEST INFRASTRUCTURE ONLY -- the oracle.  Slow, literal, numpy float64.  Only
+`tests/`, `__graft_entry__.smoke()` and `bench.py`'s CPU-baseline legs use it.
+It shares no code with the CUDA path.
+
+What it follows (arXiv 2405.08971, "Computation-Aware Kalman Filtering and
+Smoothing"):
+
+* Model: the space-time separable Gauss-Markov lemma (appendix, "Space-time
+  separable Gauss-Markov processes"): A = A^t (x) I, Q = Q^t (x) K.  With an
+  Ornstein-Uhlenbeck temporal factor (D'=1) this is A = a I, Q = (1-a^2) K,
+  a = exp(-dt/l_t), and the stationary prior covariance Sigma_k = K for all k.
+  A known prior mean mu_k enters as b_{k-1} = mu_k - a mu_{k-1}.
+* Filter: Alg. 1 (CAKF) with the iterative update step (appendix algorithm
+  "CAKF Update Step (Iterative Version)"), CG policy = the current residual
+  (Sec. 3.3).  Predict / update in downdate form (Prop. "Downdate-form Kalman
+  filter"): P^- = Sigma - M^- M^-T, M = (M^-, P^- W).
+* Truncate: Sec. 3.2 -- keep the top-r eigen-directions of M M^T (computed from
+  the small Gram M^T M, same eigenvectors up to the map u -> M u).
+* Smoother: Alg. 3 (CAKS), the inverse-free RTS recursion in downdate form
+  (Prop. "Inverse-free RTS smoother").
+* NLL: not in the paper (named as future work at the end of the conclusion).
+  Defined here as the negative log density of the projected data S_k^T y_k
+  under the modified observation model (eq. proj-observation), in Euclidean-
+  normalised coordinates:
+      nll_k = 1/2 logdet(2 pi S^T G S) + 1/2 (S^T r0)^T (S^T G S)^{-1} (S^T r0)
+              - 1/2 logdet(S^T S),
+  G = H P^- H^T + sigma_n^2 I, r0 = y - H m^-.  At full budget it is the exact
+  Kalman-filter NLL term.
+* Gradient: central finite differences of the NLL with the actions S_k and the
+  truncation rotations U_k frozen (exact inference in a fixed modified model).
+
+Readings where the paper is ambiguous (each one is listed in the design doc):
+  R1 residual/action order in the iterative update: per iteration
+     r = r0 - G v; s = r; alpha = s^T r; d = (I - V V^T G) s; eta = s^T G d;
+     v += (alpha/eta) d; V <- (V, d/sqrt(eta)).
+  R2 stopping: i = min(budget, m_k); stop early if cg_rtol > 0 and
+     ||r|| <= cg_rtol ||r0||, or on breakdown (eta not finite, or
+     eta <= 1e-12 * s^T G s).
+  R4 truncation by eig of M^T M, descending; no truncation when #cols <= r.
+  R5 smoother truncation: same rank r, Euclidean eig of Ws^T Ws.
+  R6 the smoother uses the untruncated filter factor M_k (filter covariance
+     P_k = K - M_k M_k^T) and the predicted P^-_k = K - a^2 M+_{k-1} M+_{k-1}^T.
+  R7 smoother loop k = T-1 .. 0 with w_0 = 0, W_0 empty.
+  R9 Matern kernels in the Rasmussen-Williams form, output scale = variance.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional
+
+import numpy as np
+
+MATERN12, MATERN32, MATERN52 = 0, 1, 2
+_BLOCK_BYTES = 256 << 20
+
+
+# ----------------------------------------------------------------------------- kernel
+def matern(u: np.ndarray, kernel: int) -> np.ndarray:
+    """Unit-variance Matern correlation of the scaled distance u = d / l (R9)."""
+    if kernel == MATERN12:
+        return np.exp(-u)
+    if kernel == MATERN32:
+        s = math.sqrt(3.0) * u
+        return (1.0 + s) * np.exp(-s)
+    if kernel == MATERN52:
+        s = math.sqrt(5.0) * u
+        return (1.0 + s + s * s / 3.0) * np.exp(-s)
+    raise ValueError(f"unknown kernel {kernel}")
+
+
+def kernel_matrix(Xa: np.ndarray, Xb: np.ndarray, kernel: int, lx: float, sf2: float) -> np.ndarray:
+    """Dense Gram matrix sigma_f^2 k(|x_a - x_b| / l_x) between two coordinate sets."""
+    diff = Xa[:, None, :] - Xb[None, :, :]
+    d = np.sqrt(np.sum(diff * diff, axis=-1))
+    return sf2 * matern(d / lx, kernel)
+
+
+@dataclasses.dataclass
+class Model:
+    """Separable OU x Matern state-space model on a fixed grid (appendix lemma on STSGMPs)."""
+    X: np.ndarray
+    kernel: int
+    lx: float
+    sf2: float
+    a: float
+    sn2: float
+    mu: Optional[np.ndarray]   # (T+1, n) prior mean or None
+
+    @property
+    def n(self):
+        return self.X.shape[0]
+
+    def K_times(self, B: np.ndarray, rows: Optional[np.ndarray] = None,
+                cols: Optional[np.ndarray] = None) -> np.ndarray:
+        """K(X[rows], X[cols]) @ B without holding the full Gram matrix (row blocks)."""
+        Xr = self.X if rows is None else self.X[rows]
+        Xc = self.X if cols is None else self.X[cols]
+        B2 = B.reshape(B.shape[0], -1)
+        out = np.empty((Xr.shape[0], B2.shape[1]))
+        step = max(1, _BLOCK_BYTES // (8 * max(1, Xc.shape[0]) * (2 + Xc.shape[1])))
+        for lo in range(0, Xr.shape[0], step):
+            hi = min(lo + step, Xr.shape[0])
+            out[lo:hi] = kernel_matrix(Xr[lo:hi], Xc, self.kernel, self.lx, self.sf2) @ B2
+        return out.reshape((Xr.shape[0],) + B.shape[1:])
+
+    def b(self, k: int) -> np.ndarray:
+        """Dynamics offset b_{k-1} so that the prior mean at step k is mu_k."""
+        if self.mu is None:
+            return np.zeros(self.n)
+        return self.mu[k] - self.a * self.mu[k - 1]
+
+    def m0(self) -> np.ndarray:
+        return np.zeros(self.n) if self.mu is None else self.mu[0].copy()
+
+
+def model_from(w, log_lx=None, log_lt=None, log_sf2=None, log_sn2=None) -> Model:
+    """Model of a `synth.Workload` (hyperparameters optionally overridden, in log space)."""
+    lx = math.exp(w.log_lx if log_lx is None else log_lx)
+    lt = math.exp(w.log_lt if log_lt is None else log_lt)
+    sf2 = math.exp(w.log_sf2 if log_sf2 is None else log_sf2)
+    sn2 = math.exp(w.log_sn2 if log_sn2 is None else log_sn2)
+    return Model(X=np.asarray(w.coords, dtype=np.float64), kernel=w.kernel, lx=lx, sf2=sf2,
+                 a=math.exp(-w.dt / lt), sn2=sn2, mu=w.prior_mean)
+
+
+# ----------------------------------------------------------------------------- truncation
+def truncate(M: np.ndarray, r: int):
+    """Truncate (Sec. 3.2): M M^T = M+ M+^T + N N^T keeping the top-r eigen-directions.
+
+    Returns (M_plus, U_r or None, eigenvalues kept, eigenvalues dropped).  U_r
+    holds the eigenvectors of M^T M for the r largest eigenvalues (descending),
+    so M+ = M U_r.  No truncation when r <= 0 or #cols <= r (R4)."""
+    if r <= 0 or M.shape[1] <= r:
+        return M, None, None, None
+    lam, U = np.linalg.eigh(M.T @ M)
+    order = np.argsort(lam)[::-1]
+    lam, U = lam[order], U[:, order]
+    return M @ U[:, :r], U[:, :r], lam[:r], lam[r:]
+
+
+# ----------------------------------------------------------------------------- filter
+@dataclasses.dataclass
+class FilterResult:
+    m: np.ndarray                 # (T+1, n) filter means
+    var: np.ndarray               # (T+1, n) filter marginal variances (pre-truncation)
+    M_hat: List[np.ndarray]       # updated factor per step (untruncated); [0] is n x 0
+    M_pred: List[np.ndarray]      # predictive factor a M+_{k-1} per step; [0] is n x 0
+    w: List[np.ndarray]           # filter message w_k = H^T v (dense n-vector); [0] zeros
+    W: List[np.ndarray]           # filter message W_k = H^T V (dense n x j); [0] empty
+    S: List[np.ndarray]           # actions per step (m_k x j)
+    U: List[Optional[np.ndarray]] # truncation rotations per step (None: not truncated)
+    nll: np.ndarray               # (T+1,) per-step NLL terms, [0] = 0
+    iters: np.ndarray             # (T+1,) actions used per step
+    dropped: np.ndarray           # (T+1,) discarded truncation mass sum(dropped eigenvalues)
+    G: List[Optional[np.ndarray]] # dense projected innovation Grams (kept for tests)
+    r0: List[Optional[np.ndarray]]
+
+
+def update_iterative(model: Model, m_pred, M_pred, obs, y, budget, cg_rtol=0.0, S_replay=None):
+    """CAKF update step, iterative version (appendix algorithm, reading R1/R2).
+
+    Forms G = H P^- H^T + sigma_n^2 I densely (m x m; this is the oracle) and
+    runs the G-orthogonalised projected update with CG actions s = current
+    residual.  Returns (m, M_hat, w, W, S, V, G, r0)."""
+    n = model.n
+    Xo = obs
+    mo = len(obs)
+    Ko = model.K_times(np.eye(mo), rows=Xo, cols=Xo)
+    Mo = M_pred[obs]
+    G = Ko - Mo @ Mo.T + model.sn2 * np.eye(mo)
+    r0 = y - m_pred[obs]
+    v = np.zeros(mo)
+    V = np.zeros((mo, 0))
+    S = []
+    nmax = min(budget, mo) if S_replay is None else S_replay.shape[1]
+    r0n = np.linalg.norm(r0)
+    for it in range(nmax):
+        r = r0 - G @ v
+        if S_replay is None and cg_rtol > 0 and np.linalg.norm(r) <= cg_rtol * r0n:
+            break
+        s = r if S_replay is None else S_replay[:, it]
+        alpha = s @ r
+        Gs = G @ s
+        d = s - V @ (V.T @ Gs)
+        eta = s @ (G @ d)
+        if not np.isfinite(eta) or eta <= 1e-12 * (s @ Gs):
+            break
+        v = v + (alpha / eta) * d
+        V = np.concatenate([V, (d / math.sqrt(eta))[:, None]], axis=1)
+        S.append(s)
+    S = np.stack(S, axis=1) if S else np.zeros((mo, 0))
+    # w = H^T v, W = H^T V; P^- [W w] = K(X, X_o) [V v] - M^- (M_o^T [V v])
+    Vv = np.concatenate([V, v[:, None]], axis=1)
+    PVv = model.K_times(Vv, cols=Xo) - M_pred @ (Mo.T @ Vv)
+    m_new = m_pred + PVv[:, -1]
+    M_hat = np.concatenate([M_pred, PVv[:, :-1]], axis=1)
+    w = np.zeros(n)
+    w[obs] = v
+    W = np.zeros((n, V.shape[1]))
+    W[obs] = V
+    return m_new, M_hat, w, W, S, V, G, r0
+
+
+def _nll_step(G, S, r0):
+    """Per-step NLL of the projected data (definition in the module docstring)."""
+    j = S.shape[1]
+    if j == 0:
+        return 0.0
+    Gh = S.T @ G @ S
+    yh = S.T @ r0
+    L = np.linalg.cholesky(Gh)
+    Ls = np.linalg.cholesky(S.T @ S)
+    z = np.linalg.solve(L, yh)
+    return (0.5 * j * math.log(2 * math.pi) + np.sum(np.log(np.diag(L))) + 0.5 * z @ z
+            - np.sum(np.log(np.diag(Ls))))
+
+
+def filter_run(w, model: Optional[Model] = None, budget=None, rank_r=None, cg_rtol=0.0,
+               S_replay=None, U_replay=None, keep_G=False) -> FilterResult:
+    """Alg. 1 (CAKF) over steps k = 1..T of a `synth.Workload`."""
+    model = model or model_from(w)
+    budget = w.budget_i if budget is None else budget
+    rank_r = w.rank_r if rank_r is None else rank_r
+    n, T = model.n, w.T
+    m = np.zeros((T + 1, n))
+    var = np.zeros((T + 1, n))
+    m[0] = model.m0()
+    var[0] = model.sf2
+    Mplus = np.zeros((n, 0))
+    res = FilterResult(m=m, var=var, M_hat=[Mplus], M_pred=[Mplus], w=[np.zeros(n)],
+                       W=[np.zeros((n, 0))], S=[np.zeros((0, 0))], U=[None], nll=np.zeros(T + 1),
+                       iters=np.zeros(T + 1, dtype=np.int64), dropped=np.zeros(T + 1), G=[None], r0=[None])
+    for k in range(1, T + 1):
+        # predict (Alg. 1): m^- = A m + b, M^- = A M+
+        m_pred = model.a * m[k - 1] + model.b(k)
+        M_pred = model.a * Mplus
+        obs = w.obs(k)
+        if len(obs) == 0:   # IsMissing
+            m_new, M_hat = m_pred, M_pred
+            wk, Wk, S, G, r0 = np.zeros(n), np.zeros((n, 0)), np.zeros((0, 0)), None, None
+        else:
+            Srep = None if S_replay is None else S_replay[k]
+            m_new, M_hat, wk, Wk, S, V, G, r0 = update_iterative(
+                model, m_pred, M_pred, obs, w.yk(k), budget, cg_rtol, Srep)
+            res.nll[k] = _nll_step(G, S, r0)
+        m[k] = m_new
+        var[k] = model.sf2 - np.sum(M_hat * M_hat, axis=1)
+        if U_replay is not None:   # frozen truncation: None = the base run kept the factor
+            U, lam_drop = U_replay[k], None
+            Mplus = M_hat if U is None else M_hat @ U
+        else:
+            Mplus, U, _, lam_drop = truncate(M_hat, rank_r)
+        res.M_hat.append(M_hat)
+        res.M_pred.append(M_pred)
+        res.w.append(wk)
+        res.W.append(Wk)
+        res.S.append(S)
+        res.U.append(U)
+        res.iters[k] = S.shape[1]
+        res.dropped[k] = 0.0 if lam_drop is None else float(np.sum(lam_drop))
+        res.G.append(G if keep_G else None)
+        res.r0.append(r0 if keep_G else None)
+    return res
+
+
+# ----------------------------------------------------------------------------- smoother
+def smoother_run(w, filt: FilterResult, model: Optional[Model] = None, rank_r=None, U_replay=None):
+    """Alg. 3 (CAKS): backward pass k = T-1 .. 0 (readings R5-R7).
+
+    Returns (means, variances, per-step smoother truncation rotations)."""
+    model = model or model_from(w)
+    rank_r = w.rank_r if rank_r is None else rank_r
+    T, n, a = w.T, model.n, model.a
+    ms = np.zeros((T + 1, n))
+    vs = np.zeros((T + 1, n))
+    ms[T] = filt.m[T]
+    vs[T] = filt.var[T]
+    ws = filt.w[T]
+    Ws = filt.W[T]
+    Us: List[Optional[np.ndarray]] = [None] * (T + 1)
+    for k in range(T - 1, -1, -1):
+        X = a * np.concatenate([Ws, ws[:, None]], axis=1)          # A^T [Ws ws]
+        Mk = filt.M_hat[k]
+        PX = model.K_times(X) - Mk @ (Mk.T @ X)                      # P_k A^T [Ws ws]
+        ms[k] = filt.m[k] + PX[:, -1]
+        E = PX[:, :-1]
+        vs[k] = filt.var[k] - np.sum(E * E, axis=1)                 # M^s_k = (M_k, P_k A^T Ws)
+        if k == 0:
+            break
+        Mp = filt.M_pred[k]
+        PmX = model.K_times(X) - Mp @ (Mp.T @ X)                     # P^-_k A^T [Ws ws]
+        Wk = filt.W[k]
+        Y2 = X - Wk @ (Wk.T @ PmX)                                   # (I - W W^T P^-) A^T [Ws ws]
+        ws = filt.w[k] + Y2[:, -1]
+        Wfull = np.concatenate([Wk, Y2[:, :-1]], axis=1)
+        if U_replay is not None:
+            Us[k] = U_replay[k]
+            Ws = Wfull if Us[k] is None else Wfull @ Us[k]
+        else:
+            Ws, Us[k], _, _ = truncate(Wfull, rank_r)
+    return ms, vs, Us
+
+
+# ----------------------------------------------------------------------------- NLL and gradient
+def nll_terms(filt: FilterResult) -> np.ndarray:
+    return filt.nll.copy()
+
+
+def nll_total(filt: FilterResult) -> float:
+    return float(np.sum(filt.nll))
+
+
+def nll_grad_fd(w, h=1e-4, budget=None, rank_r=None):
+    """Central finite-difference gradient of the NLL w.r.t. (log l_x, log l_t, log sigma_f^2,
+    log sigma_n^2) with the actions and truncation rotations of the base run frozen.
+
+    Returns (nll at the base point, gradient[4])."""
+    base = filter_run(w, budget=budget, rank_r=rank_r)
+    theta0 = np.array([w.log_lx, w.log_lt, w.log_sf2, w.log_sn2])
+    g = np.zeros(4)
+    for p in range(4):
+        vals = []
+        for sgn in (+1, -1):
+            th = theta0.copy()
+            th[p] += sgn * h
+            f = filter_run(w, model=model_from(w, *th), budget=budget, rank_r=rank_r,
+                           S_replay=base.S, U_replay=base.U)
+            vals.append(nll_total(f))
+        g[p] = (vals[0] - vals[1]) / (2 * h)
+    return nll_total(base), g

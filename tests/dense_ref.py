@@ -1,0 +1,213 @@
+"""Independent dense FP64 references used to pin the oracle (tests only).
+
+None of this code is shared with `oracle/`: every routine is written from its
+textbook / paper definition with dense matrices.
+
+* `kf_rts`: the Kalman filter (Thm. "Kalman filter") and the RTS smoother
+  (Thm. "RTS smoother") with dense covariances and an explicit smoother gain.
+* `batch_gp`: the iteratively approximated batch GP posterior (Def.
+  "Iteratively approximated batch GP regression") with block-diagonal actions
+  (Prop. "Connecting batch spatio-temporal GP regression and filtering and
+  smoothing"), on the full space-time covariance a^|k-k'| K(x, x').
+* `dense_truncated`: the CAKF / CAKS with dense covariance matrices and the
+  truncation done on the n x n downdate (eig of Sigma - P, resp. of Ws Ws^T),
+  i.e. the outer-product form of Alg. 1 / Alg. 3 without any factors.
+* `batch_nll_grad`: the analytic gradient of the projected batch NLL with
+  frozen actions, 1/2 tr(Gh^-1 S^T dKy S) - 1/2 b^T S^T dKy S b.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def _kern(Xa, Xb, kernel, lx, sf2):
+    d = np.sqrt(((Xa[:, None, :] - Xb[None, :, :]) ** 2).sum(-1))
+    u = d / lx
+    if kernel == 0:
+        return sf2 * np.exp(-u)
+    if kernel == 1:
+        return sf2 * (1 + math.sqrt(3) * u) * np.exp(-math.sqrt(3) * u)
+    return sf2 * (1 + math.sqrt(5) * u + 5 * u * u / 3) * np.exp(-math.sqrt(5) * u)
+
+
+def _dkern_dloglx(Xa, Xb, kernel, lx, sf2):
+    d = np.sqrt(((Xa[:, None, :] - Xb[None, :, :]) ** 2).sum(-1))
+    u = d / lx
+    if kernel == 0:
+        dk = -np.exp(-u)
+    elif kernel == 1:
+        dk = -3 * u * np.exp(-math.sqrt(3) * u)
+    else:
+        dk = -(5.0 / 3.0) * u * (1 + math.sqrt(5) * u) * np.exp(-math.sqrt(5) * u)
+    return sf2 * dk * (-u)        # d/dlog l of k(d/l) = k'(u) * (-u)
+
+
+def _params(w):
+    lx, lt, sf2, sn2 = (math.exp(w.log_lx), math.exp(w.log_lt), math.exp(w.log_sf2), math.exp(w.log_sn2))
+    return lx, lt, sf2, sn2, math.exp(-w.dt / lt)
+
+
+def _mu(w, k):
+    return np.zeros(w.n) if w.prior_mean is None else w.prior_mean[k]
+
+
+def kf_rts(w):
+    """Dense Kalman filter + RTS smoother; returns dict of means/vars (T+1, n) and per-step NLL."""
+    lx, lt, sf2, sn2, a = _params(w)
+    K = _kern(w.coords, w.coords, w.kernel, lx, sf2)
+    n, T = w.n, w.T
+    m, P = _mu(w, 0).copy(), K.copy()
+    mf, Pf, mp, Pp = [m], [P], [None], [None]
+    nll = np.zeros(T + 1)
+    for k in range(1, T + 1):
+        mpk = a * m + (_mu(w, k) - a * _mu(w, k - 1))
+        Ppk = a * a * P + (1 - a * a) * K
+        o = w.obs(k)
+        if len(o):
+            G = Ppk[np.ix_(o, o)] + sn2 * np.eye(len(o))
+            r = w.yk(k) - mpk[o]
+            gain = np.linalg.solve(G, Ppk[o, :]).T
+            m = mpk + gain @ r
+            P = Ppk - gain @ Ppk[o, :]
+            sign, ld = np.linalg.slogdet(2 * np.pi * G)
+            nll[k] = 0.5 * ld + 0.5 * r @ np.linalg.solve(G, r)
+        else:
+            m, P = mpk, Ppk
+        mf.append(m); Pf.append(P); mp.append(mpk); Pp.append(Ppk)
+    ms, Ps = [None] * (T + 1), [None] * (T + 1)
+    ms[T], Ps[T] = mf[T], Pf[T]
+    for k in range(T - 1, -1, -1):
+        J = a * np.linalg.solve(Pp[k + 1].T, Pf[k].T).T          # P_k A^T (P^-_{k+1})^{-1}
+        ms[k] = mf[k] + J @ (ms[k + 1] - mp[k + 1])
+        Ps[k] = Pf[k] + J @ (Ps[k + 1] - Pp[k + 1]) @ J.T
+    return dict(mf=np.array(mf), vf=np.array([np.diag(p) for p in Pf]),
+                ms=np.array(ms), vs=np.array([np.diag(p) for p in Ps]), nll=nll)
+
+
+def _spacetime(w, upto=None):
+    """Observation list Z=(step, index) and the space-time prior blocks."""
+    lx, lt, sf2, sn2, a = _params(w)
+    K = _kern(w.coords, w.coords, w.kernel, lx, sf2)
+    T = w.T if upto is None else upto
+    steps = np.concatenate([np.full(len(w.obs(k)), k) for k in range(1, T + 1)]) if T > 0 else np.zeros(0, int)
+    idx = np.concatenate([w.obs(k) for k in range(1, T + 1)]) if T > 0 else np.zeros(0, int)
+    return K, steps.astype(int), idx.astype(int), a, sn2
+
+
+def batch_gp(w, S_list, upto=None, k_eval=None):
+    """Iteratively approximated batch GP posterior marginals at all grid points of step k_eval,
+    using data of steps 1..upto and block-diagonal actions S = diag(S_1, ..., S_upto)."""
+    K, st, ix, a, sn2 = _spacetime(w, upto)
+    T = w.T if upto is None else upto
+    N = ix.size
+    Kzz = (a ** np.abs(st[:, None] - st[None, :])) * K[np.ix_(ix, ix)]
+    Ky = Kzz + sn2 * np.eye(N)
+    cols = sum(S_list[k].shape[1] for k in range(1, T + 1))
+    S = np.zeros((N, cols))
+    r0 = c0 = 0
+    for k in range(1, T + 1):
+        Sk = S_list[k]
+        S[r0:r0 + Sk.shape[0], c0:c0 + Sk.shape[1]] = Sk
+        r0 += Sk.shape[0]
+        c0 += Sk.shape[1]
+    ybar = np.concatenate([w.yk(k) - _mu(w, k)[w.obs(k)] for k in range(1, T + 1)])
+    C = S @ np.linalg.solve(S.T @ Ky @ S, S.T)
+    kk = T if k_eval is None else k_eval
+    Kxz = (a ** np.abs(kk - st))[None, :] * K[:, ix]
+    mean = _mu(w, kk) + Kxz @ (C @ ybar)
+    var = np.diag(K) - np.einsum("ij,jk,ik->i", Kxz, C, Kxz)
+    Gh = S.T @ Ky @ S
+    yh = S.T @ ybar
+    nll = (0.5 * cols * math.log(2 * math.pi) + 0.5 * np.linalg.slogdet(Gh)[1]
+           + 0.5 * yh @ np.linalg.solve(Gh, yh) - 0.5 * np.linalg.slogdet(S.T @ S)[1])
+    return mean, var, nll
+
+
+def batch_nll_grad(w, S_list):
+    """Analytic d NLL / d(log l_x, log l_t, log sf2, log sn2) of the projected batch NLL, frozen S."""
+    lx, lt, sf2, sn2, a = _params(w)
+    K, st, ix, a, sn2 = _spacetime(w)
+    N = ix.size
+    dk = np.abs(st[:, None] - st[None, :])
+    At = a ** dk
+    Kzz = At * K[np.ix_(ix, ix)]
+    Ky = Kzz + sn2 * np.eye(N)
+    cols = sum(S_list[k].shape[1] for k in range(1, w.T + 1))
+    S = np.zeros((N, cols))
+    r0 = c0 = 0
+    for k in range(1, w.T + 1):
+        Sk = S_list[k]
+        S[r0:r0 + Sk.shape[0], c0:c0 + Sk.shape[1]] = Sk
+        r0 += Sk.shape[0]
+        c0 += Sk.shape[1]
+    ybar = np.concatenate([w.yk(k) - _mu(w, k)[w.obs(k)] for k in range(1, w.T + 1)])
+    Gh = S.T @ Ky @ S
+    b = np.linalg.solve(Gh, S.T @ ybar)
+    Ghi = np.linalg.inv(Gh)
+    dK = [
+        At * _dkern_dloglx(w.coords[ix], w.coords[ix], w.kernel, lx, sf2),
+        Kzz * dk * (w.dt / lt),
+        Kzz,
+        sn2 * np.eye(N),
+    ]
+    g = np.zeros(4)
+    for p, D in enumerate(dK):
+        SDS = S.T @ D @ S
+        g[p] = 0.5 * np.trace(Ghi @ SDS) - 0.5 * b @ SDS @ b
+    return g
+
+
+def dense_truncated(w, S_list, r):
+    """Outer-product (dense covariance) CAKF + CAKS with truncation on the n x n downdates.
+
+    Filter: P^-_k = a^2 P~_{k-1} + (1-a^2) K; update with the given actions S_k;
+    truncation P~_k = K - best_rank_r(K - P_k).  Smoother (Alg. 3 in outer-product
+    form): Omega_k = W_k W_k^T + B Omega~_{k+1} B^T with B = (I - W W^T P^-_k) a and
+    Omega~ = best_rank_r(Omega); mean m^s_k = m_k + P_k a ws_{k+1};
+    cov P^s_k = P_k - a^2 P_k Omega~_{k+1} P_k."""
+    lx, lt, sf2, sn2, a = _params(w)
+    K = _kern(w.coords, w.coords, w.kernel, lx, sf2)
+    n, T = w.n, w.T
+
+    def rank_r(D):
+        if r <= 0:
+            return D
+        lam, U = np.linalg.eigh(D)
+        o = np.argsort(lam)[::-1][:r]
+        return (U[:, o] * lam[o]) @ U[:, o].T
+
+    m, Pt = _mu(w, 0).copy(), K.copy()
+    mf, Pf, Pm, Ww, ww = [m], [K.copy()], [K.copy()], [np.zeros((n, n))], [np.zeros(n)]
+    for k in range(1, T + 1):
+        mpk = a * m + (_mu(w, k) - a * _mu(w, k - 1))
+        Ppk = a * a * Pt + (1 - a * a) * K
+        o = w.obs(k)
+        Sk = S_list[k]
+        if len(o) and Sk.shape[1]:
+            H = np.zeros((len(o), n))
+            H[np.arange(len(o)), o] = 1.0
+            Hs = Sk.T @ H
+            Gh = Hs @ Ppk @ Hs.T + sn2 * Sk.T @ Sk
+            Ginv = np.linalg.inv(Gh)
+            wk = Hs.T @ Ginv @ (Sk.T @ (w.yk(k) - mpk[o]))
+            WW = Hs.T @ Ginv @ Hs
+            m = mpk + Ppk @ wk
+            P = Ppk - Ppk @ WW @ Ppk
+        else:
+            wk, WW, m, P = np.zeros(n), np.zeros((n, n)), mpk, Ppk
+        mf.append(m); Pf.append(P); Pm.append(Ppk); Ww.append(WW); ww.append(wk)
+        Pt = K - rank_r(K - P)
+    ms, vs = [None] * (T + 1), [None] * (T + 1)
+    ms[T], vs[T] = mf[T], np.diag(Pf[T])
+    ws, Om = ww[T], Ww[T]
+    for k in range(T - 1, -1, -1):
+        ms[k] = mf[k] + a * Pf[k] @ ws
+        vs[k] = np.diag(Pf[k] - a * a * Pf[k] @ Om @ Pf[k])
+        if k == 0:
+            break
+        B = a * (np.eye(n) - Ww[k] @ Pm[k])
+        ws = ww[k] + B @ ws
+        Om = rank_r(Ww[k] + B @ Om @ B.T)
+    return dict(mf=np.array(mf), vf=np.array([np.diag(p) for p in Pf]), ms=np.array(ms), vs=np.array(vs))

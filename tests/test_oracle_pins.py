@@ -1,0 +1,186 @@
+"""Pins of the FP64 oracle against results the paper and the mathematics fix (CPU only).
+
+Every check compares the oracle with an independent computation:
+* the scalar Kalman filter written out by hand (n = 1);
+* the dense Kalman filter / RTS smoother at full action budget (the projection
+  then loses nothing, Sec. 3.1; Prop. "Downdate-form Kalman filter"; Prop.
+  "Inverse-free RTS smoother");
+* the iteratively approximated batch GP with block-diagonal actions for any
+  budget without truncation (Prop. "Connecting ... filtering and smoothing");
+* the dense outer-product form of the filter and smoother with truncation on
+  the n x n downdates (Sec. 3.2, Alg. 3);
+* Eckart-Young via a direct SVD of the factor (Sec. 3.2);
+* the analytic gradient of the projected batch NLL with frozen actions;
+* the Matern kernels against scikit-learn's implementation when available.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import dense_ref
+import oracle
+import synth
+from oracle import cakf as oc
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.max(np.abs(a - b)) / max(1e-300, np.max(np.abs(b))))
+
+
+def test_scalar_kalman_closed_form():
+    """n = 1: the CAKF reduces to the scalar Kalman filter (textbook recursion by hand)."""
+    w = synth.small(n=1, m=1, T=7, budget_i=1, rank_r=0, seed=5)
+    f = oracle.filter_run(w)
+    lx, lt, sf2, sn2 = math.exp(w.log_lx), math.exp(w.log_lt), math.exp(w.log_sf2), math.exp(w.log_sn2)
+    a = math.exp(-w.dt / lt)
+    m, P = 0.0, sf2
+    nll = 0.0
+    for k in range(1, w.T + 1):
+        mp, Pp = a * m, a * a * P + (1 - a * a) * sf2
+        y = float(w.yk(k)[0])
+        g = Pp + sn2
+        m = mp + Pp / g * (y - mp)
+        P = Pp - Pp * Pp / g
+        nll += 0.5 * math.log(2 * math.pi * g) + 0.5 * (y - mp) ** 2 / g
+        assert abs(f.m[k, 0] - m) < 1e-12 * max(1, abs(m))
+        assert abs(f.var[k, 0] - P) < 1e-12
+    assert abs(oracle.nll_total(f) - nll) < 1e-10 * abs(nll)
+
+
+@pytest.mark.parametrize("kernel,seasonal", [(synth.MATERN32, True), (synth.MATERN52, False), (synth.MATERN12, False)])
+def test_full_budget_equals_kf_rts(kernel, seasonal):
+    """i_k = m_k, no truncation: CAKF/CAKS = dense KF/RTS (means, variances, NLL)."""
+    w = synth.small(n=36, dim=1, m=9, T=6, budget_i=9, rank_r=0, kernel=kernel, seasonal=seasonal,
+                    missing=(3,), seed=21)
+    f = oracle.filter_run(w)
+    ms, vs, _ = oracle.smoother_run(w, f)
+    ref = dense_ref.kf_rts(w)
+    assert rel(f.m, ref["mf"]) < 1e-9
+    assert rel(f.var, ref["vf"]) < 1e-9
+    assert rel(ms, ref["ms"]) < 1e-9
+    assert rel(vs, ref["vs"]) < 1e-9
+    assert np.allclose(f.nll, ref["nll"], rtol=1e-9, atol=1e-10)
+
+
+@pytest.mark.parametrize("budget", [1, 3, 5])
+def test_partial_budget_equals_batch_gp(budget):
+    """Any budget, no truncation: filter at k = batch GP on data 1..k; smoother = batch GP on all
+    data; sum of NLL terms = projected batch NLL."""
+    w = synth.small(n=30, dim=2, m=10, T=5, budget_i=budget, rank_r=0, seasonal=True, seed=7)
+    f = oracle.filter_run(w)
+    ms, vs, _ = oracle.smoother_run(w, f)
+    for k in range(1, w.T + 1):
+        mb, vb, _ = dense_ref.batch_gp(w, f.S, upto=k, k_eval=k)
+        assert rel(f.m[k], mb) < 1e-9
+        assert rel(f.var[k], vb) < 1e-9
+    for k in range(0, w.T + 1):
+        mb, vb, nb = dense_ref.batch_gp(w, f.S, upto=w.T, k_eval=k)
+        assert rel(ms[k], mb) < 1e-9, k
+        assert rel(vs[k], vb) < 1e-9, k
+    assert abs(oracle.nll_total(f) - nb) < 1e-9 * abs(nb)
+
+
+def test_update_internal_identities():
+    """V^T G V = I per step, CG actions mutually orthogonal, and the batch update (Alg. 2) with the
+    recorded actions gives the same w and W W^T (Prop. on the equivalence of the two updates)."""
+    w = synth.small(n=50, dim=2, m=15, T=4, budget_i=6, rank_r=0, seed=9)
+    f = oracle.filter_run(w, keep_G=True)
+    for k in range(1, w.T + 1):
+        o = w.obs(k)
+        V = f.W[k][o]
+        G = f.G[k]
+        assert np.allclose(V.T @ G @ V, np.eye(V.shape[1]), atol=1e-10)
+        S = f.S[k]
+        SS = S.T @ S
+        assert np.allclose(SS - np.diag(np.diag(SS)), 0, atol=1e-9 * np.max(np.diag(SS)))
+        Gh = S.T @ G @ S
+        v_batch = S @ np.linalg.solve(Gh, S.T @ f.r0[k])
+        assert rel(f.w[k][o], v_batch) < 1e-9
+        assert rel(V @ V.T, S @ np.linalg.solve(Gh, S.T)) < 1e-9
+
+
+def test_truncate_eckart_young():
+    """Truncate keeps the best rank-r part: M+ M+^T equals the rank-r SVD truncation of M M^T and
+    M M^T = M+ M+^T + N N^T with N N^T PSD (Sec. 3.2)."""
+    rng = np.random.default_rng(3)
+    M = rng.standard_normal((40, 12)) @ np.diag(np.logspace(0, -3, 12))
+    Mp, U, lk, ld = oracle.truncate(M, 7)
+    Us, s, _ = np.linalg.svd(M, full_matrices=False)
+    best = (Us[:, :7] * s[:7] ** 2) @ Us[:, :7].T
+    assert rel(Mp @ Mp.T, best) < 1e-12
+    NN = M @ M.T - Mp @ Mp.T
+    assert np.min(np.linalg.eigvalsh(NN)) > -1e-12
+    assert np.allclose(np.sort(np.concatenate([lk, ld]))[::-1], s ** 2, rtol=1e-10)
+    same, U2, _, _ = oracle.truncate(M, 12)
+    assert U2 is None and same is M
+
+
+def test_truncated_run_matches_dense_outer_product():
+    """With truncation: oracle (factors, small Gram eig) = dense outer-product form (n x n eig)."""
+    w = synth.small(n=34, dim=2, m=10, T=7, budget_i=4, rank_r=6, seasonal=True, seed=13)
+    f = oracle.filter_run(w)
+    ms, vs, _ = oracle.smoother_run(w, f)
+    ref = dense_ref.dense_truncated(w, f.S, w.rank_r)
+    assert rel(f.m, ref["mf"]) < 1e-9
+    assert rel(f.var, ref["vf"]) < 1e-9
+    assert rel(ms, ref["ms"]) < 1e-9
+    assert rel(vs, ref["vs"]) < 1e-9
+
+
+def test_truncation_is_conservative_and_rank_large_is_identity():
+    """Same actions: truncation never lowers a marginal variance (Sec. 3.2, computational noise);
+    a rank above the number of columns changes nothing."""
+    w = synth.small(n=40, dim=2, m=12, T=6, budget_i=4, rank_r=5, seed=17)
+    ft = oracle.filter_run(w)
+    fu = oracle.filter_run(w, rank_r=0, S_replay=ft.S, U_replay=[None] * (w.T + 1))
+    assert np.all(ft.var >= fu.var - 1e-12)
+    mst, vst, _ = oracle.smoother_run(w, ft)
+    msu, vsu, _ = oracle.smoother_run(w, fu, rank_r=0)
+    assert np.all(vst >= vsu - 1e-12)
+    fbig = oracle.filter_run(w, rank_r=10 ** 6)
+    f0 = oracle.filter_run(w, rank_r=0)
+    assert rel(fbig.var, f0.var) < 1e-14 and rel(fbig.m, f0.m) < 1e-14
+
+
+def test_fd_gradient_matches_batch_analytic():
+    """Central FD of the oracle NLL (frozen actions) = analytic gradient of the projected batch NLL."""
+    w = synth.small(n=25, dim=2, m=8, T=4, budget_i=3, rank_r=0, seasonal=True, seed=19)
+    nll, g_fd = oracle.nll_grad_fd(w, h=1e-5)
+    f = oracle.filter_run(w)
+    g_an = dense_ref.batch_nll_grad(w, f.S)
+    assert np.allclose(g_fd, g_an, rtol=1e-6, atol=1e-6 * np.max(np.abs(g_an)))
+
+
+def test_matern_against_sklearn():
+    sk = pytest.importorskip("sklearn.gaussian_process.kernels")
+    rng = np.random.default_rng(0)
+    X = rng.uniform(size=(20, 3))
+    for code, nu in [(0, 0.5), (1, 1.5), (2, 2.5)]:
+        ours = oracle.kernel_matrix(X, X, code, 0.37, 1.0)
+        ref = sk.Matern(length_scale=0.37, nu=nu)(X)
+        assert np.allclose(ours, ref, rtol=1e-12, atol=1e-14)
+
+
+def test_pins_catch_planted_mistakes(monkeypatch):
+    """A dropped term in the kernel, or a wrong smoother sign, makes the pins fail."""
+    w = synth.small(n=20, dim=1, m=6, T=4, budget_i=6, rank_r=0, seed=23)
+    ref = dense_ref.kf_rts(w)
+
+    def bad_matern(u, kernel):
+        return np.exp(-math.sqrt(3.0) * u)          # Matern-3/2 without its (1 + sqrt(3) u) factor
+    monkeypatch.setattr(oc, "matern", bad_matern)
+    f = oracle.filter_run(w)
+    assert rel(f.m, ref["mf"]) > 1e-3
+    monkeypatch.undo()
+
+    orig = oc.Model.K_times
+
+    def sign_flip(self, B, rows=None, cols=None):
+        out = orig(self, B, rows, cols)
+        return -out if (rows is None and cols is None) else out   # only the smoother's K X products
+    monkeypatch.setattr(oc.Model, "K_times", sign_flip)
+    f = oracle.filter_run(w)
+    ms, vs, _ = oracle.smoother_run(w, f)
+    assert rel(vs, ref["vs"]) > 1e-3
