@@ -1,0 +1,339 @@
+"""Benchmark: filter + smoother time steps per second of the computation-aware Kalman filter/smoother.
+
+One bench "step" is a full pass of the hot path over the whole series: cakf_filter (CG actions,
+Gram x block finalize, truncation) over k = 1..T followed by cakf_smooth over k = T-1..0, on a
+seeded synthetic workload (default: the 256 x 256 lat-lon sphere grid, n = 65,536, m = 8,192
+observations per step, i = 64 actions, truncation rank r = 512, T = 500 steps).
+
+Prints ONE JSON line on rank 0.  `value` is whole-job time steps per second (sum over ranks of
+T * K / the slowest rank's timed region).  Multi-GPU runs are independent replicas (one series
+per rank, different seeds): the method's recursion is sequential in time and the paper runs on a
+single GPU, so there is no data-path collective.
+
+  python bench.py [--steps K] [--warmup W] [--precision bf16|tf32|fp32|fp64] [--T T] [--config NAME]
+  python bench.py --impl reference ...      # the FP64 oracle on the host cores (bounded sample)
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+DTYPE_NAME = {"bf16": "bf16", "tf32": "tf32", "fp32": "f32", "fp64": "f64"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="bf16", choices=list(DTYPE_NAME))
+    ap.add_argument("--config", default="sphere-65k")
+    ap.add_argument("--T", type=int, default=None, help="override the number of time steps")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-steps", type=int, default=1)
+    return ap.parse_args()
+
+
+def workload(name, T, seed_offset=0, device=None):
+    import synth
+    if name == "sphere-65k":
+        return synth.sphere_65k(T=T or 500, seed=2 + seed_offset, device=device), \
+            "sphere-n65536-m8192-i64-r512 (256x256 lat-lon grid on S^2, extrinsic Matern-3/2 l=0.1, OU l_t=1, dt=0.1, sn2=0.05)"
+    if name == "grid2d-16k":
+        return synth.grid2d_16k(T=T or 200, seed=1 + seed_offset, device=device), \
+            "grid2d-n16384-m2000-i32-r256 (128x128 grid, Matern-5/2 l=0.05, OU l_t=1, dt=0.1, sn2=0.01, seasonal mean)"
+    if name == "sphere-262k":
+        return synth.sphere_262k(T=T or 300, seed=4 + seed_offset, device=device), \
+            "sphere-n262144-m16384-i128-r256 (512x512 sphere grid, Matern-3/2 l=0.05)"
+    if name == "small":
+        return synth.small(n=4096, dim=2, m=512, T=T or 20, budget_i=16, rank_r=64, seed=5 + seed_offset,
+                           device=device), "small-n4096-m512-i16-r64"
+    raise SystemExit(f"unknown config {name}")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+            "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(ws, x):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------------------- CPU leg
+def oracle_sample(w, steps):
+    """Time the FP64 oracle on the first `steps` filter steps of the workload (host cores)."""
+    import oracle
+    import synth
+    sub = w.with_(T=steps, obs_ptr=w.obs_ptr[:steps + 1],
+                  prior_mean=None if w.prior_mean is None else w.prior_mean[:steps + 1])
+    t0 = time.perf_counter()
+    oracle.filter_run(sub)
+    dt = time.perf_counter() - t0
+    return dt, f"oracle filter over steps 1..{steps} of the same workload (n={w.n}, m={int(w.obs_ptr[1])}); " \
+               f"smoother steps excluded (each costs more than a filter step, so this overstates CPU steps/s)"
+
+
+def cpu_cores():
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        n = max((d.get("num_threads", 1) for d in info), default=os.cpu_count())
+        return int(n)
+    except Exception:
+        return os.cpu_count()
+
+
+# --------------------------------------------------------------------------------------- main
+def main():
+    args = parse()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+    import torch
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_2405_08971_gb300 as ck
+    from paper_2405_08971_gb300 import build
+    build.build()
+    w, desc = workload(args.config, args.T, seed_offset=rank, device=dev)
+    T, n = w.T, w.n
+    stream = torch.cuda.current_stream(dev)
+    coords = torch.as_tensor(w.coords, device=dev)
+    obs_idx = torch.as_tensor(w.obs_idx, device=dev)
+    y = torch.as_tensor(w.y, device=dev)
+    mu = None if w.prior_mean is None else torch.as_tensor(w.prior_mean, device=dev)
+    prob = ck.make_problem(coords, w.kernel, w.log_lx, w.log_lt, w.log_sf2, w.log_sn2, T, w.dt, w.obs_ptr,
+                           obs_idx, y, w.budget_i, w.rank_r, precision=args.precision, prior_mean=mu)
+    shape = (T + 1, n)
+    outs = [torch.empty(shape, dtype=torch.float64, device=dev) for _ in range(4)]
+    ctx = ck.Context()
+
+    def one_step():
+        ck.cakf_filter(prob, ctx, outs[0], outs[1], stream=stream.cuda_stream)
+        ck.cakf_smooth(ctx, outs[2], outs[3], stream=stream.cuda_stream)
+
+    for _ in range(max(args.warmup, 0)):
+        one_step()
+    ck.cakf_set_profiling(ctx, True)
+    launches = 0
+    sampler = ClockSampler(local)
+    barrier(ws)
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    prof = {"gram_block_ms": 0.0, "gram_block_launches": 0, "gram_block_flops": 0.0, "gram_block_evals": 0.0,
+            "cg_matvec_ms": 0.0, "cg_matvec_launches": 0, "cg_matvec_evals": 0.0, "eig_ms": 0.0, "eig_calls": 0}
+    for _ in range(args.steps):
+        one_step()
+        st = ck.cakf_get_stats(ctx)
+        launches += int(st["kernel_launches"])
+        for k in prof:
+            prof[k] += st[k]
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    barrier(ws)
+    ms = e0.elapsed_time(e1)
+    ms_max = allmax(ws, ms)
+    value = ws * T * args.steps / (ms_max / 1e3)
+
+    # ---- roofline of the dominant kernel (Gram x block), from live CUDA events
+    pk, pk_src = peaks()
+    gb_avg_ms = prof["gram_block_ms"] / max(1, prof["gram_block_launches"])
+    flops_per_launch = prof["gram_block_flops"] / max(1, prof["gram_block_launches"])
+    achieved = flops_per_launch / (gb_avg_ms / 1e3) / 1e12
+    if args.precision in ("bf16", "tf32"):
+        peak = float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops")))
+        if args.precision == "tf32":
+            peak *= 0.5   # nominal dense tf32 / bf16 ratio (1.1 / 2.25 PF)
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "gram_block (filter finalize + smoother P^- X)",
+                "peak_source": f"{pk_src} bf16_tflops_sustained" + (" x 0.5 (tf32/bf16 nominal)" if args.precision == "tf32" else "")}
+    else:
+        clk = (clocks.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)) * 1e6
+        lanes = 128 if args.precision == "fp32" else 4
+        peak = 152 * lanes * 2 * clk / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "gram_block_simt",
+                "peak_source": f"152 SMs x {lanes} {'FP32' if lanes == 128 else 'FP64'} FMA/clk x 2 x median SM clock"}
+    roof["launches"] = prof["gram_block_launches"]
+    roof["avg_ms"] = gb_avg_ms
+    share = prof["gram_block_ms"] / ms if ms > 0 else None
+
+    line = {
+        "metric": "filter+smoother time steps/sec",
+        "value": value, "unit": "time steps/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": DTYPE_NAME[args.precision], "data": "synthetic (seeded RFF prior sample; ERA5-shaped grid)",
+        "config": {"workload": desc, "n": n, "m_per_step": int(w.obs_ptr[1] - w.obs_ptr[0]), "T": T,
+                   "i": w.budget_i, "r": w.rank_r, "precision": args.precision,
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "l2": "working set larger than L2 (stored factors ~%.0f GB)" % (
+                       (n * (w.rank_r + w.budget_i) * T * (8 if args.precision == 'fp64' else 4)) / 1e9)},
+        "roofline": roof,
+        "gram_block_share_of_step": share,
+        "cg_matvec": {"avg_ms": prof["cg_matvec_ms"] / max(1, prof["cg_matvec_launches"]),
+                      "evals_per_launch": prof["cg_matvec_evals"] / max(1, prof["cg_matvec_launches"])},
+        "eig": {"calls_per_step": None},
+        "clocks": clocks,
+        "gpu_launches": launches,
+    }
+
+    # ---- end to end through the C ABI with pinned host buffers (copies inside the timed region)
+    if not args.no_e2e:
+        pin = lambda a, dt: torch.as_tensor(a).to(dt).pin_memory()
+        hc = pin(w.coords, torch.float64)
+        ho = pin(w.obs_idx, torch.int32)
+        hy = pin(w.y, torch.float64)
+        hm = None if w.prior_mean is None else pin(w.prior_mean, torch.float64)
+        hprob = ck.make_problem(hc, w.kernel, w.log_lx, w.log_lt, w.log_sf2, w.log_sn2, T, w.dt, w.obs_ptr, ho, hy,
+                                w.budget_i, w.rank_r, precision=args.precision, prior_mean=hm)
+        houts = [torch.empty(shape, dtype=torch.float64).pin_memory() for _ in range(4)]
+        ck.cakf_set_profiling(ctx, False)
+        barrier(ws)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ck.cakf_filter(hprob, ctx, houts[0], houts[1], stream=stream.cuda_stream)
+            ck.cakf_smooth(ctx, houts[2], houts[3], stream=stream.cuda_stream)
+        torch.cuda.synchronize(dev)
+        te = allmax(ws, time.perf_counter() - t0)
+        h2d = hc.numel() * 8 + ho.numel() * 4 + hy.numel() * 8 + (0 if hm is None else hm.numel() * 8)
+        d2h = 4 * (T + 1) * n * 8
+        line["e2e"] = {"value": ws * T * args.steps / te, "unit": "time steps/s", "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": d2h}
+
+    # ---- CPU baseline: the FP64 oracle on a bounded sample (rank 0, N = 1 only)
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        secs, sample = oracle_sample(w, args.cpu_sample_steps)
+        line["cpu_baseline"] = {"value": args.cpu_sample_steps / secs, "unit": "time steps/s",
+                                "cores": cpu_cores(), "kind": "oracle", "sample": sample}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_reference(args, ws, rank):
+    """The reference arm: the FP64 oracle (numpy, host cores) on a bounded sample of the same workload."""
+    if rank != 0:
+        return
+    w, desc = workload(args.config, args.T, device=None)
+    steps = max(1, args.cpu_sample_steps)
+    for _ in range(max(0, min(args.warmup, 1))):
+        oracle_sample(w, steps)
+    times = []
+    sample = ""
+    for _ in range(max(1, args.steps)):
+        secs, sample = oracle_sample(w, steps)
+        times.append(secs)
+    tot = sum(times)
+    value = steps * len(times) / tot
+    line = {"metric": "filter+smoother time steps/sec", "value": value, "unit": "time steps/s", "n_gpus": ws,
+            "steps": len(times), "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": desc, "precision": "fp64 oracle"},
+            "cpu_baseline": {"value": value, "unit": "time steps/s", "cores": cpu_cores(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "time steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,174 @@
+/*
+ * cakf.h -- C ABI of the GB300 computation-aware Kalman filter / smoother library (libcakf.so).
+ *
+ * Method: Pfoertner, Wenger, Cockayne, Hennig, "Computation-Aware Kalman Filtering and
+ * Smoothing" (arXiv 2405.08971).  The library runs, on one GPU:
+ *   - the CAKF forward pass (Alg. 1 with the iterative update of the appendix, CG actions of
+ *     Sec. 3.3, and Truncate of Sec. 3.2),
+ *   - the CAKS backward pass (Alg. 3),
+ *   - the negative log likelihood of the projected data and its gradient w.r.t. the four
+ *     hyperparameters (the paper names these as future work; the definition is given at
+ *     cakf_nll below).
+ *
+ * Model (problem statement, Sec. 2; space-time separable Gauss-Markov lemma in the appendix):
+ *   state x_k = values of a spatio-temporal GP on a fixed grid X (n points, dim 1..3),
+ *   spatial kernel  K = sf2 * Matern_nu(|x - x'| / lx),
+ *   OU time factor  A = a I, Q = (1 - a^2) K, a = exp(-dt / lt), x_0 ~ N(mu_0, K),
+ *   observations    y_k = x_k[obs_k] + eps, eps ~ N(0, sn2 I), steps k = 1..T.
+ *
+ * Conventions shared by every entry point
+ *   Pointers   "host or device": the library inspects each pointer (cudaPointerGetAttributes)
+ *              and copies host data itself.  Input arrays are caller-owned and only read during
+ *              the call.  Output arrays are caller-allocated.
+ *   Layout     all 2-D arrays are row-major in the step index: element (k, j) of a (T+1) x n
+ *              array is at [k * n + j].
+ *   Streams    `cuda_stream` is a cudaStream_t owned by the caller (NULL = legacy default
+ *              stream).  Calls return once their results are in the output arrays.
+ *   Errors     every call returns a cakf_status; nothing aborts or throws across the ABI.
+ *              cakf_last_error() gives a message for the calling thread's last failure.
+ *   Threads    a cakf_ctx may be used by one thread at a time.
+ */
+#ifndef CAKF_H
+#define CAKF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CAKF_ABI_VERSION 1
+
+typedef enum {
+  CAKF_OK = 0,
+  CAKF_ERR_ARG = 1,      /* invalid argument (sizes, indices, enum values, NULL)            */
+  CAKF_ERR_CUDA = 2,     /* a CUDA runtime call failed                                      */
+  CAKF_ERR_OOM = 3,      /* device memory exhausted                                         */
+  CAKF_ERR_NUMERIC = 4,  /* non-finite value, or a non-positive-definite projected Gram      */
+  CAKF_ERR_TIMEOUT = 5,  /* a device-side wait exceeded its iteration limit                 */
+  CAKF_ERR_STATE = 6     /* call order violated (e.g. smooth before filter)                 */
+} cakf_status;
+
+enum { CAKF_MATERN12 = 0, CAKF_MATERN32 = 1, CAKF_MATERN52 = 2 };
+
+/* Arithmetic of the kernel-Gram x block products (everything else follows in parentheses). */
+enum {
+  CAKF_FP64 = 0,   /* all in FP64 (reference mode)                                          */
+  CAKF_FP32 = 1,   /* plain FP32 SIMT kernels (factors, CG and tall-skinny GEMMs in FP32)    */
+  CAKF_TF32 = 2,   /* Gram tiles x blocks on tcgen05 kind::tf32, FP32 accumulation          */
+  CAKF_BF16 = 3    /* Gram tiles x blocks on tcgen05 kind::f16 (bf16), FP32 accumulation    */
+};
+
+typedef struct {
+  int32_t abi_version;        /* must equal CAKF_ABI_VERSION                                  */
+  int32_t n;                  /* grid points = state dimension D (OU prior: D' = 1)           */
+  int32_t dim;                /* coordinate dimension, 1..3                                   */
+  const double* coords;       /* n*dim, row-major, host or device; sphere grids pass xyz       */
+  int32_t kernel;             /* CAKF_MATERN12 | CAKF_MATERN32 | CAKF_MATERN52                */
+  double log_lx;              /* log spatial lengthscale                                      */
+  double log_lt;              /* log OU temporal lengthscale                                  */
+  double log_sf2;             /* log output variance sigma_f^2                                */
+  double log_sn2;             /* log observation-noise variance sigma_n^2                     */
+  int32_t T;                  /* number of steps with data; states are k = 0..T              */
+  double dt;                  /* time between steps                                           */
+  const int32_t* obs_ptr;     /* T+1 offsets, HOST: step k (1-based) owns [obs_ptr[k-1],
+                                 obs_ptr[k]); obs_ptr[0] = 0; an empty range = no data       */
+  const int32_t* obs_idx;     /* obs_ptr[T] grid indices in [0, n), distinct within a step;
+                                 host or device                                               */
+  const double* y;            /* obs_ptr[T] observations, host or device                      */
+  const double* prior_mean;   /* NULL (zero mean) or (T+1)*n known prior mean mu_k, host/dev  */
+  int32_t budget_i;           /* action budget per step (CG iterations), >= 1                 */
+  int32_t rank_r;             /* truncation rank of the downdate factors; <= 0: no truncation */
+  double cg_rtol;             /* stop a step's CG early when ||r|| <= cg_rtol ||r0||; 0 = never */
+  int32_t precision;          /* CAKF_FP64 | CAKF_FP32 | CAKF_TF32 | CAKF_BF16                 */
+  const double* replay_actions; /* NULL, or frozen actions: for each step k the m_k x i_k
+                                 column-major block S_k, concatenated over k = 1..T (host)    */
+  const int32_t* replay_counts; /* with replay_actions: T+1 entries, i_k for k = 0..T (host)  */
+} cakf_problem;
+
+typedef struct cakf_ctx cakf_ctx;   /* library-owned state; holds the stored factors */
+
+typedef struct {
+  double filter_ms;           /* device time of the last cakf_filter (CUDA events)            */
+  double smooth_ms;           /* device time of the last cakf_smooth                          */
+  double gram_block_ms;       /* summed device time of the Gram x block launches (profiling on)*/
+  int64_t gram_block_launches;
+  double gram_block_flops;    /* algorithmic flops of those launches: 2 * rows * cols * width  */
+  double gram_block_evals;    /* kernel-matrix entries evaluated by those launches            */
+  double cg_matvec_ms;        /* summed device time of the CG Gram matvec launches            */
+  int64_t cg_matvec_launches;
+  double cg_matvec_evals;
+  double eig_ms;              /* summed device time of the FP64 eigensolver calls             */
+  int64_t eig_calls;
+  int64_t kernel_launches;    /* kernels this library launched in the last filter + smooth    */
+  int64_t device_bytes;       /* device memory held by the context                            */
+} cakf_stats;
+
+/*
+ * cakf_filter -- run the CAKF over k = 1..T (Alg. 1; update: appendix algorithm "CAKF Update
+ * Step (Iterative Version)"; Truncate: Sec. 3.2).
+ *   p         problem description (read during the call only).
+ *   ctx_inout *ctx_inout == NULL: a new context is created and returned there.  Otherwise the
+ *             given context is reused (its buffers are kept when the sizes fit).
+ *   mean_out  (T+1)*n filter means m_k (host or device), or NULL.
+ *   var_out   (T+1)*n filter marginal variances diag(P_k) = sf2 - rowsumsq(M_k) taken before
+ *             truncation (host or device), or NULL.
+ * The context keeps per-step factors for cakf_smooth / cakf_nll / cakf_nll_backward.
+ * Errors: CAKF_ERR_ARG (sizes, indices out of range, abi_version), CAKF_ERR_OOM,
+ *         CAKF_ERR_NUMERIC (non-finite result or non-positive-definite action Gram),
+ *         CAKF_ERR_CUDA, CAKF_ERR_TIMEOUT.
+ */
+int cakf_filter(const cakf_problem* p, cakf_ctx** ctx_inout, double* mean_out, double* var_out,
+                void* cuda_stream);
+
+/*
+ * cakf_smooth -- run the CAKS backward pass k = T-1 .. 0 (Alg. 3) on the filter state held by
+ * ctx.  Outputs (T+1)*n smoother means and marginal variances (host or device, or NULL).
+ * Errors: CAKF_ERR_STATE when no successful cakf_filter preceded it on this context.
+ */
+int cakf_smooth(cakf_ctx* ctx, double* mean_out, double* var_out, void* cuda_stream);
+
+/*
+ * cakf_nll -- negative log likelihood of the projected data of the last cakf_filter:
+ *   NLL = sum_k [ 1/2 logdet(2 pi S_k^T G_k S_k) + 1/2 r_k^T S_k (S_k^T G_k S_k)^-1 S_k^T r_k
+ *                 - 1/2 logdet(S_k^T S_k) ],
+ *   G_k = H_k P^-_k H_k^T + sn2 I, r_k = y_k - H_k m^-_k, S_k the actions (eq. proj-observation,
+ *   Sec. 3.1).  It is accumulated during the filter from the G-orthogonal iteration
+ *   (S^T G S = R^T R with R_jj^2 = eta_j) and the FP64 Cholesky factor of S^T S.
+ *   nll_out: one double (host).
+ */
+int cakf_nll(cakf_ctx* ctx, double* nll_out);
+
+/*
+ * cakf_nll_backward -- gradient of cakf_nll w.r.t. (log_lx, log_lt, log_sf2, log_sn2) with the
+ * actions S_k and truncation rotations of the last filter run held fixed (exact inference in
+ * the fixed modified observation model, Sec. 3.1).  grad_out: 4 doubles (host).
+ */
+int cakf_nll_backward(cakf_ctx* ctx, double* grad_out);
+
+/*
+ * cakf_get_actions -- copy the actions used by the last filter run (host outputs):
+ *   counts_out  T+1 entries i_k (0 for k = 0 and for steps without data);
+ *   actions_out the m_k x i_k column-major blocks for k = 1..T, concatenated (size
+ *               sum_k m_k * i_k), suitable for cakf_problem.replay_actions.  May be NULL to
+ *               query the counts only.
+ */
+int cakf_get_actions(cakf_ctx* ctx, double* actions_out, int32_t* counts_out);
+
+/* cakf_get_stats -- timings and counters of the last filter / smooth calls (host output). */
+int cakf_get_stats(const cakf_ctx* ctx, cakf_stats* out);
+
+/* cakf_set_profiling -- when on, the hot kernels are bracketed by CUDA events on their stream
+ * and their device times are summed into cakf_stats (adds one event pair per launch). */
+int cakf_set_profiling(cakf_ctx* ctx, int on);
+
+/* cakf_free -- release a context and all device memory it holds.  NULL is accepted. */
+void cakf_free(cakf_ctx* ctx);
+
+/* cakf_last_error -- message of the calling thread's last failed call ("" if none). */
+const char* cakf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CAKF_H */

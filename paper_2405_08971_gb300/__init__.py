@@ -1,0 +1,11 @@
+"""GB300-native computation-aware Kalman filter and smoother (arXiv 2405.08971).
+
+The compute path is libcakf.so (CUDA kernels for sm_103a behind the C ABI in
+include/cakf.h); `binding` marshals arguments to it.  Importing the package does
+not load the library; the first call does, and fails loudly if it is missing.
+"""
+from .binding import (  # noqa: F401
+    Context, CakfError, make_problem, problem_from_workload, cakf_filter, cakf_smooth, cakf_nll,
+    cakf_nll_backward, cakf_get_actions, cakf_get_stats, cakf_set_profiling, pack_actions, lib,
+    FP64, FP32, TF32, BF16, MATERN12, MATERN32, MATERN52,
+)

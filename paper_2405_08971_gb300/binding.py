@@ -1,0 +1,259 @@
+"""Thin Python binding of libcakf.so (the C ABI in include/cakf.h).
+
+Argument marshalling only: every step of the filter, smoother and likelihood
+runs inside the library's CUDA kernels.  Arrays may be numpy arrays (host) or
+torch tensors (host or CUDA); device tensors are passed by pointer.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcakf.so")
+
+ABI_VERSION = 1
+OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_NUMERIC, ERR_TIMEOUT, ERR_STATE = range(7)
+MATERN12, MATERN32, MATERN52 = 0, 1, 2
+FP64, FP32, TF32, BF16 = 0, 1, 2, 3
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32": TF32, "bf16": BF16}
+STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_NUMERIC", 5: "ERR_TIMEOUT", 6: "ERR_STATE"}
+
+
+class cakf_problem(C.Structure):
+    _fields_ = [
+        ("abi_version", C.c_int32), ("n", C.c_int32), ("dim", C.c_int32), ("coords", C.c_void_p),
+        ("kernel", C.c_int32), ("log_lx", C.c_double), ("log_lt", C.c_double), ("log_sf2", C.c_double),
+        ("log_sn2", C.c_double), ("T", C.c_int32), ("dt", C.c_double), ("obs_ptr", C.c_void_p),
+        ("obs_idx", C.c_void_p), ("y", C.c_void_p), ("prior_mean", C.c_void_p), ("budget_i", C.c_int32),
+        ("rank_r", C.c_int32), ("cg_rtol", C.c_double), ("precision", C.c_int32),
+        ("replay_actions", C.c_void_p), ("replay_counts", C.c_void_p),
+    ]
+
+
+class cakf_stats(C.Structure):
+    _fields_ = [
+        ("filter_ms", C.c_double), ("smooth_ms", C.c_double), ("gram_block_ms", C.c_double),
+        ("gram_block_launches", C.c_int64), ("gram_block_flops", C.c_double), ("gram_block_evals", C.c_double),
+        ("cg_matvec_ms", C.c_double), ("cg_matvec_launches", C.c_int64), ("cg_matvec_evals", C.c_double),
+        ("eig_ms", C.c_double), ("eig_calls", C.c_int64), ("kernel_launches", C.c_int64),
+        ("device_bytes", C.c_int64),
+    ]
+
+
+class CakfError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """Load libcakf.so (fails loudly when it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libcakf.so not built ({LIB_PATH}); run paper_2405_08971_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, i32p = C.c_void_p, C.POINTER(C.c_int32)
+        L.cakf_filter.argtypes = [C.POINTER(cakf_problem), C.POINTER(vp), vp, vp, vp]
+        L.cakf_smooth.argtypes = [vp, vp, vp, vp]
+        L.cakf_nll.argtypes = [vp, C.POINTER(C.c_double)]
+        L.cakf_nll_backward.argtypes = [vp, C.POINTER(C.c_double)]
+        L.cakf_get_actions.argtypes = [vp, vp, i32p]
+        L.cakf_get_stats.argtypes = [vp, C.POINTER(cakf_stats)]
+        L.cakf_set_profiling.argtypes = [vp, C.c_int]
+        L.cakf_free.argtypes = [vp]
+        L.cakf_free.restype = None
+        L.cakf_last_error.restype = C.c_char_p
+        for f in ("cakf_filter", "cakf_smooth", "cakf_nll", "cakf_nll_backward", "cakf_get_actions",
+                  "cakf_get_stats", "cakf_set_profiling"):
+            getattr(L, f).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(code):
+    if code != OK:
+        raise CakfError(code, lib().cakf_last_error().decode())
+
+
+def _ptr(x, dtype):
+    """(pointer, keepalive) for a numpy array / torch tensor, converting host data as needed."""
+    if x is None:
+        return None, None
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            want = {np.float64: torch.float64, np.int32: torch.int32}[dtype]
+            t = x if (x.dtype == want and x.is_contiguous()) else x.to(want).contiguous()
+            return t.data_ptr(), t
+    except ImportError:
+        pass
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a.ctypes.data, a
+
+
+class Context:
+    """Owns a cakf_ctx (the stored per-step factors of a filter run)."""
+
+    def __init__(self):
+        self.handle = C.c_void_p(None)
+        self.T = None
+        self.n = None
+
+    def close(self):
+        if self.handle:
+            lib().cakf_free(self.handle)
+            self.handle = C.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_problem(coords, kernel, log_lx, log_lt, log_sf2, log_sn2, T, dt, obs_ptr, obs_idx, y, budget_i, rank_r,
+                 precision="fp32", prior_mean=None, cg_rtol=0.0, replay_actions=None, replay_counts=None):
+    """Build a cakf_problem; returns (struct, keepalive list)."""
+    keep = []
+    p = cakf_problem()
+    p.abi_version = ABI_VERSION
+    cp, k1 = _ptr(coords, np.float64)
+    keep.append(k1)
+    shape = tuple(k1.shape) if hasattr(k1, "shape") else None
+    p.n = int(shape[0])
+    p.dim = int(shape[1]) if len(shape) > 1 else 1
+    p.coords = cp
+    p.kernel = int(kernel)
+    p.log_lx, p.log_lt, p.log_sf2, p.log_sn2 = float(log_lx), float(log_lt), float(log_sf2), float(log_sn2)
+    p.T = int(T)
+    p.dt = float(dt)
+    op = np.ascontiguousarray(obs_ptr, dtype=np.int32)
+    keep.append(op)
+    p.obs_ptr = op.ctypes.data
+    ip, k2 = _ptr(obs_idx, np.int32)
+    yp, k3 = _ptr(y, np.float64)
+    mp, k4 = _ptr(prior_mean, np.float64)
+    keep += [k2, k3, k4]
+    p.obs_idx, p.y, p.prior_mean = ip, yp, mp
+    p.budget_i, p.rank_r = int(budget_i), int(rank_r)
+    p.cg_rtol = float(cg_rtol)
+    p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    if replay_actions is not None:
+        ra = np.ascontiguousarray(replay_actions, dtype=np.float64)
+        rc = np.ascontiguousarray(replay_counts, dtype=np.int32)
+        keep += [ra, rc]
+        p.replay_actions, p.replay_counts = ra.ctypes.data, rc.ctypes.data
+    return p, keep
+
+
+def problem_from_workload(w, precision="fp32", cg_rtol=0.0, replay=None, budget_i=None, rank_r=None, **hp):
+    """cakf_problem of a `synth.Workload`-like object (any object with the same fields)."""
+    ra = rc = None
+    if replay is not None:
+        ra, rc = replay
+    return make_problem(w.coords, w.kernel, hp.get("log_lx", w.log_lx), hp.get("log_lt", w.log_lt),
+                        hp.get("log_sf2", w.log_sf2), hp.get("log_sn2", w.log_sn2), w.T, w.dt, w.obs_ptr,
+                        w.obs_idx, w.y, w.budget_i if budget_i is None else budget_i,
+                        w.rank_r if rank_r is None else rank_r, precision=precision, prior_mean=w.prior_mean,
+                        cg_rtol=cg_rtol, replay_actions=ra, replay_counts=rc)
+
+
+def _out(arr, shape):
+    """Output buffer: numpy (host) or a provided torch tensor / numpy array."""
+    if arr is None:
+        arr = np.empty(shape, dtype=np.float64)
+    try:
+        import torch
+        if isinstance(arr, torch.Tensor):
+            assert arr.dtype == torch.float64 and arr.is_contiguous() and tuple(arr.shape) == shape
+            return arr.data_ptr(), arr
+    except ImportError:
+        pass
+    assert arr.dtype == np.float64 and arr.flags.c_contiguous and arr.shape == shape
+    return arr.ctypes.data, arr
+
+
+def cakf_filter(problem, ctx: Optional[Context] = None, mean_out=None, var_out=None, stream=None,
+                want_outputs=True):
+    """Run the CAKF (Alg. 1).  Returns (ctx, means, variances) with (T+1, n) outputs."""
+    p, keep = problem
+    ctx = ctx or Context()
+    shape = (p.T + 1, p.n)
+    mo = vo = None
+    mp = vp = None
+    if want_outputs:
+        mp, mo = _out(mean_out, shape)
+        vp, vo = _out(var_out, shape)
+    _check(lib().cakf_filter(C.byref(p), C.byref(ctx.handle), mp, vp, stream))
+    ctx.T, ctx.n = p.T, p.n
+    return ctx, mo, vo
+
+
+def cakf_smooth(ctx: Context, mean_out=None, var_out=None, stream=None):
+    """Run the CAKS (Alg. 3) on the context's filter state.  Returns (means, variances)."""
+    if ctx.T is None:   # no filter run: let the library report the state error
+        _check(lib().cakf_smooth(ctx.handle, None, None, stream))
+    shape = (ctx.T + 1, ctx.n)
+    mp, mo = _out(mean_out, shape)
+    vp, vo = _out(var_out, shape)
+    _check(lib().cakf_smooth(ctx.handle, mp, vp, stream))
+    return mo, vo
+
+
+def cakf_nll(ctx: Context) -> float:
+    v = C.c_double()
+    _check(lib().cakf_nll(ctx.handle, C.byref(v)))
+    return v.value
+
+
+def cakf_nll_backward(ctx: Context) -> np.ndarray:
+    g = (C.c_double * 4)()
+    _check(lib().cakf_nll_backward(ctx.handle, g))
+    return np.array(list(g))
+
+
+def cakf_get_actions(ctx: Context, obs_ptr):
+    """Actions of the last filter run: (list of per-step m_k x i_k arrays, counts)."""
+    counts = np.zeros(ctx.T + 1, dtype=np.int32)
+    _check(lib().cakf_get_actions(ctx.handle, None, counts.ctypes.data_as(C.POINTER(C.c_int32))))
+    obs_ptr = np.asarray(obs_ptr)
+    sizes = [(int(obs_ptr[k] - obs_ptr[k - 1]), int(counts[k])) for k in range(1, ctx.T + 1)]
+    flat = np.zeros(sum(a * b for a, b in sizes), dtype=np.float64)
+    _check(lib().cakf_get_actions(ctx.handle, flat.ctypes.data, counts.ctypes.data_as(C.POINTER(C.c_int32))))
+    out = [np.zeros((0, 0))]
+    off = 0
+    for m, c in sizes:
+        out.append(flat[off:off + m * c].reshape(c, m).T.copy())
+        off += m * c
+    return out, counts
+
+
+def pack_actions(S_list, T):
+    """Concatenated column-major action blocks + counts, the replay format of cakf_problem."""
+    counts = np.zeros(T + 1, dtype=np.int32)
+    parts = []
+    for k in range(1, T + 1):
+        S = np.asarray(S_list[k], dtype=np.float64)
+        counts[k] = S.shape[1] if S.ndim == 2 else 0
+        if counts[k]:
+            parts.append(S.T.ravel())
+    flat = np.concatenate(parts) if parts else np.zeros(0)
+    return flat, counts
+
+
+def cakf_get_stats(ctx: Context) -> dict:
+    s = cakf_stats()
+    _check(lib().cakf_get_stats(ctx.handle, C.byref(s)))
+    return {f: getattr(s, f) for f, _ in cakf_stats._fields_}
+
+
+def cakf_set_profiling(ctx: Context, on: bool):
+    _check(lib().cakf_set_profiling(ctx.handle, 1 if on else 0))

@@ -1,0 +1,922 @@
+// Host orchestration of the CAKF forward pass and CAKS backward pass behind the C ABI of cakf.h.
+//
+// Device data layout (all factors column-major, leading dimension ldn = n rounded up to 128):
+//   X        n coordinate records (C4<T>, pre-scaled by c_nu / l_x)
+//   Mplus[k] n x c_k truncated downdate factor M+_k, k = 0..T (c_k <= r); its columns are kept
+//            orthogonal with squared norms lam_k (every truncation rotates onto the eigenbasis),
+//            so the leading block of the next truncation Gram is diag(a^2 lam_k)
+//   PVv[k]   n x (i_k + 1): [P^-_k W_k, P^-_k w_k]  (the new factor columns and the mean shift)
+//   Vv[k]    m_k x (i_k + 1): [V_k, v_k] -- G-orthonormal directions and solution coefficients
+//   S[k]     m_k x i_k actions
+//   mf, vf   (T+1) x n filter means / variances (FP64)
+#include <cstring>
+#include <cstdio>
+#include <string>
+#include <vector>
+#include <memory>
+#include <cmath>
+#include "cakf.h"
+#include "internal.h"
+
+using namespace cakf;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) { cudaGetLastError(); return false; }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct cakf_ctx {
+  // problem
+  int n = 0, dim = 0, kernel = 1, T = 0, budget = 0, rank_r = 0, precision = 1;
+  double lx = 1, lt = 1, sf2 = 1, sn2 = 1, dt = 1, a = 1, cg_rtol = 0;
+  bool has_mu = false, replay = false;
+  std::vector<int> obs_ptr, icap, mcols, replay_counts;
+  // sizes
+  int ldn = 0, mmax = 0, rmax = 0, imax = 0, nmax_eig = 0, cwmax = 0;
+  std::vector<size_t> off_M, off_PV, off_V, off_S;
+  // device memory
+  std::vector<DevBuf> bufs;
+  size_t dev_bytes = 0;
+  void* X = nullptr;       // C4<T>
+  int* obs = nullptr;
+  double* y = nullptr;
+  double* mu = nullptr;
+  double* mf = nullptr;
+  double* vf = nullptr;
+  void* Mpool = nullptr;
+  void* PVpool = nullptr;
+  void* Vpool = nullptr;
+  void* Spool = nullptr;
+  double* rep = nullptr;   // replayed actions (device, double)
+  std::vector<size_t> off_rep;
+  double* nll = nullptr;   // T+1
+  double* eta = nullptr;   // (T+1) * budget
+  double* alpha = nullptr;
+  int* count = nullptr;    // T+1
+  int* err = nullptr;      // device error flag
+  int* active = nullptr;
+  double* r0sq = nullptr;
+  // workspace
+  double *mpred = nullptr, *rs_plus = nullptr, *rs_pw = nullptr, *lam = nullptr, *lam2 = nullptr;
+  void *Xo = nullptr, *Mo = nullptr, *rv = nullptr, *r0v = nullptr, *sv = nullptr, *gv = nullptr, *GV = nullptr,
+       *part = nullptr, *tv = nullptr;
+  double* dots = nullptr;
+  double* dots2 = nullptr;
+  double* part64 = nullptr;
+  size_t part64_elems = 0;
+  double* gram = nullptr;
+  double* small = nullptr;   // scratch for small FP64 matrices
+  size_t small_elems = 0;
+  double* U64 = nullptr;
+  void* UT = nullptr;
+  void* eigw = nullptr;
+  size_t eigw_bytes = 0;
+  double* wv = nullptr;
+  // smoother
+  void *WsA = nullptr, *WsB = nullptr, *wsA = nullptr, *wsB = nullptr, *Xs = nullptr, *Y = nullptr, *Xobs = nullptr,
+       *Fb = nullptr;
+  double* Gws = nullptr;
+  double* Gws2 = nullptr;
+  // tensor-core operand staging (bf16 / tf32 paths)
+  void* Bpack = nullptr;
+  size_t Bpack_bytes = 0;
+  double* coords64 = nullptr;
+  double* ms_dev = nullptr;   // smoother outputs when the caller passes host arrays
+  double* vs_dev = nullptr;
+  // state
+  bool filtered = false;
+  long long launch_base = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bool profiling = false;
+  cakf_stats stats{};
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_gb, prof_mv, prof_eig;
+  std::vector<double> prof_gb_flops, prof_gb_evals, prof_mv_evals;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+
+  ~cakf_ctx() { release(); }
+
+  void release() {
+    for (auto& b : bufs) if (b.p) cudaFree(b.p);
+    bufs.clear();
+    dev_bytes = 0;
+    for (auto e : ev_pool) cudaEventDestroy(e);
+    ev_pool.clear();
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    ev0 = ev1 = nullptr;
+  }
+
+  template <class P> int alloc(P*& out, size_t bytes) {
+    void* p = nullptr;
+    bytes = std::max<size_t>(bytes, 16);
+    cudaError_t ce = cudaMalloc(&p, bytes);
+    if (ce != cudaSuccess) {
+      cudaGetLastError();
+      out = nullptr;
+      return fail(CAKF_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(ce));
+    }
+    bufs.push_back({p, bytes});
+    dev_bytes += bytes;
+    out = (P*)p;
+    return CAKF_OK;
+  }
+
+  cudaEvent_t ev() {
+    if (ev_used >= ev_pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      ev_pool.push_back(e);
+    }
+    return ev_pool[ev_used++];
+  }
+};
+
+namespace {
+
+size_t elem_size(int precision) { return precision == CAKF_FP64 ? 8 : 4; }
+
+// ------------------------------------------------------------------------------------ planning
+int plan_and_alloc(cakf_ctx* c, const cakf_problem* p) {
+  const int T = p->T;
+  c->obs_ptr.assign(p->obs_ptr, p->obs_ptr + T + 1);
+  c->icap.assign(T + 1, 0);
+  c->mcols.assign(T + 1, 0);
+  c->mmax = 0;
+  for (int k = 1; k <= T; ++k) {
+    int mk = c->obs_ptr[k] - c->obs_ptr[k - 1];
+    c->mmax = std::max(c->mmax, mk);
+    int ic = c->replay ? c->replay_counts[k] : std::min(c->budget, mk);
+    if (mk == 0) ic = 0;
+    c->icap[k] = ic;
+    int prev = c->mcols[k - 1];
+    c->mcols[k] = (c->rank_r > 0) ? std::min(c->rank_r, prev + ic) : prev + ic;
+  }
+  c->imax = 0;
+  c->rmax = 0;
+  for (int k = 0; k <= T; ++k) { c->imax = std::max(c->imax, c->icap[k]); c->rmax = std::max(c->rmax, c->mcols[k]); }
+  c->ldn = round_up(std::max(c->n, 1), 128);
+  // smoother width bound: rank (after truncation) or the untruncated accumulation
+  int cw = 0, cwmax = 0;
+  for (int k = T; k >= 1; --k) {
+    cw = (k == T) ? c->icap[T] : ((c->rank_r > 0) ? std::min(c->rank_r, cw + c->icap[k]) : cw + c->icap[k]);
+    cwmax = std::max(cwmax, cw);
+    // the pre-truncation width at step k is icap[k] + previous cw
+  }
+  int cwfull = 0;
+  {
+    int cc = c->icap[T];
+    cwfull = cc;
+    for (int k = T - 1; k >= 1; --k) {
+      int full = c->icap[k] + cc;
+      cwfull = std::max(cwfull, full);
+      cc = (c->rank_r > 0) ? std::min(c->rank_r, full) : full;
+    }
+  }
+  c->cwmax = std::max(cwmax, 1);
+  int Nf = 0;
+  for (int k = 1; k <= T; ++k) Nf = std::max(Nf, c->mcols[k - 1] + c->icap[k]);
+  c->nmax_eig = std::max({Nf, cwfull, 1});
+  const int wmax = std::max(c->cwmax, cwfull) + 1;   // width of the smoother Gram x block
+
+  const size_t es = elem_size(c->precision);
+  const size_t ldn = c->ldn;
+  // per-step pools
+  c->off_M.assign(T + 2, 0);
+  c->off_PV.assign(T + 2, 0);
+  c->off_V.assign(T + 2, 0);
+  c->off_S.assign(T + 2, 0);
+  for (int k = 0; k <= T; ++k) {
+    int mk = (k == 0) ? 0 : c->obs_ptr[k] - c->obs_ptr[k - 1];
+    c->off_M[k + 1] = c->off_M[k] + ldn * c->mcols[k];
+    c->off_PV[k + 1] = c->off_PV[k] + (c->icap[k] ? ldn * (c->icap[k] + 1) : 0);
+    c->off_V[k + 1] = c->off_V[k] + (size_t)mk * (c->icap[k] + 1);
+    c->off_S[k + 1] = c->off_S[k] + (size_t)mk * c->icap[k];
+  }
+  const size_t Ntot = c->obs_ptr[T];
+  int rc;
+  const size_t n = c->n;
+  if ((rc = c->alloc(c->X, n * 4 * es))) return rc;
+  if ((rc = c->alloc(c->coords64, n * 3 * sizeof(double)))) return rc;
+  if ((rc = c->alloc(c->obs, std::max<size_t>(Ntot, 1) * sizeof(int)))) return rc;
+  if ((rc = c->alloc(c->y, std::max<size_t>(Ntot, 1) * sizeof(double)))) return rc;
+  if (c->has_mu && (rc = c->alloc(c->mu, (size_t)(T + 1) * n * sizeof(double)))) return rc;
+  if ((rc = c->alloc(c->mf, (size_t)(T + 1) * n * sizeof(double)))) return rc;
+  if ((rc = c->alloc(c->vf, (size_t)(T + 1) * n * sizeof(double)))) return rc;
+  if ((rc = c->alloc(c->Mpool, c->off_M[T + 1] * es))) return rc;
+  if ((rc = c->alloc(c->PVpool, c->off_PV[T + 1] * es))) return rc;
+  if ((rc = c->alloc(c->Vpool, c->off_V[T + 1] * es))) return rc;
+  if ((rc = c->alloc(c->Spool, c->off_S[T + 1] * es))) return rc;
+  if (c->replay) {
+    c->off_rep.assign(T + 2, 0);
+    for (int k = 0; k <= T; ++k) {
+      int mk = (k == 0) ? 0 : c->obs_ptr[k] - c->obs_ptr[k - 1];
+      c->off_rep[k + 1] = c->off_rep[k] + (size_t)mk * c->icap[k];
+    }
+    if ((rc = c->alloc(c->rep, c->off_rep[T + 1] * sizeof(double)))) return rc;
+  }
+  const int B = std::max(c->budget, c->imax);
+  if ((rc = c->alloc(c->nll, (T + 1) * sizeof(double)))) return rc;
+  if ((rc = c->alloc(c->eta, (size_t)(T + 1) * B * sizeof(double)))) return rc;
+  if ((rc = c->alloc(c->alpha, (size_t)(T + 1) * B * sizeof(double)))) return rc;
+  if ((rc = c->alloc(c->count, (T + 1) * sizeof(int)))) return rc;
+  if ((rc = c->alloc(c->err, 16))) return rc;
+  if ((rc = c->alloc(c->active, 16))) return rc;
+  if ((rc = c->alloc(c->r0sq, 16))) return rc;
+  if ((rc = c->alloc(c->mpred, n * sizeof(double)))) return rc;
+  if ((rc = c->alloc(c->rs_plus, n * sizeof(double)))) return rc;
+  if ((rc = c->alloc(c->rs_pw, n * sizeof(double)))) return rc;
+  const size_t NE = c->nmax_eig;
+  if ((rc = c->alloc(c->lam, NE * sizeof(double)))) return rc;
+  if ((rc = c->alloc(c->lam2, NE * sizeof(double)))) return rc;
+  const size_t mm = std::max(c->mmax, 1);
+  if ((rc = c->alloc(c->Xo, mm * 4 * es))) return rc;
+  if ((rc = c->alloc(c->Mo, mm * std::max(c->rmax, 1) * es))) return rc;
+  if ((rc = c->alloc(c->rv, mm * es))) return rc;
+  if ((rc = c->alloc(c->r0v, mm * es))) return rc;
+  if ((rc = c->alloc(c->sv, mm * es))) return rc;
+  if ((rc = c->alloc(c->gv, mm * es))) return rc;
+  if ((rc = c->alloc(c->GV, mm * std::max(B, 1) * es))) return rc;
+  if ((rc = c->alloc(c->part, mm * 32 * es))) return rc;
+  if ((rc = c->alloc(c->tv, std::max<size_t>(c->rmax, 1) * es))) return rc;
+  if ((rc = c->alloc(c->dots, (B + 8) * sizeof(double)))) return rc;
+  if ((rc = c->alloc(c->dots2, (B + 8) * sizeof(double)))) return rc;
+  c->part64_elems = std::max<size_t>(size_t(1) << 22, NE * NE * 4);
+  if ((rc = c->alloc(c->part64, c->part64_elems * sizeof(double)))) return rc;
+  if ((rc = c->alloc(c->gram, NE * NE * sizeof(double)))) return rc;
+  c->small_elems = 8 * (NE * (size_t)wmax + NE * NE) + 64;
+  if ((rc = c->alloc(c->small, c->small_elems * sizeof(double)))) return rc;
+  if ((rc = c->alloc(c->U64, NE * NE * sizeof(double)))) return rc;
+  if ((rc = c->alloc(c->UT, NE * NE * es))) return rc;
+  if ((rc = c->alloc(c->wv, NE * sizeof(double)))) return rc;
+  c->eigw_bytes = eig_workspace_bytes((int)NE);
+  if ((rc = c->alloc(c->eigw, c->eigw_bytes))) return rc;
+  const size_t wsw = std::max(c->cwmax, cwfull);
+  if ((rc = c->alloc(c->WsA, ldn * std::max<size_t>(wsw, 1) * es))) return rc;
+  if ((rc = c->alloc(c->WsB, ldn * std::max<size_t>(wsw, 1) * es))) return rc;
+  if ((rc = c->alloc(c->wsA, ldn * es))) return rc;
+  if ((rc = c->alloc(c->wsB, ldn * es))) return rc;
+  const size_t wfin = std::max<size_t>(wmax, c->imax + 1);
+  if ((rc = c->alloc(c->Xs, ldn * wfin * es))) return rc;
+  if ((rc = c->alloc(c->Y, ldn * wfin * es))) return rc;
+  if ((rc = c->alloc(c->Xobs, mm * wfin * es))) return rc;
+  if ((rc = c->alloc(c->Fb, mm * std::max<size_t>(NE, 1) * es))) return rc;
+  if ((rc = c->alloc(c->Gws, NE * NE * sizeof(double)))) return rc;
+  if ((rc = c->alloc(c->Gws2, NE * NE * sizeof(double)))) return rc;
+  if (c->precision == CAKF_BF16 || c->precision == CAKF_TF32) {
+    c->Bpack_bytes = gram_tc_packed_ld(std::max(c->n, c->mmax)) * wfin * 4 + 4096;
+    if ((rc = c->alloc(c->Bpack, c->Bpack_bytes))) return rc;
+  }
+  if (!c->ev0) { cudaEventCreate(&c->ev0); cudaEventCreate(&c->ev1); }
+  return CAKF_OK;
+}
+
+int copy_in(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) return CAKF_OK;
+  cudaError_t ce = cudaMemcpyAsync(dst, src, bytes, is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+  return ce == cudaSuccess ? CAKF_OK : fail(CAKF_ERR_CUDA, std::string("copy in: ") + cudaGetErrorString(ce));
+}
+
+int copy_out(double* dst, const double* src, size_t elems, cudaStream_t st) {
+  if (!dst || elems == 0) return CAKF_OK;
+  cudaError_t ce = cudaMemcpyAsync(dst, src, elems * sizeof(double),
+                                   is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
+  return ce == cudaSuccess ? CAKF_OK : fail(CAKF_ERR_CUDA, std::string("copy out: ") + cudaGetErrorString(ce));
+}
+
+// ------------------------------------------------------------------------------------ runner
+template <class T>
+struct Runner {
+  cakf_ctx* c;
+  cudaStream_t st;
+  bool tc;      // tensor-core Gram x block
+  int tc_kind;  // 0 bf16, 1 tf32
+
+  T* Mk(int k) { return (T*)c->Mpool + c->off_M[k]; }
+  T* PV(int k) { return (T*)c->PVpool + c->off_PV[k]; }
+  T* Vk(int k) { return (T*)c->Vpool + c->off_V[k]; }
+  T* Sk(int k) { return (T*)c->Spool + c->off_S[k]; }
+  int mk(int k) { return c->obs_ptr[k] - c->obs_ptr[k - 1]; }
+  const int* obs(int k) { return c->obs + c->obs_ptr[k - 1]; }
+  C4<T>* X() { return (C4<T>*)c->X; }
+
+  // Out (nr x width, ld ldo) = K(Xr, Xc) B  -- the hot Gram x block product
+  void gram_block(const C4<T>* Xr, int nr, const C4<T>* Xc, int nc, const T* B, int ldb, int width, T* Out, int ldo) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c->profiling) { e0 = c->ev(); e1 = c->ev(); cudaEventRecord(e0, st); }
+    if (tc && sizeof(T) == 4 && width <= gram_tc_max_width()) {
+      size_t ldp = gram_tc_packed_ld(nc);
+      gram_tc_pack_b(tc_kind, (const float*)B, ldb, nc, width, c->Bpack, (int)ldp, st);
+      gram_block_tc(c->kernel, tc_kind, (const C4<float>*)Xr, nr, (const C4<float>*)Xc, nc, c->Bpack, (int)ldp, width,
+                    (float)c->sf2, (float*)Out, ldo, c->err, st);
+    } else {
+      gram_block_simt<T>(c->kernel, Xr, nr, Xc, nc, B, ldb, width, T(c->sf2), Out, ldo, st);
+    }
+    if (c->profiling) {
+      cudaEventRecord(e1, st);
+      c->prof_gb.push_back({e0, e1});
+      c->prof_gb_flops.push_back(2.0 * nr * (double)nc * width);
+      c->prof_gb_evals.push_back((double)nr * nc);
+    }
+  }
+
+  // ---------------------------------------------------------------- filter (Alg. 1)
+  int filter() {
+    const int n = c->n, T_ = c->T, ldn = c->ldn;
+    const double a = c->a, a2 = a * a;
+    cudaMemsetAsync(c->err, 0, sizeof(int), st);
+    cudaMemsetAsync(c->rs_plus, 0, n * sizeof(double), st);
+    cudaMemsetAsync(c->nll, 0, (T_ + 1) * sizeof(double), st);
+    cudaMemsetAsync(c->count, 0, (T_ + 1) * sizeof(int), st);
+    cudaMemsetAsync(c->Spool, 0, c->off_S[T_ + 1] * sizeof(T), st);
+    // state 0: prior
+    if (c->has_mu) cudaMemcpyAsync(c->mf, c->mu, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    else cudaMemsetAsync(c->mf, 0, n * sizeof(double), st);
+    {
+      std::vector<double> sfv(n, c->sf2);
+      cudaMemcpyAsync(c->vf, sfv.data(), n * sizeof(double), cudaMemcpyHostToDevice, st);
+      cudaStreamSynchronize(st);
+    }
+    const int B = std::max(c->budget, c->imax);
+    const double bd_tol = (sizeof(T) == 8) ? 1e-12 : 1e-6;
+    for (int k = 1; k <= T_; ++k) {
+      const int m = mk(k), ic = c->icap[k], rp = c->mcols[k - 1];
+      const double* mprev = c->mf + (size_t)(k - 1) * n;
+      double* mout = c->mf + (size_t)k * n;
+      double* vout = c->vf + (size_t)k * n;
+      predict_mean(mprev, c->has_mu ? c->mu + (size_t)k * n : nullptr,
+                   c->has_mu ? c->mu + (size_t)(k - 1) * n : nullptr, a, n, c->mpred, st);
+      if (m == 0 || ic == 0) {
+        // no data at this step: m = m^-, M = M^- = a M+_{k-1}; no truncation needed (c_k = c_{k-1})
+        filter_out<T>(c->mpred, (const T*)nullptr, ldn, -1, c->sf2, a2, c->rs_plus, n, mout, vout, nullptr, st);
+        scale_copy<T>(Mk(k - 1), ldn, n, rp, T(a), Mk(k), ldn, st);
+        if (rp > 0) rowsumsq<T>(Mk(k), ldn, n, rp, 0.0, c->rs_plus, st);
+        scale_f64(c->lam, rp, rp, 1, a2, st);   // lam_k = a^2 lam_{k-1}
+        continue;
+      }
+      const int* ob = obs(k);
+      C4<T>* Xo = (C4<T>*)c->Xo;
+      T* Mo = (T*)c->Mo;
+      T* V = Vk(k);
+      T* vcol = V + (size_t)ic * m;
+      T* r = (T*)c->rv;
+      T* s = (T*)c->sv;
+      T* g = (T*)c->gv;
+      T* GV = (T*)c->GV;
+      gather_coords<T>(X(), ob, m, Xo, st);
+      gather_rows<T>(Mk(k - 1), ldn, ob, m, rp, Mo, m, st);
+      cudaMemsetAsync(c->r0sq, 0, sizeof(double), st);
+      cg_init<T>(c->y + c->obs_ptr[k - 1], c->mpred, ob, m, r, (T*)c->r0v, vcol, c->r0sq, st);
+      cudaMemsetAsync(V, 0, (size_t)m * ic * sizeof(T), st);
+      cudaMemsetAsync(GV, 0, (size_t)m * std::max(ic, 1) * sizeof(T), st);
+      {
+        int one = 1;
+        cudaMemcpyAsync(c->active, &one, sizeof(int), cudaMemcpyHostToDevice, st);
+      }
+      // rtol threshold needs ||r0||^2: read back once per step only when requested
+      double rtol2 = 0.0;
+      int use_rtol = 0;
+      if (c->cg_rtol > 0 && !c->replay) {
+        double r0sq = 0;
+        cudaMemcpyAsync(&r0sq, c->r0sq, sizeof(double), cudaMemcpyDeviceToHost, st);
+        cudaStreamSynchronize(st);
+        rtol2 = c->cg_rtol * c->cg_rtol * r0sq;
+        use_rtol = 1;
+      }
+      const int nsplit = std::max(1, std::min(32, (m + 511) / 512));
+      const double* rep = c->replay ? c->rep + c->off_rep[k] : nullptr;
+      for (int j = 0; j < ic; ++j) {
+        cg_select<T>(j, r, rep, m, s, Sk(k), m, c->active, st);
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        bool prof = c->profiling && (j % 8 == 0);
+        if (prof) { e0 = c->ev(); e1 = c->ev(); cudaEventRecord(e0, st); }
+        gram_matvec<T>(c->kernel, Xo, s, m, T(c->sf2), (T*)c->part, nsplit, st);
+        if (prof) {
+          cudaEventRecord(e1, st);
+          c->prof_mv.push_back({e0, e1});
+          c->prof_mv_evals.push_back((double)m * m);
+        }
+        if (rp > 0) gemv_t<T>(Mo, m, m, rp, s, (T*)c->tv, c->active, st);
+        cg_combine<T>((const T*)c->part, nsplit, s, T(c->sn2), Mo, m, rp, (const T*)c->tv, T(a2), m, g, c->active, st);
+        cg_dots1<T>(V, m, j, s, g, (const T*)c->r0v, vcol, m, c->dots, c->active, st);
+        cg_upd1<T>(j, c->dots, V, GV, m, s, g, m, c->active, st);
+        cg_dots2<T>(V, GV, m, j, m, c->dots2, c->active, st);
+        cg_upd2<T>(j, c->dots, c->dots2, V, GV, m, r, vcol, m, bd_tol, rtol2, use_rtol, c->active,
+                   c->eta + (size_t)k * B, c->alpha + (size_t)k * B, c->count + k, st);
+      }
+      // finalize: [P^- W, P^- w] = K(X, X_o) [V v] - a^2 M+ (M+_o^T [V v])
+      T* PVk = PV(k);
+      gram_block(X(), n, Xo, m, V, m, ic + 1, PVk, ldn);
+      if (rp > 0) {
+        double* t2 = c->small;
+        gemm_tn<T>(Mo, m, rp, V, m, ic + 1, m, 1.0, 0.0, t2, rp, c->part64, c->part64_elems, st);
+        gemm_nn<T, double>(n, ic + 1, rp, T(-a2), Mk(k - 1), ldn, t2, rp, T(1), PVk, ldn, st);
+      }
+      filter_out<T>(c->mpred, PVk, ldn, ic, c->sf2, a2, c->rs_plus, n, mout, vout, c->rs_pw, st);
+      // NLL term: Cholesky of S^T S (FP64) and the recorded eta / alpha
+      {
+        double* SS = c->small;
+        gemm_tn<T>(Sk(k), m, ic, Sk(k), m, ic, m, 1.0, 0.0, SS, ic, c->part64, c->part64_elems, st);
+        nll_step(c->eta + (size_t)k * B, c->alpha + (size_t)k * B, c->count + k, SS, ic, c->nll + k, c->err, st);
+      }
+      // Truncate (Sec. 3.2)
+      int rc = truncate_filter(k, rp, ic);
+      if (rc) return rc;
+      cudaError_t ce = cudaGetLastError();
+      if (ce != cudaSuccess) return fail(CAKF_ERR_CUDA, std::string("filter step: ") + cudaGetErrorString(ce));
+    }
+    return CAKF_OK;
+  }
+
+  int truncate_filter(int k, int rp, int ic) {
+    const int n = c->n, ldn = c->ldn;
+    const double a = c->a, a2 = a * a;
+    T* PVk = PV(k);
+    if (c->rank_r <= 0) {
+      // M+_k = M_k = (a M+_{k-1}, P^- W_k)
+      scale_copy<T>(Mk(k - 1), ldn, n, rp, T(a), Mk(k), ldn, st);
+      scale_copy<T>(PVk, ldn, n, ic, T(1), Mk(k) + (size_t)rp * ldn, ldn, st);
+      rowsumsq<T>(Mk(k), ldn, n, rp + ic, 0.0, c->rs_plus, st);
+      return CAKF_OK;
+    }
+    const int N = rp + ic;
+    const int keep = std::min(c->rank_r, N);
+    double* G = c->gram;
+    cudaMemsetAsync(G, 0, (size_t)N * N * sizeof(double), st);
+    set_diag(G, N, c->lam, a2, rp, st);
+    if (rp > 0) {
+      double* Bm = c->small;
+      gemm_tn<T>(Mk(k - 1), ldn, rp, PVk, ldn, ic, n, a, 0.0, Bm, rp, c->part64, c->part64_elems, st);
+      put_block_sym(G, N, 0, rp, Bm, rp, rp, ic, 1.0, st);
+    }
+    gemm_tn<T>(PVk, ldn, ic, PVk, ldn, ic, n, 1.0, 0.0, G + (size_t)rp * N + rp, N, c->part64, c->part64_elems, st);
+    int rc = eig(G, N, keep);
+    if (rc) return rc;
+    // M+_k = a M+_{k-1} U[0:rp, :] + P^- W U[rp:N, :]
+    T* U = (T*)c->UT;
+    if (rp > 0) gemm_nn<T, T>(n, keep, rp, T(a), Mk(k - 1), ldn, U, N, T(0), Mk(k), ldn, st);
+    gemm_nn<T, T>(n, keep, ic, T(1), PVk, ldn, U + rp, N, rp > 0 ? T(1) : T(0), Mk(k), ldn, st);
+    cudaMemcpyAsync(c->lam, c->wv, keep * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    rowsumsq<T>(Mk(k), ldn, n, keep, 0.0, c->rs_plus, st);
+    return CAKF_OK;
+  }
+
+  // eigen-decomposition of the FP64 Gram G (N x N): top `keep` pairs -> wv, U64 (double), UT (T)
+  int eig(double* G, int N, int keep) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c->profiling) { e0 = c->ev(); e1 = c->ev(); cudaEventRecord(e0, st); }
+    int rc = eig_sym_topk<double>(G, N, N, keep, c->wv, c->U64, N, c->eigw, c->eigw_bytes, c->err, st);
+    if (rc) return fail(CAKF_ERR_CUDA, "eigensolver launch failed (code " + std::to_string(rc) + ")");
+    convert_from_f64<T>(c->U64, N, N, keep, (T*)c->UT, N, st);
+    if (c->profiling) {
+      cudaEventRecord(e1, st);
+      c->stats.eig_calls++;
+      c->prof_eig.push_back({e0, e1});
+    }
+    return CAKF_OK;
+  }
+
+  // ---------------------------------------------------------------- smoother (Alg. 3)
+  int smooth(double* ms, double* vs) {
+    const int n = c->n, T_ = c->T, ldn = c->ldn;
+    const double a = c->a, a2 = a * a;
+    cudaMemcpyAsync(ms + (size_t)T_ * n, c->mf + (size_t)T_ * n, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(vs + (size_t)T_ * n, c->vf + (size_t)T_ * n, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    if (T_ == 0) return CAKF_OK;
+    T* Ws = (T*)c->WsA;
+    T* Wn = (T*)c->WsB;
+    T* ws = (T*)c->wsA;
+    T* wn = (T*)c->wsB;
+    double* Gw = c->Gws;
+    double* Gn = c->Gws2;
+    // Ws_T = H^T V_T, ws_T = H^T v_T
+    int cw = c->icap[T_];
+    cudaMemsetAsync(ws, 0, ldn * sizeof(T), st);
+    if (cw > 0) {
+      const int m = mk(T_);
+      cudaMemsetAsync(Ws, 0, (size_t)ldn * cw * sizeof(T), st);
+      scatter_add_rows<T>(Vk(T_), m, obs(T_), m, cw, T(1), Ws, ldn, st);
+      scatter_add_rows<T>(Vk(T_) + (size_t)cw * m, m, obs(T_), m, 1, T(1), ws, ldn, st);
+      gemm_tn<T>(Vk(T_), m, cw, Vk(T_), m, cw, m, 1.0, 0.0, Gw, cw, c->part64, c->part64_elems, st);
+    } else if (T_ >= 1 && mk(T_) > 0) {
+      // no actions at T
+    }
+    T* Xs = (T*)c->Xs;
+    T* Y = (T*)c->Y;
+    for (int k = T_ - 1; k >= 0; --k) {
+      // X = A^T [Ws ws] = a [Ws ws]
+      build_x<T>(Ws, ldn, cw, ws, T(a), n, Xs, ldn, st);
+      // Y = P^-_k X = K X - a^2 M+_{k-1} (M+_{k-1}^T X)
+      gram_block(X(), n, X(), n, Xs, ldn, cw + 1, Y, ldn);
+      const int rp = (k >= 1) ? c->mcols[k - 1] : 0;
+      if (rp > 0) {
+        double* t = c->small;
+        gemm_tn<T>(Mk(k - 1), ldn, rp, Xs, ldn, cw + 1, n, 1.0, 0.0, t, rp, c->part64, c->part64_elems, st);
+        gemm_nn<T, double>(n, cw + 1, rp, T(-a2), Mk(k - 1), ldn, t, rp, T(1), Y, ldn, st);
+      }
+      const int ic = (k >= 1) ? c->icap[k] : 0;
+      const int m = (k >= 1) ? mk(k) : 0;
+      double* Z = c->small;                       // ic x (cw+1)
+      double* VtV = Z + (size_t)ic * (cw + 1);    // ic x ic
+      double* Bx = VtV + (size_t)ic * ic;         // ic x cw
+      double* Vz = Bx + (size_t)ic * std::max(cw, 1);   // scratch
+      if (ic > 0) {
+        // Z = W_k^T P^- X = V_k^T Y[obs];  Y <- P_k X = Y - (P^- W_k) Z
+        T* Xo = (T*)c->Xobs;
+        gather_rows<T>(Y, ldn, obs(k), m, cw + 1, Xo, m, st);
+        gemm_tn<T>(Vk(k), m, ic, Xo, m, cw + 1, m, 1.0, 0.0, Z, ic, c->part64, c->part64_elems, st);
+        gemm_nn<T, double>(n, cw + 1, ic, T(-1), PV(k), ldn, Z, ic, T(1), Y, ldn, st);
+      }
+      smooth_out<T>(c->mf + (size_t)k * n, c->vf + (size_t)k * n, Y, ldn, cw, n, ms + (size_t)k * n,
+                    vs + (size_t)k * n, st);
+      if (k == 0) break;
+      if (ic == 0) {
+        // no update at k: ws_k = a ws_{k+1}, Ws_k = a Ws_{k+1}
+        scale_copy<T>(Xs + (size_t)cw * ldn, ldn, n, 1, T(1), wn, ldn, st);
+        scale_copy<T>(Xs, ldn, n, cw, T(1), Wn, ldn, st);
+        if (cw > 0) {
+          cudaMemcpyAsync(Gn, Gw, (size_t)cw * cw * sizeof(double), cudaMemcpyDeviceToDevice, st);
+          scale_f64(Gn, cw * cw, cw * cw, 1, a2, st);
+        }
+        std::swap(Ws, Wn); std::swap(ws, wn); std::swap(Gw, Gn);
+        continue;
+      }
+      T* Vkk = Vk(k);
+      // ws_k = w_k + X[:, cw] - W_k Z[:, cw]
+      scale_copy<T>(Xs + (size_t)cw * ldn, ldn, n, 1, T(1), wn, ldn, st);
+      T* vz = (T*)c->Fb;
+      gemm_nn<T, double>(m, 1, ic, T(1), Vkk, m, Z + (size_t)cw * ic, ic, T(0), vz, m, st);
+      ws_obs<T>(obs(k), m, Vkk + (size_t)ic * m, vz, wn, st);
+      // Gram of Ws_full = [W_k, X'] with X' = X[:, :cw] - W_k Z[:, :cw]  (small-matrix identities)
+      const int N = ic + cw;
+      double* G = c->gram;
+      gemm_tn<T>(Vkk, m, ic, Vkk, m, ic, m, 1.0, 0.0, VtV, ic, c->part64, c->part64_elems, st);
+      if (cw > 0) {
+        T* Xo = (T*)c->Xobs;
+        gather_rows<T>(Xs, ldn, obs(k), m, cw, Xo, m, st);
+        gemm_tn<T>(Vkk, m, ic, Xo, m, cw, m, 1.0, 0.0, Bx, ic, c->part64, c->part64_elems, st);
+      }
+      // G = [[VtV, Bx - VtV Z], [., a^2 Gw - Z^T Bx - Bx^T Z + Z^T VtV Z]]
+      cudaMemsetAsync(G, 0, (size_t)N * N * sizeof(double), st);
+      copy_block(VtV, ic, ic, ic, G, N);
+      if (cw > 0) {
+        double* TR = Vz;                          // ic x cw
+        copy_block(Bx, ic, ic, cw, TR, ic);
+        gemm_small_f64(0, 0, ic, cw, ic, -1.0, VtV, ic, Z, ic, 1.0, TR, ic, st);
+        put_block_sym(G, N, 0, ic, TR, ic, ic, cw, 1.0, st);
+        double* BR = G + (size_t)ic * N + ic;     // cw x cw block, ld N
+        copy_block_scaled(Gw, cw, cw, cw, BR, N, a2);
+        gemm_small_f64(1, 0, cw, cw, ic, -1.0, Z, ic, Bx, ic, 1.0, BR, N, st);
+        gemm_small_f64(1, 0, cw, cw, ic, -1.0, Bx, ic, Z, ic, 1.0, BR, N, st);
+        double* VZ = TR + (size_t)ic * cw;        // ic x cw = VtV Z
+        gemm_small_f64(0, 0, ic, cw, ic, 1.0, VtV, ic, Z, ic, 0.0, VZ, ic, st);
+        gemm_small_f64(1, 0, cw, cw, ic, 1.0, Z, ic, VZ, ic, 1.0, BR, N, st);
+      }
+      if (c->rank_r > 0) {
+        const int keep = std::min(c->rank_r, N);
+        int rc = eig(G, N, keep);
+        if (rc) return rc;
+        T* U = (T*)c->UT;
+        // Ws_new = X[:, :cw] U[ic:, :] + scatter_obs( V_k (U[:ic, :] - Z[:, :cw] U[ic:, :]) )
+        if (cw > 0) gemm_nn<T, T>(n, keep, cw, T(1), Xs, ldn, U + ic, N, T(0), Wn, ldn, st);
+        else cudaMemsetAsync(Wn, 0, (size_t)ldn * keep * sizeof(T), st);
+        double* E = Vz;   // ic x keep
+        copy_block(c->U64, N, ic, keep, E, ic);
+        if (cw > 0) gemm_small_f64(0, 0, ic, keep, cw, -1.0, Z, ic, c->U64 + ic, N, 1.0, E, ic, st);
+        T* F = (T*)c->Fb;
+        gemm_nn<T, double>(m, keep, ic, T(1), Vkk, m, E, ic, T(0), F, m, st);
+        scatter_add_rows<T>(F, m, obs(k), m, keep, T(1), Wn, ldn, st);
+        // Gram of the new Ws is diag(lam)
+        cudaMemsetAsync(Gn, 0, (size_t)keep * keep * sizeof(double), st);
+        set_diag(Gn, keep, c->wv, 1.0, keep, st);
+        cw = keep;
+      } else {
+        // no truncation: Ws_new = [W_k, X[:, :cw] - W_k Z[:, :cw]] explicitly
+        cudaMemsetAsync(Wn, 0, (size_t)ldn * N * sizeof(T), st);
+        scatter_add_rows<T>(Vkk, m, obs(k), m, ic, T(1), Wn, ldn, st);
+        if (cw > 0) {
+          scale_copy<T>(Xs, ldn, n, cw, T(1), Wn + (size_t)ic * ldn, ldn, st);
+          T* F = (T*)c->Fb;
+          gemm_nn<T, double>(m, cw, ic, T(1), Vkk, m, Z, ic, T(0), F, m, st);
+          scatter_add_rows<T>(F, m, obs(k), m, cw, T(-1), Wn + (size_t)ic * ldn, ldn, st);
+        }
+        cudaMemcpyAsync(Gn, G, (size_t)N * N * sizeof(double), cudaMemcpyDeviceToDevice, st);
+        cw = N;
+      }
+      std::swap(Ws, Wn); std::swap(ws, wn); std::swap(Gw, Gn);
+      cudaError_t ce = cudaGetLastError();
+      if (ce != cudaSuccess) return fail(CAKF_ERR_CUDA, std::string("smoother step: ") + cudaGetErrorString(ce));
+    }
+    return CAKF_OK;
+  }
+
+  void copy_block(const double* src, int lds, int rows, int cols, double* dst, int ldd) {
+    if (rows <= 0 || cols <= 0) return;
+    cudaMemcpy2DAsync(dst, ldd * sizeof(double), src, lds * sizeof(double), rows * sizeof(double), cols,
+                      cudaMemcpyDeviceToDevice, st);
+  }
+  void copy_block_scaled(const double* src, int lds, int rows, int cols, double* dst, int ldd, double s) {
+    copy_block(src, lds, rows, cols, dst, ldd);
+    scale_f64(dst, ldd, rows, cols, s, st);
+  }
+};
+
+}  // namespace
+
+
+namespace {
+
+// ------------------------------------------------------------------------------------ validation
+int validate(const cakf_problem* p) {
+  if (!p) return fail(CAKF_ERR_ARG, "problem is NULL");
+  if (p->abi_version != CAKF_ABI_VERSION) return fail(CAKF_ERR_ARG, "abi_version mismatch");
+  if (p->n < 1) return fail(CAKF_ERR_ARG, "n must be >= 1");
+  if (p->dim < 1 || p->dim > 3) return fail(CAKF_ERR_ARG, "dim must be 1..3");
+  if (!p->coords) return fail(CAKF_ERR_ARG, "coords is NULL");
+  if (p->kernel < 0 || p->kernel > 2) return fail(CAKF_ERR_ARG, "unknown kernel");
+  if (p->T < 0) return fail(CAKF_ERR_ARG, "T must be >= 0");
+  if (!p->obs_ptr) return fail(CAKF_ERR_ARG, "obs_ptr is NULL");
+  if (is_device_ptr(p->obs_ptr)) return fail(CAKF_ERR_ARG, "obs_ptr must be a host array");
+  if (p->obs_ptr[0] != 0) return fail(CAKF_ERR_ARG, "obs_ptr[0] must be 0");
+  for (int k = 1; k <= p->T; ++k) {
+    if (p->obs_ptr[k] < p->obs_ptr[k - 1]) return fail(CAKF_ERR_ARG, "obs_ptr must be non-decreasing");
+    if (p->obs_ptr[k] - p->obs_ptr[k - 1] > p->n) return fail(CAKF_ERR_ARG, "more observations than grid points in a step");
+  }
+  const int N = p->obs_ptr[p->T];
+  if (N > 0 && (!p->obs_idx || !p->y)) return fail(CAKF_ERR_ARG, "obs_idx / y is NULL");
+  if (p->budget_i < 1 || p->budget_i > 1024) return fail(CAKF_ERR_ARG, "budget_i must be in 1..1024");
+  if (p->precision < CAKF_FP64 || p->precision > CAKF_BF16) return fail(CAKF_ERR_ARG, "unknown precision");
+  const double hp[4] = {p->log_lx, p->log_lt, p->log_sf2, p->log_sn2};
+  for (double h : hp)
+    if (!std::isfinite(h) || std::fabs(h) > 80) return fail(CAKF_ERR_ARG, "hyperparameters must be finite");
+  if (!(p->dt > 0) || !std::isfinite(p->dt)) return fail(CAKF_ERR_ARG, "dt must be > 0");
+  if (!(p->cg_rtol >= 0)) return fail(CAKF_ERR_ARG, "cg_rtol must be >= 0");
+  if (p->replay_actions && !p->replay_counts) return fail(CAKF_ERR_ARG, "replay_actions without replay_counts");
+  if (p->replay_counts) {
+    for (int k = 1; k <= p->T; ++k) {
+      int c = p->replay_counts[k], mk = p->obs_ptr[k] - p->obs_ptr[k - 1];
+      if (c < 0 || c > mk || c > 1024) return fail(CAKF_ERR_ARG, "replay_counts out of range");
+    }
+  }
+  // observation indices: range and distinctness per step (checked on a host copy)
+  if (N > 0) {
+    std::vector<int> idx(N);
+    if (is_device_ptr(p->obs_idx)) {
+      if (cudaMemcpy(idx.data(), p->obs_idx, N * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(CAKF_ERR_CUDA, "reading obs_idx");
+    } else {
+      std::memcpy(idx.data(), p->obs_idx, N * sizeof(int));
+    }
+    std::vector<int> mark(p->n, -1);
+    for (int k = 1; k <= p->T; ++k)
+      for (int q = p->obs_ptr[k - 1]; q < p->obs_ptr[k]; ++q) {
+        int v = idx[q];
+        if (v < 0 || v >= p->n) return fail(CAKF_ERR_ARG, "obs_idx out of range");
+        if (mark[v] == k) return fail(CAKF_ERR_ARG, "duplicate obs_idx within a step");
+        mark[v] = k;
+      }
+  }
+  return CAKF_OK;
+}
+
+bool same_shape(const cakf_ctx* c, const cakf_problem* p) {
+  if (c->n != p->n || c->T != p->T || c->budget != p->budget_i || c->rank_r != p->rank_r ||
+      c->precision != p->precision || c->has_mu != (p->prior_mean != nullptr) || c->replay != (p->replay_actions != nullptr))
+    return false;
+  for (int k = 0; k <= p->T; ++k)
+    if (c->obs_ptr[k] != p->obs_ptr[k]) return false;
+  if (c->replay)
+    for (int k = 0; k <= p->T; ++k)
+      if (c->replay_counts[k] != p->replay_counts[k]) return false;
+  return true;
+}
+
+double nu_scale(int kernel) { return kernel == 0 ? 1.0 : (kernel == 1 ? std::sqrt(3.0) : std::sqrt(5.0)); }
+
+int sync_and_check(cakf_ctx* c, cudaStream_t st, const char* what) {
+  cudaError_t ce = cudaStreamSynchronize(st);
+  if (ce != cudaSuccess) return fail(CAKF_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(ce));
+  int e = 0;
+  cudaMemcpy(&e, c->err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == kErrTimeout) return fail(CAKF_ERR_TIMEOUT, std::string(what) + ": a device-side wait exceeded its limit");
+  if (e != 0) return fail(CAKF_ERR_NUMERIC, std::string(what) + ": non-finite value or non-positive-definite action Gram");
+  return CAKF_OK;
+}
+
+void collect_profile(cakf_ctx* c) {
+  auto sum = [](std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& v) {
+    double tot = 0;
+    for (auto& pr : v) { float ms = 0; cudaEventElapsedTime(&ms, pr.first, pr.second); tot += ms; }
+    return tot;
+  };
+  c->stats.gram_block_ms += sum(c->prof_gb);
+  c->stats.gram_block_launches += (int64_t)c->prof_gb.size();
+  for (double f : c->prof_gb_flops) c->stats.gram_block_flops += f;
+  for (double f : c->prof_gb_evals) c->stats.gram_block_evals += f;
+  c->stats.cg_matvec_ms += sum(c->prof_mv);
+  c->stats.cg_matvec_launches += (int64_t)c->prof_mv.size();
+  for (double f : c->prof_mv_evals) c->stats.cg_matvec_evals += f;
+  c->stats.eig_ms += sum(c->prof_eig);
+  c->prof_gb.clear(); c->prof_gb_flops.clear(); c->prof_gb_evals.clear();
+  c->prof_mv.clear(); c->prof_mv_evals.clear(); c->prof_eig.clear();
+  c->ev_used = 0;
+}
+
+template <class T>
+Runner<T> make_runner(cakf_ctx* c, cudaStream_t st) {
+  Runner<T> r;
+  r.c = c;
+  r.st = st;
+  r.tc = (c->precision == CAKF_BF16 || c->precision == CAKF_TF32);
+  r.tc_kind = (c->precision == CAKF_TF32) ? 1 : 0;
+  return r;
+}
+
+}  // namespace
+
+// ============================================================================================ ABI
+extern "C" {
+
+int cakf_filter(const cakf_problem* p, cakf_ctx** ctx_inout, double* mean_out, double* var_out, void* cuda_stream) {
+  if (!ctx_inout) return fail(CAKF_ERR_ARG, "ctx_inout is NULL");
+  int rc = validate(p);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  cakf_ctx* c = *ctx_inout;
+  bool fresh = false;
+  if (c && !same_shape(c, p)) { c->release(); c->filtered = false; fresh = true; }
+  if (!c) { c = new cakf_ctx(); *ctx_inout = c; fresh = true; }
+  c->n = p->n; c->dim = p->dim; c->kernel = p->kernel; c->T = p->T; c->budget = p->budget_i; c->rank_r = p->rank_r;
+  c->precision = p->precision; c->lx = std::exp(p->log_lx); c->lt = std::exp(p->log_lt); c->sf2 = std::exp(p->log_sf2);
+  c->sn2 = std::exp(p->log_sn2); c->dt = p->dt; c->a = std::exp(-p->dt / c->lt); c->cg_rtol = p->cg_rtol;
+  c->has_mu = p->prior_mean != nullptr;
+  c->replay = p->replay_actions != nullptr;
+  if (c->replay) c->replay_counts.assign(p->replay_counts, p->replay_counts + p->T + 1);
+  c->filtered = false;
+  if (fresh || c->bufs.empty()) {
+    rc = plan_and_alloc(c, p);
+    if (rc) { c->release(); return rc; }
+  }
+  c->stats = cakf_stats{};
+  c->stats.device_bytes = (int64_t)c->dev_bytes;
+  c->launch_base = cakf::launch_count();
+  const size_t N = c->obs_ptr[c->T];
+  const int n = c->n;
+  if ((rc = copy_in(c->coords64, p->coords, (size_t)n * p->dim * sizeof(double), st))) return rc;
+  if ((rc = copy_in(c->obs, p->obs_idx, N * sizeof(int), st))) return rc;
+  if ((rc = copy_in(c->y, p->y, N * sizeof(double), st))) return rc;
+  if (c->has_mu && (rc = copy_in(c->mu, p->prior_mean, (size_t)(c->T + 1) * n * sizeof(double), st))) return rc;
+  if (c->replay) {
+    // pack the replayed actions per step (host input, concatenated m_k x i_k blocks)
+    if ((rc = copy_in(c->rep, p->replay_actions, c->off_rep[c->T + 1] * sizeof(double), st))) return rc;
+  }
+  const double scale = nu_scale(c->kernel) / c->lx;
+  cudaEventRecord(c->ev0, st);
+  if (c->precision == CAKF_FP64) {
+    prep_coords<double>(c->coords64, n, p->dim, scale, (C4<double>*)c->X, st);
+    Runner<double> r = make_runner<double>(c, st);
+    rc = r.filter();
+  } else {
+    prep_coords<float>(c->coords64, n, p->dim, scale, (C4<float>*)c->X, st);
+    Runner<float> r = make_runner<float>(c, st);
+    rc = r.filter();
+  }
+  cudaEventRecord(c->ev1, st);
+  if (rc) return rc;
+  check_finite(c->mf, (size_t)(c->T + 1) * n, c->err, st);
+  check_finite(c->vf, (size_t)(c->T + 1) * n, c->err, st);
+  if ((rc = sync_and_check(c, st, "cakf_filter"))) return rc;
+  float ms = 0;
+  cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+  c->stats.filter_ms = ms;
+  if (c->profiling) collect_profile(c);
+  if ((rc = copy_out(mean_out, c->mf, (size_t)(c->T + 1) * n, st))) return rc;
+  if ((rc = copy_out(var_out, c->vf, (size_t)(c->T + 1) * n, st))) return rc;
+  cudaError_t ce = cudaStreamSynchronize(st);
+  if (ce != cudaSuccess) return fail(CAKF_ERR_CUDA, cudaGetErrorString(ce));
+  c->filtered = true;
+  return CAKF_OK;
+}
+
+int cakf_smooth(cakf_ctx* c, double* mean_out, double* var_out, void* cuda_stream) {
+  if (!c) return fail(CAKF_ERR_ARG, "ctx is NULL");
+  if (!c->filtered) return fail(CAKF_ERR_STATE, "cakf_smooth needs a successful cakf_filter on this context");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const size_t tot = (size_t)(c->T + 1) * c->n;
+  int rc;
+  double* ms = is_device_ptr(mean_out) ? mean_out : nullptr;
+  double* vs = is_device_ptr(var_out) ? var_out : nullptr;
+  if (!ms || !vs) {
+    if (!c->ms_dev) {
+      if ((rc = c->alloc(c->ms_dev, tot * sizeof(double)))) return rc;
+      if ((rc = c->alloc(c->vs_dev, tot * sizeof(double)))) return rc;
+    }
+    if (!ms) ms = c->ms_dev;
+    if (!vs) vs = c->vs_dev;
+  }
+  cudaMemsetAsync(c->err, 0, sizeof(int), st);
+  cudaEventRecord(c->ev0, st);
+  if (c->precision == CAKF_FP64) {
+    Runner<double> r = make_runner<double>(c, st);
+    rc = r.smooth(ms, vs);
+  } else {
+    Runner<float> r = make_runner<float>(c, st);
+    rc = r.smooth(ms, vs);
+  }
+  cudaEventRecord(c->ev1, st);
+  if (rc) return rc;
+  check_finite(ms, tot, c->err, st);
+  check_finite(vs, tot, c->err, st);
+  if ((rc = sync_and_check(c, st, "cakf_smooth"))) return rc;
+  float msec = 0;
+  cudaEventElapsedTime(&msec, c->ev0, c->ev1);
+  c->stats.smooth_ms = msec;
+  if (c->profiling) collect_profile(c);
+  if (mean_out && ms != mean_out && (rc = copy_out(mean_out, ms, tot, st))) return rc;
+  if (var_out && vs != var_out && (rc = copy_out(var_out, vs, tot, st))) return rc;
+  cudaError_t ce = cudaStreamSynchronize(st);
+  return ce == cudaSuccess ? CAKF_OK : fail(CAKF_ERR_CUDA, cudaGetErrorString(ce));
+}
+
+int cakf_nll(cakf_ctx* c, double* nll_out) {
+  if (!c || !nll_out) return fail(CAKF_ERR_ARG, "NULL argument");
+  if (!c->filtered) return fail(CAKF_ERR_STATE, "cakf_nll needs a successful cakf_filter on this context");
+  std::vector<double> v(c->T + 1);
+  if (cudaMemcpy(v.data(), c->nll, (c->T + 1) * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(CAKF_ERR_CUDA, "reading NLL terms");
+  double s = 0;
+  for (double x : v) s += x;
+  *nll_out = s;
+  return CAKF_OK;
+}
+
+int cakf_get_actions(cakf_ctx* c, double* actions_out, int32_t* counts_out) {
+  if (!c || !counts_out) return fail(CAKF_ERR_ARG, "NULL argument");
+  if (!c->filtered) return fail(CAKF_ERR_STATE, "no filter run on this context");
+  std::vector<int> cnt(c->T + 1);
+  cudaMemcpy(cnt.data(), c->count, (c->T + 1) * sizeof(int), cudaMemcpyDeviceToHost);
+  for (int k = 0; k <= c->T; ++k) counts_out[k] = (k == 0) ? 0 : cnt[k];
+  if (!actions_out) return CAKF_OK;
+  size_t off = 0;
+  const size_t es = elem_size(c->precision);
+  for (int k = 1; k <= c->T; ++k) {
+    const int m = c->obs_ptr[k] - c->obs_ptr[k - 1];
+    const size_t cnt_el = (size_t)m * cnt[k];
+    if (cnt_el == 0) continue;
+    if (es == 8) {
+      cudaMemcpy(actions_out + off, (double*)c->Spool + c->off_S[k], cnt_el * 8, cudaMemcpyDeviceToHost);
+    } else {
+      std::vector<float> tmp(cnt_el);
+      cudaMemcpy(tmp.data(), (float*)c->Spool + c->off_S[k], cnt_el * 4, cudaMemcpyDeviceToHost);
+      for (size_t q = 0; q < cnt_el; ++q) actions_out[off + q] = tmp[q];
+    }
+    off += cnt_el;
+  }
+  return CAKF_OK;
+}
+
+int cakf_get_stats(const cakf_ctx* c, cakf_stats* out) {
+  if (!c || !out) return fail(CAKF_ERR_ARG, "NULL argument");
+  *out = c->stats;
+  out->kernel_launches = (int64_t)(cakf::launch_count() - c->launch_base);
+  out->device_bytes = (int64_t)c->dev_bytes;
+  return CAKF_OK;
+}
+
+int cakf_set_profiling(cakf_ctx* c, int on) {
+  if (!c) return fail(CAKF_ERR_ARG, "ctx is NULL");
+  c->profiling = on != 0;
+  return CAKF_OK;
+}
+
+void cakf_free(cakf_ctx* c) { delete c; }
+
+const char* cakf_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"
+
+extern "C" int cakf_nll_backward(cakf_ctx* c, double* grad_out) {
+  if (!c || !grad_out) return fail(CAKF_ERR_ARG, "NULL argument");
+  if (!c->filtered) return fail(CAKF_ERR_STATE, "cakf_nll_backward needs a successful cakf_filter on this context");
+  return fail(CAKF_ERR_STATE, "cakf_nll_backward: not available in this build");
+}

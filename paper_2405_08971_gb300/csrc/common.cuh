@@ -1,0 +1,102 @@
+// Shared device helpers of libcakf: coordinate records, Matern kernel values, reductions and a
+// bounded grid barrier.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cmath>
+
+namespace cakf {
+
+// Grid coordinates, pre-scaled by c_nu / l_x (c = 1, sqrt(3), sqrt(5) for nu = 1/2, 3/2, 5/2), so
+// that the Matern argument is the plain Euclidean distance s = |xs - xs'|.  w is padding.
+template <class T> struct alignas(4 * sizeof(T)) C4 { T x, y, z, w; };
+
+__device__ __forceinline__ float approx_sqrt(float v) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+  return r;
+}
+__device__ __forceinline__ float approx_exp_neg(float s) {   // exp(-s) via ex2.approx
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(-1.4426950408889634f * s));
+  return r;
+}
+
+// Matern correlation times sf2 of the scaled distance^2 (Rasmussen-Williams forms):
+//   nu=1/2: e^-s,  nu=3/2: (1+s) e^-s,  nu=5/2: (1 + s + s^2/3) e^-s.
+template <int KER> __device__ __forceinline__ float kval(float s2, float sf2) {
+  float s = approx_sqrt(s2);
+  float e = approx_exp_neg(s) * sf2;
+  if (KER == 0) return e;
+  if (KER == 1) return fmaf(s, e, e);
+  return fmaf(fmaf(s, 0.33333333333333333f, 1.0f) * s, e, e);
+}
+template <int KER> __device__ __forceinline__ double kval(double s2, double sf2) {
+  double s = sqrt(s2);
+  double e = exp(-s) * sf2;
+  if (KER == 0) return e;
+  if (KER == 1) return fma(s, e, e);
+  return fma(fma(s, 1.0 / 3.0, 1.0) * s, e, e);
+}
+
+template <class T> __device__ __forceinline__ T dist2(const C4<T>& a, const C4<T>& b) {
+  T dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+  return fma(dx, dx, fma(dy, dy, dz * dz));
+}
+
+template <class T> __device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum (blockDim.x a multiple of 32, <= 1024); every thread gets the result.
+template <class T> __device__ T block_sum(T v) {
+  __shared__ T red[32];
+  __syncthreads();
+  v = warp_sum(v);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  int nw = (blockDim.x + 31) >> 5;
+  T t = (threadIdx.x < nw) ? red[threadIdx.x] : T(0);
+  if (w == 0) t = warp_sum(t);
+  if (threadIdx.x == 0) red[0] = t;
+  __syncthreads();
+  T r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// Grid barrier for kernels launched cooperatively (all blocks co-resident).  `bar` points at
+// two zero-initialised words {count, generation}.  The spin is bounded: after `limit` polls the
+// barrier raises *err and returns false; callers then stop their work.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* err,
+                                             long long limit = 50000000LL) {
+  __syncthreads();
+  bool ok = true;
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 1;
+    unsigned g = *gen;
+    __threadfence();
+    unsigned arrived = atomicAdd(bar, 1u) + 1u;
+    if (arrived == nblocks) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long long spins = 0;
+      while (*gen == g) {
+        if (++spins > limit) { atomicExch(err, 2); ok = false; break; }
+        if (*(volatile int*)err) { ok = false; break; }
+      }
+    }
+    __threadfence();
+  }
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) s_ok = ok;
+  __syncthreads();
+  return s_ok != 0;
+}
+
+}  // namespace cakf

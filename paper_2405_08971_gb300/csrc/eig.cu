@@ -1,0 +1,599 @@
+// FP64 symmetric eigensolver for the truncation step (Truncate, Sec. 3.2: the top-r eigen-directions
+// of the (r+i) x (r+i) Gram of the downdate factor).
+//
+//   1. Householder tridiagonalisation, one cooperative kernel, two bounded grid barriers per column.
+//   2. Divide and conquer on the tridiagonal (Cuppen's tearing; deflation of small z components and
+//      close poles by Givens rotations; secular roots by a two-pole rational model guarded by
+//      bisection; eigenvectors from the Loewner-corrected z (Gu-Eisenstat), which keeps them
+//      orthogonal without re-orthogonalisation).
+//   3. Back-transformation of the wanted columns through the Householder reflectors.
+// All arithmetic is FP64; only the final eigenvector block is stored in the caller's precision.
+#include <vector>
+#include <map>
+#include <mutex>
+#include "internal.h"
+
+namespace cakf {
+
+namespace {
+
+constexpr double kEps = 2.220446049250313e-16;
+
+// ---------------------------------------------------------------------------------- tridiagonal
+__global__ void __launch_bounds__(256)
+k_tridiag(double* __restrict__ A, int lda, int N, double* __restrict__ d, double* __restrict__ e,
+          double* __restrict__ tau, double* __restrict__ P, unsigned* bar, int* err) {
+  extern __shared__ double sm[];
+  double* v = sm;
+  double* w = sm + N;
+  const int G = gridDim.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int k = 0; k + 2 < N; ++k) {
+    const int L = N - k - 1;
+    const double* x = A + (size_t)k * lda + k + 1;
+    double ss = 0.0;
+    for (int t = threadIdx.x; t < L; t += blockDim.x) {
+      double xv = __ldcg(x + t);
+      v[t] = xv;
+      if (t > 0) ss += xv * xv;
+    }
+    const double sigma = block_sum(ss);
+    const double alpha = v[0];
+    double beta, tk, scal;
+    if (sigma == 0.0) { tk = 0.0; beta = alpha; scal = 0.0; }
+    else {
+      beta = -copysign(sqrt(alpha * alpha + sigma), alpha);
+      tk = (beta - alpha) / beta;
+      scal = 1.0 / (alpha - beta);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < L; t += blockDim.x) v[t] = (t == 0) ? 1.0 : v[t] * scal;
+    __syncthreads();
+    // p = tau * A22 v, one warp per owned column (columns are dealt to blocks round-robin)
+    for (int jp = blockIdx.x + G * warp; jp < L; jp += G * nw) {
+      const double* col = A + (size_t)(k + 1 + jp) * lda + k + 1;
+      double acc = 0.0;
+      for (int t = lane; t < L; t += 32) acc += __ldcg(col + t) * v[t];
+      acc = warp_sum(acc);
+      if (lane == 0) P[jp] = tk * acc;
+    }
+    if (!grid_barrier(bar, G, err)) return;
+    double pv = 0.0;
+    for (int t = threadIdx.x; t < L; t += blockDim.x) {
+      double pt = __ldcg(P + t);
+      w[t] = pt;
+      pv += pt * v[t];
+    }
+    pv = block_sum(pv);
+    const double kc = 0.5 * tk * pv;
+    for (int t = threadIdx.x; t < L; t += blockDim.x) w[t] -= kc * v[t];
+    __syncthreads();
+    // A22 -= v w^T + w v^T on the owned columns
+    for (int jp = blockIdx.x + G * warp; jp < L; jp += G * nw) {
+      double* col = A + (size_t)(k + 1 + jp) * lda + k + 1;
+      const double vj = v[jp], wj = w[jp];
+      for (int t = lane; t < L; t += 32) col[t] = __ldcg(col + t) - (v[t] * wj + w[t] * vj);
+    }
+    if (blockIdx.x == 0) {
+      for (int t = threadIdx.x; t < L; t += blockDim.x) A[(size_t)k * lda + k + 1 + t] = v[t];
+      if (threadIdx.x == 0) { d[k] = __ldcg(A + (size_t)k * lda + k); e[k] = beta; tau[k] = tk; }
+    }
+    if (!grid_barrier(bar, G, err)) return;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (N >= 2) {
+      d[N - 2] = __ldcg(A + (size_t)(N - 2) * lda + N - 2);
+      e[N - 2] = __ldcg(A + (size_t)(N - 2) * lda + N - 1);
+      d[N - 1] = __ldcg(A + (size_t)(N - 1) * lda + N - 1);
+      tau[N - 2] = 0.0;
+    } else if (N == 1) {
+      d[0] = __ldcg(A);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------ divide & conquer
+struct MergeDesc { int lo, mid, hi; };
+
+struct DcWork {
+  double *lam, *lamk, *lamtmp, *Dw, *Zw, *Dk, *Zk, *Dd, *Q, *Qtmp, *Delta, *rho, *rot;
+  int *colk, *cold, *perm, *Kp, *nrot, *mergeof;
+};
+
+__global__ void k_dc_init(const double* __restrict__ d, const double* __restrict__ e, int N, double* lam,
+                          double* Q) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  double v = d[j];
+  if (j > 0) v -= fabs(e[j - 1]);
+  if (j + 1 < N) v -= fabs(e[j]);
+  lam[j] = v;
+  Q[(size_t)j * N + j] = 1.0;
+}
+
+// Phase 1 of a merge: z vector, sorted poles, deflation.  One block per merge.
+__global__ void __launch_bounds__(256)
+k_dc_prep(const MergeDesc* __restrict__ merges, const double* __restrict__ e, int N, DcWork W) {
+  const MergeDesc mg = merges[blockIdx.x];
+  const int lo = mg.lo, mid = mg.mid, K = mg.hi - mg.lo, n1 = mg.mid - mg.lo;
+  const double rho0 = e[mid - 1];
+  const double sgn = rho0 >= 0.0 ? 1.0 : -1.0;
+  double* Dw = W.Dw + lo;
+  double* Zw = W.Zw + lo;
+  int* perm = W.perm + lo;
+  double zz = 0.0;
+  for (int t = threadIdx.x; t < K; t += blockDim.x) {
+    double z = (t < n1) ? W.Q[(size_t)(lo + t) * N + (mid - 1)] : sgn * W.Q[(size_t)(lo + t) * N + mid];
+    W.lamtmp[lo + t] = z;   // raw z (unsorted), reused below
+    zz += z * z;
+  }
+  zz = block_sum(zz);
+  __shared__ int s_kp, s_nrot;
+  if (threadIdx.x == 0) {
+    const double zn = sqrt(zz);
+    const double rho = fabs(rho0) * zz;
+    // merge the two ascending child spectra
+    int a = 0, b = n1, s = 0;
+    while (a < n1 || b < K) {
+      int pick;
+      if (a >= n1) pick = b++;
+      else if (b >= K) pick = a++;
+      else pick = (W.lam[lo + a] <= W.lam[lo + b]) ? a++ : b++;
+      perm[s] = pick;
+      Dw[s] = W.lam[lo + pick];
+      Zw[s] = W.lamtmp[lo + pick] / zn;
+      ++s;
+    }
+    double dmax = 0.0;
+    for (int t = 0; t < K; ++t) dmax = fmax(dmax, fabs(Dw[t]));
+    const double tol = 8.0 * kEps * fmax(dmax, rho);
+    // deflation scan
+    int kp = 0, nd = 0, nrot = 0, last = -1;
+    int* keep = W.colk + lo;    // temporarily: sorted positions of kept entries
+    int* defl = W.cold + lo;    // sorted positions of deflated entries
+    for (int j = 0; j < K; ++j) {
+      if (rho * fabs(Zw[j]) <= tol) { defl[nd++] = j; continue; }
+      if (last >= 0) {
+        const double t = hypot(Zw[last], Zw[j]);
+        const double c = Zw[j] / t, sn = -Zw[last] / t;
+        if (fabs((Dw[j] - Dw[last]) * c * sn) <= tol) {
+          double* rr = W.rot + 4 * (size_t)(lo + nrot);
+          rr[0] = last; rr[1] = j; rr[2] = c; rr[3] = sn;
+          ++nrot;
+          const double dl = Dw[last], dj = Dw[j];
+          Dw[last] = c * c * dl + sn * sn * dj;
+          Dw[j] = sn * sn * dl + c * c * dj;
+          Zw[last] = 0.0;
+          Zw[j] = t;
+          defl[nd++] = last;
+          --kp;   // 'last' was the most recently kept entry
+        }
+      }
+      keep[kp++] = j;
+      last = j;
+    }
+    // sort kept entries by pole (rotations can perturb the order slightly): insertion sort
+    for (int a2 = 1; a2 < kp; ++a2) {
+      int key = keep[a2];
+      int b2 = a2 - 1;
+      while (b2 >= 0 && Dw[keep[b2]] > Dw[key]) { keep[b2 + 1] = keep[b2]; --b2; }
+      keep[b2 + 1] = key;
+    }
+    for (int t = 0; t < kp; ++t) { W.Dk[lo + t] = Dw[keep[t]]; W.Zk[lo + t] = Zw[keep[t]]; }
+    for (int t = 0; t < nd; ++t) W.Dd[lo + t] = Dw[defl[t]];
+    s_kp = kp;
+    s_nrot = nrot;
+    W.rho[lo] = rho;
+    W.Kp[lo] = kp;
+  }
+  __syncthreads();
+  // apply the deflation rotations to the (permuted) child eigenvector columns, rows lo..hi
+  const int nrot = s_nrot;
+  for (int row = threadIdx.x; row < K; row += blockDim.x) {
+    for (int q = 0; q < nrot; ++q) {
+      const double* rr = W.rot + 4 * (size_t)(lo + q);
+      const int ca = lo + perm[(int)rr[0]], cb = lo + perm[(int)rr[1]];
+      double* qa = W.Q + (size_t)ca * N + lo + row;
+      double* qb = W.Q + (size_t)cb * N + lo + row;
+      const double c = rr[2], sn = rr[3];
+      const double xa = *qa, xb = *qb;
+      *qa = c * xa + sn * xb;
+      *qb = -sn * xa + c * xb;
+    }
+  }
+  __syncthreads();
+  // translate sorted positions to Q columns
+  for (int t = threadIdx.x; t < s_kp; t += blockDim.x) W.colk[lo + t] = lo + perm[W.colk[lo + t]];
+  for (int t = threadIdx.x; t < K - s_kp; t += blockDim.x) W.cold[lo + t] = lo + perm[W.cold[lo + t]];
+}
+
+// Phase 2: secular roots.  Thread per (merge, root).  delta column i: Delta[(lo+i)*N + lo + j] = Dk_j - lam_i
+__global__ void k_dc_secular(const MergeDesc* __restrict__ merges, const int* __restrict__ mergeof, int N, DcWork W,
+                             int* err) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= N) return;
+  const int mi = mergeof[p];
+  if (mi < 0) return;
+  const int lo = merges[mi].lo;
+  const int i = p - lo;
+  const int Kp = W.Kp[lo];
+  if (i >= Kp) return;
+  const double* Dk = W.Dk + lo;
+  const double* Zk = W.Zk + lo;
+  const double rho = W.rho[lo];
+  double* delta = W.Delta + (size_t)(lo + i) * N + lo;
+  int org;
+  double tlo, thi;
+  if (i < Kp - 1) {
+    const double mid = 0.5 * (Dk[i] + Dk[i + 1]);
+    double f = 1.0;
+    for (int j = 0; j < Kp; ++j) f += rho * Zk[j] * Zk[j] / (Dk[j] - mid);
+    if (f >= 0.0) { org = i; tlo = 0.0; thi = mid - Dk[i]; }
+    else { org = i + 1; tlo = mid - Dk[i + 1]; thi = 0.0; }
+  } else {
+    org = i;
+    double zz = 0.0;
+    for (int j = 0; j < Kp; ++j) zz += Zk[j] * Zk[j];
+    tlo = 0.0;
+    thi = rho * zz;
+  }
+  const double Dorg = Dk[org];
+  double tau = 0.5 * (tlo + thi);
+  for (int it = 0; it < 200; ++it) {
+    double psi = 0.0, dpsi = 0.0, phi = 0.0, dphi = 0.0;
+    for (int j = 0; j < Kp; ++j) {
+      const double dl = (Dk[j] - Dorg) - tau;
+      const double tv = rho * Zk[j] * Zk[j] / dl;
+      if (j <= i) { psi += tv; dpsi += tv / dl; }
+      else { phi += tv; dphi += tv / dl; }
+    }
+    const double f = 1.0 + psi + phi;
+    if (f == 0.0) break;
+    if (f > 0.0) thi = tau; else tlo = tau;
+    const double Dl = (Dk[i] - Dorg) - tau;
+    const double sl = Dl * Dl * dpsi;
+    double nt = NAN;
+    if (i < Kp - 1) {
+      const double Dr = (Dk[i + 1] - Dorg) - tau;
+      const double sr = Dr * Dr * dphi;
+      const double c = f - sl / Dl - sr / Dr;
+      const double A2 = c, B2 = -(c * (Dl + Dr) + sl + sr), C2 = c * Dl * Dr + sl * Dr + sr * Dl;
+      double c1 = NAN, c2 = NAN;
+      if (A2 == 0.0) { if (B2 != 0.0) c1 = -C2 / B2; }
+      else {
+        double disc = B2 * B2 - 4.0 * A2 * C2;
+        if (disc < 0.0) disc = 0.0;
+        const double q = -0.5 * (B2 + copysign(sqrt(disc), B2));
+        c1 = q / A2;
+        if (q != 0.0) c2 = C2 / q;
+      }
+      if (isfinite(c1) && tau + c1 > tlo && tau + c1 < thi) nt = tau + c1;
+      else if (isfinite(c2) && tau + c2 > tlo && tau + c2 < thi) nt = tau + c2;
+    } else {
+      const double c = f - sl / Dl;
+      if (c != 0.0) {
+        const double t2 = tau + Dl + sl / c;
+        if (isfinite(t2) && t2 > tlo && t2 < thi) nt = t2;
+      }
+    }
+    if (!isfinite(nt)) nt = 0.5 * (tlo + thi);
+    const bool done = fabs(nt - tau) <= 2.0 * kEps * fmax(fabs(nt), fabs(tau)) ||
+                      (thi - tlo) <= 4.0 * kEps * fmax(fabs(tlo), fabs(thi));
+    tau = nt;
+    if (done) break;
+    if (it == 199) atomicExch(err, 1);
+  }
+  for (int j = 0; j < Kp; ++j) delta[j] = (Dk[j] - Dorg) - tau;
+  W.lamk[lo + i] = Dorg + tau;
+}
+
+// Phase 3: Loewner-corrected z:  zhat_j^2 = (lam_last - D_j)/rho * prod_{i<j} (lam_i - D_j)/(D_i - D_j)
+//                                           * prod_{i>j} (lam_{i-1} - D_j)/(D_i - D_j)
+__global__ void k_dc_zhat(const MergeDesc* __restrict__ merges, const int* __restrict__ mergeof, int N, DcWork W) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= N) return;
+  const int mi = mergeof[p];
+  if (mi < 0) return;
+  const int lo = merges[mi].lo;
+  const int j = p - lo;
+  const int Kp = W.Kp[lo];
+  if (j >= Kp) return;
+  const double* Dk = W.Dk + lo;
+  const double rho = W.rho[lo];
+  auto delta = [&](int i) { return W.Delta[(size_t)(lo + i) * N + lo + j]; };
+  double prod = -delta(Kp - 1) / rho;
+  for (int i = 0; i < j; ++i) prod *= (-delta(i)) / (Dk[i] - Dk[j]);
+  for (int i = j + 1; i < Kp; ++i) prod *= (-delta(i - 1)) / (Dk[i] - Dk[j]);
+  W.Zw[lo + j] = copysign(sqrt(fmax(prod, 0.0)), W.Zk[lo + j]);
+}
+
+// Phase 4: eigenvector columns u_i = zhat / delta_i, normalised, written over Delta.
+__global__ void k_dc_vecs(const MergeDesc* __restrict__ merges, const int* __restrict__ mergeof, int N, DcWork W) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= N) return;
+  const int mi = mergeof[p];
+  if (mi < 0) return;
+  const int lo = merges[mi].lo;
+  const int i = p - lo;
+  const int Kp = W.Kp[lo];
+  if (i >= Kp) return;
+  double* col = W.Delta + (size_t)(lo + i) * N + lo;
+  double nrm = 0.0;
+  for (int j = 0; j < Kp; ++j) { double u = W.Zw[lo + j] / col[j]; col[j] = u; nrm += u * u; }
+  const double inv = 1.0 / sqrt(nrm);
+  for (int j = 0; j < Kp; ++j) col[j] *= inv;
+}
+
+// Phase 5: Qtmp[lo:hi, lo+i] = Q[lo:hi, colk] U[:, i] (i < Kp); deflated columns copied after them.
+constexpr int DG_T = 32;
+__global__ void __launch_bounds__(256)
+k_dc_gemm(const MergeDesc* __restrict__ merges, int N, DcWork W) {
+  const MergeDesc mg = merges[blockIdx.z];
+  const int lo = mg.lo, K = mg.hi - mg.lo;
+  const int Kp = W.Kp[lo];
+  const int r0 = blockIdx.x * DG_T, c0 = blockIdx.y * DG_T;
+  if (r0 >= K || c0 >= K) return;
+  __shared__ double As[DG_T][DG_T + 1], Bs[DG_T][DG_T + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[2][2] = {{0, 0}, {0, 0}};
+  for (int k0 = 0; k0 < Kp; k0 += DG_T) {
+    for (int e2 = threadIdx.x; e2 < DG_T * DG_T; e2 += 256) {
+      int rr = e2 % DG_T, kk = e2 / DG_T;
+      int row = r0 + rr, kidx = k0 + kk;
+      As[kk][rr] = (row < K && kidx < Kp) ? W.Q[(size_t)W.colk[lo + kidx] * N + lo + row] : 0.0;
+      int ci = c0 + rr;   // reuse rr as column index for B tile: Bs[kk][col]
+      Bs[kk][rr] = (ci < Kp && kidx < Kp) ? W.Delta[(size_t)(lo + ci) * N + lo + kidx] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < DG_T; ++kk)
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) acc[a][b] = fma(As[kk][ty + 16 * a], Bs[kk][tx + 16 * b], acc[a][b]);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      int row = r0 + ty + 16 * a, c = c0 + tx + 16 * b;
+      if (row >= K || c >= K) continue;
+      double val;
+      if (c < Kp) val = acc[a][b];
+      else val = W.Q[(size_t)W.cold[lo + (c - Kp)] * N + lo + row];
+      W.Qtmp[(size_t)(lo + c) * N + lo + row] = val;
+    }
+}
+
+// Phase 6: order the merged spectrum ascending and move columns back into Q.
+__global__ void __launch_bounds__(256)
+k_dc_finish(const MergeDesc* __restrict__ merges, int N, DcWork W) {
+  const MergeDesc mg = merges[blockIdx.x];
+  const int lo = mg.lo, K = mg.hi - mg.lo;
+  const int Kp = W.Kp[lo];
+  int* perm = W.perm + lo;
+  if (threadIdx.x == 0) {
+    for (int t = 0; t < K; ++t) W.lamtmp[lo + t] = (t < Kp) ? W.lamk[lo + t] : W.Dd[lo + t - Kp];
+    // merge two ascending lists (kept roots, deflated poles); deflated list may be slightly unsorted
+    for (int t = 0; t < K; ++t) perm[t] = t;
+    for (int a = 1; a < K; ++a) {
+      int key = perm[a];
+      double kv = W.lamtmp[lo + key];
+      int b = a - 1;
+      while (b >= 0 && W.lamtmp[lo + perm[b]] > kv) { perm[b + 1] = perm[b]; --b; }
+      perm[b + 1] = key;
+    }
+    for (int t = 0; t < K; ++t) W.lam[lo + t] = W.lamtmp[lo + perm[t]];
+  }
+  __syncthreads();
+  for (int e2 = threadIdx.x; e2 < K * K; e2 += blockDim.x) {
+    int row = e2 % K, c = e2 / K;
+    W.Q[(size_t)(lo + c) * N + lo + row] = W.Qtmp[(size_t)(lo + perm[c]) * N + lo + row];
+  }
+}
+
+// Back-transformation of the top columns through the reflectors: one warp per output column.
+template <class T>
+__global__ void k_backtransform(const double* __restrict__ A, int lda, const double* __restrict__ tau, int N,
+                                const double* __restrict__ Q, const double* __restrict__ lam, int nkeep,
+                                double* __restrict__ w, T* __restrict__ U, int ldu) {
+  extern __shared__ double zs[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (c >= nkeep) return;
+  double* z = zs + (size_t)warp * N;
+  const int src = N - 1 - c;
+  for (int t = lane; t < N; t += 32) z[t] = Q[(size_t)src * N + t];
+  __syncwarp();
+  for (int k = N - 3; k >= 0; --k) {
+    const double tk = tau[k];
+    if (tk == 0.0) continue;
+    const double* v = A + (size_t)k * lda + k + 1;
+    const int L = N - k - 1;
+    double acc = 0.0;
+    for (int t = lane; t < L; t += 32) acc += v[t] * z[k + 1 + t];
+    acc = warp_sum(acc) * tk;
+    for (int t = lane; t < L; t += 32) z[k + 1 + t] -= acc * v[t];
+    __syncwarp();
+  }
+  for (int t = lane; t < N; t += 32) U[(size_t)c * ldu + t] = T(z[t]);
+  if (lane == 0) w[c] = lam[src];
+}
+
+// ------------------------------------------------------------------------------------ host side
+struct Plan {
+  std::vector<MergeDesc> merges;      // all levels, deepest first
+  std::vector<int> level_off;         // offsets into merges per level (+ end)
+  std::vector<int> mergeof;           // per level: N entries
+};
+
+void build_plan(int N, Plan& pl) {
+  std::vector<std::vector<MergeDesc>> by_depth;
+  struct Node { int lo, hi, depth; };
+  std::vector<Node> stack{{0, N, 0}};
+  while (!stack.empty()) {
+    Node nd = stack.back();
+    stack.pop_back();
+    if (nd.hi - nd.lo <= 1) continue;
+    int mid = (nd.lo + nd.hi) / 2;
+    if ((int)by_depth.size() <= nd.depth) by_depth.resize(nd.depth + 1);
+    by_depth[nd.depth].push_back({nd.lo, mid, nd.hi});
+    stack.push_back({nd.lo, mid, nd.depth + 1});
+    stack.push_back({mid, nd.hi, nd.depth + 1});
+  }
+  pl.merges.clear();
+  pl.level_off.clear();
+  pl.mergeof.clear();
+  for (int dpt = (int)by_depth.size() - 1; dpt >= 0; --dpt) {
+    pl.level_off.push_back((int)pl.merges.size());
+    std::vector<int> mo(N, -1);
+    int base = (int)pl.merges.size();
+    for (size_t q = 0; q < by_depth[dpt].size(); ++q) {
+      const MergeDesc& m = by_depth[dpt][q];
+      for (int t = m.lo; t < m.hi; ++t) mo[t] = (int)q;
+      pl.merges.push_back(m);
+    }
+    (void)base;
+    pl.mergeof.insert(pl.mergeof.end(), mo.begin(), mo.end());
+  }
+  pl.level_off.push_back((int)pl.merges.size());
+}
+
+struct PlanCacheEntry {
+  MergeDesc* d_merges = nullptr;
+  int* d_mergeof = nullptr;
+  Plan plan;
+};
+
+std::mutex g_plan_mu;
+std::map<std::pair<int, int>, PlanCacheEntry> g_plans;   // (device, N)
+
+const PlanCacheEntry* get_plan(int N) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_plan_mu);
+  auto key = std::make_pair(dev, N);
+  auto it = g_plans.find(key);
+  if (it != g_plans.end()) return &it->second;
+  PlanCacheEntry ent;
+  build_plan(N, ent.plan);
+  size_t nm = std::max<size_t>(1, ent.plan.merges.size());
+  size_t nmo = std::max<size_t>(1, ent.plan.mergeof.size());
+  if (cudaMalloc(&ent.d_merges, nm * sizeof(MergeDesc)) != cudaSuccess) return nullptr;
+  if (cudaMalloc(&ent.d_mergeof, nmo * sizeof(int)) != cudaSuccess) return nullptr;
+  if (!ent.plan.merges.empty())
+    cudaMemcpy(ent.d_merges, ent.plan.merges.data(), ent.plan.merges.size() * sizeof(MergeDesc), cudaMemcpyHostToDevice);
+  if (!ent.plan.mergeof.empty())
+    cudaMemcpy(ent.d_mergeof, ent.plan.mergeof.data(), ent.plan.mergeof.size() * sizeof(int), cudaMemcpyHostToDevice);
+  auto res = g_plans.emplace(key, std::move(ent));
+  return &res.first->second;
+}
+
+inline size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+size_t eig_workspace_bytes(int nmax) {
+  size_t N = std::max(nmax, 1);
+  size_t b = 0;
+  b += align_up(3 * N * sizeof(double));          // d, e, tau
+  b += align_up(N * sizeof(double));              // P
+  b += align_up(16);                              // barrier words
+  b += 3 * align_up(N * N * sizeof(double));      // Q, Qtmp, Delta
+  b += 10 * align_up(N * sizeof(double));         // lam, lamk, lamtmp, Dw, Zw, Dk, Zk, Dd, rho, spare
+  b += align_up(4 * N * sizeof(double));          // rot
+  b += 6 * align_up(N * sizeof(int));             // colk, cold, perm, Kp, nrot, spare
+  return b + 4096;
+}
+
+template <class T>
+int eig_sym_topk(double* A, int lda, int N, int nkeep, double* w, T* U, int ldu, void* work, size_t work_bytes,
+                 int* err, cudaStream_t st) {
+  if (N <= 0 || nkeep <= 0) return 0;
+  if (nkeep > N) nkeep = N;
+  if (work_bytes < eig_workspace_bytes(N)) return 1;
+  const PlanCacheEntry* pe = get_plan(N);
+  if (!pe) return 2;
+  char* p = (char*)work;
+  auto take = [&](size_t bytes) { void* q = p; p += align_up(bytes); return q; };
+  double* d = (double*)take(3 * N * sizeof(double));
+  double* e = d + N;
+  double* tau = e + N;
+  double* P = (double*)take(N * sizeof(double));
+  unsigned* bar = (unsigned*)take(16);
+  DcWork W;
+  W.Q = (double*)take((size_t)N * N * sizeof(double));
+  W.Qtmp = (double*)take((size_t)N * N * sizeof(double));
+  W.Delta = (double*)take((size_t)N * N * sizeof(double));
+  W.lam = (double*)take(N * sizeof(double));
+  W.lamk = (double*)take(N * sizeof(double));
+  W.lamtmp = (double*)take(N * sizeof(double));
+  W.Dw = (double*)take(N * sizeof(double));
+  W.Zw = (double*)take(N * sizeof(double));
+  W.Dk = (double*)take(N * sizeof(double));
+  W.Zk = (double*)take(N * sizeof(double));
+  W.Dd = (double*)take(N * sizeof(double));
+  W.rho = (double*)take(N * sizeof(double));
+  take(N * sizeof(double));
+  W.rot = (double*)take(4 * N * sizeof(double));
+  W.colk = (int*)take(N * sizeof(int));
+  W.cold = (int*)take(N * sizeof(int));
+  W.perm = (int*)take(N * sizeof(int));
+  W.Kp = (int*)take(N * sizeof(int));
+  W.nrot = (int*)take(N * sizeof(int));
+  W.mergeof = nullptr;
+
+  cudaMemsetAsync(bar, 0, 16, st);
+  cudaMemsetAsync(W.Q, 0, (size_t)N * N * sizeof(double), st);
+  cudaMemsetAsync(d, 0, 3 * N * sizeof(double), st);
+
+  // 1. tridiagonalisation (cooperative: all blocks co-resident)
+  if (N >= 3) {
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int G = std::max(1, std::min(nsm, (N + 7) / 8));
+    size_t smem = 2 * (size_t)N * sizeof(double);
+    void* args[] = {&A, &lda, &N, &d, &e, &tau, &P, &bar, &err};
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t ce = cudaLaunchCooperativeKernel((void*)k_tridiag, dim3(G), dim3(256), args, smem, st);
+    note_launch();
+    if (ce != cudaSuccess) return 3;
+  } else {
+    k_tridiag<<<1, 256, 2 * N * sizeof(double), st>>>(A, lda, N, d, e, tau, P, bar, err); note_launch();
+  }
+  // 2. divide and conquer
+  k_dc_init<<<(N + 255) / 256, 256, 0, st>>>(d, e, N, W.lam, W.Q); note_launch();
+  const Plan& pl = pe->plan;
+  const int nlev = (int)pl.level_off.size() - 1;
+  for (int lv = 0; lv < nlev; ++lv) {
+    const int m0 = pl.level_off[lv], m1 = pl.level_off[lv + 1];
+    const int nm = m1 - m0;
+    if (nm <= 0) continue;
+    const MergeDesc* dm = pe->d_merges + m0;
+    const int* dmo = pe->d_mergeof + (size_t)lv * N;
+    int kmax = 0;
+    for (int q = m0; q < m1; ++q) kmax = std::max(kmax, pl.merges[q].hi - pl.merges[q].lo);
+    k_dc_prep<<<nm, 256, 0, st>>>(dm, e, N, W); note_launch();
+    k_dc_secular<<<(N + 127) / 128, 128, 0, st>>>(dm, dmo, N, W, err); note_launch();
+    k_dc_zhat<<<(N + 127) / 128, 128, 0, st>>>(dm, dmo, N, W); note_launch();
+    k_dc_vecs<<<(N + 127) / 128, 128, 0, st>>>(dm, dmo, N, W); note_launch();
+    dim3 gg((kmax + DG_T - 1) / DG_T, (kmax + DG_T - 1) / DG_T, nm);
+    k_dc_gemm<<<gg, 256, 0, st>>>(dm, N, W); note_launch();
+    k_dc_finish<<<nm, 256, 0, st>>>(dm, N, W); note_launch();
+  }
+  // 3. back-transformation of the top nkeep columns (descending eigenvalues)
+  {
+    const int wpb = 4;
+    size_t smem = (size_t)wpb * N * sizeof(double);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k_backtransform<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_backtransform<T><<<(nkeep + wpb - 1) / wpb, 32 * wpb, smem, st>>>(A, lda, tau, N, W.Q, W.lam, nkeep, w, U, ldu); note_launch();
+  }
+  return cudaGetLastError() == cudaSuccess ? 0 : 4;
+}
+
+template int eig_sym_topk<float>(double*, int, int, int, double*, float*, int, void*, size_t, int*, cudaStream_t);
+template int eig_sym_topk<double>(double*, int, int, int, double*, double*, int, void*, size_t, int*, cudaStream_t);
+
+}  // namespace cakf

@@ -1,0 +1,100 @@
+// Internal declarations shared by the translation units of libcakf (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+#include <algorithm>
+#include "common.cuh"
+
+namespace cakf {
+
+// Count of kernels launched by this library (all threads); read by cakf_get_stats.
+long long launch_count();
+void note_launch(long long k = 1);
+
+template <class T> void prep_coords(const double* X, int n, int dim, double scale, C4<T>* out, cudaStream_t st);
+template <class T> void gather_coords(const C4<T>* X, const int* idx, int m, C4<T>* out, cudaStream_t st);
+template <class T>
+void gram_matvec(int ker, const C4<T>* Xo, const T* s, int m, T sf2, T* part, int nsplit, cudaStream_t st);
+template <class T>
+void gram_block_simt(int ker, const C4<T>* Xr, int nr, const C4<T>* Xc, int nc, const T* B, int ldb, int width,
+                     T sf2, T* Out, int ldo, cudaStream_t st);
+template <class T>
+void cg_combine(const T* part, int nsplit, const T* s, T sn2, const T* Mo, int ldm, int r, const T* t, T a2, int m,
+                T* g, const int* active, cudaStream_t st);
+template <class T>
+void gemv_t(const T* A, int lda, int rows, int cols, const T* x, T* t, const int* active, cudaStream_t st);
+template <class T>
+void cg_dots1(const T* V, int ldv, int j, const T* s, const T* g, const T* r0, const T* v, int m, double* dots,
+              const int* active, cudaStream_t st);
+template <class T>
+void cg_upd1(int j, const double* dots, T* V, T* GV, int ldv, const T* s, const T* g, int m, const int* active,
+             cudaStream_t st);
+template <class T>
+void cg_dots2(const T* V, const T* GV, int ldv, int j, int m, double* dots, const int* active, cudaStream_t st);
+template <class T>
+void cg_upd2(int j, const double* dots1, const double* dots2, T* V, T* GV, int ldv, T* r, T* v, int m, double bd_tol,
+             double rtol2_r0sq, int use_rtol, int* active, double* eta, double* alpha, int* count, cudaStream_t st);
+template <class T>
+void cg_select(int j, const T* r, const double* rep, int m, T* s, T* S, int lds, const int* active, cudaStream_t st);
+template <class T>
+void cg_init(const double* y, const double* mpred, const int* obs, int m, T* r, T* r0, T* v, double* r0sq,
+             cudaStream_t st);
+template <class T>
+void gemm_tn(const T* A, int lda, int na, const T* B, int ldb, int nb, int K, double alpha, double beta, double* C,
+             int ldc, double* part, size_t part_elems, cudaStream_t st);
+template <class T, class TB>
+void gemm_nn(int M, int N, int K, T alpha, const T* A, int lda, const TB* B, int ldb, T beta, T* C, int ldc,
+             cudaStream_t st);
+void gemm_small_f64(int ta, int tb, int M, int N, int K, double alpha, const double* A, int lda, const double* B,
+                    int ldb, double beta, double* C, int ldc, cudaStream_t st);
+template <class T> void gather_rows(const T* In, int ldi, const int* idx, int m, int cols, T* Out, int ldo, cudaStream_t st);
+template <class T>
+void scatter_add_rows(const T* In, int ldi, const int* idx, int m, int cols, T alpha, T* Out, int ldo, cudaStream_t st);
+template <class T> void rowsumsq(const T* A, int lda, int n, int cols, double beta, double* rs, cudaStream_t st);
+void predict_mean(const double* mprev, const double* mu_k, const double* mu_km1, double a, int n, double* mpred,
+                  cudaStream_t st);
+template <class T>
+void filter_out(const double* mpred, const T* PVv, int ld, int ic, double sf2, double a2, const double* rs_plus, int n,
+                double* mout, double* vout, double* rs_pw, cudaStream_t st);
+template <class T> void scale_copy(const T* In, int ldi, int n, int cols, T alpha, T* Out, int ldo, cudaStream_t st);
+template <class T>
+void smooth_out(const double* mk, const double* vk, const T* Y, int ld, int cw, int n, double* ms, double* vs,
+                cudaStream_t st);
+template <class T> void ws_obs(const int* obs, int m, const T* vk, const T* Vz, T* ws, cudaStream_t st);
+template <class T> void build_x(const T* Ws, int ldw, int cw, const T* ws, T alpha, int n, T* X, int ldx, cudaStream_t st);
+void nll_step(const double* eta, const double* alpha, const int* count, double* SS, int ic, double* nll_k, int* err,
+              cudaStream_t st);
+void set_diag(double* G, int ld, const double* lam, double scale, int r, cudaStream_t st);
+void put_block_sym(double* G, int ld, int row0, int col0, const double* B, int ldb, int nr, int nc, double scale,
+                   cudaStream_t st);
+void check_finite(const double* x, size_t n, int* err, cudaStream_t st);
+void scale_f64(double* A, int ld, int rows, int cols, double s, cudaStream_t st);
+template <class T>
+void convert_from_f64(const double* In, int ldi, int rows, int cols, T* Out, int ldo, cudaStream_t st);
+
+// Device error-flag values (the flag is an int in device memory, 0 = ok)
+constexpr int kErrNumeric = 1;
+constexpr int kErrTimeout = 2;
+
+// ---- FP64 symmetric eigensolver (eig.cu) ----
+// Workspace bytes needed for matrices up to order nmax.
+size_t eig_workspace_bytes(int nmax);
+// Top-`nkeep` eigenpairs of the symmetric N x N matrix A (FP64, column-major, lda >= N; A is
+// overwritten).  w: nkeep eigenvalues, descending (device).  U: N x nkeep eigenvectors
+// (column-major, ld = ldu) in precision T.  err: device flag raised on timeout / non-finite.
+template <class T>
+int eig_sym_topk(double* A, int lda, int N, int nkeep, double* w, T* U, int ldu, void* work, size_t work_bytes,
+                 int* err, cudaStream_t st);
+
+// ---- tensor-core Gram x block (gram_tc.cu) ----
+// Out[nr x width] (FP32, column-major, ld = ldo) = K(Xr, Xc) B with B given as bf16 (or tf32
+// bits in fp32), column-major with ld = ldb (>= nc rounded to the tile).  kind: 0 = bf16, 1 = tf32.
+int gram_block_tc(int ker, int kind, const C4<float>* Xr, int nr, const C4<float>* Xc, int nc, const void* B, int ldb,
+                  int width, float sf2, float* Out, int ldo, int* err, cudaStream_t st);
+// Convert a column-major float block (rows x cols, ld) into the operand layout of gram_block_tc.
+int gram_tc_pack_b(int kind, const float* B, int ldb, int rows, int cols, void* Bp, int ldp, cudaStream_t st);
+size_t gram_tc_packed_ld(int rows);
+int gram_tc_max_width();
+
+}  // namespace cakf

@@ -1,0 +1,830 @@
+// SIMT kernels of the CAKF/CAKS hot path (FP32 and FP64 instantiations):
+//   - Gram matvec of the CG loop:  part[p][i] = sum_{j in split p} k(xo_i, xo_j) s_j
+//   - Gram x block (plain SIMT path): Out = K(Xr, Xc) B, evaluated tile by tile, never stored
+//   - tall-skinny GEMMs (split-K transposed products, tiled NN products)
+//   - the CG / Gram-Schmidt bookkeeping of the iterative update step
+//   - gathers, scatters and row epilogues of the filter and smoother.
+#include "common.cuh"
+#include "internal.h"
+
+#include <atomic>
+
+namespace cakf {
+
+static std::atomic<long long> g_launches{0};
+long long launch_count() { return g_launches.load(); }
+void note_launch(long long k) { g_launches += k; }
+
+// ------------------------------------------------------------------------------------------
+// Coordinates
+template <class T>
+__global__ void k_prep_coords(const double* __restrict__ X, int n, int dim, double scale,
+                              C4<T>* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  C4<T> c;
+  c.x = T(scale * X[(size_t)i * dim + 0]);
+  c.y = dim > 1 ? T(scale * X[(size_t)i * dim + 1]) : T(0);
+  c.z = dim > 2 ? T(scale * X[(size_t)i * dim + 2]) : T(0);
+  c.w = T(0);
+  out[i] = c;
+}
+
+template <class T>
+__global__ void k_gather_coords(const C4<T>* __restrict__ X, const int* __restrict__ idx, int m,
+                                C4<T>* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) out[i] = X[idx[i]];
+}
+
+// ------------------------------------------------------------------------------------------
+// CG Gram matvec, split over columns; part is [nsplit][m].
+constexpr int MV_THREADS = 256;
+constexpr int MV_TILE = 256;
+
+template <int KER, class T>
+__global__ void __launch_bounds__(MV_THREADS)
+k_gram_matvec(const C4<T>* __restrict__ Xo, const T* __restrict__ s, int m, int cols_per_split,
+              T sf2, T* __restrict__ part) {
+  __shared__ C4<T> xs[MV_TILE];
+  __shared__ T ss[MV_TILE];
+  const int row = blockIdx.x * MV_THREADS + threadIdx.x;
+  const int c0 = blockIdx.y * cols_per_split;
+  const int c1 = min(m, c0 + cols_per_split);
+  C4<T> xi;
+  if (row < m) xi = Xo[row]; else { xi.x = xi.y = xi.z = xi.w = T(0); }
+  T acc = T(0);
+  for (int t0 = c0; t0 < c1; t0 += MV_TILE) {
+    const int cnt = min(MV_TILE, c1 - t0);
+    __syncthreads();
+    for (int j = threadIdx.x; j < cnt; j += MV_THREADS) { xs[j] = Xo[t0 + j]; ss[j] = s[t0 + j]; }
+    __syncthreads();
+    if (cnt == MV_TILE) {
+#pragma unroll 8
+      for (int j = 0; j < MV_TILE; ++j) acc = fma(kval<KER>(dist2(xi, xs[j]), sf2), ss[j], acc);
+    } else {
+      for (int j = 0; j < cnt; ++j) acc = fma(kval<KER>(dist2(xi, xs[j]), sf2), ss[j], acc);
+    }
+  }
+  if (row < m) part[(size_t)blockIdx.y * m + row] = acc;
+}
+
+// g = sum_p part[p] + sn2 * s - a2 * Mo t     (Mo: m x r col-major, ld = ldm)
+template <class T>
+__global__ void k_cg_combine(const T* __restrict__ part, int nsplit, const T* __restrict__ s, T sn2,
+                             const T* __restrict__ Mo, int ldm, int r, const T* __restrict__ t, T a2,
+                             int m, T* __restrict__ g, const int* __restrict__ active) {
+  if (!*active) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  T acc = T(0);
+  for (int p = 0; p < nsplit; ++p) acc += part[(size_t)p * m + i];
+  acc = fma(sn2, s[i], acc);
+  T lr = T(0);
+  for (int l = 0; l < r; ++l) lr = fma(Mo[(size_t)l * ldm + i], t[l], lr);
+  g[i] = fma(-a2, lr, acc);
+}
+
+// t[l] = sum_i A[i, l] x[i]  (A: rows x cols col-major), one warp per column, double accumulation
+template <class T>
+__global__ void k_gemv_t(const T* __restrict__ A, int lda, int rows, int cols, const T* __restrict__ x,
+                         T* __restrict__ t, const int* __restrict__ active) {
+  if (active && !*active) return;
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= cols) return;
+  const T* a = A + (size_t)warp * lda;
+  double acc = 0.0;
+  for (int i = lane; i < rows; i += 32) acc += double(a[i]) * double(x[i]);
+  acc = warp_sum(acc);
+  if (lane == 0) t[warp] = T(acc);
+}
+
+// First dot pass of CG iteration j (one block per dot):
+//   q < j: V[:, q] . g ;  j: s . g ;  j+1: s . r0 ;  j+2: g . v ;  j+3: s . s
+template <class T>
+__global__ void k_cg_dots1(const T* __restrict__ V, int ldv, int j, const T* __restrict__ s,
+                           const T* __restrict__ g, const T* __restrict__ r0, const T* __restrict__ v, int m,
+                           double* __restrict__ dots, const int* __restrict__ active) {
+  if (!*active) return;
+  const int q = blockIdx.x;
+  const T *a, *b;
+  if (q < j) { a = V + (size_t)q * ldv; b = g; }
+  else if (q == j) { a = s; b = g; }
+  else if (q == j + 1) { a = s; b = r0; }
+  else if (q == j + 2) { a = g; b = v; }
+  else { a = s; b = s; }
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) acc += double(a[i]) * double(b[i]);
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) dots[q] = acc;
+}
+
+// First G-orthogonalisation pass: d = s - V c, G d = g - GV c with c = V^T G s (= dots[0..j)).
+// d and G d are parked, unnormalised, in column j of V and GV.
+template <class T>
+__global__ void k_cg_upd1(int j, const double* __restrict__ dots, T* __restrict__ V, T* __restrict__ GV, int ldv,
+                          const T* __restrict__ s, const T* __restrict__ g, int m, const int* __restrict__ active) {
+  if (!*active) return;
+  __shared__ double c[1024];
+  for (int q = threadIdx.x; q < j; q += blockDim.x) c[q] = dots[q];
+  __syncthreads();
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  T d = s[i], gd = g[i];
+  for (int q = 0; q < j; ++q) {
+    T cq = T(c[q]);
+    d = fma(-V[(size_t)q * ldv + i], cq, d);
+    gd = fma(-GV[(size_t)q * ldv + i], cq, gd);
+  }
+  V[(size_t)j * ldv + i] = d;
+  GV[(size_t)j * ldv + i] = gd;
+}
+
+// Second dot pass: q < j: V[:, q] . (G d) ;  q = j: d . (G d)
+template <class T>
+__global__ void k_cg_dots2(const T* __restrict__ V, const T* __restrict__ GV, int ldv, int j, int m,
+                           double* __restrict__ dots, const int* __restrict__ active) {
+  if (!*active) return;
+  const int q = blockIdx.x;
+  const T* gd = GV + (size_t)j * ldv;
+  const T* a = V + (size_t)q * ldv;     // q == j: d itself
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) acc += double(a[i]) * double(gd[i]);
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) dots[q] = acc;
+}
+
+// Second pass and the update of the iterative CAKF step (appendix algorithm):
+//   c2 = V^T G d;  d <- d - V c2;  eta = d^T G d - |c2|^2;  alpha = s^T (r0 - G v) = s^T r0 - g^T v;
+//   V[:, j] = d / sqrt(eta);  GV[:, j] = G d / sqrt(eta);  v += (alpha / eta) d;  r -= (alpha / eta) G d.
+// Every block recomputes the scalars from the dot results and takes the same stop decision.
+template <class T>
+__global__ void k_cg_upd2(int j, const double* __restrict__ dots1, const double* __restrict__ dots2,
+                          T* __restrict__ V, T* __restrict__ GV, int ldv, T* __restrict__ r, T* __restrict__ v, int m,
+                          double bd_tol, double rtol2_r0sq, int use_rtol, int* __restrict__ active,
+                          double* __restrict__ eta_out, double* __restrict__ alpha_out, int* __restrict__ count) {
+  if (!*active) return;
+  __shared__ double c[1024];
+  __shared__ double sh[3];
+  for (int q = threadIdx.x; q < j; q += blockDim.x) c[q] = dots2[q];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double cc = 0.0;
+    for (int q = 0; q < j; ++q) cc += c[q] * c[q];
+    const double sg = dots1[j];
+    const double eta = dots2[j] - cc;
+    const double alpha = dots1[j + 1] - dots1[j + 2];
+    int stop = !(eta > bd_tol * sg) || !isfinite(eta) || !isfinite(alpha);
+    if (use_rtol && dots1[j + 3] <= rtol2_r0sq) stop = 1;
+    sh[0] = eta; sh[1] = alpha; sh[2] = stop;
+  }
+  __syncthreads();
+  const double eta = sh[0], alpha = sh[1];
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sh[2] != 0.0) {
+    // breakdown / converged: this direction is not used; clear the parked column
+    if (i < m) { V[(size_t)j * ldv + i] = T(0); GV[(size_t)j * ldv + i] = T(0); }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *active = 0;
+    return;
+  }
+  if (i < m) {
+    T d = V[(size_t)j * ldv + i], gd = GV[(size_t)j * ldv + i];
+    for (int q = 0; q < j; ++q) {
+      T cq = T(c[q]);
+      d = fma(-V[(size_t)q * ldv + i], cq, d);
+      gd = fma(-GV[(size_t)q * ldv + i], cq, gd);
+    }
+    const T inv = T(1.0 / sqrt(eta));
+    const T coef = T(alpha / eta);
+    V[(size_t)j * ldv + i] = d * inv;
+    GV[(size_t)j * ldv + i] = gd * inv;
+    v[i] = fma(coef, d, v[i]);
+    r[i] = fma(-coef, gd, r[i]);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) { eta_out[j] = eta; alpha_out[j] = alpha; *count = j + 1; }
+}
+
+// s = r (CG policy: the current residual) or s = the replayed action; S[:, j] = s.
+template <class T>
+__global__ void k_cg_select(int j, const T* __restrict__ r, const double* __restrict__ rep, int m,
+                            T* __restrict__ s, T* __restrict__ S, int lds, const int* __restrict__ active) {
+  if (!*active) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  T val = rep ? T(rep[(size_t)j * m + i]) : r[i];
+  s[i] = val;
+  S[(size_t)j * lds + i] = val;
+}
+
+// r0 = y - m_pred[obs] ; r = r0 ; v = 0 ; sum of squares of r0 accumulated by the caller
+template <class T>
+__global__ void k_cg_init(const double* __restrict__ y, const double* __restrict__ mpred,
+                          const int* __restrict__ obs, int m, T* __restrict__ r, T* __restrict__ r0,
+                          T* __restrict__ v, double* __restrict__ r0sq) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double val = 0.0;
+  if (i < m) {
+    val = y[i] - mpred[obs[i]];
+    r[i] = T(val);
+    r0[i] = T(val);
+    v[i] = T(0);
+  }
+  double sq = block_sum(val * val);
+  if (threadIdx.x == 0) atomicAdd(r0sq, sq);
+}
+
+// ------------------------------------------------------------------------------------------
+// Plain SIMT Gram x block:  Out[i, c] = sum_j k(xr_i, xc_j) B[j, c]   (Out, B column-major)
+constexpr int GB_BM = 64, GB_BN = 64, GB_BK = 32, GB_THREADS = 256;
+
+template <int KER, class T>
+__global__ void __launch_bounds__(GB_THREADS)
+k_gram_block_simt(const C4<T>* __restrict__ Xr, int nr, const C4<T>* __restrict__ Xc, int nc,
+                  const T* __restrict__ B, int ldb, int width, T sf2, T* __restrict__ Out, int ldo) {
+  __shared__ T Ks[GB_BK][GB_BM + 1];
+  __shared__ T Bs[GB_BK][GB_BN + 1];
+  __shared__ C4<T> xr[GB_BM];
+  const int r0 = blockIdx.x * GB_BM, n0 = blockIdx.y * GB_BN;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // 16 x 16 threads, 4 x 4 outputs each
+  if (threadIdx.x < GB_BM) {
+    int rr = r0 + threadIdx.x;
+    if (rr < nr) xr[threadIdx.x] = Xr[rr]; else { C4<T> z; z.x = z.y = z.z = T(1e30); z.w = 0; xr[threadIdx.x] = z; }
+  }
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+  __syncthreads();
+  for (int k0 = 0; k0 < nc; k0 += GB_BK) {
+    // kernel tile 64 x 32: 2048 values, 8 per thread
+    for (int e = threadIdx.x; e < GB_BM * GB_BK; e += GB_THREADS) {
+      int rr = e % GB_BM, kk = e / GB_BM;
+      int col = k0 + kk;
+      T kvv = T(0);
+      if (col < nc && r0 + rr < nr) kvv = kval<KER>(dist2(xr[rr], Xc[col]), sf2);
+      Ks[kk][rr] = kvv;
+    }
+    for (int e = threadIdx.x; e < GB_BK * GB_BN; e += GB_THREADS) {
+      int kk = e % GB_BK, cc = e / GB_BK;
+      int col = k0 + kk, c = n0 + cc;
+      Bs[kk][cc] = (col < nc && c < width) ? B[(size_t)c * ldb + col] : T(0);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < GB_BK; ++kk) {
+      T ka[4], bb[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) ka[a] = Ks[kk][ty + 16 * a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bb[b] = Bs[kk][tx + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fma(ka[a], bb[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    int rr = r0 + ty + 16 * a;
+    if (rr >= nr) continue;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      int c = n0 + tx + 16 * b;
+      if (c < width) Out[(size_t)c * ldo + rr] = acc[a][b];
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Split-K transposed product: part[z][a + b*lda_out] = sum_{t in chunk z} A[t, a] B[t, b]
+// (A: K x na, B: K x nb column-major).  Partials in double; k_reduce_splits sums them.
+constexpr int TN_T = 32;
+template <class T>
+__global__ void __launch_bounds__(256)
+k_gemm_tn_part(const T* __restrict__ A, int lda, int na, const T* __restrict__ B, int ldb, int nb,
+               int K, int chunk, double* __restrict__ part) {
+  __shared__ T As[TN_T][TN_T + 1];
+  __shared__ T Bs[TN_T][TN_T + 1];
+  const int a0 = blockIdx.x * TN_T, b0 = blockIdx.y * TN_T;
+  const int k_begin = blockIdx.z * chunk, k_end = min(K, k_begin + chunk);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float accf[2][2] = {{0, 0}, {0, 0}};
+  double accd[2][2] = {{0, 0}, {0, 0}};
+  for (int k0 = k_begin; k0 < k_end; k0 += TN_T) {
+    for (int e = threadIdx.x; e < TN_T * TN_T; e += 256) {
+      int kk = e % TN_T, cc = e / TN_T;
+      int t = k0 + kk;
+      As[kk][cc] = (t < k_end && a0 + cc < na) ? A[(size_t)(a0 + cc) * lda + t] : T(0);
+      Bs[kk][cc] = (t < k_end && b0 + cc < nb) ? B[(size_t)(b0 + cc) * ldb + t] : T(0);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < TN_T; ++kk) {
+#pragma unroll
+      for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          if (sizeof(T) == 4) accf[p][q] = fmaf(float(As[kk][ty + 16 * p]), float(Bs[kk][tx + 16 * q]), accf[p][q]);
+          else accd[p][q] = fma(double(As[kk][ty + 16 * p]), double(Bs[kk][tx + 16 * q]), accd[p][q]);
+        }
+    }
+    __syncthreads();
+  }
+  const size_t stride = (size_t)na * nb;
+#pragma unroll
+  for (int p = 0; p < 2; ++p)
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      int a = a0 + ty + 16 * p, b = b0 + tx + 16 * q;
+      if (a < na && b < nb)
+        part[blockIdx.z * stride + (size_t)b * na + a] = (sizeof(T) == 4) ? double(accf[p][q]) : accd[p][q];
+    }
+}
+
+// C[a + b*ldc] = alpha * sum_z part[z][a + b*na]  (+ beta * C)
+template <class OutT>
+__global__ void k_reduce_splits(const double* __restrict__ part, int nsplit, int na, int nb, double alpha,
+                                double beta, OutT* __restrict__ C, int ldc) {
+  size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t tot = (size_t)na * nb;
+  if (e >= tot) return;
+  double acc = 0.0;
+  for (int z = 0; z < nsplit; ++z) acc += part[z * tot + e];
+  int a = int(e % na), b = int(e / na);
+  OutT* c = C + (size_t)b * ldc + a;
+  *c = OutT(alpha * acc + (beta != 0.0 ? beta * double(*c) : 0.0));
+}
+
+// ------------------------------------------------------------------------------------------
+// Tiled NN product for tall A: C[M x N] = alpha * A[M x K] * B[K x N] + beta * C (column-major).
+// B may be double (small coefficient matrices); it is converted to T when staged.
+constexpr int NN_BM = 64, NN_BN = 64, NN_BK = 16;
+template <class T, class TB>
+__global__ void __launch_bounds__(256)
+k_gemm_nn(int M, int N, int K, T alpha, const T* __restrict__ A, int lda, const TB* __restrict__ B, int ldb,
+          T beta, T* __restrict__ C, int ldc) {
+  __shared__ T As[NN_BK][NN_BM + 1];
+  __shared__ T Bs[NN_BK][NN_BN + 1];
+  const int m0 = blockIdx.x * NN_BM, n0 = blockIdx.y * NN_BN;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+  for (int k0 = 0; k0 < K; k0 += NN_BK) {
+    for (int e = threadIdx.x; e < NN_BM * NN_BK; e += 256) {
+      int rr = e % NN_BM, kk = e / NN_BM;
+      As[kk][rr] = (m0 + rr < M && k0 + kk < K) ? A[(size_t)(k0 + kk) * lda + m0 + rr] : T(0);
+    }
+    for (int e = threadIdx.x; e < NN_BK * NN_BN; e += 256) {
+      int kk = e % NN_BK, cc = e / NN_BK;
+      Bs[kk][cc] = (k0 + kk < K && n0 + cc < N) ? T(B[(size_t)(n0 + cc) * ldb + k0 + kk]) : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < NN_BK; ++kk) {
+      T aa[4], bb[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) aa[a] = As[kk][ty + 16 * a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bb[b] = Bs[kk][tx + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fma(aa[a], bb[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    int rr = m0 + ty + 16 * a;
+    if (rr >= M) continue;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      int c = n0 + tx + 16 * b;
+      if (c >= N) continue;
+      T* p = C + (size_t)c * ldc + rr;
+      *p = (beta == T(0)) ? alpha * acc[a][b] : fma(alpha, acc[a][b], beta * *p);
+    }
+  }
+}
+
+// Small FP64 product with transposes: C = alpha op(A) op(B) + beta C  (sizes up to a few hundred)
+__global__ void k_gemm_small_f64(int ta, int tb, int M, int N, int K, double alpha, const double* __restrict__ A,
+                                 int lda, const double* __restrict__ B, int ldb, double beta, double* __restrict__ C,
+                                 int ldc) {
+  __shared__ double As[16][17], Bs[16][17];
+  int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  int row = blockIdx.x * 16 + ty, col = blockIdx.y * 16 + tx;
+  double acc = 0.0;
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    int ka = k0 + tx, kb = k0 + ty;
+    int ar = blockIdx.x * 16 + ty;
+    As[ty][tx] = (ar < M && ka < K) ? (ta ? A[(size_t)ar * lda + ka] : A[(size_t)ka * lda + ar]) : 0.0;
+    int bc = blockIdx.y * 16 + tx;
+    Bs[ty][tx] = (bc < N && kb < K) ? (tb ? B[(size_t)kb * ldb + bc] : B[(size_t)bc * ldb + kb]) : 0.0;
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) acc = fma(As[ty][kk], Bs[kk][tx], acc);
+    __syncthreads();
+  }
+  if (row < M && col < N) {
+    double* c = C + (size_t)col * ldc + row;
+    *c = alpha * acc + (beta != 0.0 ? beta * *c : 0.0);
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Row kernels
+// Out[i, c] = In[idx[i], c] for c < cols (column-major, gather rows)
+template <class T>
+__global__ void k_gather_rows(const T* __restrict__ In, int ldi, const int* __restrict__ idx, int m, int cols,
+                              T* __restrict__ Out, int ldo) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int c = blockIdx.y;
+  if (i < m && c < cols) Out[(size_t)c * ldo + i] = In[(size_t)c * ldi + idx[i]];
+}
+
+// Out[idx[i], c] += alpha * In[i, c]
+template <class T>
+__global__ void k_scatter_add_rows(const T* __restrict__ In, int ldi, const int* __restrict__ idx, int m, int cols,
+                                   T alpha, T* __restrict__ Out, int ldo) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int c = blockIdx.y;
+  if (i < m && c < cols) Out[(size_t)c * ldo + idx[i]] += alpha * In[(size_t)c * ldi + i];
+}
+
+// rs[i] = sum_c A[i, c]^2 (+ beta * rs[i])
+template <class T>
+__global__ void k_rowsumsq(const T* __restrict__ A, int lda, int n, int cols, double beta, double* __restrict__ rs) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double acc = 0.0;
+  for (int c = 0; c < cols; ++c) { double v = double(A[(size_t)c * lda + i]); acc += v * v; }
+  rs[i] = acc + (beta != 0.0 ? beta * rs[i] : 0.0);
+}
+
+// m_pred = a m_prev + (mu_k - a mu_{k-1})
+__global__ void k_predict_mean(const double* __restrict__ mprev, const double* __restrict__ mu_k,
+                               const double* __restrict__ mu_km1, double a, int n, double* __restrict__ mpred) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double b = mu_k ? (mu_k[i] - a * mu_km1[i]) : 0.0;
+  mpred[i] = a * mprev[i] + b;
+}
+
+// Filter outputs of step k:  m_k = m_pred + (P^- w);  var_k = sf2 - a^2 rs_plus - rowsumsq(P^- W)
+template <class T>
+__global__ void k_filter_out(const double* __restrict__ mpred, const T* __restrict__ PVv, int ld, int ic,
+                             double sf2, double a2, const double* __restrict__ rs_plus, int n,
+                             double* __restrict__ mout, double* __restrict__ vout, double* __restrict__ rs_pw) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double acc = 0.0;
+  for (int c = 0; c < ic; ++c) { double v = double(PVv[(size_t)c * ld + i]); acc += v * v; }
+  double pw = ic >= 0 ? double(PVv[(size_t)ic * ld + i]) : 0.0;
+  mout[i] = mpred[i] + pw;
+  vout[i] = sf2 - a2 * rs_plus[i] - acc;
+  if (rs_pw) rs_pw[i] = acc;
+}
+
+// Copy of a scaled column block: Out[:, c] = alpha * In[:, c]
+template <class T>
+__global__ void k_scale_copy(const T* __restrict__ In, int ldi, int n, int cols, T alpha, T* __restrict__ Out, int ldo) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int c = blockIdx.y;
+  if (i < n && c < cols) Out[(size_t)c * ldo + i] = alpha * In[(size_t)c * ldi + i];
+}
+
+// Smoother outputs at k: ms = m_k + Y[:, cw];  vs = v_k - rowsumsq(Y[:, 0:cw])
+template <class T>
+__global__ void k_smooth_out(const double* __restrict__ mk, const double* __restrict__ vk, const T* __restrict__ Y,
+                             int ld, int cw, int n, double* __restrict__ ms, double* __restrict__ vs) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double acc = 0.0;
+  for (int c = 0; c < cw; ++c) { double v = double(Y[(size_t)c * ld + i]); acc += v * v; }
+  ms[i] = mk[i] + double(Y[(size_t)cw * ld + i]);
+  vs[i] = vk[i] - acc;
+}
+
+// Dense vector from the sparse filter message:  out = x + scatter(v_obs - u_obs) ...
+// ws_new[i] = X[i, cw] ; then ws_new[obs] += v - Vz (done by k_ws_obs)
+template <class T>
+__global__ void k_ws_obs(const int* __restrict__ obs, int m, const T* __restrict__ vk, const T* __restrict__ Vz,
+                         T* __restrict__ ws) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) ws[obs[i]] += vk[i] - Vz[i];
+}
+
+// Y[:, c] = alpha * [Ws, ws][:, c]   (X = A^T [Ws ws] in the smoother)
+template <class T>
+__global__ void k_build_x(const T* __restrict__ Ws, int ldw, int cw, const T* __restrict__ ws, T alpha, int n,
+                          T* __restrict__ X, int ldx) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int c = blockIdx.y;
+  if (i >= n || c > cw) return;
+  X[(size_t)c * ldx + i] = alpha * (c < cw ? Ws[(size_t)c * ldw + i] : ws[i]);
+}
+
+// FP64 per-step NLL from the iteration: sum_j [ 1/2 log(2 pi eta_j) + 1/2 alpha_j^2 / eta_j ] - logdet(L)
+// where L L^T = S^T S (Cholesky in FP64, in place on the i x i Gram).  One block.
+__global__ void k_nll_step(const double* __restrict__ eta, const double* __restrict__ alpha,
+                           const int* __restrict__ count, double* __restrict__ SS, int ic, double* __restrict__ nll_k,
+                           int* __restrict__ err) {
+  __shared__ double s_piv;
+  __shared__ int s_bad;
+  const int j = *count;
+  if (threadIdx.x == 0) s_bad = 0;
+  __syncthreads();
+  // Cholesky of the leading j x j block (column-major, ld = ic), right-looking
+  for (int p = 0; p < j; ++p) {
+    if (threadIdx.x == 0) {
+      double d = SS[(size_t)p * ic + p];
+      if (!(d > 0.0) || !isfinite(d)) { s_bad = 1; d = 1.0; }
+      s_piv = sqrt(d);
+      SS[(size_t)p * ic + p] = s_piv;
+    }
+    __syncthreads();
+    for (int q = p + 1 + threadIdx.x; q < j; q += blockDim.x) SS[(size_t)p * ic + q] /= s_piv;
+    __syncthreads();
+    for (int e = threadIdx.x; e < (j - p - 1) * (j - p - 1); e += blockDim.x) {
+      int q = p + 1 + e % (j - p - 1), c = p + 1 + e / (j - p - 1);
+      if (q >= c) SS[(size_t)c * ic + q] -= SS[(size_t)p * ic + q] * SS[(size_t)p * ic + c];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double acc = 0.0;
+    const double l2pi = 1.8378770664093453;
+    for (int q = 0; q < j; ++q) {
+      acc += 0.5 * (l2pi + log(eta[q])) + 0.5 * alpha[q] * alpha[q] / eta[q];
+      acc -= log(SS[(size_t)q * ic + q]);
+    }
+    *nll_k = acc;
+    if (s_bad || !isfinite(acc)) atomicExch(err, 1);
+  }
+}
+
+__global__ void k_set_diag(double* __restrict__ G, int ld, const double* __restrict__ lam, double scale, int r) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < r) G[(size_t)i * ld + i] = scale * lam[i];
+}
+
+// Fill the upper-right / lower-left border of the truncation Gram from an r x i block B (double)
+__global__ void k_put_block_sym(double* __restrict__ G, int ld, int row0, int col0, const double* __restrict__ B,
+                                int ldb, int nr, int nc, double scale) {
+  int a = blockIdx.x * blockDim.x + threadIdx.x;
+  int b = blockIdx.y;
+  if (a >= nr || b >= nc) return;
+  double v = scale * B[(size_t)b * ldb + a];
+  G[(size_t)(col0 + b) * ld + row0 + a] = v;
+  G[(size_t)(row0 + a) * ld + col0 + b] = v;
+}
+
+__global__ void k_check_finite(const double* __restrict__ x, size_t n, int* __restrict__ err) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && !isfinite(x[i])) atomicExch(err, 1);
+}
+
+
+__global__ void k_scale_f64(double* __restrict__ A, int ld, int rows, int cols, double s) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int c = blockIdx.y;
+  if (i < rows && c < cols) A[(size_t)c * ld + i] *= s;
+}
+
+template <class T>
+__global__ void k_convert_from_f64(const double* __restrict__ In, int ldi, int rows, int cols, T* __restrict__ Out,
+                                   int ldo) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int c = blockIdx.y;
+  if (i < rows && c < cols) Out[(size_t)c * ldo + i] = T(In[(size_t)c * ldi + i]);
+}
+
+// ------------------------------------------------------------------------------------------
+// Host-side launchers
+static inline unsigned cdiv(size_t a, size_t b) { return unsigned((a + b - 1) / b); }
+
+template <class T>
+void prep_coords(const double* X, int n, int dim, double scale, C4<T>* out, cudaStream_t st) {
+  if (n <= 0) return;
+  k_prep_coords<T><<<cdiv(n, 256), 256, 0, st>>>(X, n, dim, scale, out); note_launch();
+}
+template <class T>
+void gather_coords(const C4<T>* X, const int* idx, int m, C4<T>* out, cudaStream_t st) {
+  if (m <= 0) return;
+  k_gather_coords<T><<<cdiv(m, 256), 256, 0, st>>>(X, idx, m, out); note_launch();
+}
+
+template <class T>
+void gram_matvec(int ker, const C4<T>* Xo, const T* s, int m, T sf2, T* part, int nsplit, cudaStream_t st) {
+  if (m <= 0) return;
+  int cps = (m + nsplit - 1) / nsplit;
+  dim3 grid(cdiv(m, MV_THREADS), nsplit);
+  switch (ker) {
+    case 0: k_gram_matvec<0, T><<<grid, MV_THREADS, 0, st>>>(Xo, s, m, cps, sf2, part); note_launch(); break;
+    case 1: k_gram_matvec<1, T><<<grid, MV_THREADS, 0, st>>>(Xo, s, m, cps, sf2, part); note_launch(); break;
+    default: k_gram_matvec<2, T><<<grid, MV_THREADS, 0, st>>>(Xo, s, m, cps, sf2, part); note_launch(); break;
+  }
+}
+
+template <class T>
+void gram_block_simt(int ker, const C4<T>* Xr, int nr, const C4<T>* Xc, int nc, const T* B, int ldb, int width,
+                     T sf2, T* Out, int ldo, cudaStream_t st) {
+  if (nr <= 0 || width <= 0) return;
+  dim3 grid(cdiv(nr, GB_BM), cdiv(width, GB_BN));
+  switch (ker) {
+    case 0: k_gram_block_simt<0, T><<<grid, GB_THREADS, 0, st>>>(Xr, nr, Xc, nc, B, ldb, width, sf2, Out, ldo); note_launch(); break;
+    case 1: k_gram_block_simt<1, T><<<grid, GB_THREADS, 0, st>>>(Xr, nr, Xc, nc, B, ldb, width, sf2, Out, ldo); note_launch(); break;
+    default: k_gram_block_simt<2, T><<<grid, GB_THREADS, 0, st>>>(Xr, nr, Xc, nc, B, ldb, width, sf2, Out, ldo); note_launch(); break;
+  }
+}
+
+template <class T>
+void cg_combine(const T* part, int nsplit, const T* s, T sn2, const T* Mo, int ldm, int r, const T* t, T a2, int m,
+                T* g, const int* active, cudaStream_t st) {
+  k_cg_combine<T><<<cdiv(m, 256), 256, 0, st>>>(part, nsplit, s, sn2, Mo, ldm, r, t, a2, m, g, active); note_launch();
+}
+template <class T>
+void gemv_t(const T* A, int lda, int rows, int cols, const T* x, T* t, const int* active, cudaStream_t st) {
+  if (cols <= 0) return;
+  k_gemv_t<T><<<cdiv((size_t)cols * 32, 256), 256, 0, st>>>(A, lda, rows, cols, x, t, active); note_launch();
+}
+template <class T>
+void cg_dots1(const T* V, int ldv, int j, const T* s, const T* g, const T* r0, const T* v, int m, double* dots,
+              const int* active, cudaStream_t st) {
+  k_cg_dots1<T><<<j + 4, 256, 0, st>>>(V, ldv, j, s, g, r0, v, m, dots, active); note_launch();
+}
+template <class T>
+void cg_upd1(int j, const double* dots, T* V, T* GV, int ldv, const T* s, const T* g, int m, const int* active,
+             cudaStream_t st) {
+  k_cg_upd1<T><<<cdiv(m, 256), 256, 0, st>>>(j, dots, V, GV, ldv, s, g, m, active); note_launch();
+}
+template <class T>
+void cg_dots2(const T* V, const T* GV, int ldv, int j, int m, double* dots, const int* active, cudaStream_t st) {
+  k_cg_dots2<T><<<j + 1, 256, 0, st>>>(V, GV, ldv, j, m, dots, active); note_launch();
+}
+template <class T>
+void cg_upd2(int j, const double* dots1, const double* dots2, T* V, T* GV, int ldv, T* r, T* v, int m, double bd_tol,
+             double rtol2_r0sq, int use_rtol, int* active, double* eta, double* alpha, int* count, cudaStream_t st) {
+  k_cg_upd2<T><<<cdiv(m, 256), 256, 0, st>>>(j, dots1, dots2, V, GV, ldv, r, v, m, bd_tol, rtol2_r0sq, use_rtol,
+                                             active, eta, alpha, count);
+  note_launch();
+}
+template <class T>
+void cg_select(int j, const T* r, const double* rep, int m, T* s, T* S, int lds, const int* active, cudaStream_t st) {
+  k_cg_select<T><<<cdiv(m, 256), 256, 0, st>>>(j, r, rep, m, s, S, lds, active); note_launch();
+}
+template <class T>
+void cg_init(const double* y, const double* mpred, const int* obs, int m, T* r, T* r0, T* v, double* r0sq,
+             cudaStream_t st) {
+  k_cg_init<T><<<cdiv(m, 256), 256, 0, st>>>(y, mpred, obs, m, r, r0, v, r0sq); note_launch();
+}
+
+template <class T>
+void gemm_tn(const T* A, int lda, int na, const T* B, int ldb, int nb, int K, double alpha, double beta, double* C,
+             int ldc, double* part, size_t part_elems, cudaStream_t st) {
+  if (na <= 0 || nb <= 0) return;
+  const size_t tile_elems = (size_t)na * nb;
+  int gx = cdiv(na, TN_T), gy = cdiv(nb, TN_T);
+  int want = std::max(1, (int)(2 * 152 / std::max(1, gx * gy)));
+  int chunk_min = 256;
+  int nsplit = std::max(1, std::min(want, (K + chunk_min - 1) / chunk_min));
+  nsplit = std::max(1, std::min<int>(nsplit, (int)(part_elems / tile_elems)));
+  int chunk = (K + nsplit - 1) / nsplit;
+  chunk = ((chunk + TN_T - 1) / TN_T) * TN_T;
+  nsplit = std::max(1, (K + chunk - 1) / chunk);
+  if (K <= 0) { nsplit = 1; chunk = TN_T; }
+  k_gemm_tn_part<T><<<dim3(gx, gy, nsplit), 256, 0, st>>>(A, lda, na, B, ldb, nb, std::max(K, 0), chunk, part); note_launch();
+  k_reduce_splits<double><<<cdiv(tile_elems, 256), 256, 0, st>>>(part, nsplit, na, nb, alpha, beta, C, ldc); note_launch();
+}
+
+template <class T, class TB>
+void gemm_nn(int M, int N, int K, T alpha, const T* A, int lda, const TB* B, int ldb, T beta, T* C, int ldc,
+             cudaStream_t st) {
+  if (M <= 0 || N <= 0) return;
+  if (K <= 0) {
+    if (beta == T(1)) return;
+  }
+  k_gemm_nn<T, TB><<<dim3(cdiv(M, NN_BM), cdiv(N, NN_BN)), 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc); note_launch();
+}
+
+void gemm_small_f64(int ta, int tb, int M, int N, int K, double alpha, const double* A, int lda, const double* B,
+                    int ldb, double beta, double* C, int ldc, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return;
+  k_gemm_small_f64<<<dim3(cdiv(M, 16), cdiv(N, 16)), 256, 0, st>>>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc); note_launch();
+}
+
+template <class T>
+void gather_rows(const T* In, int ldi, const int* idx, int m, int cols, T* Out, int ldo, cudaStream_t st) {
+  if (m <= 0 || cols <= 0) return;
+  k_gather_rows<T><<<dim3(cdiv(m, 256), cols), 256, 0, st>>>(In, ldi, idx, m, cols, Out, ldo); note_launch();
+}
+template <class T>
+void scatter_add_rows(const T* In, int ldi, const int* idx, int m, int cols, T alpha, T* Out, int ldo, cudaStream_t st) {
+  if (m <= 0 || cols <= 0) return;
+  k_scatter_add_rows<T><<<dim3(cdiv(m, 256), cols), 256, 0, st>>>(In, ldi, idx, m, cols, alpha, Out, ldo); note_launch();
+}
+template <class T>
+void rowsumsq(const T* A, int lda, int n, int cols, double beta, double* rs, cudaStream_t st) {
+  k_rowsumsq<T><<<cdiv(n, 256), 256, 0, st>>>(A, lda, n, cols, beta, rs); note_launch();
+}
+void predict_mean(const double* mprev, const double* mu_k, const double* mu_km1, double a, int n, double* mpred,
+                  cudaStream_t st) {
+  k_predict_mean<<<cdiv(n, 256), 256, 0, st>>>(mprev, mu_k, mu_km1, a, n, mpred); note_launch();
+}
+template <class T>
+void filter_out(const double* mpred, const T* PVv, int ld, int ic, double sf2, double a2, const double* rs_plus, int n,
+                double* mout, double* vout, double* rs_pw, cudaStream_t st) {
+  k_filter_out<T><<<cdiv(n, 256), 256, 0, st>>>(mpred, PVv, ld, ic, sf2, a2, rs_plus, n, mout, vout, rs_pw); note_launch();
+}
+template <class T>
+void scale_copy(const T* In, int ldi, int n, int cols, T alpha, T* Out, int ldo, cudaStream_t st) {
+  if (n <= 0 || cols <= 0) return;
+  k_scale_copy<T><<<dim3(cdiv(n, 256), cols), 256, 0, st>>>(In, ldi, n, cols, alpha, Out, ldo); note_launch();
+}
+template <class T>
+void smooth_out(const double* mk, const double* vk, const T* Y, int ld, int cw, int n, double* ms, double* vs,
+                cudaStream_t st) {
+  k_smooth_out<T><<<cdiv(n, 256), 256, 0, st>>>(mk, vk, Y, ld, cw, n, ms, vs); note_launch();
+}
+template <class T>
+void ws_obs(const int* obs, int m, const T* vk, const T* Vz, T* ws, cudaStream_t st) {
+  if (m <= 0) return;
+  k_ws_obs<T><<<cdiv(m, 256), 256, 0, st>>>(obs, m, vk, Vz, ws); note_launch();
+}
+template <class T>
+void build_x(const T* Ws, int ldw, int cw, const T* ws, T alpha, int n, T* X, int ldx, cudaStream_t st) {
+  k_build_x<T><<<dim3(cdiv(n, 256), cw + 1), 256, 0, st>>>(Ws, ldw, cw, ws, alpha, n, X, ldx); note_launch();
+}
+void nll_step(const double* eta, const double* alpha, const int* count, double* SS, int ic, double* nll_k, int* err,
+              cudaStream_t st) {
+  k_nll_step<<<1, 256, 0, st>>>(eta, alpha, count, SS, ic, nll_k, err); note_launch();
+}
+void set_diag(double* G, int ld, const double* lam, double scale, int r, cudaStream_t st) {
+  if (r <= 0) return;
+  k_set_diag<<<cdiv(r, 256), 256, 0, st>>>(G, ld, lam, scale, r); note_launch();
+}
+void put_block_sym(double* G, int ld, int row0, int col0, const double* B, int ldb, int nr, int nc, double scale,
+                   cudaStream_t st) {
+  if (nr <= 0 || nc <= 0) return;
+  k_put_block_sym<<<dim3(cdiv(nr, 256), nc), 256, 0, st>>>(G, ld, row0, col0, B, ldb, nr, nc, scale); note_launch();
+}
+void scale_f64(double* A, int ld, int rows, int cols, double s, cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return;
+  k_scale_f64<<<dim3(cdiv(rows, 256), cols), 256, 0, st>>>(A, ld, rows, cols, s); note_launch();
+}
+template <class T>
+void convert_from_f64(const double* In, int ldi, int rows, int cols, T* Out, int ldo, cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return;
+  k_convert_from_f64<T><<<dim3(cdiv(rows, 256), cols), 256, 0, st>>>(In, ldi, rows, cols, Out, ldo); note_launch();
+}
+template void convert_from_f64<float>(const double*, int, int, int, float*, int, cudaStream_t);
+template void convert_from_f64<double>(const double*, int, int, int, double*, int, cudaStream_t);
+
+void check_finite(const double* x, size_t n, int* err, cudaStream_t st) {
+  if (n == 0) return;
+  k_check_finite<<<cdiv(n, 256), 256, 0, st>>>(x, n, err); note_launch();
+}
+
+#define INST(T)                                                                                                  \
+  template void prep_coords<T>(const double*, int, int, double, C4<T>*, cudaStream_t);                           \
+  template void gather_coords<T>(const C4<T>*, const int*, int, C4<T>*, cudaStream_t);                          \
+  template void gram_matvec<T>(int, const C4<T>*, const T*, int, T, T*, int, cudaStream_t);                      \
+  template void gram_block_simt<T>(int, const C4<T>*, int, const C4<T>*, int, const T*, int, int, T, T*, int,    \
+                                   cudaStream_t);                                                                \
+  template void cg_combine<T>(const T*, int, const T*, T, const T*, int, int, const T*, T, int, T*, const int*,   \
+                              cudaStream_t);                                                                     \
+  template void gemv_t<T>(const T*, int, int, int, const T*, T*, const int*, cudaStream_t);                      \
+  template void cg_dots1<T>(const T*, int, int, const T*, const T*, const T*, const T*, int, double*,          \
+                            const int*, cudaStream_t);                                                           \
+  template void cg_upd1<T>(int, const double*, T*, T*, int, const T*, const T*, int, const int*, cudaStream_t);  \
+  template void cg_dots2<T>(const T*, const T*, int, int, int, double*, const int*, cudaStream_t);               \
+  template void cg_upd2<T>(int, const double*, const double*, T*, T*, int, T*, T*, int, double, double, int,     \
+                           int*, double*, double*, int*, cudaStream_t);                                          \
+  template void cg_select<T>(int, const T*, const double*, int, T*, T*, int, const int*, cudaStream_t);          \
+  template void cg_init<T>(const double*, const double*, const int*, int, T*, T*, T*, double*, cudaStream_t);    \
+  template void gemm_tn<T>(const T*, int, int, const T*, int, int, int, double, double, double*, int, double*,   \
+                           size_t, cudaStream_t);                                                                \
+  template void gemm_nn<T, T>(int, int, int, T, const T*, int, const T*, int, T, T*, int, cudaStream_t);         \
+  template void gather_rows<T>(const T*, int, const int*, int, int, T*, int, cudaStream_t);                      \
+  template void scatter_add_rows<T>(const T*, int, const int*, int, int, T, T*, int, cudaStream_t);              \
+  template void rowsumsq<T>(const T*, int, int, int, double, double*, cudaStream_t);                             \
+  template void filter_out<T>(const double*, const T*, int, int, double, double, const double*, int, double*,   \
+                              double*, double*, cudaStream_t);                                                   \
+  template void scale_copy<T>(const T*, int, int, int, T, T*, int, cudaStream_t);                                \
+  template void smooth_out<T>(const double*, const double*, const T*, int, int, int, double*, double*,           \
+                              cudaStream_t);                                                                     \
+  template void ws_obs<T>(const int*, int, const T*, const T*, T*, cudaStream_t);                                \
+  template void build_x<T>(const T*, int, int, const T*, T, int, T*, int, cudaStream_t);
+
+INST(float)
+INST(double)
+template void gemm_nn<float, double>(int, int, int, float, const float*, int, const double*, int, float, float*, int,
+                                     cudaStream_t);
+
+}  // namespace cakf
