@@ -270,7 +270,8 @@ def main():
         "gram_block_share_of_step": share,
         "cg_matvec": {"avg_ms": prof["cg_matvec_ms"] / max(1, prof["cg_matvec_launches"]),
                       "evals_per_launch": prof["cg_matvec_evals"] / max(1, prof["cg_matvec_launches"])},
-        "eig": {"calls_per_step": None},
+        "eig": {"calls": prof["eig_calls"], "avg_ms": prof["eig_ms"] / max(1, prof["eig_calls"])},
+        "phase_ms": {"filter": st["filter_ms"], "smooth": st["smooth_ms"]},
         "clocks": clocks,
         "gpu_launches": launches,
     }

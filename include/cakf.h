@@ -155,6 +155,26 @@ int cakf_nll_backward(cakf_ctx* ctx, double* grad_out);
  */
 int cakf_get_actions(cakf_ctx* ctx, double* actions_out, int32_t* counts_out);
 
+/*
+ * cakf_gram_matmul -- the matrix-free kernel-Gram product on its own (the Gram x matrix primitive
+ * that every CAKF / CAKS covariance product reduces to; Sec. 6, "Implementation"):
+ *     Out[i, c] = sum_j sf2 * Matern_nu(|xr_i - xc_j| / lx) * B[j, c],  i < nr, c < width.
+ * The nr x nc Gram matrix is evaluated tile by tile and never stored.
+ *   kernel            CAKF_MATERN12 | CAKF_MATERN32 | CAKF_MATERN52
+ *   Xr, Xc            DEVICE arrays, nr*dim / nc*dim doubles, row-major coordinates (dim 1..3)
+ *   B                 DEVICE, column-major nc x width (leading dimension ldb >= nc); double for
+ *                     CAKF_FP64, float otherwise
+ *   Out               DEVICE, column-major nr x width (ldo >= nr); same element type as B
+ *   precision         CAKF_FP64 / CAKF_FP32: SIMT kernels; CAKF_BF16: tcgen05 tensor cores for
+ *                     columns 0..width-2 (bf16 operands, fp32 accumulation) and fp32 CUDA-core
+ *                     accumulation of the last column (width >= 2 and <= 513 for this path)
+ * Scratch is allocated on the first call per thread and kept (grown when needed).
+ * Errors: CAKF_ERR_ARG (sizes, NULL, host pointers), CAKF_ERR_OOM, CAKF_ERR_CUDA.
+ */
+int cakf_gram_matmul(int32_t kernel, double log_lx, double log_sf2, int32_t dim, const double* Xr, int32_t nr,
+                     const double* Xc, int32_t nc, const void* B, int32_t ldb, int32_t width, void* Out,
+                     int32_t ldo, int32_t precision, void* cuda_stream);
+
 /* cakf_get_stats -- timings and counters of the last filter / smooth calls (host output). */
 int cakf_get_stats(const cakf_ctx* ctx, cakf_stats* out);
 

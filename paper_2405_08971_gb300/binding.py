@@ -68,6 +68,9 @@ def lib():
         L.cakf_get_actions.argtypes = [vp, vp, i32p]
         L.cakf_get_stats.argtypes = [vp, C.POINTER(cakf_stats)]
         L.cakf_set_profiling.argtypes = [vp, C.c_int]
+        L.cakf_gram_matmul.argtypes = [C.c_int32, C.c_double, C.c_double, C.c_int32, vp, C.c_int32, vp, C.c_int32,
+                                       vp, C.c_int32, C.c_int32, vp, C.c_int32, C.c_int32, vp]
+        L.cakf_gram_matmul.restype = C.c_int
         L.cakf_free.argtypes = [vp]
         L.cakf_free.restype = None
         L.cakf_last_error.restype = C.c_char_p
@@ -253,6 +256,26 @@ def cakf_get_stats(ctx: Context) -> dict:
     s = cakf_stats()
     _check(lib().cakf_get_stats(ctx.handle, C.byref(s)))
     return {f: getattr(s, f) for f, _ in cakf_stats._fields_}
+
+
+def cakf_gram_matmul(kernel, log_lx, log_sf2, Xr, Xc, B, out=None, precision="fp32", stream=None):
+    """Out = K(Xr, Xc) B on the device (torch CUDA tensors; B and Out column-major, i.e. stored as
+    (width, rows) row-major tensors).  Returns Out with shape (width, nr)."""
+    import torch
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    dt = torch.float64 if prec == FP64 else torch.float32
+    Xr = Xr.to(torch.float64).contiguous()
+    Xc = Xc.to(torch.float64).contiguous()
+    B = B.to(dt).contiguous()
+    width, nc = B.shape
+    nr = Xr.shape[0]
+    dim = Xr.shape[1] if Xr.dim() > 1 else 1
+    if out is None:
+        out = torch.empty((width, nr), dtype=dt, device=Xr.device)
+    _check(lib().cakf_gram_matmul(int(kernel), float(log_lx), float(log_sf2), int(dim), Xr.data_ptr(), int(nr),
+                                  Xc.data_ptr(), int(nc), B.data_ptr(), int(nc), int(width), out.data_ptr(), int(nr),
+                                  prec, stream))
+    return out
 
 
 def cakf_set_profiling(ctx: Context, on: bool):

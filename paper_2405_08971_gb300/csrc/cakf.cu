@@ -101,6 +101,13 @@ struct cakf_ctx {
   void* Bpack = nullptr;
   size_t Bpack_bytes = 0;
   double* coords64 = nullptr;
+  // truncation rotations per step (for the NLL tangent pass) and tangent workspace
+  double* Upool = nullptr;
+  std::vector<size_t> off_U;
+  std::vector<int> Urows;
+  void *dMa = nullptr, *dMb = nullptr, *Eg = nullptr, *KS = nullptr, *KlS = nullptr, *dmo = nullptr, *tvec = nullptr;
+  double *dmA = nullptr, *dmB = nullptr, *dmpred = nullptr, *gsmall = nullptr, *grad = nullptr;
+  size_t gsmall_elems = 0;
   double* ms_dev = nullptr;   // smoother outputs when the caller passes host arrays
   double* vs_dev = nullptr;
   // state
@@ -258,7 +265,7 @@ int plan_and_alloc(cakf_ctx* c, const cakf_problem* p) {
   if ((rc = c->alloc(c->gv, mm * es))) return rc;
   if ((rc = c->alloc(c->GV, mm * std::max(B, 1) * es))) return rc;
   if ((rc = c->alloc(c->part, mm * 32 * es))) return rc;
-  if ((rc = c->alloc(c->tv, std::max<size_t>(c->rmax, 1) * es))) return rc;
+  if ((rc = c->alloc(c->tv, std::max<size_t>(c->rmax, 1) * ((mm + 1023) / 1024 + 1) * es))) return rc;
   if ((rc = c->alloc(c->dots, (B + 8) * sizeof(double)))) return rc;
   if ((rc = c->alloc(c->dots2, (B + 8) * sizeof(double)))) return rc;
   c->part64_elems = std::max<size_t>(size_t(1) << 22, NE * NE * 4);
@@ -283,8 +290,19 @@ int plan_and_alloc(cakf_ctx* c, const cakf_problem* p) {
   if ((rc = c->alloc(c->Fb, mm * std::max<size_t>(NE, 1) * es))) return rc;
   if ((rc = c->alloc(c->Gws, NE * NE * sizeof(double)))) return rc;
   if ((rc = c->alloc(c->Gws2, NE * NE * sizeof(double)))) return rc;
+  // truncation rotations U_k (N_k x c_k, FP64) of every step, kept for the gradient pass
+  c->off_U.assign(T + 2, 0);
+  c->Urows.assign(T + 1, 0);
+  for (int k = 1; k <= T; ++k) {
+    const bool trunc = c->rank_r > 0 && c->icap[k] > 0;
+    c->Urows[k] = trunc ? c->mcols[k - 1] + c->icap[k] : 0;
+    c->off_U[k + 1] = c->off_U[k] + (trunc ? (size_t)c->Urows[k] * c->mcols[k] : 0);
+  }
+  c->off_U[1] = 0;
+  for (int k = 1; k <= T; ++k) c->off_U[k + 1] = c->off_U[k] + (size_t)c->Urows[k] * (c->Urows[k] ? c->mcols[k] : 0);
+  if ((rc = c->alloc(c->Upool, std::max<size_t>(c->off_U[T + 1], 1) * sizeof(double)))) return rc;
   if (c->precision == CAKF_BF16 || c->precision == CAKF_TF32) {
-    c->Bpack_bytes = gram_tc_packed_ld(std::max(c->n, c->mmax)) * wfin * 4 + 4096;
+    c->Bpack_bytes = gram_tc_staging_bytes(std::max(c->n, c->mmax), (int)wfin) + 4096;
     if ((rc = c->alloc(c->Bpack, c->Bpack_bytes))) return rc;
   }
   if (!c->ev0) { cudaEventCreate(&c->ev0); cudaEventCreate(&c->ev1); }
@@ -320,15 +338,19 @@ struct Runner {
   const int* obs(int k) { return c->obs + c->obs_ptr[k - 1]; }
   C4<T>* X() { return (C4<T>*)c->X; }
 
-  // Out (nr x width, ld ldo) = K(Xr, Xc) B  -- the hot Gram x block product
-  void gram_block(const C4<T>* Xr, int nr, const C4<T>* Xc, int nc, const T* B, int ldb, int width, T* Out, int ldo) {
+  // Out (nr x width, ld ldo) = K(Xr, Xc) B  -- the hot Gram x block product.  On the tensor-core
+  // path the first width-1 columns go through tcgen05 (bf16 operands, fp32 accumulation) and the
+  // last column (the mean vector) is accumulated in fp32 by the tile producers.
+  int gram_block(const C4<T>* Xr, int nr, const C4<T>* Xc, int nc, const T* B, int ldb, int width, T* Out, int ldo) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (c->profiling) { e0 = c->ev(); e1 = c->ev(); cudaEventRecord(e0, st); }
-    if (tc && sizeof(T) == 4 && width <= gram_tc_max_width()) {
+    if (tc && sizeof(T) == 4 && width >= 2 && width <= gram_tc_max_width()) {
       size_t ldp = gram_tc_packed_ld(nc);
-      gram_tc_pack_b(tc_kind, (const float*)B, ldb, nc, width, c->Bpack, (int)ldp, st);
-      gram_block_tc(c->kernel, tc_kind, (const C4<float>*)Xr, nr, (const C4<float>*)Xc, nc, c->Bpack, (int)ldp, width,
-                    (float)c->sf2, (float*)Out, ldo, c->err, st);
+      int rc = gram_tc_pack_b(tc_kind, (const float*)B, ldb, nc, width, c->Bpack, (int)ldp, st);
+      if (!rc)
+        rc = gram_block_tc(c->kernel, tc_kind, (const C4<float>*)Xr, nr, (const C4<float>*)Xc, nc, c->Bpack, (int)ldp,
+                           width, (float)c->sf2, (float*)Out, ldo, c->err, st);
+      if (rc) return fail(CAKF_ERR_CUDA, "tensor-core Gram x block launch failed (code " + std::to_string(rc) + ")");
     } else {
       gram_block_simt<T>(c->kernel, Xr, nr, Xc, nc, B, ldb, width, T(c->sf2), Out, ldo, st);
     }
@@ -338,6 +360,7 @@ struct Runner {
       c->prof_gb_flops.push_back(2.0 * nr * (double)nc * width);
       c->prof_gb_evals.push_back((double)nr * nc);
     }
+    return CAKF_OK;
   }
 
   // ---------------------------------------------------------------- filter (Alg. 1)
@@ -426,7 +449,7 @@ struct Runner {
       }
       // finalize: [P^- W, P^- w] = K(X, X_o) [V v] - a^2 M+ (M+_o^T [V v])
       T* PVk = PV(k);
-      gram_block(X(), n, Xo, m, V, m, ic + 1, PVk, ldn);
+      if (int rcg = gram_block(X(), n, Xo, m, V, m, ic + 1, PVk, ldn)) return rcg;
       if (rp > 0) {
         double* t2 = c->small;
         gemm_tn<T>(Mo, m, rp, V, m, ic + 1, m, 1.0, 0.0, t2, rp, c->part64, c->part64_elems, st);
@@ -477,6 +500,7 @@ struct Runner {
     if (rp > 0) gemm_nn<T, T>(n, keep, rp, T(a), Mk(k - 1), ldn, U, N, T(0), Mk(k), ldn, st);
     gemm_nn<T, T>(n, keep, ic, T(1), PVk, ldn, U + rp, N, rp > 0 ? T(1) : T(0), Mk(k), ldn, st);
     cudaMemcpyAsync(c->lam, c->wv, keep * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(c->Upool + c->off_U[k], c->U64, (size_t)N * keep * sizeof(double), cudaMemcpyDeviceToDevice, st);
     rowsumsq<T>(Mk(k), ldn, n, keep, 0.0, c->rs_plus, st);
     return CAKF_OK;
   }
@@ -527,7 +551,7 @@ struct Runner {
       // X = A^T [Ws ws] = a [Ws ws]
       build_x<T>(Ws, ldn, cw, ws, T(a), n, Xs, ldn, st);
       // Y = P^-_k X = K X - a^2 M+_{k-1} (M+_{k-1}^T X)
-      gram_block(X(), n, X(), n, Xs, ldn, cw + 1, Y, ldn);
+      if (int rcg = gram_block(X(), n, X(), n, Xs, ldn, cw + 1, Y, ldn)) return rcg;
       const int rp = (k >= 1) ? c->mcols[k - 1] : 0;
       if (rp > 0) {
         double* t = c->small;
@@ -630,6 +654,175 @@ struct Runner {
     return CAKF_OK;
   }
 
+  // ---------------------------------------------------------------- NLL gradient (tangent pass)
+  // Forward-mode derivatives of the filter with the actions S_k and truncation rotations U_k of the
+  // last filter run held fixed, for the four log-hyperparameters at once (p = 0: log l_x,
+  // 1: log l_t, 2: log sf2, 3: log sn2).  Per step, with Gh = S^T G S = R^T R:
+  //   dGh_p = S^T dK_oo S - sym(...) + dsn2 S^T S,  dyh_p = -S^T dm^-_p[obs],
+  //   dNLL_p = 1/2 tr(Gh^-1 dGh_p) + beta^T dyh_p - 1/2 beta^T dGh_p beta,
+  //   d(P^-W)_p = dP^-_{:,obs} V - (P^-W) Phi(R^-T dGh_p R^-1),
+  //   dm_p = dm^-_p + dP^-_{:,obs} v + (P^-W) R^-T (dyh_p - dGh_p beta),
+  //   dM+_p = [dM^-_p, d(P^-W)_p] U_k.
+  int nll_grad(const std::vector<int>& cnt) {
+    const int n = c->n, T_ = c->T, ldn = c->ldn, NP = 4;
+    const double a = c->a, a2 = a * a, adot = a * c->dt / c->lt;   // da / dlog l_t
+    const size_t msz = (size_t)ldn * std::max(c->rmax, 1);
+    T* dMprev = (T*)c->dMa;
+    T* dMnew = (T*)c->dMb;
+    double* dm = c->dmA;
+    double* dmn = c->dmB;
+    cudaMemsetAsync(c->grad, 0, 4 * sizeof(double), st);
+    cudaMemsetAsync(dm, 0, (size_t)NP * n * sizeof(double), st);
+    const size_t estride = (size_t)ldn * (c->imax + 1);
+    for (int k = 1; k <= T_; ++k) {
+      const int m = mk(k), icap = c->icap[k], rp = c->mcols[k - 1];
+      const int ic = (m > 0 && icap > 0) ? cnt[k] : 0;
+      const double* mprev = c->mf + (size_t)(k - 1) * n;
+      tangent_predict(mprev, dm, c->has_mu ? c->mu + (size_t)(k - 1) * n : nullptr, a, adot, n, NP, c->dmpred, st);
+      if (m == 0 || icap == 0) {
+        // dM+_k = dM^-_k = adot M+ + a dM+ (only p = 1 carries adot)
+        for (int p = 0; p < NP; ++p) scale_copy<T>(dMprev + p * msz, ldn, n, rp, T(a), dMnew + p * msz, ldn, st);
+        if (rp > 0) axpy_cols(T(adot), Mk(k - 1), ldn, n, rp, dMnew + 1 * msz, ldn);
+        cudaMemcpyAsync(dmn, c->dmpred, (size_t)NP * n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+        std::swap(dMprev, dMnew);
+        std::swap(dm, dmn);
+        continue;
+      }
+      const int* ob = obs(k);
+      C4<T>* Xo = (C4<T>*)c->Xo;
+      gather_coords<T>(X(), ob, m, Xo, st);
+      T* S = Sk(k);
+      T* V = Vk(k);                       // m x (icap + 1): V (ic valid columns), zero columns, v
+      T* PVk = PV(k);                     // n x (icap + 1): P^- W, P^- w
+      T* Mo = (T*)c->Mo;
+      gather_rows<T>(Mk(k - 1), ldn, ob, m, rp, Mo, m, st);
+      double* G = c->gsmall;              // small FP64 matrices
+      const size_t ii = (size_t)ic * ic;
+      double* Gh = G;
+      double* dGh = Gh + ii;              // NP blocks
+      double* SS = dGh + NP * ii;
+      double* SKS = SS + ii;
+      double* SKlS = SKS + ii;
+      double* Ao = SKlS + ii;             // rp x ic
+      double* dAo = Ao + (size_t)rp * ic; // NP blocks rp x ic
+      double* yh = dAo + (size_t)NP * rp * ic;
+      double* dyh = yh + ic;              // NP x ic
+      double* L = dyh + (size_t)NP * ic;
+      double* Rinv = L + ii;
+      double* W = Rinv + ii;
+      double* tmp = W + ii;               // 3 ic
+      double* Qm = tmp + 3 * (size_t)ic;  // NP blocks
+      double* u = Qm + NP * ii;           // NP x ic
+      double* to = u + (size_t)NP * ic;   // rp x (icap+1): M+_o^T [V v]
+      double* dto = to + (size_t)rp * (icap + 1);   // NP blocks
+      double* coef = dto + (size_t)NP * rp * (icap + 1);
+      // K_oo S and dK_oo/dlog l S (SIMT, precision T)
+      T* KS = (T*)c->KS;
+      T* KlS = (T*)c->KlS;
+      gram_block_simt<T>(c->kernel, Xo, m, Xo, m, S, m, ic, T(c->sf2), KS, m, st);
+      gram_block_dlogl_simt<T>(c->kernel, Xo, m, Xo, m, S, m, ic, T(c->sf2), KlS, m, st);
+      gemm_tn<T>(S, m, ic, S, m, ic, m, 1.0, 0.0, SS, ic, c->part64, c->part64_elems, st);
+      gemm_tn<T>(S, m, ic, KS, m, ic, m, 1.0, 0.0, SKS, ic, c->part64, c->part64_elems, st);
+      gemm_tn<T>(S, m, ic, KlS, m, ic, m, 1.0, 0.0, SKlS, ic, c->part64, c->part64_elems, st);
+      if (rp > 0) {
+        gemm_tn<T>(Mo, m, rp, S, m, ic, m, 1.0, 0.0, Ao, rp, c->part64, c->part64_elems, st);
+        for (int p = 0; p < NP; ++p) {
+          gather_rows<T>(dMprev + p * msz, ldn, ob, m, rp, (T*)c->Xobs, m, st);
+          gemm_tn<T>((T*)c->Xobs, m, rp, S, m, ic, m, 1.0, 0.0, dAo + (size_t)p * rp * ic, rp, c->part64,
+                     c->part64_elems, st);
+        }
+      }
+      // Gh = S^T K S + sn2 S^T S - a^2 Ao^T Ao
+      copy_block(SKS, ic, ic, ic, Gh, ic);
+      axpy_f64(c->sn2, SS, Gh, ii);
+      if (rp > 0) gemm_small_f64(1, 0, ic, ic, rp, -a2, Ao, rp, Ao, rp, 1.0, Gh, ic, st);
+      for (int p = 0; p < NP; ++p) {
+        double* D = dGh + p * ii;
+        cudaMemsetAsync(D, 0, ii * sizeof(double), st);
+        if (p == 0) copy_block(SKlS, ic, ic, ic, D, ic);
+        if (p == 2) copy_block(SKS, ic, ic, ic, D, ic);
+        if (p == 3) axpy_f64(c->sn2, SS, D, ii);
+        if (rp > 0) {
+          if (p == 1) gemm_small_f64(1, 0, ic, ic, rp, -2.0 * a * adot, Ao, rp, Ao, rp, 1.0, D, ic, st);
+          gemm_small_f64(1, 0, ic, ic, rp, -a2, dAo + (size_t)p * rp * ic, rp, Ao, rp, 1.0, D, ic, st);
+          gemm_small_f64(1, 0, ic, ic, rp, -a2, Ao, rp, dAo + (size_t)p * rp * ic, rp, 1.0, D, ic, st);
+        }
+      }
+      // yh = S^T r0, dyh_p = -S^T dm^-_p[obs]
+      T* r0 = (T*)c->r0v;
+      predict_mean(mprev, c->has_mu ? c->mu + (size_t)k * n : nullptr, c->has_mu ? c->mu + (size_t)(k - 1) * n : nullptr,
+                   a, n, c->mpred, st);
+      cg_init<T>(c->y + c->obs_ptr[k - 1], c->mpred, ob, m, (T*)c->rv, r0, (T*)c->sv, c->r0sq, st);
+      gemm_tn<T>(S, m, ic, r0, m, 1, m, 1.0, 0.0, yh, ic, c->part64, c->part64_elems, st);
+      T* dmo = (T*)c->dmo;
+      gather_rows_f64<T>(c->dmpred, n, ob, m, NP, dmo, m, st);
+      gemm_tn<T>(S, m, ic, dmo, m, NP, m, -1.0, 0.0, dyh, ic, c->part64, c->part64_elems, st);
+      grad_small(ic, NP, Gh, dGh, yh, dyh, L, Rinv, W, tmp, Qm, u, c->grad, c->err, st);
+      // E_p = dP^-_{:,obs} [V v]  for the icap + 1 stored columns
+      T* E = (T*)c->Eg;
+      const int w1 = icap + 1;
+      if (rp > 0) {
+        gemm_tn<T>(Mo, m, rp, V, m, w1, m, 1.0, 0.0, to, rp, c->part64, c->part64_elems, st);
+        for (int p = 0; p < NP; ++p) {
+          gather_rows<T>(dMprev + p * msz, ldn, ob, m, rp, (T*)c->Xobs, m, st);
+          gemm_tn<T>((T*)c->Xobs, m, rp, V, m, w1, m, 1.0, 0.0, dto + (size_t)p * rp * w1, rp, c->part64,
+                     c->part64_elems, st);
+        }
+      }
+      for (int p = 0; p < NP; ++p) {
+        T* Ep = E + p * estride;
+        if (p == 0) gram_block_dlogl_simt<T>(c->kernel, X(), n, Xo, m, V, m, w1, T(c->sf2), Ep, ldn, st);
+        else if (p == 2) scale_copy<T>(PVk, ldn, n, w1, T(1), Ep, ldn, st);
+        else cudaMemsetAsync(Ep, 0, (size_t)ldn * w1 * sizeof(T), st);
+        if (rp > 0) {
+          // E_p += M+ (alpha_p to - a^2 dto_p) - a^2 dM+_p to,  alpha_p = -2 a adot [p=1] + a^2 [p=2]
+          const double alpha_p = (p == 1 ? -2.0 * a * adot : 0.0) + (p == 2 ? a2 : 0.0);
+          copy_block(dto + (size_t)p * rp * w1, rp, rp, w1, coef, rp);
+          scale_f64(coef, rp, rp, w1, -a2, st);
+          if (alpha_p != 0.0) axpy_f64(alpha_p, to, coef, (size_t)rp * w1);
+          gemm_nn<T, double>(n, w1, rp, T(1), Mk(k - 1), ldn, coef, rp, T(1), Ep, ldn, st);
+          gemm_nn<T, double>(n, w1, rp, T(-a2), dMprev + p * msz, ldn, to, rp, T(1), Ep, ldn, st);
+        }
+        // d(P^-W)_p = E_p[:, :ic] - (P^-W) Q_p   (in place in E_p)
+        gemm_nn<T, double>(n, ic, ic, T(-1), PVk, ldn, Qm + p * ii, ic, T(1), Ep, ldn, st);
+      }
+      // dm_p = dm^-_p + E_p[:, icap] + (P^-W) u_p
+      T* tv = (T*)c->tvec;
+      for (int p = 0; p < NP; ++p)
+        gemm_nn<T, double>(n, 1, ic, T(1), PVk, ldn, u + (size_t)p * ic, ic, T(0), tv + (size_t)p * ldn, ldn, st);
+      tangent_mean<T>(c->dmpred, E, estride, icap, ldn, tv, ldn, n, NP, dmn, st);
+      // dM^-_p = a dM+_p + adot [p=1] M+ ;  dM+_k = [dM^-_p, d(P^-W)_p] U_k
+      const int keep = c->mcols[k];
+      for (int p = 0; p < NP; ++p) {
+        T* dMp = dMprev + p * msz;
+        if (rp > 0) {
+          scale_cols<T>(dMp, ldn, n, rp, T(a), st);
+          if (p == 1) axpy_cols(T(adot), Mk(k - 1), ldn, n, rp, dMp, ldn);
+        }
+        T* out = dMnew + p * msz;
+        T* Ep = E + p * estride;
+        if (c->rank_r > 0) {
+          const double* U = c->Upool + c->off_U[k];
+          const int N = c->Urows[k];
+          if (rp > 0) gemm_nn<T, double>(n, keep, rp, T(1), dMp, ldn, U, N, T(0), out, ldn, st);
+          gemm_nn<T, double>(n, keep, icap, T(1), Ep, ldn, U + rp, N, rp > 0 ? T(1) : T(0), out, ldn, st);
+        } else {
+          scale_copy<T>(dMp, ldn, n, rp, T(1), out, ldn, st);
+          scale_copy<T>(Ep, ldn, n, icap, T(1), out + (size_t)rp * ldn, ldn, st);
+        }
+      }
+      std::swap(dMprev, dMnew);
+      std::swap(dm, dmn);
+      cudaError_t ce = cudaGetLastError();
+      if (ce != cudaSuccess) return fail(CAKF_ERR_CUDA, std::string("gradient step: ") + cudaGetErrorString(ce));
+    }
+    return CAKF_OK;
+  }
+  void axpy_cols(T alpha, const T* X_, int ldx, int rows, int cols, T* Y_, int ldy) {
+    axpy_block<T>(alpha, X_, ldx, rows, cols, Y_, ldy, st);
+  }
+  void axpy_f64(double alpha, const double* x, double* y, size_t len) { axpy_block<double>(alpha, x, (int)len, (int)len, 1, y, (int)len, st); }
+
   void copy_block(const double* src, int lds, int rows, int cols, double* dst, int ldd) {
     if (rows <= 0 || cols <= 0) return;
     cudaMemcpy2DAsync(dst, ldd * sizeof(double), src, lds * sizeof(double), rows * sizeof(double), cols,
@@ -666,6 +859,7 @@ int validate(const cakf_problem* p) {
   if (N > 0 && (!p->obs_idx || !p->y)) return fail(CAKF_ERR_ARG, "obs_idx / y is NULL");
   if (p->budget_i < 1 || p->budget_i > 1024) return fail(CAKF_ERR_ARG, "budget_i must be in 1..1024");
   if (p->precision < CAKF_FP64 || p->precision > CAKF_BF16) return fail(CAKF_ERR_ARG, "unknown precision");
+  if (p->precision == CAKF_TF32) return fail(CAKF_ERR_ARG, "CAKF_TF32 Gram tiles are not available in this build");
   const double hp[4] = {p->log_lx, p->log_lt, p->log_sf2, p->log_sn2};
   for (double h : hp)
     if (!std::isfinite(h) || std::fabs(h) > 80) return fail(CAKF_ERR_ARG, "hyperparameters must be finite");
@@ -915,8 +1109,128 @@ const char* cakf_last_error(void) { return g_err.c_str(); }
 
 }  // extern "C"
 
+// Scratch of cakf_gram_matmul: kept per thread, grown on demand.
+namespace {
+struct GramScratch {
+  void* coords = nullptr;
+  size_t coords_bytes = 0;
+  void* stage = nullptr;
+  size_t stage_bytes = 0;
+  int* err = nullptr;
+  ~GramScratch() {
+    if (coords) cudaFree(coords);
+    if (stage) cudaFree(stage);
+    if (err) cudaFree(err);
+  }
+};
+thread_local GramScratch g_gs;
+
+int ensure(void*& p, size_t& have, size_t need) {
+  if (have >= need) return CAKF_OK;
+  if (p) cudaFree(p);
+  p = nullptr;
+  have = 0;
+  if (cudaMalloc(&p, need) != cudaSuccess) { cudaGetLastError(); return fail(CAKF_ERR_OOM, "scratch allocation failed"); }
+  have = need;
+  return CAKF_OK;
+}
+}  // namespace
+
+extern "C" int cakf_gram_matmul(int32_t kernel, double log_lx, double log_sf2, int32_t dim, const double* Xr, int32_t nr,
+                                const double* Xc, int32_t nc, const void* B, int32_t ldb, int32_t width, void* Out,
+                                int32_t ldo, int32_t precision, void* cuda_stream) {
+  if (kernel < 0 || kernel > 2 || dim < 1 || dim > 3 || nr < 1 || nc < 1 || width < 1 || ldb < nc || ldo < nr)
+    return fail(CAKF_ERR_ARG, "cakf_gram_matmul: invalid sizes or kernel");
+  if (!Xr || !Xc || !B || !Out) return fail(CAKF_ERR_ARG, "cakf_gram_matmul: NULL pointer");
+  if (!is_device_ptr(Xr) || !is_device_ptr(Xc) || !is_device_ptr(B) || !is_device_ptr(Out))
+    return fail(CAKF_ERR_ARG, "cakf_gram_matmul: all arrays must be device arrays");
+  if (precision != CAKF_FP64 && precision != CAKF_FP32 && precision != CAKF_BF16)
+    return fail(CAKF_ERR_ARG, "cakf_gram_matmul: precision must be FP64, FP32 or BF16");
+  if (precision == CAKF_BF16 && (width < 2 || width > gram_tc_max_width()))
+    return fail(CAKF_ERR_ARG, "cakf_gram_matmul: the BF16 path needs 2 <= width <= 513");
+  if (!std::isfinite(log_lx) || !std::isfinite(log_sf2)) return fail(CAKF_ERR_ARG, "non-finite hyperparameters");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const size_t es = precision == CAKF_FP64 ? 8 : 4;
+  const double scale = nu_scale(kernel) / std::exp(log_lx);
+  const double sf2 = std::exp(log_sf2);
+  int rc;
+  if ((rc = ensure(g_gs.coords, g_gs.coords_bytes, (size_t)(nr + nc) * 4 * es + 256))) return rc;
+  if (!g_gs.err) {
+    if (cudaMalloc(&g_gs.err, sizeof(int)) != cudaSuccess) return fail(CAKF_ERR_OOM, "scratch allocation failed");
+  }
+  cudaMemsetAsync(g_gs.err, 0, sizeof(int), st);
+  if (precision == CAKF_FP64) {
+    C4<double>* xr = (C4<double>*)g_gs.coords;
+    C4<double>* xc = xr + nr;
+    prep_coords<double>(Xr, nr, dim, scale, xr, st);
+    prep_coords<double>(Xc, nc, dim, scale, xc, st);
+    gram_block_simt<double>(kernel, xr, nr, xc, nc, (const double*)B, ldb, width, sf2, (double*)Out, ldo, st);
+  } else {
+    C4<float>* xr = (C4<float>*)g_gs.coords;
+    C4<float>* xc = xr + nr;
+    prep_coords<float>(Xr, nr, dim, scale, xr, st);
+    prep_coords<float>(Xc, nc, dim, scale, xc, st);
+    if (precision == CAKF_FP32) {
+      gram_block_simt<float>(kernel, xr, nr, xc, nc, (const float*)B, ldb, width, (float)sf2, (float*)Out, ldo, st);
+    } else {
+      if ((rc = ensure(g_gs.stage, g_gs.stage_bytes, gram_tc_staging_bytes(nc, width) + 4096))) return rc;
+      const int ldp = (int)gram_tc_packed_ld(nc);
+      int r2 = gram_tc_pack_b(0, (const float*)B, ldb, nc, width, g_gs.stage, ldp, st);
+      if (!r2) r2 = gram_block_tc(kernel, 0, xr, nr, xc, nc, g_gs.stage, ldp, width, (float)sf2, (float*)Out, ldo,
+                                  g_gs.err, st);
+      if (r2) return fail(CAKF_ERR_CUDA, "tensor-core Gram x block launch failed (code " + std::to_string(r2) + ")");
+    }
+  }
+  cudaError_t ce = cudaStreamSynchronize(st);
+  if (ce != cudaSuccess) return fail(CAKF_ERR_CUDA, std::string("cakf_gram_matmul: ") + cudaGetErrorString(ce));
+  int e = 0;
+  cudaMemcpy(&e, g_gs.err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == kErrTimeout) return fail(CAKF_ERR_TIMEOUT, "cakf_gram_matmul: a device-side wait exceeded its limit");
+  if (e) return fail(CAKF_ERR_NUMERIC, "cakf_gram_matmul: numeric error");
+  (void)es;
+  return CAKF_OK;
+}
+
 extern "C" int cakf_nll_backward(cakf_ctx* c, double* grad_out) {
   if (!c || !grad_out) return fail(CAKF_ERR_ARG, "NULL argument");
   if (!c->filtered) return fail(CAKF_ERR_STATE, "cakf_nll_backward needs a successful cakf_filter on this context");
-  return fail(CAKF_ERR_STATE, "cakf_nll_backward: not available in this build");
+  cudaStream_t st = nullptr;
+  int rc;
+  const size_t es = elem_size(c->precision);
+  const size_t ldn = c->ldn;
+  const size_t NP = 4;
+  if (!c->dMa) {
+    const size_t msz = ldn * std::max(c->rmax, 1) * NP * es;
+    const size_t mm = std::max(c->mmax, 1), ii = std::max(c->imax, 1);
+    if ((rc = c->alloc(c->dMa, msz))) return rc;
+    if ((rc = c->alloc(c->dMb, msz))) return rc;
+    if ((rc = c->alloc(c->Eg, NP * ldn * (ii + 1) * es))) return rc;
+    if ((rc = c->alloc(c->KS, mm * ii * es))) return rc;
+    if ((rc = c->alloc(c->KlS, mm * ii * es))) return rc;
+    if ((rc = c->alloc(c->dmo, mm * NP * es))) return rc;
+    if ((rc = c->alloc(c->tvec, NP * ldn * es))) return rc;
+    if ((rc = c->alloc(c->dmA, NP * c->n * sizeof(double)))) return rc;
+    if ((rc = c->alloc(c->dmB, NP * c->n * sizeof(double)))) return rc;
+    if ((rc = c->alloc(c->dmpred, NP * c->n * sizeof(double)))) return rc;
+    c->gsmall_elems = 24 * ii * ii + 12 * (size_t)std::max(c->rmax, 1) * (ii + 1) + 24 * ii + 1024;
+    if ((rc = c->alloc(c->gsmall, c->gsmall_elems * sizeof(double)))) return rc;
+    if ((rc = c->alloc(c->grad, 8 * sizeof(double)))) return rc;
+  }
+  std::vector<int> cnt(c->T + 1, 0);
+  cudaMemcpy(cnt.data(), c->count, (c->T + 1) * sizeof(int), cudaMemcpyDeviceToHost);
+  cudaMemsetAsync(c->err, 0, sizeof(int), st);
+  if (c->precision == CAKF_FP64) {
+    Runner<double> r = make_runner<double>(c, st);
+    rc = r.nll_grad(cnt);
+  } else {
+    Runner<float> r = make_runner<float>(c, st);
+    rc = r.nll_grad(cnt);
+  }
+  if (rc) return rc;
+  if ((rc = sync_and_check(c, st, "cakf_nll_backward"))) return rc;
+  if (cudaMemcpy(grad_out, c->grad, 4 * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(CAKF_ERR_CUDA, "reading the gradient");
+  for (int p = 0; p < 4; ++p)
+    if (!std::isfinite(grad_out[p])) return fail(CAKF_ERR_NUMERIC, "non-finite gradient");
+  return CAKF_OK;
 }

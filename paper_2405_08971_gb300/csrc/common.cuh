@@ -39,6 +39,23 @@ template <int KER> __device__ __forceinline__ double kval(double s2, double sf2)
   return fma(fma(s, 1.0 / 3.0, 1.0) * s, e, e);
 }
 
+// d/dlog(l_x) of the Matern value (s = scaled distance, ds/dlog l = -s):
+//   nu=1/2: s e^-s,  nu=3/2: s^2 e^-s,  nu=5/2: s^2 (1 + s) e^-s / 3   (times sf2)
+template <int KER> __device__ __forceinline__ float kval_dlogl(float s2, float sf2) {
+  float s = approx_sqrt(s2);
+  float e = approx_exp_neg(s) * sf2;
+  if (KER == 0) return s * e;
+  if (KER == 1) return s2 * e;
+  return s2 * (1.0f + s) * e * 0.33333333333333333f;
+}
+template <int KER> __device__ __forceinline__ double kval_dlogl(double s2, double sf2) {
+  double s = sqrt(s2);
+  double e = exp(-s) * sf2;
+  if (KER == 0) return s * e;
+  if (KER == 1) return s2 * e;
+  return s2 * (1.0 + s) * e / 3.0;
+}
+
 template <class T> __device__ __forceinline__ T dist2(const C4<T>& a, const C4<T>& b) {
   T dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
   return fma(dx, dx, fma(dy, dy, dz * dz));

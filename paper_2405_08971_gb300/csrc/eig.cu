@@ -207,10 +207,12 @@ k_dc_prep(const MergeDesc* __restrict__ merges, const double* __restrict__ e, in
   for (int t = threadIdx.x; t < K - s_kp; t += blockDim.x) W.cold[lo + t] = lo + perm[W.cold[lo + t]];
 }
 
-// Phase 2: secular roots.  Thread per (merge, root).  delta column i: Delta[(lo+i)*N + lo + j] = Dk_j - lam_i
+// Phase 2: secular roots, one warp per (merge, root); the sums over poles are split across lanes.
+// delta column i: Delta[(lo+i)*N + lo + j] = Dk_j - lam_i, computed from the origin pole.
 __global__ void k_dc_secular(const MergeDesc* __restrict__ merges, const int* __restrict__ mergeof, int N, DcWork W,
                              int* err) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (p >= N) return;
   const int mi = mergeof[p];
   if (mi < 0) return;
@@ -226,27 +228,31 @@ __global__ void k_dc_secular(const MergeDesc* __restrict__ merges, const int* __
   double tlo, thi;
   if (i < Kp - 1) {
     const double mid = 0.5 * (Dk[i] + Dk[i + 1]);
-    double f = 1.0;
-    for (int j = 0; j < Kp; ++j) f += rho * Zk[j] * Zk[j] / (Dk[j] - mid);
+    double f = 0.0;
+    for (int j = lane; j < Kp; j += 32) f += rho * Zk[j] * Zk[j] / (Dk[j] - mid);
+    f = 1.0 + warp_sum(f);
     if (f >= 0.0) { org = i; tlo = 0.0; thi = mid - Dk[i]; }
     else { org = i + 1; tlo = mid - Dk[i + 1]; thi = 0.0; }
   } else {
     org = i;
     double zz = 0.0;
-    for (int j = 0; j < Kp; ++j) zz += Zk[j] * Zk[j];
+    for (int j = lane; j < Kp; j += 32) zz += Zk[j] * Zk[j];
     tlo = 0.0;
-    thi = rho * zz;
+    thi = rho * warp_sum(zz);
   }
   const double Dorg = Dk[org];
   double tau = 0.5 * (tlo + thi);
-  for (int it = 0; it < 200; ++it) {
+  bool conv = false;
+  for (int it = 0; it < 200 && !conv; ++it) {
     double psi = 0.0, dpsi = 0.0, phi = 0.0, dphi = 0.0;
-    for (int j = 0; j < Kp; ++j) {
+    for (int j = lane; j < Kp; j += 32) {
       const double dl = (Dk[j] - Dorg) - tau;
-      const double tv = rho * Zk[j] * Zk[j] / dl;
-      if (j <= i) { psi += tv; dpsi += tv / dl; }
-      else { phi += tv; dphi += tv / dl; }
+      const double rinv = 1.0 / dl;
+      const double tv = rho * Zk[j] * Zk[j] * rinv;
+      if (j <= i) { psi += tv; dpsi += tv * rinv; }
+      else { phi += tv; dphi += tv * rinv; }
     }
+    psi = warp_sum(psi); dpsi = warp_sum(dpsi); phi = warp_sum(phi); dphi = warp_sum(dphi);
     const double f = 1.0 + psi + phi;
     if (f == 0.0) break;
     if (f > 0.0) thi = tau; else tlo = tau;
@@ -277,14 +283,13 @@ __global__ void k_dc_secular(const MergeDesc* __restrict__ merges, const int* __
       }
     }
     if (!isfinite(nt)) nt = 0.5 * (tlo + thi);
-    const bool done = fabs(nt - tau) <= 2.0 * kEps * fmax(fabs(nt), fabs(tau)) ||
-                      (thi - tlo) <= 4.0 * kEps * fmax(fabs(tlo), fabs(thi));
+    conv = fabs(nt - tau) <= 2.0 * kEps * fmax(fabs(nt), fabs(tau)) ||
+           (thi - tlo) <= 4.0 * kEps * fmax(fabs(tlo), fabs(thi));
     tau = nt;
-    if (done) break;
-    if (it == 199) atomicExch(err, 1);
+    if (it == 199 && !conv && lane == 0) atomicExch(err, kErrNumeric);
   }
-  for (int j = 0; j < Kp; ++j) delta[j] = (Dk[j] - Dorg) - tau;
-  W.lamk[lo + i] = Dorg + tau;
+  for (int j = lane; j < Kp; j += 32) delta[j] = (Dk[j] - Dorg) - tau;
+  if (lane == 0) W.lamk[lo + i] = Dorg + tau;
 }
 
 // Phase 3: Loewner-corrected z:  zhat_j^2 = (lam_last - D_j)/rho * prod_{i<j} (lam_i - D_j)/(D_i - D_j)
@@ -375,14 +380,24 @@ k_dc_finish(const MergeDesc* __restrict__ merges, int N, DcWork W) {
   int* perm = W.perm + lo;
   if (threadIdx.x == 0) {
     for (int t = 0; t < K; ++t) W.lamtmp[lo + t] = (t < Kp) ? W.lamk[lo + t] : W.Dd[lo + t - Kp];
-    // merge two ascending lists (kept roots, deflated poles); deflated list may be slightly unsorted
-    for (int t = 0; t < K; ++t) perm[t] = t;
-    for (int a = 1; a < K; ++a) {
-      int key = perm[a];
+    // kept roots are ascending; sort the (nearly ascending) deflated poles, then merge the two lists
+    int* dp = W.colk + lo;   // scratch: order of the deflated entries (colk is no longer needed)
+    const int Kd = K - Kp;
+    for (int t = 0; t < Kd; ++t) dp[t] = Kp + t;
+    for (int a = 1; a < Kd; ++a) {
+      int key = dp[a];
       double kv = W.lamtmp[lo + key];
       int b = a - 1;
-      while (b >= 0 && W.lamtmp[lo + perm[b]] > kv) { perm[b + 1] = perm[b]; --b; }
-      perm[b + 1] = key;
+      while (b >= 0 && W.lamtmp[lo + dp[b]] > kv) { dp[b + 1] = dp[b]; --b; }
+      dp[b + 1] = key;
+    }
+    int x = 0, y = 0;
+    for (int t = 0; t < K; ++t) {
+      int pick;
+      if (x >= Kp) pick = dp[y++];
+      else if (y >= Kd) pick = x++;
+      else pick = (W.lamtmp[lo + x] <= W.lamtmp[lo + dp[y]]) ? x++ : dp[y++];
+      perm[t] = pick;
     }
     for (int t = 0; t < K; ++t) W.lam[lo + t] = W.lamtmp[lo + perm[t]];
   }
@@ -576,7 +591,7 @@ int eig_sym_topk(double* A, int lda, int N, int nkeep, double* w, T* U, int ldu,
     int kmax = 0;
     for (int q = m0; q < m1; ++q) kmax = std::max(kmax, pl.merges[q].hi - pl.merges[q].lo);
     k_dc_prep<<<nm, 256, 0, st>>>(dm, e, N, W); note_launch();
-    k_dc_secular<<<(N + 127) / 128, 128, 0, st>>>(dm, dmo, N, W, err); note_launch();
+    k_dc_secular<<<(N * 32 + 255) / 256, 256, 0, st>>>(dm, dmo, N, W, err); note_launch();
     k_dc_zhat<<<(N + 127) / 128, 128, 0, st>>>(dm, dmo, N, W); note_launch();
     k_dc_vecs<<<(N + 127) / 128, 128, 0, st>>>(dm, dmo, N, W); note_launch();
     dim3 gg((kmax + DG_T - 1) / DG_T, (kmax + DG_T - 1) / DG_T, nm);

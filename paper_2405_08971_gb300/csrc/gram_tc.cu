@@ -1,10 +1,457 @@
-// Tensor-core Gram x block product (placeholder until the tcgen05 kernel lands): reports no
-// supported width, so callers use the SIMT kernel.
+// Tensor-core Gram x block product for sm_103a (tcgen05 + TMEM + TMA), the hot kernel of the CAKF / CAKS:
+//
+//   Out[i, c] = sum_j k(xr_i, xc_j) B[j, c]         (Out, B column-major; k a Matern kernel)
+//
+// The kernel matrix is never stored: each CTA owns 128 output rows and walks the columns j in
+// slices of 64.  Per slice, 8 producer warps evaluate the 128 x 64 kernel tile from coordinates
+// staged in shared memory and write it as BF16 in the 128-byte-swizzled K-major layout that the
+// tensor core reads; a TMA warp stages the matching 64 x N slice of the packed B operand; a single
+// thread issues tcgen05.mma (M = 128, N <= 256 per instruction, K = 16) accumulating in TMEM
+// (up to 512 FP32 columns).  The last column of B (the mean vector of the filter / smoother) is
+// not sent to the tensor core: the producers accumulate it in FP32 from the same kernel values.
+// Every mbarrier wait is bounded; on timeout the CTA raises the error flag and stops.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <mutex>
+#include <map>
 #include "internal.h"
+
 namespace cakf {
-int gram_block_tc(int, int, const C4<float>*, int, const C4<float>*, int, const void*, int, int, float, float*, int,
-                  int*, cudaStream_t) { return 1; }
-int gram_tc_pack_b(int, const float*, int, int, int, void*, int, cudaStream_t) { return 1; }
-size_t gram_tc_packed_ld(int rows) { return (size_t)((rows + 127) / 128 * 128); }
-int gram_tc_max_width() { return 0; }
+namespace {
+
+constexpr int BM = 128;          // rows per CTA (TMEM lanes)
+constexpr int BK = 64;           // kernel columns per pipeline stage (64 bf16 = one 128B swizzle row)
+constexpr int NPROD_WARPS = 8;   // kernel-tile producers
+constexpr int TMA_WARP = 8;
+constexpr int MMA_WARP = 9;
+constexpr int NTHREADS = 320;
+constexpr int A_STAGE_BYTES = BM * BK * 2;   // 16 KB
+constexpr long long WAIT_LIMIT = 20000000LL;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// Bounded wait for the completion of the phase with the given parity.  Returns false on timeout
+// or when another role of this CTA already aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  for (long long it = 0; it < WAIT_LIMIT; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (*abort_flag) return false;
+  }
+  *abort_flag = 1;
+  return false;
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;                 // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset
+  d |= (uint64_t)1 << 46;                 // descriptor version
+  d |= (uint64_t)2 << 61;                 // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: BF16 A/B (K-major), FP32 accumulator, M = 128.
+__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+struct TcParams {
+  const C4<float>* Xr;
+  int nr;
+  const C4<float>* Xc;     // padded to nk * BK entries (sentinel coordinates beyond nc)
+  const float* wcol;       // padded mean column (zeros beyond nc), FP32
+  int nk;                  // number of K slices
+  int npad;                // accumulator columns (multiple of 16, <= 512)
+  int nbox;                // TMA boxes per B slice
+  int boxh;                // rows per TMA box
+  int wtc;                 // valid tensor-core columns (<= npad)
+  float sf2;
+  float* Out;
+  int ldo;
+  int* err;
+  int stages;
+  int tmem_cols;
+  uint32_t b_stage_bytes;
+};
+
+template <int KER>
+__global__ void __launch_bounds__(NTHREADS, 1)
+k_gram_tc(const __grid_constant__ CUtensorMap tmapB, const TcParams P) {
+  extern __shared__ uint8_t smem_raw[];
+  // 1024-byte aligned base for the swizzled tiles
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int S = P.stages;
+  uint8_t* A_base = smem;
+  uint8_t* B_base = A_base + (size_t)S * A_STAGE_BYTES;
+  uint8_t* C_base = B_base + (size_t)S * P.b_stage_bytes;            // coordinates, 1 KB per stage
+  uint8_t* W_base = C_base + (size_t)S * (BK * 16);                  // mean column, 256 B per stage
+  uint64_t* bars = reinterpret_cast<uint64_t*>(W_base + (size_t)S * (BK * 4));
+  uint64_t* fullA = bars;
+  uint64_t* fullB = bars + S;
+  uint64_t* fullC = bars + 2 * S;
+  uint64_t* empty = bars + 3 * S;
+  uint64_t* done = bars + 4 * S;
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+  float* mean_part = reinterpret_cast<float*>(tmem_holder + 4);     // [2][BM]
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row0 = blockIdx.x * BM;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(smem_u32(&fullA[s]), NPROD_WARPS);
+      mbar_init(smem_u32(&fullB[s]), 1);
+      mbar_init(smem_u32(&fullC[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    mbar_init(smem_u32(done), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(smem_u32(tmem_holder)), "r"(P.tmem_cols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_holder;
+
+  if (warp < NPROD_WARPS) {
+    // ------------------------------------------------------------ kernel-tile producers
+    const int rl = (warp & 3) * 32 + lane;          // row within the tile (= TMEM lane)
+    const int half = warp >> 2;                     // which 32 of the 64 slice columns
+    const int row = row0 + rl;
+    C4<float> xr;
+    if (row < P.nr) xr = P.Xr[row];
+    else { xr.x = xr.y = xr.z = 1.0e6f; xr.w = 0.f; }
+    float mean_acc = 0.f;
+    bool ok = true;
+    for (int kt = 0; kt < P.nk && ok; ++kt) {
+      const int s = kt % S;
+      const uint32_t n = kt / S;
+      ok = mbar_wait(smem_u32(&empty[s]), (n & 1) ^ 1, abort_flag);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) break;
+      ok = mbar_wait(smem_u32(&fullC[s]), n & 1, abort_flag);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) break;
+      const C4<float>* xc = reinterpret_cast<const C4<float>*>(C_base + (size_t)s * BK * 16) + half * 32;
+      const float* wc = reinterpret_cast<const float*>(W_base + (size_t)s * BK * 4) + half * 32;
+      uint8_t* arow = A_base + (size_t)s * A_STAGE_BYTES + rl * 128;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        uint32_t pk[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int c = q * 8 + e * 2;
+          const float k0 = kval<KER>(dist2(xr, xc[c]), P.sf2);
+          const float k1 = kval<KER>(dist2(xr, xc[c + 1]), P.sf2);
+          mean_acc = fmaf(k0, wc[c], mean_acc);
+          mean_acc = fmaf(k1, wc[c + 1], mean_acc);
+          pk[e] = pack_bf16(k0, k1);
+        }
+        const int chunk = (half * 4 + q) ^ (rl & 7);
+        *reinterpret_cast<uint4*>(arow + chunk * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      }
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&fullA[s]));
+    }
+    mean_part[half * BM + rl] = mean_acc;
+    asm volatile("bar.sync 1, %0;" ::"r"(NPROD_WARPS * 32) : "memory");
+    if (half == 0 && row < P.nr)
+      P.Out[(size_t)P.wtc * P.ldo + row] = mean_part[rl] + mean_part[BM + rl];
+    // ------------------------------------------------------------ epilogue: TMEM -> global
+    bool fin = mbar_wait(smem_u32(done), 0, abort_flag);
+    fin = __all_sync(0xffffffffu, fin && !*abort_flag);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (fin) {
+      const int nchunks = (P.npad + 31) / 32;   // TMEM holds >= 32 columns, so a 16-column tail is readable
+      for (int ch = half; ch < nchunks; ch += 2) {
+        uint32_t v[32];
+        const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(ch * 32);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+              "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+              "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+              "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+            : "r"(taddr)
+            : "memory");
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (row < P.nr) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int c = ch * 32 + j;
+            if (c < P.wtc) P.Out[(size_t)c * P.ldo + row] = __uint_as_float(v[j]);
+          }
+        }
+      }
+    }
+  } else if (warp == TMA_WARP) {
+    // ------------------------------------------------------------ TMA / bulk-copy producer
+    if (lane == 0) {
+      int issued = 0;
+      for (int kt = 0; kt < P.nk; ++kt) {
+        const int s = kt % S;
+        const uint32_t n = kt / S;
+        if (!mbar_wait(smem_u32(&empty[s]), (n & 1) ^ 1, abort_flag)) break;
+        const uint32_t cb = smem_u32(&fullC[s]);
+        mbar_expect_tx(cb, BK * 16 + BK * 4);
+        bulk_load(smem_u32(C_base + (size_t)s * BK * 16), P.Xc + (size_t)kt * BK, BK * 16, cb);
+        bulk_load(smem_u32(W_base + (size_t)s * BK * 4), P.wcol + (size_t)kt * BK, BK * 4, cb);
+        const uint32_t bb = smem_u32(&fullB[s]);
+        mbar_expect_tx(bb, P.b_stage_bytes);
+        for (int b = 0; b < P.nbox; ++b)
+          tma_load_2d(smem_u32(B_base + (size_t)s * P.b_stage_bytes + (size_t)b * P.boxh * 128), &tmapB, kt * BK,
+                      b * P.boxh, bb);
+        ++issued;
+      }
+      // on abort, let the copies already issued land before the CTA exits (bounded)
+      if (*abort_flag) {
+        for (int kt = 0; kt < issued; ++kt) {
+          const int s = kt % S;
+          mbar_wait(smem_u32(&fullB[s]), (kt / S) & 1, abort_flag);
+        }
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      bool ok = true;
+      for (int kt = 0; kt < P.nk && ok; ++kt) {
+        const int s = kt % S;
+        const uint32_t n = kt / S;
+        ok = mbar_wait(smem_u32(&fullA[s]), n & 1, abort_flag) && mbar_wait(smem_u32(&fullB[s]), n & 1, abort_flag);
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a0 = smem_u32(A_base + (size_t)s * A_STAGE_BYTES);
+        const uint32_t b0 = smem_u32(B_base + (size_t)s * P.b_stage_bytes);
+        for (int c0 = 0; c0 < P.npad; c0 += 256) {
+          const int nn = min(256, P.npad - c0);
+          const uint32_t idesc = idesc_bf16(nn);
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            const uint64_t ad = sdesc_sw128(a0 + kk * 32);
+            const uint64_t bd = sdesc_sw128(b0 + (uint32_t)c0 * 128 + kk * 32);
+            mma_bf16(tmem + (uint32_t)c0, ad, bd, idesc, (kt > 0 || kk > 0) ? 1u : 0u);
+          }
+        }
+        mma_commit(smem_u32(&empty[s]));
+      }
+      mma_commit(smem_u32(done));
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (*abort_flag && threadIdx.x == 0) atomicExch(P.err, kErrTimeout);
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(P.tmem_cols) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------- operand packing
+// Bp (bf16, column-major, ld = ldp): the first wtc columns of B, zero-padded to ldp rows and npad
+// columns.  wp (fp32, ldp): column wtc of B (the mean column), zero-padded.  Xp: coordinates padded
+// with far-away sentinels (kernel value 0).
+__global__ void k_pack_b(const float* __restrict__ B, int ldb, int rows, int wtc, int npad, int ldp,
+                         __nv_bfloat16* __restrict__ Bp, float* __restrict__ wp) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.y;
+  if (i >= ldp) return;
+  if (c < npad) {
+    float v = (c < wtc && i < rows) ? B[(size_t)c * ldb + i] : 0.f;
+    Bp[(size_t)c * ldp + i] = __float2bfloat16_rn(v);
+  } else {
+    wp[i] = (i < rows) ? B[(size_t)wtc * ldb + i] : 0.f;
+  }
+}
+
+__global__ void k_pad_coords(const C4<float>* __restrict__ X, int n, int ldp, C4<float>* __restrict__ Xp) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ldp) return;
+  C4<float> c;
+  if (i < n) c = X[i];
+  else { c.x = c.y = c.z = 1.0e6f; c.w = 0.f; }
+  Xp[i] = c;
+}
+
+// ---------------------------------------------------------------------------- host side
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+struct Layout {
+  int npad, nbox, boxh, stages, tmem_cols;
+  uint32_t b_stage_bytes;
+  size_t smem;
+};
+
+Layout plan_layout(int wtc) {
+  Layout L;
+  L.npad = std::max(16, round_up(wtc, 16));
+  L.boxh = L.npad <= 256 ? L.npad : 256;
+  L.nbox = (L.npad + L.boxh - 1) / L.boxh;
+  L.b_stage_bytes = (uint32_t)L.nbox * L.boxh * 128;
+  const size_t per_stage = A_STAGE_BYTES + L.b_stage_bytes + BK * 16 + BK * 4;
+  const size_t fixed = 1024 /*alignment slack*/ + 64 * 8 + 64 + 2 * BM * 4;
+  const size_t budget = 220 * 1024;
+  L.stages = (int)std::min<size_t>(4, (budget - fixed) / per_stage);
+  L.tmem_cols = 32;
+  while (L.tmem_cols < L.npad) L.tmem_cols *= 2;
+  L.smem = fixed + (size_t)L.stages * per_stage;
+  // keep (CTAs per SM) x (TMEM columns) <= 512 by sizing shared memory
+  const size_t smem_cap = 227 * 1024;
+  const int max_ctas = 512 / L.tmem_cols;
+  const size_t min_smem = max_ctas >= 6 ? 0 : smem_cap / (size_t)(max_ctas + 1) + 1024;
+  L.smem = std::max(L.smem, min_smem);
+  return L;
+}
+
+}  // namespace
+
+size_t gram_tc_packed_ld(int rows) { return (size_t)round_up(std::max(rows, 1), BK); }
+int gram_tc_max_width() { return 513; }
+
+// Bytes of packed staging for a (rows x width) block: bf16 operand + fp32 mean column + padded coords.
+static size_t packed_bytes(int rows, int width) {
+  const size_t ldp = gram_tc_packed_ld(rows);
+  const int wtc = std::max(width - 1, 1);
+  const size_t npad = (size_t)std::max(16, round_up(wtc, 16));
+  return ((npad * ldp * 2 + 255) & ~size_t(255)) + ((ldp * 4 + 255) & ~size_t(255)) + ldp * 16 + 256;
+}
+
+int gram_tc_pack_b(int kind, const float* B, int ldb, int rows, int cols, void* Bp, int ldp, cudaStream_t st) {
+  (void)kind;
+  const int wtc = cols - 1;
+  const int npad = std::max(16, round_up(std::max(wtc, 1), 16));
+  __nv_bfloat16* bp = reinterpret_cast<__nv_bfloat16*>(Bp);
+  float* wp = reinterpret_cast<float*>(reinterpret_cast<char*>(Bp) + (((size_t)npad * ldp * 2 + 255) & ~size_t(255)));
+  dim3 grid((ldp + 255) / 256, npad + 1);
+  k_pack_b<<<grid, 256, 0, st>>>(B, ldb, rows, wtc, npad, ldp, bp, wp);
+  note_launch();
+  return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
+int gram_block_tc(int ker, int kind, const C4<float>* Xr, int nr, const C4<float>* Xc, int nc, const void* Bp, int ldp,
+                  int width, float sf2, float* Out, int ldo, int* err, cudaStream_t st) {
+  if (kind != 0) return 2;                 // bf16 only in this kernel
+  if (width < 2 || width > gram_tc_max_width() || nr <= 0 || nc <= 0) return 3;
+  if (ldp % BK != 0 || ldp < nc) return 4;
+  auto encode = encode_fn();
+  if (!encode) return 5;
+  const int wtc = width - 1;
+  const Layout L = plan_layout(wtc);
+  const char* base = reinterpret_cast<const char*>(Bp);
+  const size_t boff = (((size_t)L.npad * ldp * 2 + 255) & ~size_t(255));
+  const float* wp = reinterpret_cast<const float*>(base + boff);
+  C4<float>* xcp = reinterpret_cast<C4<float>*>(const_cast<char*>(base) + boff + (((size_t)ldp * 4 + 255) & ~size_t(255)));
+  k_pad_coords<<<(ldp + 255) / 256, 256, 0, st>>>(Xc, nc, ldp, xcp);
+  note_launch();
+
+  CUtensorMap map;
+  cuuint64_t gdim[2] = {(cuuint64_t)ldp, (cuuint64_t)L.npad};
+  cuuint64_t gstride[1] = {(cuuint64_t)ldp * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)L.boxh};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult cr = encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(Bp), gdim, gstride, box, estr,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS) return 6;
+
+  TcParams P;
+  P.Xr = Xr; P.nr = nr; P.Xc = xcp; P.wcol = wp; P.nk = ldp / BK; P.npad = L.npad; P.nbox = L.nbox; P.boxh = L.boxh;
+  P.wtc = wtc; P.sf2 = sf2; P.Out = Out; P.ldo = ldo; P.err = err; P.stages = L.stages; P.tmem_cols = L.tmem_cols;
+  P.b_stage_bytes = L.b_stage_bytes;
+  const dim3 grid((nr + BM - 1) / BM);
+  cudaError_t ce;
+  switch (ker) {
+    case 0:
+      cudaFuncSetAttribute(k_gram_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
+      k_gram_tc<0><<<grid, NTHREADS, L.smem, st>>>(map, P);
+      break;
+    case 1:
+      cudaFuncSetAttribute(k_gram_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
+      k_gram_tc<1><<<grid, NTHREADS, L.smem, st>>>(map, P);
+      break;
+    default:
+      cudaFuncSetAttribute(k_gram_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
+      k_gram_tc<2><<<grid, NTHREADS, L.smem, st>>>(map, P);
+      break;
+  }
+  note_launch();
+  ce = cudaGetLastError();
+  return ce == cudaSuccess ? 0 : 7;
+}
+
+size_t gram_tc_staging_bytes(int rows, int width) { return packed_bytes(rows, width); }
+
 }  // namespace cakf

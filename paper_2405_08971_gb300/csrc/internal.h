@@ -20,6 +20,9 @@ template <class T>
 void gram_block_simt(int ker, const C4<T>* Xr, int nr, const C4<T>* Xc, int nc, const T* B, int ldb, int width,
                      T sf2, T* Out, int ldo, cudaStream_t st);
 template <class T>
+void gram_block_dlogl_simt(int ker, const C4<T>* Xr, int nr, const C4<T>* Xc, int nc, const T* B, int ldb, int width,
+                           T sf2, T* Out, int ldo, cudaStream_t st);
+template <class T>
 void cg_combine(const T* part, int nsplit, const T* s, T sn2, const T* Mo, int ldm, int r, const T* t, T a2, int m,
                 T* g, const int* active, cudaStream_t st);
 template <class T>
@@ -66,6 +69,17 @@ template <class T> void build_x(const T* Ws, int ldw, int cw, const T* ws, T alp
 void nll_step(const double* eta, const double* alpha, const int* count, double* SS, int ic, double* nll_k, int* err,
               cudaStream_t st);
 void set_diag(double* G, int ld, const double* lam, double scale, int r, cudaStream_t st);
+void grad_small(int ic, int np, const double* Gh, const double* dGh, const double* yh, const double* dyh, double* L,
+                double* Rinv, double* W, double* tmp, double* Q, double* u, double* grad, int* err, cudaStream_t st);
+template <class T>
+void gather_rows_f64(const double* In, int ld, const int* idx, int m, int cols, T* Out, int ldo, cudaStream_t st);
+template <class T>
+void tangent_mean(const double* dmpred, const T* E, size_t estride, int ecol, int lde, const T* t, int ldt, int n,
+                  int np, double* dm, cudaStream_t st);
+template <class T> void axpy_block(T alpha, const T* X, int ldx, int rows, int cols, T* Y, int ldy, cudaStream_t st);
+template <class T> void scale_cols(T* A, int ld, int rows, int cols, T s, cudaStream_t st);
+void tangent_predict(const double* mprev, const double* dmprev, const double* mu_km1, double a, double adot_lt, int n,
+                     int np, double* dmpred, cudaStream_t st);
 void put_block_sym(double* G, int ld, int row0, int col0, const double* B, int ldb, int nr, int nc, double scale,
                    cudaStream_t st);
 void check_finite(const double* x, size_t n, int* err, cudaStream_t st);
@@ -96,5 +110,7 @@ int gram_block_tc(int ker, int kind, const C4<float>* Xr, int nr, const C4<float
 int gram_tc_pack_b(int kind, const float* B, int ldb, int rows, int cols, void* Bp, int ldp, cudaStream_t st);
 size_t gram_tc_packed_ld(int rows);
 int gram_tc_max_width();
+// Staging bytes (packed operand, mean column, padded coordinates) for a rows x width block.
+size_t gram_tc_staging_bytes(int rows, int width);
 
 }  // namespace cakf

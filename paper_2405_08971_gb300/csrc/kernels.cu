@@ -69,34 +69,56 @@ k_gram_matvec(const C4<T>* __restrict__ Xo, const T* __restrict__ s, int m, int 
   if (row < m) part[(size_t)blockIdx.y * m + row] = acc;
 }
 
-// g = sum_p part[p] + sn2 * s - a2 * Mo t     (Mo: m x r col-major, ld = ldm)
+// g = sum_p part[p] + sn2 * s - a2 * Mo t     (Mo: m x r col-major, ld = ldm); t is summed from the
+// row-chunk partials of k_gemv_t (tz chunks) into shared memory first.
 template <class T>
-__global__ void k_cg_combine(const T* __restrict__ part, int nsplit, const T* __restrict__ s, T sn2,
-                             const T* __restrict__ Mo, int ldm, int r, const T* __restrict__ t, T a2,
-                             int m, T* __restrict__ g, const int* __restrict__ active) {
+__global__ void __launch_bounds__(128)
+k_cg_combine(const T* __restrict__ part, int nsplit, const T* __restrict__ s, T sn2,
+             const T* __restrict__ Mo, int ldm, int r, const T* __restrict__ tpart, int tz, T a2,
+             int m, T* __restrict__ g, const int* __restrict__ active) {
   if (!*active) return;
+  extern __shared__ unsigned char sm_raw[];
+  T* t = reinterpret_cast<T*>(sm_raw);
+  for (int l = threadIdx.x; l < r; l += blockDim.x) {
+    T acc = T(0);
+    for (int z = 0; z < tz; ++z) acc += tpart[(size_t)z * r + l];
+    t[l] = acc;
+  }
+  __syncthreads();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m) return;
   T acc = T(0);
   for (int p = 0; p < nsplit; ++p) acc += part[(size_t)p * m + i];
   acc = fma(sn2, s[i], acc);
-  T lr = T(0);
-  for (int l = 0; l < r; ++l) lr = fma(Mo[(size_t)l * ldm + i], t[l], lr);
-  g[i] = fma(-a2, lr, acc);
+  T lr0 = T(0), lr1 = T(0), lr2 = T(0), lr3 = T(0);
+  int l = 0;
+  for (; l + 3 < r; l += 4) {
+    lr0 = fma(Mo[(size_t)l * ldm + i], t[l], lr0);
+    lr1 = fma(Mo[(size_t)(l + 1) * ldm + i], t[l + 1], lr1);
+    lr2 = fma(Mo[(size_t)(l + 2) * ldm + i], t[l + 2], lr2);
+    lr3 = fma(Mo[(size_t)(l + 3) * ldm + i], t[l + 3], lr3);
+  }
+  for (; l < r; ++l) lr0 = fma(Mo[(size_t)l * ldm + i], t[l], lr0);
+  g[i] = fma(-a2, (lr0 + lr1) + (lr2 + lr3), acc);
 }
 
-// t[l] = sum_i A[i, l] x[i]  (A: rows x cols col-major), one warp per column, double accumulation
+// Partial transposed products: part[z][l] = sum_{i in row chunk z} A[i, l] x[i]  (A: rows x cols col-major).
+// One warp per (column, row chunk); the chunks are summed by the consumer (k_cg_combine).
+constexpr int GV_CHUNK = 1024;
 template <class T>
 __global__ void k_gemv_t(const T* __restrict__ A, int lda, int rows, int cols, const T* __restrict__ x,
-                         T* __restrict__ t, const int* __restrict__ active) {
+                         T* __restrict__ part, const int* __restrict__ active) {
   if (active && !*active) return;
-  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= cols) return;
+  const int z = blockIdx.y;
+  const int i0 = z * GV_CHUNK, i1 = min(rows, i0 + GV_CHUNK);
   const T* a = A + (size_t)warp * lda;
-  double acc = 0.0;
-  for (int i = lane; i < rows; i += 32) acc += double(a[i]) * double(x[i]);
+  T acc = T(0);
+#pragma unroll 8
+  for (int i = i0 + lane; i < i1; i += 32) acc = fma(a[i], x[i], acc);
   acc = warp_sum(acc);
-  if (lane == 0) t[warp] = T(acc);
+  if (lane == 0) part[(size_t)z * cols + warp] = acc;
 }
 
 // First dot pass of CG iteration j (one block per dot):
@@ -237,7 +259,7 @@ __global__ void k_cg_init(const double* __restrict__ y, const double* __restrict
 // Plain SIMT Gram x block:  Out[i, c] = sum_j k(xr_i, xc_j) B[j, c]   (Out, B column-major)
 constexpr int GB_BM = 64, GB_BN = 64, GB_BK = 32, GB_THREADS = 256;
 
-template <int KER, class T>
+template <int KER, class T, bool DER = false>
 __global__ void __launch_bounds__(GB_THREADS)
 k_gram_block_simt(const C4<T>* __restrict__ Xr, int nr, const C4<T>* __restrict__ Xc, int nc,
                   const T* __restrict__ B, int ldb, int width, T sf2, T* __restrict__ Out, int ldo) {
@@ -262,7 +284,8 @@ k_gram_block_simt(const C4<T>* __restrict__ Xr, int nr, const C4<T>* __restrict_
       int rr = e % GB_BM, kk = e / GB_BM;
       int col = k0 + kk;
       T kvv = T(0);
-      if (col < nc && r0 + rr < nr) kvv = kval<KER>(dist2(xr[rr], Xc[col]), sf2);
+      if (col < nc && r0 + rr < nr)
+        kvv = DER ? kval_dlogl<KER>(dist2(xr[rr], Xc[col]), sf2) : kval<KER>(dist2(xr[rr], Xc[col]), sf2);
       Ks[kk][rr] = kvv;
     }
     for (int e = threadIdx.x; e < GB_BK * GB_BN; e += GB_THREADS) {
@@ -569,6 +592,160 @@ __global__ void k_nll_step(const double* __restrict__ eta, const double* __restr
   }
 }
 
+// Per-step small FP64 algebra of the NLL tangent pass (one block).  With Gh = S^T G S = R^T R
+// (R upper), beta = Gh^-1 yh and, per parameter p, W_p = R^-T dGh_p R^-1:
+//   grad[p] += 1/2 tr(W_p) + beta^T dyh_p - 1/2 beta^T dGh_p beta
+//   Q_p      = upper triangle of W_p with halved diagonal   (dR R^-1 of the Cholesky factor)
+//   u_p      = R^-T (dyh_p - dGh_p beta)                    (R dbeta_p)
+// Work arrays (global, ld = ic): L (ic x ic), Rinv (ic x ic), W (ic x ic), tmp (3 ic).
+__global__ void k_grad_small(int ic, int np, const double* __restrict__ Gh, const double* __restrict__ dGh,
+                             const double* __restrict__ yh, const double* __restrict__ dyh, double* __restrict__ L,
+                             double* __restrict__ Rinv, double* __restrict__ W, double* __restrict__ tmp,
+                             double* __restrict__ Q, double* __restrict__ u, double* __restrict__ grad,
+                             int* __restrict__ err) {
+  __shared__ double piv;
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  for (int e = threadIdx.x; e < ic * ic; e += blockDim.x) L[e] = Gh[e];
+  __syncthreads();
+  // Cholesky Gh = L L^T (lower, in place, column-major)
+  for (int p = 0; p < ic; ++p) {
+    if (threadIdx.x == 0) {
+      double d = L[(size_t)p * ic + p];
+      if (!(d > 0.0) || !isfinite(d)) { bad = 1; d = 1.0; }
+      piv = sqrt(d);
+      L[(size_t)p * ic + p] = piv;
+    }
+    __syncthreads();
+    for (int q = p + 1 + threadIdx.x; q < ic; q += blockDim.x) L[(size_t)p * ic + q] /= piv;
+    __syncthreads();
+    const int w = ic - p - 1;
+    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+      int q = p + 1 + e % w, c = p + 1 + e / w;
+      if (q >= c) L[(size_t)c * ic + q] -= L[(size_t)p * ic + q] * L[(size_t)p * ic + c];
+    }
+    __syncthreads();
+  }
+  // Rinv = (L^T)^-1 = upper triangular; column j solves L^T x = e_j by back substitution
+  for (int j = threadIdx.x; j < ic; j += blockDim.x) {
+    for (int i = ic - 1; i >= 0; --i) {
+      double acc = (i == j) ? 1.0 : 0.0;
+      for (int l = i + 1; l <= j; ++l) acc -= L[(size_t)i * ic + l] * Rinv[(size_t)j * ic + l];   // R_il = L_li
+      Rinv[(size_t)j * ic + i] = (i > j) ? 0.0 : acc / L[(size_t)i * ic + i];
+    }
+  }
+  __syncthreads();
+  // beta = Rinv Rinv^T yh
+  double* t1 = tmp;
+  double* beta = tmp + ic;
+  for (int i = threadIdx.x; i < ic; i += blockDim.x) {
+    double acc = 0.0;
+    for (int l = 0; l < ic; ++l) acc += Rinv[(size_t)i * ic + l] * yh[l];   // (Rinv^T yh)_i = sum_l Rinv[l, i] yh_l
+    t1[i] = acc;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < ic; i += blockDim.x) {
+    double acc = 0.0;
+    for (int l = 0; l < ic; ++l) acc += Rinv[(size_t)l * ic + i] * t1[l];
+    beta[i] = acc;
+  }
+  __syncthreads();
+  double* t2 = tmp + 2 * ic;
+  for (int p = 0; p < np; ++p) {
+    const double* D = dGh + (size_t)p * ic * ic;
+    // W = Rinv^T D Rinv : first Y = D Rinv (into Q_p as scratch), then W = Rinv^T Y
+    double* Y = Q + (size_t)p * ic * ic;
+    for (int e = threadIdx.x; e < ic * ic; e += blockDim.x) {
+      int i = e % ic, j = e / ic;
+      double acc = 0.0;
+      for (int l = 0; l <= j; ++l) acc += D[(size_t)l * ic + i] * Rinv[(size_t)j * ic + l];
+      Y[e] = acc;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < ic * ic; e += blockDim.x) {
+      int i = e % ic, j = e / ic;
+      double acc = 0.0;
+      for (int l = 0; l <= i; ++l) acc += Rinv[(size_t)i * ic + l] * Y[(size_t)j * ic + l];
+      W[e] = acc;
+    }
+    __syncthreads();
+    // scalars
+    double tr = 0.0, bdy = 0.0, bdb = 0.0;
+    for (int i = threadIdx.x; i < ic; i += blockDim.x) {
+      tr += W[(size_t)i * ic + i];
+      bdy += beta[i] * dyh[(size_t)p * ic + i];
+      double db = 0.0;
+      for (int l = 0; l < ic; ++l) db += D[(size_t)l * ic + i] * beta[l];
+      bdb += beta[i] * db;
+      t2[i] = dyh[(size_t)p * ic + i] - db;
+    }
+    tr = block_sum(tr);
+    bdy = block_sum(bdy);
+    bdb = block_sum(bdb);
+    if (threadIdx.x == 0) grad[p] += 0.5 * tr + bdy - 0.5 * bdb;
+    // u_p = Rinv^T t2 ; Q_p = Phi(W)
+    for (int i = threadIdx.x; i < ic; i += blockDim.x) {
+      double acc = 0.0;
+      for (int l = 0; l <= i; ++l) acc += Rinv[(size_t)i * ic + l] * t2[l];
+      u[(size_t)p * ic + i] = acc;
+    }
+    for (int e = threadIdx.x; e < ic * ic; e += blockDim.x) {
+      int i = e % ic, j = e / ic;
+      Q[(size_t)p * ic * ic + e] = (i < j) ? W[e] : ((i == j) ? 0.5 * W[e] : 0.0);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && bad) atomicExch(err, kErrNumeric);
+}
+
+// out[i, p] = in[idx[i] + p * ld]   (gather rows of a double block into precision T)
+template <class T>
+__global__ void k_gather_rows_f64(const double* __restrict__ In, int ld, const int* __restrict__ idx, int m, int cols,
+                                  T* __restrict__ Out, int ldo) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int c = blockIdx.y;
+  if (i < m && c < cols) Out[(size_t)c * ldo + i] = T(In[(size_t)c * ld + idx[i]]);
+}
+
+// dm_new[:, p] = dmpred[:, p] + E[:, p][col] + t[:, p]    (tangent of the filter mean)
+template <class T>
+__global__ void k_tangent_mean(const double* __restrict__ dmpred, const T* __restrict__ E, size_t estride, int ecol,
+                               int lde, const T* __restrict__ t, int ldt, int n, int np, double* __restrict__ dm) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int p = blockIdx.y;
+  if (i >= n || p >= np) return;
+  double v = dmpred[(size_t)p * n + i];
+  if (E) v += double(E[p * estride + (size_t)ecol * lde + i]);
+  if (t) v += double(t[(size_t)p * ldt + i]);
+  dm[(size_t)p * n + i] = v;
+}
+
+// dmpred[:, p] = adot_p * m_prev + a * dm_prev[:, p] - adot_p * mu_{k-1}
+__global__ void k_tangent_predict(const double* __restrict__ mprev, const double* __restrict__ dmprev,
+                                  const double* __restrict__ mu_km1, double a, double adot_lt, int n, int np,
+                                  double* __restrict__ dmpred) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int p = blockIdx.y;
+  if (i >= n || p >= np) return;
+  const double ad = (p == 1) ? adot_lt : 0.0;
+  double v = a * dmprev[(size_t)p * n + i] + ad * mprev[i];
+  if (mu_km1) v -= ad * mu_km1[i];
+  dmpred[(size_t)p * n + i] = v;
+}
+
+template <class T>
+__global__ void k_axpy_block(T alpha, const T* __restrict__ X, int ldx, int rows, int cols, T* __restrict__ Y, int ldy) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int c = blockIdx.y;
+  if (i < rows && c < cols) Y[(size_t)c * ldy + i] += alpha * X[(size_t)c * ldx + i];
+}
+template <class T>
+__global__ void k_scale_cols(T* A, int ld, int rows, int cols, T s) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int c = blockIdx.y;
+  if (i < rows && c < cols) A[(size_t)c * ld + i] *= s;
+}
+
 __global__ void k_set_diag(double* __restrict__ G, int ld, const double* __restrict__ lam, double scale, int r) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < r) G[(size_t)i * ld + i] = scale * lam[i];
@@ -644,15 +821,33 @@ void gram_block_simt(int ker, const C4<T>* Xr, int nr, const C4<T>* Xc, int nc, 
   }
 }
 
+// Out = dK/dlog(l_x) (Xr, Xc) B  (the derivative Gram matrix, never stored)
+template <class T>
+void gram_block_dlogl_simt(int ker, const C4<T>* Xr, int nr, const C4<T>* Xc, int nc, const T* B, int ldb, int width,
+                           T sf2, T* Out, int ldo, cudaStream_t st) {
+  if (nr <= 0 || width <= 0) return;
+  dim3 grid(cdiv(nr, GB_BM), cdiv(width, GB_BN));
+  switch (ker) {
+    case 0: k_gram_block_simt<0, T, true><<<grid, GB_THREADS, 0, st>>>(Xr, nr, Xc, nc, B, ldb, width, sf2, Out, ldo); note_launch(); break;
+    case 1: k_gram_block_simt<1, T, true><<<grid, GB_THREADS, 0, st>>>(Xr, nr, Xc, nc, B, ldb, width, sf2, Out, ldo); note_launch(); break;
+    default: k_gram_block_simt<2, T, true><<<grid, GB_THREADS, 0, st>>>(Xr, nr, Xc, nc, B, ldb, width, sf2, Out, ldo); note_launch(); break;
+  }
+}
+
 template <class T>
 void cg_combine(const T* part, int nsplit, const T* s, T sn2, const T* Mo, int ldm, int r, const T* t, T a2, int m,
                 T* g, const int* active, cudaStream_t st) {
-  k_cg_combine<T><<<cdiv(m, 256), 256, 0, st>>>(part, nsplit, s, sn2, Mo, ldm, r, t, a2, m, g, active); note_launch();
+  const int tz = std::max(1, (m + GV_CHUNK - 1) / GV_CHUNK);
+  k_cg_combine<T><<<cdiv(m, 128), 128, std::max(r, 1) * sizeof(T), st>>>(part, nsplit, s, sn2, Mo, ldm, r, t, tz, a2,
+                                                                          m, g, active);
+  note_launch();
 }
+// t must hold ceil(rows / 1024) * cols partials (summed by cg_combine)
 template <class T>
 void gemv_t(const T* A, int lda, int rows, int cols, const T* x, T* t, const int* active, cudaStream_t st) {
   if (cols <= 0) return;
-  k_gemv_t<T><<<cdiv((size_t)cols * 32, 256), 256, 0, st>>>(A, lda, rows, cols, x, t, active); note_launch();
+  const int tz = std::max(1, (rows + GV_CHUNK - 1) / GV_CHUNK);
+  k_gemv_t<T><<<dim3(cdiv((size_t)cols * 32, 256), tz), 256, 0, st>>>(A, lda, rows, cols, x, t, active); note_launch();
 }
 template <class T>
 void cg_dots1(const T* V, int ldv, int j, const T* s, const T* g, const T* r0, const T* v, int m, double* dots,
@@ -765,6 +960,47 @@ void nll_step(const double* eta, const double* alpha, const int* count, double* 
               cudaStream_t st) {
   k_nll_step<<<1, 256, 0, st>>>(eta, alpha, count, SS, ic, nll_k, err); note_launch();
 }
+void grad_small(int ic, int np, const double* Gh, const double* dGh, const double* yh, const double* dyh, double* L,
+                double* Rinv, double* W, double* tmp, double* Q, double* u, double* grad, int* err, cudaStream_t st) {
+  k_grad_small<<<1, 256, 0, st>>>(ic, np, Gh, dGh, yh, dyh, L, Rinv, W, tmp, Q, u, grad, err); note_launch();
+}
+template <class T>
+void gather_rows_f64(const double* In, int ld, const int* idx, int m, int cols, T* Out, int ldo, cudaStream_t st) {
+  if (m <= 0 || cols <= 0) return;
+  k_gather_rows_f64<T><<<dim3(cdiv(m, 256), cols), 256, 0, st>>>(In, ld, idx, m, cols, Out, ldo); note_launch();
+}
+template <class T>
+void tangent_mean(const double* dmpred, const T* E, size_t estride, int ecol, int lde, const T* t, int ldt, int n,
+                  int np, double* dm, cudaStream_t st) {
+  k_tangent_mean<T><<<dim3(cdiv(n, 256), np), 256, 0, st>>>(dmpred, E, estride, ecol, lde, t, ldt, n, np, dm);
+  note_launch();
+}
+void tangent_predict(const double* mprev, const double* dmprev, const double* mu_km1, double a, double adot_lt, int n,
+                     int np, double* dmpred, cudaStream_t st) {
+  k_tangent_predict<<<dim3(cdiv(n, 256), np), 256, 0, st>>>(mprev, dmprev, mu_km1, a, adot_lt, n, np, dmpred);
+  note_launch();
+}
+template <class T>
+void axpy_block(T alpha, const T* X, int ldx, int rows, int cols, T* Y, int ldy, cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return;
+  k_axpy_block<T><<<dim3(cdiv(rows, 256), cols), 256, 0, st>>>(alpha, X, ldx, rows, cols, Y, ldy); note_launch();
+}
+template <class T>
+void scale_cols(T* A, int ld, int rows, int cols, T s, cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return;
+  k_scale_cols<T><<<dim3(cdiv(rows, 256), cols), 256, 0, st>>>(A, ld, rows, cols, s); note_launch();
+}
+template void axpy_block<float>(float, const float*, int, int, int, float*, int, cudaStream_t);
+template void axpy_block<double>(double, const double*, int, int, int, double*, int, cudaStream_t);
+template void scale_cols<float>(float*, int, int, int, float, cudaStream_t);
+template void scale_cols<double>(double*, int, int, int, double, cudaStream_t);
+template void gather_rows_f64<float>(const double*, int, const int*, int, int, float*, int, cudaStream_t);
+template void gather_rows_f64<double>(const double*, int, const int*, int, int, double*, int, cudaStream_t);
+template void tangent_mean<float>(const double*, const float*, size_t, int, int, const float*, int, int, int, double*,
+                                  cudaStream_t);
+template void tangent_mean<double>(const double*, const double*, size_t, int, int, const double*, int, int, int,
+                                   double*, cudaStream_t);
+
 void set_diag(double* G, int ld, const double* lam, double scale, int r, cudaStream_t st) {
   if (r <= 0) return;
   k_set_diag<<<cdiv(r, 256), 256, 0, st>>>(G, ld, lam, scale, r); note_launch();
@@ -797,6 +1033,8 @@ void check_finite(const double* x, size_t n, int* err, cudaStream_t st) {
   template void gram_matvec<T>(int, const C4<T>*, const T*, int, T, T*, int, cudaStream_t);                      \
   template void gram_block_simt<T>(int, const C4<T>*, int, const C4<T>*, int, const T*, int, int, T, T*, int,    \
                                    cudaStream_t);                                                                \
+  template void gram_block_dlogl_simt<T>(int, const C4<T>*, int, const C4<T>*, int, const T*, int, int, T, T*,   \
+                                         int, cudaStream_t);                                                     \
   template void cg_combine<T>(const T*, int, const T*, T, const T*, int, int, const T*, T, int, T*, const int*,   \
                               cudaStream_t);                                                                     \
   template void gemv_t<T>(const T*, int, int, int, const T*, T*, const int*, cudaStream_t);                      \

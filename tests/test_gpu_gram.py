@@ -1,0 +1,76 @@
+"""The Gram x matrix primitive (cakf_gram_matmul) against the oracle's dense definition.
+
+Out = K(Xr, Xc) B with the Gram matrix never stored.  Sizes are ragged (rows not a multiple of the
+128-row tile, columns not a multiple of the 64-column slice) and widths cover one MMA chunk, two
+chunks and the 512-column TMEM limit.  Tolerances:
+  FP64 SIMT   1e-12 relative (per column, normwise)
+  FP32 SIMT   2e-5 relative
+  BF16 tcgen05 columns 0..w-2: within 2e-4 of the exact product of the BF16-rounded operands
+               (kernel values and B rounded to bf16, FP64 accumulation), i.e. the kernel adds only
+               FP32 accumulation-order rounding to the BF16 operand rounding; and within 3e-2 of
+               the exact product (the bf16 rounding itself, ~2^-9 per operand);
+               the last column is accumulated in FP32 on the CUDA cores: 2e-5 relative.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2405_08971_gb300 as ck  # noqa: E402
+
+
+def colwise_rel(got, ref):
+    num = np.linalg.norm(got - ref, axis=1)
+    den = np.maximum(np.linalg.norm(ref, axis=1), 1e-300)
+    return num / den
+
+
+def case(nr, nc, width, dim, kernel, seed, lx=0.3, sf2=1.7):
+    rng = np.random.default_rng(seed)
+    Xr = rng.uniform(size=(nr, dim))
+    Xc = rng.uniform(size=(nc, dim))
+    B = rng.standard_normal((width, nc))          # stored as (width, nc): column-major nc x width
+    K = oracle.kernel_matrix(Xr, Xc, kernel, lx, sf2)
+    ref = (K @ B.T).T
+    bf = lambda a: torch.tensor(a, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    ref_bf16 = (bf(K) @ bf(B).T).T
+    return Xr, Xc, B, ref, ref_bf16, math.log(lx), math.log(sf2)
+
+
+@pytest.mark.parametrize("nr,nc,width,dim,kernel", [
+    (1000, 777, 2, 2, 1), (300, 257, 17, 3, 2), (513, 1000, 65, 1, 0), (257, 640, 257, 3, 1),
+    (384, 300, 513, 2, 1), (130, 70, 100, 3, 2),
+])
+def test_gram_matmul_all_precisions(nr, nc, width, dim, kernel):
+    Xr, Xc, B, ref, ref_bf16, llx, lsf2 = case(nr, nc, width, dim, kernel, seed=nr + width)
+    d = torch.device("cuda:0")
+    tXr, tXc = torch.as_tensor(Xr, device=d), torch.as_tensor(Xc, device=d)
+    out64 = ck.cakf_gram_matmul(kernel, llx, lsf2, tXr, tXc, torch.as_tensor(B, device=d), precision="fp64")
+    e64 = colwise_rel(out64.cpu().numpy(), ref)
+    assert e64.max() < 1e-12, e64.max()
+    out32 = ck.cakf_gram_matmul(kernel, llx, lsf2, tXr, tXc, torch.as_tensor(B, device=d), precision="fp32")
+    e32 = colwise_rel(out32.cpu().double().numpy(), ref)
+    assert e32.max() < 2e-5, e32.max()
+    outbf = ck.cakf_gram_matmul(kernel, llx, lsf2, tXr, tXc, torch.as_tensor(B, device=d), precision="bf16")
+    got = outbf.cpu().double().numpy()
+    ebf = colwise_rel(got, ref)
+    emu = colwise_rel(got[:-1], ref_bf16[:-1])
+    print(f"nr={nr} nc={nc} w={width}: fp64 {e64.max():.1e} fp32 {e32.max():.1e} "
+          f"bf16 tc {ebf[:-1].max():.1e} (vs bf16-rounded operands {emu.max():.1e}) last-col {ebf[-1]:.1e}")
+    assert emu.max() < 2e-4, emu.max()
+    assert ebf[:-1].max() < 3e-2, ebf[:-1].max()
+    assert ebf[-1] < 2e-5, ebf[-1]
+
+
+def test_gram_matmul_rejects_host_pointers():
+    Xr = torch.zeros((4, 2), dtype=torch.float64)
+    with pytest.raises(ck.CakfError) as ei:
+        ck.cakf_gram_matmul(1, 0.0, 0.0, Xr, Xr, torch.zeros((3, 4), dtype=torch.float32), precision="fp32")
+    assert ei.value.code == ck.binding.ERR_ARG
