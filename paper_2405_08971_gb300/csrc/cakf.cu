@@ -79,7 +79,7 @@ struct cakf_ctx {
   // workspace
   double *mpred = nullptr, *rs_plus = nullptr, *rs_pw = nullptr, *lam = nullptr, *lam2 = nullptr;
   void *Xo = nullptr, *Mo = nullptr, *rv = nullptr, *r0v = nullptr, *sv = nullptr, *gv = nullptr, *GV = nullptr,
-       *part = nullptr, *tv = nullptr;
+       *part = nullptr, *tv = nullptr, *GS = nullptr, *Qa = nullptr;
   double* dots = nullptr;
   double* dots2 = nullptr;
   double* part64 = nullptr;
@@ -264,6 +264,8 @@ int plan_and_alloc(cakf_ctx* c, const cakf_problem* p) {
   if ((rc = c->alloc(c->sv, mm * es))) return rc;
   if ((rc = c->alloc(c->gv, mm * es))) return rc;
   if ((rc = c->alloc(c->GV, mm * std::max(B, 1) * es))) return rc;
+  if ((rc = c->alloc(c->GS, mm * std::max(B, 1) * es))) return rc;
+  if ((rc = c->alloc(c->Qa, mm * std::max(B, 1) * es))) return rc;
   if ((rc = c->alloc(c->part, mm * 32 * es))) return rc;
   if ((rc = c->alloc(c->tv, std::max<size_t>(c->rmax, 1) * ((mm + 1023) / 1024 + 1) * es))) return rc;
   if ((rc = c->alloc(c->dots, (B + 8) * sizeof(double)))) return rc;
@@ -404,14 +406,15 @@ struct Runner {
       T* vcol = V + (size_t)ic * m;
       T* r = (T*)c->rv;
       T* s = (T*)c->sv;
-      T* g = (T*)c->gv;
       T* GV = (T*)c->GV;
+      T* GSk = (T*)c->GS;      // G s_j of every iteration (column j), for the NLL
       gather_coords<T>(X(), ob, m, Xo, st);
       gather_rows<T>(Mk(k - 1), ldn, ob, m, rp, Mo, m, st);
       cudaMemsetAsync(c->r0sq, 0, sizeof(double), st);
       cg_init<T>(c->y + c->obs_ptr[k - 1], c->mpred, ob, m, r, (T*)c->r0v, vcol, c->r0sq, st);
       cudaMemsetAsync(V, 0, (size_t)m * ic * sizeof(T), st);
       cudaMemsetAsync(GV, 0, (size_t)m * std::max(ic, 1) * sizeof(T), st);
+      cudaMemsetAsync(GSk, 0, (size_t)m * std::max(ic, 1) * sizeof(T), st);
       {
         int one = 1;
         cudaMemcpyAsync(c->active, &one, sizeof(int), cudaMemcpyHostToDevice, st);
@@ -428,8 +431,11 @@ struct Runner {
       }
       const int nsplit = std::max(1, std::min(32, (m + 511) / 512));
       const double* rep = c->replay ? c->rep + c->off_rep[k] : nullptr;
+      T* Qa = (T*)c->Qa;       // orthonormal basis of the previous actions (CG policy only)
       for (int j = 0; j < ic; ++j) {
+        T* g = GSk + (size_t)j * m;
         cg_select<T>(j, r, rep, m, s, Sk(k), m, c->active, st);
+        if (!rep) cg_reorth<T>(Qa, m, j, s, m, c->dots2, Sk(k), m, c->active, st);
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         bool prof = c->profiling && (j % 8 == 0);
         if (prof) { e0 = c->ev(); e1 = c->ev(); cudaEventRecord(e0, st); }
@@ -444,8 +450,8 @@ struct Runner {
         cg_dots1<T>(V, m, j, s, g, (const T*)c->r0v, vcol, m, c->dots, c->active, st);
         cg_upd1<T>(j, c->dots, V, GV, m, s, g, m, c->active, st);
         cg_dots2<T>(V, GV, m, j, m, c->dots2, c->active, st);
-        cg_upd2<T>(j, c->dots, c->dots2, V, GV, m, r, vcol, m, bd_tol, rtol2, use_rtol, c->active,
-                   c->eta + (size_t)k * B, c->alpha + (size_t)k * B, c->count + k, st);
+        cg_upd2<T>(j, c->dots, c->dots2, V, GV, m, r, vcol, s, rep ? nullptr : Qa, m, bd_tol, rtol2, use_rtol,
+                   c->active, c->eta + (size_t)k * B, c->alpha + (size_t)k * B, c->count + k, st);
       }
       // finalize: [P^- W, P^- w] = K(X, X_o) [V v] - a^2 M+ (M+_o^T [V v])
       T* PVk = PV(k);
@@ -456,11 +462,16 @@ struct Runner {
         gemm_nn<T, double>(n, ic + 1, rp, T(-a2), Mk(k - 1), ldn, t2, rp, T(1), PVk, ldn, st);
       }
       filter_out<T>(c->mpred, PVk, ldn, ic, c->sf2, a2, c->rs_plus, n, mout, vout, c->rs_pw, st);
-      // NLL term: Cholesky of S^T S (FP64) and the recorded eta / alpha
+      // NLL term from its definition: S^T G S (with the stored G s_j), S^T S and S^T r0, FP64 Cholesky
       {
         double* SS = c->small;
+        double* Gh = SS + (size_t)ic * ic;
+        double* yh = Gh + (size_t)ic * ic;
+        double* zs = yh + ic;
         gemm_tn<T>(Sk(k), m, ic, Sk(k), m, ic, m, 1.0, 0.0, SS, ic, c->part64, c->part64_elems, st);
-        nll_step(c->eta + (size_t)k * B, c->alpha + (size_t)k * B, c->count + k, SS, ic, c->nll + k, c->err, st);
+        gemm_tn<T>(Sk(k), m, ic, GSk, m, ic, m, 1.0, 0.0, Gh, ic, c->part64, c->part64_elems, st);
+        gemm_tn<T>(Sk(k), m, ic, (const T*)c->r0v, m, 1, m, 1.0, 0.0, yh, ic, c->part64, c->part64_elems, st);
+        nll_def(c->count + k, Gh, SS, ic, yh, zs, c->nll + k, c->err, st);
       }
       // Truncate (Sec. 3.2)
       int rc = truncate_filter(k, rp, ic);
@@ -938,6 +949,8 @@ void collect_profile(cakf_ctx* c) {
 
 template <class T>
 Runner<T> make_runner(cakf_ctx* c, cudaStream_t st) {
+  // plain FP32 factor products: cuBLAS FP32; mixed mode: cuBLAS FP32 emulated on BF16 tensor cores
+  set_gemm_mode(c->precision == CAKF_FP64 ? 0 : (c->precision == CAKF_FP32 ? 1 : 2));
   Runner<T> r;
   r.c = c;
   r.st = st;

@@ -20,47 +20,76 @@ namespace {
 constexpr double kEps = 2.220446049250313e-16;
 
 // ---------------------------------------------------------------------------------- tridiagonal
+// Householder tridiagonalisation (lower), one grid barrier per column.  Columns of the trailing
+// block are owned by (block, warp) round-robin.  At step k every block knows v_k, tau_k (computed
+// redundantly) and reads p_k = tau_k A22 v_k and the pre-update pivot column k+1 from double
+// buffers written before the barrier; it then forms w_k, the updated column k+1 and from it
+// v_{k+1}, tau_{k+1}; the owners update their columns and, in the same pass, compute the entries
+// of p_{k+1} and publish the next pivot column.  Reflector v_k is stored in column k below the
+// subdiagonal (v_k[0] = 1).
+__device__ __forceinline__ void householder(const double* x, int L, double* v, double& tau, double& beta) {
+  // x (smem, length L) -> v (smem) with v[0] = 1, H = I - tau v v^T, H x = beta e_1
+  double ss = 0.0;
+  for (int t = threadIdx.x; t < L; t += blockDim.x) if (t > 0) ss += x[t] * x[t];
+  const double sigma = block_sum(ss);
+  const double alpha = x[0];
+  double scal;
+  if (sigma == 0.0) { tau = 0.0; beta = alpha; scal = 0.0; }
+  else {
+    beta = -copysign(sqrt(alpha * alpha + sigma), alpha);
+    tau = (beta - alpha) / beta;
+    scal = 1.0 / (alpha - beta);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < L; t += blockDim.x) v[t] = (t == 0) ? 1.0 : x[t] * scal;
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(256)
 k_tridiag(double* __restrict__ A, int lda, int N, double* __restrict__ d, double* __restrict__ e,
-          double* __restrict__ tau, double* __restrict__ P, unsigned* bar, int* err) {
+          double* __restrict__ tau, double* __restrict__ Pbuf, double* __restrict__ Cbuf, unsigned* bar, int* err) {
   extern __shared__ double sm[];
-  double* v = sm;
-  double* w = sm + N;
+  double* v = sm;            // v_k
+  double* v2 = sm + N;       // v_{k+1}
+  double* w = sm + 2 * N;    // w_k
+  double* c = sm + 3 * N;    // updated pivot column
   const int G = gridDim.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (N <= 2) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      d[0] = A[0];
+      if (N == 2) { e[0] = A[1]; d[1] = A[(size_t)lda + 1]; tau[0] = 0.0; }
+    }
+    return;
+  }
+  // ---- prologue: v_0 from column 0; p_0; publish column 1
+  double tk, bk;
+  {
+    const int L = N - 1;
+    for (int t = threadIdx.x; t < L; t += blockDim.x) c[t] = A[1 + t];
+    __syncthreads();
+    householder(c, L, v, tk, bk);
+    for (int j = 1 + blockIdx.x + G * warp; j < N; j += G * nw) {
+      const double* col = A + (size_t)j * lda + 1;
+      double acc = 0.0;
+      for (int t = lane; t < L; t += 32) acc += col[t] * v[t];
+      acc = warp_sum(acc);
+      if (lane == 0) Pbuf[j - 1] = tk * acc;
+      if (j == 1) for (int t = lane; t < L; t += 32) Cbuf[t] = col[t];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) d[0] = A[0];
+    if (!grid_barrier(bar, G, err)) return;
+  }
   for (int k = 0; k + 2 < N; ++k) {
     const int L = N - k - 1;
-    const double* x = A + (size_t)k * lda + k + 1;
-    double ss = 0.0;
-    for (int t = threadIdx.x; t < L; t += blockDim.x) {
-      double xv = __ldcg(x + t);
-      v[t] = xv;
-      if (t > 0) ss += xv * xv;
-    }
-    const double sigma = block_sum(ss);
-    const double alpha = v[0];
-    double beta, tk, scal;
-    if (sigma == 0.0) { tk = 0.0; beta = alpha; scal = 0.0; }
-    else {
-      beta = -copysign(sqrt(alpha * alpha + sigma), alpha);
-      tk = (beta - alpha) / beta;
-      scal = 1.0 / (alpha - beta);
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < L; t += blockDim.x) v[t] = (t == 0) ? 1.0 : v[t] * scal;
-    __syncthreads();
-    // p = tau * A22 v, one warp per owned column (columns are dealt to blocks round-robin)
-    for (int jp = blockIdx.x + G * warp; jp < L; jp += G * nw) {
-      const double* col = A + (size_t)(k + 1 + jp) * lda + k + 1;
-      double acc = 0.0;
-      for (int t = lane; t < L; t += 32) acc += __ldcg(col + t) * v[t];
-      acc = warp_sum(acc);
-      if (lane == 0) P[jp] = tk * acc;
-    }
-    if (!grid_barrier(bar, G, err)) return;
+    const double* Pk = Pbuf + (size_t)(k & 1) * N;
+    double* Pn = Pbuf + (size_t)((k + 1) & 1) * N;
+    const double* Ck = Cbuf + (size_t)(k & 1) * N;
+    double* Cn = Cbuf + (size_t)((k + 1) & 1) * N;
+    // (1) w_k = p_k - 1/2 tau_k (p_k . v_k) v_k
     double pv = 0.0;
     for (int t = threadIdx.x; t < L; t += blockDim.x) {
-      double pt = __ldcg(P + t);
+      const double pt = __ldcg(Pk + t);
       w[t] = pt;
       pv += pt * v[t];
     }
@@ -68,28 +97,46 @@ k_tridiag(double* __restrict__ A, int lda, int N, double* __restrict__ d, double
     const double kc = 0.5 * tk * pv;
     for (int t = threadIdx.x; t < L; t += blockDim.x) w[t] -= kc * v[t];
     __syncthreads();
-    // A22 -= v w^T + w v^T on the owned columns
-    for (int jp = blockIdx.x + G * warp; jp < L; jp += G * nw) {
-      double* col = A + (size_t)(k + 1 + jp) * lda + k + 1;
-      const double vj = v[jp], wj = w[jp];
-      for (int t = lane; t < L; t += 32) col[t] = __ldcg(col + t) - (v[t] * wj + w[t] * vj);
+    // (2) updated pivot column k+1 (rows k+1..N-1) and the next reflector
+    for (int t = threadIdx.x; t < L; t += blockDim.x) c[t] = __ldcg(Ck + t) - v[t] * w[0] - w[t] * v[0];
+    __syncthreads();
+    const bool next = (k + 3 < N);      // a reflector for column k+1 exists
+    double tn = 0.0, bn = 0.0;
+    if (next) householder(c + 1, L - 1, v2, tn, bn);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      d[k + 1] = c[0];
+      e[k] = bk;
+      tau[k] = tk;
+      if (!next) { e[k + 1] = c[1]; tau[k + 1] = 0.0; }
     }
-    if (blockIdx.x == 0) {
+    // (3) owners: A22 -= v w^T + w v^T; fused dot for p_{k+1}; publish pivot column k+2
+    for (int j = k + 1 + ((blockIdx.x - (k + 1) % G + G) % G) + G * warp; j < N; j += G * nw) {
+      const int tj = j - (k + 1);
+      double* col = A + (size_t)j * lda + k + 1;
+      const double vj = v[tj], wj = w[tj];
+      const bool publish = next && tj == 1;       // column k+2 becomes the next pivot column
+      double acc = 0.0;
+      for (int t = lane; t < L; t += 32) {
+        const double nv = __ldcg(col + t) - (v[t] * wj + w[t] * vj);
+        col[t] = nv;
+        if (next && t >= 1) acc += nv * v2[t - 1];
+        if (publish && t >= 1) Cn[t - 1] = nv;
+      }
+      if (next && tj >= 1) {
+        acc = warp_sum(acc);
+        if (lane == 0) Pn[tj - 1] = tn * acc;
+      }
+    }
+    // (4) store the reflector v_k below the subdiagonal of column k
+    if (blockIdx.x == 0)
       for (int t = threadIdx.x; t < L; t += blockDim.x) A[(size_t)k * lda + k + 1 + t] = v[t];
-      if (threadIdx.x == 0) { d[k] = __ldcg(A + (size_t)k * lda + k); e[k] = beta; tau[k] = tk; }
-    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < L - 1; t += blockDim.x) v[t] = v2[t];
+    tk = tn;
+    bk = bn;
     if (!grid_barrier(bar, G, err)) return;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    if (N >= 2) {
-      d[N - 2] = __ldcg(A + (size_t)(N - 2) * lda + N - 2);
-      e[N - 2] = __ldcg(A + (size_t)(N - 2) * lda + N - 1);
-      d[N - 1] = __ldcg(A + (size_t)(N - 1) * lda + N - 1);
-      tau[N - 2] = 0.0;
-    } else if (N == 1) {
-      d[0] = __ldcg(A);
-    }
-  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) d[N - 1] = __ldcg(A + (size_t)(N - 1) * lda + N - 1);
 }
 
 // ------------------------------------------------------------------------------ divide & conquer
@@ -292,10 +339,12 @@ __global__ void k_dc_secular(const MergeDesc* __restrict__ merges, const int* __
   if (lane == 0) W.lamk[lo + i] = Dorg + tau;
 }
 
-// Phase 3: Loewner-corrected z:  zhat_j^2 = (lam_last - D_j)/rho * prod_{i<j} (lam_i - D_j)/(D_i - D_j)
-//                                           * prod_{i>j} (lam_{i-1} - D_j)/(D_i - D_j)
+// Phase 3: Loewner-corrected z (one warp per j):
+//   zhat_j^2 = (lam_last - D_j)/rho * prod_{i<j} (lam_i - D_j)/(D_i - D_j) * prod_{i>j} (lam_{i-1} - D_j)/(D_i - D_j)
+// The product is formed as a sum of logarithms of the (positive) factors split across lanes.
 __global__ void k_dc_zhat(const MergeDesc* __restrict__ merges, const int* __restrict__ mergeof, int N, DcWork W) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (p >= N) return;
   const int mi = mergeof[p];
   if (mi < 0) return;
@@ -305,16 +354,25 @@ __global__ void k_dc_zhat(const MergeDesc* __restrict__ merges, const int* __res
   if (j >= Kp) return;
   const double* Dk = W.Dk + lo;
   const double rho = W.rho[lo];
-  auto delta = [&](int i) { return W.Delta[(size_t)(lo + i) * N + lo + j]; };
-  double prod = -delta(Kp - 1) / rho;
-  for (int i = 0; i < j; ++i) prod *= (-delta(i)) / (Dk[i] - Dk[j]);
-  for (int i = j + 1; i < Kp; ++i) prod *= (-delta(i - 1)) / (Dk[i] - Dk[j]);
-  W.Zw[lo + j] = copysign(sqrt(fmax(prod, 0.0)), W.Zk[lo + j]);
+  const double Dj = Dk[j];
+  double lg = 0.0;
+  for (int i = lane; i < Kp; i += 32) {
+    if (i == j) continue;
+    const int ii = (i < j) ? i : i - 1;                       // lam_i for i < j, lam_{i-1} for i > j
+    const double num = -W.Delta[(size_t)(lo + ii) * N + lo + j];
+    lg += log(fabs(num / (Dk[i] - Dj)));
+  }
+  lg = warp_sum(lg);
+  if (lane == 0) {
+    const double last = -W.Delta[(size_t)(lo + Kp - 1) * N + lo + j] / rho;
+    W.Zw[lo + j] = copysign(sqrt(fabs(last)) * exp(0.5 * lg), W.Zk[lo + j]);
+  }
 }
 
-// Phase 4: eigenvector columns u_i = zhat / delta_i, normalised, written over Delta.
+// Phase 4: eigenvector columns u_i = zhat / delta_i, normalised, written over Delta (one warp per i).
 __global__ void k_dc_vecs(const MergeDesc* __restrict__ merges, const int* __restrict__ mergeof, int N, DcWork W) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (p >= N) return;
   const int mi = mergeof[p];
   if (mi < 0) return;
@@ -324,9 +382,10 @@ __global__ void k_dc_vecs(const MergeDesc* __restrict__ merges, const int* __res
   if (i >= Kp) return;
   double* col = W.Delta + (size_t)(lo + i) * N + lo;
   double nrm = 0.0;
-  for (int j = 0; j < Kp; ++j) { double u = W.Zw[lo + j] / col[j]; col[j] = u; nrm += u * u; }
+  for (int j = lane; j < Kp; j += 32) { double u = W.Zw[lo + j] / col[j]; col[j] = u; nrm += u * u; }
+  nrm = warp_sum(nrm);
   const double inv = 1.0 / sqrt(nrm);
-  for (int j = 0; j < Kp; ++j) col[j] *= inv;
+  for (int j = lane; j < Kp; j += 32) col[j] *= inv;
 }
 
 // Phase 5: Qtmp[lo:hi, lo+i] = Q[lo:hi, colk] U[:, i] (i < Kp); deflated columns copied after them.
@@ -513,7 +572,7 @@ size_t eig_workspace_bytes(int nmax) {
   size_t N = std::max(nmax, 1);
   size_t b = 0;
   b += align_up(3 * N * sizeof(double));          // d, e, tau
-  b += align_up(N * sizeof(double));              // P
+  b += 2 * align_up(2 * N * sizeof(double));      // P, C (double buffered)
   b += align_up(16);                              // barrier words
   b += 3 * align_up(N * N * sizeof(double));      // Q, Qtmp, Delta
   b += 10 * align_up(N * sizeof(double));         // lam, lamk, lamtmp, Dw, Zw, Dk, Zk, Dd, rho, spare
@@ -535,7 +594,8 @@ int eig_sym_topk(double* A, int lda, int N, int nkeep, double* w, T* U, int ldu,
   double* d = (double*)take(3 * N * sizeof(double));
   double* e = d + N;
   double* tau = e + N;
-  double* P = (double*)take(N * sizeof(double));
+  double* P = (double*)take(2 * N * sizeof(double));
+  double* Cb = (double*)take(2 * N * sizeof(double));
   unsigned* bar = (unsigned*)take(16);
   DcWork W;
   W.Q = (double*)take((size_t)N * N * sizeof(double));
@@ -564,19 +624,17 @@ int eig_sym_topk(double* A, int lda, int N, int nkeep, double* w, T* U, int ldu,
   cudaMemsetAsync(d, 0, 3 * N * sizeof(double), st);
 
   // 1. tridiagonalisation (cooperative: all blocks co-resident)
-  if (N >= 3) {
+  {
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    int G = std::max(1, std::min(nsm, (N + 7) / 8));
-    size_t smem = 2 * (size_t)N * sizeof(double);
-    void* args[] = {&A, &lda, &N, &d, &e, &tau, &P, &bar, &err};
+    int G = N >= 3 ? std::max(1, std::min(nsm, (N + 7) / 8)) : 1;
+    size_t smem = 4 * (size_t)N * sizeof(double);
+    void* args[] = {&A, &lda, &N, &d, &e, &tau, &P, &Cb, &bar, &err};
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaError_t ce = cudaLaunchCooperativeKernel((void*)k_tridiag, dim3(G), dim3(256), args, smem, st);
     note_launch();
     if (ce != cudaSuccess) return 3;
-  } else {
-    k_tridiag<<<1, 256, 2 * N * sizeof(double), st>>>(A, lda, N, d, e, tau, P, bar, err); note_launch();
   }
   // 2. divide and conquer
   k_dc_init<<<(N + 255) / 256, 256, 0, st>>>(d, e, N, W.lam, W.Q); note_launch();
@@ -592,8 +650,8 @@ int eig_sym_topk(double* A, int lda, int N, int nkeep, double* w, T* U, int ldu,
     for (int q = m0; q < m1; ++q) kmax = std::max(kmax, pl.merges[q].hi - pl.merges[q].lo);
     k_dc_prep<<<nm, 256, 0, st>>>(dm, e, N, W); note_launch();
     k_dc_secular<<<(N * 32 + 255) / 256, 256, 0, st>>>(dm, dmo, N, W, err); note_launch();
-    k_dc_zhat<<<(N + 127) / 128, 128, 0, st>>>(dm, dmo, N, W); note_launch();
-    k_dc_vecs<<<(N + 127) / 128, 128, 0, st>>>(dm, dmo, N, W); note_launch();
+    k_dc_zhat<<<(N * 32 + 255) / 256, 256, 0, st>>>(dm, dmo, N, W); note_launch();
+    k_dc_vecs<<<(N * 32 + 255) / 256, 256, 0, st>>>(dm, dmo, N, W); note_launch();
     dim3 gg((kmax + DG_T - 1) / DG_T, (kmax + DG_T - 1) / DG_T, nm);
     k_dc_gemm<<<gg, 256, 0, st>>>(dm, N, W); note_launch();
     k_dc_finish<<<nm, 256, 0, st>>>(dm, N, W); note_launch();

@@ -36,8 +36,11 @@ void cg_upd1(int j, const double* dots, T* V, T* GV, int ldv, const T* s, const 
 template <class T>
 void cg_dots2(const T* V, const T* GV, int ldv, int j, int m, double* dots, const int* active, cudaStream_t st);
 template <class T>
-void cg_upd2(int j, const double* dots1, const double* dots2, T* V, T* GV, int ldv, T* r, T* v, int m, double bd_tol,
-             double rtol2_r0sq, int use_rtol, int* active, double* eta, double* alpha, int* count, cudaStream_t st);
+void cg_upd2(int j, const double* dots1, const double* dots2, T* V, T* GV, int ldv, T* r, T* v, const T* s, T* Q,
+             int m, double bd_tol, double rtol2_r0sq, int use_rtol, int* active, double* eta, double* alpha,
+             int* count, cudaStream_t st);
+template <class T>
+void cg_reorth(const T* Q, int ldq, int j, T* s, int m, double* qd, T* S, int lds, const int* active, cudaStream_t st);
 template <class T>
 void cg_select(int j, const T* r, const double* rep, int m, T* s, T* S, int lds, const int* active, cudaStream_t st);
 template <class T>
@@ -69,6 +72,8 @@ template <class T> void build_x(const T* Ws, int ldw, int cw, const T* ws, T alp
 void nll_step(const double* eta, const double* alpha, const int* count, double* SS, int ic, double* nll_k, int* err,
               cudaStream_t st);
 void set_diag(double* G, int ld, const double* lam, double scale, int r, cudaStream_t st);
+void nll_def(const int* count, double* Gh, double* SS, int ld, const double* yh, double* z, double* nll_k, int* err,
+             cudaStream_t st);
 void grad_small(int ic, int np, const double* Gh, const double* dGh, const double* yh, const double* dyh, double* L,
                 double* Rinv, double* W, double* tmp, double* Q, double* u, double* grad, int* err, cudaStream_t st);
 template <class T>
@@ -90,6 +95,14 @@ void convert_from_f64(const double* In, int ldi, int rows, int cols, T* Out, int
 // Device error-flag values (the flag is an int in device memory, 0 = ok)
 constexpr int kErrNumeric = 1;
 constexpr int kErrTimeout = 2;
+
+// ---- cuBLAS GEMMs for the plain FP32 factor products (blas.cu) ----
+int blas_gemm_f32(int emulate_bf16x9, int transA, int M, int N, int K, float alpha, const float* A, int lda,
+                  const float* B, int ldb, float beta, float* C, int ldc, cudaStream_t st);
+// Global switch for the FP32 GEMM launchers: 0 = own SIMT kernels, 1 = cuBLAS FP32, 2 = cuBLAS
+// FP32 emulated on BF16 tensor cores.  Set by the orchestration per call (thread-local).
+void set_gemm_mode(int mode);
+int gemm_mode();
 
 // ---- FP64 symmetric eigensolver (eig.cu) ----
 // Workspace bytes needed for matrices up to order nmax.

@@ -12,6 +12,9 @@
 namespace cakf {
 
 static std::atomic<long long> g_launches{0};
+static thread_local int t_gemm_mode = 0;
+void set_gemm_mode(int mode) { t_gemm_mode = mode; }
+int gemm_mode() { return t_gemm_mode; }
 long long launch_count() { return g_launches.load(); }
 void note_launch(long long k) { g_launches += k; }
 
@@ -182,7 +185,8 @@ __global__ void k_cg_dots2(const T* __restrict__ V, const T* __restrict__ GV, in
 // Every block recomputes the scalars from the dot results and takes the same stop decision.
 template <class T>
 __global__ void k_cg_upd2(int j, const double* __restrict__ dots1, const double* __restrict__ dots2,
-                          T* __restrict__ V, T* __restrict__ GV, int ldv, T* __restrict__ r, T* __restrict__ v, int m,
+                          T* __restrict__ V, T* __restrict__ GV, int ldv, T* __restrict__ r, T* __restrict__ v,
+                          const T* __restrict__ s, T* __restrict__ Q, int m,
                           double bd_tol, double rtol2_r0sq, int use_rtol, int* __restrict__ active,
                           double* __restrict__ eta_out, double* __restrict__ alpha_out, int* __restrict__ count) {
   if (!*active) return;
@@ -222,8 +226,39 @@ __global__ void k_cg_upd2(int j, const double* __restrict__ dots1, const double*
     GV[(size_t)j * ldv + i] = gd * inv;
     v[i] = fma(coef, d, v[i]);
     r[i] = fma(-coef, gd, r[i]);
+    if (Q) Q[(size_t)j * ldv + i] = s[i] * T(1.0 / sqrt(dots1[j + 3]));
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) { eta_out[j] = eta; alpha_out[j] = alpha; *count = j + 1; }
+}
+
+// Projection coefficients of the action on the orthonormal basis Q of the previous actions:
+// qd[l] = Q[:, l] . s  (one block per l)
+template <class T>
+__global__ void k_cg_qdots(const T* __restrict__ Q, int ldq, int j, const T* __restrict__ s, int m,
+                           double* __restrict__ qd, const int* __restrict__ active) {
+  if (!*active) return;
+  const int l = blockIdx.x;
+  const T* a = Q + (size_t)l * ldq;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) acc += double(a[i]) * double(s[i]);
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) qd[l] = acc;
+}
+// s -= Q[:, :j] qd   (Gram-Schmidt against the previous actions; a no-op in exact arithmetic for CG
+// residuals, which are mutually orthogonal).  On the last pass S[:, j] = s.
+template <class T>
+__global__ void k_cg_qorth(const T* __restrict__ Q, int ldq, int j, const double* __restrict__ qd, T* __restrict__ s,
+                           int m, T* __restrict__ S, int lds, const int* __restrict__ active) {
+  if (!*active) return;
+  __shared__ double c[1024];
+  for (int q = threadIdx.x; q < j; q += blockDim.x) c[q] = qd[q];
+  __syncthreads();
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  T v = s[i];
+  for (int q = 0; q < j; ++q) v = fma(-Q[(size_t)q * ldq + i], T(c[q]), v);
+  s[i] = v;
+  if (S) S[(size_t)j * lds + i] = v;
 }
 
 // s = r (CG policy: the current residual) or s = the replayed action; S[:, j] = s.
@@ -746,6 +781,70 @@ __global__ void k_scale_cols(T* A, int ld, int rows, int cols, T s) {
   if (i < rows && c < cols) A[(size_t)c * ld + i] *= s;
 }
 
+// In-place Cholesky (lower) of the leading j x j block of a symmetric matrix (column-major, ld),
+// symmetrised from both triangles first.  Block-wide; returns false (on all threads) if not PD.
+__device__ bool block_cholesky(double* A, int ld, int j) {
+  __shared__ double piv;
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  for (int e = threadIdx.x; e < j * j; e += blockDim.x) {
+    int r = e % j, c = e / j;
+    if (r > c) {
+      double v = 0.5 * (A[(size_t)c * ld + r] + A[(size_t)r * ld + c]);
+      A[(size_t)c * ld + r] = v;
+    }
+  }
+  __syncthreads();
+  for (int p = 0; p < j; ++p) {
+    if (threadIdx.x == 0) {
+      double d = A[(size_t)p * ld + p];
+      if (!(d > 0.0) || !isfinite(d)) { bad = 1; d = 1.0; }
+      piv = sqrt(d);
+      A[(size_t)p * ld + p] = piv;
+    }
+    __syncthreads();
+    for (int q = p + 1 + threadIdx.x; q < j; q += blockDim.x) A[(size_t)p * ld + q] /= piv;
+    __syncthreads();
+    const int w = j - p - 1;
+    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+      int q = p + 1 + e % w, c = p + 1 + e / w;
+      if (q >= c) A[(size_t)c * ld + q] -= A[(size_t)p * ld + q] * A[(size_t)p * ld + c];
+    }
+    __syncthreads();
+  }
+  bool ok = bad == 0;
+  __syncthreads();
+  return ok;
+}
+
+// Per-step NLL from its definition (eq. proj-observation with the actions S of the step):
+//   nll = 1/2 [ j log 2 pi + logdet(S^T G S) ] + 1/2 yh^T (S^T G S)^-1 yh - 1/2 logdet(S^T S),
+// yh = S^T r0, with both log-determinants from FP64 Cholesky factors of the leading j x j blocks.
+// z (length >= j) is scratch for the forward substitution.
+__global__ void k_nll_def(const int* __restrict__ count, double* __restrict__ Gh, double* __restrict__ SS, int ld,
+                          const double* __restrict__ yh, double* __restrict__ z, double* __restrict__ nll_k,
+                          int* __restrict__ err) {
+  const int j = *count;
+  const bool ok1 = block_cholesky(Gh, ld, j);
+  const bool ok2 = block_cholesky(SS, ld, j);
+  if (threadIdx.x == 0) {
+    double ld1 = 0.0, ld2 = 0.0, quad = 0.0;
+    for (int q = 0; q < j; ++q) {
+      ld1 += log(Gh[(size_t)q * ld + q]);
+      ld2 += log(SS[(size_t)q * ld + q]);
+    }
+    for (int q = 0; q < j; ++q) {          // L z = yh, L = lower Cholesky factor of S^T G S
+      double acc = yh[q];
+      for (int l = 0; l < q; ++l) acc -= Gh[(size_t)l * ld + q] * z[l];
+      z[q] = acc / Gh[(size_t)q * ld + q];
+      quad += z[q] * z[q];
+    }
+    const double val = 0.5 * j * 1.8378770664093453 + ld1 + 0.5 * quad - ld2;
+    *nll_k = val;
+    if (!ok1 || !ok2 || !isfinite(val)) atomicExch(err, kErrNumeric);
+  }
+}
+
 __global__ void k_set_diag(double* __restrict__ G, int ld, const double* __restrict__ lam, double scale, int r) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < r) G[(size_t)i * ld + i] = scale * lam[i];
@@ -864,11 +963,23 @@ void cg_dots2(const T* V, const T* GV, int ldv, int j, int m, double* dots, cons
   k_cg_dots2<T><<<j + 1, 256, 0, st>>>(V, GV, ldv, j, m, dots, active); note_launch();
 }
 template <class T>
-void cg_upd2(int j, const double* dots1, const double* dots2, T* V, T* GV, int ldv, T* r, T* v, int m, double bd_tol,
-             double rtol2_r0sq, int use_rtol, int* active, double* eta, double* alpha, int* count, cudaStream_t st) {
-  k_cg_upd2<T><<<cdiv(m, 256), 256, 0, st>>>(j, dots1, dots2, V, GV, ldv, r, v, m, bd_tol, rtol2_r0sq, use_rtol,
-                                             active, eta, alpha, count);
+void cg_upd2(int j, const double* dots1, const double* dots2, T* V, T* GV, int ldv, T* r, T* v, const T* s, T* Q,
+             int m, double bd_tol, double rtol2_r0sq, int use_rtol, int* active, double* eta, double* alpha,
+             int* count, cudaStream_t st) {
+  k_cg_upd2<T><<<cdiv(m, 256), 256, 0, st>>>(j, dots1, dots2, V, GV, ldv, r, v, s, Q, m, bd_tol, rtol2_r0sq,
+                                             use_rtol, active, eta, alpha, count);
   note_launch();
+}
+template <class T>
+void cg_reorth(const T* Q, int ldq, int j, T* s, int m, double* qd, T* S, int lds, const int* active, cudaStream_t st) {
+  // two classical Gram-Schmidt passes against the previous (orthonormal) action basis
+  for (int pass = 0; pass < 2; ++pass) {
+    if (j > 0) {
+      k_cg_qdots<T><<<j, 256, 0, st>>>(Q, ldq, j, s, m, qd, active); note_launch();
+    }
+    k_cg_qorth<T><<<cdiv(m, 256), 256, 0, st>>>(Q, ldq, j, qd, s, m, pass == 1 ? S : nullptr, lds, active);
+    note_launch();
+  }
 }
 template <class T>
 void cg_select(int j, const T* r, const double* rep, int m, T* s, T* S, int lds, const int* active, cudaStream_t st) {
@@ -880,10 +991,28 @@ void cg_init(const double* y, const double* mpred, const int* obs, int m, T* r, 
   k_cg_init<T><<<cdiv(m, 256), 256, 0, st>>>(y, mpred, obs, m, r, r0, v, r0sq); note_launch();
 }
 
+__global__ void k_axpby_f32_f64(const float* __restrict__ X, int ldx, int rows, int cols, double alpha, double beta,
+                                double* __restrict__ C, int ldc) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int c = blockIdx.y;
+  if (i >= rows || c >= cols) return;
+  double* p = C + (size_t)c * ldc + i;
+  *p = alpha * double(X[(size_t)c * ldx + i]) + (beta != 0.0 ? beta * *p : 0.0);
+}
+
 template <class T>
 void gemm_tn(const T* A, int lda, int na, const T* B, int ldb, int nb, int K, double alpha, double beta, double* C,
              int ldc, double* part, size_t part_elems, cudaStream_t st) {
   if (na <= 0 || nb <= 0) return;
+  if (sizeof(T) == 4 && t_gemm_mode > 0 && (double)na * nb * K > 2e7 && part_elems * 2 >= (size_t)na * nb) {
+    // FP32 product into the partial buffer (reinterpreted as floats), then scale into C (double)
+    float* tmp = reinterpret_cast<float*>(part);
+    if (blas_gemm_f32(t_gemm_mode == 2, 1, na, nb, K, 1.0f, (const float*)A, lda, (const float*)B, ldb, 0.0f, tmp, na,
+                      st) == 0) {
+      k_axpby_f32_f64<<<dim3(cdiv(na, 256), nb), 256, 0, st>>>(tmp, na, na, nb, alpha, beta, C, ldc); note_launch();
+      return;
+    }
+  }
   const size_t tile_elems = (size_t)na * nb;
   int gx = cdiv(na, TN_T), gy = cdiv(nb, TN_T);
   int want = std::max(1, (int)(2 * 152 / std::max(1, gx * gy)));
@@ -898,12 +1027,43 @@ void gemm_tn(const T* A, int lda, int na, const T* B, int ldb, int nb, int K, do
   k_reduce_splits<double><<<cdiv(tile_elems, 256), 256, 0, st>>>(part, nsplit, na, nb, alpha, beta, C, ldc); note_launch();
 }
 
+// FP32 copy of a small double coefficient block for the cuBLAS path (thread-local device scratch)
+static thread_local float* t_bscratch = nullptr;
+static thread_local size_t t_bscratch_elems = 0;
+static float* bscratch(size_t elems) {
+  if (elems > t_bscratch_elems) {
+    if (t_bscratch) cudaFree(t_bscratch);
+    t_bscratch = nullptr;
+    t_bscratch_elems = 0;
+    if (cudaMalloc(&t_bscratch, elems * sizeof(float)) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    t_bscratch_elems = elems;
+  }
+  return t_bscratch;
+}
+
 template <class T, class TB>
 void gemm_nn(int M, int N, int K, T alpha, const T* A, int lda, const TB* B, int ldb, T beta, T* C, int ldc,
              cudaStream_t st) {
   if (M <= 0 || N <= 0) return;
   if (K <= 0) {
     if (beta == T(1)) return;
+  }
+  if (sizeof(T) == 4 && t_gemm_mode > 0 && K > 0 && (double)M * N * K > 2e7) {
+    const float* Bf = reinterpret_cast<const float*>(B);
+    int ldbf = ldb;
+    if (sizeof(TB) == 8) {
+      float* sb = bscratch((size_t)K * N);
+      if (sb) {
+        convert_from_f64<float>(reinterpret_cast<const double*>(B), ldb, K, N, sb, K, st);
+        Bf = sb;
+        ldbf = K;
+      } else {
+        Bf = nullptr;
+      }
+    }
+    if (Bf && blas_gemm_f32(t_gemm_mode == 2, 0, M, N, K, (float)alpha, (const float*)A, lda, Bf, ldbf, (float)beta,
+                            (float*)C, ldc, st) == 0)
+      return;
   }
   k_gemm_nn<T, TB><<<dim3(cdiv(M, NN_BM), cdiv(N, NN_BN)), 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc); note_launch();
 }
@@ -1001,6 +1161,11 @@ template void tangent_mean<float>(const double*, const float*, size_t, int, int,
 template void tangent_mean<double>(const double*, const double*, size_t, int, int, const double*, int, int, int,
                                    double*, cudaStream_t);
 
+void nll_def(const int* count, double* Gh, double* SS, int ld, const double* yh, double* z, double* nll_k, int* err,
+             cudaStream_t st) {
+  k_nll_def<<<1, 256, 0, st>>>(count, Gh, SS, ld, yh, z, nll_k, err); note_launch();
+}
+
 void set_diag(double* G, int ld, const double* lam, double scale, int r, cudaStream_t st) {
   if (r <= 0) return;
   k_set_diag<<<cdiv(r, 256), 256, 0, st>>>(G, ld, lam, scale, r); note_launch();
@@ -1042,8 +1207,9 @@ void check_finite(const double* x, size_t n, int* err, cudaStream_t st) {
                             const int*, cudaStream_t);                                                           \
   template void cg_upd1<T>(int, const double*, T*, T*, int, const T*, const T*, int, const int*, cudaStream_t);  \
   template void cg_dots2<T>(const T*, const T*, int, int, int, double*, const int*, cudaStream_t);               \
-  template void cg_upd2<T>(int, const double*, const double*, T*, T*, int, T*, T*, int, double, double, int,     \
-                           int*, double*, double*, int*, cudaStream_t);                                          \
+  template void cg_upd2<T>(int, const double*, const double*, T*, T*, int, T*, T*, const T*, T*, int, double,  \
+                           double, int, int*, double*, double*, int*, cudaStream_t);                             \
+  template void cg_reorth<T>(const T*, int, int, T*, int, double*, T*, int, const int*, cudaStream_t);          \
   template void cg_select<T>(int, const T*, const double*, int, T*, T*, int, const int*, cudaStream_t);          \
   template void cg_init<T>(const double*, const double*, const int*, int, T*, T*, T*, double*, cudaStream_t);    \
   template void gemm_tn<T>(const T*, int, int, const T*, int, int, int, double, double, double*, int, double*,   \
