@@ -218,12 +218,14 @@ def main():
     e0.record(stream)
     prof = {"gram_block_ms": 0.0, "gram_block_launches": 0, "gram_block_flops": 0.0, "gram_block_evals": 0.0,
             "cg_matvec_ms": 0.0, "cg_matvec_launches": 0, "cg_matvec_evals": 0.0, "eig_ms": 0.0, "eig_calls": 0}
+    phases = [0.0] * 8
     for _ in range(args.steps):
         one_step()
         st = ck.cakf_get_stats(ctx)
         launches += int(st["kernel_launches"])
         for k in prof:
             prof[k] += st[k]
+        phases = [a + b for a, b in zip(phases, st["phase_ms"])]
     e1.record(stream)
     torch.cuda.synchronize(dev)
     clocks = sampler.stop()
@@ -272,6 +274,9 @@ def main():
                       "evals_per_launch": prof["cg_matvec_evals"] / max(1, prof["cg_matvec_launches"])},
         "eig": {"calls": prof["eig_calls"], "avg_ms": prof["eig_ms"] / max(1, prof["eig_calls"])},
         "phase_ms": {"filter": st["filter_ms"], "smooth": st["smooth_ms"]},
+        "phase_ms_per_pass": dict(zip(["filter_cg", "filter_finalize", "filter_truncate", "smooth_gram",
+                                       "smooth_combine", "smooth_truncate", "nll", "reserved"],
+                                      [p / max(1, args.steps) for p in phases])),
         "clocks": clocks,
         "gpu_launches": launches,
     }

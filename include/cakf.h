@@ -102,6 +102,15 @@ typedef struct {
   int64_t eig_calls;
   int64_t kernel_launches;    /* kernels this library launched in the last filter + smooth    */
   int64_t device_bytes;       /* device memory held by the context                            */
+  /* device time per phase, summed over the steps (profiling on):
+     [0] filter CG loop (actions, G s products, G-orthogonalisation)
+     [1] filter Gram x block finalize incl. its low-rank correction and outputs
+     [2] filter truncation (Gram, FP64 eig, rotation)
+     [3] smoother P^- X (Gram x block + low-rank correction)
+     [4] smoother combine and outputs (Z, P X, ws)
+     [5] smoother truncation (Gram identities, FP64 eig, rotation)
+     [6] NLL term per step                                      [7] reserved               */
+  double phase_ms[8];
 } cakf_stats;
 
 /*

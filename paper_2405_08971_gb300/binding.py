@@ -40,7 +40,7 @@ class cakf_stats(C.Structure):
         ("gram_block_launches", C.c_int64), ("gram_block_flops", C.c_double), ("gram_block_evals", C.c_double),
         ("cg_matvec_ms", C.c_double), ("cg_matvec_launches", C.c_int64), ("cg_matvec_evals", C.c_double),
         ("eig_ms", C.c_double), ("eig_calls", C.c_int64), ("kernel_launches", C.c_int64),
-        ("device_bytes", C.c_int64),
+        ("device_bytes", C.c_int64), ("phase_ms", C.c_double * 8),
     ]
 
 
@@ -255,7 +255,9 @@ def pack_actions(S_list, T):
 def cakf_get_stats(ctx: Context) -> dict:
     s = cakf_stats()
     _check(lib().cakf_get_stats(ctx.handle, C.byref(s)))
-    return {f: getattr(s, f) for f, _ in cakf_stats._fields_}
+    out = {f: getattr(s, f) for f, _ in cakf_stats._fields_}
+    out["phase_ms"] = list(out["phase_ms"])
+    return out
 
 
 def cakf_gram_matmul(kernel, log_lx, log_sf2, Xr, Xc, B, out=None, precision="fp32", stream=None):

@@ -117,6 +117,7 @@ struct cakf_ctx {
   bool profiling = false;
   cakf_stats stats{};
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_gb, prof_mv, prof_eig;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_phase;
   std::vector<double> prof_gb_flops, prof_gb_evals, prof_mv_evals;
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
@@ -332,6 +333,20 @@ struct Runner {
   bool tc;      // tensor-core Gram x block
   int tc_kind;  // 0 bf16, 1 tf32
 
+  // phase timers (profiling on): begin returns the start event, end records the pair
+  cudaEvent_t ph_begin() {
+    if (!c->profiling) return nullptr;
+    cudaEvent_t e = c->ev();
+    cudaEventRecord(e, st);
+    return e;
+  }
+  void ph_end(int id, cudaEvent_t e0) {
+    if (!e0) return;
+    cudaEvent_t e1 = c->ev();
+    cudaEventRecord(e1, st);
+    c->prof_phase.push_back({id, {e0, e1}});
+  }
+
   T* Mk(int k) { return (T*)c->Mpool + c->off_M[k]; }
   T* PV(int k) { return (T*)c->PVpool + c->off_PV[k]; }
   T* Vk(int k) { return (T*)c->Vpool + c->off_V[k]; }
@@ -408,6 +423,7 @@ struct Runner {
       T* s = (T*)c->sv;
       T* GV = (T*)c->GV;
       T* GSk = (T*)c->GS;      // G s_j of every iteration (column j), for the NLL
+      cudaEvent_t ph0 = ph_begin();
       gather_coords<T>(X(), ob, m, Xo, st);
       gather_rows<T>(Mk(k - 1), ldn, ob, m, rp, Mo, m, st);
       cudaMemsetAsync(c->r0sq, 0, sizeof(double), st);
@@ -453,7 +469,9 @@ struct Runner {
         cg_upd2<T>(j, c->dots, c->dots2, V, GV, m, r, vcol, s, rep ? nullptr : Qa, m, bd_tol, rtol2, use_rtol,
                    c->active, c->eta + (size_t)k * B, c->alpha + (size_t)k * B, c->count + k, st);
       }
+      ph_end(0, ph0);
       // finalize: [P^- W, P^- w] = K(X, X_o) [V v] - a^2 M+ (M+_o^T [V v])
+      cudaEvent_t ph1 = ph_begin();
       T* PVk = PV(k);
       if (int rcg = gram_block(X(), n, Xo, m, V, m, ic + 1, PVk, ldn)) return rcg;
       if (rp > 0) {
@@ -462,6 +480,8 @@ struct Runner {
         gemm_nn<T, double>(n, ic + 1, rp, T(-a2), Mk(k - 1), ldn, t2, rp, T(1), PVk, ldn, st);
       }
       filter_out<T>(c->mpred, PVk, ldn, ic, c->sf2, a2, c->rs_plus, n, mout, vout, c->rs_pw, st);
+      ph_end(1, ph1);
+      cudaEvent_t ph6 = ph_begin();
       // NLL term from its definition: S^T G S (with the stored G s_j), S^T S and S^T r0, FP64 Cholesky
       {
         double* SS = c->small;
@@ -473,9 +493,12 @@ struct Runner {
         gemm_tn<T>(Sk(k), m, ic, (const T*)c->r0v, m, 1, m, 1.0, 0.0, yh, ic, c->part64, c->part64_elems, st);
         nll_def(c->count + k, Gh, SS, ic, yh, zs, c->nll + k, c->err, st);
       }
+      ph_end(6, ph6);
       // Truncate (Sec. 3.2)
+      cudaEvent_t ph2 = ph_begin();
       int rc = truncate_filter(k, rp, ic);
       if (rc) return rc;
+      ph_end(2, ph2);
       cudaError_t ce = cudaGetLastError();
       if (ce != cudaSuccess) return fail(CAKF_ERR_CUDA, std::string("filter step: ") + cudaGetErrorString(ce));
     }
@@ -521,7 +544,11 @@ struct Runner {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (c->profiling) { e0 = c->ev(); e1 = c->ev(); cudaEventRecord(e0, st); }
     int rc = eig_sym_topk<double>(G, N, N, keep, c->wv, c->U64, N, c->eigw, c->eigw_bytes, c->err, st);
-    if (rc) return fail(CAKF_ERR_CUDA, "eigensolver launch failed (code " + std::to_string(rc) + ")");
+    if (rc) {
+      cudaGetLastError();
+      std::string why = rc >= 1000 ? cudaGetErrorString((cudaError_t)(rc - 1000)) : std::to_string(rc);
+      return fail(CAKF_ERR_CUDA, "eigensolver launch failed (N = " + std::to_string(N) + "): " + why);
+    }
     convert_from_f64<T>(c->U64, N, N, keep, (T*)c->UT, N, st);
     if (c->profiling) {
       cudaEventRecord(e1, st);
@@ -560,6 +587,7 @@ struct Runner {
     T* Y = (T*)c->Y;
     for (int k = T_ - 1; k >= 0; --k) {
       // X = A^T [Ws ws] = a [Ws ws]
+      cudaEvent_t ph3 = ph_begin();
       build_x<T>(Ws, ldn, cw, ws, T(a), n, Xs, ldn, st);
       // Y = P^-_k X = K X - a^2 M+_{k-1} (M+_{k-1}^T X)
       if (int rcg = gram_block(X(), n, X(), n, Xs, ldn, cw + 1, Y, ldn)) return rcg;
@@ -569,6 +597,8 @@ struct Runner {
         gemm_tn<T>(Mk(k - 1), ldn, rp, Xs, ldn, cw + 1, n, 1.0, 0.0, t, rp, c->part64, c->part64_elems, st);
         gemm_nn<T, double>(n, cw + 1, rp, T(-a2), Mk(k - 1), ldn, t, rp, T(1), Y, ldn, st);
       }
+      ph_end(3, ph3);
+      cudaEvent_t ph4 = ph_begin();
       const int ic = (k >= 1) ? c->icap[k] : 0;
       const int m = (k >= 1) ? mk(k) : 0;
       double* Z = c->small;                       // ic x (cw+1)
@@ -602,6 +632,8 @@ struct Runner {
       T* vz = (T*)c->Fb;
       gemm_nn<T, double>(m, 1, ic, T(1), Vkk, m, Z + (size_t)cw * ic, ic, T(0), vz, m, st);
       ws_obs<T>(obs(k), m, Vkk + (size_t)ic * m, vz, wn, st);
+      ph_end(4, ph4);
+      cudaEvent_t ph5 = ph_begin();
       // Gram of Ws_full = [W_k, X'] with X' = X[:, :cw] - W_k Z[:, :cw]  (small-matrix identities)
       const int N = ic + cw;
       double* G = c->gram;
@@ -658,6 +690,7 @@ struct Runner {
         cudaMemcpyAsync(Gn, G, (size_t)N * N * sizeof(double), cudaMemcpyDeviceToDevice, st);
         cw = N;
       }
+      ph_end(5, ph5);
       std::swap(Ws, Wn); std::swap(ws, wn); std::swap(Gw, Gn);
       cudaError_t ce = cudaGetLastError();
       if (ce != cudaSuccess) return fail(CAKF_ERR_CUDA, std::string("smoother step: ") + cudaGetErrorString(ce));
@@ -942,6 +975,12 @@ void collect_profile(cakf_ctx* c) {
   c->stats.cg_matvec_launches += (int64_t)c->prof_mv.size();
   for (double f : c->prof_mv_evals) c->stats.cg_matvec_evals += f;
   c->stats.eig_ms += sum(c->prof_eig);
+  for (auto& ph : c->prof_phase) {
+    float ms = 0;
+    cudaEventElapsedTime(&ms, ph.second.first, ph.second.second);
+    c->stats.phase_ms[ph.first] += ms;
+  }
+  c->prof_phase.clear();
   c->prof_gb.clear(); c->prof_gb_flops.clear(); c->prof_gb_evals.clear();
   c->prof_mv.clear(); c->prof_mv_evals.clear(); c->prof_eig.clear();
   c->ev_used = 0;

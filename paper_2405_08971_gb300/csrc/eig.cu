@@ -19,6 +19,22 @@ namespace {
 
 constexpr double kEps = 2.220446049250313e-16;
 
+// Reciprocal by Newton-Raphson: an FP32 seed (rcp.approx, ~2^-23 relative) refined by two FP64
+// Newton steps r <- r + r (1 - x r), which square the relative error each time (2^-46, 2^-92), so
+// the result is accurate to the last bit or two of FP64.  Falls back to division outside the FP32
+// exponent range.
+__device__ __forceinline__ double nr_rcp(double x) {
+  const float xf = (float)x;
+  const float ax = fabsf(xf);
+  if (!(ax > 1e-36f && ax < 1e36f)) return 1.0 / x;
+  float rf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(xf));
+  double r = (double)rf;
+  r = fma(r, fma(-x, r, 1.0), r);
+  r = fma(r, fma(-x, r, 1.0), r);
+  return r;
+}
+
 // ---------------------------------------------------------------------------------- tridiagonal
 // Householder tridiagonalisation (lower), one grid barrier per column.  Columns of the trailing
 // block are owned by (block, warp) round-robin.  At step k every block knows v_k, tau_k (computed
@@ -53,14 +69,21 @@ k_tridiag(double* __restrict__ A, int lda, int N, double* __restrict__ d, double
   double* v2 = sm + N;       // v_{k+1}
   double* w = sm + 2 * N;    // w_k
   double* c = sm + 3 * N;    // updated pivot column
+  double* cols = sm + 4 * N; // owned columns (full length N), resident for the whole reduction
   const int G = gridDim.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int nslot = (N + G - 1) / G;   // column j lives in block j % G, slot j / G
   if (N <= 2) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       d[0] = A[0];
       if (N == 2) { e[0] = A[1]; d[1] = A[(size_t)lda + 1]; tau[0] = 0.0; }
     }
     return;
+  }
+  for (int q = 0; q < nslot; ++q) {
+    const int j = q * G + blockIdx.x;
+    if (j >= N) break;
+    for (int t = threadIdx.x; t < N; t += blockDim.x) cols[(size_t)q * N + t] = A[(size_t)j * lda + t];
   }
   // ---- prologue: v_0 from column 0; p_0; publish column 1
   double tk, bk;
@@ -69,8 +92,10 @@ k_tridiag(double* __restrict__ A, int lda, int N, double* __restrict__ d, double
     for (int t = threadIdx.x; t < L; t += blockDim.x) c[t] = A[1 + t];
     __syncthreads();
     householder(c, L, v, tk, bk);
-    for (int j = 1 + blockIdx.x + G * warp; j < N; j += G * nw) {
-      const double* col = A + (size_t)j * lda + 1;
+    for (int q = warp; q < nslot; q += nw) {
+      const int j = q * G + blockIdx.x;
+      if (j < 1 || j >= N) continue;
+      const double* col = cols + (size_t)q * N + 1;
       double acc = 0.0;
       for (int t = lane; t < L; t += 32) acc += col[t] * v[t];
       acc = warp_sum(acc);
@@ -86,7 +111,7 @@ k_tridiag(double* __restrict__ A, int lda, int N, double* __restrict__ d, double
     double* Pn = Pbuf + (size_t)((k + 1) & 1) * N;
     const double* Ck = Cbuf + (size_t)(k & 1) * N;
     double* Cn = Cbuf + (size_t)((k + 1) & 1) * N;
-    // (1) w_k = p_k - 1/2 tau_k (p_k . v_k) v_k
+    // (1) w_k = p_k - 1/2 tau_k (p_k . v_k) v_k ; (2) updated pivot column k+1
     double pv = 0.0;
     for (int t = threadIdx.x; t < L; t += blockDim.x) {
       const double pt = __ldcg(Pk + t);
@@ -97,7 +122,6 @@ k_tridiag(double* __restrict__ A, int lda, int N, double* __restrict__ d, double
     const double kc = 0.5 * tk * pv;
     for (int t = threadIdx.x; t < L; t += blockDim.x) w[t] -= kc * v[t];
     __syncthreads();
-    // (2) updated pivot column k+1 (rows k+1..N-1) and the next reflector
     for (int t = threadIdx.x; t < L; t += blockDim.x) c[t] = __ldcg(Ck + t) - v[t] * w[0] - w[t] * v[0];
     __syncthreads();
     const bool next = (k + 3 < N);      // a reflector for column k+1 exists
@@ -109,15 +133,17 @@ k_tridiag(double* __restrict__ A, int lda, int N, double* __restrict__ d, double
       tau[k] = tk;
       if (!next) { e[k + 1] = c[1]; tau[k + 1] = 0.0; }
     }
-    // (3) owners: A22 -= v w^T + w v^T; fused dot for p_{k+1}; publish pivot column k+2
-    for (int j = k + 1 + ((blockIdx.x - (k + 1) % G + G) % G) + G * warp; j < N; j += G * nw) {
+    // (3) owned columns: A22 -= v w^T + w v^T (rows k+1..), fused dot for p_{k+1}, publish column k+2
+    for (int q = warp; q < nslot; q += nw) {
+      const int j = q * G + blockIdx.x;
+      if (j < k + 1 || j >= N) continue;
       const int tj = j - (k + 1);
-      double* col = A + (size_t)j * lda + k + 1;
+      double* col = cols + (size_t)q * N + k + 1;
       const double vj = v[tj], wj = w[tj];
       const bool publish = next && tj == 1;       // column k+2 becomes the next pivot column
       double acc = 0.0;
       for (int t = lane; t < L; t += 32) {
-        const double nv = __ldcg(col + t) - (v[t] * wj + w[t] * vj);
+        const double nv = col[t] - (v[t] * wj + w[t] * vj);
         col[t] = nv;
         if (next && t >= 1) acc += nv * v2[t - 1];
         if (publish && t >= 1) Cn[t - 1] = nv;
@@ -126,8 +152,12 @@ k_tridiag(double* __restrict__ A, int lda, int N, double* __restrict__ d, double
         acc = warp_sum(acc);
         if (lane == 0) Pn[tj - 1] = tn * acc;
       }
+      if (k + 3 == N && j == N - 1) {                  // last diagonal entry (written by lane L-1)
+        __syncwarp();
+        if (lane == 0) d[N - 1] = col[L - 1];
+      }
     }
-    // (4) store the reflector v_k below the subdiagonal of column k
+    // (4) store the reflector v_k below the subdiagonal of column k (for the back-transformation)
     if (blockIdx.x == 0)
       for (int t = threadIdx.x; t < L; t += blockDim.x) A[(size_t)k * lda + k + 1 + t] = v[t];
     __syncthreads();
@@ -136,14 +166,13 @@ k_tridiag(double* __restrict__ A, int lda, int N, double* __restrict__ d, double
     bk = bn;
     if (!grid_barrier(bar, G, err)) return;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) d[N - 1] = __ldcg(A + (size_t)(N - 1) * lda + N - 1);
 }
 
 // ------------------------------------------------------------------------------ divide & conquer
 struct MergeDesc { int lo, mid, hi; };
 
 struct DcWork {
-  double *lam, *lamk, *lamtmp, *Dw, *Zw, *Dk, *Zk, *Dd, *Q, *Qtmp, *Delta, *rho, *rot;
+  double *lam, *lamk, *lamtmp, *Dw, *Zw, *Dk, *Zk, *Dd, *Q, *Qtmp, *Delta, *rho, *rot, *z2;
   int *colk, *cold, *perm, *Kp, *nrot, *mergeof;
 };
 
@@ -161,85 +190,105 @@ __global__ void k_dc_init(const double* __restrict__ d, const double* __restrict
 // Phase 1 of a merge: z vector, sorted poles, deflation.  One block per merge.
 __global__ void __launch_bounds__(256)
 k_dc_prep(const MergeDesc* __restrict__ merges, const double* __restrict__ e, int N, DcWork W) {
+  // The sequential part (merge of the two child spectra, deflation scan, ordering) runs on one
+  // thread over shared-memory copies; loads and stores are done by the whole block.
+  extern __shared__ double psm[];
   const MergeDesc mg = merges[blockIdx.x];
   const int lo = mg.lo, mid = mg.mid, K = mg.hi - mg.lo, n1 = mg.mid - mg.lo;
+  double* sLam = psm;
+  double* sZr = psm + K;
+  double* sD = psm + 2 * K;
+  double* sZ = psm + 3 * K;
+  int* sPerm = reinterpret_cast<int*>(psm + 4 * K);
+  int* sKeep = sPerm + K;
+  int* sDefl = sKeep + K;
   const double rho0 = e[mid - 1];
   const double sgn = rho0 >= 0.0 ? 1.0 : -1.0;
-  double* Dw = W.Dw + lo;
-  double* Zw = W.Zw + lo;
-  int* perm = W.perm + lo;
   double zz = 0.0;
   for (int t = threadIdx.x; t < K; t += blockDim.x) {
-    double z = (t < n1) ? W.Q[(size_t)(lo + t) * N + (mid - 1)] : sgn * W.Q[(size_t)(lo + t) * N + mid];
-    W.lamtmp[lo + t] = z;   // raw z (unsorted), reused below
+    const double z = (t < n1) ? W.Q[(size_t)(lo + t) * N + (mid - 1)] : sgn * W.Q[(size_t)(lo + t) * N + mid];
+    sZr[t] = z;
+    sLam[t] = W.lam[lo + t];
     zz += z * z;
   }
   zz = block_sum(zz);
-  __shared__ int s_kp, s_nrot;
+  __shared__ int s_kp, s_nd, s_nrot;
+  __shared__ double s_rho;
   if (threadIdx.x == 0) {
     const double zn = sqrt(zz);
     const double rho = fabs(rho0) * zz;
     // merge the two ascending child spectra
-    int a = 0, b = n1, s = 0;
+    int a = 0, b = n1, o = 0;
     while (a < n1 || b < K) {
       int pick;
       if (a >= n1) pick = b++;
       else if (b >= K) pick = a++;
-      else pick = (W.lam[lo + a] <= W.lam[lo + b]) ? a++ : b++;
-      perm[s] = pick;
-      Dw[s] = W.lam[lo + pick];
-      Zw[s] = W.lamtmp[lo + pick] / zn;
-      ++s;
+      else pick = (sLam[a] <= sLam[b]) ? a++ : b++;
+      sPerm[o] = pick;
+      sD[o] = sLam[pick];
+      sZ[o] = sZr[pick] / zn;
+      ++o;
     }
     double dmax = 0.0;
-    for (int t = 0; t < K; ++t) dmax = fmax(dmax, fabs(Dw[t]));
+    for (int t = 0; t < K; ++t) dmax = fmax(dmax, fabs(sD[t]));
     const double tol = 8.0 * kEps * fmax(dmax, rho);
-    // deflation scan
+    // deflation scan: small z components, then pairs of close poles (Givens rotation)
     int kp = 0, nd = 0, nrot = 0, last = -1;
-    int* keep = W.colk + lo;    // temporarily: sorted positions of kept entries
-    int* defl = W.cold + lo;    // sorted positions of deflated entries
     for (int j = 0; j < K; ++j) {
-      if (rho * fabs(Zw[j]) <= tol) { defl[nd++] = j; continue; }
+      if (rho * fabs(sZ[j]) <= tol) { sDefl[nd++] = j; continue; }
       if (last >= 0) {
-        const double t = hypot(Zw[last], Zw[j]);
-        const double c = Zw[j] / t, sn = -Zw[last] / t;
-        if (fabs((Dw[j] - Dw[last]) * c * sn) <= tol) {
+        const double t = hypot(sZ[last], sZ[j]);
+        const double c = sZ[j] / t, sn = -sZ[last] / t;
+        if (fabs((sD[j] - sD[last]) * c * sn) <= tol) {
           double* rr = W.rot + 4 * (size_t)(lo + nrot);
           rr[0] = last; rr[1] = j; rr[2] = c; rr[3] = sn;
           ++nrot;
-          const double dl = Dw[last], dj = Dw[j];
-          Dw[last] = c * c * dl + sn * sn * dj;
-          Dw[j] = sn * sn * dl + c * c * dj;
-          Zw[last] = 0.0;
-          Zw[j] = t;
-          defl[nd++] = last;
+          const double dl = sD[last], dj = sD[j];
+          sD[last] = c * c * dl + sn * sn * dj;
+          sD[j] = sn * sn * dl + c * c * dj;
+          sZ[last] = 0.0;
+          sZ[j] = t;
+          sDefl[nd++] = last;
           --kp;   // 'last' was the most recently kept entry
         }
       }
-      keep[kp++] = j;
+      sKeep[kp++] = j;
       last = j;
     }
-    // sort kept entries by pole (rotations can perturb the order slightly): insertion sort
+    // rotations can perturb the order of kept poles slightly: insertion sort (nearly sorted input)
     for (int a2 = 1; a2 < kp; ++a2) {
-      int key = keep[a2];
+      const int key = sKeep[a2];
       int b2 = a2 - 1;
-      while (b2 >= 0 && Dw[keep[b2]] > Dw[key]) { keep[b2 + 1] = keep[b2]; --b2; }
-      keep[b2 + 1] = key;
+      while (b2 >= 0 && sD[sKeep[b2]] > sD[key]) { sKeep[b2 + 1] = sKeep[b2]; --b2; }
+      sKeep[b2 + 1] = key;
     }
-    for (int t = 0; t < kp; ++t) { W.Dk[lo + t] = Dw[keep[t]]; W.Zk[lo + t] = Zw[keep[t]]; }
-    for (int t = 0; t < nd; ++t) W.Dd[lo + t] = Dw[defl[t]];
     s_kp = kp;
+    s_nd = nd;
     s_nrot = nrot;
+    s_rho = rho;
     W.rho[lo] = rho;
     W.Kp[lo] = kp;
   }
   __syncthreads();
+  const int kp = s_kp, nd = s_nd, nrot = s_nrot;
+  const double rho = s_rho;
+  for (int t = threadIdx.x; t < kp; t += blockDim.x) {
+    const int q = sKeep[t];
+    W.Dk[lo + t] = sD[q];
+    W.Zk[lo + t] = sZ[q];
+    W.z2[lo + t] = rho * sZ[q] * sZ[q];
+    W.colk[lo + t] = lo + sPerm[q];
+  }
+  for (int t = threadIdx.x; t < nd; t += blockDim.x) {
+    W.Dd[lo + t] = sD[sDefl[t]];
+    W.cold[lo + t] = lo + sPerm[sDefl[t]];
+  }
+  __syncthreads();
   // apply the deflation rotations to the (permuted) child eigenvector columns, rows lo..hi
-  const int nrot = s_nrot;
   for (int row = threadIdx.x; row < K; row += blockDim.x) {
     for (int q = 0; q < nrot; ++q) {
       const double* rr = W.rot + 4 * (size_t)(lo + q);
-      const int ca = lo + perm[(int)rr[0]], cb = lo + perm[(int)rr[1]];
+      const int ca = lo + sPerm[(int)rr[0]], cb = lo + sPerm[(int)rr[1]];
       double* qa = W.Q + (size_t)ca * N + lo + row;
       double* qb = W.Q + (size_t)cb * N + lo + row;
       const double c = rr[2], sn = rr[3];
@@ -248,10 +297,6 @@ k_dc_prep(const MergeDesc* __restrict__ merges, const double* __restrict__ e, in
       *qb = -sn * xa + c * xb;
     }
   }
-  __syncthreads();
-  // translate sorted positions to Q columns
-  for (int t = threadIdx.x; t < s_kp; t += blockDim.x) W.colk[lo + t] = lo + perm[W.colk[lo + t]];
-  for (int t = threadIdx.x; t < K - s_kp; t += blockDim.x) W.cold[lo + t] = lo + perm[W.cold[lo + t]];
 }
 
 // Phase 2: secular roots, one warp per (merge, root); the sums over poles are split across lanes.
@@ -269,6 +314,7 @@ __global__ void k_dc_secular(const MergeDesc* __restrict__ merges, const int* __
   if (i >= Kp) return;
   const double* Dk = W.Dk + lo;
   const double* Zk = W.Zk + lo;
+  const double* z2 = W.z2 + lo;
   const double rho = W.rho[lo];
   double* delta = W.Delta + (size_t)(lo + i) * N + lo;
   int org;
@@ -276,7 +322,7 @@ __global__ void k_dc_secular(const MergeDesc* __restrict__ merges, const int* __
   if (i < Kp - 1) {
     const double mid = 0.5 * (Dk[i] + Dk[i + 1]);
     double f = 0.0;
-    for (int j = lane; j < Kp; j += 32) f += rho * Zk[j] * Zk[j] / (Dk[j] - mid);
+    for (int j = lane; j < Kp; j += 32) f += z2[j] * nr_rcp(Dk[j] - mid);
     f = 1.0 + warp_sum(f);
     if (f >= 0.0) { org = i; tlo = 0.0; thi = mid - Dk[i]; }
     else { org = i + 1; tlo = mid - Dk[i + 1]; thi = 0.0; }
@@ -294,14 +340,16 @@ __global__ void k_dc_secular(const MergeDesc* __restrict__ merges, const int* __
     double psi = 0.0, dpsi = 0.0, phi = 0.0, dphi = 0.0;
     for (int j = lane; j < Kp; j += 32) {
       const double dl = (Dk[j] - Dorg) - tau;
-      const double rinv = 1.0 / dl;
-      const double tv = rho * Zk[j] * Zk[j] * rinv;
+      const double rinv = nr_rcp(dl);
+      const double tv = z2[j] * rinv;
       if (j <= i) { psi += tv; dpsi += tv * rinv; }
       else { phi += tv; dphi += tv * rinv; }
     }
     psi = warp_sum(psi); dpsi = warp_sum(dpsi); phi = warp_sum(phi); dphi = warp_sum(dphi);
     const double f = 1.0 + psi + phi;
     if (f == 0.0) break;
+    // residual test: f is as small as rounding of its terms allows (psi < 0 < phi term-wise)
+    if (fabs(f) <= 8.0 * kEps * (1.0 - psi + phi)) break;
     if (f > 0.0) thi = tau; else tlo = tau;
     const double Dl = (Dk[i] - Dorg) - tau;
     const double sl = Dl * Dl * dpsi;
@@ -382,7 +430,7 @@ __global__ void k_dc_vecs(const MergeDesc* __restrict__ merges, const int* __res
   if (i >= Kp) return;
   double* col = W.Delta + (size_t)(lo + i) * N + lo;
   double nrm = 0.0;
-  for (int j = lane; j < Kp; j += 32) { double u = W.Zw[lo + j] / col[j]; col[j] = u; nrm += u * u; }
+  for (int j = lane; j < Kp; j += 32) { double u = W.Zw[lo + j] * nr_rcp(col[j]); col[j] = u; nrm += u * u; }
   nrm = warp_sum(nrm);
   const double inv = 1.0 / sqrt(nrm);
   for (int j = lane; j < Kp; j += 32) col[j] *= inv;
@@ -433,21 +481,24 @@ k_dc_gemm(const MergeDesc* __restrict__ merges, int N, DcWork W) {
 // Phase 6: order the merged spectrum ascending and move columns back into Q.
 __global__ void __launch_bounds__(256)
 k_dc_finish(const MergeDesc* __restrict__ merges, int N, DcWork W) {
+  extern __shared__ double fsm[];
   const MergeDesc mg = merges[blockIdx.x];
   const int lo = mg.lo, K = mg.hi - mg.lo;
   const int Kp = W.Kp[lo];
-  int* perm = W.perm + lo;
+  double* sl = fsm;                                   // K merged eigenvalues (kept roots, deflated poles)
+  int* perm = reinterpret_cast<int*>(fsm + K);
+  int* dp = perm + K;
+  for (int t = threadIdx.x; t < K; t += blockDim.x) sl[t] = (t < Kp) ? W.lamk[lo + t] : W.Dd[lo + t - Kp];
+  __syncthreads();
   if (threadIdx.x == 0) {
-    for (int t = 0; t < K; ++t) W.lamtmp[lo + t] = (t < Kp) ? W.lamk[lo + t] : W.Dd[lo + t - Kp];
     // kept roots are ascending; sort the (nearly ascending) deflated poles, then merge the two lists
-    int* dp = W.colk + lo;   // scratch: order of the deflated entries (colk is no longer needed)
     const int Kd = K - Kp;
     for (int t = 0; t < Kd; ++t) dp[t] = Kp + t;
     for (int a = 1; a < Kd; ++a) {
-      int key = dp[a];
-      double kv = W.lamtmp[lo + key];
+      const int key = dp[a];
+      const double kv = sl[key];
       int b = a - 1;
-      while (b >= 0 && W.lamtmp[lo + dp[b]] > kv) { dp[b + 1] = dp[b]; --b; }
+      while (b >= 0 && sl[dp[b]] > kv) { dp[b + 1] = dp[b]; --b; }
       dp[b + 1] = key;
     }
     int x = 0, y = 0;
@@ -455,14 +506,14 @@ k_dc_finish(const MergeDesc* __restrict__ merges, int N, DcWork W) {
       int pick;
       if (x >= Kp) pick = dp[y++];
       else if (y >= Kd) pick = x++;
-      else pick = (W.lamtmp[lo + x] <= W.lamtmp[lo + dp[y]]) ? x++ : dp[y++];
+      else pick = (sl[x] <= sl[dp[y]]) ? x++ : dp[y++];
       perm[t] = pick;
     }
-    for (int t = 0; t < K; ++t) W.lam[lo + t] = W.lamtmp[lo + perm[t]];
   }
   __syncthreads();
+  for (int t = threadIdx.x; t < K; t += blockDim.x) W.lam[lo + t] = sl[perm[t]];
   for (int e2 = threadIdx.x; e2 < K * K; e2 += blockDim.x) {
-    int row = e2 % K, c = e2 / K;
+    const int row = e2 % K, c = e2 / K;
     W.Q[(size_t)(lo + c) * N + lo + row] = W.Qtmp[(size_t)(lo + perm[c]) * N + lo + row];
   }
 }
@@ -610,7 +661,7 @@ int eig_sym_topk(double* A, int lda, int N, int nkeep, double* w, T* U, int ldu,
   W.Zk = (double*)take(N * sizeof(double));
   W.Dd = (double*)take(N * sizeof(double));
   W.rho = (double*)take(N * sizeof(double));
-  take(N * sizeof(double));
+  W.z2 = (double*)take(N * sizeof(double));
   W.rot = (double*)take(4 * N * sizeof(double));
   W.colk = (int*)take(N * sizeof(int));
   W.cold = (int*)take(N * sizeof(int));
@@ -629,12 +680,22 @@ int eig_sym_topk(double* A, int lda, int N, int nkeep, double* w, T* U, int ldu,
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     int G = N >= 3 ? std::max(1, std::min(nsm, (N + 7) / 8)) : 1;
-    size_t smem = 4 * (size_t)N * sizeof(double);
+    cudaFuncSetAttribute(k_tridiag, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    size_t smem = 0;
+    for (int attempt = 0; attempt < 8; ++attempt) {
+      const int nslot = (N + G - 1) / G;
+      smem = (4 + (size_t)nslot) * N * sizeof(double);
+      cudaFuncSetAttribute(k_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 48 * 1024));
+      int occ = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tridiag, 256, smem);
+      if ((long long)occ * nsm >= G) break;
+      G = std::max(1, occ * nsm);     // fewer blocks own more columns each
+      if (occ == 0) { cudaGetLastError(); return 1000 + (int)cudaErrorCooperativeLaunchTooLarge; }
+    }
     void* args[] = {&A, &lda, &N, &d, &e, &tau, &P, &Cb, &bar, &err};
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaError_t ce = cudaLaunchCooperativeKernel((void*)k_tridiag, dim3(G), dim3(256), args, smem, st);
     note_launch();
-    if (ce != cudaSuccess) return 3;
+    if (ce != cudaSuccess) return 1000 + (int)ce;
   }
   // 2. divide and conquer
   k_dc_init<<<(N + 255) / 256, 256, 0, st>>>(d, e, N, W.lam, W.Q); note_launch();
@@ -648,13 +709,17 @@ int eig_sym_topk(double* A, int lda, int N, int nkeep, double* w, T* U, int ldu,
     const int* dmo = pe->d_mergeof + (size_t)lv * N;
     int kmax = 0;
     for (int q = m0; q < m1; ++q) kmax = std::max(kmax, pl.merges[q].hi - pl.merges[q].lo);
-    k_dc_prep<<<nm, 256, 0, st>>>(dm, e, N, W); note_launch();
+    const size_t psmem = (size_t)kmax * (4 * sizeof(double) + 3 * sizeof(int));
+    if (psmem > 48 * 1024) cudaFuncSetAttribute(k_dc_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
+    k_dc_prep<<<nm, 256, psmem, st>>>(dm, e, N, W); note_launch();
     k_dc_secular<<<(N * 32 + 255) / 256, 256, 0, st>>>(dm, dmo, N, W, err); note_launch();
     k_dc_zhat<<<(N * 32 + 255) / 256, 256, 0, st>>>(dm, dmo, N, W); note_launch();
     k_dc_vecs<<<(N * 32 + 255) / 256, 256, 0, st>>>(dm, dmo, N, W); note_launch();
     dim3 gg((kmax + DG_T - 1) / DG_T, (kmax + DG_T - 1) / DG_T, nm);
     k_dc_gemm<<<gg, 256, 0, st>>>(dm, N, W); note_launch();
-    k_dc_finish<<<nm, 256, 0, st>>>(dm, N, W); note_launch();
+    const size_t fsmem = (size_t)kmax * (sizeof(double) + 2 * sizeof(int));
+    if (fsmem > 48 * 1024) cudaFuncSetAttribute(k_dc_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
+    k_dc_finish<<<nm, 256, fsmem, st>>>(dm, N, W); note_launch();
   }
   // 3. back-transformation of the top nkeep columns (descending eigenvalues)
   {

@@ -24,7 +24,7 @@ constexpr int BM = 128;          // rows per CTA (TMEM lanes)
 constexpr int BK = 64;           // kernel columns per pipeline stage (64 bf16 = one 128B swizzle row)
 constexpr int NPROD_WARPS = 8;   // kernel-tile producers
 constexpr int TMA_WARP = 8;
-constexpr int MMA_WARP = 9;
+constexpr int MMA_WARP = 9;      // the remaining warp issues the MMAs
 constexpr int NTHREADS = 320;
 constexpr int A_STAGE_BYTES = BM * BK * 2;   // 16 KB
 constexpr long long WAIT_LIMIT = 20000000LL;
@@ -271,7 +271,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmapB, const TcParams P) {
         }
       }
     }
-  } else {
+  } else if (warp == MMA_WARP) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       bool ok = true;
