@@ -32,6 +32,7 @@
 #define CAKF_H
 
 #include <stdint.h>
+#include <stddef.h>
 
 #ifdef __cplusplus
 extern "C" {
@@ -183,6 +184,39 @@ int cakf_get_actions(cakf_ctx* ctx, double* actions_out, int32_t* counts_out);
 int cakf_gram_matmul(int32_t kernel, double log_lx, double log_sf2, int32_t dim, const double* Xr, int32_t nr,
                      const double* Xc, int32_t nc, const void* B, int32_t ldb, int32_t width, void* Out,
                      int32_t ldo, int32_t precision, void* cuda_stream);
+
+/*
+ * cakf_gram_matmul_noalloc -- cakf_gram_matmul (same arguments, same results, same kernels)
+ * for callers that must not allocate device memory.  The paper has no counterpart: it is a
+ * library integration variant, not part of the method.
+ *
+ * Who needs it: cakf_gram_matmul grows a per-thread scratch with cudaMalloc / cudaFree.  Those
+ * calls synchronise the device and can fail when another allocator (a framework's caching
+ * allocator, a pool sized at start-up) already holds almost all device memory; a caller in a
+ * latency-bound loop, or one working inside a fixed memory plan, cannot accept either.  This
+ * entry point performs no device allocation of its own: its scratch is one statically sized
+ * device array of the library, CAKF_NOALLOC_SCRATCH_BYTES per device, reserved when the
+ * library's module is loaded on that device.
+ *
+ * Limit: the scratch must hold 256 bytes + (nr + nc) coordinate records (32 bytes each for
+ * CAKF_FP64, 16 otherwise, rounded up to 256) and, for CAKF_BF16, the packed operand
+ * (about 2 * nc * (width - 1) bytes plus 20 * nc).  A call needing more returns CAKF_ERR_ARG
+ * with the required size in cakf_last_error, before any device work; for example BF16 with
+ * nc = 32768, width = 513 fits, nc = 65536 needs width <= 257.
+ * Zero state: only the device error flag inside the scratch has to start at zero; the call
+ * clears it on its stream before use.  All other scratch bytes are written before being read.
+ * Concurrency: every call on a device uses the same scratch, so calls that overlap in time on
+ * one device (other streams, other host threads) race and corrupt each other's results.  The
+ * call synchronises its stream before returning; serialise calls across threads.
+ * Setup: the first call on a device looks up the scratch address (cudaGetSymbolAddress, with
+ * that device current) and sets kernel attributes; make that first call before any stream
+ * capture begins on the device.
+ * Errors: as cakf_gram_matmul, with CAKF_ERR_ARG also for calls exceeding the scratch.
+ */
+#define CAKF_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
+int cakf_gram_matmul_noalloc(int32_t kernel, double log_lx, double log_sf2, int32_t dim, const double* Xr,
+                             int32_t nr, const double* Xc, int32_t nc, const void* B, int32_t ldb, int32_t width,
+                             void* Out, int32_t ldo, int32_t precision, void* cuda_stream);
 
 /* cakf_get_stats -- timings and counters of the last filter / smooth calls (host output). */
 int cakf_get_stats(const cakf_ctx* ctx, cakf_stats* out);

@@ -71,6 +71,8 @@ def lib():
         L.cakf_gram_matmul.argtypes = [C.c_int32, C.c_double, C.c_double, C.c_int32, vp, C.c_int32, vp, C.c_int32,
                                        vp, C.c_int32, C.c_int32, vp, C.c_int32, C.c_int32, vp]
         L.cakf_gram_matmul.restype = C.c_int
+        L.cakf_gram_matmul_noalloc.argtypes = L.cakf_gram_matmul.argtypes
+        L.cakf_gram_matmul_noalloc.restype = C.c_int
         L.cakf_free.argtypes = [vp]
         L.cakf_free.restype = None
         L.cakf_last_error.restype = C.c_char_p
@@ -277,6 +279,28 @@ def cakf_gram_matmul(kernel, log_lx, log_sf2, Xr, Xc, B, out=None, precision="fp
     _check(lib().cakf_gram_matmul(int(kernel), float(log_lx), float(log_sf2), int(dim), Xr.data_ptr(), int(nr),
                                   Xc.data_ptr(), int(nc), B.data_ptr(), int(nc), int(width), out.data_ptr(), int(nr),
                                   prec, stream))
+    return out
+
+
+def cakf_gram_matmul_noalloc(kernel, log_lx, log_sf2, Xr, Xc, B, out, precision="fp32", stream=None):
+    """cakf_gram_matmul into a caller-provided `out`, with no device allocation by the library or
+    by this binding: Xr, Xc must be contiguous float64 CUDA tensors, B and out contiguous CUDA
+    tensors of the precision's element type (float64 for fp64, float32 otherwise), B of shape
+    (width, nc) and out of shape (width, nr) (column-major blocks).  Returns out."""
+    import torch
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    dt = torch.float64 if prec == FP64 else torch.float32
+    for name, t, want in (("Xr", Xr, torch.float64), ("Xc", Xc, torch.float64), ("B", B, dt), ("out", out, dt)):
+        if t.dtype != want or not t.is_contiguous():
+            raise ValueError(f"cakf_gram_matmul_noalloc: {name} must be a contiguous {want} tensor")
+    width, nc = B.shape
+    nr = Xr.shape[0]
+    dim = Xr.shape[1] if Xr.dim() > 1 else 1
+    if tuple(out.shape) != (width, nr):
+        raise ValueError("cakf_gram_matmul_noalloc: out must have shape (width, nr)")
+    _check(lib().cakf_gram_matmul_noalloc(int(kernel), float(log_lx), float(log_sf2), int(dim), Xr.data_ptr(),
+                                          int(nr), Xc.data_ptr(), int(nc), B.data_ptr(), int(nc), int(width),
+                                          out.data_ptr(), int(nr), prec, stream))
     return out
 
 

@@ -1161,6 +1161,9 @@ const char* cakf_last_error(void) { return g_err.c_str(); }
 
 }  // extern "C"
 
+// Lets the other translation units of the library report through cakf_last_error.
+int cakf::set_last_error(int code, const char* msg) { return fail(code, msg); }
+
 // Scratch of cakf_gram_matmul: kept per thread, grown on demand.
 namespace {
 struct GramScratch {

@@ -92,6 +92,9 @@ void scale_f64(double* A, int ld, int rows, int cols, double s, cudaStream_t st)
 template <class T>
 void convert_from_f64(const double* In, int ldi, int rows, int cols, T* Out, int ldo, cudaStream_t st);
 
+// Record msg as the calling thread's cakf_last_error message; returns code.
+int set_last_error(int code, const char* msg);
+
 // Device error-flag values (the flag is an int in device memory, 0 = ok)
 constexpr int kErrNumeric = 1;
 constexpr int kErrTimeout = 2;
