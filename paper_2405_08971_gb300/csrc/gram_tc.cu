@@ -22,10 +22,12 @@ namespace {
 
 constexpr int BM = 128;          // rows per CTA (TMEM lanes)
 constexpr int BK = 64;           // kernel columns per pipeline stage (64 bf16 = one 128B swizzle row)
-constexpr int NPROD_WARPS = 8;   // kernel-tile producers
-constexpr int TMA_WARP = 8;
-constexpr int MMA_WARP = 9;      // the remaining warp issues the MMAs
-constexpr int NTHREADS = 320;
+constexpr int NPROD_WARPS = 16;  // kernel-tile producers (and epilogue)
+constexpr int NQ = NPROD_WARPS / 4;   // producer warps per TMEM lane group: each takes BK / NQ columns
+constexpr int QCOLS = BK / NQ;        // kernel-tile columns per producer thread and slice
+constexpr int TMA_WARP = NPROD_WARPS;
+constexpr int MMA_WARP = NPROD_WARPS + 1;   // the remaining warp issues the MMAs
+constexpr int NTHREADS = (NPROD_WARPS + 2) * 32;
 constexpr int A_STAGE_BYTES = BM * BK * 2;   // 16 KB
 constexpr long long WAIT_LIMIT = 20000000LL;
 
@@ -111,7 +113,8 @@ struct TcParams {
   int nr;
   const C4<float>* Xc;     // padded to nk * BK entries (sentinel coordinates beyond nc)
   const float* wcol;       // padded mean column (zeros beyond nc), FP32
-  int nk;                  // number of K slices
+  int nk;                  // number of K slices per row tile
+  int ntiles;              // row tiles of BM rows
   int npad;                // accumulator columns (multiple of 16, <= 512)
   int nbox;                // TMA boxes per B slice
   int boxh;                // rows per TMA box
@@ -125,6 +128,34 @@ struct TcParams {
   uint32_t b_stage_bytes;
 };
 
+// Uniform vote over the producer warps (named barrier 1): true iff every producer passes true.
+__device__ __forceinline__ bool producers_all(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(NPROD_WARPS * 32)
+      : "memory");
+  return r != 0;
+}
+
+// Bounded wait that ignores the abort flag (used to let copies in flight land before exit).
+__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity) {
+  for (long long it = 0; it < WAIT_LIMIT; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return;
+  }
+}
+
+// Persistent schedule (stream-K): the work is the sequence of (row tile, K slice) units, tile-major;
+// CTA b takes units [total*b/G, total*(b+1)/G).  With G <= ntiles every CTA covers at least one full
+// tile's worth of slices, so a tile is shared by at most two CTAs; those add their partial sums
+// into an output zeroed beforehand (two addends onto zero: the result does not depend on order).
 template <int KER>
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_gram_tc(const __grid_constant__ CUtensorMap tmapB, const TcParams P) {
@@ -141,13 +172,16 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmapB, const TcParams P) {
   uint64_t* fullB = bars + S;
   uint64_t* fullC = bars + 2 * S;
   uint64_t* empty = bars + 3 * S;
-  uint64_t* done = bars + 4 * S;
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* done = bars + 4 * S;           // MMA -> epilogue: a tile's accumulator is complete
+  uint64_t* tfree = bars + 4 * S + 1;      // epilogue -> MMA: the accumulator has been read out
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 4 * S + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
-  float* mean_part = reinterpret_cast<float*>(tmem_holder + 4);     // [2][BM]
+  float* mean_part = reinterpret_cast<float*>(tmem_holder + 4);     // [2][NQ][BM]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row0 = blockIdx.x * BM;
+  const long long total = (long long)P.ntiles * P.nk;
+  const long long u0 = total * blockIdx.x / gridDim.x;
+  const long long u1 = total * (blockIdx.x + 1) / gridDim.x;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -157,6 +191,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmapB, const TcParams P) {
       mbar_init(smem_u32(&empty[s]), 1);
     }
     mbar_init(smem_u32(done), 1);
+    mbar_init(smem_u32(tfree), NPROD_WARPS);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -171,86 +206,116 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmapB, const TcParams P) {
   const uint32_t tmem = *tmem_holder;
 
   if (warp < NPROD_WARPS) {
-    // ------------------------------------------------------------ kernel-tile producers
-    const int rl = (warp & 3) * 32 + lane;          // row within the tile (= TMEM lane)
-    const int half = warp >> 2;                     // which 32 of the 64 slice columns
-    const int row = row0 + rl;
-    C4<float> xr;
-    if (row < P.nr) xr = P.Xr[row];
-    else { xr.x = xr.y = xr.z = 1.0e6f; xr.w = 0.f; }
-    float mean_acc = 0.f;
+    // ------------------------------------------------------------ kernel-tile producers + epilogue
+    const int lg = warp & 3;                        // TMEM lane group of this warp
+    const int qt = warp >> 2;                       // which NQ-th of the slice columns
+    const int rl = lg * 32 + lane;                  // row within the tile (= TMEM lane)
+    long long u = u0;
+    int tcount = 0;
     bool ok = true;
-    for (int kt = 0; kt < P.nk && ok; ++kt) {
-      const int s = kt % S;
-      const uint32_t n = kt / S;
-      ok = mbar_wait(smem_u32(&empty[s]), (n & 1) ^ 1, abort_flag);
-      ok = __all_sync(0xffffffffu, ok);
-      if (!ok) break;
-      ok = mbar_wait(smem_u32(&fullC[s]), n & 1, abort_flag);
-      ok = __all_sync(0xffffffffu, ok);
-      if (!ok) break;
-      const C4<float>* xc = reinterpret_cast<const C4<float>*>(C_base + (size_t)s * BK * 16) + half * 32;
-      const float* wc = reinterpret_cast<const float*>(W_base + (size_t)s * BK * 4) + half * 32;
-      uint8_t* arow = A_base + (size_t)s * A_STAGE_BYTES + rl * 128;
+    while (u < u1) {
+      const int tile = (int)(u / P.nk);
+      const long long tbeg = (long long)tile * P.nk, tend = tbeg + P.nk;
+      const long long uend = u1 < tend ? u1 : tend;
+      const bool split = (u != tbeg) || (uend != tend);
+      const int row = tile * BM + rl;
+      C4<float> xr;
+      if (row < P.nr) xr = P.Xr[row];
+      else { xr.x = xr.y = xr.z = 1.0e6f; xr.w = 0.f; }
+      float mean_acc = 0.f;
+      for (; u < uend; ++u) {
+        const long long it = u - u0;
+        const int s = (int)(it % S);
+        const uint32_t n = (uint32_t)(it / S);
+        ok = mbar_wait(smem_u32(&empty[s]), (n & 1) ^ 1, abort_flag);
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) break;
+        ok = mbar_wait(smem_u32(&fullC[s]), n & 1, abort_flag);
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) break;
+        const C4<float>* xc = reinterpret_cast<const C4<float>*>(C_base + (size_t)s * BK * 16) + qt * QCOLS;
+        const float* wc = reinterpret_cast<const float*>(W_base + (size_t)s * BK * 4) + qt * QCOLS;
+        uint8_t* arow = A_base + (size_t)s * A_STAGE_BYTES + rl * 128;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        uint32_t pk[4];
+        for (int q = 0; q < QCOLS / 8; ++q) {
+          uint32_t pk[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int c = q * 8 + e * 2;
-          const float k0 = kval<KER>(dist2(xr, xc[c]), P.sf2);
-          const float k1 = kval<KER>(dist2(xr, xc[c + 1]), P.sf2);
-          mean_acc = fmaf(k0, wc[c], mean_acc);
-          mean_acc = fmaf(k1, wc[c + 1], mean_acc);
-          pk[e] = pack_bf16(k0, k1);
+          for (int e = 0; e < 4; ++e) {
+            const int c = q * 8 + e * 2;
+            const float k0 = kval<KER>(dist2(xr, xc[c]), P.sf2);
+            const float k1 = kval<KER>(dist2(xr, xc[c + 1]), P.sf2);
+            mean_acc = fmaf(k0, wc[c], mean_acc);
+            mean_acc = fmaf(k1, wc[c + 1], mean_acc);
+            pk[e] = pack_bf16(k0, k1);
+          }
+          const int chunk = (qt * (QCOLS / 8) + q) ^ (rl & 7);
+          *reinterpret_cast<uint4*>(arow + chunk * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
         }
-        const int chunk = (half * 4 + q) ^ (rl & 7);
-        *reinterpret_cast<uint4*>(arow + chunk * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&fullA[s]));
       }
-      fence_proxy_async();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&fullA[s]));
-    }
-    mean_part[half * BM + rl] = mean_acc;
-    asm volatile("bar.sync 1, %0;" ::"r"(NPROD_WARPS * 32) : "memory");
-    if (half == 0 && row < P.nr)
-      P.Out[(size_t)P.wtc * P.ldo + row] = mean_part[rl] + mean_part[BM + rl];
-    // ------------------------------------------------------------ epilogue: TMEM -> global
-    bool fin = mbar_wait(smem_u32(done), 0, abort_flag);
-    fin = __all_sync(0xffffffffu, fin && !*abort_flag);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (fin) {
-      const int nchunks = (P.npad + 31) / 32;   // TMEM holds >= 32 columns, so a 16-column tail is readable
-      for (int ch = half; ch < nchunks; ch += 2) {
-        uint32_t v[32];
-        const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(ch * 32);
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-              "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-              "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-              "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-            : "r"(taddr)
-            : "memory");
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (row < P.nr) {
+      // ---- end of this CTA's part of the tile: every producer warp arrives here, also on abort
+      float* mp = mean_part + (tcount & 1) * (NQ * BM);
+      mp[qt * BM + rl] = mean_acc;
+      ok = producers_all(ok && !*abort_flag);
+      if (!ok) break;
+      if (qt == 0 && row < P.nr) {
+        float m = mp[rl];
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int c = ch * 32 + j;
-            if (c < P.wtc) P.Out[(size_t)c * P.ldo + row] = __uint_as_float(v[j]);
+        for (int j = 1; j < NQ; ++j) m += mp[j * BM + rl];
+        float* dst = P.Out + (size_t)P.wtc * P.ldo + row;
+        if (split) atomicAdd(dst, m);
+        else *dst = m;
+      }
+      ok = mbar_wait(smem_u32(done), tcount & 1, abort_flag);
+      ok = __all_sync(0xffffffffu, ok);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (ok) {
+        const int nchunks = (P.npad + 31) / 32;   // TMEM holds >= 32 columns, so a 16-column tail is readable
+        for (int ch = qt; ch < nchunks; ch += NQ) {
+          uint32_t v[32];
+          const uint32_t taddr = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(ch * 32);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+              "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+              : "r"(taddr)
+              : "memory");
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          if (row < P.nr) {
+            float* o = P.Out + row;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int c = ch * 32 + j;
+              if (c < P.wtc) {
+                if (split) atomicAdd(o + (size_t)c * P.ldo, __uint_as_float(v[j]));
+                else o[(size_t)c * P.ldo] = __uint_as_float(v[j]);
+              }
+            }
           }
         }
       }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(tfree));
+      ++tcount;
+      ok = producers_all(ok);
+      if (!ok) break;
     }
   } else if (warp == TMA_WARP) {
     // ------------------------------------------------------------ TMA / bulk-copy producer
     if (lane == 0) {
-      int issued = 0;
-      for (int kt = 0; kt < P.nk; ++kt) {
-        const int s = kt % S;
-        const uint32_t n = kt / S;
+      long long issued = 0;
+      for (long long u = u0; u < u1; ++u) {
+        const long long it = u - u0;
+        const int s = (int)(it % S);
+        const uint32_t n = (uint32_t)(it / S);
+        const int kt = (int)(u % P.nk);
         if (!mbar_wait(smem_u32(&empty[s]), (n & 1) ^ 1, abort_flag)) break;
         const uint32_t cb = smem_u32(&fullC[s]);
         mbar_expect_tx(cb, BK * 16 + BK * 4);
@@ -263,11 +328,13 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmapB, const TcParams P) {
                       b * P.boxh, bb);
         ++issued;
       }
-      // on abort, let the copies already issued land before the CTA exits (bounded)
+      // on abort, let the copies possibly still in flight (the last S issued) land before exit
       if (*abort_flag) {
-        for (int kt = 0; kt < issued; ++kt) {
-          const int s = kt % S;
-          mbar_wait(smem_u32(&fullB[s]), (kt / S) & 1, abort_flag);
+        for (long long it = issued > S ? issued - S : 0; it < issued; ++it) {
+          const int s = (int)(it % S);
+          const uint32_t par = (uint32_t)(it / S) & 1;
+          mbar_drain(smem_u32(&fullB[s]), par);
+          mbar_drain(smem_u32(&fullC[s]), par);
         }
       }
     }
@@ -275,27 +342,43 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmapB, const TcParams P) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       bool ok = true;
-      for (int kt = 0; kt < P.nk && ok; ++kt) {
-        const int s = kt % S;
-        const uint32_t n = kt / S;
-        ok = mbar_wait(smem_u32(&fullA[s]), n & 1, abort_flag) && mbar_wait(smem_u32(&fullB[s]), n & 1, abort_flag);
-        if (!ok) break;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t a0 = smem_u32(A_base + (size_t)s * A_STAGE_BYTES);
-        const uint32_t b0 = smem_u32(B_base + (size_t)s * P.b_stage_bytes);
-        for (int c0 = 0; c0 < P.npad; c0 += 256) {
-          const int nn = min(256, P.npad - c0);
-          const uint32_t idesc = idesc_bf16(nn);
-#pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk) {
-            const uint64_t ad = sdesc_sw128(a0 + kk * 32);
-            const uint64_t bd = sdesc_sw128(b0 + (uint32_t)c0 * 128 + kk * 32);
-            mma_bf16(tmem + (uint32_t)c0, ad, bd, idesc, (kt > 0 || kk > 0) ? 1u : 0u);
-          }
+      long long u = u0;
+      int tcount = 0;
+      while (u < u1 && ok) {
+        const long long tend = (u / P.nk + 1) * P.nk;
+        const long long uend = u1 < tend ? u1 : tend;
+        if (tcount > 0) {   // the epilogue of the previous tile must have read the accumulator out
+          ok = mbar_wait(smem_u32(tfree), (tcount - 1) & 1, abort_flag);
+          if (!ok) break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         }
-        mma_commit(smem_u32(&empty[s]));
+        bool first = true;
+        for (; u < uend; ++u) {
+          const long long it = u - u0;
+          const int s = (int)(it % S);
+          const uint32_t n = (uint32_t)(it / S);
+          ok = mbar_wait(smem_u32(&fullA[s]), n & 1, abort_flag) && mbar_wait(smem_u32(&fullB[s]), n & 1, abort_flag);
+          if (!ok) break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t a0 = smem_u32(A_base + (size_t)s * A_STAGE_BYTES);
+          const uint32_t b0 = smem_u32(B_base + (size_t)s * P.b_stage_bytes);
+          for (int c0 = 0; c0 < P.npad; c0 += 256) {
+            const int nn = min(256, P.npad - c0);
+            const uint32_t idesc = idesc_bf16(nn);
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+              const uint64_t ad = sdesc_sw128(a0 + kk * 32);
+              const uint64_t bd = sdesc_sw128(b0 + (uint32_t)c0 * 128 + kk * 32);
+              mma_bf16(tmem + (uint32_t)c0, ad, bd, idesc, (first && kk == 0) ? 0u : 1u);
+            }
+          }
+          first = false;
+          mma_commit(smem_u32(&empty[s]));
+        }
+        if (!ok) break;
+        mma_commit(smem_u32(done));
+        ++tcount;
       }
-      mma_commit(smem_u32(done));
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -349,6 +432,20 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
+// Multiprocessor count of the current device (cached per device).
+int sm_count() {
+  static int cache[128] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 128) return 1;
+  if (!cache[dev]) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    cache[dev] = v > 0 ? v : 1;
+  }
+  return cache[dev];
+}
+
 struct Layout {
   int npad, nbox, boxh, stages, tmem_cols;
   uint32_t b_stage_bytes;
@@ -362,7 +459,7 @@ Layout plan_layout(int wtc) {
   L.nbox = (L.npad + L.boxh - 1) / L.boxh;
   L.b_stage_bytes = (uint32_t)L.nbox * L.boxh * 128;
   const size_t per_stage = A_STAGE_BYTES + L.b_stage_bytes + BK * 16 + BK * 4;
-  const size_t fixed = 1024 /*alignment slack*/ + 64 * 8 + 64 + 2 * BM * 4;
+  const size_t fixed = 1024 /*alignment slack*/ + 64 * 8 + 64 + 2 * NQ * BM * 4;
   const size_t budget = 220 * 1024;
   L.stages = (int)std::min<size_t>(4, (budget - fixed) / per_stage);
   L.tmem_cols = 32;
@@ -428,24 +525,31 @@ int gram_block_tc(int ker, int kind, const C4<float>* Xr, int nr, const C4<float
   if (cr != CUDA_SUCCESS) return 6;
 
   TcParams P;
-  P.Xr = Xr; P.nr = nr; P.Xc = xcp; P.wcol = wp; P.nk = ldp / BK; P.npad = L.npad; P.nbox = L.nbox; P.boxh = L.boxh;
-  P.wtc = wtc; P.sf2 = sf2; P.Out = Out; P.ldo = ldo; P.err = err; P.stages = L.stages; P.tmem_cols = L.tmem_cols;
-  P.b_stage_bytes = L.b_stage_bytes;
-  const dim3 grid((nr + BM - 1) / BM);
-  cudaError_t ce;
+  P.Xr = Xr; P.nr = nr; P.Xc = xcp; P.wcol = wp; P.nk = ldp / BK; P.ntiles = (nr + BM - 1) / BM; P.npad = L.npad;
+  P.nbox = L.nbox; P.boxh = L.boxh; P.wtc = wtc; P.sf2 = sf2; P.Out = Out; P.ldo = ldo; P.err = err;
+  P.stages = L.stages; P.tmem_cols = L.tmem_cols; P.b_stage_bytes = L.b_stage_bytes;
+
+  const void* fn = ker == 0 ? (const void*)k_gram_tc<0> : (ker == 1 ? (const void*)k_gram_tc<1> : (const void*)k_gram_tc<2>);
+  cudaError_t ce = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
+  if (ce != cudaSuccess) return 8;
+  int per_sm = 0;
+  ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NTHREADS, L.smem);
+  if (ce != cudaSuccess || per_sm < 1) return 9;
+  per_sm = std::min(per_sm, 512 / L.tmem_cols);   // every resident CTA holds tmem_cols TMEM columns
+  const long long slots = (long long)sm_count() * per_sm;
+  const int grid = (int)std::min<long long>(P.ntiles, slots);
+  // tiles shared by two CTAs are accumulated with atomic adds onto zeros
+  const long long total = (long long)P.ntiles * P.nk;
+  bool split = false;
+  for (int b = 1; b < grid && !split; ++b) split = (total * b / grid) % P.nk != 0;
+  if (split) {
+    ce = cudaMemset2DAsync(Out, (size_t)ldo * sizeof(float), 0, (size_t)nr * sizeof(float), (size_t)width, st);
+    if (ce != cudaSuccess) return 10;
+  }
   switch (ker) {
-    case 0:
-      cudaFuncSetAttribute(k_gram_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
-      k_gram_tc<0><<<grid, NTHREADS, L.smem, st>>>(map, P);
-      break;
-    case 1:
-      cudaFuncSetAttribute(k_gram_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
-      k_gram_tc<1><<<grid, NTHREADS, L.smem, st>>>(map, P);
-      break;
-    default:
-      cudaFuncSetAttribute(k_gram_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
-      k_gram_tc<2><<<grid, NTHREADS, L.smem, st>>>(map, P);
-      break;
+    case 0: k_gram_tc<0><<<grid, NTHREADS, L.smem, st>>>(map, P); break;
+    case 1: k_gram_tc<1><<<grid, NTHREADS, L.smem, st>>>(map, P); break;
+    default: k_gram_tc<2><<<grid, NTHREADS, L.smem, st>>>(map, P); break;
   }
   note_launch();
   ce = cudaGetLastError();

@@ -2,7 +2,8 @@
 
 Out = K(Xr, Xc) B with the Gram matrix never stored.  Sizes are ragged (rows not a multiple of the
 128-row tile, columns not a multiple of the 64-column slice) and widths cover one MMA chunk, two
-chunks and the 512-column TMEM limit.  Tolerances:
+chunks and the 512-column TMEM limit; one case has more row tiles than the GPU has SMs, so the
+persistent tensor-core grid splits tiles between CTAs.  Tolerances:
   FP64 SIMT   1e-12 relative (per column, normwise)
   FP32 SIMT   2e-5 relative
   BF16 tcgen05 columns 0..w-2: within 2e-4 of the exact product of the BF16-rounded operands
@@ -47,6 +48,7 @@ def case(nr, nc, width, dim, kernel, seed, lx=0.3, sf2=1.7):
 @pytest.mark.parametrize("nr,nc,width,dim,kernel", [
     (1000, 777, 2, 2, 1), (300, 257, 17, 3, 2), (513, 1000, 65, 1, 0), (257, 640, 257, 3, 1),
     (384, 300, 513, 2, 1), (130, 70, 100, 3, 2),
+    (19500, 1000, 129, 2, 1),   # 153 row tiles: the persistent grid shares tiles between CTAs
 ])
 def test_gram_matmul_all_precisions(nr, nc, width, dim, kernel):
     Xr, Xc, B, ref, ref_bf16, llx, lsf2 = case(nr, nc, width, dim, kernel, seed=nr + width)
