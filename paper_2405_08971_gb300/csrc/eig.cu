@@ -35,6 +35,31 @@ __device__ __forceinline__ double nr_rcp(double x) {
   return r;
 }
 
+// Grid barrier on a monotonic arrival counter (the kernel is launched cooperatively, all blocks
+// co-resident): barrier number b completes when the counter reaches (b + 1) * gridDim.x, so no
+// block has to reset anything and a waiting block needs one read to see the last arrival.  The
+// wait is bounded: after `limit` polls it raises *err (timeout) and returns false.
+__device__ __forceinline__ bool mono_barrier(unsigned* count, unsigned target, int* err,
+                                             long long limit = 50000000LL) {
+  __syncthreads();
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();
+    atomicAdd(count, 1u);
+    const volatile unsigned* vc = count;
+    long long spins = 0;
+    while (*vc < target) {
+      if (++spins > limit) { atomicExch(err, kErrTimeout); ok = 0; break; }
+      if ((spins & 1023) == 0 && *(volatile int*)err) { ok = 0; break; }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
 // ---------------------------------------------------------------------------------- tridiagonal
 // Householder tridiagonalisation (lower), one grid barrier per column.  Columns of the trailing
 // block are owned by (block, warp) round-robin.  At step k every block knows v_k, tau_k (computed
@@ -103,8 +128,9 @@ k_tridiag(double* __restrict__ A, int lda, int N, double* __restrict__ d, double
       if (j == 1) for (int t = lane; t < L; t += 32) Cbuf[t] = col[t];
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) d[0] = A[0];
-    if (!grid_barrier(bar, G, err)) return;
+    if (!mono_barrier(bar, (unsigned)G, err)) return;
   }
+  unsigned nbar = 1;
   for (int k = 0; k + 2 < N; ++k) {
     const int L = N - k - 1;
     const double* Pk = Pbuf + (size_t)(k & 1) * N;
@@ -164,7 +190,7 @@ k_tridiag(double* __restrict__ A, int lda, int N, double* __restrict__ d, double
     for (int t = threadIdx.x; t < L - 1; t += blockDim.x) v[t] = v2[t];
     tk = tn;
     bk = bn;
-    if (!grid_barrier(bar, G, err)) return;
+    if (!mono_barrier(bar, (unsigned)G * ++nbar, err)) return;
   }
 }
 
@@ -199,7 +225,8 @@ k_dc_prep(const MergeDesc* __restrict__ merges, const double* __restrict__ e, in
   double* sZr = psm + K;
   double* sD = psm + 2 * K;
   double* sZ = psm + 3 * K;
-  int* sPerm = reinterpret_cast<int*>(psm + 4 * K);
+  double* sRot = psm + 4 * K;          // up to K rotations: {last, j, c, s}
+  int* sPerm = reinterpret_cast<int*>(psm + 8 * K);
   int* sKeep = sPerm + K;
   int* sDefl = sKeep + K;
   const double rho0 = e[mid - 1];
@@ -232,15 +259,20 @@ k_dc_prep(const MergeDesc* __restrict__ merges, const double* __restrict__ e, in
     double dmax = 0.0;
     for (int t = 0; t < K; ++t) dmax = fmax(dmax, fabs(sD[t]));
     const double tol = 8.0 * kEps * fmax(dmax, rho);
-    // deflation scan: small z components, then pairs of close poles (Givens rotation)
+    // deflation scan: small z components, then pairs of close poles (Givens rotation).  The
+    // close-pole test |(D_j - D_l) c s| <= tol with c s = -z_l z_j / t^2 is evaluated without the
+    // division, as |D_j - D_l| |z_l z_j| <= tol t^2; c and s are formed only for a rotation.
     int kp = 0, nd = 0, nrot = 0, last = -1;
     for (int j = 0; j < K; ++j) {
-      if (rho * fabs(sZ[j]) <= tol) { sDefl[nd++] = j; continue; }
+      const double zj = sZ[j];
+      if (rho * fabs(zj) <= tol) { sDefl[nd++] = j; continue; }
       if (last >= 0) {
-        const double t = hypot(sZ[last], sZ[j]);
-        const double c = sZ[j] / t, sn = -sZ[last] / t;
-        if (fabs((sD[j] - sD[last]) * c * sn) <= tol) {
-          double* rr = W.rot + 4 * (size_t)(lo + nrot);
+        const double zl = sZ[last];
+        const double t2 = fma(zl, zl, zj * zj);
+        if (fabs(sD[j] - sD[last]) * fabs(zl * zj) <= tol * t2) {
+          const double t = sqrt(t2);
+          const double c = zj / t, sn = -zl / t;
+          double* rr = sRot + 4 * nrot;
           rr[0] = last; rr[1] = j; rr[2] = c; rr[3] = sn;
           ++nrot;
           const double dl = sD[last], dj = sD[j];
@@ -284,17 +316,43 @@ k_dc_prep(const MergeDesc* __restrict__ merges, const double* __restrict__ e, in
     W.cold[lo + t] = lo + sPerm[sDefl[t]];
   }
   __syncthreads();
-  // apply the deflation rotations to the (permuted) child eigenvector columns, rows lo..hi
+  // apply the deflation rotations to the (permuted) child eigenvector columns, rows lo..hi.
+  // Rotation q acts on (a_q, b_q) with b_q a column no earlier rotation touched, and a_q either
+  // untouched as well or equal to b_{q-1}; so each group of RG rotations loads its operands up
+  // front (independent loads), and the a_q = b_{q-1} chain is carried in a register.
+  constexpr int RG = 8;
   for (int row = threadIdx.x; row < K; row += blockDim.x) {
-    for (int q = 0; q < nrot; ++q) {
-      const double* rr = W.rot + 4 * (size_t)(lo + q);
-      const int ca = lo + sPerm[(int)rr[0]], cb = lo + sPerm[(int)rr[1]];
-      double* qa = W.Q + (size_t)ca * N + lo + row;
-      double* qb = W.Q + (size_t)cb * N + lo + row;
-      const double c = rr[2], sn = rr[3];
-      const double xa = *qa, xb = *qb;
-      *qa = c * xa + sn * xb;
-      *qb = -sn * xa + c * xb;
+    double* qrow = W.Q + lo + row;
+    double carry = 0.0;
+    int carry_col = -1;
+    for (int q0 = 0; q0 < nrot; q0 += RG) {
+      const int nq = min(RG, nrot - q0);
+      int ca[RG], cb[RG];
+      double xa[RG], xb[RG];
+#pragma unroll
+      for (int u = 0; u < RG; ++u) {
+        if (u >= nq) break;
+        const double* rr = sRot + 4 * (q0 + u);
+        ca[u] = lo + sPerm[(int)rr[0]];
+        cb[u] = lo + sPerm[(int)rr[1]];
+        const int prev = (u == 0) ? carry_col : cb[u - 1];
+        xb[u] = qrow[(size_t)cb[u] * N];
+        xa[u] = (ca[u] == prev) ? 0.0 : qrow[(size_t)ca[u] * N];
+      }
+#pragma unroll
+      for (int u = 0; u < RG; ++u) {
+        if (u >= nq) break;
+        const double* rr = sRot + 4 * (q0 + u);
+        const double c = rr[2], sn = rr[3];
+        const int prev = (u == 0) ? carry_col : cb[u - 1];
+        const double a = (ca[u] == prev) ? carry : xa[u];
+        const double na = c * a + sn * xb[u];
+        const double nb = -sn * a + c * xb[u];
+        qrow[(size_t)ca[u] * N] = na;
+        qrow[(size_t)cb[u] * N] = nb;
+        carry = nb;
+        carry_col = cb[u];
+      }
     }
   }
 }
@@ -478,43 +536,71 @@ k_dc_gemm(const MergeDesc* __restrict__ merges, int N, DcWork W) {
     }
 }
 
-// Phase 6: order the merged spectrum ascending and move columns back into Q.
+// Order-preserving integer key of a double (IEEE bit pattern; negative values mirrored), so the
+// sorting below compares on the integer units instead of the FP64 pipe.
+__device__ __forceinline__ long long order_key(double x) {
+  const long long b = __double_as_longlong(x);
+  return b >= 0 ? b : (b ^ 0x7FFFFFFFFFFFFFFFLL);
+}
+
+// Phase 6a: order the merged spectrum ascending (one block per merge): W.lam and the column
+// permutation W.perm (relative to lo) for phase 6b.
 __global__ void __launch_bounds__(256)
 k_dc_finish(const MergeDesc* __restrict__ merges, int N, DcWork W) {
   extern __shared__ double fsm[];
   const MergeDesc mg = merges[blockIdx.x];
   const int lo = mg.lo, K = mg.hi - mg.lo;
   const int Kp = W.Kp[lo];
-  double* sl = fsm;                                   // K merged eigenvalues (kept roots, deflated poles)
-  int* perm = reinterpret_cast<int*>(fsm + K);
+  double* sl = fsm;                                          // K merged eigenvalues (kept roots, deflated poles)
+  long long* key = reinterpret_cast<long long*>(fsm + K);
+  int* perm = reinterpret_cast<int*>(fsm + 2 * K);
   int* dp = perm + K;
-  for (int t = threadIdx.x; t < K; t += blockDim.x) sl[t] = (t < Kp) ? W.lamk[lo + t] : W.Dd[lo + t - Kp];
+  for (int t = threadIdx.x; t < K; t += blockDim.x) {
+    const double v = (t < Kp) ? W.lamk[lo + t] : W.Dd[lo + t - Kp];
+    sl[t] = v;
+    key[t] = order_key(v);
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     // kept roots are ascending; sort the (nearly ascending) deflated poles, then merge the two lists
     const int Kd = K - Kp;
     for (int t = 0; t < Kd; ++t) dp[t] = Kp + t;
     for (int a = 1; a < Kd; ++a) {
-      const int key = dp[a];
-      const double kv = sl[key];
+      const int kidx = dp[a];
+      const long long kv = key[kidx];
       int b = a - 1;
-      while (b >= 0 && sl[dp[b]] > kv) { dp[b + 1] = dp[b]; --b; }
-      dp[b + 1] = key;
+      while (b >= 0 && key[dp[b]] > kv) { dp[b + 1] = dp[b]; --b; }
+      dp[b + 1] = kidx;
     }
     int x = 0, y = 0;
     for (int t = 0; t < K; ++t) {
       int pick;
       if (x >= Kp) pick = dp[y++];
       else if (y >= Kd) pick = x++;
-      else pick = (sl[x] <= sl[dp[y]]) ? x++ : dp[y++];
+      else pick = (key[x] <= key[dp[y]]) ? x++ : dp[y++];
       perm[t] = pick;
     }
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < K; t += blockDim.x) W.lam[lo + t] = sl[perm[t]];
-  for (int e2 = threadIdx.x; e2 < K * K; e2 += blockDim.x) {
-    const int row = e2 % K, c = e2 / K;
-    W.Q[(size_t)(lo + c) * N + lo + row] = W.Qtmp[(size_t)(lo + perm[c]) * N + lo + row];
+  for (int t = threadIdx.x; t < K; t += blockDim.x) {
+    W.lam[lo + t] = sl[perm[t]];
+    W.perm[lo + t] = perm[t];
+  }
+}
+
+// Phase 6b: move the merged eigenvector columns back into Q in ascending order
+// (grid: column groups of 8 x merges).
+__global__ void __launch_bounds__(256)
+k_dc_copy(const MergeDesc* __restrict__ merges, int N, DcWork W) {
+  const MergeDesc mg = merges[blockIdx.y];
+  const int lo = mg.lo, K = mg.hi - mg.lo;
+  const int c0 = blockIdx.x * 8;
+  if (c0 >= K) return;
+  const int c1 = min(K, c0 + 8);
+  for (int c = c0; c < c1; ++c) {
+    const double* src = W.Qtmp + (size_t)(lo + W.perm[lo + c]) * N + lo;
+    double* dst = W.Q + (size_t)(lo + c) * N + lo;
+    for (int row = threadIdx.x; row < K; row += blockDim.x) dst[row] = src[row];
   }
 }
 
@@ -679,7 +765,7 @@ int eig_sym_topk(double* A, int lda, int N, int nkeep, double* w, T* U, int ldu,
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    int G = N >= 3 ? std::max(1, std::min(nsm, (N + 7) / 8)) : 1;
+    int G = N >= 3 ? std::max(1, std::min(nsm, (N + 3) / 4)) : 1;
     cudaFuncSetAttribute(k_tridiag, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     size_t smem = 0;
     for (int attempt = 0; attempt < 8; ++attempt) {
@@ -709,7 +795,7 @@ int eig_sym_topk(double* A, int lda, int N, int nkeep, double* w, T* U, int ldu,
     const int* dmo = pe->d_mergeof + (size_t)lv * N;
     int kmax = 0;
     for (int q = m0; q < m1; ++q) kmax = std::max(kmax, pl.merges[q].hi - pl.merges[q].lo);
-    const size_t psmem = (size_t)kmax * (4 * sizeof(double) + 3 * sizeof(int));
+    const size_t psmem = (size_t)kmax * (8 * sizeof(double) + 3 * sizeof(int));
     if (psmem > 48 * 1024) cudaFuncSetAttribute(k_dc_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
     k_dc_prep<<<nm, 256, psmem, st>>>(dm, e, N, W); note_launch();
     k_dc_secular<<<(N * 32 + 255) / 256, 256, 0, st>>>(dm, dmo, N, W, err); note_launch();
@@ -717,13 +803,14 @@ int eig_sym_topk(double* A, int lda, int N, int nkeep, double* w, T* U, int ldu,
     k_dc_vecs<<<(N * 32 + 255) / 256, 256, 0, st>>>(dm, dmo, N, W); note_launch();
     dim3 gg((kmax + DG_T - 1) / DG_T, (kmax + DG_T - 1) / DG_T, nm);
     k_dc_gemm<<<gg, 256, 0, st>>>(dm, N, W); note_launch();
-    const size_t fsmem = (size_t)kmax * (sizeof(double) + 2 * sizeof(int));
+    const size_t fsmem = (size_t)kmax * (2 * sizeof(double) + 2 * sizeof(int));
     if (fsmem > 48 * 1024) cudaFuncSetAttribute(k_dc_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
     k_dc_finish<<<nm, 256, fsmem, st>>>(dm, N, W); note_launch();
+    k_dc_copy<<<dim3((kmax + 7) / 8, nm), 256, 0, st>>>(dm, N, W); note_launch();
   }
   // 3. back-transformation of the top nkeep columns (descending eigenvalues)
   {
-    const int wpb = 4;
+    const int wpb = 2;   // 2 warps (columns) per block: the blocks spread over all SMs' FP64 units
     size_t smem = (size_t)wpb * N * sizeof(double);
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_backtransform<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_backtransform<T><<<(nkeep + wpb - 1) / wpb, 32 * wpb, smem, st>>>(A, lda, tau, N, W.Q, W.lam, nkeep, w, U, ldu); note_launch();

@@ -24,7 +24,6 @@ constexpr int BM = 128;          // rows per CTA (TMEM lanes)
 constexpr int BK = 64;           // kernel columns per pipeline stage (64 bf16 = one 128B swizzle row)
 constexpr int NPROD_WARPS = 16;  // kernel-tile producers (and epilogue)
 constexpr int NQ = NPROD_WARPS / 4;   // producer warps per TMEM lane group: each takes BK / NQ columns
-constexpr int QCOLS = BK / NQ;        // kernel-tile columns per producer thread and slice
 constexpr int TMA_WARP = NPROD_WARPS;
 constexpr int MMA_WARP = NPROD_WARPS + 1;   // the remaining warp issues the MMAs
 constexpr int NTHREADS = (NPROD_WARPS + 2) * 32;
@@ -108,10 +107,71 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return *reinterpret_cast<uint32_t*>(&v);
 }
 
+// ---- packed FP32 pairs (two columns of one row): f32x2 arithmetic on 64-bit registers
+__device__ __forceinline__ uint64_t f2_make(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2_split(uint64_t v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+__device__ __forceinline__ float f2_sum(uint64_t v) {
+  float lo, hi;
+  f2_split(v, lo, hi);
+  return lo + hi;
+}
+__device__ __forceinline__ uint32_t f2_bf16(uint64_t v) {
+  float lo, hi;
+  f2_split(v, lo, hi);
+  return pack_bf16(lo, hi);
+}
+
+// Matern correlation (without sf2) of one row against a column pair.  Coordinates are pre-scaled
+// by c_nu / l_x, so with s the Euclidean distance:  nu=1/2: e^-s,  nu=3/2: (1+s) e^-s,
+// nu=5/2: (1 + s + s^2/3) e^-s.  sqrt and exp2 run on the MUFU unit (approximate, ftz).
+template <int KER>
+__device__ __forceinline__ uint64_t kpair(uint64_t rx, uint64_t ry, uint64_t rz, uint64_t cx, uint64_t cy,
+                                          uint64_t cz) {
+  const uint64_t dx = f2_sub(rx, cx), dy = f2_sub(ry, cy), dz = f2_sub(rz, cz);
+  uint64_t d2 = f2_mul(dz, dz);
+  d2 = f2_fma(dy, dy, d2);
+  d2 = f2_fma(dx, dx, d2);
+  float a, b;
+  f2_split(d2, a, b);
+  const uint64_t sd = f2_make(approx_sqrt(a), approx_sqrt(b));
+  const uint64_t t = f2_mul(sd, f2_make(-1.4426950408889634f, -1.4426950408889634f));
+  f2_split(t, a, b);
+  float ea, eb;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(ea) : "f"(a));
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(eb) : "f"(b));
+  const uint64_t e = f2_make(ea, eb);
+  if (KER == 0) return e;
+  if (KER == 1) return f2_fma(sd, e, e);
+  const uint64_t p = f2_mul(f2_fma(sd, f2_make(0.33333333333333333f, 0.33333333333333333f),
+                                   f2_make(1.0f, 1.0f)), sd);
+  return f2_fma(p, e, e);
+}
+
 struct TcParams {
   const C4<float>* Xr;
   int nr;
-  const C4<float>* Xc;     // padded to nk * BK entries (sentinel coordinates beyond nc)
+  const C4<float>* Xc;     // nk * BK columns in pair layout (see k_pad_coords), sentinels beyond nc
   const float* wcol;       // padded mean column (zeros beyond nc), FP32
   int nk;                  // number of K slices per row tile
   int ntiles;              // row tiles of BM rows
@@ -176,7 +236,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmapB, const TcParams P) {
   uint64_t* tfree = bars + 4 * S + 1;      // epilogue -> MMA: the accumulator has been read out
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 4 * S + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
-  float* mean_part = reinterpret_cast<float*>(tmem_holder + 4);     // [2][NQ][BM]
+  float* mean_part = reinterpret_cast<float*>(tmem_holder + 4);     // [2][8][BM]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long total = (long long)P.ntiles * P.nk;
@@ -207,9 +267,15 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmapB, const TcParams P) {
 
   if (warp < NPROD_WARPS) {
     // ------------------------------------------------------------ kernel-tile producers + epilogue
+    // Producer role: warp w computes rows {rh*32 + lane, rh*32 + lane + 64} (rh = w & 1) for the
+    // 8-column chunk c8 = w >> 1 of every slice, two columns at a time in packed f32x2 arithmetic.
+    // Epilogue role: warp w reads TMEM lanes 32*(w & 3).. (the lane group it may access) for the
+    // column chunks qt, qt + NQ, ... (qt = w >> 2).
+    const int rh = warp & 1, c8 = warp >> 1;
     const int lg = warp & 3;                        // TMEM lane group of this warp
-    const int qt = warp >> 2;                       // which NQ-th of the slice columns
-    const int rl = lg * 32 + lane;                  // row within the tile (= TMEM lane)
+    const int qt = warp >> 2;                       // which NQ-th of the 32-column epilogue chunks
+    const int rl = lg * 32 + lane;                  // epilogue row within the tile (= TMEM lane)
+    const int pr0 = rh * 32 + lane, pr1 = pr0 + 64; // producer rows within the tile
     long long u = u0;
     int tcount = 0;
     bool ok = true;
@@ -219,51 +285,59 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmapB, const TcParams P) {
       const long long uend = u1 < tend ? u1 : tend;
       const bool split = (u != tbeg) || (uend != tend);
       const int row = tile * BM + rl;
-      C4<float> xr;
-      if (row < P.nr) xr = P.Xr[row];
-      else { xr.x = xr.y = xr.z = 1.0e6f; xr.w = 0.f; }
-      float mean_acc = 0.f;
+      uint64_t rx0, ry0, rz0, rx1, ry1, rz1;        // the two producer rows' coordinates, duplicated
+      {
+        C4<float> x0, x1;
+        const int g0 = tile * BM + pr0, g1 = tile * BM + pr1;
+        if (g0 < P.nr) x0 = P.Xr[g0]; else { x0.x = x0.y = x0.z = 1.0e6f; x0.w = 0.f; }
+        if (g1 < P.nr) x1 = P.Xr[g1]; else { x1.x = x1.y = x1.z = 1.0e6f; x1.w = 0.f; }
+        rx0 = f2_make(x0.x, x0.x); ry0 = f2_make(x0.y, x0.y); rz0 = f2_make(x0.z, x0.z);
+        rx1 = f2_make(x1.x, x1.x); ry1 = f2_make(x1.y, x1.y); rz1 = f2_make(x1.z, x1.z);
+      }
+      uint64_t macc0 = 0ull, macc1 = 0ull;          // (even, odd column) partial means, FP32 pairs
       for (; u < uend; ++u) {
         const long long it = u - u0;
         const int s = (int)(it % S);
         const uint32_t n = (uint32_t)(it / S);
-        ok = mbar_wait(smem_u32(&empty[s]), (n & 1) ^ 1, abort_flag);
-        ok = __all_sync(0xffffffffu, ok);
-        if (!ok) break;
+        // fullC completes only after the TMA warp saw empty[s] (the MMAs of this stage's previous
+        // use are done) and its copies landed, so it also releases the A stage to the producers.
         ok = mbar_wait(smem_u32(&fullC[s]), n & 1, abort_flag);
         ok = __all_sync(0xffffffffu, ok);
         if (!ok) break;
-        const C4<float>* xc = reinterpret_cast<const C4<float>*>(C_base + (size_t)s * BK * 16) + qt * QCOLS;
-        const float* wc = reinterpret_cast<const float*>(W_base + (size_t)s * BK * 4) + qt * QCOLS;
-        uint8_t* arow = A_base + (size_t)s * A_STAGE_BYTES + rl * 128;
+        const uint8_t* cp = C_base + (size_t)s * BK * 16 + (size_t)c8 * 4 * 32;   // 4 column pairs
+        const float* wc = reinterpret_cast<const float*>(W_base + (size_t)s * BK * 4) + c8 * 8;
+        uint32_t pk0[4], pk1[4];
 #pragma unroll
-        for (int q = 0; q < QCOLS / 8; ++q) {
-          uint32_t pk[4];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int c = q * 8 + e * 2;
-            const float k0 = kval<KER>(dist2(xr, xc[c]), P.sf2);
-            const float k1 = kval<KER>(dist2(xr, xc[c + 1]), P.sf2);
-            mean_acc = fmaf(k0, wc[c], mean_acc);
-            mean_acc = fmaf(k1, wc[c + 1], mean_acc);
-            pk[e] = pack_bf16(k0, k1);
-          }
-          const int chunk = (qt * (QCOLS / 8) + q) ^ (rl & 7);
-          *reinterpret_cast<uint4*>(arow + chunk * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        for (int q = 0; q < 4; ++q) {
+          const ulonglong2 xy = *reinterpret_cast<const ulonglong2*>(cp + q * 32);
+          const uint64_t cz = *reinterpret_cast<const uint64_t*>(cp + q * 32 + 16);
+          const uint64_t w2 = *reinterpret_cast<const uint64_t*>(wc + 2 * q);
+          const uint64_t k0 = kpair<KER>(rx0, ry0, rz0, xy.x, xy.y, cz);
+          const uint64_t k1 = kpair<KER>(rx1, ry1, rz1, xy.x, xy.y, cz);
+          macc0 = f2_fma(k0, w2, macc0);
+          macc1 = f2_fma(k1, w2, macc1);
+          pk0[q] = f2_bf16(k0);
+          pk1[q] = f2_bf16(k1);
         }
+        uint8_t* ast = A_base + (size_t)s * A_STAGE_BYTES;
+        const int chunk = c8 ^ (pr0 & 7);           // pr1 = pr0 + 64 has the same swizzle phase
+        *reinterpret_cast<uint4*>(ast + pr0 * 128 + chunk * 16) = make_uint4(pk0[0], pk0[1], pk0[2], pk0[3]);
+        *reinterpret_cast<uint4*>(ast + pr1 * 128 + chunk * 16) = make_uint4(pk1[0], pk1[1], pk1[2], pk1[3]);
         fence_proxy_async();
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&fullA[s]));
       }
       // ---- end of this CTA's part of the tile: every producer warp arrives here, also on abort
-      float* mp = mean_part + (tcount & 1) * (NQ * BM);
-      mp[qt * BM + rl] = mean_acc;
+      float* mp = mean_part + (tcount & 1) * (8 * BM);
+      mp[c8 * BM + pr0] = f2_sum(macc0);
+      mp[c8 * BM + pr1] = f2_sum(macc1);
       ok = producers_all(ok && !*abort_flag);
       if (!ok) break;
       if (qt == 0 && row < P.nr) {
         float m = mp[rl];
 #pragma unroll
-        for (int j = 1; j < NQ; ++j) m += mp[j * BM + rl];
+        for (int j = 1; j < 8; ++j) m += mp[j * BM + rl];
+        m *= P.sf2;
         float* dst = P.Out + (size_t)P.wtc * P.ldo + row;
         if (split) atomicAdd(dst, m);
         else *dst = m;
@@ -293,8 +367,9 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmapB, const TcParams P) {
             for (int j = 0; j < 32; ++j) {
               const int c = ch * 32 + j;
               if (c < P.wtc) {
-                if (split) atomicAdd(o + (size_t)c * P.ldo, __uint_as_float(v[j]));
-                else o[(size_t)c * P.ldo] = __uint_as_float(v[j]);
+                const float val = P.sf2 * __uint_as_float(v[j]);
+                if (split) atomicAdd(o + (size_t)c * P.ldo, val);
+                else o[(size_t)c * P.ldo] = val;
               }
             }
           }
@@ -407,13 +482,19 @@ __global__ void k_pack_b(const float* __restrict__ B, int ldb, int rows, int wtc
   }
 }
 
-__global__ void k_pad_coords(const C4<float>* __restrict__ X, int n, int ldp, C4<float>* __restrict__ Xp) {
+// Xp holds the columns' coordinates in pairs: for columns 2p, 2p + 1 the 8 floats
+// {x0, x1, y0, y1, z0, z1, 0, 0} (32 bytes), the layout the producers read as f32x2 operands.
+__global__ void k_pad_coords(const C4<float>* __restrict__ X, int n, int ldp, float* __restrict__ Xp) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ldp) return;
   C4<float> c;
   if (i < n) c = X[i];
   else { c.x = c.y = c.z = 1.0e6f; c.w = 0.f; }
-  Xp[i] = c;
+  float* o = Xp + (size_t)(i >> 1) * 8 + (i & 1);
+  o[0] = c.x;
+  o[2] = c.y;
+  o[4] = c.z;
+  o[6] = 0.f;
 }
 
 // ---------------------------------------------------------------------------- host side
@@ -459,7 +540,7 @@ Layout plan_layout(int wtc) {
   L.nbox = (L.npad + L.boxh - 1) / L.boxh;
   L.b_stage_bytes = (uint32_t)L.nbox * L.boxh * 128;
   const size_t per_stage = A_STAGE_BYTES + L.b_stage_bytes + BK * 16 + BK * 4;
-  const size_t fixed = 1024 /*alignment slack*/ + 64 * 8 + 64 + 2 * NQ * BM * 4;
+  const size_t fixed = 1024 /*alignment slack*/ + 64 * 8 + 64 + 2 * 8 * BM * 4;
   const size_t budget = 220 * 1024;
   L.stages = (int)std::min<size_t>(4, (budget - fixed) / per_stage);
   L.tmem_cols = 32;
@@ -511,7 +592,7 @@ int gram_block_tc(int ker, int kind, const C4<float>* Xr, int nr, const C4<float
   const size_t boff = (((size_t)L.npad * ldp * 2 + 255) & ~size_t(255));
   const float* wp = reinterpret_cast<const float*>(base + boff);
   C4<float>* xcp = reinterpret_cast<C4<float>*>(const_cast<char*>(base) + boff + (((size_t)ldp * 4 + 255) & ~size_t(255)));
-  k_pad_coords<<<(ldp + 255) / 256, 256, 0, st>>>(Xc, nc, ldp, xcp);
+  k_pad_coords<<<(ldp + 255) / 256, 256, 0, st>>>(Xc, nc, ldp, reinterpret_cast<float*>(xcp));
   note_launch();
 
   CUtensorMap map;

@@ -72,37 +72,58 @@ k_gram_matvec(const C4<T>* __restrict__ Xo, const T* __restrict__ s, int m, int 
   if (row < m) part[(size_t)blockIdx.y * m + row] = acc;
 }
 
-// g = sum_p part[p] + sn2 * s - a2 * Mo t     (Mo: m x r col-major, ld = ldm); t is summed from the
-// row-chunk partials of k_gemv_t (tz chunks) into shared memory first.
+// g = sum_p part[p] + sn2 * s - a2 * Mo t     (Mo: m x r col-major, ld = ldm).  t is summed from
+// the row-chunk partials of k_gemv_t (tz chunks) into shared memory first.  A block owns CB_ROWS
+// rows: lane = row, each of the CB_WARPS warps takes every CB_WARPS-th column of Mo (coalesced
+// 128-byte column segments, CB_UNROLL independent accumulators), and the warps' sums are added
+// in shared memory.
+constexpr int CB_ROWS = 32, CB_WARPS = 8, CB_UNROLL = 8;
 template <class T>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(CB_WARPS * 32)
 k_cg_combine(const T* __restrict__ part, int nsplit, const T* __restrict__ s, T sn2,
              const T* __restrict__ Mo, int ldm, int r, const T* __restrict__ tpart, int tz, T a2,
              int m, T* __restrict__ g, const int* __restrict__ active) {
   if (!*active) return;
   extern __shared__ unsigned char sm_raw[];
-  T* t = reinterpret_cast<T*>(sm_raw);
+  T* t = reinterpret_cast<T*>(sm_raw);                 // r coefficients
+  __shared__ T red[CB_WARPS][CB_ROWS];
   for (int l = threadIdx.x; l < r; l += blockDim.x) {
     T acc = T(0);
     for (int z = 0; z < tz; ++z) acc += tpart[(size_t)z * r + l];
     t[l] = acc;
   }
   __syncthreads();
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m) return;
-  T acc = T(0);
-  for (int p = 0; p < nsplit; ++p) acc += part[(size_t)p * m + i];
-  acc = fma(sn2, s[i], acc);
-  T lr0 = T(0), lr1 = T(0), lr2 = T(0), lr3 = T(0);
-  int l = 0;
-  for (; l + 3 < r; l += 4) {
-    lr0 = fma(Mo[(size_t)l * ldm + i], t[l], lr0);
-    lr1 = fma(Mo[(size_t)(l + 1) * ldm + i], t[l + 1], lr1);
-    lr2 = fma(Mo[(size_t)(l + 2) * ldm + i], t[l + 2], lr2);
-    lr3 = fma(Mo[(size_t)(l + 3) * ldm + i], t[l + 3], lr3);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * CB_ROWS + lane;
+  const bool valid = i < m;
+  T acc[CB_UNROLL];
+#pragma unroll
+  for (int u = 0; u < CB_UNROLL; ++u) acc[u] = T(0);
+  if (valid) {
+    int l = warp;
+    for (; l + (CB_UNROLL - 1) * CB_WARPS < r; l += CB_UNROLL * CB_WARPS) {
+#pragma unroll
+      for (int u = 0; u < CB_UNROLL; ++u) {
+        const int lu = l + u * CB_WARPS;
+        acc[u] = fma(Mo[(size_t)lu * ldm + i], t[lu], acc[u]);
+      }
+    }
+    for (; l < r; l += CB_WARPS) acc[0] = fma(Mo[(size_t)l * ldm + i], t[l], acc[0]);
   }
-  for (; l < r; ++l) lr0 = fma(Mo[(size_t)l * ldm + i], t[l], lr0);
-  g[i] = fma(-a2, (lr0 + lr1) + (lr2 + lr3), acc);
+  T lr = T(0);
+#pragma unroll
+  for (int u = 0; u < CB_UNROLL; ++u) lr += acc[u];
+  red[warp][lane] = lr;
+  __syncthreads();
+  if (warp == 0 && valid) {
+    T low = T(0);
+#pragma unroll
+    for (int w = 0; w < CB_WARPS; ++w) low += red[w][lane];
+    T kv = T(0);
+    for (int p = 0; p < nsplit; ++p) kv += part[(size_t)p * m + i];
+    kv = fma(sn2, s[i], kv);
+    g[i] = fma(-a2, low, kv);
+  }
 }
 
 // Partial transposed products: part[z][l] = sum_{i in row chunk z} A[i, l] x[i]  (A: rows x cols col-major).
@@ -124,6 +145,29 @@ __global__ void k_gemv_t(const T* __restrict__ A, int lda, int rows, int cols, c
   if (lane == 0) part[(size_t)z * cols + warp] = acc;
 }
 
+// Per-thread share of a block-wide dot product a . b over m entries (strided by blockDim.x).
+// FP32 data: four FP32 FMA chains combined in FP64, so the FP64 pipe (slow on this GPU) sees a
+// handful of operations per thread; FP64 data: FP64 throughout.
+template <class T> __device__ __forceinline__ double dot_part(const T* __restrict__ a, const T* __restrict__ b, int m) {
+  const int st = blockDim.x;
+  int i = threadIdx.x;
+  if constexpr (sizeof(T) == 8) {
+    double acc = 0.0;
+    for (; i < m; i += st) acc = fma(a[i], b[i], acc);
+    return acc;
+  } else {
+    float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+    for (; i + 3 * st < m; i += 4 * st) {
+      p0 = fmaf(a[i], b[i], p0);
+      p1 = fmaf(a[i + st], b[i + st], p1);
+      p2 = fmaf(a[i + 2 * st], b[i + 2 * st], p2);
+      p3 = fmaf(a[i + 3 * st], b[i + 3 * st], p3);
+    }
+    for (; i < m; i += st) p0 = fmaf(a[i], b[i], p0);
+    return (double(p0) + double(p1)) + (double(p2) + double(p3));
+  }
+}
+
 // First dot pass of CG iteration j (one block per dot):
 //   q < j: V[:, q] . g ;  j: s . g ;  j+1: s . r0 ;  j+2: g . v ;  j+3: s . s
 template <class T>
@@ -138,9 +182,7 @@ __global__ void k_cg_dots1(const T* __restrict__ V, int ldv, int j, const T* __r
   else if (q == j + 1) { a = s; b = r0; }
   else if (q == j + 2) { a = g; b = v; }
   else { a = s; b = s; }
-  double acc = 0.0;
-  for (int i = threadIdx.x; i < m; i += blockDim.x) acc += double(a[i]) * double(b[i]);
-  acc = block_sum(acc);
+  const double acc = block_sum(dot_part(a, b, m));
   if (threadIdx.x == 0) dots[q] = acc;
 }
 
@@ -150,14 +192,14 @@ template <class T>
 __global__ void k_cg_upd1(int j, const double* __restrict__ dots, T* __restrict__ V, T* __restrict__ GV, int ldv,
                           const T* __restrict__ s, const T* __restrict__ g, int m, const int* __restrict__ active) {
   if (!*active) return;
-  __shared__ double c[1024];
-  for (int q = threadIdx.x; q < j; q += blockDim.x) c[q] = dots[q];
+  __shared__ T c[1024];
+  for (int q = threadIdx.x; q < j; q += blockDim.x) c[q] = T(dots[q]);
   __syncthreads();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m) return;
   T d = s[i], gd = g[i];
   for (int q = 0; q < j; ++q) {
-    T cq = T(c[q]);
+    const T cq = c[q];
     d = fma(-V[(size_t)q * ldv + i], cq, d);
     gd = fma(-GV[(size_t)q * ldv + i], cq, gd);
   }
@@ -173,9 +215,7 @@ __global__ void k_cg_dots2(const T* __restrict__ V, const T* __restrict__ GV, in
   const int q = blockIdx.x;
   const T* gd = GV + (size_t)j * ldv;
   const T* a = V + (size_t)q * ldv;     // q == j: d itself
-  double acc = 0.0;
-  for (int i = threadIdx.x; i < m; i += blockDim.x) acc += double(a[i]) * double(gd[i]);
-  acc = block_sum(acc);
+  const double acc = block_sum(dot_part(a, gd, m));
   if (threadIdx.x == 0) dots[q] = acc;
 }
 
@@ -190,13 +230,13 @@ __global__ void k_cg_upd2(int j, const double* __restrict__ dots1, const double*
                           double bd_tol, double rtol2_r0sq, int use_rtol, int* __restrict__ active,
                           double* __restrict__ eta_out, double* __restrict__ alpha_out, int* __restrict__ count) {
   if (!*active) return;
-  __shared__ double c[1024];
+  __shared__ T c[1024];
   __shared__ double sh[3];
-  for (int q = threadIdx.x; q < j; q += blockDim.x) c[q] = dots2[q];
-  __syncthreads();
+  for (int q = threadIdx.x; q < j; q += blockDim.x) c[q] = T(dots2[q]);
+  double ccp = 0.0;
+  for (int q = threadIdx.x; q < j; q += blockDim.x) ccp = fma(dots2[q], dots2[q], ccp);
+  const double cc = block_sum(ccp);
   if (threadIdx.x == 0) {
-    double cc = 0.0;
-    for (int q = 0; q < j; ++q) cc += c[q] * c[q];
     const double sg = dots1[j];
     const double eta = dots2[j] - cc;
     const double alpha = dots1[j + 1] - dots1[j + 2];
@@ -216,7 +256,7 @@ __global__ void k_cg_upd2(int j, const double* __restrict__ dots1, const double*
   if (i < m) {
     T d = V[(size_t)j * ldv + i], gd = GV[(size_t)j * ldv + i];
     for (int q = 0; q < j; ++q) {
-      T cq = T(c[q]);
+      const T cq = c[q];
       d = fma(-V[(size_t)q * ldv + i], cq, d);
       gd = fma(-GV[(size_t)q * ldv + i], cq, gd);
     }
@@ -239,9 +279,7 @@ __global__ void k_cg_qdots(const T* __restrict__ Q, int ldq, int j, const T* __r
   if (!*active) return;
   const int l = blockIdx.x;
   const T* a = Q + (size_t)l * ldq;
-  double acc = 0.0;
-  for (int i = threadIdx.x; i < m; i += blockDim.x) acc += double(a[i]) * double(s[i]);
-  acc = block_sum(acc);
+  const double acc = block_sum(dot_part(a, s, m));
   if (threadIdx.x == 0) qd[l] = acc;
 }
 // s -= Q[:, :j] qd   (Gram-Schmidt against the previous actions; a no-op in exact arithmetic for CG
@@ -250,13 +288,13 @@ template <class T>
 __global__ void k_cg_qorth(const T* __restrict__ Q, int ldq, int j, const double* __restrict__ qd, T* __restrict__ s,
                            int m, T* __restrict__ S, int lds, const int* __restrict__ active) {
   if (!*active) return;
-  __shared__ double c[1024];
-  for (int q = threadIdx.x; q < j; q += blockDim.x) c[q] = qd[q];
+  __shared__ T c[1024];
+  for (int q = threadIdx.x; q < j; q += blockDim.x) c[q] = T(qd[q]);
   __syncthreads();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m) return;
   T v = s[i];
-  for (int q = 0; q < j; ++q) v = fma(-Q[(size_t)q * ldq + i], T(c[q]), v);
+  for (int q = 0; q < j; ++q) v = fma(-Q[(size_t)q * ldq + i], c[q], v);
   s[i] = v;
   if (S) S[(size_t)j * lds + i] = v;
 }
@@ -937,8 +975,8 @@ template <class T>
 void cg_combine(const T* part, int nsplit, const T* s, T sn2, const T* Mo, int ldm, int r, const T* t, T a2, int m,
                 T* g, const int* active, cudaStream_t st) {
   const int tz = std::max(1, (m + GV_CHUNK - 1) / GV_CHUNK);
-  k_cg_combine<T><<<cdiv(m, 128), 128, std::max(r, 1) * sizeof(T), st>>>(part, nsplit, s, sn2, Mo, ldm, r, t, tz, a2,
-                                                                          m, g, active);
+  k_cg_combine<T><<<cdiv(m, CB_ROWS), CB_WARPS * 32, std::max(r, 1) * sizeof(T), st>>>(part, nsplit, s, sn2, Mo, ldm,
+                                                                                      r, t, tz, a2, m, g, active);
   note_launch();
 }
 // t must hold ceil(rows / 1024) * cols partials (summed by cg_combine)

@@ -7,7 +7,8 @@ persistent tensor-core grid splits tiles between CTAs.  Tolerances:
   FP64 SIMT   1e-12 relative (per column, normwise)
   FP32 SIMT   2e-5 relative
   BF16 tcgen05 columns 0..w-2: within 2e-4 of the exact product of the BF16-rounded operands
-               (kernel values and B rounded to bf16, FP64 accumulation), i.e. the kernel adds only
+               (correlations and B rounded to bf16, FP64 accumulation, times sf2 after the
+               contraction), i.e. the kernel adds only
                FP32 accumulation-order rounding to the BF16 operand rounding; and within 3e-2 of
                the exact product (the bf16 rounding itself, ~2^-9 per operand);
                the last column is accumulated in FP32 on the CUDA cores: 2e-5 relative.
@@ -38,10 +39,10 @@ def case(nr, nc, width, dim, kernel, seed, lx=0.3, sf2=1.7):
     Xr = rng.uniform(size=(nr, dim))
     Xc = rng.uniform(size=(nc, dim))
     B = rng.standard_normal((width, nc))          # stored as (width, nc): column-major nc x width
-    K = oracle.kernel_matrix(Xr, Xc, kernel, lx, sf2)
-    ref = (K @ B.T).T
+    C = oracle.kernel_matrix(Xr, Xc, kernel, lx, 1.0)     # correlations; K = sf2 * C
+    ref = sf2 * (C @ B.T).T
     bf = lambda a: torch.tensor(a, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
-    ref_bf16 = (bf(K) @ bf(B).T).T
+    ref_bf16 = sf2 * (bf(C) @ bf(B).T).T
     return Xr, Xc, B, ref, ref_bf16, math.log(lx), math.log(sf2)
 
 
