@@ -94,7 +94,8 @@ typedef struct {
   double smooth_ms;           /* device time of the last cakf_smooth                          */
   double gram_block_ms;       /* summed device time of the Gram x block launches (profiling on)*/
   int64_t gram_block_launches;
-  double gram_block_flops;    /* algorithmic flops of those launches: 2 * rows * cols * width  */
+  double gram_block_flops;    /* algorithmic flops of those launches: 2*rows*cols*(width-1) on
+                                 the tensor-core path, 2*rows*cols*width on the SIMT path     */
   double gram_block_evals;    /* kernel-matrix entries evaluated by those launches            */
   double cg_matvec_ms;        /* summed device time of the CG Gram matvec launches            */
   int64_t cg_matvec_launches;

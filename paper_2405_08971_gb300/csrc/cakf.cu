@@ -361,7 +361,8 @@ struct Runner {
   int gram_block(const C4<T>* Xr, int nr, const C4<T>* Xc, int nc, const T* B, int ldb, int width, T* Out, int ldo) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (c->profiling) { e0 = c->ev(); e1 = c->ev(); cudaEventRecord(e0, st); }
-    if (tc && sizeof(T) == 4 && width >= 2 && width <= gram_tc_max_width()) {
+    const bool on_tc = tc && sizeof(T) == 4 && width >= 2 && width <= gram_tc_max_width();
+    if (on_tc) {
       size_t ldp = gram_tc_packed_ld(nc);
       int rc = gram_tc_pack_b(tc_kind, (const float*)B, ldb, nc, width, c->Bpack, (int)ldp, st);
       if (!rc)
@@ -374,7 +375,9 @@ struct Runner {
     if (c->profiling) {
       cudaEventRecord(e1, st);
       c->prof_gb.push_back({e0, e1});
-      c->prof_gb_flops.push_back(2.0 * nr * (double)nc * width);
+      // tensor-core path: the flops of the width-1 tensor-core columns (the last column runs on the
+      // CUDA cores); the bracket also holds the operand packing, so the rate is conservative
+      c->prof_gb_flops.push_back(2.0 * nr * (double)nc * (on_tc ? width - 1 : width));
       c->prof_gb_evals.push_back((double)nr * nc);
     }
     return CAKF_OK;
