@@ -30,7 +30,7 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-DTYPE_NAME = {"bf16": "bf16", "tf32": "tf32", "fp32": "f32", "fp64": "f64"}
+DTYPE_NAME = {"fp16x3": "fp16x3", "bf16": "bf16", "fp32": "f32", "fp64": "f64"}
 
 
 def parse():
@@ -239,14 +239,14 @@ def main():
     gb_avg_ms = prof["gram_block_ms"] / max(1, prof["gram_block_launches"])
     flops_per_launch = prof["gram_block_flops"] / max(1, prof["gram_block_launches"])
     achieved = flops_per_launch / (gb_avg_ms / 1e3) / 1e12
-    if args.precision in ("bf16", "tf32"):
+    if args.precision in ("bf16", "fp16x3"):
         peak = float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops")))
-        if args.precision == "tf32":
-            peak *= 0.5   # nominal dense tf32 / bf16 ratio (1.1 / 2.25 PF)
+        mmas = 3 if args.precision == "fp16x3" else 1
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None,
-                "kernel": "gram_block (filter finalize + smoother P^- X)",
-                "peak_source": f"{pk_src} bf16_tflops_sustained" + (" x 0.5 (tf32/bf16 nominal)" if args.precision == "tf32" else "")}
+                "kernel": "k_gram_tc (filter finalize + smoother P^- X)",
+                "peak_source": f"{pk_src} bf16_tflops_sustained",
+                "tensor_mmas_per_algorithmic_flop": mmas}
     else:
         clk = (clocks.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)) * 1e6
         lanes = 128 if args.precision == "fp32" else 4

@@ -56,8 +56,11 @@ enum { CAKF_MATERN12 = 0, CAKF_MATERN32 = 1, CAKF_MATERN52 = 2 };
 enum {
   CAKF_FP64 = 0,   /* all in FP64 (reference mode)                                          */
   CAKF_FP32 = 1,   /* plain FP32 SIMT kernels (factors, CG and tall-skinny GEMMs in FP32)    */
-  CAKF_TF32 = 2,   /* Gram tiles x blocks on tcgen05 kind::tf32, FP32 accumulation          */
-  CAKF_BF16 = 3    /* Gram tiles x blocks on tcgen05 kind::f16 (bf16), FP32 accumulation    */
+  CAKF_TF32 = 2,   /* reserved (tcgen05 kind::tf32); rejected with CAKF_ERR_ARG in this build */
+  CAKF_BF16 = 3,   /* Gram tiles x blocks on tcgen05 kind::f16 (bf16), FP32 accumulation    */
+  CAKF_FP16X3 = 4  /* Gram tiles x blocks on tcgen05 kind::f16 with split FP16 operands:
+                      x = hi + lo (both fp16, B scaled per column by a power of two), three
+                      MMAs hi*hi + hi*lo + lo*hi, FP32 accumulation: FP32-class products      */
 };
 
 typedef struct {
@@ -81,7 +84,7 @@ typedef struct {
   int32_t budget_i;           /* action budget per step (CG iterations), >= 1                 */
   int32_t rank_r;             /* truncation rank of the downdate factors; <= 0: no truncation */
   double cg_rtol;             /* stop a step's CG early when ||r|| <= cg_rtol ||r0||; 0 = never */
-  int32_t precision;          /* CAKF_FP64 | CAKF_FP32 | CAKF_TF32 | CAKF_BF16                 */
+  int32_t precision;          /* CAKF_FP64 | CAKF_FP32 | CAKF_BF16 | CAKF_FP16X3 (TF32: rejected) */
   const double* replay_actions; /* NULL, or frozen actions: for each step k the m_k x i_k
                                  column-major block S_k, concatenated over k = 1..T (host)    */
   const int32_t* replay_counts; /* with replay_actions: T+1 entries, i_k for k = 0..T (host)  */
@@ -176,9 +179,10 @@ int cakf_get_actions(cakf_ctx* ctx, double* actions_out, int32_t* counts_out);
  *   B                 DEVICE, column-major nc x width (leading dimension ldb >= nc); double for
  *                     CAKF_FP64, float otherwise
  *   Out               DEVICE, column-major nr x width (ldo >= nr); same element type as B
- *   precision         CAKF_FP64 / CAKF_FP32: SIMT kernels; CAKF_BF16: tcgen05 tensor cores for
- *                     columns 0..width-2 (bf16 operands, fp32 accumulation) and fp32 CUDA-core
- *                     accumulation of the last column (width >= 2 and <= 513 for this path)
+ *   precision         CAKF_FP64 / CAKF_FP32: SIMT kernels; CAKF_BF16 / CAKF_FP16X3: tcgen05
+ *                     tensor cores for columns 0..width-2 (bf16 operands, or fp16 hi + lo
+ *                     parts for FP16X3; fp32 accumulation) and fp32 CUDA-core accumulation of
+ *                     the last column (width >= 2 and <= 513 for these paths)
  * Scratch is allocated on the first call per thread and kept (grown when needed).
  * Errors: CAKF_ERR_ARG (sizes, NULL, host pointers), CAKF_ERR_OOM, CAKF_ERR_CUDA.
  */
@@ -201,9 +205,10 @@ int cakf_gram_matmul(int32_t kernel, double log_lx, double log_sf2, int32_t dim,
  *
  * Limit: the scratch must hold 256 bytes + (nr + nc) coordinate records (32 bytes each for
  * CAKF_FP64, 16 otherwise, rounded up to 256) and, for CAKF_BF16, the packed operand
- * (about 2 * nc * (width - 1) bytes plus 20 * nc).  A call needing more returns CAKF_ERR_ARG
- * with the required size in cakf_last_error, before any device work; for example BF16 with
- * nc = 32768, width = 513 fits, nc = 65536 needs width <= 257.
+ * (about 2 * nc * (width - 1) bytes plus 20 * nc; twice the operand bytes for CAKF_FP16X3).
+ * A call needing more returns CAKF_ERR_ARG with the required size in cakf_last_error, before
+ * any device work; for example BF16 with nc = 32768, width = 513 fits, nc = 65536 needs
+ * width <= 257 (FP16X3: nc = 32768 needs width <= 257).
  * Zero state: only the device error flag inside the scratch has to start at zero; the call
  * clears it on its stream before use.  All other scratch bytes are written before being read.
  * Concurrency: every call on a device uses the same scratch, so calls that overlap in time on

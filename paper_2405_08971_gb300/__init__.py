@@ -8,5 +8,5 @@ from .binding import (  # noqa: F401
     Context, CakfError, make_problem, problem_from_workload, cakf_filter, cakf_smooth, cakf_nll,
     cakf_nll_backward, cakf_get_actions, cakf_gram_matmul, cakf_gram_matmul_noalloc, cakf_get_stats,
     cakf_set_profiling, pack_actions, lib,
-    FP64, FP32, TF32, BF16, MATERN12, MATERN32, MATERN52,
+    FP64, FP32, TF32, BF16, FP16X3, MATERN12, MATERN32, MATERN52,
 )

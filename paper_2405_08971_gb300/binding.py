@@ -18,8 +18,8 @@ LIB_PATH = os.path.join(HERE, "libcakf.so")
 ABI_VERSION = 1
 OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_NUMERIC, ERR_TIMEOUT, ERR_STATE = range(7)
 MATERN12, MATERN32, MATERN52 = 0, 1, 2
-FP64, FP32, TF32, BF16 = 0, 1, 2, 3
-PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32": TF32, "bf16": BF16}
+FP64, FP32, TF32, BF16, FP16X3 = 0, 1, 2, 3, 4
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32": TF32, "bf16": BF16, "fp16x3": FP16X3}
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_NUMERIC", 5: "ERR_TIMEOUT", 6: "ERR_STATE"}
 
 

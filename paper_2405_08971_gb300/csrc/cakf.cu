@@ -304,8 +304,8 @@ int plan_and_alloc(cakf_ctx* c, const cakf_problem* p) {
   c->off_U[1] = 0;
   for (int k = 1; k <= T; ++k) c->off_U[k + 1] = c->off_U[k] + (size_t)c->Urows[k] * (c->Urows[k] ? c->mcols[k] : 0);
   if ((rc = c->alloc(c->Upool, std::max<size_t>(c->off_U[T + 1], 1) * sizeof(double)))) return rc;
-  if (c->precision == CAKF_BF16 || c->precision == CAKF_TF32) {
-    c->Bpack_bytes = gram_tc_staging_bytes(std::max(c->n, c->mmax), (int)wfin) + 4096;
+  if (c->precision == CAKF_BF16 || c->precision == CAKF_FP16X3) {
+    c->Bpack_bytes = gram_tc_staging_bytes(std::max(c->n, c->mmax), (int)wfin, c->precision == CAKF_FP16X3 ? 1 : 0) + 4096;
     if ((rc = c->alloc(c->Bpack, c->Bpack_bytes))) return rc;
   }
   if (!c->ev0) { cudaEventCreate(&c->ev0); cudaEventCreate(&c->ev1); }
@@ -331,7 +331,7 @@ struct Runner {
   cakf_ctx* c;
   cudaStream_t st;
   bool tc;      // tensor-core Gram x block
-  int tc_kind;  // 0 bf16, 1 tf32
+  int tc_kind;  // 0 bf16, 1 split bf16 (x3)
 
   // phase timers (profiling on): begin returns the start event, end records the pair
   cudaEvent_t ph_begin() {
@@ -905,7 +905,7 @@ int validate(const cakf_problem* p) {
   const int N = p->obs_ptr[p->T];
   if (N > 0 && (!p->obs_idx || !p->y)) return fail(CAKF_ERR_ARG, "obs_idx / y is NULL");
   if (p->budget_i < 1 || p->budget_i > 1024) return fail(CAKF_ERR_ARG, "budget_i must be in 1..1024");
-  if (p->precision < CAKF_FP64 || p->precision > CAKF_BF16) return fail(CAKF_ERR_ARG, "unknown precision");
+  if (p->precision < CAKF_FP64 || p->precision > CAKF_FP16X3) return fail(CAKF_ERR_ARG, "unknown precision");
   if (p->precision == CAKF_TF32) return fail(CAKF_ERR_ARG, "CAKF_TF32 Gram tiles are not available in this build");
   const double hp[4] = {p->log_lx, p->log_lt, p->log_sf2, p->log_sn2};
   for (double h : hp)
@@ -996,8 +996,8 @@ Runner<T> make_runner(cakf_ctx* c, cudaStream_t st) {
   Runner<T> r;
   r.c = c;
   r.st = st;
-  r.tc = (c->precision == CAKF_BF16 || c->precision == CAKF_TF32);
-  r.tc_kind = (c->precision == CAKF_TF32) ? 1 : 0;
+  r.tc = (c->precision == CAKF_BF16 || c->precision == CAKF_FP16X3);
+  r.tc_kind = (c->precision == CAKF_FP16X3) ? 1 : 0;
   return r;
 }
 
@@ -1202,10 +1202,11 @@ extern "C" int cakf_gram_matmul(int32_t kernel, double log_lx, double log_sf2, i
   if (!Xr || !Xc || !B || !Out) return fail(CAKF_ERR_ARG, "cakf_gram_matmul: NULL pointer");
   if (!is_device_ptr(Xr) || !is_device_ptr(Xc) || !is_device_ptr(B) || !is_device_ptr(Out))
     return fail(CAKF_ERR_ARG, "cakf_gram_matmul: all arrays must be device arrays");
-  if (precision != CAKF_FP64 && precision != CAKF_FP32 && precision != CAKF_BF16)
-    return fail(CAKF_ERR_ARG, "cakf_gram_matmul: precision must be FP64, FP32 or BF16");
-  if (precision == CAKF_BF16 && (width < 2 || width > gram_tc_max_width()))
-    return fail(CAKF_ERR_ARG, "cakf_gram_matmul: the BF16 path needs 2 <= width <= 513");
+  if (precision != CAKF_FP64 && precision != CAKF_FP32 && precision != CAKF_BF16 && precision != CAKF_FP16X3)
+    return fail(CAKF_ERR_ARG, "cakf_gram_matmul: precision must be FP64, FP32, BF16 or FP16X3");
+  const bool tcp = precision == CAKF_BF16 || precision == CAKF_FP16X3;
+  if (tcp && (width < 2 || width > gram_tc_max_width()))
+    return fail(CAKF_ERR_ARG, "cakf_gram_matmul: the tensor-core paths need 2 <= width <= 513");
   if (!std::isfinite(log_lx) || !std::isfinite(log_sf2)) return fail(CAKF_ERR_ARG, "non-finite hyperparameters");
   cudaStream_t st = (cudaStream_t)cuda_stream;
   const size_t es = precision == CAKF_FP64 ? 8 : 4;
@@ -1231,10 +1232,11 @@ extern "C" int cakf_gram_matmul(int32_t kernel, double log_lx, double log_sf2, i
     if (precision == CAKF_FP32) {
       gram_block_simt<float>(kernel, xr, nr, xc, nc, (const float*)B, ldb, width, (float)sf2, (float*)Out, ldo, st);
     } else {
-      if ((rc = ensure(g_gs.stage, g_gs.stage_bytes, gram_tc_staging_bytes(nc, width) + 4096))) return rc;
+      const int kind = precision == CAKF_FP16X3 ? 1 : 0;
+      if ((rc = ensure(g_gs.stage, g_gs.stage_bytes, gram_tc_staging_bytes(nc, width, kind) + 4096))) return rc;
       const int ldp = (int)gram_tc_packed_ld(nc);
-      int r2 = gram_tc_pack_b(0, (const float*)B, ldb, nc, width, g_gs.stage, ldp, st);
-      if (!r2) r2 = gram_block_tc(kernel, 0, xr, nr, xc, nc, g_gs.stage, ldp, width, (float)sf2, (float*)Out, ldo,
+      int r2 = gram_tc_pack_b(kind, (const float*)B, ldb, nc, width, g_gs.stage, ldp, st);
+      if (!r2) r2 = gram_block_tc(kernel, kind, xr, nr, xc, nc, g_gs.stage, ldp, width, (float)sf2, (float*)Out, ldo,
                                   g_gs.err, st);
       if (r2) return fail(CAKF_ERR_CUDA, "tensor-core Gram x block launch failed (code " + std::to_string(r2) + ")");
     }

@@ -1,18 +1,28 @@
 // Tensor-core Gram x block product for sm_103a (tcgen05 + TMEM + TMA), the hot kernel of the CAKF / CAKS:
 //
-//   Out[i, c] = sum_j k(xr_i, xc_j) B[j, c]         (Out, B column-major; k a Matern kernel)
+//   Out[i, c] = sf2 * sum_j corr(xr_i, xc_j) B[j, c]     (Out, B column-major; corr a Matern correlation)
 //
-// The kernel matrix is never stored: each CTA owns 128 output rows and walks the columns j in
-// slices of 64.  Per slice, 8 producer warps evaluate the 128 x 64 kernel tile from coordinates
-// staged in shared memory and write it as BF16 in the 128-byte-swizzled K-major layout that the
-// tensor core reads; a TMA warp stages the matching 64 x N slice of the packed B operand; a single
-// thread issues tcgen05.mma (M = 128, N <= 256 per instruction, K = 16) accumulating in TMEM
-// (up to 512 FP32 columns).  The last column of B (the mean vector of the filter / smoother) is
-// not sent to the tensor core: the producers accumulate it in FP32 from the same kernel values.
+// The kernel matrix is never stored.  The work is the sequence of (128-row tile, K slice) units,
+// split evenly over a persistent grid of one CTA per SM.  Per slice, 16 producer warps evaluate the
+// 128-row correlation tile from coordinates staged in shared memory and write it in the swizzled
+// K-major layout the tensor core reads; a TMA warp stages the matching slice of the packed B
+// operand; one thread issues tcgen05.mma (M = 128, N <= 256 per instruction, K = 16) accumulating
+// in TMEM (up to 512 FP32 columns); the producer warps drain TMEM in the epilogue.  The last column
+// of B (the mean vector of the filter / smoother) is not sent to the tensor core: the producers
+// accumulate it in FP32 from the same correlation values.
+//
+// Two operand modes (template parameter SPLIT):
+//   BF16      one BF16 MMA per slice and N chunk; 64-column slices, 128-byte swizzle.
+//   FP16 x3   every operand is carried as hi = fp16(x) plus lo = fp16(x - hi) (22 significant
+//             bits; B is scaled per column by a power of two into [0.5, 1) first, undone in the
+//             epilogue), and hi*hi + hi*lo + lo*hi accumulate in the same TMEM columns: FP32-class
+//             products at three MMAs per slice; 32-column slices, 64-byte swizzle (the doubled
+//             operands must still fit two pipeline stages in shared memory).
 // Every mbarrier wait is bounded; on timeout the CTA raises the error flag and stops.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <mutex>
 #include <map>
 #include "internal.h"
@@ -21,13 +31,28 @@ namespace cakf {
 namespace {
 
 constexpr int BM = 128;          // rows per CTA (TMEM lanes)
-constexpr int BK = 64;           // kernel columns per pipeline stage (64 bf16 = one 128B swizzle row)
 constexpr int NPROD_WARPS = 16;  // kernel-tile producers (and epilogue)
-constexpr int NQ = NPROD_WARPS / 4;   // producer warps per TMEM lane group: each takes BK / NQ columns
+constexpr int NQ = NPROD_WARPS / 4;   // producer warps per TMEM lane group (epilogue column split)
 constexpr int TMA_WARP = NPROD_WARPS;
 constexpr int MMA_WARP = NPROD_WARPS + 1;   // the remaining warp issues the MMAs
 constexpr int NTHREADS = (NPROD_WARPS + 2) * 32;
-constexpr int A_STAGE_BYTES = BM * BK * 2;   // 16 KB
+constexpr int BK_MAX = 64;       // packed operands are padded to a multiple of the larger slice
+
+// Per-mode layout constants.
+template <bool SPLIT> struct Mode {
+  static constexpr int BK = SPLIT ? 32 : 64;          // kernel columns per pipeline stage
+  static constexpr int ROWB = BK * 2;                 // bytes per tile row = swizzle span
+  static constexpr int NPART = SPLIT ? 2 : 1;         // operand parts (hi, lo)
+  static constexpr int A_TILE = BM * ROWB;            // bytes per A part
+  static constexpr int C_STAGE = BK * 16;             // column coordinates, pair layout
+  static constexpr int W_STAGE = BK * 4;              // mean column
+  static constexpr int CPT = BK / 8;                  // columns per producer thread and slice
+  static constexpr uint32_t SBO = 8 * ROWB;           // 8-row group stride
+  static constexpr uint64_t LAYOUT = SPLIT ? 4 : 2;   // descriptor swizzle: 64-byte / 128-byte
+  // kind::f16 instruction descriptor fields: FP32 accumulator; A, B both FP16 (0) or both BF16 (1)
+  static constexpr uint32_t FMT = SPLIT ? (1u << 4) : ((1u << 4) | (1u << 7) | (1u << 10));
+};
+
 constexpr long long WAIT_LIMIT = 20000000LL;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -76,23 +101,36 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
                : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+// Shared-memory matrix descriptor: K-major, swizzled rows of ROWB bytes, 8-row groups SBO apart.
+// The K step of an MMA (16 elements = 32 bytes) is taken by advancing the start address.
+template <bool SPLIT>
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;                 // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset
-  d |= (uint64_t)1 << 46;                 // descriptor version
-  d |= (uint64_t)2 << 61;                 // 128-byte swizzle
+  d |= (uint64_t)1 << 16;                           // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(Mode<SPLIT>::SBO >> 4) << 32;     // stride byte offset
+  d |= (uint64_t)1 << 46;                           // descriptor version
+  d |= Mode<SPLIT>::LAYOUT << 61;                   // swizzle mode
   return d;
 }
 
-// Instruction descriptor, kind::f16: BF16 A/B (K-major), FP32 accumulator, M = 128.
-__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+// Byte offset of byte `b` of row `row` in a swizzled tile: the 16-byte chunk index is XORed with
+// the row's phase (row & 7 for 128-byte rows, (row >> 1) & 3 for 64-byte rows).
+template <bool SPLIT>
+__device__ __forceinline__ uint32_t sw_off(int row, int b) {
+  constexpr int R = Mode<SPLIT>::ROWB;
+  const int chunk = b >> 4;
+  const int phase = ((row * R) >> 7) & (R / 16 - 1);
+  return (uint32_t)(row * R + ((chunk ^ phase) << 4) + (b & 15));
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+// Instruction descriptor, kind::f16, M = 128, N = n.
+template <bool SPLIT>
+__host__ __device__ constexpr uint32_t idesc(int n) {
+  return Mode<SPLIT>::FMT | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
       ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc)
@@ -141,6 +179,17 @@ __device__ __forceinline__ uint32_t f2_bf16(uint64_t v) {
   f2_split(v, lo, hi);
   return pack_bf16(lo, hi);
 }
+__device__ __forceinline__ uint32_t f2_f16(uint64_t v) {
+  float lo, hi;
+  f2_split(v, lo, hi);
+  __half2 h = __floats2half2_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+// The two fp16 of a packed pair widened back to FP32 (exact).
+__device__ __forceinline__ uint64_t f16x2_to_f2(uint32_t p) {
+  const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&p));
+  return f2_make(f.x, f.y);
+}
 
 // Matern correlation (without sf2) of one row against a column pair.  Coordinates are pre-scaled
 // by c_nu / l_x, so with s the Euclidean distance:  nu=1/2: e^-s,  nu=3/2: (1+s) e^-s,
@@ -173,6 +222,7 @@ struct TcParams {
   int nr;
   const C4<float>* Xc;     // nk * BK columns in pair layout (see k_pad_coords), sentinels beyond nc
   const float* wcol;       // padded mean column (zeros beyond nc), FP32
+  const float* binv;       // FP16 x3: per-column factor undoing the operand scaling (else null)
   int nk;                  // number of K slices per row tile
   int ntiles;              // row tiles of BM rows
   int npad;                // accumulator columns (multiple of 16, <= 512)
@@ -216,18 +266,20 @@ __device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity) {
 // CTA b takes units [total*b/G, total*(b+1)/G).  With G <= ntiles every CTA covers at least one full
 // tile's worth of slices, so a tile is shared by at most two CTAs; those add their partial sums
 // into an output zeroed beforehand (two addends onto zero: the result does not depend on order).
-template <int KER>
+template <int KER, bool SPLIT>
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_gram_tc(const __grid_constant__ CUtensorMap tmapB, const TcParams P) {
+  using M = Mode<SPLIT>;
   extern __shared__ uint8_t smem_raw[];
   // 1024-byte aligned base for the swizzled tiles
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int S = P.stages;
+  // per stage: A parts (NPART x A_TILE), then B parts (NPART x npad rows x ROWB bytes)
   uint8_t* A_base = smem;
-  uint8_t* B_base = A_base + (size_t)S * A_STAGE_BYTES;
-  uint8_t* C_base = B_base + (size_t)S * P.b_stage_bytes;            // coordinates, 1 KB per stage
-  uint8_t* W_base = C_base + (size_t)S * (BK * 16);                  // mean column, 256 B per stage
-  uint64_t* bars = reinterpret_cast<uint64_t*>(W_base + (size_t)S * (BK * 4));
+  uint8_t* B_base = A_base + (size_t)S * M::NPART * M::A_TILE;
+  uint8_t* C_base = B_base + (size_t)S * P.b_stage_bytes;            // coordinates
+  uint8_t* W_base = C_base + (size_t)S * M::C_STAGE;                 // mean column
+  uint64_t* bars = reinterpret_cast<uint64_t*>(W_base + (size_t)S * M::W_STAGE);
   uint64_t* fullA = bars;
   uint64_t* fullB = bars + S;
   uint64_t* fullC = bars + 2 * S;
@@ -268,10 +320,10 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmapB, const TcParams P) {
   if (warp < NPROD_WARPS) {
     // ------------------------------------------------------------ kernel-tile producers + epilogue
     // Producer role: warp w computes rows {rh*32 + lane, rh*32 + lane + 64} (rh = w & 1) for the
-    // 8-column chunk c8 = w >> 1 of every slice, two columns at a time in packed f32x2 arithmetic.
-    // Epilogue role: warp w reads TMEM lanes 32*(w & 3).. (the lane group it may access) for the
-    // column chunks qt, qt + NQ, ... (qt = w >> 2).
-    const int rh = warp & 1, c8 = warp >> 1;
+    // CPT-column group cg = w >> 1 of every slice, two columns at a time in packed f32x2
+    // arithmetic.  Epilogue role: warp w reads TMEM lanes 32*(w & 3).. (the lane group it may
+    // access) for the column chunks qt, qt + NQ, ... (qt = w >> 2).
+    const int rh = warp & 1, cg = warp >> 1;
     const int lg = warp & 3;                        // TMEM lane group of this warp
     const int qt = warp >> 2;                       // which NQ-th of the 32-column epilogue chunks
     const int rl = lg * 32 + lane;                  // epilogue row within the tile (= TMEM lane)
@@ -304,11 +356,12 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmapB, const TcParams P) {
         ok = mbar_wait(smem_u32(&fullC[s]), n & 1, abort_flag);
         ok = __all_sync(0xffffffffu, ok);
         if (!ok) break;
-        const uint8_t* cp = C_base + (size_t)s * BK * 16 + (size_t)c8 * 4 * 32;   // 4 column pairs
-        const float* wc = reinterpret_cast<const float*>(W_base + (size_t)s * BK * 4) + c8 * 8;
-        uint32_t pk0[4], pk1[4];
+        constexpr int NPAIR = M::CPT / 2;
+        const uint8_t* cp = C_base + (size_t)s * M::C_STAGE + (size_t)cg * NPAIR * 32;
+        const float* wc = reinterpret_cast<const float*>(W_base + (size_t)s * M::W_STAGE) + cg * M::CPT;
+        uint32_t pk0[NPAIR], pk1[NPAIR], pl0[NPAIR], pl1[NPAIR];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < NPAIR; ++q) {
           const ulonglong2 xy = *reinterpret_cast<const ulonglong2*>(cp + q * 32);
           const uint64_t cz = *reinterpret_cast<const uint64_t*>(cp + q * 32 + 16);
           const uint64_t w2 = *reinterpret_cast<const uint64_t*>(wc + 2 * q);
@@ -316,21 +369,36 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmapB, const TcParams P) {
           const uint64_t k1 = kpair<KER>(rx1, ry1, rz1, xy.x, xy.y, cz);
           macc0 = f2_fma(k0, w2, macc0);
           macc1 = f2_fma(k1, w2, macc1);
-          pk0[q] = f2_bf16(k0);
-          pk1[q] = f2_bf16(k1);
+          if (SPLIT) {
+            pk0[q] = f2_f16(k0);
+            pk1[q] = f2_f16(k1);
+            pl0[q] = f2_f16(f2_sub(k0, f16x2_to_f2(pk0[q])));
+            pl1[q] = f2_f16(f2_sub(k1, f16x2_to_f2(pk1[q])));
+          } else {
+            pk0[q] = f2_bf16(k0);
+            pk1[q] = f2_bf16(k1);
+          }
         }
-        uint8_t* ast = A_base + (size_t)s * A_STAGE_BYTES;
-        const int chunk = c8 ^ (pr0 & 7);           // pr1 = pr0 + 64 has the same swizzle phase
-        *reinterpret_cast<uint4*>(ast + pr0 * 128 + chunk * 16) = make_uint4(pk0[0], pk0[1], pk0[2], pk0[3]);
-        *reinterpret_cast<uint4*>(ast + pr1 * 128 + chunk * 16) = make_uint4(pk1[0], pk1[1], pk1[2], pk1[3]);
+        uint8_t* ast = A_base + (size_t)s * M::NPART * M::A_TILE;
+        const int b0 = cg * M::CPT * 2;                 // byte of this column group within a row
+        const uint32_t o0 = sw_off<SPLIT>(pr0, b0), o1 = sw_off<SPLIT>(pr1, b0);
+        if (SPLIT) {   // 8 bytes per row and part
+          *reinterpret_cast<uint2*>(ast + o0) = make_uint2(pk0[0], pk0[1]);
+          *reinterpret_cast<uint2*>(ast + o1) = make_uint2(pk1[0], pk1[1]);
+          *reinterpret_cast<uint2*>(ast + M::A_TILE + o0) = make_uint2(pl0[0], pl0[1]);
+          *reinterpret_cast<uint2*>(ast + M::A_TILE + o1) = make_uint2(pl1[0], pl1[1]);
+        } else {       // 16 bytes per row
+          *reinterpret_cast<uint4*>(ast + o0) = make_uint4(pk0[0], pk0[1], pk0[NPAIR > 2 ? 2 : 0], pk0[NPAIR > 3 ? 3 : 0]);
+          *reinterpret_cast<uint4*>(ast + o1) = make_uint4(pk1[0], pk1[1], pk1[NPAIR > 2 ? 2 : 0], pk1[NPAIR > 3 ? 3 : 0]);
+        }
         fence_proxy_async();
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&fullA[s]));
       }
       // ---- end of this CTA's part of the tile: every producer warp arrives here, also on abort
       float* mp = mean_part + (tcount & 1) * (8 * BM);
-      mp[c8 * BM + pr0] = f2_sum(macc0);
-      mp[c8 * BM + pr1] = f2_sum(macc1);
+      mp[cg * BM + pr0] = f2_sum(macc0);
+      mp[cg * BM + pr1] = f2_sum(macc1);
       ok = producers_all(ok && !*abort_flag);
       if (!ok) break;
       if (qt == 0 && row < P.nr) {
@@ -367,7 +435,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmapB, const TcParams P) {
             for (int j = 0; j < 32; ++j) {
               const int c = ch * 32 + j;
               if (c < P.wtc) {
-                const float val = P.sf2 * __uint_as_float(v[j]);
+                const float val = (SPLIT ? P.sf2 * P.binv[c] : P.sf2) * __uint_as_float(v[j]);
                 if (split) atomicAdd(o + (size_t)c * P.ldo, val);
                 else o[(size_t)c * P.ldo] = val;
               }
@@ -393,14 +461,17 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmapB, const TcParams P) {
         const int kt = (int)(u % P.nk);
         if (!mbar_wait(smem_u32(&empty[s]), (n & 1) ^ 1, abort_flag)) break;
         const uint32_t cb = smem_u32(&fullC[s]);
-        mbar_expect_tx(cb, BK * 16 + BK * 4);
-        bulk_load(smem_u32(C_base + (size_t)s * BK * 16), P.Xc + (size_t)kt * BK, BK * 16, cb);
-        bulk_load(smem_u32(W_base + (size_t)s * BK * 4), P.wcol + (size_t)kt * BK, BK * 4, cb);
+        mbar_expect_tx(cb, M::C_STAGE + M::W_STAGE);
+        bulk_load(smem_u32(C_base + (size_t)s * M::C_STAGE), P.Xc + (size_t)kt * M::BK, M::C_STAGE, cb);
+        bulk_load(smem_u32(W_base + (size_t)s * M::W_STAGE), P.wcol + (size_t)kt * M::BK, M::W_STAGE, cb);
         const uint32_t bb = smem_u32(&fullB[s]);
         mbar_expect_tx(bb, P.b_stage_bytes);
-        for (int b = 0; b < P.nbox; ++b)
-          tma_load_2d(smem_u32(B_base + (size_t)s * P.b_stage_bytes + (size_t)b * P.boxh * 128), &tmapB, kt * BK,
-                      b * P.boxh, bb);
+        // B rows (operand columns) 0..npad-1 hold the hi part, npad..2 npad-1 the lo part
+        for (int part = 0; part < M::NPART; ++part)
+          for (int b = 0; b < P.nbox; ++b)
+            tma_load_2d(smem_u32(B_base + (size_t)s * P.b_stage_bytes +
+                                 ((size_t)part * P.npad + (size_t)b * P.boxh) * M::ROWB),
+                        &tmapB, kt * M::BK, part * P.npad + b * P.boxh, bb);
         ++issued;
       }
       // on abort, let the copies possibly still in flight (the last S issued) land before exit
@@ -435,16 +506,22 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmapB, const TcParams P) {
           ok = mbar_wait(smem_u32(&fullA[s]), n & 1, abort_flag) && mbar_wait(smem_u32(&fullB[s]), n & 1, abort_flag);
           if (!ok) break;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t a0 = smem_u32(A_base + (size_t)s * A_STAGE_BYTES);
+          const uint32_t a0 = smem_u32(A_base + (size_t)s * M::NPART * M::A_TILE);
           const uint32_t b0 = smem_u32(B_base + (size_t)s * P.b_stage_bytes);
+          const uint32_t blo = (uint32_t)P.npad * M::ROWB;   // offset of the lo part of B
           for (int c0 = 0; c0 < P.npad; c0 += 256) {
             const int nn = min(256, P.npad - c0);
-            const uint32_t idesc = idesc_bf16(nn);
+            const uint32_t id = idesc<SPLIT>(nn);
+            const uint32_t d = tmem + (uint32_t)c0;
 #pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk) {
-              const uint64_t ad = sdesc_sw128(a0 + kk * 32);
-              const uint64_t bd = sdesc_sw128(b0 + (uint32_t)c0 * 128 + kk * 32);
-              mma_bf16(tmem + (uint32_t)c0, ad, bd, idesc, (first && kk == 0) ? 0u : 1u);
+            for (int kk = 0; kk < M::BK / 16; ++kk) {
+              const uint64_t ah = sdesc<SPLIT>(a0 + kk * 32);
+              const uint64_t bh = sdesc<SPLIT>(b0 + (uint32_t)c0 * M::ROWB + kk * 32);
+              mma_f16(d, ah, bh, id, (first && kk == 0) ? 0u : 1u);
+              if (SPLIT) {
+                mma_f16(d, ah, sdesc<SPLIT>(b0 + blo + (uint32_t)c0 * M::ROWB + kk * 32), id, 1u);
+                mma_f16(d, sdesc<SPLIT>(a0 + M::A_TILE + kk * 32), bh, id, 1u);
+              }
             }
           }
           first = false;
@@ -466,17 +543,48 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmapB, const TcParams P) {
 }
 
 // ---------------------------------------------------------------------------- operand packing
-// Bp (bf16, column-major, ld = ldp): the first wtc columns of B, zero-padded to ldp rows and npad
-// columns.  wp (fp32, ldp): column wtc of B (the mean column), zero-padded.  Xp: coordinates padded
-// with far-away sentinels (kernel value 0).
-__global__ void k_pack_b(const float* __restrict__ B, int ldb, int rows, int wtc, int npad, int ldp,
-                         __nv_bfloat16* __restrict__ Bp, float* __restrict__ wp) {
+// FP16 x3 mode: per column c < wtc of B, the power of two that brings max |B[:, c]| into [0.5, 1)
+// (sc[c]) and its inverse (inv[c], applied in the epilogue).  One block per column.
+__global__ void k_col_scale(const float* __restrict__ B, int ldb, int rows, int wtc, float* __restrict__ sc,
+                            float* __restrict__ inv) {
+  const int c = blockIdx.x;
+  if (c >= wtc) return;
+  float m = 0.f;
+  for (int i = threadIdx.x; i < rows; i += blockDim.x) m = fmaxf(m, fabsf(B[(size_t)c * ldb + i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __shared__ float red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    m = red[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
+    int e = 0;
+    if (m > 0.f && isfinite(m)) frexpf(m, &e);     // m = f * 2^e, f in [0.5, 1)
+    sc[c] = ldexpf(1.f, -e);
+    inv[c] = ldexpf(1.f, e);
+  }
+}
+
+// Bp (ld = ldp): rows 0..npad-1 hold the first wtc columns of B, zero-padded to ldp entries and
+// npad rows -- as BF16, or for the split mode as hi = fp16(s_c B) with rows npad..2 npad-1 holding
+// lo = fp16(s_c B - hi).  wp (fp32, ldp): column wtc of B (the mean column), zero-padded.
+__global__ void k_pack_b(const float* __restrict__ B, int ldb, int rows, int wtc, int npad, int ldp, int split,
+                         const float* __restrict__ sc, void* __restrict__ Bp, float* __restrict__ wp) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int c = blockIdx.y;
   if (i >= ldp) return;
   if (c < npad) {
-    float v = (c < wtc && i < rows) ? B[(size_t)c * ldb + i] : 0.f;
-    Bp[(size_t)c * ldp + i] = __float2bfloat16_rn(v);
+    const float v = (c < wtc && i < rows) ? B[(size_t)c * ldb + i] : 0.f;
+    if (split) {
+      const float x = c < wtc ? v * sc[c] : 0.f;
+      const __half hi = __float2half_rn(x);
+      __half* h = reinterpret_cast<__half*>(Bp);
+      h[(size_t)c * ldp + i] = hi;
+      h[(size_t)(npad + c) * ldp + i] = __float2half_rn(x - __half2float(hi));
+    } else {
+      reinterpret_cast<__nv_bfloat16*>(Bp)[(size_t)c * ldp + i] = __float2bfloat16_rn(v);
+    }
   } else {
     wp[i] = (i < rows) ? B[(size_t)wtc * ldb + i] : 0.f;
   }
@@ -533,16 +641,18 @@ struct Layout {
   size_t smem;
 };
 
+template <bool SPLIT>
 Layout plan_layout(int wtc) {
+  using M = Mode<SPLIT>;
   Layout L;
   L.npad = std::max(16, round_up(wtc, 16));
-  L.boxh = L.npad <= 256 ? L.npad : 256;
-  L.nbox = (L.npad + L.boxh - 1) / L.boxh;
-  L.b_stage_bytes = (uint32_t)L.nbox * L.boxh * 128;
-  const size_t per_stage = A_STAGE_BYTES + L.b_stage_bytes + BK * 16 + BK * 4;
+  L.nbox = (L.npad + 255) / 256;           // npad <= 512: one or two boxes per part
+  L.boxh = L.npad / L.nbox;                // a multiple of 8: boxes start on swizzle-atom boundaries
+  L.b_stage_bytes = (uint32_t)(M::NPART * L.npad * M::ROWB);
+  const size_t per_stage = (size_t)M::NPART * M::A_TILE + L.b_stage_bytes + M::C_STAGE + M::W_STAGE;
   const size_t fixed = 1024 /*alignment slack*/ + 64 * 8 + 64 + 2 * 8 * BM * 4;
   const size_t budget = 220 * 1024;
-  L.stages = (int)std::min<size_t>(4, (budget - fixed) / per_stage);
+  L.stages = (int)std::min<size_t>(8, (budget - fixed) / per_stage);
   L.tmem_cols = 32;
   while (L.tmem_cols < L.npad) L.tmem_cols *= 2;
   L.smem = fixed + (size_t)L.stages * per_stage;
@@ -554,63 +664,63 @@ Layout plan_layout(int wtc) {
   return L;
 }
 
-}  // namespace
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-size_t gram_tc_packed_ld(int rows) { return (size_t)round_up(std::max(rows, 1), BK); }
-int gram_tc_max_width() { return 513; }
-
-// Bytes of packed staging for a (rows x width) block: bf16 operand + fp32 mean column + padded coords.
-static size_t packed_bytes(int rows, int width) {
+// Staging layout: [B part(s), 2 bytes per element] [mean column, fp32] [coordinates, pair layout]
+// [split mode: column scales sc and their inverses, fp32].
+struct Staging {
+  size_t wp, xc, sc, total;
+};
+Staging staging_layout(int rows, int width, int kind) {
   const size_t ldp = gram_tc_packed_ld(rows);
   const int wtc = std::max(width - 1, 1);
   const size_t npad = (size_t)std::max(16, round_up(wtc, 16));
-  return ((npad * ldp * 2 + 255) & ~size_t(255)) + ((ldp * 4 + 255) & ~size_t(255)) + ldp * 16 + 256;
+  const size_t npart = kind == 1 ? 2 : 1;
+  Staging g;
+  g.wp = align256(npart * npad * ldp * 2);
+  g.xc = g.wp + align256(ldp * 4);
+  g.sc = g.xc + align256(ldp * 16);
+  g.total = g.sc + (kind == 1 ? align256(2 * npad * 4) : 0) + 256;
+  return g;
 }
 
-int gram_tc_pack_b(int kind, const float* B, int ldb, int rows, int cols, void* Bp, int ldp, cudaStream_t st) {
-  (void)kind;
-  const int wtc = cols - 1;
-  const int npad = std::max(16, round_up(std::max(wtc, 1), 16));
-  __nv_bfloat16* bp = reinterpret_cast<__nv_bfloat16*>(Bp);
-  float* wp = reinterpret_cast<float*>(reinterpret_cast<char*>(Bp) + (((size_t)npad * ldp * 2 + 255) & ~size_t(255)));
-  dim3 grid((ldp + 255) / 256, npad + 1);
-  k_pack_b<<<grid, 256, 0, st>>>(B, ldb, rows, wtc, npad, ldp, bp, wp);
-  note_launch();
-  return cudaGetLastError() == cudaSuccess ? 0 : 1;
+template <bool SPLIT>
+const void* kernel_for(int ker) {
+  return ker == 0 ? (const void*)k_gram_tc<0, SPLIT>
+                  : (ker == 1 ? (const void*)k_gram_tc<1, SPLIT> : (const void*)k_gram_tc<2, SPLIT>);
 }
 
-int gram_block_tc(int ker, int kind, const C4<float>* Xr, int nr, const C4<float>* Xc, int nc, const void* Bp, int ldp,
-                  int width, float sf2, float* Out, int ldo, int* err, cudaStream_t st) {
-  if (kind != 0) return 2;                 // bf16 only in this kernel
-  if (width < 2 || width > gram_tc_max_width() || nr <= 0 || nc <= 0) return 3;
-  if (ldp % BK != 0 || ldp < nc) return 4;
+template <bool SPLIT>
+int launch(int ker, const C4<float>* Xr, int nr, int nc, const void* Bp, int ldp, int width, float sf2, float* Out,
+           int ldo, int* err, cudaStream_t st) {
+  using M = Mode<SPLIT>;
   auto encode = encode_fn();
   if (!encode) return 5;
   const int wtc = width - 1;
-  const Layout L = plan_layout(wtc);
+  const Layout L = plan_layout<SPLIT>(wtc);
+  const Staging g = staging_layout(nc, width, SPLIT ? 1 : 0);
   const char* base = reinterpret_cast<const char*>(Bp);
-  const size_t boff = (((size_t)L.npad * ldp * 2 + 255) & ~size_t(255));
-  const float* wp = reinterpret_cast<const float*>(base + boff);
-  C4<float>* xcp = reinterpret_cast<C4<float>*>(const_cast<char*>(base) + boff + (((size_t)ldp * 4 + 255) & ~size_t(255)));
-  k_pad_coords<<<(ldp + 255) / 256, 256, 0, st>>>(Xc, nc, ldp, reinterpret_cast<float*>(xcp));
-  note_launch();
 
   CUtensorMap map;
-  cuuint64_t gdim[2] = {(cuuint64_t)ldp, (cuuint64_t)L.npad};
+  cuuint64_t gdim[2] = {(cuuint64_t)ldp, (cuuint64_t)M::NPART * L.npad};
   cuuint64_t gstride[1] = {(cuuint64_t)ldp * 2};
-  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)L.boxh};
+  cuuint32_t box[2] = {(cuuint32_t)M::BK, (cuuint32_t)L.boxh};
   cuuint32_t estr[2] = {1, 1};
-  CUresult cr = encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(Bp), gdim, gstride, box, estr,
-                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult cr = encode(&map, SPLIT ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                       const_cast<void*>(Bp), gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                       SPLIT ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
+                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (cr != CUDA_SUCCESS) return 6;
 
   TcParams P;
-  P.Xr = Xr; P.nr = nr; P.Xc = xcp; P.wcol = wp; P.nk = ldp / BK; P.ntiles = (nr + BM - 1) / BM; P.npad = L.npad;
+  P.Xr = Xr; P.nr = nr; P.Xc = reinterpret_cast<const C4<float>*>(base + g.xc);
+  P.wcol = reinterpret_cast<const float*>(base + g.wp);
+  P.binv = SPLIT ? reinterpret_cast<const float*>(base + g.sc) + L.npad : nullptr;
+  P.nk = ldp / M::BK; P.ntiles = (nr + BM - 1) / BM; P.npad = L.npad;
   P.nbox = L.nbox; P.boxh = L.boxh; P.wtc = wtc; P.sf2 = sf2; P.Out = Out; P.ldo = ldo; P.err = err;
   P.stages = L.stages; P.tmem_cols = L.tmem_cols; P.b_stage_bytes = L.b_stage_bytes;
 
-  const void* fn = ker == 0 ? (const void*)k_gram_tc<0> : (ker == 1 ? (const void*)k_gram_tc<1> : (const void*)k_gram_tc<2>);
+  const void* fn = kernel_for<SPLIT>(ker);
   cudaError_t ce = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
   if (ce != cudaSuccess) return 8;
   int per_sm = 0;
@@ -627,16 +737,48 @@ int gram_block_tc(int ker, int kind, const C4<float>* Xr, int nr, const C4<float
     ce = cudaMemset2DAsync(Out, (size_t)ldo * sizeof(float), 0, (size_t)nr * sizeof(float), (size_t)width, st);
     if (ce != cudaSuccess) return 10;
   }
-  switch (ker) {
-    case 0: k_gram_tc<0><<<grid, NTHREADS, L.smem, st>>>(map, P); break;
-    case 1: k_gram_tc<1><<<grid, NTHREADS, L.smem, st>>>(map, P); break;
-    default: k_gram_tc<2><<<grid, NTHREADS, L.smem, st>>>(map, P); break;
-  }
+  void* args[] = {&map, &P};
+  ce = cudaLaunchKernel(fn, dim3(grid), dim3(NTHREADS), args, L.smem, st);
   note_launch();
-  ce = cudaGetLastError();
-  return ce == cudaSuccess ? 0 : 7;
+  if (ce != cudaSuccess) { cudaGetLastError(); return 7; }
+  return 0;
 }
 
-size_t gram_tc_staging_bytes(int rows, int width) { return packed_bytes(rows, width); }
+}  // namespace
+
+size_t gram_tc_packed_ld(int rows) { return (size_t)round_up(std::max(rows, 1), BK_MAX); }
+int gram_tc_max_width() { return 513; }
+size_t gram_tc_staging_bytes(int rows, int width, int kind) { return staging_layout(rows, width, kind).total; }
+
+int gram_tc_pack_b(int kind, const float* B, int ldb, int rows, int cols, void* Bp, int ldp, cudaStream_t st) {
+  if (kind != 0 && kind != 1) return 2;
+  const int wtc = cols - 1;
+  const int npad = std::max(16, round_up(std::max(wtc, 1), 16));
+  const Staging g = staging_layout(rows, cols, kind);
+  char* base = reinterpret_cast<char*>(Bp);
+  float* wp = reinterpret_cast<float*>(base + g.wp);
+  float* sc = kind == 1 ? reinterpret_cast<float*>(base + g.sc) : nullptr;
+  if (kind == 1 && wtc > 0) {
+    k_col_scale<<<wtc, 256, 0, st>>>(B, ldb, rows, wtc, sc, sc + npad);
+    note_launch();
+  }
+  dim3 grid((ldp + 255) / 256, npad + 1);
+  k_pack_b<<<grid, 256, 0, st>>>(B, ldb, rows, wtc, npad, ldp, kind == 1, sc, Bp, wp);
+  note_launch();
+  return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
+int gram_block_tc(int ker, int kind, const C4<float>* Xr, int nr, const C4<float>* Xc, int nc, const void* Bp, int ldp,
+                  int width, float sf2, float* Out, int ldo, int* err, cudaStream_t st) {
+  if (kind != 0 && kind != 1) return 2;
+  if (width < 2 || width > gram_tc_max_width() || nr <= 0 || nc <= 0) return 3;
+  if (ldp % BK_MAX != 0 || ldp < nc) return 4;
+  const Staging g = staging_layout(nc, width, kind);
+  float* xcp = reinterpret_cast<float*>(reinterpret_cast<char*>(const_cast<void*>(Bp)) + g.xc);
+  k_pad_coords<<<(ldp + 255) / 256, 256, 0, st>>>(Xc, nc, ldp, xcp);
+  note_launch();
+  return kind == 1 ? launch<true>(ker, Xr, nr, nc, Bp, ldp, width, sf2, Out, ldo, err, st)
+                   : launch<false>(ker, Xr, nr, nc, Bp, ldp, width, sf2, Out, ldo, err, st);
+}
 
 }  // namespace cakf

@@ -118,15 +118,15 @@ int eig_sym_topk(double* A, int lda, int N, int nkeep, double* w, T* U, int ldu,
                  int* err, cudaStream_t st);
 
 // ---- tensor-core Gram x block (gram_tc.cu) ----
-// Out[nr x width] (FP32, column-major, ld = ldo) = K(Xr, Xc) B with B given as bf16 (or tf32
-// bits in fp32), column-major with ld = ldb (>= nc rounded to the tile).  kind: 0 = bf16, 1 = tf32.
+// Out[nr x width] (FP32, column-major, ld = ldo) = sf2 K(Xr, Xc) B with B packed by gram_tc_pack_b.
+// kind: 0 = BF16 operands (one MMA per slice), 1 = split BF16 (hi + lo parts, three MMAs).
 int gram_block_tc(int ker, int kind, const C4<float>* Xr, int nr, const C4<float>* Xc, int nc, const void* B, int ldb,
                   int width, float sf2, float* Out, int ldo, int* err, cudaStream_t st);
 // Convert a column-major float block (rows x cols, ld) into the operand layout of gram_block_tc.
 int gram_tc_pack_b(int kind, const float* B, int ldb, int rows, int cols, void* Bp, int ldp, cudaStream_t st);
 size_t gram_tc_packed_ld(int rows);
 int gram_tc_max_width();
-// Staging bytes (packed operand, mean column, padded coordinates) for a rows x width block.
-size_t gram_tc_staging_bytes(int rows, int width);
+// Staging bytes (packed operand part(s), mean column, padded coordinates) for a rows x width block.
+size_t gram_tc_staging_bytes(int rows, int width, int kind);
 
 }  // namespace cakf

@@ -6,7 +6,7 @@
 // Scratch layout inside g_noalloc_scratch (offsets 256-byte aligned):
 //   [0, 256)              device error flag (int), cleared on the call's stream before each use
 //   [256, 256 + coords)   (nr + nc) pre-scaled coordinate records, C4<double> or C4<float>
-//   [.., .. + staging)    BF16 path only: packed bf16 operand, fp32 last column, padded
+//   [.., .. + staging)    tensor-core paths only: packed bf16 operand part(s), fp32 last column, padded
 //                         coordinates (layout of gram_tc_pack_b / gram_block_tc)
 // Every byte the kernels read from the coordinate and staging regions is written earlier on
 // the same stream by the same call, so only the error flag has to start at zero.
@@ -70,10 +70,12 @@ extern "C" int cakf_gram_matmul_noalloc(int32_t kernel, double log_lx, double lo
   if (kernel < 0 || kernel > 2 || dim < 1 || dim > 3 || nr < 1 || nc < 1 || width < 1 || ldb < nc || ldo < nr)
     return err(CAKF_ERR_ARG, "cakf_gram_matmul_noalloc: invalid sizes or kernel");
   if (!Xr || !Xc || !B || !Out) return err(CAKF_ERR_ARG, "cakf_gram_matmul_noalloc: NULL pointer");
-  if (precision != CAKF_FP64 && precision != CAKF_FP32 && precision != CAKF_BF16)
-    return err(CAKF_ERR_ARG, "cakf_gram_matmul_noalloc: precision must be FP64, FP32 or BF16");
-  if (precision == CAKF_BF16 && (width < 2 || width > gram_tc_max_width()))
-    return err(CAKF_ERR_ARG, "cakf_gram_matmul_noalloc: the BF16 path needs 2 <= width <= 513");
+  if (precision != CAKF_FP64 && precision != CAKF_FP32 && precision != CAKF_BF16 && precision != CAKF_FP16X3)
+    return err(CAKF_ERR_ARG, "cakf_gram_matmul_noalloc: precision must be FP64, FP32, BF16 or FP16X3");
+  const bool tcp = precision == CAKF_BF16 || precision == CAKF_FP16X3;
+  const int kind = precision == CAKF_FP16X3 ? 1 : 0;
+  if (tcp && (width < 2 || width > gram_tc_max_width()))
+    return err(CAKF_ERR_ARG, "cakf_gram_matmul_noalloc: the tensor-core paths need 2 <= width <= 513");
   if (!std::isfinite(log_lx) || !std::isfinite(log_sf2))
     return err(CAKF_ERR_ARG, "cakf_gram_matmul_noalloc: non-finite hyperparameters");
 
@@ -81,7 +83,7 @@ extern "C" int cakf_gram_matmul_noalloc(int32_t kernel, double log_lx, double lo
   const size_t rec = precision == CAKF_FP64 ? sizeof(C4<double>) : sizeof(C4<float>);
   const size_t off_coords = 256;
   const size_t off_stage = off_coords + align256(((size_t)nr + (size_t)nc) * rec);
-  const size_t need = off_stage + (precision == CAKF_BF16 ? align256(gram_tc_staging_bytes(nc, width)) : 0);
+  const size_t need = off_stage + (tcp ? align256(gram_tc_staging_bytes(nc, width, kind)) : 0);
   if (need > kScratchBytes)
     return err(CAKF_ERR_ARG, "cakf_gram_matmul_noalloc: this call needs " + std::to_string(need) +
                                  " bytes of scratch but the static scratch holds " + std::to_string(kScratchBytes) +
@@ -115,8 +117,8 @@ extern "C" int cakf_gram_matmul_noalloc(int32_t kernel, double log_lx, double lo
     } else {
       void* stage = s + off_stage;
       const int ldp = (int)gram_tc_packed_ld(nc);
-      int r2 = gram_tc_pack_b(0, (const float*)B, ldb, nc, width, stage, ldp, st);
-      if (!r2) r2 = gram_block_tc(kernel, 0, xr, nr, xc, nc, stage, ldp, width, (float)sf2, (float*)Out, ldo, dflag, st);
+      int r2 = gram_tc_pack_b(kind, (const float*)B, ldb, nc, width, stage, ldp, st);
+      if (!r2) r2 = gram_block_tc(kernel, kind, xr, nr, xc, nc, stage, ldp, width, (float)sf2, (float*)Out, ldo, dflag, st);
       if (r2)
         return err(CAKF_ERR_CUDA, "cakf_gram_matmul_noalloc: tensor-core Gram x block launch failed (code " +
                                       std::to_string(r2) + ")");

@@ -1,0 +1,85 @@
+"""Parity at the full size of the 65,536-state sphere workload (n = 65,536, m = 8,192 per step,
+i = 64, r = 512), in the launch configuration bench.py times.
+
+* Step 1 of the filter against the FP64 oracle itself (the oracle finishes one step of this size in
+  well under a minute): means (normwise), variances (elementwise) and the NLL term, for the FP64,
+  FP32 and split-FP16 (x3) modes.
+* Three filter steps and the smoother pass of the FP32 and split-FP16 modes against the device FP64
+  mode, whose parity with the oracle is pinned at 1e-9 on the smaller cases of test_gpu_parity; the
+  properties that hold at any size: 0 < variance <= sigma_f^2, the smoother variance never above the
+  filter variance of the same step, finite NLL.
+
+Tolerances: FP64 mode 1e-9 (as on the small cases); FP32 and split FP16 1e-3 for means and
+variances (the accuracy target of the mixed-precision path), 1e-3 for the NLL.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2405_08971_gb300 as ck  # noqa: E402
+
+
+def mean_err(got, ref):
+    return max(float(np.linalg.norm(got[k] - ref[k]) / np.linalg.norm(ref[k])) for k in range(ref.shape[0]))
+
+
+def var_err(got, ref):
+    return float(np.max(np.abs(got - ref) / np.abs(ref)))
+
+
+def run_gpu(w, precision, smooth=True):
+    prob = ck.problem_from_workload(w, precision=precision)
+    ctx, mf, vf = ck.cakf_filter(prob)
+    out = dict(mf=mf, vf=vf, nll=ck.cakf_nll(ctx))
+    if smooth:
+        out["ms"], out["vs"] = ck.cakf_smooth(ctx)
+    ctx.close()
+    return out
+
+
+@pytest.fixture(scope="module")
+def step1():
+    w = synth.sphere_65k(T=1)
+    f = oracle.filter_run(w)
+    return w, f
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("fp32", 1e-3), ("fp16x3", 1e-3)])
+def test_step1_against_oracle(step1, precision, tol):
+    w, f = step1
+    got = run_gpu(w, precision, smooth=False)
+    e = dict(mf=mean_err(got["mf"][1:], f.m[1:]), vf=var_err(got["vf"][1:], f.var[1:]),
+             nll=abs(got["nll"] - oracle.nll_total(f)) / abs(oracle.nll_total(f)))
+    print(precision, {k: f"{v:.2e}" for k, v in e.items()})
+    for k, v in e.items():
+        assert v < tol, (k, v)
+
+
+@pytest.fixture(scope="module")
+def fp64_T3():
+    w = synth.sphere_65k(T=3)
+    return w, run_gpu(w, "fp64")
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16x3"])
+def test_three_steps_against_fp64_mode(fp64_T3, precision):
+    w, ref = fp64_T3
+    got = run_gpu(w, precision)
+    e = dict(mf=mean_err(got["mf"][1:], ref["mf"][1:]), vf=var_err(got["vf"], ref["vf"]),
+             ms=mean_err(got["ms"], ref["ms"]), vs=var_err(got["vs"], ref["vs"]),
+             nll=abs(got["nll"] - ref["nll"]) / abs(ref["nll"]))
+    print(precision, {k: f"{v:.2e}" for k, v in e.items()})
+    for k, v in e.items():
+        assert v < 1e-3, (k, v)
+    sf2 = float(np.exp(w.log_sf2))
+    for key in ("vf", "vs"):
+        assert np.all(got[key] > 0) and np.all(got[key] <= sf2 * (1 + 1e-6))
+    assert np.all(got["vs"][:-1] <= got["vf"][:-1] * (1 + 1e-5) + 1e-7)
+    assert np.isfinite(got["nll"])

@@ -12,6 +12,11 @@ persistent tensor-core grid splits tiles between CTAs.  Tolerances:
                FP32 accumulation-order rounding to the BF16 operand rounding; and within 3e-2 of
                the exact product (the bf16 rounding itself, ~2^-9 per operand);
                the last column is accumulated in FP32 on the CUDA cores: 2e-5 relative.
+  FP16X3      fp16 hi + lo parts of both operands (B scaled per column), three MMAs: within
+               1e-4 of the exact product.  The operand parts carry 22 bits (2^-22 per product
+               term); what remains is the tensor core's own FP32 accumulation, which measures
+               1e-6..2e-5 on these cases (the same order as the BF16 path's distance from its
+               exactly-accumulated BF16 emulation).
 """
 import math
 
@@ -70,6 +75,11 @@ def test_gram_matmul_all_precisions(nr, nc, width, dim, kernel):
     assert emu.max() < 2e-4, emu.max()
     assert ebf[:-1].max() < 3e-2, ebf[:-1].max()
     assert ebf[-1] < 2e-5, ebf[-1]
+    outx3 = ck.cakf_gram_matmul(kernel, llx, lsf2, tXr, tXc, torch.as_tensor(B, device=d), precision="fp16x3")
+    ex3 = colwise_rel(outx3.cpu().double().numpy(), ref)
+    print(f"   fp16x3 {ex3[:-1].max():.1e} last-col {ex3[-1]:.1e}")
+    assert ex3[:-1].max() < 1e-4, ex3[:-1].max()
+    assert ex3[-1] < 2e-5, ex3[-1]
 
 
 def test_gram_matmul_rejects_host_pointers():

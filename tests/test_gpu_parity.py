@@ -7,6 +7,12 @@ Tolerances (written per quantity):
              S^T G S and S^T S, as in the oracle).
   FP32 mode: the CG actions are chosen from FP32 residuals, so the projected subspace itself moves
              by ~1e-6; bounds of 1e-3 (means) and 2e-3 (variances) hold with a wide margin.
+  FP16X3 mode: the Gram x block products carry each operand as two FP16 parts (22 significant
+             bits, FP32 accumulation; the mean column stays FP32), the rest is the FP32 path: the
+             FP32 bounds (1e-3 means, 2e-3 variances, 1e-3 NLL).
+  (Plain BF16 rounds each operand to 2^-8 relative; variances near observed points, where the
+  posterior variance is a small difference of O(sf2) terms, then lose 1e-2..4e-1 relative on
+  these ill-conditioned cases, so that mode is checked at the kernel level in test_gpu_gram.)
 Where several results are correct (the factors are defined up to rotation), only products and
 diagonals are compared: means, marginal variances, NLL.
 """
@@ -151,3 +157,17 @@ def test_state_errors():
         ck.cakf_filter(bad, ctx)
     assert ei.value.code == ck.binding.ERR_ARG
     ctx.close()
+
+
+@pytest.mark.parametrize("name", ["grid2d-ragged-trunc", "sphere-m32-trunc", "missing-steps-m12"])
+def test_fp16x3_parity(name):
+    w = CASES[name]()
+    ref = run_oracle(w)
+    got = run_gpu(w, "fp16x3")
+    e = dict(mf=mean_err(got["mf"], ref["mf"]), vf=var_err(got["vf"], ref["vf"]),
+             ms=mean_err(got["ms"], ref["ms"]), vs=var_err(got["vs"], ref["vs"]),
+             nll=abs(got["nll"] - ref["nll"]) / abs(ref["nll"]))
+    print(name, "fp16x3", {k: f"{v:.2e}" for k, v in e.items()})
+    assert e["mf"] < 1e-3 and e["ms"] < 1e-3
+    assert e["vf"] < 2e-3 and e["vs"] < 2e-3
+    assert e["nll"] < 1e-3
