@@ -10,7 +10,12 @@ T * K / the slowest rank's timed region).  Multi-GPU runs are independent replic
 per rank, different seeds): the method's recursion is sequential in time and the paper runs on a
 single GPU, so there is no data-path collective.
 
-  python bench.py [--steps K] [--warmup W] [--precision bf16|tf32|fp32|fp64] [--T T] [--config NAME]
+The default precision is fp16x3 (Gram tiles x blocks on the tensor cores with split FP16 operands,
+FP32-class products: the mixed-precision mode that holds the 1e-3 relative error target on means
+and variances); bf16 is the single-MMA mode (faster, 2^-8 operand rounding), fp32 the plain SIMT
+path, fp64 the reference mode.
+
+  python bench.py [--steps K] [--warmup W] [--precision fp16x3|bf16|fp32|fp64] [--T T] [--config NAME]
   python bench.py --impl reference ...      # the FP64 oracle on the host cores (bounded sample)
 """
 from __future__ import annotations
@@ -39,7 +44,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="bf16", choices=list(DTYPE_NAME))
+    ap.add_argument("--precision", default="fp16x3", choices=list(DTYPE_NAME))
     ap.add_argument("--config", default="sphere-65k")
     ap.add_argument("--T", type=int, default=None, help="override the number of time steps")
     ap.add_argument("--no-e2e", action="store_true")
@@ -219,6 +224,7 @@ def main():
     prof = {"gram_block_ms": 0.0, "gram_block_launches": 0, "gram_block_flops": 0.0, "gram_block_evals": 0.0,
             "cg_matvec_ms": 0.0, "cg_matvec_launches": 0, "cg_matvec_evals": 0.0, "eig_ms": 0.0, "eig_calls": 0}
     phases = [0.0] * 8
+    eig_parts = [0.0] * 3
     for _ in range(args.steps):
         one_step()
         st = ck.cakf_get_stats(ctx)
@@ -226,6 +232,7 @@ def main():
         for k in prof:
             prof[k] += st[k]
         phases = [a + b for a, b in zip(phases, st["phase_ms"])]
+        eig_parts = [a + b for a, b in zip(eig_parts, st["eig_phase_ms"])]
     e1.record(stream)
     torch.cuda.synchronize(dev)
     clocks = sampler.stop()
@@ -272,7 +279,9 @@ def main():
         "gram_block_share_of_step": share,
         "cg_matvec": {"avg_ms": prof["cg_matvec_ms"] / max(1, prof["cg_matvec_launches"]),
                       "evals_per_launch": prof["cg_matvec_evals"] / max(1, prof["cg_matvec_launches"])},
-        "eig": {"calls": prof["eig_calls"], "avg_ms": prof["eig_ms"] / max(1, prof["eig_calls"])},
+        "eig": {"calls": prof["eig_calls"], "avg_ms": prof["eig_ms"] / max(1, prof["eig_calls"]),
+                "avg_ms_parts": dict(zip(["tridiagonalisation", "divide_conquer", "back_transform"],
+                                         [p / max(1, prof["eig_calls"]) for p in eig_parts]))},
         "phase_ms": {"filter": st["filter_ms"], "smooth": st["smooth_ms"]},
         "phase_ms_per_pass": dict(zip(["filter_cg", "filter_finalize", "filter_truncate", "smooth_gram",
                                        "smooth_combine", "smooth_truncate", "nll", "reserved"],

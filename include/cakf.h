@@ -116,6 +116,9 @@ typedef struct {
      [5] smoother truncation (Gram identities, FP64 eig, rotation)
      [6] NLL term per step                                      [7] reserved               */
   double phase_ms[8];
+  /* summed device time of the eigensolver's parts (profiling on): [0] tridiagonalisation,
+     [1] divide & conquer, [2] back-transformation and conversion of the kept vectors      */
+  double eig_phase_ms[3];
 } cakf_stats;
 
 /*
@@ -223,6 +226,19 @@ int cakf_gram_matmul(int32_t kernel, double log_lx, double log_sf2, int32_t dim,
 int cakf_gram_matmul_noalloc(int32_t kernel, double log_lx, double log_sf2, int32_t dim, const double* Xr,
                              int32_t nr, const double* Xc, int32_t nc, const void* B, int32_t ldb, int32_t width,
                              void* Out, int32_t ldo, int32_t precision, void* cuda_stream);
+
+/*
+ * cakf_eig_topk -- the FP64 symmetric eigensolver of Truncate (Sec. 3.2) on its own: the top
+ * `keep` eigenpairs of the N x N symmetric matrix A (the Gram M^T M of a downdate factor in the
+ * filter and smoother), the same device code the filter and smoother run.
+ *   A       DEVICE, N*N doubles, column-major (only read; a copy is factorised)
+ *   w_out   DEVICE, keep doubles: eigenvalues in descending order
+ *   U_out   DEVICE, N*keep doubles, column-major: the matching orthonormal eigenvectors
+ * Allocates and frees its workspace on every call (it is meant for verification and tools, not
+ * for the hot loop).  Errors: CAKF_ERR_ARG, CAKF_ERR_OOM, CAKF_ERR_CUDA, CAKF_ERR_TIMEOUT,
+ * CAKF_ERR_NUMERIC (secular iteration without convergence or non-finite values).
+ */
+int cakf_eig_topk(const double* A, int32_t N, int32_t keep, double* w_out, double* U_out, void* cuda_stream);
 
 /* cakf_get_stats -- timings and counters of the last filter / smooth calls (host output). */
 int cakf_get_stats(const cakf_ctx* ctx, cakf_stats* out);

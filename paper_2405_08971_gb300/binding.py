@@ -40,7 +40,7 @@ class cakf_stats(C.Structure):
         ("gram_block_launches", C.c_int64), ("gram_block_flops", C.c_double), ("gram_block_evals", C.c_double),
         ("cg_matvec_ms", C.c_double), ("cg_matvec_launches", C.c_int64), ("cg_matvec_evals", C.c_double),
         ("eig_ms", C.c_double), ("eig_calls", C.c_int64), ("kernel_launches", C.c_int64),
-        ("device_bytes", C.c_int64), ("phase_ms", C.c_double * 8),
+        ("device_bytes", C.c_int64), ("phase_ms", C.c_double * 8), ("eig_phase_ms", C.c_double * 3),
     ]
 
 
@@ -72,6 +72,8 @@ def lib():
                                        vp, C.c_int32, C.c_int32, vp, C.c_int32, C.c_int32, vp]
         L.cakf_gram_matmul.restype = C.c_int
         L.cakf_gram_matmul_noalloc.argtypes = L.cakf_gram_matmul.argtypes
+        L.cakf_eig_topk.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, vp]
+        L.cakf_eig_topk.restype = C.c_int
         L.cakf_gram_matmul_noalloc.restype = C.c_int
         L.cakf_free.argtypes = [vp]
         L.cakf_free.restype = None
@@ -259,6 +261,7 @@ def cakf_get_stats(ctx: Context) -> dict:
     _check(lib().cakf_get_stats(ctx.handle, C.byref(s)))
     out = {f: getattr(s, f) for f, _ in cakf_stats._fields_}
     out["phase_ms"] = list(out["phase_ms"])
+    out["eig_phase_ms"] = list(out["eig_phase_ms"])
     return out
 
 
@@ -302,6 +305,21 @@ def cakf_gram_matmul_noalloc(kernel, log_lx, log_sf2, Xr, Xc, B, out, precision=
                                           int(nr), Xc.data_ptr(), int(nc), B.data_ptr(), int(nc), int(width),
                                           out.data_ptr(), int(nr), prec, stream))
     return out
+
+
+def cakf_eig_topk(A, keep, stream=None):
+    """Top `keep` eigenpairs of the symmetric CUDA float64 tensor A (N x N) through the library's
+    FP64 eigensolver.  Returns (w, U): w descending (keep,), U with shape (keep, N) (column-major
+    N x keep, i.e. row q of U is the q-th eigenvector)."""
+    import torch
+    if A.dtype != torch.float64 or not A.is_cuda:
+        raise ValueError("cakf_eig_topk: A must be a CUDA float64 tensor")
+    N = A.shape[0]
+    Ac = A.t().contiguous()          # column-major copy (A is symmetric: same values)
+    w = torch.empty(keep, dtype=torch.float64, device=A.device)
+    U = torch.empty((keep, N), dtype=torch.float64, device=A.device)
+    _check(lib().cakf_eig_topk(Ac.data_ptr(), int(N), int(keep), w.data_ptr(), U.data_ptr(), stream))
+    return w, U
 
 
 def cakf_set_profiling(ctx: Context, on: bool):

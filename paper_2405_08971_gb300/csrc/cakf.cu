@@ -116,7 +116,7 @@ struct cakf_ctx {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bool profiling = false;
   cakf_stats stats{};
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_gb, prof_mv, prof_eig;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_gb, prof_mv, prof_eig, prof_eig_tri, prof_eig_dc, prof_eig_bt;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_phase;
   std::vector<double> prof_gb_flops, prof_gb_evals, prof_mv_evals;
   std::vector<cudaEvent_t> ev_pool;
@@ -544,9 +544,10 @@ struct Runner {
 
   // eigen-decomposition of the FP64 Gram G (N x N): top `keep` pairs -> wv, U64 (double), UT (T)
   int eig(double* G, int N, int keep) {
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (c->profiling) { e0 = c->ev(); e1 = c->ev(); cudaEventRecord(e0, st); }
-    int rc = eig_sym_topk<double>(G, N, N, keep, c->wv, c->U64, N, c->eigw, c->eigw_bytes, c->err, st);
+    cudaEvent_t e0 = nullptr, e1 = nullptr, mk[2] = {nullptr, nullptr};
+    if (c->profiling) { e0 = c->ev(); e1 = c->ev(); mk[0] = c->ev(); mk[1] = c->ev(); cudaEventRecord(e0, st); }
+    int rc = eig_sym_topk<double>(G, N, N, keep, c->wv, c->U64, N, c->eigw, c->eigw_bytes, c->err, st,
+                                  c->profiling ? mk : nullptr);
     if (rc) {
       cudaGetLastError();
       std::string why = rc >= 1000 ? cudaGetErrorString((cudaError_t)(rc - 1000)) : std::to_string(rc);
@@ -557,6 +558,9 @@ struct Runner {
       cudaEventRecord(e1, st);
       c->stats.eig_calls++;
       c->prof_eig.push_back({e0, e1});
+      c->prof_eig_tri.push_back({e0, mk[0]});
+      c->prof_eig_dc.push_back({mk[0], mk[1]});
+      c->prof_eig_bt.push_back({mk[1], e1});
     }
     return CAKF_OK;
   }
@@ -978,6 +982,9 @@ void collect_profile(cakf_ctx* c) {
   c->stats.cg_matvec_launches += (int64_t)c->prof_mv.size();
   for (double f : c->prof_mv_evals) c->stats.cg_matvec_evals += f;
   c->stats.eig_ms += sum(c->prof_eig);
+  c->stats.eig_phase_ms[0] += sum(c->prof_eig_tri);
+  c->stats.eig_phase_ms[1] += sum(c->prof_eig_dc);
+  c->stats.eig_phase_ms[2] += sum(c->prof_eig_bt);
   for (auto& ph : c->prof_phase) {
     float ms = 0;
     cudaEventElapsedTime(&ms, ph.second.first, ph.second.second);
@@ -986,6 +993,7 @@ void collect_profile(cakf_ctx* c) {
   c->prof_phase.clear();
   c->prof_gb.clear(); c->prof_gb_flops.clear(); c->prof_gb_evals.clear();
   c->prof_mv.clear(); c->prof_mv_evals.clear(); c->prof_eig.clear();
+  c->prof_eig_tri.clear(); c->prof_eig_dc.clear(); c->prof_eig_bt.clear();
   c->ev_used = 0;
 }
 
@@ -1248,6 +1256,36 @@ extern "C" int cakf_gram_matmul(int32_t kernel, double log_lx, double log_sf2, i
   if (e == kErrTimeout) return fail(CAKF_ERR_TIMEOUT, "cakf_gram_matmul: a device-side wait exceeded its limit");
   if (e) return fail(CAKF_ERR_NUMERIC, "cakf_gram_matmul: numeric error");
   (void)es;
+  return CAKF_OK;
+}
+
+extern "C" int cakf_eig_topk(const double* A, int32_t N, int32_t keep, double* w_out, double* U_out, void* cuda_stream) {
+  if (!A || !w_out || !U_out || N < 1 || keep < 1 || keep > N) return fail(CAKF_ERR_ARG, "cakf_eig_topk: invalid arguments");
+  if (!is_device_ptr(A) || !is_device_ptr(w_out) || !is_device_ptr(U_out))
+    return fail(CAKF_ERR_ARG, "cakf_eig_topk: all arrays must be device arrays");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const size_t wb = eig_workspace_bytes(N);
+  double* Aw = nullptr;
+  void* work = nullptr;
+  int* err = nullptr;
+  auto release = [&]() { if (Aw) cudaFree(Aw); if (work) cudaFree(work); if (err) cudaFree(err); };
+  if (cudaMalloc(&Aw, (size_t)N * N * sizeof(double)) != cudaSuccess || cudaMalloc(&work, wb) != cudaSuccess ||
+      cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    release();
+    return fail(CAKF_ERR_OOM, "cakf_eig_topk: workspace allocation failed");
+  }
+  cudaMemsetAsync(err, 0, sizeof(int), st);
+  cudaMemcpyAsync(Aw, A, (size_t)N * N * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  int rc = eig_sym_topk<double>(Aw, N, N, keep, w_out, U_out, N, work, wb, err, st);
+  cudaError_t ce = cudaStreamSynchronize(st);
+  int e = 0;
+  if (ce == cudaSuccess) cudaMemcpy(&e, err, sizeof(int), cudaMemcpyDeviceToHost);
+  release();
+  if (rc) return fail(CAKF_ERR_CUDA, "cakf_eig_topk: eigensolver launch failed (code " + std::to_string(rc) + ")");
+  if (ce != cudaSuccess) return fail(CAKF_ERR_CUDA, std::string("cakf_eig_topk: ") + cudaGetErrorString(ce));
+  if (e == kErrTimeout) return fail(CAKF_ERR_TIMEOUT, "cakf_eig_topk: a device-side wait exceeded its limit");
+  if (e) return fail(CAKF_ERR_NUMERIC, "cakf_eig_topk: numeric error");
   return CAKF_OK;
 }
 

@@ -198,7 +198,7 @@ k_tridiag(double* __restrict__ A, int lda, int N, double* __restrict__ d, double
 struct MergeDesc { int lo, mid, hi; };
 
 struct DcWork {
-  double *lam, *lamk, *lamtmp, *Dw, *Zw, *Dk, *Zk, *Dd, *Q, *Qtmp, *Delta, *rho, *rot, *z2;
+  double *lam, *lamk, *lamtmp, *Dw, *Zw, *Dk, *Zk, *Dd, *Q, *Qtmp, *Delta, *rho, *rot, *z2, *Tm;
   int *colk, *cold, *perm, *Kp, *nrot, *mergeof;
 };
 
@@ -604,32 +604,127 @@ k_dc_copy(const MergeDesc* __restrict__ merges, int N, DcWork W) {
   }
 }
 
-// Back-transformation of the top columns through the reflectors: one warp per output column.
-template <class T>
-__global__ void k_backtransform(const double* __restrict__ A, int lda, const double* __restrict__ tau, int N,
-                                const double* __restrict__ Q, const double* __restrict__ lam, int nkeep,
-                                double* __restrict__ w, T* __restrict__ U, int ldu) {
-  extern __shared__ double zs[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int c = blockIdx.x * (blockDim.x >> 5) + warp;
-  if (c >= nkeep) return;
-  double* z = zs + (size_t)warp * N;
-  const int src = N - 1 - c;
-  for (int t = lane; t < N; t += 32) z[t] = Q[(size_t)src * N + t];
-  __syncwarp();
-  for (int k = N - 3; k >= 0; --k) {
-    const double tk = tau[k];
-    if (tk == 0.0) continue;
-    const double* v = A + (size_t)k * lda + k + 1;
-    const int L = N - k - 1;
-    double acc = 0.0;
-    for (int t = lane; t < L; t += 32) acc += v[t] * z[k + 1 + t];
-    acc = warp_sum(acc) * tk;
-    for (int t = lane; t < L; t += 32) z[k + 1 + t] -= acc * v[t];
-    __syncwarp();
+// Back-transformation of the top columns through the reflectors, RB reflectors at a time in the
+// compact WY form: H_k0 H_k0+1 ... H_k0+RB-1 = I - V T V^T (V the RB reflectors, T upper
+// triangular).  A block owns CB output columns; per group it stages V in shared memory once for
+// all its columns, forms Y = V^T Z (RB x CB dots), Y <- T Y, and Z -= V Y.
+constexpr int RB = 8;
+constexpr int CB = 4;
+
+// T of every group (one warp per group): T_ii = tau_i, T[0:i, i] = -tau_i T[0:i, 0:i] V[:, 0:i]^T v_i.
+__global__ void k_bt_tmat(const double* __restrict__ A, int lda, const double* __restrict__ tau, int N,
+                          double* __restrict__ Tm) {
+  const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int nref = N - 2, ng = (nref + RB - 1) / RB;
+  if (g >= ng) return;
+  const int k0 = g * RB, nb = min(RB, nref - k0);
+  double vv[RB][RB];
+#pragma unroll
+  for (int a = 0; a < RB; ++a)
+#pragma unroll
+    for (int b = 0; b < RB; ++b) vv[a][b] = 0.0;
+  for (int b = 1; b < nb; ++b) {
+    const double* vb = A + (size_t)(k0 + b) * lda;
+    for (int a = 0; a < b; ++a) {
+      const double* va = A + (size_t)(k0 + a) * lda;
+      double acc = 0.0;
+      for (int row = k0 + b + 1 + lane; row < N; row += 32) acc = fma(va[row], vb[row], acc);
+      acc = warp_sum(acc);
+#pragma unroll
+      for (int aa = 0; aa < RB; ++aa)
+#pragma unroll
+        for (int bb = 0; bb < RB; ++bb)
+          if (aa == a && bb == b) vv[aa][bb] = acc;
+    }
   }
-  for (int t = lane; t < N; t += 32) U[(size_t)c * ldu + t] = T(z[t]);
-  if (lane == 0) w[c] = lam[src];
+  if (lane == 0) {
+    double T[RB][RB];
+#pragma unroll
+    for (int i = 0; i < RB; ++i)
+#pragma unroll
+      for (int j = 0; j < RB; ++j) T[i][j] = 0.0;
+#pragma unroll
+    for (int i = 0; i < RB; ++i) {
+      if (i < nb) {
+        const double ti = tau[k0 + i];
+        T[i][i] = ti;
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+          if (r < i) {
+            double acc = 0.0;
+#pragma unroll
+            for (int c = 0; c < RB; ++c)
+              if (c >= r && c < i) acc = fma(T[r][c], vv[c][i], acc);
+            T[r][i] = -ti * acc;
+          }
+        }
+      }
+    }
+    for (int i = 0; i < RB; ++i)
+      for (int j = 0; j < RB; ++j) Tm[(size_t)g * RB * RB + i * RB + j] = T[i][j];
+  }
+}
+
+// One block per CB output columns (descending eigenvalue order: column c holds Q[:, N-1-c]).
+template <class T>
+__global__ void __launch_bounds__(256)
+k_backtransform(const double* __restrict__ A, int lda, const double* __restrict__ Tm, int N,
+                const double* __restrict__ Q, const double* __restrict__ lam, int nkeep,
+                double* __restrict__ w, T* __restrict__ U, int ldu) {
+  extern __shared__ double bsm[];
+  double* Vs = bsm;                      // RB x N, the group's reflectors (zero outside support)
+  double* Z = bsm + (size_t)RB * N;      // CB x N, the columns being transformed
+  __shared__ double Y[RB][CB], Yt[RB][CB];
+  const int c0 = blockIdx.x * CB;
+  const int ncol = min(CB, nkeep - c0);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int e = threadIdx.x; e < CB * N; e += blockDim.x) {
+    const int c = e / N, t = e - c * N;
+    Z[e] = (c < ncol) ? Q[(size_t)(N - 1 - (c0 + c)) * N + t] : 0.0;
+  }
+  const int nref = N - 2, ng = (nref + RB - 1) / RB;
+  for (int g = ng - 1; g >= 0; --g) {
+    const int k0 = g * RB, nb = min(RB, nref - k0), r0 = k0 + 1, L = N - r0;
+    __syncthreads();
+    for (int e = threadIdx.x; e < RB * L; e += blockDim.x) {
+      const int a = e / L, row = r0 + (e - a * L);
+      Vs[(size_t)a * N + row] = (a < nb && row >= k0 + a + 1) ? A[(size_t)(k0 + a) * lda + row] : 0.0;
+    }
+    __syncthreads();
+    // Y = V^T Z: RB * CB dots, one warp per dot (round robin)
+    for (int p = warp; p < RB * CB; p += nw) {
+      const int a = p / CB, c = p - a * CB;
+      const double* va = Vs + (size_t)a * N;
+      const double* zc = Z + (size_t)c * N;
+      double acc = 0.0;
+      for (int row = r0 + lane; row < N; row += 32) acc = fma(va[row], zc[row], acc);
+      acc = warp_sum(acc);
+      if (lane == 0) Y[a][c] = acc;
+    }
+    __syncthreads();
+    // Yt = T Y (T upper triangular), then Z -= V Yt
+    if (threadIdx.x < RB * CB) {
+      const int i = threadIdx.x / CB, c = threadIdx.x - i * CB;
+      const double* Tg = Tm + (size_t)g * RB * RB + i * RB;
+      double acc = 0.0;
+      for (int j = i; j < RB; ++j) acc = fma(Tg[j], Y[j][c], acc);
+      Yt[i][c] = acc;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < CB * L; e += blockDim.x) {
+      const int c = e / L, row = r0 + (e - c * L);
+      double upd = 0.0;
+#pragma unroll
+      for (int a = 0; a < RB; ++a) upd = fma(Vs[(size_t)a * N + row], Yt[a][c], upd);
+      Z[(size_t)c * N + row] -= upd;
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < ncol * N; e += blockDim.x) {
+    const int c = e / N, t = e - c * N;
+    U[(size_t)(c0 + c) * ldu + t] = T(Z[e]);
+  }
+  if (threadIdx.x < ncol) w[c0 + threadIdx.x] = lam[N - 1 - (c0 + threadIdx.x)];
 }
 
 // ------------------------------------------------------------------------------------ host side
@@ -714,13 +809,14 @@ size_t eig_workspace_bytes(int nmax) {
   b += 3 * align_up(N * N * sizeof(double));      // Q, Qtmp, Delta
   b += 10 * align_up(N * sizeof(double));         // lam, lamk, lamtmp, Dw, Zw, Dk, Zk, Dd, rho, spare
   b += align_up(4 * N * sizeof(double));          // rot
+  b += align_up((N / RB + 2) * RB * RB * sizeof(double));   // back-transform T blocks
   b += 6 * align_up(N * sizeof(int));             // colk, cold, perm, Kp, nrot, spare
   return b + 4096;
 }
 
 template <class T>
 int eig_sym_topk(double* A, int lda, int N, int nkeep, double* w, T* U, int ldu, void* work, size_t work_bytes,
-                 int* err, cudaStream_t st) {
+                 int* err, cudaStream_t st, cudaEvent_t* marks) {
   if (N <= 0 || nkeep <= 0) return 0;
   if (nkeep > N) nkeep = N;
   if (work_bytes < eig_workspace_bytes(N)) return 1;
@@ -749,6 +845,7 @@ int eig_sym_topk(double* A, int lda, int N, int nkeep, double* w, T* U, int ldu,
   W.rho = (double*)take(N * sizeof(double));
   W.z2 = (double*)take(N * sizeof(double));
   W.rot = (double*)take(4 * N * sizeof(double));
+  W.Tm = (double*)take(((size_t)N / RB + 2) * RB * RB * sizeof(double));
   W.colk = (int*)take(N * sizeof(int));
   W.cold = (int*)take(N * sizeof(int));
   W.perm = (int*)take(N * sizeof(int));
@@ -783,6 +880,7 @@ int eig_sym_topk(double* A, int lda, int N, int nkeep, double* w, T* U, int ldu,
     note_launch();
     if (ce != cudaSuccess) return 1000 + (int)ce;
   }
+  if (marks) cudaEventRecord(marks[0], st);
   // 2. divide and conquer
   k_dc_init<<<(N + 255) / 256, 256, 0, st>>>(d, e, N, W.lam, W.Q); note_launch();
   const Plan& pl = pe->plan;
@@ -796,7 +894,7 @@ int eig_sym_topk(double* A, int lda, int N, int nkeep, double* w, T* U, int ldu,
     int kmax = 0;
     for (int q = m0; q < m1; ++q) kmax = std::max(kmax, pl.merges[q].hi - pl.merges[q].lo);
     const size_t psmem = (size_t)kmax * (8 * sizeof(double) + 3 * sizeof(int));
-    if (psmem > 48 * 1024) cudaFuncSetAttribute(k_dc_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
+    if (psmem > 40 * 1024) cudaFuncSetAttribute(k_dc_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
     k_dc_prep<<<nm, 256, psmem, st>>>(dm, e, N, W); note_launch();
     k_dc_secular<<<(N * 32 + 255) / 256, 256, 0, st>>>(dm, dmo, N, W, err); note_launch();
     k_dc_zhat<<<(N * 32 + 255) / 256, 256, 0, st>>>(dm, dmo, N, W); note_launch();
@@ -804,21 +902,27 @@ int eig_sym_topk(double* A, int lda, int N, int nkeep, double* w, T* U, int ldu,
     dim3 gg((kmax + DG_T - 1) / DG_T, (kmax + DG_T - 1) / DG_T, nm);
     k_dc_gemm<<<gg, 256, 0, st>>>(dm, N, W); note_launch();
     const size_t fsmem = (size_t)kmax * (2 * sizeof(double) + 2 * sizeof(int));
-    if (fsmem > 48 * 1024) cudaFuncSetAttribute(k_dc_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
+    if (fsmem > 40 * 1024) cudaFuncSetAttribute(k_dc_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
     k_dc_finish<<<nm, 256, fsmem, st>>>(dm, N, W); note_launch();
     k_dc_copy<<<dim3((kmax + 7) / 8, nm), 256, 0, st>>>(dm, N, W); note_launch();
   }
+  if (marks) cudaEventRecord(marks[1], st);
   // 3. back-transformation of the top nkeep columns (descending eigenvalues)
   {
-    const int wpb = 2;   // 2 warps (columns) per block: the blocks spread over all SMs' FP64 units
-    size_t smem = (size_t)wpb * N * sizeof(double);
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k_backtransform<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_backtransform<T><<<(nkeep + wpb - 1) / wpb, 32 * wpb, smem, st>>>(A, lda, tau, N, W.Q, W.lam, nkeep, w, U, ldu); note_launch();
+    const int ng = std::max(1, (N - 2 + RB - 1) / RB);
+    if (N >= 3) {
+      k_bt_tmat<<<(ng * 32 + 255) / 256, 256, 0, st>>>(A, lda, tau, N, W.Tm); note_launch();
+    }
+    const size_t smem = (size_t)(RB + CB) * N * sizeof(double);
+    if (smem > 40 * 1024) cudaFuncSetAttribute(k_backtransform<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_backtransform<T><<<(nkeep + CB - 1) / CB, 256, smem, st>>>(A, lda, W.Tm, N, W.Q, W.lam, nkeep, w, U, ldu); note_launch();
   }
   return cudaGetLastError() == cudaSuccess ? 0 : 4;
 }
 
-template int eig_sym_topk<float>(double*, int, int, int, double*, float*, int, void*, size_t, int*, cudaStream_t);
-template int eig_sym_topk<double>(double*, int, int, int, double*, double*, int, void*, size_t, int*, cudaStream_t);
+template int eig_sym_topk<float>(double*, int, int, int, double*, float*, int, void*, size_t, int*, cudaStream_t,
+                                  cudaEvent_t*);
+template int eig_sym_topk<double>(double*, int, int, int, double*, double*, int, void*, size_t, int*, cudaStream_t,
+                                   cudaEvent_t*);
 
 }  // namespace cakf

@@ -113,9 +113,10 @@ size_t eig_workspace_bytes(int nmax);
 // Top-`nkeep` eigenpairs of the symmetric N x N matrix A (FP64, column-major, lda >= N; A is
 // overwritten).  w: nkeep eigenvalues, descending (device).  U: N x nkeep eigenvectors
 // (column-major, ld = ldu) in precision T.  err: device flag raised on timeout / non-finite.
+// marks: NULL, or two events recorded after the tridiagonalisation and after divide & conquer.
 template <class T>
 int eig_sym_topk(double* A, int lda, int N, int nkeep, double* w, T* U, int ldu, void* work, size_t work_bytes,
-                 int* err, cudaStream_t st);
+                 int* err, cudaStream_t st, cudaEvent_t* marks = nullptr);
 
 // ---- tensor-core Gram x block (gram_tc.cu) ----
 // Out[nr x width] (FP32, column-major, ld = ldo) = sf2 K(Xr, Xc) B with B packed by gram_tc_pack_b.

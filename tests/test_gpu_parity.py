@@ -81,6 +81,16 @@ CASES = {
                                                  kernel=synth.MATERN52),
 }
 
+# Truncation Grams of order 512 (r + i = 448 + 64): the eigensolver's larger shared-memory
+# configurations.  Checked with the oracle's actions replayed: 64 CG iterations amplify FP64
+# rounding differences in the action directions to ~1e-9 (means) / ~1e-7 (variances) even on this
+# well-determined problem (relative CG residual ~1e-3 after 64 iterations), so the device-chosen
+# actions are not a 1e-9 pin of the truncation path; the replayed ones are.
+LARGE = {
+    "large-rank-trunc": lambda: synth.small(n=2000, dim=2, m=1000, T=9, budget_i=64, rank_r=448, seed=35,
+                                            lx=0.05),
+}
+
 
 @pytest.mark.parametrize("name", list(CASES))
 def test_fp64_parity(name):
@@ -96,10 +106,10 @@ def test_fp64_parity(name):
         assert v < 1e-9, (k, v)
 
 
-@pytest.mark.parametrize("name", ["grid2d-ragged-trunc", "sphere-m32-trunc"])
+@pytest.mark.parametrize("name", ["grid2d-ragged-trunc", "sphere-m32-trunc", "large-rank-trunc"])
 def test_fp64_replayed_actions(name):
     """With the oracle's actions replayed, the device update is Alg. 2 on the same subspace."""
-    w = CASES[name]()
+    w = {**CASES, **LARGE}[name]()
     ref = run_oracle(w)
     flat, counts = ck.pack_actions(ref["S"], w.T)
     got = run_gpu(w, "fp64", replay=(flat, counts))
