@@ -45,15 +45,17 @@ __device__ __forceinline__ bool mono_barrier(unsigned* count, unsigned target, i
   __shared__ int s_ok;
   if (threadIdx.x == 0) {
     int ok = 1;
-    __threadfence();
-    atomicAdd(count, 1u);
-    const volatile unsigned* vc = count;
+    // release: the block's writes (ordered before this thread by the barrier above) become visible
+    // to any block whose acquiring read sees this arrival
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
     long long spins = 0;
-    while (*vc < target) {
+    unsigned v;
+    while (true) {
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+      if (v >= target) break;
       if (++spins > limit) { atomicExch(err, kErrTimeout); ok = 0; break; }
       if ((spins & 1023) == 0 && *(volatile int*)err) { ok = 0; break; }
     }
-    __threadfence();
     s_ok = ok;
   }
   __syncthreads();
@@ -62,44 +64,48 @@ __device__ __forceinline__ bool mono_barrier(unsigned* count, unsigned target, i
 
 // ---------------------------------------------------------------------------------- tridiagonal
 // Householder tridiagonalisation (lower), one grid barrier per column.  Columns of the trailing
-// block are owned by (block, warp) round-robin.  At step k every block knows v_k, tau_k (computed
-// redundantly) and reads p_k = tau_k A22 v_k and the pre-update pivot column k+1 from double
-// buffers written before the barrier; it then forms w_k, the updated column k+1 and from it
-// v_{k+1}, tau_{k+1}; the owners update their columns and, in the same pass, compute the entries
-// of p_{k+1} and publish the next pivot column.  Reflector v_k is stored in column k below the
-// subdiagonal (v_k[0] = 1).
-__device__ __forceinline__ void householder(const double* x, int L, double* v, double& tau, double& beta) {
-  // x (smem, length L) -> v (smem) with v[0] = 1, H = I - tau v v^T, H x = beta e_1
-  double ss = 0.0;
-  for (int t = threadIdx.x; t < L; t += blockDim.x) if (t > 0) ss += x[t] * x[t];
-  const double sigma = block_sum(ss);
-  const double alpha = x[0];
-  double scal;
-  if (sigma == 0.0) { tau = 0.0; beta = alpha; scal = 0.0; }
-  else {
-    beta = -copysign(sqrt(alpha * alpha + sigma), alpha);
-    tau = (beta - alpha) / beta;
-    scal = 1.0 / (alpha - beta);
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < L; t += blockDim.x) v[t] = (t == 0) ? 1.0 : x[t] * scal;
-  __syncthreads();
+// block are owned by (block, warp) round-robin and stay resident in shared memory.  At step k every
+// block reads p_k = tau_k A22 v_k and the pre-update pivot column k+1 from double buffers written
+// before the barrier, forms w_k = p_k - 1/2 tau_k (p_k . v_k) v_k, the updated pivot column and
+// from it v_{k+1}, tau_{k+1} (all redundantly, so no second barrier is needed); the owners then
+// update their columns and, in the same pass, compute their entries of p_{k+1} and publish the
+// next pivot column.  Reflector v_k is stored in column k below the subdiagonal (v_k[0] = 1).
+// Block reductions go through shared memory and one warp (the FP64 pipe is narrow on this GPU, so
+// a shuffle tree in every warp would cost more than the data it sums).
+constexpr int TD_THREADS = 128;
+
+// Householder scalars for x (x[0] = alpha, sum of the squares of x[1..] = sigma): H x = beta e_1,
+// H = I - tau v v^T with v[0] = 1 and v[t] = x[t] * scal.
+__device__ __forceinline__ void house_scalars(double alpha, double sigma, double& tau, double& beta, double& scal) {
+  if (sigma == 0.0) { tau = 0.0; beta = alpha; scal = 0.0; return; }
+  beta = -copysign(sqrt(alpha * alpha + sigma), alpha);
+  tau = (beta - alpha) / beta;
+  scal = 1.0 / (alpha - beta);
 }
 
-__global__ void __launch_bounds__(256)
+// Sum of red[0 .. blockDim.x) by warp 0 (called by warp 0 only); the result is in every lane.
+__device__ __forceinline__ double warp0_sum(const double* red) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int i = lane; i < (int)blockDim.x; i += 32) s += red[i];
+  return warp_sum(s);
+}
+
+__global__ void __launch_bounds__(TD_THREADS)
 k_tridiag(double* __restrict__ A, int lda, int N, double* __restrict__ d, double* __restrict__ e,
           double* __restrict__ tau, double* __restrict__ Pbuf, double* __restrict__ Cbuf, unsigned* bar, int* err) {
   extern __shared__ double sm[];
-  double* v = sm;            // v_k
-  double* v2 = sm + N;       // v_{k+1}
-  double* w = sm + 2 * N;    // w_k
-  double* c = sm + 3 * N;    // updated pivot column
-  double* cols = sm + 4 * N; // owned columns (full length N), resident for the whole reduction
-  const int G = gridDim.x;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  // sm[0, N) and sm[N, 2N): v_k and v_{k+1}, swapped every step
+  double* w = sm + 2 * N;           // w_k
+  double* c = sm + 3 * N;           // updated pivot column k+1
+  double* cols = sm + 4 * N;        // owned columns (full length N), resident for the whole reduction
+  __shared__ double red[TD_THREADS];
+  __shared__ double bc[4];          // broadcast scalars
+  const int G = gridDim.x, tid = threadIdx.x, TB = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nw = TB >> 5;
   const int nslot = (N + G - 1) / G;   // column j lives in block j % G, slot j / G
   if (N <= 2) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (blockIdx.x == 0 && tid == 0) {
       d[0] = A[0];
       if (N == 2) { e[0] = A[1]; d[1] = A[(size_t)lda + 1]; tau[0] = 0.0; }
     }
@@ -108,26 +114,45 @@ k_tridiag(double* __restrict__ A, int lda, int N, double* __restrict__ d, double
   for (int q = 0; q < nslot; ++q) {
     const int j = q * G + blockIdx.x;
     if (j >= N) break;
-    for (int t = threadIdx.x; t < N; t += blockDim.x) cols[(size_t)q * N + t] = A[(size_t)j * lda + t];
+    for (int t = tid; t < N; t += TB) cols[(size_t)q * N + t] = A[(size_t)j * lda + t];
   }
   // ---- prologue: v_0 from column 0; p_0; publish column 1
   double tk, bk;
   {
     const int L = N - 1;
-    for (int t = threadIdx.x; t < L; t += blockDim.x) c[t] = A[1 + t];
+    double part = 0.0;
+    for (int t = tid; t < L; t += TB) {
+      const double x = A[1 + t];
+      c[t] = x;
+      if (t >= 1) part = fma(x, x, part);
+    }
+    red[tid] = part;
     __syncthreads();
-    householder(c, L, v, tk, bk);
+    if (warp == 0) {
+      const double sigma = warp0_sum(red);
+      if (lane == 0) {
+        double ta, be, sc;
+        house_scalars(c[0], sigma, ta, be, sc);
+        bc[0] = ta; bc[1] = be; bc[2] = sc;
+      }
+    }
+    __syncthreads();
+    tk = bc[0]; bk = bc[1];
+    const double sc = bc[2];
+    double* v = sm;
+    for (int t = tid; t < L; t += TB) v[t] = (t == 0) ? 1.0 : c[t] * sc;
+    __syncthreads();
     for (int q = warp; q < nslot; q += nw) {
       const int j = q * G + blockIdx.x;
       if (j < 1 || j >= N) continue;
       const double* col = cols + (size_t)q * N + 1;
       double acc = 0.0;
-      for (int t = lane; t < L; t += 32) acc += col[t] * v[t];
+      for (int t = lane; t < L; t += 32) acc = fma(col[t], v[t], acc);
       acc = warp_sum(acc);
       if (lane == 0) Pbuf[j - 1] = tk * acc;
       if (j == 1) for (int t = lane; t < L; t += 32) Cbuf[t] = col[t];
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) d[0] = A[0];
+    if (blockIdx.x == 0 && tid == 0) d[0] = A[0];
     if (!mono_barrier(bar, (unsigned)G, err)) return;
   }
   unsigned nbar = 1;
@@ -137,29 +162,61 @@ k_tridiag(double* __restrict__ A, int lda, int N, double* __restrict__ d, double
     double* Pn = Pbuf + (size_t)((k + 1) & 1) * N;
     const double* Ck = Cbuf + (size_t)(k & 1) * N;
     double* Cn = Cbuf + (size_t)((k + 1) & 1) * N;
-    // (1) w_k = p_k - 1/2 tau_k (p_k . v_k) v_k ; (2) updated pivot column k+1
-    double pv = 0.0;
-    for (int t = threadIdx.x; t < L; t += blockDim.x) {
-      const double pt = __ldcg(Pk + t);
-      w[t] = pt;
-      pv += pt * v[t];
-    }
-    pv = block_sum(pv);
-    const double kc = 0.5 * tk * pv;
-    for (int t = threadIdx.x; t < L; t += blockDim.x) w[t] -= kc * v[t];
-    __syncthreads();
-    for (int t = threadIdx.x; t < L; t += blockDim.x) c[t] = __ldcg(Ck + t) - v[t] * w[0] - w[t] * v[0];
-    __syncthreads();
+    const double* v = sm + (size_t)(k & 1) * N;
+    double* v2 = sm + (size_t)((k + 1) & 1) * N;
     const bool next = (k + 3 < N);      // a reflector for column k+1 exists
-    double tn = 0.0, bn = 0.0;
-    if (next) householder(c + 1, L - 1, v2, tn, bn);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      d[k + 1] = c[0];
-      e[k] = bk;
-      tau[k] = tk;
-      if (!next) { e[k + 1] = c[1]; tau[k + 1] = 0.0; }
+    // (1) p_k . v_k; the pivot column C_k is fetched in the same pass (into c)
+    double part = 0.0;
+    for (int t = tid; t < L; t += TB) {
+      const double pt = __ldcg(Pk + t);
+      c[t] = __ldcg(Ck + t);
+      w[t] = pt;
+      part = fma(pt, v[t], part);
     }
-    // (3) owned columns: A22 -= v w^T + w v^T (rows k+1..), fused dot for p_{k+1}, publish column k+2
+    red[tid] = part;
+    __syncthreads();
+    if (warp == 0) {
+      const double pv = warp0_sum(red);
+      if (lane == 0) {
+        const double kc = 0.5 * tk * pv;
+        bc[0] = kc;
+        bc[1] = w[0] - kc;               // w_k[0] (v_k[0] = 1)
+      }
+    }
+    __syncthreads();
+    const double kc = bc[0], w0 = bc[1];
+    // (2) w_k and the updated pivot column c = C_k - v w0 - w v0 (v0 = 1); sum of squares of c[2..]
+    part = 0.0;
+    for (int t = tid; t < L; t += TB) {
+      const double wt = fma(-kc, v[t], w[t]);
+      w[t] = wt;
+      const double ct = fma(-v[t], w0, c[t]) - wt;
+      c[t] = ct;
+      if (t >= 2) part = fma(ct, ct, part);
+    }
+    red[tid] = part;
+    __syncthreads();
+    if (warp == 0) {
+      const double sigma = warp0_sum(red);
+      if (lane == 0) {
+        double ta = 0.0, be = 0.0, sc = 0.0;
+        if (next) house_scalars(c[1], sigma, ta, be, sc);
+        bc[2] = ta; bc[3] = be; red[0] = sc;
+        if (blockIdx.x == 0) {
+          d[k + 1] = c[0];
+          e[k] = bk;
+          tau[k] = tk;
+          if (!next) { e[k + 1] = c[1]; tau[k + 1] = 0.0; }
+        }
+      }
+    }
+    __syncthreads();
+    const double tn = bc[2], bn = bc[3], scn = red[0];
+    // (3) v_{k+1}
+    if (next)
+      for (int t = tid; t < L - 1; t += TB) v2[t] = (t == 0) ? 1.0 : c[t + 1] * scn;
+    __syncthreads();
+    // (4) owned columns: A22 -= v w^T + w v^T (rows k+1..), fused dot for p_{k+1}, publish column k+2
     for (int q = warp; q < nslot; q += nw) {
       const int j = q * G + blockIdx.x;
       if (j < k + 1 || j >= N) continue;
@@ -169,9 +226,9 @@ k_tridiag(double* __restrict__ A, int lda, int N, double* __restrict__ d, double
       const bool publish = next && tj == 1;       // column k+2 becomes the next pivot column
       double acc = 0.0;
       for (int t = lane; t < L; t += 32) {
-        const double nv = col[t] - (v[t] * wj + w[t] * vj);
+        const double nv = fma(-v[t], wj, fma(-w[t], vj, col[t]));
         col[t] = nv;
-        if (next && t >= 1) acc += nv * v2[t - 1];
+        if (next && t >= 1) acc = fma(nv, v2[t - 1], acc);
         if (publish && t >= 1) Cn[t - 1] = nv;
       }
       if (next && tj >= 1) {
@@ -183,11 +240,9 @@ k_tridiag(double* __restrict__ A, int lda, int N, double* __restrict__ d, double
         if (lane == 0) d[N - 1] = col[L - 1];
       }
     }
-    // (4) store the reflector v_k below the subdiagonal of column k (for the back-transformation)
+    // (5) store the reflector v_k below the subdiagonal of column k (for the back-transformation)
     if (blockIdx.x == 0)
-      for (int t = threadIdx.x; t < L; t += blockDim.x) A[(size_t)k * lda + k + 1 + t] = v[t];
-    __syncthreads();
-    for (int t = threadIdx.x; t < L - 1; t += blockDim.x) v[t] = v2[t];
+      for (int t = tid; t < L; t += TB) A[(size_t)k * lda + k + 1 + t] = v[t];
     tk = tn;
     bk = bn;
     if (!mono_barrier(bar, (unsigned)G * ++nbar, err)) return;
@@ -870,13 +925,13 @@ int eig_sym_topk(double* A, int lda, int N, int nkeep, double* w, T* U, int ldu,
       smem = (4 + (size_t)nslot) * N * sizeof(double);
       cudaFuncSetAttribute(k_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 48 * 1024));
       int occ = 0;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tridiag, 256, smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tridiag, TD_THREADS, smem);
       if ((long long)occ * nsm >= G) break;
       G = std::max(1, occ * nsm);     // fewer blocks own more columns each
       if (occ == 0) { cudaGetLastError(); return 1000 + (int)cudaErrorCooperativeLaunchTooLarge; }
     }
     void* args[] = {&A, &lda, &N, &d, &e, &tau, &P, &Cb, &bar, &err};
-    cudaError_t ce = cudaLaunchCooperativeKernel((void*)k_tridiag, dim3(G), dim3(256), args, smem, st);
+    cudaError_t ce = cudaLaunchCooperativeKernel((void*)k_tridiag, dim3(G), dim3(TD_THREADS), args, smem, st);
     note_launch();
     if (ce != cudaSuccess) return 1000 + (int)ce;
   }
