@@ -225,6 +225,7 @@ def main():
             "cg_matvec_ms": 0.0, "cg_matvec_launches": 0, "cg_matvec_evals": 0.0, "eig_ms": 0.0, "eig_calls": 0}
     phases = [0.0] * 8
     eig_parts = [0.0] * 3
+    eig_flops = [0.0] * 2
     for _ in range(args.steps):
         one_step()
         st = ck.cakf_get_stats(ctx)
@@ -233,6 +234,8 @@ def main():
             prof[k] += st[k]
         phases = [a + b for a, b in zip(phases, st["phase_ms"])]
         eig_parts = [a + b for a, b in zip(eig_parts, st["eig_phase_ms"])]
+        eig_flops = [a + b for a, b in zip(eig_flops, st["eig_flops"])]
+    phases_launches_cg = 8.0   # the matvec is timed on every 8th CG iteration: total ~ 8 x the sampled time
     e1.record(stream)
     torch.cuda.synchronize(dev)
     clocks = sampler.stop()
@@ -241,29 +244,53 @@ def main():
     ms_max = allmax(ws, ms)
     value = ws * T * args.steps / (ms_max / 1e3)
 
-    # ---- roofline of the dominant kernel (Gram x block), from live CUDA events
+    # ---- rooflines from live CUDA events (per kernel class), the dominant one reported as `roofline`
     pk, pk_src = peaks()
-    gb_avg_ms = prof["gram_block_ms"] / max(1, prof["gram_block_launches"])
-    flops_per_launch = prof["gram_block_flops"] / max(1, prof["gram_block_launches"])
-    achieved = flops_per_launch / (gb_avg_ms / 1e3) / 1e12
-    if args.precision in ("bf16", "fp16x3"):
-        peak = float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops")))
-        mmas = 3 if args.precision == "fp16x3" else 1
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "kernel": "k_gram_tc (filter finalize + smoother P^- X)",
-                "peak_source": f"{pk_src} bf16_tflops_sustained",
-                "tensor_mmas_per_algorithmic_flop": mmas}
-    else:
-        clk = (clocks.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)) * 1e6
-        lanes = 128 if args.precision == "fp32" else 4
-        peak = 152 * lanes * 2 * clk / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "gram_block_simt",
-                "peak_source": f"152 SMs x {lanes} {'FP32' if lanes == 128 else 'FP64'} FMA/clk x 2 x median SM clock"}
-    roof["launches"] = prof["gram_block_launches"]
-    roof["avg_ms"] = gb_avg_ms
-    share = prof["gram_block_ms"] / ms if ms > 0 else None
+    clk_mhz = clocks.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
+    clk = clk_mhz * 1e6
+    nsm = 152
+    fp64_peak = nsm * 2 * 2 * clk / 1e12          # 2 FP64 FMA per clock per SM
+    mufu_peak = nsm * 16 * clk / 1e12             # 16 MUFU results per clock per SM (T ops/s)
+    peak_note = f"derived: {nsm} SMs x {{}} x median SM clock {clk_mhz:.0f} MHz"
+    kernels = {}
+    # FP64 tridiagonalisation (the eigensolver's dominant part): (4/3) N^3 flops per call
+    tri_ms = eig_parts[0]
+    if prof["eig_calls"] and tri_ms > 0:
+        ach = eig_flops[0] / (tri_ms / 1e3) / 1e12
+        kernels["k_tridiag"] = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                                "frac": ach / fp64_peak, "traffic": None,
+                                "peak_source": peak_note.format("2 FP64 FMA/clk x 2"),
+                                "launches": prof["eig_calls"], "avg_ms": tri_ms / prof["eig_calls"],
+                                "ms_total": tri_ms,
+                                "note": "one grid barrier per Householder column: bound by barrier latency, not by FP64"}
+    # tensor-core / SIMT Gram x block (filter finalize): kernel entries on MUFU (sqrt + exp2 each)
+    if prof["gram_block_launches"]:
+        gb_ms = prof["gram_block_ms"]
+        evals = prof["gram_block_evals"] / (gb_ms / 1e3) / 1e12
+        tfl = prof["gram_block_flops"] / (gb_ms / 1e3) / 1e12
+        ent = {"bound": "alu", "achieved": 2 * evals, "peak": mufu_peak, "unit": "TMUFU-op/s",
+               "frac": 2 * evals / mufu_peak, "traffic": None, "peak_source": peak_note.format("16 MUFU/clk"),
+               "launches": prof["gram_block_launches"], "avg_ms": gb_ms / prof["gram_block_launches"],
+               "ms_total": gb_ms, "tensor_tflops": tfl}
+        if args.precision in ("bf16", "fp16x3"):
+            tpk = float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops")))
+            mmas = 3 if args.precision == "fp16x3" else 1
+            ent["tensor_frac"] = mmas * tfl / tpk
+            ent["tensor_peak_source"] = f"{pk_src} bf16_tflops_sustained; {mmas} MMA(s) per algorithmic flop"
+        kernels["k_gram_tc" if args.precision in ("bf16", "fp16x3") else "k_gram_block_simt"] = ent
+    # CG Gram matvec (sampled every 8th iteration): m^2 kernel entries per launch on MUFU
+    if prof["cg_matvec_launches"]:
+        mv_ms = prof["cg_matvec_ms"]
+        evals = prof["cg_matvec_evals"] / (mv_ms / 1e3) / 1e12
+        kernels["k_gram_matvec"] = {"bound": "alu", "achieved": 2 * evals, "peak": mufu_peak,
+                                    "unit": "TMUFU-op/s", "frac": 2 * evals / mufu_peak, "traffic": None,
+                                    "peak_source": peak_note.format("16 MUFU/clk"),
+                                    "launches_sampled": prof["cg_matvec_launches"],
+                                    "avg_ms": mv_ms / prof["cg_matvec_launches"],
+                                    "ms_total": mv_ms * phases_launches_cg}
+    dominant = max(kernels, key=lambda k: kernels[k]["ms_total"]) if kernels else None
+    roof = dict(kernels[dominant], kernel=dominant) if dominant else None
+    share = roof["ms_total"] / ms if roof and ms > 0 else None
 
     line = {
         "metric": "filter+smoother time steps/sec",
@@ -276,7 +303,8 @@ def main():
                    "l2": "working set larger than L2 (stored factors ~%.0f GB)" % (
                        (n * (w.rank_r + w.budget_i) * T * (8 if args.precision == 'fp64' else 4)) / 1e9)},
         "roofline": roof,
-        "gram_block_share_of_step": share,
+        "dominant_kernel_share_of_step": share,
+        "roofline_kernels": kernels,
         "cg_matvec": {"avg_ms": prof["cg_matvec_ms"] / max(1, prof["cg_matvec_launches"]),
                       "evals_per_launch": prof["cg_matvec_evals"] / max(1, prof["cg_matvec_launches"])},
         "eig": {"calls": prof["eig_calls"], "avg_ms": prof["eig_ms"] / max(1, prof["eig_calls"]),

@@ -119,6 +119,9 @@ typedef struct {
   /* summed device time of the eigensolver's parts (profiling on): [0] tridiagonalisation,
      [1] divide & conquer, [2] back-transformation and conversion of the kept vectors      */
   double eig_phase_ms[3];
+  double eig_flops[2];        /* algorithmic FP64 flops of those eigensolver calls, per part:
+                                 [0] (4/3) N^3 (tridiagonalisation), [1] 2 N^2 keep (back-
+                                 transformation); divide & conquer depends on deflation: not counted */
 } cakf_stats;
 
 /*

@@ -41,6 +41,7 @@ class cakf_stats(C.Structure):
         ("cg_matvec_ms", C.c_double), ("cg_matvec_launches", C.c_int64), ("cg_matvec_evals", C.c_double),
         ("eig_ms", C.c_double), ("eig_calls", C.c_int64), ("kernel_launches", C.c_int64),
         ("device_bytes", C.c_int64), ("phase_ms", C.c_double * 8), ("eig_phase_ms", C.c_double * 3),
+        ("eig_flops", C.c_double * 2),
     ]
 
 
@@ -262,6 +263,7 @@ def cakf_get_stats(ctx: Context) -> dict:
     out = {f: getattr(s, f) for f, _ in cakf_stats._fields_}
     out["phase_ms"] = list(out["phase_ms"])
     out["eig_phase_ms"] = list(out["eig_phase_ms"])
+    out["eig_flops"] = list(out["eig_flops"])
     return out
 
 

@@ -65,6 +65,7 @@ struct cakf_ctx {
   double* vf = nullptr;
   void* Mpool = nullptr;
   void* PVpool = nullptr;
+  void* KVpool = nullptr;     // K(X, X_o)[V v] per step (PV before its low-rank correction)
   void* Vpool = nullptr;
   void* Spool = nullptr;
   double* rep = nullptr;   // replayed actions (device, double)
@@ -93,6 +94,7 @@ struct cakf_ctx {
   size_t eigw_bytes = 0;
   double* wv = nullptr;
   // smoother
+  void *KWa = nullptr, *KWb = nullptr;   // smoother: K [Ws, ws] (ldn x (cw + 1)), double buffered
   void *WsA = nullptr, *WsB = nullptr, *wsA = nullptr, *wsB = nullptr, *Xs = nullptr, *Y = nullptr, *Xobs = nullptr,
        *Fb = nullptr;
   double* Gws = nullptr;
@@ -233,6 +235,7 @@ int plan_and_alloc(cakf_ctx* c, const cakf_problem* p) {
   if ((rc = c->alloc(c->vf, (size_t)(T + 1) * n * sizeof(double)))) return rc;
   if ((rc = c->alloc(c->Mpool, c->off_M[T + 1] * es))) return rc;
   if ((rc = c->alloc(c->PVpool, c->off_PV[T + 1] * es))) return rc;
+  if ((rc = c->alloc(c->KVpool, c->off_PV[T + 1] * es))) return rc;
   if ((rc = c->alloc(c->Vpool, c->off_V[T + 1] * es))) return rc;
   if ((rc = c->alloc(c->Spool, c->off_S[T + 1] * es))) return rc;
   if (c->replay) {
@@ -286,6 +289,8 @@ int plan_and_alloc(cakf_ctx* c, const cakf_problem* p) {
   if ((rc = c->alloc(c->WsB, ldn * std::max<size_t>(wsw, 1) * es))) return rc;
   if ((rc = c->alloc(c->wsA, ldn * es))) return rc;
   if ((rc = c->alloc(c->wsB, ldn * es))) return rc;
+  if ((rc = c->alloc(c->KWa, ldn * (wsw + 1) * es))) return rc;
+  if ((rc = c->alloc(c->KWb, ldn * (wsw + 1) * es))) return rc;
   const size_t wfin = std::max<size_t>(wmax, c->imax + 1);
   if ((rc = c->alloc(c->Xs, ldn * wfin * es))) return rc;
   if ((rc = c->alloc(c->Y, ldn * wfin * es))) return rc;
@@ -349,6 +354,7 @@ struct Runner {
 
   T* Mk(int k) { return (T*)c->Mpool + c->off_M[k]; }
   T* PV(int k) { return (T*)c->PVpool + c->off_PV[k]; }
+  T* KV(int k) { return (T*)c->KVpool + c->off_PV[k]; }
   T* Vk(int k) { return (T*)c->Vpool + c->off_V[k]; }
   T* Sk(int k) { return (T*)c->Spool + c->off_S[k]; }
   int mk(int k) { return c->obs_ptr[k] - c->obs_ptr[k - 1]; }
@@ -476,7 +482,10 @@ struct Runner {
       // finalize: [P^- W, P^- w] = K(X, X_o) [V v] - a^2 M+ (M+_o^T [V v])
       cudaEvent_t ph1 = ph_begin();
       T* PVk = PV(k);
-      if (int rcg = gram_block(X(), n, Xo, m, V, m, ic + 1, PVk, ldn)) return rcg;
+      // K(X, X_o)[V v] is kept (the smoother propagates K [Ws, ws] from it); P^- [W w] = that minus
+      // the low-rank part
+      if (int rcg = gram_block(X(), n, Xo, m, V, m, ic + 1, KV(k), ldn)) return rcg;
+      cudaMemcpyAsync(PVk, KV(k), (size_t)ldn * (ic + 1) * sizeof(T), cudaMemcpyDeviceToDevice, st);
       if (rp > 0) {
         double* t2 = c->small;
         gemm_tn<T>(Mo, m, rp, V, m, ic + 1, m, 1.0, 0.0, t2, rp, c->part64, c->part64_elems, st);
@@ -557,12 +566,23 @@ struct Runner {
     if (c->profiling) {
       cudaEventRecord(e1, st);
       c->stats.eig_calls++;
+      c->stats.eig_flops[0] += 4.0 / 3.0 * (double)N * N * N;
+      c->stats.eig_flops[1] += 2.0 * (double)N * N * keep;
       c->prof_eig.push_back({e0, e1});
       c->prof_eig_tri.push_back({e0, mk[0]});
       c->prof_eig_dc.push_back({mk[0], mk[1]});
       c->prof_eig_bt.push_back({mk[1], e1});
     }
     return CAKF_OK;
+  }
+
+  // K ws_new = K w_k + a KW[:, cw] - K W_k Z[:, cw] into out (n), with KVk = K [W_k w_k] (ic + 1
+  // columns) and Z (ic x (cw + 1), FP64) from the smoother step.
+  void kws_update(const T* KVk, int ic, const T* KW, int cw, const double* Z, T* out) {
+    const int n = c->n, ldn = c->ldn;
+    scale_copy<T>(KW + (size_t)cw * ldn, ldn, n, 1, T(c->a), out, ldn, st);
+    axpy_block<T>(T(1), KVk + (size_t)ic * ldn, ldn, n, 1, out, ldn, st);
+    gemm_nn<T, double>(n, 1, ic, T(-1), KVk, ldn, Z + (size_t)cw * ic, ic, T(1), out, ldn, st);
   }
 
   // ---------------------------------------------------------------- smoother (Alg. 3)
@@ -592,12 +612,18 @@ struct Runner {
     }
     T* Xs = (T*)c->Xs;
     T* Y = (T*)c->Y;
+    // KW = K [Ws ws] is carried along with [Ws ws] through the same linear recursion, starting from
+    // the filter's K(X, X_o)[V_T v_T]; so K X = a KW needs no kernel evaluations in the smoother.
+    T* KW = (T*)c->KWa;
+    T* KWn = (T*)c->KWb;
+    if (cw > 0) cudaMemcpyAsync(KW, KV(T_), (size_t)ldn * (cw + 1) * sizeof(T), cudaMemcpyDeviceToDevice, st);
+    else cudaMemsetAsync(KW, 0, (size_t)ldn * sizeof(T), st);
     for (int k = T_ - 1; k >= 0; --k) {
       // X = A^T [Ws ws] = a [Ws ws]
       cudaEvent_t ph3 = ph_begin();
       build_x<T>(Ws, ldn, cw, ws, T(a), n, Xs, ldn, st);
-      // Y = P^-_k X = K X - a^2 M+_{k-1} (M+_{k-1}^T X)
-      if (int rcg = gram_block(X(), n, X(), n, Xs, ldn, cw + 1, Y, ldn)) return rcg;
+      // Y = P^-_k X = K X - a^2 M+_{k-1} (M+_{k-1}^T X),  K X = a KW
+      scale_copy<T>(KW, ldn, n, cw + 1, T(a), Y, ldn, st);
       const int rp = (k >= 1) ? c->mcols[k - 1] : 0;
       if (rp > 0) {
         double* t = c->small;
@@ -626,11 +652,12 @@ struct Runner {
         // no update at k: ws_k = a ws_{k+1}, Ws_k = a Ws_{k+1}
         scale_copy<T>(Xs + (size_t)cw * ldn, ldn, n, 1, T(1), wn, ldn, st);
         scale_copy<T>(Xs, ldn, n, cw, T(1), Wn, ldn, st);
+        scale_copy<T>(KW, ldn, n, cw + 1, T(a), KWn, ldn, st);      // K [Wn wn] = a K [Ws ws]
         if (cw > 0) {
           cudaMemcpyAsync(Gn, Gw, (size_t)cw * cw * sizeof(double), cudaMemcpyDeviceToDevice, st);
           scale_f64(Gn, cw * cw, cw * cw, 1, a2, st);
         }
-        std::swap(Ws, Wn); std::swap(ws, wn); std::swap(Gw, Gn);
+        std::swap(Ws, Wn); std::swap(ws, wn); std::swap(Gw, Gn); std::swap(KW, KWn);
         continue;
       }
       T* Vkk = Vk(k);
@@ -639,6 +666,7 @@ struct Runner {
       T* vz = (T*)c->Fb;
       gemm_nn<T, double>(m, 1, ic, T(1), Vkk, m, Z + (size_t)cw * ic, ic, T(0), vz, m, st);
       ws_obs<T>(obs(k), m, Vkk + (size_t)ic * m, vz, wn, st);
+      T* KVk = KV(k);
       ph_end(4, ph4);
       cudaEvent_t ph5 = ph_begin();
       // Gram of Ws_full = [W_k, X'] with X' = X[:, :cw] - W_k Z[:, :cw]  (small-matrix identities)
@@ -680,6 +708,10 @@ struct Runner {
         T* F = (T*)c->Fb;
         gemm_nn<T, double>(m, keep, ic, T(1), Vkk, m, E, ic, T(0), F, m, st);
         scatter_add_rows<T>(F, m, obs(k), m, keep, T(1), Wn, ldn, st);
+        // K Ws_new = a KW[:, :cw] U_bot + K W_k E
+        if (cw > 0) gemm_nn<T, T>(n, keep, cw, T(a), KW, ldn, U + ic, N, T(0), KWn, ldn, st);
+        gemm_nn<T, double>(n, keep, ic, T(1), KVk, ldn, E, ic, cw > 0 ? T(1) : T(0), KWn, ldn, st);
+        kws_update(KVk, ic, KW, cw, Z, KWn + (size_t)keep * ldn);
         // Gram of the new Ws is diag(lam)
         cudaMemsetAsync(Gn, 0, (size_t)keep * keep * sizeof(double), st);
         set_diag(Gn, keep, c->wv, 1.0, keep, st);
@@ -694,11 +726,18 @@ struct Runner {
           gemm_nn<T, double>(m, cw, ic, T(1), Vkk, m, Z, ic, T(0), F, m, st);
           scatter_add_rows<T>(F, m, obs(k), m, cw, T(-1), Wn + (size_t)ic * ldn, ldn, st);
         }
+        // K Ws_full = [K W_k, a KW[:, :cw] - K W_k Z[:, :cw]]
+        scale_copy<T>(KVk, ldn, n, ic, T(1), KWn, ldn, st);
+        if (cw > 0) {
+          scale_copy<T>(KW, ldn, n, cw, T(a), KWn + (size_t)ic * ldn, ldn, st);
+          gemm_nn<T, double>(n, cw, ic, T(-1), KVk, ldn, Z, ic, T(1), KWn + (size_t)ic * ldn, ldn, st);
+        }
+        kws_update(KVk, ic, KW, cw, Z, KWn + (size_t)N * ldn);
         cudaMemcpyAsync(Gn, G, (size_t)N * N * sizeof(double), cudaMemcpyDeviceToDevice, st);
         cw = N;
       }
       ph_end(5, ph5);
-      std::swap(Ws, Wn); std::swap(ws, wn); std::swap(Gw, Gn);
+      std::swap(Ws, Wn); std::swap(ws, wn); std::swap(Gw, Gn); std::swap(KW, KWn);
       cudaError_t ce = cudaGetLastError();
       if (ce != cudaSuccess) return fail(CAKF_ERR_CUDA, std::string("smoother step: ") + cudaGetErrorString(ce));
     }
