@@ -457,10 +457,14 @@ struct Runner {
       const int nsplit = std::max(1, std::min(32, (m + 511) / 512));
       const double* rep = c->replay ? c->rep + c->off_rep[k] : nullptr;
       T* Qa = (T*)c->Qa;       // orthonormal basis of the previous actions (CG policy only)
+      // Re-orthogonalising each action against the previous ones leaves span(S) -- and so every
+      // output -- unchanged; it keeps S^T S well conditioned for the NLL's FP64 Cholesky, which the
+      // FP64 mode's 1e-9 agreement needs.  The FP32-based modes run without it.
+      const bool reorth = !rep && sizeof(T) == 8;
       for (int j = 0; j < ic; ++j) {
         T* g = GSk + (size_t)j * m;
         cg_select<T>(j, r, rep, m, s, Sk(k), m, c->active, st);
-        if (!rep) cg_reorth<T>(Qa, m, j, s, m, c->dots2, Sk(k), m, c->active, st);
+        if (reorth) cg_reorth<T>(Qa, m, j, s, m, c->dots2, Sk(k), m, c->active, st);
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         bool prof = c->profiling && (j % 8 == 0);
         if (prof) { e0 = c->ev(); e1 = c->ev(); cudaEventRecord(e0, st); }
@@ -475,7 +479,7 @@ struct Runner {
         cg_dots1<T>(V, m, j, s, g, (const T*)c->r0v, vcol, m, c->dots, c->active, st);
         cg_upd1<T>(j, c->dots, V, GV, m, s, g, m, c->active, st);
         cg_dots2<T>(V, GV, m, j, m, c->dots2, c->active, st);
-        cg_upd2<T>(j, c->dots, c->dots2, V, GV, m, r, vcol, s, rep ? nullptr : Qa, m, bd_tol, rtol2, use_rtol,
+        cg_upd2<T>(j, c->dots, c->dots2, V, GV, m, r, vcol, s, reorth ? Qa : nullptr, m, bd_tol, rtol2, use_rtol,
                    c->active, c->eta + (size_t)k * B, c->alpha + (size_t)k * B, c->count + k, st);
       }
       ph_end(0, ph0);
