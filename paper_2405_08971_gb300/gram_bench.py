@@ -1,6 +1,7 @@
 """Time the kernel-Gram x block primitive (cakf_gram_matmul) on one shape.
 
     python -m paper_2405_08971_gb300.gram_bench --nr 65536 --nc 65536 --width 513 --precision bf16
+    python -m paper_2405_08971_gb300.gram_bench --nr 65536 --nc 8192 --width 65 --precision fp16x3
 
 Coordinates are uniform on the unit sphere (the layout of the 256 x 256 lat-lon workload), B is
 standard normal; all inputs are created on the device before timing.  Each repetition is one
@@ -25,7 +26,7 @@ def main():
     ap.add_argument("--width", type=int, default=513)
     ap.add_argument("--kernel", type=int, default=1, help="0, 1, 2: Matern 1/2, 3/2, 5/2")
     ap.add_argument("--lx", type=float, default=0.1)
-    ap.add_argument("--precision", default="bf16", choices=["fp64", "fp32", "bf16"])
+    ap.add_argument("--precision", default="bf16", choices=["fp64", "fp32", "bf16", "fp16x3"])
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=2)
     a = ap.parse_args()
