@@ -278,7 +278,8 @@ def main():
             ent["tensor_frac"] = mmas * tfl / tpk
             ent["tensor_peak_source"] = f"{pk_src} bf16_tflops_sustained; {mmas} MMA(s) per algorithmic flop"
         kernels["k_gram_tc" if args.precision in ("bf16", "fp16x3") else "k_gram_block_simt"] = ent
-    # CG Gram matvec (sampled every 8th iteration): m^2 kernel entries per launch on MUFU
+    # CG Gram matvec (sampled every 8th iteration): m (m + 1) / 2 unique kernel entries per launch
+    # (the symmetric Gram is evaluated once per entry pair), 2 MUFU operations each
     if prof["cg_matvec_launches"]:
         mv_ms = prof["cg_matvec_ms"]
         evals = prof["cg_matvec_evals"] / (mv_ms / 1e3) / 1e12

@@ -83,6 +83,7 @@ struct cakf_ctx {
        *part = nullptr, *tv = nullptr, *GS = nullptr, *Qa = nullptr;
   double* dots = nullptr;
   double* dots2 = nullptr;
+  double* dpart = nullptr;     // per-block partials of the CG dot passes
   double* part64 = nullptr;
   size_t part64_elems = 0;
   double* gram = nullptr;
@@ -270,10 +271,11 @@ int plan_and_alloc(cakf_ctx* c, const cakf_problem* p) {
   if ((rc = c->alloc(c->GV, mm * std::max(B, 1) * es))) return rc;
   if ((rc = c->alloc(c->GS, mm * std::max(B, 1) * es))) return rc;
   if ((rc = c->alloc(c->Qa, mm * std::max(B, 1) * es))) return rc;
-  if ((rc = c->alloc(c->part, mm * 32 * es))) return rc;
+  if ((rc = c->alloc(c->part, mm * std::max(32, gram_matvec_slots((int)mm)) * es))) return rc;
   if ((rc = c->alloc(c->tv, std::max<size_t>(c->rmax, 1) * ((mm + 1023) / 1024 + 1) * es))) return rc;
   if ((rc = c->alloc(c->dots, (B + 8) * sizeof(double)))) return rc;
   if ((rc = c->alloc(c->dots2, (B + 8) * sizeof(double)))) return rc;
+  if ((rc = c->alloc(c->dpart, cg_dpart_elems((int)mm, B) * sizeof(double)))) return rc;
   c->part64_elems = std::max<size_t>(size_t(1) << 22, NE * NE * 4);
   if ((rc = c->alloc(c->part64, c->part64_elems * sizeof(double)))) return rc;
   if ((rc = c->alloc(c->gram, NE * NE * sizeof(double)))) return rc;
@@ -336,7 +338,7 @@ struct Runner {
   cakf_ctx* c;
   cudaStream_t st;
   bool tc;      // tensor-core Gram x block
-  int tc_kind;  // 0 bf16, 1 split bf16 (x3)
+  int tc_kind;  // 0 BF16, 1 split FP16 (three MMAs per slice)
 
   // phase timers (profiling on): begin returns the start event, end records the pair
   cudaEvent_t ph_begin() {
@@ -454,33 +456,37 @@ struct Runner {
         rtol2 = c->cg_rtol * c->cg_rtol * r0sq;
         use_rtol = 1;
       }
-      const int nsplit = std::max(1, std::min(32, (m + 511) / 512));
+      const int nsplit = gram_matvec_slots(m);
       const double* rep = c->replay ? c->rep + c->off_rep[k] : nullptr;
       T* Qa = (T*)c->Qa;       // orthonormal basis of the previous actions (CG policy only)
       // Re-orthogonalising each action against the previous ones leaves span(S) -- and so every
       // output -- unchanged; it keeps S^T S well conditioned for the NLL's FP64 Cholesky, which the
       // FP64 mode's 1e-9 agreement needs.  The FP32-based modes run without it.
       const bool reorth = !rep && sizeof(T) == 8;
+      // CG policy without re-orthogonalisation: k_cg_upd2 writes the next action (the updated
+      // residual) itself, so the selection runs only for the first action
+      const bool fused_select = !rep && !reorth;
+      double* dpart1 = c->dpart;
+      double* dpart2 = c->dpart + (size_t)(B + 4) * ((m + 31) / 32);
       for (int j = 0; j < ic; ++j) {
         T* g = GSk + (size_t)j * m;
-        cg_select<T>(j, r, rep, m, s, Sk(k), m, c->active, st);
+        if (!fused_select || j == 0) cg_select<T>(j, r, rep, m, s, Sk(k), m, c->active, st);
         if (reorth) cg_reorth<T>(Qa, m, j, s, m, c->dots2, Sk(k), m, c->active, st);
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         bool prof = c->profiling && (j % 8 == 0);
         if (prof) { e0 = c->ev(); e1 = c->ev(); cudaEventRecord(e0, st); }
-        gram_matvec<T>(c->kernel, Xo, s, m, T(c->sf2), (T*)c->part, nsplit, st);
+        gram_matvec<T>(c->kernel, Xo, s, m, T(c->sf2), (T*)c->part, Mo, m, rp, (T*)c->tv, c->active, st);
         if (prof) {
           cudaEventRecord(e1, st);
           c->prof_mv.push_back({e0, e1});
-          c->prof_mv_evals.push_back((double)m * m);
+          c->prof_mv_evals.push_back(0.5 * (double)m * (m + 1));   // unique entries of K(X_o, X_o)
         }
-        if (rp > 0) gemv_t<T>(Mo, m, m, rp, s, (T*)c->tv, c->active, st);
-        cg_combine<T>((const T*)c->part, nsplit, s, T(c->sn2), Mo, m, rp, (const T*)c->tv, T(a2), m, g, c->active, st);
-        cg_dots1<T>(V, m, j, s, g, (const T*)c->r0v, vcol, m, c->dots, c->active, st);
-        cg_upd1<T>(j, c->dots, V, GV, m, s, g, m, c->active, st);
-        cg_dots2<T>(V, GV, m, j, m, c->dots2, c->active, st);
-        cg_upd2<T>(j, c->dots, c->dots2, V, GV, m, r, vcol, s, reorth ? Qa : nullptr, m, bd_tol, rtol2, use_rtol,
-                   c->active, c->eta + (size_t)k * B, c->alpha + (size_t)k * B, c->count + k, st);
+        cg_combine<T>((const T*)c->part, nsplit, s, T(c->sn2), Mo, m, rp, (const T*)c->tv, T(a2), m, g, V, m, j,
+                      (const T*)c->r0v, vcol, dpart1, c->active, st);
+        cg_upd1<T>(j, dpart1, c->dots, V, GV, m, s, g, m, dpart2, c->active, st);
+        T* snext = (fused_select && j + 1 < ic) ? Sk(k) + (size_t)(j + 1) * m : nullptr;
+        cg_upd2<T>(j, c->dots, dpart2, V, GV, m, r, vcol, s, reorth ? Qa : nullptr, m, bd_tol, rtol2, use_rtol,
+                   c->active, c->eta + (size_t)k * B, c->alpha + (size_t)k * B, c->count + k, snext, st);
       }
       ph_end(0, ph0);
       // finalize: [P^- W, P^- w] = K(X, X_o) [V v] - a^2 M+ (M+_o^T [V v])

@@ -254,7 +254,7 @@ struct MergeDesc { int lo, mid, hi; };
 
 struct DcWork {
   double *lam, *lamk, *lamtmp, *Dw, *Zw, *Dk, *Zk, *Dd, *Q, *Qtmp, *Delta, *rho, *rot, *z2, *Tm;
-  int *colk, *cold, *perm, *Kp, *nrot, *mergeof;
+  int *colk, *cold, *perm, *Kp, *nrot, *mergeof, *gperm, *gcnt;
 };
 
 __global__ void k_dc_init(const double* __restrict__ d, const double* __restrict__ e, int N, double* lam,
@@ -268,11 +268,76 @@ __global__ void k_dc_init(const double* __restrict__ d, const double* __restrict
   Q[(size_t)j * N + j] = 1.0;
 }
 
+// Order-preserving integer key of a double (IEEE bit pattern; negative values mirrored), so the
+// sorting below compares on the integer units instead of the FP64 pipe.
+__device__ __forceinline__ long long order_key(double x) {
+  const long long b = __double_as_longlong(x);
+  return b >= 0 ? b : (b ^ 0x7FFFFFFFFFFFFFFFLL);
+}
+
+// Block-wide maximum (every thread gets the result).
+__device__ double block_max(double v) {
+  __shared__ double red[32];
+  __syncthreads();
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double t = (l < nw) ? red[l] : 0.0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_xor_sync(0xffffffffu, t, o));
+  __syncthreads();
+  return t;
+}
+
+// Block-wide exclusive prefix sum of one int per thread (thread order); *total gets the sum.
+__device__ int block_excl_scan(int v, int* total) {
+  __shared__ int ws[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  __syncthreads();
+  if (lane == 31) ws[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int t = (lane < nw) ? ws[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    ws[lane] = t;
+  }
+  __syncthreads();
+  const int before = (wid > 0 ? ws[wid - 1] : 0) + x - v;
+  *total = ws[nw - 1];
+  __syncthreads();
+  return before;
+}
+
+constexpr int DC_THREADS = 256;
+
+// Shared memory of k_dc_prep for a merge of order K: four FP64 arrays, one int64 key array, six int arrays.
+inline size_t prep_smem_bytes(int K) { return (size_t)K * (4 * sizeof(double) + sizeof(long long) + 6 * sizeof(int)); }
+
 // Phase 1 of a merge: z vector, sorted poles, deflation.  One block per merge.
-__global__ void __launch_bounds__(256)
+//   1. The two ascending child spectra are merged by rank (each entry's position is its index
+//      plus the number of entries of the other list before it, found by binary search).
+//   2. Small z components are deflated (all entries in parallel).
+//   3. Close poles are deflated by a Givens rotation: a scan in pole order, since a rotation changes
+//      the entries the next test reads; one thread, operands carried in registers.  The rotations
+//      are written to W.rot and applied to the eigenvector rows by k_dc_rot.
+//   4. Kept and deflated entries are compacted (block prefix sums); the kept poles are re-sorted
+//      by rank when a rotation moved one.
+//   5. The kept columns are grouped by their row support (child 1 only, both, child 2 only) for the
+//      eigenvector product of phase 5.
+__global__ void __launch_bounds__(DC_THREADS)
 k_dc_prep(const MergeDesc* __restrict__ merges, const double* __restrict__ e, int N, DcWork W) {
-  // The sequential part (merge of the two child spectra, deflation scan, ordering) runs on one
-  // thread over shared-memory copies; loads and stores are done by the whole block.
   extern __shared__ double psm[];
   const MergeDesc mg = merges[blockIdx.x];
   const int lo = mg.lo, mid = mg.mid, K = mg.hi - mg.lo, n1 = mg.mid - mg.lo;
@@ -280,134 +345,200 @@ k_dc_prep(const MergeDesc* __restrict__ merges, const double* __restrict__ e, in
   double* sZr = psm + K;
   double* sD = psm + 2 * K;
   double* sZ = psm + 3 * K;
-  double* sRot = psm + 4 * K;          // up to K rotations: {last, j, c, s}
-  int* sPerm = reinterpret_cast<int*>(psm + 8 * K);
-  int* sKeep = sPerm + K;
+  long long* sKey = reinterpret_cast<long long*>(psm + 4 * K);
+  int* sPerm = reinterpret_cast<int*>(psm + 5 * K);
+  int* sStat = sPerm + K;       // 0 kept, 1 deflated (small z), 2 deflated (rotated away)
+  int* sType = sStat + K;       // row support: 1 child 1, 3 child 2, 2 both
+  int* sKeep = sType + K;
   int* sDefl = sKeep + K;
+  int* sSort = sDefl + K;
+  __shared__ int s_nrot;
   const double rho0 = e[mid - 1];
   const double sgn = rho0 >= 0.0 ? 1.0 : -1.0;
   double zz = 0.0;
   for (int t = threadIdx.x; t < K; t += blockDim.x) {
     const double z = (t < n1) ? W.Q[(size_t)(lo + t) * N + (mid - 1)] : sgn * W.Q[(size_t)(lo + t) * N + mid];
     sZr[t] = z;
-    sLam[t] = W.lam[lo + t];
+    const double l = W.lam[lo + t];
+    sLam[t] = l;
+    sKey[t] = order_key(l);
+    sPerm[t] = t;
     zz += z * z;
   }
   zz = block_sum(zz);
-  __shared__ int s_kp, s_nd, s_nrot;
-  __shared__ double s_rho;
-  if (threadIdx.x == 0) {
-    const double zn = sqrt(zz);
-    const double rho = fabs(rho0) * zz;
-    // merge the two ascending child spectra
-    int a = 0, b = n1, o = 0;
-    while (a < n1 || b < K) {
-      int pick;
-      if (a >= n1) pick = b++;
-      else if (b >= K) pick = a++;
-      else pick = (sLam[a] <= sLam[b]) ? a++ : b++;
-      sPerm[o] = pick;
-      sD[o] = sLam[pick];
-      sZ[o] = sZr[pick] / zn;
-      ++o;
+  const double zn = sqrt(zz);
+  const double rho = fabs(rho0) * zz;
+  // 1. merge by rank (ties: child 1 first)
+  for (int t = threadIdx.x; t < K; t += blockDim.x) {
+    const long long kt = sKey[t];
+    int pos;
+    if (t < n1) {
+      int a = n1, b = K;
+      while (a < b) { const int m = (a + b) >> 1; if (sKey[m] < kt) a = m + 1; else b = m; }
+      pos = t + (a - n1);
+    } else {
+      int a = 0, b = n1;
+      while (a < b) { const int m = (a + b) >> 1; if (sKey[m] <= kt) a = m + 1; else b = m; }
+      pos = (t - n1) + a;
     }
-    double dmax = 0.0;
-    for (int t = 0; t < K; ++t) dmax = fmax(dmax, fabs(sD[t]));
-    const double tol = 8.0 * kEps * fmax(dmax, rho);
-    // deflation scan: small z components, then pairs of close poles (Givens rotation).  The
-    // close-pole test |(D_j - D_l) c s| <= tol with c s = -z_l z_j / t^2 is evaluated without the
-    // division, as |D_j - D_l| |z_l z_j| <= tol t^2; c and s are formed only for a rotation.
-    int kp = 0, nd = 0, nrot = 0, last = -1;
+    sPerm[pos] = t;
+    sD[pos] = sLam[t];
+    sZ[pos] = sZr[t] / zn;
+    sType[pos] = (t < n1) ? 1 : 3;
+  }
+  __syncthreads();
+  // 2. tolerance and small-z deflation
+  double dm = 0.0;
+  for (int t = threadIdx.x; t < K; t += blockDim.x) dm = fmax(dm, fabs(sD[t]));
+  dm = block_max(dm);
+  const double tol = 8.0 * kEps * fmax(dm, rho);
+  for (int t = threadIdx.x; t < K; t += blockDim.x) sStat[t] = (rho * fabs(sZ[t]) <= tol) ? 1 : 0;
+  __syncthreads();
+  // 3. close poles.  The test |(D_j - D_l) c s| <= tol with c s = -z_l z_j / t^2 is evaluated
+  // without the division, as |D_j - D_l| |z_l z_j| <= tol t^2; c and s are formed only for a rotation.
+  if (threadIdx.x == 0) {
+    int last = -1, nrot = 0;
+    double zl = 0.0, dl = 0.0;
     for (int j = 0; j < K; ++j) {
-      const double zj = sZ[j];
-      if (rho * fabs(zj) <= tol) { sDefl[nd++] = j; continue; }
+      if (sStat[j]) continue;
+      double zj = sZ[j], dj = sD[j];
       if (last >= 0) {
-        const double zl = sZ[last];
         const double t2 = fma(zl, zl, zj * zj);
-        if (fabs(sD[j] - sD[last]) * fabs(zl * zj) <= tol * t2) {
+        if (fabs(dj - dl) * fabs(zl * zj) <= tol * t2) {
           const double t = sqrt(t2);
           const double c = zj / t, sn = -zl / t;
-          double* rr = sRot + 4 * nrot;
-          rr[0] = last; rr[1] = j; rr[2] = c; rr[3] = sn;
+          double* rr = W.rot + (size_t)4 * (lo + nrot);
+          rr[0] = (double)(lo + sPerm[last]);
+          rr[1] = (double)(lo + sPerm[j]);
+          rr[2] = c;
+          rr[3] = sn;
           ++nrot;
-          const double dl = sD[last], dj = sD[j];
           sD[last] = c * c * dl + sn * sn * dj;
-          sD[j] = sn * sn * dl + c * c * dj;
+          dj = sn * sn * dl + c * c * dj;
+          sD[j] = dj;
           sZ[last] = 0.0;
           sZ[j] = t;
-          sDefl[nd++] = last;
-          --kp;   // 'last' was the most recently kept entry
+          zj = t;
+          sStat[last] = 2;
+          if (sType[last] != sType[j]) sType[j] = 2;
         }
       }
-      sKeep[kp++] = j;
       last = j;
+      zl = zj;
+      dl = dj;
     }
-    // rotations can perturb the order of kept poles slightly: insertion sort (nearly sorted input)
-    for (int a2 = 1; a2 < kp; ++a2) {
-      const int key = sKeep[a2];
-      int b2 = a2 - 1;
-      while (b2 >= 0 && sD[sKeep[b2]] > sD[key]) { sKeep[b2 + 1] = sKeep[b2]; --b2; }
-      sKeep[b2 + 1] = key;
-    }
-    s_kp = kp;
-    s_nd = nd;
     s_nrot = nrot;
-    s_rho = rho;
-    W.rho[lo] = rho;
-    W.Kp[lo] = kp;
+    W.nrot[lo] = nrot;
   }
   __syncthreads();
-  const int kp = s_kp, nd = s_nd, nrot = s_nrot;
-  const double rho = s_rho;
-  for (int t = threadIdx.x; t < kp; t += blockDim.x) {
-    const int q = sKeep[t];
-    W.Dk[lo + t] = sD[q];
-    W.Zk[lo + t] = sZ[q];
-    W.z2[lo + t] = rho * sZ[q] * sZ[q];
-    W.colk[lo + t] = lo + sPerm[q];
-  }
-  for (int t = threadIdx.x; t < nd; t += blockDim.x) {
-    W.Dd[lo + t] = sD[sDefl[t]];
-    W.cold[lo + t] = lo + sPerm[sDefl[t]];
+  const int nrot = s_nrot;
+  // 4. compaction: kept and deflated entries in pole order
+  const int ch = (K + (int)blockDim.x - 1) / (int)blockDim.x;
+  const int c0 = min(K, (int)threadIdx.x * ch), c1 = min(K, c0 + ch);
+  int nk = 0;
+  for (int t = c0; t < c1; ++t) nk += (sStat[t] == 0);
+  int kp = 0;
+  int ok = block_excl_scan(nk, &kp);
+  int od = c0 - ok;
+  for (int t = c0; t < c1; ++t) {
+    if (sStat[t] == 0) sKeep[ok++] = t;
+    else sDefl[od++] = t;
   }
   __syncthreads();
-  // apply the deflation rotations to the (permuted) child eigenvector columns, rows lo..hi.
-  // Rotation q acts on (a_q, b_q) with b_q a column no earlier rotation touched, and a_q either
-  // untouched as well or equal to b_{q-1}; so each group of RG rotations loads its operands up
-  // front (independent loads), and the a_q = b_{q-1} chain is carried in a register.
+  const int* keep = sKeep;
+  if (nrot > 0) {
+    // a rotation can move a kept pole past its neighbours: rank sort by (value, position)
+    for (int q = threadIdx.x; q < kp; q += blockDim.x) sKey[q] = order_key(sD[sKeep[q]]);
+    __syncthreads();
+    for (int q = threadIdx.x; q < kp; q += blockDim.x) {
+      const long long kq = sKey[q];
+      int rank = 0;
+      for (int u = 0; u < kp; ++u) {
+        const long long ku = sKey[u];
+        rank += (ku < kq) || (ku == kq && u < q);
+      }
+      sSort[rank] = sKeep[q];
+    }
+    __syncthreads();
+    keep = sSort;
+  }
+  for (int q = threadIdx.x; q < kp; q += blockDim.x) {
+    const int j = keep[q];
+    W.Dk[lo + q] = sD[j];
+    W.Zk[lo + q] = sZ[j];
+    W.z2[lo + q] = rho * sZ[j] * sZ[j];
+    W.colk[lo + q] = lo + sPerm[j];
+  }
+  for (int q = threadIdx.x; q < K - kp; q += blockDim.x) {
+    const int j = sDefl[q];
+    W.Dd[lo + q] = sD[j];
+    W.cold[lo + q] = lo + sPerm[j];
+  }
+  // 5. kept columns grouped by row support: child 1 only, both children, child 2 only
+  {
+    const int kc = (kp + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int q0 = min(kp, (int)threadIdx.x * kc), q1 = min(kp, q0 + kc);
+    int cnt[3] = {0, 0, 0};
+    for (int q = q0; q < q1; ++q) ++cnt[sType[keep[q]] - 1];
+    int tot[3];
+    int off[3];
+    for (int g = 0; g < 3; ++g) off[g] = block_excl_scan(cnt[g], &tot[g]);
+    off[1] += tot[0];
+    off[2] += tot[0] + tot[1];
+    for (int q = q0; q < q1; ++q) W.gperm[lo + off[sType[keep[q]] - 1]++] = q;
+    if (threadIdx.x == 0) {
+      W.gcnt[2 * lo] = tot[0];
+      W.gcnt[2 * lo + 1] = tot[1];
+      W.rho[lo] = rho;
+      W.Kp[lo] = kp;
+    }
+  }
+}
+
+// Phase 1b: the deflation rotations applied to the child eigenvector columns, one thread per row of
+// the merge.  Rotation q acts on (a_q, b_q) with b_q a column no earlier rotation touched, and a_q
+// either untouched as well or equal to b_{q-1}; so each group of RG rotations loads its operands up
+// front (independent loads), and the a_q = b_{q-1} chain is carried in a register.
+__global__ void __launch_bounds__(128)
+k_dc_rot(const MergeDesc* __restrict__ merges, int N, DcWork W) {
+  const MergeDesc mg = merges[blockIdx.y];
+  const int lo = mg.lo, K = mg.hi - mg.lo;
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= K) return;
+  const int nrot = W.nrot[lo];
+  if (nrot == 0) return;
+  const double* rot = W.rot + (size_t)4 * lo;
+  double* qrow = W.Q + lo + row;
   constexpr int RG = 8;
-  for (int row = threadIdx.x; row < K; row += blockDim.x) {
-    double* qrow = W.Q + lo + row;
-    double carry = 0.0;
-    int carry_col = -1;
-    for (int q0 = 0; q0 < nrot; q0 += RG) {
-      const int nq = min(RG, nrot - q0);
-      int ca[RG], cb[RG];
-      double xa[RG], xb[RG];
+  double carry = 0.0;
+  int carry_col = -1;
+  for (int q0 = 0; q0 < nrot; q0 += RG) {
+    const int nq = min(RG, nrot - q0);
+    int ca[RG], cb[RG];
+    double xa[RG], xb[RG];
 #pragma unroll
-      for (int u = 0; u < RG; ++u) {
-        if (u >= nq) break;
-        const double* rr = sRot + 4 * (q0 + u);
-        ca[u] = lo + sPerm[(int)rr[0]];
-        cb[u] = lo + sPerm[(int)rr[1]];
-        const int prev = (u == 0) ? carry_col : cb[u - 1];
-        xb[u] = qrow[(size_t)cb[u] * N];
-        xa[u] = (ca[u] == prev) ? 0.0 : qrow[(size_t)ca[u] * N];
-      }
+    for (int u = 0; u < RG; ++u) {
+      if (u >= nq) break;
+      const double* rr = rot + 4 * (q0 + u);
+      ca[u] = (int)rr[0];
+      cb[u] = (int)rr[1];
+      const int prev = (u == 0) ? carry_col : cb[u - 1];
+      xb[u] = qrow[(size_t)cb[u] * N];
+      xa[u] = (ca[u] == prev) ? 0.0 : qrow[(size_t)ca[u] * N];
+    }
 #pragma unroll
-      for (int u = 0; u < RG; ++u) {
-        if (u >= nq) break;
-        const double* rr = sRot + 4 * (q0 + u);
-        const double c = rr[2], sn = rr[3];
-        const int prev = (u == 0) ? carry_col : cb[u - 1];
-        const double a = (ca[u] == prev) ? carry : xa[u];
-        const double na = c * a + sn * xb[u];
-        const double nb = -sn * a + c * xb[u];
-        qrow[(size_t)ca[u] * N] = na;
-        qrow[(size_t)cb[u] * N] = nb;
-        carry = nb;
-        carry_col = cb[u];
-      }
+    for (int u = 0; u < RG; ++u) {
+      if (u >= nq) break;
+      const double* rr = rot + 4 * (q0 + u);
+      const double c = rr[2], sn = rr[3];
+      const int prev = (u == 0) ? carry_col : cb[u - 1];
+      const double a = (ca[u] == prev) ? carry : xa[u];
+      const double na = c * a + sn * xb[u];
+      const double nb = -sn * a + c * xb[u];
+      qrow[(size_t)ca[u] * N] = na;
+      qrow[(size_t)cb[u] * N] = nb;
+      carry = nb;
+      carry_col = cb[u];
     }
   }
 }
@@ -516,13 +647,17 @@ __global__ void k_dc_zhat(const MergeDesc* __restrict__ merges, const int* __res
   const double* Dk = W.Dk + lo;
   const double rho = W.rho[lo];
   const double Dj = Dk[j];
-  double lg = 0.0;
+  // each lane multiplies its factors and takes one logarithm (more only if the product leaves
+  // [1e-150, 1e150]); the lanes' logarithms are summed
+  double lg = 0.0, prod = 1.0;
   for (int i = lane; i < Kp; i += 32) {
     if (i == j) continue;
     const int ii = (i < j) ? i : i - 1;                       // lam_i for i < j, lam_{i-1} for i > j
     const double num = -W.Delta[(size_t)(lo + ii) * N + lo + j];
-    lg += log(fabs(num / (Dk[i] - Dj)));
+    prod *= fabs(num / (Dk[i] - Dj));
+    if (!(prod > 1e-150 && prod < 1e150)) { lg += log(prod); prod = 1.0; }
   }
+  lg += log(prod);
   lg = warp_sum(lg);
   if (lane == 0) {
     const double last = -W.Delta[(size_t)(lo + Kp - 1) * N + lo + j] / rho;
@@ -550,33 +685,48 @@ __global__ void k_dc_vecs(const MergeDesc* __restrict__ merges, const int* __res
 }
 
 // Phase 5: Qtmp[lo:hi, lo+i] = Q[lo:hi, colk] U[:, i] (i < Kp); deflated columns copied after them.
+// The sum over kept poles runs in the support order of phase 1 (gperm): a row tile inside child 1
+// skips the columns supported on child 2 only and vice versa, about half of the products.
 constexpr int DG_T = 32;
 __global__ void __launch_bounds__(256)
 k_dc_gemm(const MergeDesc* __restrict__ merges, int N, DcWork W) {
   const MergeDesc mg = merges[blockIdx.z];
-  const int lo = mg.lo, K = mg.hi - mg.lo;
+  const int lo = mg.lo, K = mg.hi - mg.lo, n1 = mg.mid - mg.lo;
   const int Kp = W.Kp[lo];
   const int r0 = blockIdx.x * DG_T, c0 = blockIdx.y * DG_T;
   if (r0 >= K || c0 >= K) return;
   __shared__ double As[DG_T][DG_T + 1], Bs[DG_T][DG_T + 1];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int g1 = W.gcnt[2 * lo], g2 = W.gcnt[2 * lo + 1];
+  int kb = 0, ke = Kp;
+  if (r0 + DG_T <= n1) ke = g1 + g2;        // rows of child 1 only
+  else if (r0 >= n1) kb = g1;               // rows of child 2 only
+  const int* gp = W.gperm + lo;
   double acc[2][2] = {{0, 0}, {0, 0}};
-  for (int k0 = 0; k0 < Kp; k0 += DG_T) {
-    for (int e2 = threadIdx.x; e2 < DG_T * DG_T; e2 += 256) {
-      int rr = e2 % DG_T, kk = e2 / DG_T;
-      int row = r0 + rr, kidx = k0 + kk;
-      As[kk][rr] = (row < K && kidx < Kp) ? W.Q[(size_t)W.colk[lo + kidx] * N + lo + row] : 0.0;
-      int ci = c0 + rr;   // reuse rr as column index for B tile: Bs[kk][col]
-      Bs[kk][rr] = (ci < Kp && kidx < Kp) ? W.Delta[(size_t)(lo + ci) * N + lo + kidx] : 0.0;
-    }
-    __syncthreads();
+  if (c0 < Kp) {
+    for (int k0 = kb; k0 < ke; k0 += DG_T) {
+      for (int e2 = threadIdx.x; e2 < DG_T * DG_T; e2 += 256) {
+        const int i32 = e2 % DG_T, o32 = e2 / DG_T;
+        // A tile: consecutive threads take consecutive rows of one column
+        {
+          const int row = r0 + i32, kidx = k0 + o32;
+          As[o32][i32] = (row < K && kidx < ke) ? W.Q[(size_t)W.colk[lo + gp[kidx]] * N + lo + row] : 0.0;
+        }
+        // B tile: consecutive threads take consecutive poles of one eigenvector column
+        {
+          const int kidx = k0 + i32, ci = c0 + o32;
+          Bs[i32][o32] = (ci < Kp && kidx < ke) ? W.Delta[(size_t)(lo + ci) * N + lo + gp[kidx]] : 0.0;
+        }
+      }
+      __syncthreads();
 #pragma unroll 8
-    for (int kk = 0; kk < DG_T; ++kk)
+      for (int kk = 0; kk < DG_T; ++kk)
 #pragma unroll
-      for (int a = 0; a < 2; ++a)
+        for (int a = 0; a < 2; ++a)
 #pragma unroll
-        for (int b = 0; b < 2; ++b) acc[a][b] = fma(As[kk][ty + 16 * a], Bs[kk][tx + 16 * b], acc[a][b]);
-    __syncthreads();
+          for (int b = 0; b < 2; ++b) acc[a][b] = fma(As[kk][ty + 16 * a], Bs[kk][tx + 16 * b], acc[a][b]);
+      __syncthreads();
+    }
   }
 #pragma unroll
   for (int a = 0; a < 2; ++a)
@@ -591,15 +741,9 @@ k_dc_gemm(const MergeDesc* __restrict__ merges, int N, DcWork W) {
     }
 }
 
-// Order-preserving integer key of a double (IEEE bit pattern; negative values mirrored), so the
-// sorting below compares on the integer units instead of the FP64 pipe.
-__device__ __forceinline__ long long order_key(double x) {
-  const long long b = __double_as_longlong(x);
-  return b >= 0 ? b : (b ^ 0x7FFFFFFFFFFFFFFFLL);
-}
-
 // Phase 6a: order the merged spectrum ascending (one block per merge): W.lam and the column
-// permutation W.perm (relative to lo) for phase 6b.
+// permutation W.perm (relative to lo) for phase 6b.  Rank sort on (value key, position): the kept
+// roots come before deflated poles of equal value.
 __global__ void __launch_bounds__(256)
 k_dc_finish(const MergeDesc* __restrict__ merges, int N, DcWork W) {
   extern __shared__ double fsm[];
@@ -608,38 +752,21 @@ k_dc_finish(const MergeDesc* __restrict__ merges, int N, DcWork W) {
   const int Kp = W.Kp[lo];
   double* sl = fsm;                                          // K merged eigenvalues (kept roots, deflated poles)
   long long* key = reinterpret_cast<long long*>(fsm + K);
-  int* perm = reinterpret_cast<int*>(fsm + 2 * K);
-  int* dp = perm + K;
   for (int t = threadIdx.x; t < K; t += blockDim.x) {
     const double v = (t < Kp) ? W.lamk[lo + t] : W.Dd[lo + t - Kp];
     sl[t] = v;
     key[t] = order_key(v);
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    // kept roots are ascending; sort the (nearly ascending) deflated poles, then merge the two lists
-    const int Kd = K - Kp;
-    for (int t = 0; t < Kd; ++t) dp[t] = Kp + t;
-    for (int a = 1; a < Kd; ++a) {
-      const int kidx = dp[a];
-      const long long kv = key[kidx];
-      int b = a - 1;
-      while (b >= 0 && key[dp[b]] > kv) { dp[b + 1] = dp[b]; --b; }
-      dp[b + 1] = kidx;
-    }
-    int x = 0, y = 0;
-    for (int t = 0; t < K; ++t) {
-      int pick;
-      if (x >= Kp) pick = dp[y++];
-      else if (y >= Kd) pick = x++;
-      else pick = (key[x] <= key[dp[y]]) ? x++ : dp[y++];
-      perm[t] = pick;
-    }
-  }
-  __syncthreads();
   for (int t = threadIdx.x; t < K; t += blockDim.x) {
-    W.lam[lo + t] = sl[perm[t]];
-    W.perm[lo + t] = perm[t];
+    const long long kt = key[t];
+    int rank = 0;
+    for (int u = 0; u < K; ++u) {
+      const long long ku = key[u];
+      rank += (ku < kt) || (ku == kt && u < t);
+    }
+    W.lam[lo + rank] = sl[t];
+    W.perm[lo + rank] = t;
   }
 }
 
@@ -666,33 +793,27 @@ k_dc_copy(const MergeDesc* __restrict__ merges, int N, DcWork W) {
 constexpr int RB = 8;
 constexpr int CB = 4;
 
-// T of every group (one warp per group): T_ii = tau_i, T[0:i, i] = -tau_i T[0:i, 0:i] V[:, 0:i]^T v_i.
-__global__ void k_bt_tmat(const double* __restrict__ A, int lda, const double* __restrict__ tau, int N,
-                          double* __restrict__ Tm) {
-  const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  const int nref = N - 2, ng = (nref + RB - 1) / RB;
-  if (g >= ng) return;
+// T of every group (one block per group): T_ii = tau_i, T[0:i, i] = -tau_i T[0:i, 0:i] V[:, 0:i]^T v_i.
+// The RB (RB - 1) / 2 reflector dots are spread over the warps; one thread then forms T.
+__global__ void __launch_bounds__(256)
+k_bt_tmat(const double* __restrict__ A, int lda, const double* __restrict__ tau, int N,
+          double* __restrict__ Tm) {
+  const int g = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int nref = N - 2;
   const int k0 = g * RB, nb = min(RB, nref - k0);
-  double vv[RB][RB];
-#pragma unroll
-  for (int a = 0; a < RB; ++a)
-#pragma unroll
-    for (int b = 0; b < RB; ++b) vv[a][b] = 0.0;
-  for (int b = 1; b < nb; ++b) {
+  __shared__ double vv[RB][RB];
+  for (int pr = warp; pr < RB * RB; pr += nw) {
+    const int a = pr / RB, b = pr - a * RB;
+    if (!(a < b && b < nb)) continue;
+    const double* va = A + (size_t)(k0 + a) * lda;
     const double* vb = A + (size_t)(k0 + b) * lda;
-    for (int a = 0; a < b; ++a) {
-      const double* va = A + (size_t)(k0 + a) * lda;
-      double acc = 0.0;
-      for (int row = k0 + b + 1 + lane; row < N; row += 32) acc = fma(va[row], vb[row], acc);
-      acc = warp_sum(acc);
-#pragma unroll
-      for (int aa = 0; aa < RB; ++aa)
-#pragma unroll
-        for (int bb = 0; bb < RB; ++bb)
-          if (aa == a && bb == b) vv[aa][bb] = acc;
-    }
+    double acc = 0.0;
+    for (int row = k0 + b + 1 + lane; row < N; row += 32) acc = fma(va[row], vb[row], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) vv[a][b] = acc;
   }
-  if (lane == 0) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
     double T[RB][RB];
 #pragma unroll
     for (int i = 0; i < RB; ++i)
@@ -865,7 +986,8 @@ size_t eig_workspace_bytes(int nmax) {
   b += 10 * align_up(N * sizeof(double));         // lam, lamk, lamtmp, Dw, Zw, Dk, Zk, Dd, rho, spare
   b += align_up(4 * N * sizeof(double));          // rot
   b += align_up((N / RB + 2) * RB * RB * sizeof(double));   // back-transform T blocks
-  b += 6 * align_up(N * sizeof(int));             // colk, cold, perm, Kp, nrot, spare
+  b += 7 * align_up(N * sizeof(int));             // colk, cold, perm, Kp, nrot, gperm, spare
+  b += align_up(2 * N * sizeof(int));             // gcnt
   return b + 4096;
 }
 
@@ -906,6 +1028,8 @@ int eig_sym_topk(double* A, int lda, int N, int nkeep, double* w, T* U, int ldu,
   W.perm = (int*)take(N * sizeof(int));
   W.Kp = (int*)take(N * sizeof(int));
   W.nrot = (int*)take(N * sizeof(int));
+  W.gperm = (int*)take(N * sizeof(int));
+  W.gcnt = (int*)take(2 * N * sizeof(int));
   W.mergeof = nullptr;
 
   cudaMemsetAsync(bar, 0, 16, st);
@@ -948,15 +1072,16 @@ int eig_sym_topk(double* A, int lda, int N, int nkeep, double* w, T* U, int ldu,
     const int* dmo = pe->d_mergeof + (size_t)lv * N;
     int kmax = 0;
     for (int q = m0; q < m1; ++q) kmax = std::max(kmax, pl.merges[q].hi - pl.merges[q].lo);
-    const size_t psmem = (size_t)kmax * (8 * sizeof(double) + 3 * sizeof(int));
+    const size_t psmem = prep_smem_bytes(kmax);
     if (psmem > 40 * 1024) cudaFuncSetAttribute(k_dc_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
-    k_dc_prep<<<nm, 256, psmem, st>>>(dm, e, N, W); note_launch();
+    k_dc_prep<<<nm, DC_THREADS, psmem, st>>>(dm, e, N, W); note_launch();
+    k_dc_rot<<<dim3((kmax + 127) / 128, nm), 128, 0, st>>>(dm, N, W); note_launch();
     k_dc_secular<<<(N * 32 + 255) / 256, 256, 0, st>>>(dm, dmo, N, W, err); note_launch();
     k_dc_zhat<<<(N * 32 + 255) / 256, 256, 0, st>>>(dm, dmo, N, W); note_launch();
     k_dc_vecs<<<(N * 32 + 255) / 256, 256, 0, st>>>(dm, dmo, N, W); note_launch();
     dim3 gg((kmax + DG_T - 1) / DG_T, (kmax + DG_T - 1) / DG_T, nm);
     k_dc_gemm<<<gg, 256, 0, st>>>(dm, N, W); note_launch();
-    const size_t fsmem = (size_t)kmax * (2 * sizeof(double) + 2 * sizeof(int));
+    const size_t fsmem = (size_t)kmax * (sizeof(double) + sizeof(long long));
     if (fsmem > 40 * 1024) cudaFuncSetAttribute(k_dc_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
     k_dc_finish<<<nm, 256, fsmem, st>>>(dm, N, W); note_launch();
     k_dc_copy<<<dim3((kmax + 7) / 8, nm), 256, 0, st>>>(dm, N, W); note_launch();
@@ -966,7 +1091,7 @@ int eig_sym_topk(double* A, int lda, int N, int nkeep, double* w, T* U, int ldu,
   {
     const int ng = std::max(1, (N - 2 + RB - 1) / RB);
     if (N >= 3) {
-      k_bt_tmat<<<(ng * 32 + 255) / 256, 256, 0, st>>>(A, lda, tau, N, W.Tm); note_launch();
+      k_bt_tmat<<<ng, 256, 0, st>>>(A, lda, tau, N, W.Tm); note_launch();
     }
     const size_t smem = (size_t)(RB + CB) * N * sizeof(double);
     if (smem > 40 * 1024) cudaFuncSetAttribute(k_backtransform<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -15,30 +15,37 @@ void note_launch(long long k = 1);
 template <class T> void prep_coords(const double* X, int n, int dim, double scale, C4<T>* out, cudaStream_t st);
 template <class T> void gather_coords(const C4<T>* X, const int* idx, int m, C4<T>* out, cudaStream_t st);
 template <class T>
-void gram_matvec(int ker, const C4<T>* Xo, const T* s, int m, T sf2, T* part, int nsplit, cudaStream_t st);
+// K(X_o, X_o) s into gram_matvec_slots(m) partial rows of part; with rp > 0 the same launch forms the
+// partials of Mo^T s (Mo: m x rp, ld ldm) into tpart for cg_combine
+void gram_matvec(int ker, const C4<T>* Xo, const T* s, int m, T sf2, T* part, const T* Mo, int ldm, int rp, T* tpart,
+                 const int* active, cudaStream_t st);
+// number of partial slots (rows of part, each m long) gram_matvec writes for m observations
+int gram_matvec_slots(int m);
 template <class T>
 void gram_block_simt(int ker, const C4<T>* Xr, int nr, const C4<T>* Xc, int nc, const T* B, int ldb, int width,
                      T sf2, T* Out, int ldo, cudaStream_t st);
 template <class T>
 void gram_block_dlogl_simt(int ker, const C4<T>* Xr, int nr, const C4<T>* Xc, int nc, const T* B, int ldb, int width,
                            T sf2, T* Out, int ldo, cudaStream_t st);
+// CG iteration j (non-FP64 modes skip cg_reorth; see the loop in cakf.cu):
+//   cg_combine: g = K s + sn2 s - a2 Mo t, and per-block partials of the first-pass dots (dpart1)
+//   cg_upd1:    first G-orthogonalisation pass, per-block partials of the second-pass dots (dpart2)
+//   cg_upd2:    second pass, scalars, V/GV/v/r update; with Snext the next action s = r
 template <class T>
 void cg_combine(const T* part, int nsplit, const T* s, T sn2, const T* Mo, int ldm, int r, const T* t, T a2, int m,
-                T* g, const int* active, cudaStream_t st);
+                T* g, const T* V, int ldv, int j, const T* r0, const T* v, double* dpart1, const int* active,
+                cudaStream_t st);
 template <class T>
 void gemv_t(const T* A, int lda, int rows, int cols, const T* x, T* t, const int* active, cudaStream_t st);
+// doubles needed for dpart1 followed by dpart2 at m observations and an action budget
+size_t cg_dpart_elems(int m, int budget);
 template <class T>
-void cg_dots1(const T* V, int ldv, int j, const T* s, const T* g, const T* r0, const T* v, int m, double* dots,
-              const int* active, cudaStream_t st);
+void cg_upd1(int j, const double* dpart1, double* dots1, T* V, T* GV, int ldv, const T* s, const T* g, int m,
+             double* dpart2, const int* active, cudaStream_t st);
 template <class T>
-void cg_upd1(int j, const double* dots, T* V, T* GV, int ldv, const T* s, const T* g, int m, const int* active,
-             cudaStream_t st);
-template <class T>
-void cg_dots2(const T* V, const T* GV, int ldv, int j, int m, double* dots, const int* active, cudaStream_t st);
-template <class T>
-void cg_upd2(int j, const double* dots1, const double* dots2, T* V, T* GV, int ldv, T* r, T* v, const T* s, T* Q,
+void cg_upd2(int j, const double* dots1, const double* dpart2, T* V, T* GV, int ldv, T* r, T* v, T* s, T* Q,
              int m, double bd_tol, double rtol2_r0sq, int use_rtol, int* active, double* eta, double* alpha,
-             int* count, cudaStream_t st);
+             int* count, T* Snext, cudaStream_t st);
 template <class T>
 void cg_reorth(const T* Q, int ldq, int j, T* s, int m, double* qd, T* S, int lds, const int* active, cudaStream_t st);
 template <class T>

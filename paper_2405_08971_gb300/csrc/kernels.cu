@@ -42,51 +42,126 @@ __global__ void k_gather_coords(const C4<T>* __restrict__ X, const int* __restri
 
 // ------------------------------------------------------------------------------------------
 // CG Gram matvec, split over columns; part is [nsplit][m].
-constexpr int MV_THREADS = 256;
-constexpr int MV_TILE = 256;
-
+// K(X_o, X_o) s for the CG actions, each kernel value evaluated once: the symmetric Gram is cut into
+// MVS_T x MVS_T tiles and one block evaluates tile (I, J), I <= J.  Row sums (weights s_J) give tile
+// I's share from J and, for I < J, column sums (weights s_I) give tile J's share from I.  The
+// shares land in distinct slots -- part[J][rows of I] and part[I][rows of J] -- so every row has
+// exactly nb = ceil(m / MVS_T) slots, each written once, summed in a fixed order by k_cg_combine.
+// A lane owns MVS_R rows of the tile; each warp takes 32 of its columns (staged in shared memory)
+// and reduces a column's MVS_R * 32 products with one warp sum.
+// The first ngv blocks instead form the partials of t = Mo^T s (one warp per column of Mo and
+// chunk of GV_CHUNK rows, as k_gemv_t), which k_cg_combine needs next: one launch for both.
+constexpr int MVS_T = 128, MVS_R = MVS_T / 32, MVS_W = MVS_T / 32;
+constexpr int GV_CHUNK = 1024;
 template <int KER, class T>
-__global__ void __launch_bounds__(MV_THREADS)
-k_gram_matvec(const C4<T>* __restrict__ Xo, const T* __restrict__ s, int m, int cols_per_split,
-              T sf2, T* __restrict__ part) {
-  __shared__ C4<T> xs[MV_TILE];
-  __shared__ T ss[MV_TILE];
-  const int row = blockIdx.x * MV_THREADS + threadIdx.x;
-  const int c0 = blockIdx.y * cols_per_split;
-  const int c1 = min(m, c0 + cols_per_split);
-  C4<T> xi;
-  if (row < m) xi = Xo[row]; else { xi.x = xi.y = xi.z = xi.w = T(0); }
-  T acc = T(0);
-  for (int t0 = c0; t0 < c1; t0 += MV_TILE) {
-    const int cnt = min(MV_TILE, c1 - t0);
-    __syncthreads();
-    for (int j = threadIdx.x; j < cnt; j += MV_THREADS) { xs[j] = Xo[t0 + j]; ss[j] = s[t0 + j]; }
-    __syncthreads();
-    if (cnt == MV_TILE) {
+__global__ void __launch_bounds__(MVS_W * 32)
+k_gram_matvec(const C4<T>* __restrict__ Xo, const T* __restrict__ s, int m, int nb, T sf2, T* __restrict__ part,
+              const T* __restrict__ Mo, int ldm, int rp, int ngv, T* __restrict__ tpart,
+              const int* __restrict__ active) {
+  if (active && !*active) return;
+  __shared__ C4<T> xs[MVS_T];
+  __shared__ T ss[MVS_T];
+  __shared__ T racc[MVS_W][MVS_T];
+  if ((int)blockIdx.x < ngv) {
+    const int per_chunk = (rp + MVS_W - 1) / MVS_W;
+    const int z = blockIdx.x / per_chunk;
+    const int col = (blockIdx.x - z * per_chunk) * MVS_W + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (col >= rp) return;
+    const int i0 = z * GV_CHUNK, i1 = min(m, i0 + GV_CHUNK);
+    const T* a = Mo + (size_t)col * ldm;
+    T acc = T(0);
 #pragma unroll 8
-      for (int j = 0; j < MV_TILE; ++j) acc = fma(kval<KER>(dist2(xi, xs[j]), sf2), ss[j], acc);
-    } else {
-      for (int j = 0; j < cnt; ++j) acc = fma(kval<KER>(dist2(xi, xs[j]), sf2), ss[j], acc);
+    for (int i = i0 + lane; i < i1; i += 32) acc = fma(a[i], s[i], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) tpart[(size_t)z * rp + col] = acc;
+    return;
+  }
+  int idx = blockIdx.x - ngv, I = 0;
+  while (idx >= nb - I) { idx -= nb - I; ++I; }
+  const int J = I + idx;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int t = threadIdx.x; t < MVS_T; t += blockDim.x) {
+    const int j = J * MVS_T + t;
+    C4<T> x;
+    x.x = x.y = x.z = x.w = T(0);
+    T v = T(0);
+    if (j < m) { x = Xo[j]; v = s[j]; }
+    xs[t] = x;
+    ss[t] = v;
+  }
+  C4<T> xi[MVS_R];
+  T si[MVS_R], acc[MVS_R];
+#pragma unroll
+  for (int r = 0; r < MVS_R; ++r) {
+    const int i = I * MVS_T + lane + 32 * r;
+    xi[r].x = xi[r].y = xi[r].z = xi[r].w = T(0);
+    si[r] = T(0);
+    if (i < m) { xi[r] = Xo[i]; si[r] = s[i]; }
+    acc[r] = T(0);
+  }
+  __syncthreads();
+  T cacc = T(0);
+  if (I == J) {
+#pragma unroll 4
+    for (int jj = 0; jj < 32; ++jj) {
+      const C4<T> xj = xs[warp * 32 + jj];
+      const T sj = ss[warp * 32 + jj];
+#pragma unroll
+      for (int r = 0; r < MVS_R; ++r) acc[r] = fma(kval<KER>(dist2(xi[r], xj), sf2), sj, acc[r]);
+    }
+  } else {
+#pragma unroll 4
+    for (int jj = 0; jj < 32; ++jj) {
+      const C4<T> xj = xs[warp * 32 + jj];
+      const T sj = ss[warp * 32 + jj];
+      T cp = T(0);
+#pragma unroll
+      for (int r = 0; r < MVS_R; ++r) {
+        const T kv = kval<KER>(dist2(xi[r], xj), sf2);
+        acc[r] = fma(kv, sj, acc[r]);
+        cp = fma(kv, si[r], cp);
+      }
+      cp = warp_sum(cp);
+      if (lane == jj) cacc = cp;
     }
   }
-  if (row < m) part[(size_t)blockIdx.y * m + row] = acc;
+#pragma unroll
+  for (int r = 0; r < MVS_R; ++r) racc[warp][lane + 32 * r] = acc[r];
+  __syncthreads();
+  for (int t = threadIdx.x; t < MVS_T; t += blockDim.x) {
+    const int i = I * MVS_T + t;
+    if (i >= m) continue;
+    T v = racc[0][t];
+#pragma unroll
+    for (int w = 1; w < MVS_W; ++w) v += racc[w][t];
+    part[(size_t)J * m + i] = v;
+  }
+  if (I != J) {
+    const int j = J * MVS_T + warp * 32 + lane;
+    if (j < m) part[(size_t)I * m + j] = cacc;
+  }
 }
 
 // g = sum_p part[p] + sn2 * s - a2 * Mo t     (Mo: m x r col-major, ld = ldm).  t is summed from
 // the row-chunk partials of k_gemv_t (tz chunks) into shared memory first.  A block owns CB_ROWS
 // rows: lane = row, each of the CB_WARPS warps takes every CB_WARPS-th column of Mo (coalesced
 // 128-byte column segments, CB_UNROLL independent accumulators), and the warps' sums are added
-// in shared memory.
+// in shared memory.  The block then forms its rows' share of the first dot pass of CG iteration j
+//   q < j: V[:, q] . g ;  j: s . g ;  j+1: s . r0 ;  j+2: g . v ;  j+3: s . s
+// into dpart[q * gridDim.x + block] (summed in FP64 by k_cg_upd1, in block order).
 constexpr int CB_ROWS = 32, CB_WARPS = 8, CB_UNROLL = 8;
 template <class T>
 __global__ void __launch_bounds__(CB_WARPS * 32)
 k_cg_combine(const T* __restrict__ part, int nsplit, const T* __restrict__ s, T sn2,
              const T* __restrict__ Mo, int ldm, int r, const T* __restrict__ tpart, int tz, T a2,
-             int m, T* __restrict__ g, const int* __restrict__ active) {
+             int m, T* __restrict__ g, const T* __restrict__ V, int ldv, int j, const T* __restrict__ r0,
+             const T* __restrict__ v, double* __restrict__ dpart, const int* __restrict__ active) {
   if (!*active) return;
   extern __shared__ unsigned char sm_raw[];
   T* t = reinterpret_cast<T*>(sm_raw);                 // r coefficients
-  __shared__ T red[CB_WARPS][CB_ROWS];
+  __shared__ T red[CB_WARPS][CB_ROWS], redk[CB_WARPS][CB_ROWS];
+  __shared__ T gsh[CB_ROWS];
   for (int l = threadIdx.x; l < r; l += blockDim.x) {
     T acc = T(0);
     for (int z = 0; z < tz; ++z) acc += tpart[(size_t)z * r + l];
@@ -114,21 +189,43 @@ k_cg_combine(const T* __restrict__ part, int nsplit, const T* __restrict__ s, T 
 #pragma unroll
   for (int u = 0; u < CB_UNROLL; ++u) lr += acc[u];
   red[warp][lane] = lr;
+  // the Gram partials: warp w sums slots w, w + CB_WARPS, ...
+  T kw = T(0);
+  if (valid)
+    for (int p = warp; p < nsplit; p += CB_WARPS) kw += part[(size_t)p * m + i];
+  redk[warp][lane] = kw;
   __syncthreads();
-  if (warp == 0 && valid) {
-    T low = T(0);
+  if (warp == 0) {
+    T gv = T(0);
+    if (valid) {
+      T low = T(0), kv = T(0);
 #pragma unroll
-    for (int w = 0; w < CB_WARPS; ++w) low += red[w][lane];
-    T kv = T(0);
-    for (int p = 0; p < nsplit; ++p) kv += part[(size_t)p * m + i];
-    kv = fma(sn2, s[i], kv);
-    g[i] = fma(-a2, low, kv);
+      for (int w = 0; w < CB_WARPS; ++w) { low += red[w][lane]; kv += redk[w][lane]; }
+      kv = fma(sn2, s[i], kv);
+      gv = fma(-a2, low, kv);
+      g[i] = gv;
+    }
+    gsh[lane] = gv;
+  }
+  __syncthreads();
+  const T gi = gsh[lane];
+  const T si = valid ? s[i] : T(0);
+  for (int q = warp; q < j + 4; q += CB_WARPS) {
+    T pr = T(0);
+    if (valid) {
+      if (q < j) pr = V[(size_t)q * ldv + i] * gi;
+      else if (q == j) pr = si * gi;
+      else if (q == j + 1) pr = si * r0[i];
+      else if (q == j + 2) pr = gi * v[i];
+      else pr = si * si;
+    }
+    pr = warp_sum(pr);
+    if (lane == 0) dpart[(size_t)q * gridDim.x + blockIdx.x] = double(pr);
   }
 }
 
 // Partial transposed products: part[z][l] = sum_{i in row chunk z} A[i, l] x[i]  (A: rows x cols col-major).
 // One warp per (column, row chunk); the chunks are summed by the consumer (k_cg_combine).
-constexpr int GV_CHUNK = 1024;
 template <class T>
 __global__ void k_gemv_t(const T* __restrict__ A, int lda, int rows, int cols, const T* __restrict__ x,
                          T* __restrict__ part, const int* __restrict__ active) {
@@ -168,77 +265,98 @@ template <class T> __device__ __forceinline__ double dot_part(const T* __restric
   }
 }
 
-// First dot pass of CG iteration j (one block per dot):
-//   q < j: V[:, q] . g ;  j: s . g ;  j+1: s . r0 ;  j+2: g . v ;  j+3: s . s
+// First G-orthogonalisation pass of CG iteration j.  The first-pass dots are summed from the
+// combine blocks' partials (FP64, fixed order; block 0 also stores all j + 4 of them in dots1):
+// c = V^T G s, then d = s - V c, G d = g - GV c, parked unnormalised in column j of V and GV.
+// The block then forms its rows' share of the second-pass dots (q < j: V[:, q] . G d; j: d . G d)
+// into dpart2[q * gridDim.x + block].
+constexpr int UP_THREADS = 256;
 template <class T>
-__global__ void k_cg_dots1(const T* __restrict__ V, int ldv, int j, const T* __restrict__ s,
-                           const T* __restrict__ g, const T* __restrict__ r0, const T* __restrict__ v, int m,
-                           double* __restrict__ dots, const int* __restrict__ active) {
-  if (!*active) return;
-  const int q = blockIdx.x;
-  const T *a, *b;
-  if (q < j) { a = V + (size_t)q * ldv; b = g; }
-  else if (q == j) { a = s; b = g; }
-  else if (q == j + 1) { a = s; b = r0; }
-  else if (q == j + 2) { a = g; b = v; }
-  else { a = s; b = s; }
-  const double acc = block_sum(dot_part(a, b, m));
-  if (threadIdx.x == 0) dots[q] = acc;
-}
-
-// First G-orthogonalisation pass: d = s - V c, G d = g - GV c with c = V^T G s (= dots[0..j)).
-// d and G d are parked, unnormalised, in column j of V and GV.
-template <class T>
-__global__ void k_cg_upd1(int j, const double* __restrict__ dots, T* __restrict__ V, T* __restrict__ GV, int ldv,
-                          const T* __restrict__ s, const T* __restrict__ g, int m, const int* __restrict__ active) {
+__global__ void __launch_bounds__(UP_THREADS)
+k_cg_upd1(int j, const double* __restrict__ dpart1, int nblk1, double* __restrict__ dots1, T* __restrict__ V,
+          T* __restrict__ GV, int ldv, const T* __restrict__ s, const T* __restrict__ g, int m,
+          double* __restrict__ dpart2, const int* __restrict__ active) {
   if (!*active) return;
   __shared__ T c[1024];
-  for (int q = threadIdx.x; q < j; q += blockDim.x) c[q] = T(dots[q]);
-  __syncthreads();
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m) return;
-  T d = s[i], gd = g[i];
-  for (int q = 0; q < j; ++q) {
-    const T cq = c[q];
-    d = fma(-V[(size_t)q * ldv + i], cq, d);
-    gd = fma(-GV[(size_t)q * ldv + i], cq, gd);
+  __shared__ T sd[UP_THREADS], sgd[UP_THREADS];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int nq = (blockIdx.x == 0) ? j + 4 : j;
+  for (int q = warp; q < nq; q += nw) {
+    double acc = 0.0;
+    for (int b = lane; b < nblk1; b += 32) acc += dpart1[(size_t)q * nblk1 + b];
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      if (q < j) c[q] = T(acc);
+      if (blockIdx.x == 0) dots1[q] = acc;
+    }
   }
-  V[(size_t)j * ldv + i] = d;
-  GV[(size_t)j * ldv + i] = gd;
-}
-
-// Second dot pass: q < j: V[:, q] . (G d) ;  q = j: d . (G d)
-template <class T>
-__global__ void k_cg_dots2(const T* __restrict__ V, const T* __restrict__ GV, int ldv, int j, int m,
-                           double* __restrict__ dots, const int* __restrict__ active) {
-  if (!*active) return;
-  const int q = blockIdx.x;
-  const T* gd = GV + (size_t)j * ldv;
-  const T* a = V + (size_t)q * ldv;     // q == j: d itself
-  const double acc = block_sum(dot_part(a, gd, m));
-  if (threadIdx.x == 0) dots[q] = acc;
+  __syncthreads();
+  const int row0 = blockIdx.x * blockDim.x;
+  const int i = row0 + threadIdx.x;
+  T d = T(0), gd = T(0);
+  if (i < m) {
+    d = s[i];
+    gd = g[i];
+    for (int q = 0; q < j; ++q) {
+      const T cq = c[q];
+      d = fma(-V[(size_t)q * ldv + i], cq, d);
+      gd = fma(-GV[(size_t)q * ldv + i], cq, gd);
+    }
+    V[(size_t)j * ldv + i] = d;
+    GV[(size_t)j * ldv + i] = gd;
+  }
+  sd[threadIdx.x] = d;
+  sgd[threadIdx.x] = gd;
+  __syncthreads();
+  const int nrow = min((int)blockDim.x, m - row0);
+  for (int q = warp; q <= j; q += nw) {
+    T acc = T(0);
+    if (q < j) {
+      const T* vq = V + (size_t)q * ldv + row0;
+      for (int t = lane; t < nrow; t += 32) acc = fma(vq[t], sgd[t], acc);
+    } else {
+      for (int t = lane; t < nrow; t += 32) acc = fma(sd[t], sgd[t], acc);
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) dpart2[(size_t)q * gridDim.x + blockIdx.x] = double(acc);
+  }
 }
 
 // Second pass and the update of the iterative CAKF step (appendix algorithm):
 //   c2 = V^T G d;  d <- d - V c2;  eta = d^T G d - |c2|^2;  alpha = s^T (r0 - G v) = s^T r0 - g^T v;
 //   V[:, j] = d / sqrt(eta);  GV[:, j] = G d / sqrt(eta);  v += (alpha / eta) d;  r -= (alpha / eta) G d.
-// Every block recomputes the scalars from the dot results and takes the same stop decision.
+// Every block sums the second-pass dots from the k_cg_upd1 partials, recomputes the scalars and
+// takes the same stop decision.  With Snext (CG policy, no re-orthogonalisation) the next action
+// -- the updated residual -- is written to s and to column j + 1 of S here.
 template <class T>
-__global__ void k_cg_upd2(int j, const double* __restrict__ dots1, const double* __restrict__ dots2,
-                          T* __restrict__ V, T* __restrict__ GV, int ldv, T* __restrict__ r, T* __restrict__ v,
-                          const T* __restrict__ s, T* __restrict__ Q, int m,
-                          double bd_tol, double rtol2_r0sq, int use_rtol, int* __restrict__ active,
-                          double* __restrict__ eta_out, double* __restrict__ alpha_out, int* __restrict__ count) {
+__global__ void __launch_bounds__(UP_THREADS)
+k_cg_upd2(int j, const double* __restrict__ dots1, const double* __restrict__ dpart2, int nblk2,
+          T* __restrict__ V, T* __restrict__ GV, int ldv, T* __restrict__ r, T* __restrict__ v,
+          T* __restrict__ s, T* __restrict__ Q, int m,
+          double bd_tol, double rtol2_r0sq, int use_rtol, int* __restrict__ active,
+          double* __restrict__ eta_out, double* __restrict__ alpha_out, int* __restrict__ count,
+          T* __restrict__ Snext) {
   if (!*active) return;
   __shared__ T c[1024];
+  __shared__ double cd[1025];
   __shared__ double sh[3];
-  for (int q = threadIdx.x; q < j; q += blockDim.x) c[q] = T(dots2[q]);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int q = warp; q <= j; q += nw) {
+    double acc = 0.0;
+    for (int b = lane; b < nblk2; b += 32) acc += dpart2[(size_t)q * nblk2 + b];
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      cd[q] = acc;
+      if (q < j) c[q] = T(acc);
+    }
+  }
+  __syncthreads();
   double ccp = 0.0;
-  for (int q = threadIdx.x; q < j; q += blockDim.x) ccp = fma(dots2[q], dots2[q], ccp);
+  for (int q = threadIdx.x; q < j; q += blockDim.x) ccp = fma(cd[q], cd[q], ccp);
   const double cc = block_sum(ccp);
   if (threadIdx.x == 0) {
     const double sg = dots1[j];
-    const double eta = dots2[j] - cc;
+    const double eta = cd[j] - cc;
     const double alpha = dots1[j + 1] - dots1[j + 2];
     int stop = !(eta > bd_tol * sg) || !isfinite(eta) || !isfinite(alpha);
     if (use_rtol && dots1[j + 3] <= rtol2_r0sq) stop = 1;
@@ -265,8 +383,13 @@ __global__ void k_cg_upd2(int j, const double* __restrict__ dots1, const double*
     V[(size_t)j * ldv + i] = d * inv;
     GV[(size_t)j * ldv + i] = gd * inv;
     v[i] = fma(coef, d, v[i]);
-    r[i] = fma(-coef, gd, r[i]);
+    const T rn = fma(-coef, gd, r[i]);
+    r[i] = rn;
     if (Q) Q[(size_t)j * ldv + i] = s[i] * T(1.0 / sqrt(dots1[j + 3]));
+    if (Snext) {
+      s[i] = rn;
+      Snext[i] = rn;
+    }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) { eta_out[j] = eta; alpha_out[j] = alpha; *count = j + 1; }
 }
@@ -883,6 +1006,80 @@ __global__ void k_nll_def(const int* __restrict__ count, double* __restrict__ Gh
   }
 }
 
+// The same NLL term with both j x j factorisations in shared memory (one matrix at a time, j <= ld
+// and ld * (ld + 1) doubles of dynamic shared memory): a pivot step costs two block barriers on
+// shared memory instead of global-memory round trips.
+__device__ bool smem_cholesky(double* S, int j) {
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int p = 0; p < j; ++p) {
+    double d = S[p * j + p];
+    const bool bd = !(d > 0.0) || !isfinite(d);
+    if (bd) d = 1.0;
+    const double piv = sqrt(d);
+    for (int q = p + 1 + threadIdx.x; q < j; q += blockDim.x) S[p * j + q] /= piv;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      S[p * j + p] = piv;
+      if (bd) bad = 1;
+    }
+    const int w = j - p - 1;
+    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+      const int q = p + 1 + e % w, c = p + 1 + e / w;
+      if (q >= c) S[c * j + q] -= S[p * j + q] * S[p * j + c];
+    }
+    __syncthreads();
+  }
+  const bool ok = bad == 0;
+  __syncthreads();
+  return ok;
+}
+
+__global__ void k_nll_def_smem(const int* __restrict__ count, const double* __restrict__ Gh,
+                               const double* __restrict__ SS, int ld, const double* __restrict__ yh,
+                               double* __restrict__ nll_k, int* __restrict__ err) {
+  extern __shared__ double nsm[];
+  const int j = min(*count, ld);
+  double* S = nsm;                 // j x j, ld j
+  double* b = nsm + (size_t)j * j; // right-hand side of the forward substitution
+  __shared__ double s_ld1, s_quad;
+  // symmetrised copy of S^T G S
+  for (int e = threadIdx.x; e < j * j; e += blockDim.x) {
+    const int r = e % j, c = e / j;
+    if (r >= c) S[c * j + r] = (r == c) ? Gh[(size_t)c * ld + r] : 0.5 * (Gh[(size_t)c * ld + r] + Gh[(size_t)r * ld + c]);
+  }
+  for (int q = threadIdx.x; q < j; q += blockDim.x) b[q] = yh[q];
+  const bool ok1 = smem_cholesky(S, j);
+  // L z = yh (column oriented: z_q = b_q / L_qq, then b_l -= L_lq z_q below)
+  double quad = 0.0;
+  for (int q = 0; q < j; ++q) {
+    const double zq = b[q] / S[q * j + q];
+    quad = fma(zq, zq, quad);
+    for (int l = q + 1 + threadIdx.x; l < j; l += blockDim.x) b[l] -= S[q * j + l] * zq;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double ld1 = 0.0;
+    for (int q = 0; q < j; ++q) ld1 += log(S[q * j + q]);
+    s_ld1 = ld1;
+    s_quad = quad;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < j * j; e += blockDim.x) {
+    const int r = e % j, c = e / j;
+    if (r >= c) S[c * j + r] = (r == c) ? SS[(size_t)c * ld + r] : 0.5 * (SS[(size_t)c * ld + r] + SS[(size_t)r * ld + c]);
+  }
+  const bool ok2 = smem_cholesky(S, j);
+  if (threadIdx.x == 0) {
+    double ld2 = 0.0;
+    for (int q = 0; q < j; ++q) ld2 += log(S[q * j + q]);
+    const double val = 0.5 * j * 1.8378770664093453 + s_ld1 + 0.5 * s_quad - ld2;
+    *nll_k = val;
+    if (!ok1 || !ok2 || !isfinite(val)) atomicExch(err, kErrNumeric);
+  }
+}
+
 __global__ void k_set_diag(double* __restrict__ G, int ld, const double* __restrict__ lam, double scale, int r) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < r) G[(size_t)i * ld + i] = scale * lam[i];
@@ -934,16 +1131,21 @@ void gather_coords(const C4<T>* X, const int* idx, int m, C4<T>* out, cudaStream
   k_gather_coords<T><<<cdiv(m, 256), 256, 0, st>>>(X, idx, m, out); note_launch();
 }
 
+int gram_matvec_slots(int m) { return std::max(1, (m + MVS_T - 1) / MVS_T); }
+
 template <class T>
-void gram_matvec(int ker, const C4<T>* Xo, const T* s, int m, T sf2, T* part, int nsplit, cudaStream_t st) {
+void gram_matvec(int ker, const C4<T>* Xo, const T* s, int m, T sf2, T* part, const T* Mo, int ldm, int rp, T* tpart,
+                 const int* active, cudaStream_t st) {
   if (m <= 0) return;
-  int cps = (m + nsplit - 1) / nsplit;
-  dim3 grid(cdiv(m, MV_THREADS), nsplit);
+  const int nb = gram_matvec_slots(m);
+  const int ngv = rp > 0 ? (int)cdiv(m, GV_CHUNK) * (int)cdiv(rp, MVS_W) : 0;
+  const int grid = ngv + nb * (nb + 1) / 2;
   switch (ker) {
-    case 0: k_gram_matvec<0, T><<<grid, MV_THREADS, 0, st>>>(Xo, s, m, cps, sf2, part); note_launch(); break;
-    case 1: k_gram_matvec<1, T><<<grid, MV_THREADS, 0, st>>>(Xo, s, m, cps, sf2, part); note_launch(); break;
-    default: k_gram_matvec<2, T><<<grid, MV_THREADS, 0, st>>>(Xo, s, m, cps, sf2, part); note_launch(); break;
+    case 0: k_gram_matvec<0, T><<<grid, MVS_W * 32, 0, st>>>(Xo, s, m, nb, sf2, part, Mo, ldm, rp, ngv, tpart, active); break;
+    case 1: k_gram_matvec<1, T><<<grid, MVS_W * 32, 0, st>>>(Xo, s, m, nb, sf2, part, Mo, ldm, rp, ngv, tpart, active); break;
+    default: k_gram_matvec<2, T><<<grid, MVS_W * 32, 0, st>>>(Xo, s, m, nb, sf2, part, Mo, ldm, rp, ngv, tpart, active); break;
   }
+  note_launch();
 }
 
 template <class T>
@@ -973,10 +1175,11 @@ void gram_block_dlogl_simt(int ker, const C4<T>* Xr, int nr, const C4<T>* Xc, in
 
 template <class T>
 void cg_combine(const T* part, int nsplit, const T* s, T sn2, const T* Mo, int ldm, int r, const T* t, T a2, int m,
-                T* g, const int* active, cudaStream_t st) {
+                T* g, const T* V, int ldv, int j, const T* r0, const T* v, double* dpart1, const int* active,
+                cudaStream_t st) {
   const int tz = std::max(1, (m + GV_CHUNK - 1) / GV_CHUNK);
-  k_cg_combine<T><<<cdiv(m, CB_ROWS), CB_WARPS * 32, std::max(r, 1) * sizeof(T), st>>>(part, nsplit, s, sn2, Mo, ldm,
-                                                                                      r, t, tz, a2, m, g, active);
+  k_cg_combine<T><<<cdiv(m, CB_ROWS), CB_WARPS * 32, std::max(r, 1) * sizeof(T), st>>>(
+      part, nsplit, s, sn2, Mo, ldm, r, t, tz, a2, m, g, V, ldv, j, r0, v, dpart1, active);
   note_launch();
 }
 // t must hold ceil(rows / 1024) * cols partials (summed by cg_combine)
@@ -986,26 +1189,23 @@ void gemv_t(const T* A, int lda, int rows, int cols, const T* x, T* t, const int
   const int tz = std::max(1, (rows + GV_CHUNK - 1) / GV_CHUNK);
   k_gemv_t<T><<<dim3(cdiv((size_t)cols * 32, 256), tz), 256, 0, st>>>(A, lda, rows, cols, x, t, active); note_launch();
 }
-template <class T>
-void cg_dots1(const T* V, int ldv, int j, const T* s, const T* g, const T* r0, const T* v, int m, double* dots,
-              const int* active, cudaStream_t st) {
-  k_cg_dots1<T><<<j + 4, 256, 0, st>>>(V, ldv, j, s, g, r0, v, m, dots, active); note_launch();
+size_t cg_dpart_elems(int m, int budget) {
+  return (size_t)(budget + 4) * cdiv(std::max(m, 1), CB_ROWS) + (size_t)(budget + 1) * cdiv(std::max(m, 1), UP_THREADS);
 }
 template <class T>
-void cg_upd1(int j, const double* dots, T* V, T* GV, int ldv, const T* s, const T* g, int m, const int* active,
-             cudaStream_t st) {
-  k_cg_upd1<T><<<cdiv(m, 256), 256, 0, st>>>(j, dots, V, GV, ldv, s, g, m, active); note_launch();
+void cg_upd1(int j, const double* dpart1, double* dots1, T* V, T* GV, int ldv, const T* s, const T* g, int m,
+             double* dpart2, const int* active, cudaStream_t st) {
+  k_cg_upd1<T><<<cdiv(m, UP_THREADS), UP_THREADS, 0, st>>>(j, dpart1, (int)cdiv(m, CB_ROWS), dots1, V, GV, ldv, s, g, m,
+                                                           dpart2, active);
+  note_launch();
 }
 template <class T>
-void cg_dots2(const T* V, const T* GV, int ldv, int j, int m, double* dots, const int* active, cudaStream_t st) {
-  k_cg_dots2<T><<<j + 1, 256, 0, st>>>(V, GV, ldv, j, m, dots, active); note_launch();
-}
-template <class T>
-void cg_upd2(int j, const double* dots1, const double* dots2, T* V, T* GV, int ldv, T* r, T* v, const T* s, T* Q,
+void cg_upd2(int j, const double* dots1, const double* dpart2, T* V, T* GV, int ldv, T* r, T* v, T* s, T* Q,
              int m, double bd_tol, double rtol2_r0sq, int use_rtol, int* active, double* eta, double* alpha,
-             int* count, cudaStream_t st) {
-  k_cg_upd2<T><<<cdiv(m, 256), 256, 0, st>>>(j, dots1, dots2, V, GV, ldv, r, v, s, Q, m, bd_tol, rtol2_r0sq,
-                                             use_rtol, active, eta, alpha, count);
+             int* count, T* Snext, cudaStream_t st) {
+  k_cg_upd2<T><<<cdiv(m, UP_THREADS), UP_THREADS, 0, st>>>(j, dots1, dpart2, (int)cdiv(m, UP_THREADS), V, GV, ldv, r, v,
+                                                           s, Q, m, bd_tol, rtol2_r0sq, use_rtol, active, eta, alpha,
+                                                           count, Snext);
   note_launch();
 }
 template <class T>
@@ -1201,6 +1401,12 @@ template void tangent_mean<double>(const double*, const double*, size_t, int, in
 
 void nll_def(const int* count, double* Gh, double* SS, int ld, const double* yh, double* z, double* nll_k, int* err,
              cudaStream_t st) {
+  const size_t smem = ((size_t)ld * ld + ld) * sizeof(double);
+  if (smem <= 200 * 1024) {
+    if (smem > 40 * 1024) cudaFuncSetAttribute(k_nll_def_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_nll_def_smem<<<1, 256, smem, st>>>(count, Gh, SS, ld, yh, nll_k, err); note_launch();
+    return;
+  }
   k_nll_def<<<1, 256, 0, st>>>(count, Gh, SS, ld, yh, z, nll_k, err); note_launch();
 }
 
@@ -1233,20 +1439,19 @@ void check_finite(const double* x, size_t n, int* err, cudaStream_t st) {
 #define INST(T)                                                                                                  \
   template void prep_coords<T>(const double*, int, int, double, C4<T>*, cudaStream_t);                           \
   template void gather_coords<T>(const C4<T>*, const int*, int, C4<T>*, cudaStream_t);                          \
-  template void gram_matvec<T>(int, const C4<T>*, const T*, int, T, T*, int, cudaStream_t);                      \
+  template void gram_matvec<T>(int, const C4<T>*, const T*, int, T, T*, const T*, int, int, T*, const int*,     \
+                               cudaStream_t);                                                                   \
   template void gram_block_simt<T>(int, const C4<T>*, int, const C4<T>*, int, const T*, int, int, T, T*, int,    \
                                    cudaStream_t);                                                                \
   template void gram_block_dlogl_simt<T>(int, const C4<T>*, int, const C4<T>*, int, const T*, int, int, T, T*,   \
                                          int, cudaStream_t);                                                     \
-  template void cg_combine<T>(const T*, int, const T*, T, const T*, int, int, const T*, T, int, T*, const int*,   \
-                              cudaStream_t);                                                                     \
+  template void cg_combine<T>(const T*, int, const T*, T, const T*, int, int, const T*, T, int, T*, const T*,     \
+                              int, int, const T*, const T*, double*, const int*, cudaStream_t);                  \
   template void gemv_t<T>(const T*, int, int, int, const T*, T*, const int*, cudaStream_t);                      \
-  template void cg_dots1<T>(const T*, int, int, const T*, const T*, const T*, const T*, int, double*,          \
-                            const int*, cudaStream_t);                                                           \
-  template void cg_upd1<T>(int, const double*, T*, T*, int, const T*, const T*, int, const int*, cudaStream_t);  \
-  template void cg_dots2<T>(const T*, const T*, int, int, int, double*, const int*, cudaStream_t);               \
-  template void cg_upd2<T>(int, const double*, const double*, T*, T*, int, T*, T*, const T*, T*, int, double,  \
-                           double, int, int*, double*, double*, int*, cudaStream_t);                             \
+  template void cg_upd1<T>(int, const double*, double*, T*, T*, int, const T*, const T*, int, double*,          \
+                           const int*, cudaStream_t);                                                            \
+  template void cg_upd2<T>(int, const double*, const double*, T*, T*, int, T*, T*, T*, T*, int, double, double,  \
+                           int, int*, double*, double*, int*, T*, cudaStream_t);                                 \
   template void cg_reorth<T>(const T*, int, int, T*, int, double*, T*, int, const int*, cudaStream_t);          \
   template void cg_select<T>(int, const T*, const double*, int, T*, T*, int, const int*, cudaStream_t);          \
   template void cg_init<T>(const double*, const double*, const int*, int, T*, T*, T*, double*, cudaStream_t);    \
