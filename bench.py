@@ -262,7 +262,7 @@ def main():
                                 "peak_source": peak_note.format("2 FP64 FMA/clk x 2"),
                                 "launches": prof["eig_calls"], "avg_ms": tri_ms / prof["eig_calls"],
                                 "ms_total": tri_ms,
-                                "note": "one grid barrier per Householder column: bound by barrier latency, not by FP64"}
+                                "note": "one cross-block exchange per Householder column (epoch-tagged words, no grid barrier): bound by its latency chain, not by FP64 throughput"}
     # tensor-core / SIMT Gram x block (filter finalize): kernel entries on MUFU (sqrt + exp2 each)
     if prof["gram_block_launches"]:
         gb_ms = prof["gram_block_ms"]

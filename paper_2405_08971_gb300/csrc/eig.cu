@@ -1,7 +1,8 @@
 // FP64 symmetric eigensolver for the truncation step (Truncate, Sec. 3.2: the top-r eigen-directions
 // of the (r+i) x (r+i) Gram of the downdate factor).
 //
-//   1. Householder tridiagonalisation, one cooperative kernel, two bounded grid barriers per column.
+//   1. Householder tridiagonalisation, one cooperative kernel; the blocks exchange each column's
+//      matvec and pivot column through epoch-tagged words (no grid barrier), with bounded polling.
 //   2. Divide and conquer on the tridiagonal (Cuppen's tearing; deflation of small z components and
 //      close poles by Givens rotations; secular roots by a two-pole rational model guarded by
 //      bisection; eigenvectors from the Loewner-corrected z (Gu-Eisenstat), which keeps them
@@ -35,43 +36,41 @@ __device__ __forceinline__ double nr_rcp(double x) {
   return r;
 }
 
-// Grid barrier on a monotonic arrival counter (the kernel is launched cooperatively, all blocks
-// co-resident): barrier number b completes when the counter reaches (b + 1) * gridDim.x, so no
-// block has to reset anything and a waiting block needs one read to see the last arrival.  The
-// wait is bounded: after `limit` polls it raises *err (timeout) and returns false.
-__device__ __forceinline__ bool mono_barrier(unsigned* count, unsigned target, int* err,
-                                             long long limit = 50000000LL) {
-  __syncthreads();
-  __shared__ int s_ok;
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    // release: the block's writes (ordered before this thread by the barrier above) become visible
-    // to any block whose acquiring read sees this arrival
-    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
-    long long spins = 0;
-    unsigned v;
-    while (true) {
-      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
-      if (v >= target) break;
-      if (++spins > limit) { atomicExch(err, kErrTimeout); ok = 0; break; }
-      if ((spins & 1023) == 0 && *(volatile int*)err) { ok = 0; break; }
-    }
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
+// Per-step exchange without a grid barrier: every FP64 word a block publishes for step k carries the
+// step's epoch (k mod 4) in its two lowest mantissa bits (a relative change below 7e-16), and the
+// consumers poll the words themselves until all carry the epoch they wait for.  Each 8-byte word
+// is written and read as one access, so a reader sees either the old or the new word; the data
+// dependence of the recursion (no block can publish step k + 2 before every block has published
+// step k + 1, which needs step k consumed) makes two buffers enough.
+__device__ __forceinline__ double with_epoch(double x, int ep) {
+  return __longlong_as_double((__double_as_longlong(x) & ~3LL) | (long long)ep);
 }
+__device__ __forceinline__ int epoch_of(double x) { return (int)(__double_as_longlong(x) & 3LL); }
+__device__ __forceinline__ double ld_relaxed(const double* p) {
+  double v;
+  asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed(double* p, double v) {
+  asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+__device__ __forceinline__ int ld_relaxed_int(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+constexpr long long kPollLimit = 4000000LL;
 
 // ---------------------------------------------------------------------------------- tridiagonal
-// Householder tridiagonalisation (lower), one grid barrier per column.  Columns of the trailing
-// block are owned by (block, warp) round-robin and stay resident in shared memory.  At step k every
-// block reads p_k = tau_k A22 v_k and the pre-update pivot column k+1 from double buffers written
-// before the barrier, forms w_k = p_k - 1/2 tau_k (p_k . v_k) v_k, the updated pivot column and
-// from it v_{k+1}, tau_{k+1} (all redundantly, so no second barrier is needed); the owners then
-// update their columns and, in the same pass, compute their entries of p_{k+1} and publish the
-// next pivot column.  Reflector v_k is stored in column k below the subdiagonal (v_k[0] = 1).
-// Block reductions go through shared memory and one warp (the FP64 pipe is narrow on this GPU, so
-// a shuffle tree in every warp would cost more than the data it sums).
+// Householder tridiagonalisation (lower), one exchange of epoch-tagged words per column.  Columns
+// of the trailing block are owned by (block, warp) round-robin and stay resident in shared memory.
+// At step k every block reads p_k = tau_k A22 v_k and the pre-update pivot column k+1 from double
+// buffers the owners published during step k-1, forms w_k = p_k - 1/2 tau_k (p_k . v_k) v_k, the
+// updated pivot column and from it v_{k+1}, tau_{k+1} (all redundantly, so nothing else has to be
+// exchanged); the owners then update their columns and, in the same pass, compute their entries of
+// p_{k+1} and publish the next pivot column.  Reflector v_k is stored in column k below the
+// subdiagonal (v_k[0] = 1).  Block reductions go through shared memory and one warp (the FP64 pipe
+// is narrow on this GPU, so a shuffle tree in every warp would cost more than the data it sums).
 constexpr int TD_THREADS = 128;
 
 // Householder scalars for x (x[0] = alpha, sum of the squares of x[1..] = sigma): H x = beta e_1,
@@ -93,7 +92,7 @@ __device__ __forceinline__ double warp0_sum(const double* red) {
 
 __global__ void __launch_bounds__(TD_THREADS)
 k_tridiag(double* __restrict__ A, int lda, int N, double* __restrict__ d, double* __restrict__ e,
-          double* __restrict__ tau, double* __restrict__ Pbuf, double* __restrict__ Cbuf, unsigned* bar, int* err) {
+          double* __restrict__ tau, double* __restrict__ Pbuf, double* __restrict__ Cbuf, int* err) {
   extern __shared__ double sm[];
   // sm[0, N) and sm[N, 2N): v_k and v_{k+1}, swapped every step
   double* w = sm + 2 * N;           // w_k
@@ -149,13 +148,12 @@ k_tridiag(double* __restrict__ A, int lda, int N, double* __restrict__ d, double
       double acc = 0.0;
       for (int t = lane; t < L; t += 32) acc = fma(col[t], v[t], acc);
       acc = warp_sum(acc);
-      if (lane == 0) Pbuf[j - 1] = tk * acc;
-      if (j == 1) for (int t = lane; t < L; t += 32) Cbuf[t] = col[t];
+      if (lane == 0) st_relaxed(Pbuf + j - 1, with_epoch(tk * acc, 0));
+      if (j == 1) for (int t = lane; t < L; t += 32) st_relaxed(Cbuf + t, with_epoch(col[t], 0));
     }
     if (blockIdx.x == 0 && tid == 0) d[0] = A[0];
-    if (!mono_barrier(bar, (unsigned)G, err)) return;
+    __syncthreads();
   }
-  unsigned nbar = 1;
   for (int k = 0; k + 2 < N; ++k) {
     const int L = N - k - 1;
     const double* Pk = Pbuf + (size_t)(k & 1) * N;
@@ -165,16 +163,28 @@ k_tridiag(double* __restrict__ A, int lda, int N, double* __restrict__ d, double
     const double* v = sm + (size_t)(k & 1) * N;
     double* v2 = sm + (size_t)((k + 1) & 1) * N;
     const bool next = (k + 3 < N);      // a reflector for column k+1 exists
-    // (1) p_k . v_k; the pivot column C_k is fetched in the same pass (into c)
+    // (1) p_k . v_k; the pivot column C_k is fetched in the same pass (into c).  Each thread polls
+    // its entries of P_k and C_k until they carry epoch k mod 4 (bounded; a timeout or another
+    // block's error ends the kernel).
+    const int ek = k & 3;
     double part = 0.0;
-    for (int t = tid; t < L; t += TB) {
-      const double pt = __ldcg(Pk + t);
-      c[t] = __ldcg(Ck + t);
+    bool ok = true;
+    for (int t = tid; t < L && ok; t += TB) {
+      double pt, ct;
+      long long spins = 0;
+      while (true) {
+        pt = ld_relaxed(Pk + t);
+        ct = ld_relaxed(Ck + t);
+        if (epoch_of(pt) == ek && epoch_of(ct) == ek) break;
+        if (++spins > kPollLimit) { atomicExch(err, kErrTimeout); ok = false; break; }
+        if ((spins & 255) == 0 && ld_relaxed_int(err)) { ok = false; break; }
+      }
+      c[t] = ct;
       w[t] = pt;
       part = fma(pt, v[t], part);
     }
     red[tid] = part;
-    __syncthreads();
+    if (!__syncthreads_and(ok)) return;
     if (warp == 0) {
       const double pv = warp0_sum(red);
       if (lane == 0) {
@@ -229,11 +239,11 @@ k_tridiag(double* __restrict__ A, int lda, int N, double* __restrict__ d, double
         const double nv = fma(-v[t], wj, fma(-w[t], vj, col[t]));
         col[t] = nv;
         if (next && t >= 1) acc = fma(nv, v2[t - 1], acc);
-        if (publish && t >= 1) Cn[t - 1] = nv;
+        if (publish && t >= 1) st_relaxed(Cn + t - 1, with_epoch(nv, (k + 1) & 3));
       }
       if (next && tj >= 1) {
         acc = warp_sum(acc);
-        if (lane == 0) Pn[tj - 1] = tn * acc;
+        if (lane == 0) st_relaxed(Pn + tj - 1, with_epoch(tn * acc, (k + 1) & 3));
       }
       if (k + 3 == N && j == N - 1) {                  // last diagonal entry (written by lane L-1)
         __syncwarp();
@@ -245,7 +255,7 @@ k_tridiag(double* __restrict__ A, int lda, int N, double* __restrict__ d, double
       for (int t = tid; t < L; t += TB) A[(size_t)k * lda + k + 1 + t] = v[t];
     tk = tn;
     bk = bn;
-    if (!mono_barrier(bar, (unsigned)G * ++nbar, err)) return;
+    __syncthreads();
   }
 }
 
@@ -395,14 +405,38 @@ k_dc_prep(const MergeDesc* __restrict__ merges, const double* __restrict__ e, in
   for (int t = threadIdx.x; t < K; t += blockDim.x) sStat[t] = (rho * fabs(sZ[t]) <= tol) ? 1 : 0;
   __syncthreads();
   // 3. close poles.  The test |(D_j - D_l) c s| <= tol with c s = -z_l z_j / t^2 is evaluated
-  // without the division, as |D_j - D_l| |z_l z_j| <= tol t^2; c and s are formed only for a rotation.
+  // without the division, as |D_j - D_l| |z_l z_j| <= tol t^2; c and s are formed only for a
+  // rotation.  The pairs of consecutive candidates (entries not deflated by small z) are first tested
+  // in parallel on the merged values; a pair's test can only change after a rotation, so the
+  // sequential scan starts at the first pair that fires (in the common case none does).
+  const int ch0 = (K + (int)blockDim.x - 1) / (int)blockDim.x;
+  const int a0 = min(K, (int)threadIdx.x * ch0), a1 = min(K, a0 + ch0);
+  int ncl = 0;
+  for (int t = a0; t < a1; ++t) ncl += (sStat[t] == 0);
+  int nc = 0;
+  int oc = block_excl_scan(ncl, &nc);
+  int* sCand = sSort;                 // free until the kept poles are re-sorted below
+  for (int t = a0; t < a1; ++t)
+    if (sStat[t] == 0) sCand[oc++] = t;
+  __shared__ int s_first;
+  if (threadIdx.x == 0) s_first = nc;
+  __syncthreads();
+  for (int u = 1 + threadIdx.x; u < nc; u += blockDim.x) {
+    const int l = sCand[u - 1], jj = sCand[u];
+    const double zl = sZ[l], zj = sZ[jj];
+    const double t2 = fma(zl, zl, zj * zj);
+    if (fabs(sD[jj] - sD[l]) * fabs(zl * zj) <= tol * t2) atomicMin(&s_first, u);
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    int last = -1, nrot = 0;
-    double zl = 0.0, dl = 0.0;
-    for (int j = 0; j < K; ++j) {
-      if (sStat[j]) continue;
-      double zj = sZ[j], dj = sD[j];
-      if (last >= 0) {
+    int nrot = 0;
+    const int first = s_first;
+    if (first < nc) {
+      int last = sCand[first - 1];
+      double zl = sZ[last], dl = sD[last];
+      for (int u = first; u < nc; ++u) {
+        const int j = sCand[u];
+        double zj = sZ[j], dj = sD[j];
         const double t2 = fma(zl, zl, zj * zj);
         if (fabs(dj - dl) * fabs(zl * zj) <= tol * t2) {
           const double t = sqrt(t2);
@@ -422,10 +456,10 @@ k_dc_prep(const MergeDesc* __restrict__ merges, const double* __restrict__ e, in
           sStat[last] = 2;
           if (sType[last] != sType[j]) sType[j] = 2;
         }
+        last = j;
+        zl = zj;
+        dl = dj;
       }
-      last = j;
-      zl = zj;
-      dl = dj;
     }
     s_nrot = nrot;
     W.nrot[lo] = nrot;
@@ -543,12 +577,20 @@ k_dc_rot(const MergeDesc* __restrict__ merges, int N, DcWork W) {
   }
 }
 
-// Phase 2: secular roots, one warp per (merge, root); the sums over poles are split across lanes.
+// Sum over the LANES lanes that share one root (LANES = 32: a warp; LANES = 1: one thread).
+template <int LANES> __device__ __forceinline__ double group_sum(double v) {
+  if constexpr (LANES == 32) return warp_sum(v);
+  else return v;
+}
+
+// Phase 2: secular roots, LANES lanes per (merge, root) -- a warp for large merges, one thread for
+// small ones; the sums over poles are split across the lanes.
 // delta column i: Delta[(lo+i)*N + lo + j] = Dk_j - lam_i, computed from the origin pole.
+template <int LANES>
 __global__ void k_dc_secular(const MergeDesc* __restrict__ merges, const int* __restrict__ mergeof, int N, DcWork W,
                              int* err) {
-  const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
+  const int p = (blockIdx.x * blockDim.x + threadIdx.x) / LANES;
+  const int lane = threadIdx.x % LANES;
   if (p >= N) return;
   const int mi = mergeof[p];
   if (mi < 0) return;
@@ -561,35 +603,48 @@ __global__ void k_dc_secular(const MergeDesc* __restrict__ merges, const int* __
   const double* z2 = W.z2 + lo;
   const double rho = W.rho[lo];
   double* delta = W.Delta + (size_t)(lo + i) * N + lo;
+  // For an inner root the sums are first evaluated at the midpoint of (D_i, D_{i+1}): the sign of f
+  // there picks the origin pole (the nearer end of the root's half interval), and the same sums give
+  // the first rational-model step from the midpoint.  The last root starts from its bracket midpoint.
   int org;
-  double tlo, thi;
+  double tlo, thi, tau;
+  double psi = 0.0, dpsi = 0.0, phi = 0.0, dphi = 0.0;
+  bool have = false;            // sums already evaluated at tau
   if (i < Kp - 1) {
     const double mid = 0.5 * (Dk[i] + Dk[i + 1]);
-    double f = 0.0;
-    for (int j = lane; j < Kp; j += 32) f += z2[j] * nr_rcp(Dk[j] - mid);
-    f = 1.0 + warp_sum(f);
-    if (f >= 0.0) { org = i; tlo = 0.0; thi = mid - Dk[i]; }
-    else { org = i + 1; tlo = mid - Dk[i + 1]; thi = 0.0; }
-  } else {
-    org = i;
-    double zz = 0.0;
-    for (int j = lane; j < Kp; j += 32) zz += Zk[j] * Zk[j];
-    tlo = 0.0;
-    thi = rho * warp_sum(zz);
-  }
-  const double Dorg = Dk[org];
-  double tau = 0.5 * (tlo + thi);
-  bool conv = false;
-  for (int it = 0; it < 200 && !conv; ++it) {
-    double psi = 0.0, dpsi = 0.0, phi = 0.0, dphi = 0.0;
-    for (int j = lane; j < Kp; j += 32) {
-      const double dl = (Dk[j] - Dorg) - tau;
-      const double rinv = nr_rcp(dl);
+    for (int j = lane; j < Kp; j += LANES) {
+      const double rinv = nr_rcp(Dk[j] - mid);
       const double tv = z2[j] * rinv;
       if (j <= i) { psi += tv; dpsi += tv * rinv; }
       else { phi += tv; dphi += tv * rinv; }
     }
-    psi = warp_sum(psi); dpsi = warp_sum(dpsi); phi = warp_sum(phi); dphi = warp_sum(dphi);
+    psi = group_sum<LANES>(psi); dpsi = group_sum<LANES>(dpsi); phi = group_sum<LANES>(phi); dphi = group_sum<LANES>(dphi);
+    if (1.0 + psi + phi >= 0.0) { org = i; tlo = 0.0; thi = mid - Dk[i]; tau = thi; }
+    else { org = i + 1; tlo = mid - Dk[i + 1]; thi = 0.0; tau = tlo; }
+    have = true;
+  } else {
+    org = i;
+    double zz = 0.0;
+    for (int j = lane; j < Kp; j += LANES) zz += Zk[j] * Zk[j];
+    tlo = 0.0;
+    thi = rho * group_sum<LANES>(zz);
+    tau = 0.5 * (tlo + thi);
+  }
+  const double Dorg = Dk[org];
+  bool conv = false;
+  for (int it = 0; it < 200 && !conv; ++it) {
+    if (!have) {
+      psi = 0.0; dpsi = 0.0; phi = 0.0; dphi = 0.0;
+      for (int j = lane; j < Kp; j += LANES) {
+        const double dl = (Dk[j] - Dorg) - tau;
+        const double rinv = nr_rcp(dl);
+        const double tv = z2[j] * rinv;
+        if (j <= i) { psi += tv; dpsi += tv * rinv; }
+        else { phi += tv; dphi += tv * rinv; }
+      }
+      psi = group_sum<LANES>(psi); dpsi = group_sum<LANES>(dpsi); phi = group_sum<LANES>(phi); dphi = group_sum<LANES>(dphi);
+    }
+    have = false;
     const double f = 1.0 + psi + phi;
     if (f == 0.0) break;
     // residual test: f is as small as rounding of its terms allows (psi < 0 < phi term-wise)
@@ -627,16 +682,17 @@ __global__ void k_dc_secular(const MergeDesc* __restrict__ merges, const int* __
     tau = nt;
     if (it == 199 && !conv && lane == 0) atomicExch(err, kErrNumeric);
   }
-  for (int j = lane; j < Kp; j += 32) delta[j] = (Dk[j] - Dorg) - tau;
+  for (int j = lane; j < Kp; j += LANES) delta[j] = (Dk[j] - Dorg) - tau;
   if (lane == 0) W.lamk[lo + i] = Dorg + tau;
 }
 
 // Phase 3: Loewner-corrected z (one warp per j):
 //   zhat_j^2 = (lam_last - D_j)/rho * prod_{i<j} (lam_i - D_j)/(D_i - D_j) * prod_{i>j} (lam_{i-1} - D_j)/(D_i - D_j)
 // The product is formed as a sum of logarithms of the (positive) factors split across lanes.
+template <int LANES>
 __global__ void k_dc_zhat(const MergeDesc* __restrict__ merges, const int* __restrict__ mergeof, int N, DcWork W) {
-  const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
+  const int p = (blockIdx.x * blockDim.x + threadIdx.x) / LANES;
+  const int lane = threadIdx.x % LANES;
   if (p >= N) return;
   const int mi = mergeof[p];
   if (mi < 0) return;
@@ -650,7 +706,7 @@ __global__ void k_dc_zhat(const MergeDesc* __restrict__ merges, const int* __res
   // each lane multiplies its factors and takes one logarithm (more only if the product leaves
   // [1e-150, 1e150]); the lanes' logarithms are summed
   double lg = 0.0, prod = 1.0;
-  for (int i = lane; i < Kp; i += 32) {
+  for (int i = lane; i < Kp; i += LANES) {
     if (i == j) continue;
     const int ii = (i < j) ? i : i - 1;                       // lam_i for i < j, lam_{i-1} for i > j
     const double num = -W.Delta[(size_t)(lo + ii) * N + lo + j];
@@ -658,7 +714,7 @@ __global__ void k_dc_zhat(const MergeDesc* __restrict__ merges, const int* __res
     if (!(prod > 1e-150 && prod < 1e150)) { lg += log(prod); prod = 1.0; }
   }
   lg += log(prod);
-  lg = warp_sum(lg);
+  lg = group_sum<LANES>(lg);
   if (lane == 0) {
     const double last = -W.Delta[(size_t)(lo + Kp - 1) * N + lo + j] / rho;
     W.Zw[lo + j] = copysign(sqrt(fabs(last)) * exp(0.5 * lg), W.Zk[lo + j]);
@@ -666,9 +722,10 @@ __global__ void k_dc_zhat(const MergeDesc* __restrict__ merges, const int* __res
 }
 
 // Phase 4: eigenvector columns u_i = zhat / delta_i, normalised, written over Delta (one warp per i).
+template <int LANES>
 __global__ void k_dc_vecs(const MergeDesc* __restrict__ merges, const int* __restrict__ mergeof, int N, DcWork W) {
-  const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
+  const int p = (blockIdx.x * blockDim.x + threadIdx.x) / LANES;
+  const int lane = threadIdx.x % LANES;
   if (p >= N) return;
   const int mi = mergeof[p];
   if (mi < 0) return;
@@ -678,10 +735,10 @@ __global__ void k_dc_vecs(const MergeDesc* __restrict__ merges, const int* __res
   if (i >= Kp) return;
   double* col = W.Delta + (size_t)(lo + i) * N + lo;
   double nrm = 0.0;
-  for (int j = lane; j < Kp; j += 32) { double u = W.Zw[lo + j] * nr_rcp(col[j]); col[j] = u; nrm += u * u; }
-  nrm = warp_sum(nrm);
+  for (int j = lane; j < Kp; j += LANES) { double u = W.Zw[lo + j] * nr_rcp(col[j]); col[j] = u; nrm += u * u; }
+  nrm = group_sum<LANES>(nrm);
   const double inv = 1.0 / sqrt(nrm);
-  for (int j = lane; j < Kp; j += 32) col[j] *= inv;
+  for (int j = lane; j < Kp; j += LANES) col[j] *= inv;
 }
 
 // Phase 5: Qtmp[lo:hi, lo+i] = Q[lo:hi, colk] U[:, i] (i < Kp); deflated columns copied after them.
@@ -981,7 +1038,6 @@ size_t eig_workspace_bytes(int nmax) {
   size_t b = 0;
   b += align_up(3 * N * sizeof(double));          // d, e, tau
   b += 2 * align_up(2 * N * sizeof(double));      // P, C (double buffered)
-  b += align_up(16);                              // barrier words
   b += 3 * align_up(N * N * sizeof(double));      // Q, Qtmp, Delta
   b += 10 * align_up(N * sizeof(double));         // lam, lamk, lamtmp, Dw, Zw, Dk, Zk, Dd, rho, spare
   b += align_up(4 * N * sizeof(double));          // rot
@@ -1006,7 +1062,6 @@ int eig_sym_topk(double* A, int lda, int N, int nkeep, double* w, T* U, int ldu,
   double* tau = e + N;
   double* P = (double*)take(2 * N * sizeof(double));
   double* Cb = (double*)take(2 * N * sizeof(double));
-  unsigned* bar = (unsigned*)take(16);
   DcWork W;
   W.Q = (double*)take((size_t)N * N * sizeof(double));
   W.Qtmp = (double*)take((size_t)N * N * sizeof(double));
@@ -1032,7 +1087,10 @@ int eig_sym_topk(double* A, int lda, int N, int nkeep, double* w, T* U, int ldu,
   W.gcnt = (int*)take(2 * N * sizeof(int));
   W.mergeof = nullptr;
 
-  cudaMemsetAsync(bar, 0, 16, st);
+  // exchange buffers of the tridiagonalisation: every byte 0x03, i.e. words with epoch 3, which
+  // no consumer waits for before the buffer has been rewritten
+  cudaMemsetAsync(P, 0x03, 2 * N * sizeof(double), st);
+  cudaMemsetAsync(Cb, 0x03, 2 * N * sizeof(double), st);
   cudaMemsetAsync(W.Q, 0, (size_t)N * N * sizeof(double), st);
   cudaMemsetAsync(d, 0, 3 * N * sizeof(double), st);
 
@@ -1054,7 +1112,7 @@ int eig_sym_topk(double* A, int lda, int N, int nkeep, double* w, T* U, int ldu,
       G = std::max(1, occ * nsm);     // fewer blocks own more columns each
       if (occ == 0) { cudaGetLastError(); return 1000 + (int)cudaErrorCooperativeLaunchTooLarge; }
     }
-    void* args[] = {&A, &lda, &N, &d, &e, &tau, &P, &Cb, &bar, &err};
+    void* args[] = {&A, &lda, &N, &d, &e, &tau, &P, &Cb, &err};
     cudaError_t ce = cudaLaunchCooperativeKernel((void*)k_tridiag, dim3(G), dim3(TD_THREADS), args, smem, st);
     note_launch();
     if (ce != cudaSuccess) return 1000 + (int)ce;
@@ -1076,9 +1134,18 @@ int eig_sym_topk(double* A, int lda, int N, int nkeep, double* w, T* U, int ldu,
     if (psmem > 40 * 1024) cudaFuncSetAttribute(k_dc_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
     k_dc_prep<<<nm, DC_THREADS, psmem, st>>>(dm, e, N, W); note_launch();
     k_dc_rot<<<dim3((kmax + 127) / 128, nm), 128, 0, st>>>(dm, N, W); note_launch();
-    k_dc_secular<<<(N * 32 + 255) / 256, 256, 0, st>>>(dm, dmo, N, W, err); note_launch();
-    k_dc_zhat<<<(N * 32 + 255) / 256, 256, 0, st>>>(dm, dmo, N, W); note_launch();
-    k_dc_vecs<<<(N * 32 + 255) / 256, 256, 0, st>>>(dm, dmo, N, W); note_launch();
+    // The per-root work is FP64-bound (2 FMA/clk/SM), so the grids use small blocks to spread the
+    // roots over all SMs: one-warp blocks of 32 roots for small merges, two-warp blocks of 2 roots
+    // (one warp per root) for large ones.
+    if (kmax <= 32) {
+      k_dc_secular<1><<<(N + 31) / 32, 32, 0, st>>>(dm, dmo, N, W, err); note_launch();
+      k_dc_zhat<1><<<(N + 31) / 32, 32, 0, st>>>(dm, dmo, N, W); note_launch();
+      k_dc_vecs<1><<<(N + 31) / 32, 32, 0, st>>>(dm, dmo, N, W); note_launch();
+    } else {
+      k_dc_secular<32><<<(N + 1) / 2, 64, 0, st>>>(dm, dmo, N, W, err); note_launch();
+      k_dc_zhat<32><<<(N + 1) / 2, 64, 0, st>>>(dm, dmo, N, W); note_launch();
+      k_dc_vecs<32><<<(N + 1) / 2, 64, 0, st>>>(dm, dmo, N, W); note_launch();
+    }
     dim3 gg((kmax + DG_T - 1) / DG_T, (kmax + DG_T - 1) / DG_T, nm);
     k_dc_gemm<<<gg, 256, 0, st>>>(dm, N, W); note_launch();
     const size_t fsmem = (size_t)kmax * (sizeof(double) + sizeof(long long));

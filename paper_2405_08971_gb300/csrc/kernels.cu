@@ -1010,9 +1010,12 @@ __global__ void k_nll_def(const int* __restrict__ count, double* __restrict__ Gh
 // and ld * (ld + 1) doubles of dynamic shared memory): a pivot step costs two block barriers on
 // shared memory instead of global-memory round trips.
 __device__ bool smem_cholesky(double* S, int j) {
+  // right-looking; per pivot one barrier after the column scale and one after the trailing update.
+  // Warp w updates the trailing columns c = p+1+w, p+1+w+nw, ...; its lanes take the rows q >= c.
   __shared__ int bad;
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int p = 0; p < j; ++p) {
     double d = S[p * j + p];
     const bool bd = !(d > 0.0) || !isfinite(d);
@@ -1024,10 +1027,11 @@ __device__ bool smem_cholesky(double* S, int j) {
       S[p * j + p] = piv;
       if (bd) bad = 1;
     }
-    const int w = j - p - 1;
-    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
-      const int q = p + 1 + e % w, c = p + 1 + e / w;
-      if (q >= c) S[c * j + q] -= S[p * j + q] * S[p * j + c];
+    const double* lp = S + p * j;
+    for (int c = p + 1 + warp; c < j; c += nw) {
+      const double lc = lp[c];
+      double* col = S + c * j;
+      for (int q = c + lane; q < j; q += 32) col[q] = fma(-lp[q], lc, col[q]);
     }
     __syncthreads();
   }
