@@ -1006,81 +1006,84 @@ __global__ void k_nll_def(const int* __restrict__ count, double* __restrict__ Gh
   }
 }
 
-// The same NLL term with both j x j factorisations in shared memory (one matrix at a time, j <= ld
-// and ld * (ld + 1) doubles of dynamic shared memory): a pivot step costs two block barriers on
-// shared memory instead of global-memory round trips.
-__device__ bool smem_cholesky(double* S, int j) {
-  // right-looking; per pivot one barrier after the column scale and one after the trailing update.
-  // Warp w updates the trailing columns c = p+1+w, p+1+w+nw, ...; its lanes take the rows q >= c.
+// The same NLL term with both j x j factorisations in shared memory, side by side (2 j^2 + 3 j
+// doubles of dynamic shared memory).  GB300 issues a warp-wide FP64 instruction over 16 cycles, so
+// the scalar work of a pivot (square root, reciprocal) is done once per matrix, by one lane of warp 0
+// (S^T G S) and one lane of warp 1 (S^T S), and broadcast through shared memory; the column scale and
+// the forward substitution multiply by the stored reciprocal, and the logarithms of the pivots are
+// taken in parallel.
+constexpr int NLL_THREADS = 256;
+__global__ void __launch_bounds__(NLL_THREADS)
+k_nll_def_smem(const int* __restrict__ count, const double* __restrict__ Gh, const double* __restrict__ SS, int ld,
+               const double* __restrict__ yh, double* __restrict__ nll_k, int* __restrict__ err) {
+  extern __shared__ double nsm[];
+  const int j = min(*count, ld);
+  double* S1 = nsm;                      // S^T G S, j x j (ld j), lower triangle used
+  double* S2 = nsm + (size_t)j * j;      // S^T S
+  double* inv1 = S2 + (size_t)j * j;     // reciprocal pivots of S1
+  double* inv2 = inv1 + j;
+  double* b = inv2 + j;                  // right-hand side of the forward substitution
   __shared__ int bad;
-  if (threadIdx.x == 0) bad = 0;
-  __syncthreads();
+  __shared__ double red[NLL_THREADS / 32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int p = 0; p < j; ++p) {
-    double d = S[p * j + p];
-    const bool bd = !(d > 0.0) || !isfinite(d);
-    if (bd) d = 1.0;
-    const double piv = sqrt(d);
-    for (int q = p + 1 + threadIdx.x; q < j; q += blockDim.x) S[p * j + q] /= piv;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      S[p * j + p] = piv;
-      if (bd) bad = 1;
+  if (threadIdx.x == 0) bad = 0;
+  for (int e = threadIdx.x; e < j * j; e += blockDim.x) {
+    const int r = e % j, c = e / j;
+    if (r >= c) {
+      S1[c * j + r] = (r == c) ? Gh[(size_t)c * ld + r] : 0.5 * (Gh[(size_t)c * ld + r] + Gh[(size_t)r * ld + c]);
+      S2[c * j + r] = (r == c) ? SS[(size_t)c * ld + r] : 0.5 * (SS[(size_t)c * ld + r] + SS[(size_t)r * ld + c]);
     }
-    const double* lp = S + p * j;
-    for (int c = p + 1 + warp; c < j; c += nw) {
+  }
+  for (int q = threadIdx.x; q < j; q += blockDim.x) b[q] = yh[q];
+  __syncthreads();
+  for (int p = 0; p < j; ++p) {
+    if (lane == 0 && warp < 2) {
+      double* S = warp == 0 ? S1 : S2;
+      double d = S[p * j + p];
+      if (!(d > 0.0) || !isfinite(d)) { bad = 1; d = 1.0; }
+      const double piv = sqrt(d);
+      S[p * j + p] = piv;
+      (warp == 0 ? inv1 : inv2)[p] = 1.0 / piv;
+    }
+    __syncthreads();
+    const double i1 = inv1[p], i2 = inv2[p];
+    for (int q = p + 1 + threadIdx.x; q < j; q += blockDim.x) {
+      S1[p * j + q] *= i1;
+      S2[p * j + q] *= i2;
+    }
+    __syncthreads();
+    // trailing updates: warps take the columns c of both matrices round robin, lanes the rows q >= c
+    const int w = j - p - 1;
+    for (int cc = warp; cc < 2 * w; cc += nw) {
+      double* S = cc < w ? S1 : S2;
+      const int c = p + 1 + (cc < w ? cc : cc - w);
+      const double* lp = S + p * j;
       const double lc = lp[c];
       double* col = S + c * j;
       for (int q = c + lane; q < j; q += 32) col[q] = fma(-lp[q], lc, col[q]);
     }
     __syncthreads();
   }
-  const bool ok = bad == 0;
-  __syncthreads();
-  return ok;
-}
-
-__global__ void k_nll_def_smem(const int* __restrict__ count, const double* __restrict__ Gh,
-                               const double* __restrict__ SS, int ld, const double* __restrict__ yh,
-                               double* __restrict__ nll_k, int* __restrict__ err) {
-  extern __shared__ double nsm[];
-  const int j = min(*count, ld);
-  double* S = nsm;                 // j x j, ld j
-  double* b = nsm + (size_t)j * j; // right-hand side of the forward substitution
-  __shared__ double s_ld1, s_quad;
-  // symmetrised copy of S^T G S
-  for (int e = threadIdx.x; e < j * j; e += blockDim.x) {
-    const int r = e % j, c = e / j;
-    if (r >= c) S[c * j + r] = (r == c) ? Gh[(size_t)c * ld + r] : 0.5 * (Gh[(size_t)c * ld + r] + Gh[(size_t)r * ld + c]);
-  }
-  for (int q = threadIdx.x; q < j; q += blockDim.x) b[q] = yh[q];
-  const bool ok1 = smem_cholesky(S, j);
-  // L z = yh (column oriented: z_q = b_q / L_qq, then b_l -= L_lq z_q below)
+  // L z = yh for the factor of S^T G S (column oriented)
   double quad = 0.0;
   for (int q = 0; q < j; ++q) {
-    const double zq = b[q] / S[q * j + q];
+    const double zq = b[q] * inv1[q];
     quad = fma(zq, zq, quad);
-    for (int l = q + 1 + threadIdx.x; l < j; l += blockDim.x) b[l] -= S[q * j + l] * zq;
+    for (int l = q + 1 + threadIdx.x; l < j; l += blockDim.x) b[l] = fma(-S1[q * j + l], zq, b[l]);
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    double ld1 = 0.0;
-    for (int q = 0; q < j; ++q) ld1 += log(S[q * j + q]);
-    s_ld1 = ld1;
-    s_quad = quad;
-  }
+  // sum_q log L1_qq - sum_q log L2_qq, logarithms in parallel
+  double lg = 0.0;
+  for (int q = threadIdx.x; q < j; q += blockDim.x) lg += log(S1[q * j + q]) - log(S2[q * j + q]);
+  lg = warp_sum(lg);
+  if (lane == 0) red[warp] = lg;
   __syncthreads();
-  for (int e = threadIdx.x; e < j * j; e += blockDim.x) {
-    const int r = e % j, c = e / j;
-    if (r >= c) S[c * j + r] = (r == c) ? SS[(size_t)c * ld + r] : 0.5 * (SS[(size_t)c * ld + r] + SS[(size_t)r * ld + c]);
-  }
-  const bool ok2 = smem_cholesky(S, j);
   if (threadIdx.x == 0) {
-    double ld2 = 0.0;
-    for (int q = 0; q < j; ++q) ld2 += log(S[q * j + q]);
-    const double val = 0.5 * j * 1.8378770664093453 + s_ld1 + 0.5 * s_quad - ld2;
+    double ldiff = 0.0;
+    for (int w2 = 0; w2 < nw; ++w2) ldiff += red[w2];
+    const double val = 0.5 * j * 1.8378770664093453 + ldiff + 0.5 * quad;
     *nll_k = val;
-    if (!ok1 || !ok2 || !isfinite(val)) atomicExch(err, kErrNumeric);
+    if (bad || !isfinite(val)) atomicExch(err, kErrNumeric);
   }
 }
 
@@ -1405,10 +1408,10 @@ template void tangent_mean<double>(const double*, const double*, size_t, int, in
 
 void nll_def(const int* count, double* Gh, double* SS, int ld, const double* yh, double* z, double* nll_k, int* err,
              cudaStream_t st) {
-  const size_t smem = ((size_t)ld * ld + ld) * sizeof(double);
+  const size_t smem = (2 * (size_t)ld * ld + 3 * (size_t)ld) * sizeof(double);
   if (smem <= 200 * 1024) {
     if (smem > 40 * 1024) cudaFuncSetAttribute(k_nll_def_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_nll_def_smem<<<1, 256, smem, st>>>(count, Gh, SS, ld, yh, nll_k, err); note_launch();
+    k_nll_def_smem<<<1, NLL_THREADS, smem, st>>>(count, Gh, SS, ld, yh, nll_k, err); note_launch();
     return;
   }
   k_nll_def<<<1, 256, 0, st>>>(count, Gh, SS, ld, yh, z, nll_k, err); note_launch();
