@@ -56,6 +56,61 @@ template <int KER> __device__ __forceinline__ double kval_dlogl(double s2, doubl
   return s2 * (1.0 + s) * e / 3.0;
 }
 
+// ---- packed FP32 pairs (two columns of one row): f32x2 arithmetic on 64-bit registers
+__device__ __forceinline__ uint64_t f2_make(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2_split(uint64_t v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+__device__ __forceinline__ float f2_sum(uint64_t v) {
+  float lo, hi;
+  f2_split(v, lo, hi);
+  return lo + hi;
+}
+// Matern correlation (without sf2) of one row against a column pair.  Coordinates are pre-scaled
+// by c_nu / l_x, so with s the Euclidean distance:  nu=1/2: e^-s,  nu=3/2: (1+s) e^-s,
+// nu=5/2: (1 + s + s^2/3) e^-s.  sqrt and exp2 run on the MUFU unit (approximate, ftz).
+template <int KER>
+__device__ __forceinline__ uint64_t kpair(uint64_t rx, uint64_t ry, uint64_t rz, uint64_t cx, uint64_t cy,
+                                          uint64_t cz) {
+  const uint64_t dx = f2_sub(rx, cx), dy = f2_sub(ry, cy), dz = f2_sub(rz, cz);
+  uint64_t d2 = f2_mul(dz, dz);
+  d2 = f2_fma(dy, dy, d2);
+  d2 = f2_fma(dx, dx, d2);
+  float a, b;
+  f2_split(d2, a, b);
+  const uint64_t sd = f2_make(approx_sqrt(a), approx_sqrt(b));
+  const uint64_t t = f2_mul(sd, f2_make(-1.4426950408889634f, -1.4426950408889634f));
+  f2_split(t, a, b);
+  float ea, eb;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(ea) : "f"(a));
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(eb) : "f"(b));
+  const uint64_t e = f2_make(ea, eb);
+  if (KER == 0) return e;
+  if (KER == 1) return f2_fma(sd, e, e);
+  const uint64_t p = f2_mul(f2_fma(sd, f2_make(0.33333333333333333f, 0.33333333333333333f),
+                                   f2_make(1.0f, 1.0f)), sd);
+  return f2_fma(p, e, e);
+}
+
 template <class T> __device__ __forceinline__ T dist2(const C4<T>& a, const C4<T>& b) {
   T dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
   return fma(dx, dx, fma(dy, dy, dz * dz));

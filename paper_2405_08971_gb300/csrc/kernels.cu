@@ -143,6 +143,118 @@ k_gram_matvec(const C4<T>* __restrict__ Xo, const T* __restrict__ s, int m, int 
   }
 }
 
+// The FP32 matvec on packed pairs of rows (f32x2 arithmetic): a lane owns MVS_R = 4 rows of tile I
+// as two pairs, the column records of tile J are staged duplicated ({x,x},{y,y},{z,z},{w,w} with
+// w = sf2 s_j), and a warp's 32 per-column sums over its lanes' rows are reduced by one butterfly
+// reduce-scatter (31 shuffles) instead of one warp sum per column.  Same tiles, slots and Mo^T s
+// blocks as k_gram_matvec.
+template <int KER>
+__global__ void __launch_bounds__(MVS_W * 32)
+k_gram_matvec_f2(const C4<float>* __restrict__ Xo, const float* __restrict__ s, int m, int nb, float sf2,
+                 float* __restrict__ part, const float* __restrict__ Mo, int ldm, int rp, int ngv,
+                 float* __restrict__ tpart, const int* __restrict__ active) {
+  if (active && !*active) return;
+  __shared__ uint64_t xs2[MVS_T][4];
+  __shared__ float racc[MVS_W][MVS_T];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if ((int)blockIdx.x < ngv) {
+    const int per_chunk = (rp + MVS_W - 1) / MVS_W;
+    const int z = blockIdx.x / per_chunk;
+    const int col = (blockIdx.x - z * per_chunk) * MVS_W + warp;
+    if (col >= rp) return;
+    const int i0 = z * GV_CHUNK, i1 = min(m, i0 + GV_CHUNK);
+    const float* a = Mo + (size_t)col * ldm;
+    float acc = 0.f;
+#pragma unroll 8
+    for (int i = i0 + lane; i < i1; i += 32) acc = fmaf(a[i], s[i], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) tpart[(size_t)z * rp + col] = acc;
+    return;
+  }
+  int idx = blockIdx.x - ngv, I = 0;
+  while (idx >= nb - I) { idx -= nb - I; ++I; }
+  const int J = I + idx;
+  for (int t = threadIdx.x; t < MVS_T; t += blockDim.x) {
+    const int j = J * MVS_T + t;
+    float x = 0.f, y = 0.f, zc = 0.f, w = 0.f;
+    if (j < m) { const C4<float> c = Xo[j]; x = c.x; y = c.y; zc = c.z; w = sf2 * s[j]; }
+    xs2[t][0] = f2_make(x, x);
+    xs2[t][1] = f2_make(y, y);
+    xs2[t][2] = f2_make(zc, zc);
+    xs2[t][3] = f2_make(w, w);
+  }
+  uint64_t rx[2], ry[2], rz[2], rs[2], acc[2];
+#pragma unroll
+  for (int pr = 0; pr < 2; ++pr) {
+    float xv[2] = {0.f, 0.f}, yv[2] = {0.f, 0.f}, zv[2] = {0.f, 0.f}, sv[2] = {0.f, 0.f};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = I * MVS_T + lane + 32 * (2 * pr + h);
+      if (i < m) { const C4<float> c = Xo[i]; xv[h] = c.x; yv[h] = c.y; zv[h] = c.z; sv[h] = sf2 * s[i]; }
+    }
+    rx[pr] = f2_make(xv[0], xv[1]);
+    ry[pr] = f2_make(yv[0], yv[1]);
+    rz[pr] = f2_make(zv[0], zv[1]);
+    rs[pr] = f2_make(sv[0], sv[1]);
+    acc[pr] = f2_make(0.f, 0.f);
+  }
+  __syncthreads();
+  const uint64_t(*xc)[4] = xs2 + warp * 32;
+  float cacc = 0.f;
+  if (I == J) {
+#pragma unroll 8
+    for (int jj = 0; jj < 32; ++jj) {
+      const uint64_t cx = xc[jj][0], cy = xc[jj][1], cz = xc[jj][2], cw = xc[jj][3];
+#pragma unroll
+      for (int pr = 0; pr < 2; ++pr) acc[pr] = f2_fma(kpair<KER>(rx[pr], ry[pr], rz[pr], cx, cy, cz), cw, acc[pr]);
+    }
+  } else {
+    float v[32];
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj) {
+      const uint64_t cx = xc[jj][0], cy = xc[jj][1], cz = xc[jj][2], cw = xc[jj][3];
+      const uint64_t k0 = kpair<KER>(rx[0], ry[0], rz[0], cx, cy, cz);
+      const uint64_t k1 = kpair<KER>(rx[1], ry[1], rz[1], cx, cy, cz);
+      acc[0] = f2_fma(k0, cw, acc[0]);
+      acc[1] = f2_fma(k1, cw, acc[1]);
+      v[jj] = f2_sum(f2_fma(k1, rs[1], f2_mul(k0, rs[0])));
+    }
+    // butterfly reduce-scatter: after the stage with offset o a lane keeps the half of its
+    // column sums selected by its bit o; at the end lane l holds the sum for column l
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+      const bool up = (lane & o) != 0;
+#pragma unroll
+      for (int q = 0; q < o; ++q) {
+        const float send = up ? v[q] : v[q + o];
+        const float keep = up ? v[q + o] : v[q];
+        v[q] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+      }
+    }
+    cacc = v[0];
+  }
+#pragma unroll
+  for (int pr = 0; pr < 2; ++pr) {
+    float lo, hi;
+    f2_split(acc[pr], lo, hi);
+    racc[warp][lane + 32 * (2 * pr)] = lo;
+    racc[warp][lane + 32 * (2 * pr + 1)] = hi;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < MVS_T; t += blockDim.x) {
+    const int i = I * MVS_T + t;
+    if (i >= m) continue;
+    float vv = racc[0][t];
+#pragma unroll
+    for (int w = 1; w < MVS_W; ++w) vv += racc[w][t];
+    part[(size_t)J * m + i] = vv;
+  }
+  if (I != J) {
+    const int j = J * MVS_T + warp * 32 + lane;
+    if (j < m) part[(size_t)I * m + j] = cacc;
+  }
+}
+
 // g = sum_p part[p] + sn2 * s - a2 * Mo t     (Mo: m x r col-major, ld = ldm).  t is summed from
 // the row-chunk partials of k_gemv_t (tz chunks) into shared memory first.  A block owns CB_ROWS
 // rows: lane = row, each of the CB_WARPS warps takes every CB_WARPS-th column of Mo (coalesced
@@ -1147,10 +1259,18 @@ void gram_matvec(int ker, const C4<T>* Xo, const T* s, int m, T sf2, T* part, co
   const int nb = gram_matvec_slots(m);
   const int ngv = rp > 0 ? (int)cdiv(m, GV_CHUNK) * (int)cdiv(rp, MVS_W) : 0;
   const int grid = ngv + nb * (nb + 1) / 2;
-  switch (ker) {
-    case 0: k_gram_matvec<0, T><<<grid, MVS_W * 32, 0, st>>>(Xo, s, m, nb, sf2, part, Mo, ldm, rp, ngv, tpart, active); break;
-    case 1: k_gram_matvec<1, T><<<grid, MVS_W * 32, 0, st>>>(Xo, s, m, nb, sf2, part, Mo, ldm, rp, ngv, tpart, active); break;
-    default: k_gram_matvec<2, T><<<grid, MVS_W * 32, 0, st>>>(Xo, s, m, nb, sf2, part, Mo, ldm, rp, ngv, tpart, active); break;
+  if constexpr (sizeof(T) == 4) {
+    switch (ker) {
+      case 0: k_gram_matvec_f2<0><<<grid, MVS_W * 32, 0, st>>>(Xo, s, m, nb, sf2, part, Mo, ldm, rp, ngv, tpart, active); break;
+      case 1: k_gram_matvec_f2<1><<<grid, MVS_W * 32, 0, st>>>(Xo, s, m, nb, sf2, part, Mo, ldm, rp, ngv, tpart, active); break;
+      default: k_gram_matvec_f2<2><<<grid, MVS_W * 32, 0, st>>>(Xo, s, m, nb, sf2, part, Mo, ldm, rp, ngv, tpart, active); break;
+    }
+  } else {
+    switch (ker) {
+      case 0: k_gram_matvec<0, T><<<grid, MVS_W * 32, 0, st>>>(Xo, s, m, nb, sf2, part, Mo, ldm, rp, ngv, tpart, active); break;
+      case 1: k_gram_matvec<1, T><<<grid, MVS_W * 32, 0, st>>>(Xo, s, m, nb, sf2, part, Mo, ldm, rp, ngv, tpart, active); break;
+      default: k_gram_matvec<2, T><<<grid, MVS_W * 32, 0, st>>>(Xo, s, m, nb, sf2, part, Mo, ldm, rp, ngv, tpart, active); break;
+    }
   }
   note_launch();
 }
