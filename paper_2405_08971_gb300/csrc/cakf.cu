@@ -466,8 +466,8 @@ struct Runner {
       // CG policy without re-orthogonalisation: k_cg_upd2 writes the next action (the updated
       // residual) itself, so the selection runs only for the first action
       const bool fused_select = !rep && !reorth;
-      double* dpart1 = c->dpart;
-      double* dpart2 = c->dpart + (size_t)(B + 4) * ((m + 31) / 32);
+      T* dpart1 = (T*)c->dpart;
+      T* dpart2 = dpart1 + (size_t)(B + 4) * ((m + 31) / 32);
       for (int j = 0; j < ic; ++j) {
         T* g = GSk + (size_t)j * m;
         if (!fused_select || j == 0) cg_select<T>(j, r, rep, m, s, Sk(k), m, c->active, st);

@@ -847,11 +847,11 @@ k_dc_copy(const MergeDesc* __restrict__ merges, int N, DcWork W) {
 // compact WY form: H_k0 H_k0+1 ... H_k0+RB-1 = I - V T V^T (V the RB reflectors, T upper
 // triangular).  A block owns CB output columns; per group it stages V in shared memory once for
 // all its columns, forms Y = V^T Z (RB x CB dots), Y <- T Y, and Z -= V Y.
-constexpr int RB = 8;
+constexpr int RB = 16;
 constexpr int CB = 4;
 
 // T of every group (one block per group): T_ii = tau_i, T[0:i, i] = -tau_i T[0:i, 0:i] V[:, 0:i]^T v_i.
-// The RB (RB - 1) / 2 reflector dots are spread over the warps; one thread then forms T.
+// The RB (RB - 1) / 2 reflector dots are spread over the warps.
 __global__ void __launch_bounds__(256)
 k_bt_tmat(const double* __restrict__ A, int lda, const double* __restrict__ tau, int N,
           double* __restrict__ Tm) {
@@ -870,32 +870,23 @@ k_bt_tmat(const double* __restrict__ A, int lda, const double* __restrict__ tau,
     if (lane == 0) vv[a][b] = acc;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double T[RB][RB];
-#pragma unroll
-    for (int i = 0; i < RB; ++i)
-#pragma unroll
-      for (int j = 0; j < RB; ++j) T[i][j] = 0.0;
-#pragma unroll
-    for (int i = 0; i < RB; ++i) {
-      if (i < nb) {
-        const double ti = tau[k0 + i];
-        T[i][i] = ti;
-#pragma unroll
-        for (int r = 0; r < RB; ++r) {
-          if (r < i) {
-            double acc = 0.0;
-#pragma unroll
-            for (int c = 0; c < RB; ++c)
-              if (c >= r && c < i) acc = fma(T[r][c], vv[c][i], acc);
-            T[r][i] = -ti * acc;
-          }
-        }
-      }
+  // T column by column: thread r < i forms T[r][i] from the finished columns 0 .. i-1
+  __shared__ double Ts[RB][RB];
+  for (int e = threadIdx.x; e < RB * RB; e += blockDim.x) Ts[e / RB][e % RB] = 0.0;
+  __syncthreads();
+  for (int i = 0; i < nb; ++i) {
+    const double ti = tau[k0 + i];
+    const int r = threadIdx.x;
+    if (r < i) {
+      double acc = 0.0;
+      for (int c = r; c < i; ++c) acc = fma(Ts[r][c], vv[c][i], acc);
+      Ts[r][i] = -ti * acc;
+    } else if (r == i) {
+      Ts[i][i] = ti;
     }
-    for (int i = 0; i < RB; ++i)
-      for (int j = 0; j < RB; ++j) Tm[(size_t)g * RB * RB + i * RB + j] = T[i][j];
+    __syncthreads();
   }
+  for (int e = threadIdx.x; e < RB * RB; e += blockDim.x) Tm[(size_t)g * RB * RB + e] = Ts[e / RB][e % RB];
 }
 
 // One block per CB output columns (descending eigenvalue order: column c holds Q[:, N-1-c]).

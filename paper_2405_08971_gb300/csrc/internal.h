@@ -33,17 +33,17 @@ void gram_block_dlogl_simt(int ker, const C4<T>* Xr, int nr, const C4<T>* Xc, in
 //   cg_upd2:    second pass, scalars, V/GV/v/r update; with Snext the next action s = r
 template <class T>
 void cg_combine(const T* part, int nsplit, const T* s, T sn2, const T* Mo, int ldm, int r, const T* t, T a2, int m,
-                T* g, const T* V, int ldv, int j, const T* r0, const T* v, double* dpart1, const int* active,
+                T* g, const T* V, int ldv, int j, const T* r0, const T* v, T* dpart1, const int* active,
                 cudaStream_t st);
 template <class T>
 void gemv_t(const T* A, int lda, int rows, int cols, const T* x, T* t, const int* active, cudaStream_t st);
-// doubles needed for dpart1 followed by dpart2 at m observations and an action budget
+// elements needed for dpart1 followed by dpart2 at m observations and an action budget
 size_t cg_dpart_elems(int m, int budget);
 template <class T>
-void cg_upd1(int j, const double* dpart1, double* dots1, T* V, T* GV, int ldv, const T* s, const T* g, int m,
-             double* dpart2, const int* active, cudaStream_t st);
+void cg_upd1(int j, const T* dpart1, double* dots1, T* V, T* GV, int ldv, const T* s, const T* g, int m,
+             T* dpart2, const int* active, cudaStream_t st);
 template <class T>
-void cg_upd2(int j, const double* dots1, const double* dpart2, T* V, T* GV, int ldv, T* r, T* v, T* s, T* Q,
+void cg_upd2(int j, const double* dots1, const T* dpart2, T* V, T* GV, int ldv, T* r, T* v, T* s, T* Q,
              int m, double bd_tol, double rtol2_r0sq, int use_rtol, int* active, double* eta, double* alpha,
              int* count, T* Snext, cudaStream_t st);
 template <class T>

@@ -261,14 +261,15 @@ k_gram_matvec_f2(const C4<float>* __restrict__ Xo, const float* __restrict__ s, 
 // 128-byte column segments, CB_UNROLL independent accumulators), and the warps' sums are added
 // in shared memory.  The block then forms its rows' share of the first dot pass of CG iteration j
 //   q < j: V[:, q] . g ;  j: s . g ;  j+1: s . r0 ;  j+2: g . v ;  j+3: s . s
-// into dpart[q * gridDim.x + block] (summed in FP64 by k_cg_upd1, in block order).
+// into dpart[q * gridDim.x + block] (summed by k_cg_upd1 in a fixed order, in the working precision:
+// FP64 adds would cost more than the data they sum on this GPU).
 constexpr int CB_ROWS = 32, CB_WARPS = 8, CB_UNROLL = 8;
 template <class T>
 __global__ void __launch_bounds__(CB_WARPS * 32)
 k_cg_combine(const T* __restrict__ part, int nsplit, const T* __restrict__ s, T sn2,
              const T* __restrict__ Mo, int ldm, int r, const T* __restrict__ tpart, int tz, T a2,
              int m, T* __restrict__ g, const T* __restrict__ V, int ldv, int j, const T* __restrict__ r0,
-             const T* __restrict__ v, double* __restrict__ dpart, const int* __restrict__ active) {
+             const T* __restrict__ v, T* __restrict__ dpart, const int* __restrict__ active) {
   if (!*active) return;
   extern __shared__ unsigned char sm_raw[];
   T* t = reinterpret_cast<T*>(sm_raw);                 // r coefficients
@@ -332,7 +333,7 @@ k_cg_combine(const T* __restrict__ part, int nsplit, const T* __restrict__ s, T 
       else pr = si * si;
     }
     pr = warp_sum(pr);
-    if (lane == 0) dpart[(size_t)q * gridDim.x + blockIdx.x] = double(pr);
+    if (lane == 0) dpart[(size_t)q * gridDim.x + blockIdx.x] = pr;
   }
 }
 
@@ -385,21 +386,21 @@ template <class T> __device__ __forceinline__ double dot_part(const T* __restric
 constexpr int UP_THREADS = 256;
 template <class T>
 __global__ void __launch_bounds__(UP_THREADS)
-k_cg_upd1(int j, const double* __restrict__ dpart1, int nblk1, double* __restrict__ dots1, T* __restrict__ V,
+k_cg_upd1(int j, const T* __restrict__ dpart1, int nblk1, double* __restrict__ dots1, T* __restrict__ V,
           T* __restrict__ GV, int ldv, const T* __restrict__ s, const T* __restrict__ g, int m,
-          double* __restrict__ dpart2, const int* __restrict__ active) {
+          T* __restrict__ dpart2, const int* __restrict__ active) {
   if (!*active) return;
   __shared__ T c[1024];
   __shared__ T sd[UP_THREADS], sgd[UP_THREADS];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const int nq = (blockIdx.x == 0) ? j + 4 : j;
   for (int q = warp; q < nq; q += nw) {
-    double acc = 0.0;
+    T acc = T(0);
     for (int b = lane; b < nblk1; b += 32) acc += dpart1[(size_t)q * nblk1 + b];
     acc = warp_sum(acc);
     if (lane == 0) {
-      if (q < j) c[q] = T(acc);
-      if (blockIdx.x == 0) dots1[q] = acc;
+      if (q < j) c[q] = acc;
+      if (blockIdx.x == 0) dots1[q] = double(acc);
     }
   }
   __syncthreads();
@@ -409,6 +410,7 @@ k_cg_upd1(int j, const double* __restrict__ dpart1, int nblk1, double* __restric
   if (i < m) {
     d = s[i];
     gd = g[i];
+#pragma unroll 8
     for (int q = 0; q < j; ++q) {
       const T cq = c[q];
       d = fma(-V[(size_t)q * ldv + i], cq, d);
@@ -430,7 +432,7 @@ k_cg_upd1(int j, const double* __restrict__ dpart1, int nblk1, double* __restric
       for (int t = lane; t < nrow; t += 32) acc = fma(sd[t], sgd[t], acc);
     }
     acc = warp_sum(acc);
-    if (lane == 0) dpart2[(size_t)q * gridDim.x + blockIdx.x] = double(acc);
+    if (lane == 0) dpart2[(size_t)q * gridDim.x + blockIdx.x] = acc;
   }
 }
 
@@ -442,7 +444,7 @@ k_cg_upd1(int j, const double* __restrict__ dpart1, int nblk1, double* __restric
 // -- the updated residual -- is written to s and to column j + 1 of S here.
 template <class T>
 __global__ void __launch_bounds__(UP_THREADS)
-k_cg_upd2(int j, const double* __restrict__ dots1, const double* __restrict__ dpart2, int nblk2,
+k_cg_upd2(int j, const double* __restrict__ dots1, const T* __restrict__ dpart2, int nblk2,
           T* __restrict__ V, T* __restrict__ GV, int ldv, T* __restrict__ r, T* __restrict__ v,
           T* __restrict__ s, T* __restrict__ Q, int m,
           double bd_tol, double rtol2_r0sq, int use_rtol, int* __restrict__ active,
@@ -452,14 +454,15 @@ k_cg_upd2(int j, const double* __restrict__ dots1, const double* __restrict__ dp
   __shared__ T c[1024];
   __shared__ double cd[1025];
   __shared__ double sh[3];
+  __shared__ T shc[3];             // 1 / sqrt(eta), alpha / eta, 1 / |s| (formed once, in FP64)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int q = warp; q <= j; q += nw) {
-    double acc = 0.0;
+    T acc = T(0);
     for (int b = lane; b < nblk2; b += 32) acc += dpart2[(size_t)q * nblk2 + b];
     acc = warp_sum(acc);
     if (lane == 0) {
-      cd[q] = acc;
-      if (q < j) c[q] = T(acc);
+      cd[q] = double(acc);
+      if (q < j) c[q] = acc;
     }
   }
   __syncthreads();
@@ -473,6 +476,11 @@ k_cg_upd2(int j, const double* __restrict__ dots1, const double* __restrict__ dp
     int stop = !(eta > bd_tol * sg) || !isfinite(eta) || !isfinite(alpha);
     if (use_rtol && dots1[j + 3] <= rtol2_r0sq) stop = 1;
     sh[0] = eta; sh[1] = alpha; sh[2] = stop;
+    if (!stop) {
+      shc[0] = T(1.0 / sqrt(eta));
+      shc[1] = T(alpha / eta);
+      shc[2] = T(1.0 / sqrt(dots1[j + 3]));
+    }
   }
   __syncthreads();
   const double eta = sh[0], alpha = sh[1];
@@ -485,19 +493,20 @@ k_cg_upd2(int j, const double* __restrict__ dots1, const double* __restrict__ dp
   }
   if (i < m) {
     T d = V[(size_t)j * ldv + i], gd = GV[(size_t)j * ldv + i];
+#pragma unroll 8
     for (int q = 0; q < j; ++q) {
       const T cq = c[q];
       d = fma(-V[(size_t)q * ldv + i], cq, d);
       gd = fma(-GV[(size_t)q * ldv + i], cq, gd);
     }
-    const T inv = T(1.0 / sqrt(eta));
-    const T coef = T(alpha / eta);
+    const T inv = shc[0];
+    const T coef = shc[1];
     V[(size_t)j * ldv + i] = d * inv;
     GV[(size_t)j * ldv + i] = gd * inv;
     v[i] = fma(coef, d, v[i]);
     const T rn = fma(-coef, gd, r[i]);
     r[i] = rn;
-    if (Q) Q[(size_t)j * ldv + i] = s[i] * T(1.0 / sqrt(dots1[j + 3]));
+    if (Q) Q[(size_t)j * ldv + i] = s[i] * shc[2];
     if (Snext) {
       s[i] = rn;
       Snext[i] = rn;
@@ -1302,7 +1311,7 @@ void gram_block_dlogl_simt(int ker, const C4<T>* Xr, int nr, const C4<T>* Xc, in
 
 template <class T>
 void cg_combine(const T* part, int nsplit, const T* s, T sn2, const T* Mo, int ldm, int r, const T* t, T a2, int m,
-                T* g, const T* V, int ldv, int j, const T* r0, const T* v, double* dpart1, const int* active,
+                T* g, const T* V, int ldv, int j, const T* r0, const T* v, T* dpart1, const int* active,
                 cudaStream_t st) {
   const int tz = std::max(1, (m + GV_CHUNK - 1) / GV_CHUNK);
   k_cg_combine<T><<<cdiv(m, CB_ROWS), CB_WARPS * 32, std::max(r, 1) * sizeof(T), st>>>(
@@ -1320,14 +1329,14 @@ size_t cg_dpart_elems(int m, int budget) {
   return (size_t)(budget + 4) * cdiv(std::max(m, 1), CB_ROWS) + (size_t)(budget + 1) * cdiv(std::max(m, 1), UP_THREADS);
 }
 template <class T>
-void cg_upd1(int j, const double* dpart1, double* dots1, T* V, T* GV, int ldv, const T* s, const T* g, int m,
-             double* dpart2, const int* active, cudaStream_t st) {
+void cg_upd1(int j, const T* dpart1, double* dots1, T* V, T* GV, int ldv, const T* s, const T* g, int m,
+             T* dpart2, const int* active, cudaStream_t st) {
   k_cg_upd1<T><<<cdiv(m, UP_THREADS), UP_THREADS, 0, st>>>(j, dpart1, (int)cdiv(m, CB_ROWS), dots1, V, GV, ldv, s, g, m,
                                                            dpart2, active);
   note_launch();
 }
 template <class T>
-void cg_upd2(int j, const double* dots1, const double* dpart2, T* V, T* GV, int ldv, T* r, T* v, T* s, T* Q,
+void cg_upd2(int j, const double* dots1, const T* dpart2, T* V, T* GV, int ldv, T* r, T* v, T* s, T* Q,
              int m, double bd_tol, double rtol2_r0sq, int use_rtol, int* active, double* eta, double* alpha,
              int* count, T* Snext, cudaStream_t st) {
   k_cg_upd2<T><<<cdiv(m, UP_THREADS), UP_THREADS, 0, st>>>(j, dots1, dpart2, (int)cdiv(m, UP_THREADS), V, GV, ldv, r, v,
@@ -1573,11 +1582,11 @@ void check_finite(const double* x, size_t n, int* err, cudaStream_t st) {
   template void gram_block_dlogl_simt<T>(int, const C4<T>*, int, const C4<T>*, int, const T*, int, int, T, T*,   \
                                          int, cudaStream_t);                                                     \
   template void cg_combine<T>(const T*, int, const T*, T, const T*, int, int, const T*, T, int, T*, const T*,     \
-                              int, int, const T*, const T*, double*, const int*, cudaStream_t);                  \
+                              int, int, const T*, const T*, T*, const int*, cudaStream_t);                       \
   template void gemv_t<T>(const T*, int, int, int, const T*, T*, const int*, cudaStream_t);                      \
-  template void cg_upd1<T>(int, const double*, double*, T*, T*, int, const T*, const T*, int, double*,          \
+  template void cg_upd1<T>(int, const T*, double*, T*, T*, int, const T*, const T*, int, T*,                    \
                            const int*, cudaStream_t);                                                            \
-  template void cg_upd2<T>(int, const double*, const double*, T*, T*, int, T*, T*, T*, T*, int, double, double,  \
+  template void cg_upd2<T>(int, const double*, const T*, T*, T*, int, T*, T*, T*, T*, int, double, double,       \
                            int, int*, double*, double*, int*, T*, cudaStream_t);                                 \
   template void cg_reorth<T>(const T*, int, int, T*, int, double*, T*, int, const int*, cudaStream_t);          \
   template void cg_select<T>(int, const T*, const double*, int, T*, T*, int, const int*, cudaStream_t);          \
