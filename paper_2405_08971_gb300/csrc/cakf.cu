@@ -89,6 +89,12 @@ struct cakf_ctx {
   double* gram = nullptr;
   double* small = nullptr;   // scratch for small FP64 matrices
   size_t small_elems = 0;
+  // the per-step NLL term runs on a side stream, overlapped with the truncation eigensolver
+  cudaStream_t st_nll = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  double* small_nll = nullptr;
+  double* part_nll = nullptr;
+  size_t part_nll_elems = 0;
   double* U64 = nullptr;
   void* UT = nullptr;
   void* eigw = nullptr;
@@ -136,6 +142,11 @@ struct cakf_ctx {
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
     ev0 = ev1 = nullptr;
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    ev_fork = ev_join = nullptr;
+    if (st_nll) cudaStreamDestroy(st_nll);
+    st_nll = nullptr;
   }
 
   template <class P> int alloc(P*& out, size_t bytes) {
@@ -281,6 +292,15 @@ int plan_and_alloc(cakf_ctx* c, const cakf_problem* p) {
   if ((rc = c->alloc(c->gram, NE * NE * sizeof(double)))) return rc;
   c->small_elems = 8 * (NE * (size_t)wmax + NE * NE) + 64;
   if ((rc = c->alloc(c->small, c->small_elems * sizeof(double)))) return rc;
+  if ((rc = c->alloc(c->small_nll, (2 * (size_t)B * B + 4 * (size_t)B + 16) * sizeof(double)))) return rc;
+  c->part_nll_elems = std::max<size_t>(size_t(1) << 18, (size_t)B * B * 64);
+  if ((rc = c->alloc(c->part_nll, c->part_nll_elems * sizeof(double)))) return rc;
+  if (!c->st_nll && cudaStreamCreateWithFlags(&c->st_nll, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(CAKF_ERR_CUDA, "cudaStreamCreateWithFlags failed");
+  if (!c->ev_fork && cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess)
+    return fail(CAKF_ERR_CUDA, "cudaEventCreate failed");
+  if (!c->ev_join && cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess)
+    return fail(CAKF_ERR_CUDA, "cudaEventCreate failed");
   if ((rc = c->alloc(c->U64, NE * NE * sizeof(double)))) return rc;
   if ((rc = c->alloc(c->UT, NE * NE * es))) return rc;
   if ((rc = c->alloc(c->wv, NE * sizeof(double)))) return rc;
@@ -410,8 +430,13 @@ struct Runner {
     }
     const int B = std::max(c->budget, c->imax);
     const double bd_tol = (sizeof(T) == 8) ? 1e-12 : 1e-6;
+    bool nll_pending = false;   // an NLL term is in flight on the side stream
     for (int k = 1; k <= T_; ++k) {
       const int m = mk(k), ic = c->icap[k], rp = c->mcols[k - 1];
+      if (nll_pending) {
+        cudaStreamWaitEvent(st, c->ev_join, 0);
+        nll_pending = false;
+      }
       const double* mprev = c->mf + (size_t)(k - 1) * n;
       double* mout = c->mf + (size_t)k * n;
       double* vout = c->vf + (size_t)k * n;
@@ -503,19 +528,34 @@ struct Runner {
       }
       filter_out<T>(c->mpred, PVk, ldn, ic, c->sf2, a2, c->rs_plus, n, mout, vout, c->rs_pw, st);
       ph_end(1, ph1);
-      cudaEvent_t ph6 = ph_begin();
-      // NLL term from its definition: S^T G S (with the stored G s_j), S^T S and S^T r0, FP64 Cholesky
+      // NLL term from its definition: S^T G S (with the stored G s_j), S^T S and S^T r0, FP64 Cholesky.
+      // It reads only this step's actions, G S and r0, so it runs on the side stream while the
+      // truncation below runs here; the next step waits for it before the CG reuses those buffers.
       {
-        double* SS = c->small;
+        cudaEventRecord(c->ev_fork, st);
+        cudaStreamWaitEvent(c->st_nll, c->ev_fork, 0);
+        cudaStream_t s2 = c->st_nll;
+        cudaEvent_t ph6 = nullptr;
+        if (c->profiling) { ph6 = c->ev(); cudaEventRecord(ph6, s2); }
+        double* SS = c->small_nll;
         double* Gh = SS + (size_t)ic * ic;
         double* yh = Gh + (size_t)ic * ic;
         double* zs = yh + ic;
-        gemm_tn<T>(Sk(k), m, ic, Sk(k), m, ic, m, 1.0, 0.0, SS, ic, c->part64, c->part64_elems, st);
-        gemm_tn<T>(Sk(k), m, ic, GSk, m, ic, m, 1.0, 0.0, Gh, ic, c->part64, c->part64_elems, st);
-        gemm_tn<T>(Sk(k), m, ic, (const T*)c->r0v, m, 1, m, 1.0, 0.0, yh, ic, c->part64, c->part64_elems, st);
-        nll_def(c->count + k, Gh, SS, ic, yh, zs, c->nll + k, c->err, st);
+        const int mode = gemm_mode();
+        set_gemm_mode(0);   // own kernels only: the library GEMM handle belongs to the main stream
+        gemm_tn<T>(Sk(k), m, ic, Sk(k), m, ic, m, 1.0, 0.0, SS, ic, c->part_nll, c->part_nll_elems, s2);
+        gemm_tn<T>(Sk(k), m, ic, GSk, m, ic, m, 1.0, 0.0, Gh, ic, c->part_nll, c->part_nll_elems, s2);
+        gemm_tn<T>(Sk(k), m, ic, (const T*)c->r0v, m, 1, m, 1.0, 0.0, yh, ic, c->part_nll, c->part_nll_elems, s2);
+        set_gemm_mode(mode);
+        nll_def(c->count + k, Gh, SS, ic, yh, zs, c->nll + k, c->err, s2);
+        if (ph6) {
+          cudaEvent_t e1 = c->ev();
+          cudaEventRecord(e1, s2);
+          c->prof_phase.push_back({6, {ph6, e1}});
+        }
+        cudaEventRecord(c->ev_join, s2);
+        nll_pending = true;
       }
-      ph_end(6, ph6);
       // Truncate (Sec. 3.2)
       cudaEvent_t ph2 = ph_begin();
       int rc = truncate_filter(k, rp, ic);
@@ -524,6 +564,7 @@ struct Runner {
       cudaError_t ce = cudaGetLastError();
       if (ce != cudaSuccess) return fail(CAKF_ERR_CUDA, std::string("filter step: ") + cudaGetErrorString(ce));
     }
+    if (nll_pending) cudaStreamWaitEvent(st, c->ev_join, 0);
     return CAKF_OK;
   }
 
