@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--T", type=int, default=None, help="override the number of time steps")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp32-compare", action="store_true",
+                    help="skip the plain-FP32 comparison pass (one untimed + one timed pass at fp32)")
     ap.add_argument("--cpu-sample-steps", type=int, default=1)
     return ap.parse_args()
 
@@ -349,6 +351,29 @@ def main():
         line["cpu_baseline"] = {"value": args.cpu_sample_steps / secs, "unit": "time steps/s",
                                 "cores": cpu_cores(), "kind": "oracle", "sample": sample}
     ctx.close()
+
+    # ---- the same workload through the plain FP32 path (SIMT Gram x block, FP32 factors), for the
+    # mixed-vs-FP32 comparison the metric names: one untimed and one timed pass, events on the stream
+    if not args.no_fp32_compare and args.precision != "fp32":
+        prob32 = ck.make_problem(coords, w.kernel, w.log_lx, w.log_lt, w.log_sf2, w.log_sn2, T, w.dt, w.obs_ptr,
+                                 obs_idx, y, w.budget_i, w.rank_r, precision="fp32", prior_mean=mu)
+        ctx32 = ck.Context()
+        ck.cakf_filter(prob32, ctx32, outs[0], outs[1], stream=stream.cuda_stream)
+        ck.cakf_smooth(ctx32, outs[2], outs[3], stream=stream.cuda_stream)
+        barrier(ws)
+        torch.cuda.synchronize(dev)
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        ck.cakf_filter(prob32, ctx32, outs[0], outs[1], stream=stream.cuda_stream)
+        ck.cakf_smooth(ctx32, outs[2], outs[3], stream=stream.cuda_stream)
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms32 = allmax(ws, f0.elapsed_time(f1))
+        ctx32.close()
+        v32 = ws * T / (ms32 / 1e3)
+        line["fp32_plain"] = {"value": v32, "unit": "time steps/s", "steps": 1, "ms_per_step": ms32,
+                              "mixed_over_fp32": value / v32}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
