@@ -150,13 +150,21 @@ def barrier(ws):
 
 
 def allmax(ws, x):
+    """Maximum of x over the ranks (the slowest rank's time); a CPU tensor under gloo."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cpu" if dist.get_backend() == "gloo" else "cuda"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_value(ws, T, steps, ms_max):
+    """Whole-job time steps per second: every rank filters and smooths its own series of T steps
+    (independent replicas), so the job processes ws * T * steps time steps in the slowest rank's time."""
+    return ws * T * steps / (ms_max / 1e3)
 
 
 # --------------------------------------------------------------------------------------- CPU leg
@@ -244,7 +252,7 @@ def main():
     barrier(ws)
     ms = e0.elapsed_time(e1)
     ms_max = allmax(ws, ms)
-    value = ws * T * args.steps / (ms_max / 1e3)
+    value = job_value(ws, T, args.steps, ms_max)
 
     # ---- rooflines from live CUDA events (per kernel class), the dominant one reported as `roofline`
     pk, pk_src = peaks()
