@@ -486,8 +486,10 @@ struct Runner {
       T* Qa = (T*)c->Qa;       // orthonormal basis of the previous actions (CG policy only)
       // Re-orthogonalising each action against the previous ones leaves span(S) -- and so every
       // output -- unchanged; it keeps S^T S well conditioned for the NLL's FP64 Cholesky, which the
-      // FP64 mode's 1e-9 agreement needs.  The FP32-based modes run without it.
-      const bool reorth = !rep && sizeof(T) == 8;
+      // FP64 mode's 1e-9 agreement needs.  The FP32-based modes need it only when the budget is a
+      // large share of the observations (4 i >= m): there CG can converge within the budget and
+      // the later residuals, at FP32 rounding level, are no longer independent of the earlier ones.
+      const bool reorth = !rep && (sizeof(T) == 8 || 4 * ic >= m);
       // CG policy without re-orthogonalisation: k_cg_upd2 writes the next action (the updated
       // residual) itself, so the selection runs only for the first action
       const bool fused_select = !rep && !reorth;

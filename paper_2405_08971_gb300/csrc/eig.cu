@@ -1125,18 +1125,12 @@ int eig_sym_topk(double* A, int lda, int N, int nkeep, double* w, T* U, int ldu,
     if (psmem > 40 * 1024) cudaFuncSetAttribute(k_dc_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
     k_dc_prep<<<nm, DC_THREADS, psmem, st>>>(dm, e, N, W); note_launch();
     k_dc_rot<<<dim3((kmax + 127) / 128, nm), 128, 0, st>>>(dm, N, W); note_launch();
-    // The per-root work is FP64-bound (2 FMA/clk/SM), so the grids use small blocks to spread the
-    // roots over all SMs: one-warp blocks of 32 roots for small merges, two-warp blocks of 2 roots
-    // (one warp per root) for large ones.
-    if (kmax <= 32) {
-      k_dc_secular<1><<<(N + 31) / 32, 32, 0, st>>>(dm, dmo, N, W, err); note_launch();
-      k_dc_zhat<1><<<(N + 31) / 32, 32, 0, st>>>(dm, dmo, N, W); note_launch();
-      k_dc_vecs<1><<<(N + 31) / 32, 32, 0, st>>>(dm, dmo, N, W); note_launch();
-    } else {
-      k_dc_secular<32><<<(N + 1) / 2, 64, 0, st>>>(dm, dmo, N, W, err); note_launch();
-      k_dc_zhat<32><<<(N + 1) / 2, 64, 0, st>>>(dm, dmo, N, W); note_launch();
-      k_dc_vecs<32><<<(N + 1) / 2, 64, 0, st>>>(dm, dmo, N, W); note_launch();
-    }
+    // The per-root work is FP64-bound (2 FMA/clk/SM), so the grids use two-warp blocks (one warp per
+    // root) to spread the roots over all SMs.  (One thread per root for the small merges measured
+    // 3x slower: one warp per SM leaves its FP64 dependency chains uncovered.)
+    k_dc_secular<32><<<(N + 1) / 2, 64, 0, st>>>(dm, dmo, N, W, err); note_launch();
+    k_dc_zhat<32><<<(N + 1) / 2, 64, 0, st>>>(dm, dmo, N, W); note_launch();
+    k_dc_vecs<32><<<(N + 1) / 2, 64, 0, st>>>(dm, dmo, N, W); note_launch();
     dim3 gg((kmax + DG_T - 1) / DG_T, (kmax + DG_T - 1) / DG_T, nm);
     k_dc_gemm<<<gg, 256, 0, st>>>(dm, N, W); note_launch();
     const size_t fsmem = (size_t)kmax * (sizeof(double) + sizeof(long long));
