@@ -260,7 +260,8 @@ def main():
     clk = clk_mhz * 1e6
     nsm = 152
     fp64_peak = nsm * 2 * 2 * clk / 1e12          # 2 FP64 FMA per clock per SM
-    mufu_peak = nsm * 16 * clk / 1e12             # 16 MUFU results per clock per SM (T ops/s)
+    mufu_peak = nsm * 16 * clk / 1e12             # 16 MUFU results per clock per SM (T ops/s); ncu's
+                                                  # XU-pipe issue peak is twice that (see profiles/)
     peak_note = f"derived: {nsm} SMs x {{}} x median SM clock {clk_mhz:.0f} MHz"
     kernels = {}
     # FP64 tridiagonalisation (the eigensolver's dominant part): (4/3) N^3 flops per call
