@@ -140,35 +140,5 @@ template <class T> __device__ T block_sum(T v) {
   return r;
 }
 
-// Grid barrier for kernels launched cooperatively (all blocks co-resident).  `bar` points at
-// two zero-initialised words {count, generation}.  The spin is bounded: after `limit` polls the
-// barrier raises *err and returns false; callers then stop their work.
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* err,
-                                             long long limit = 50000000LL) {
-  __syncthreads();
-  bool ok = true;
-  if (threadIdx.x == 0) {
-    volatile unsigned* gen = bar + 1;
-    unsigned g = *gen;
-    __threadfence();
-    unsigned arrived = atomicAdd(bar, 1u) + 1u;
-    if (arrived == nblocks) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      long long spins = 0;
-      while (*gen == g) {
-        if (++spins > limit) { atomicExch(err, 2); ok = false; break; }
-        if (*(volatile int*)err) { ok = false; break; }
-      }
-    }
-    __threadfence();
-  }
-  __shared__ int s_ok;
-  if (threadIdx.x == 0) s_ok = ok;
-  __syncthreads();
-  return s_ok != 0;
-}
 
 }  // namespace cakf
