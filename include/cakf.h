@@ -111,10 +111,11 @@ typedef struct {
      [0] filter CG loop (actions, G s products, G-orthogonalisation)
      [1] filter Gram x block finalize incl. its low-rank correction and outputs
      [2] filter truncation (Gram, FP64 eig, rotation)
-     [3] smoother P^- X (Gram x block + low-rank correction)
+     [3] smoother P^- X (K X propagated from the filter's stored K(X, X_o)[V v] blocks, no kernel
+         evaluations; low-rank correction)
      [4] smoother combine and outputs (Z, P X, ws)
      [5] smoother truncation (Gram identities, FP64 eig, rotation)
-     [6] NLL term per step                                      [7] reserved               */
+     [6] NLL term per step (side stream: overlaps [2])        [7] reserved               */
   double phase_ms[8];
   /* summed device time of the eigensolver's parts (profiling on): [0] tridiagonalisation,
      [1] divide & conquer, [2] back-transformation and conversion of the kept vectors      */
@@ -153,8 +154,9 @@ int cakf_smooth(cakf_ctx* ctx, double* mean_out, double* var_out, void* cuda_str
  *   NLL = sum_k [ 1/2 logdet(2 pi S_k^T G_k S_k) + 1/2 r_k^T S_k (S_k^T G_k S_k)^-1 S_k^T r_k
  *                 - 1/2 logdet(S_k^T S_k) ],
  *   G_k = H_k P^-_k H_k^T + sn2 I, r_k = y_k - H_k m^-_k, S_k the actions (eq. proj-observation,
- *   Sec. 3.1).  It is accumulated during the filter from the G-orthogonal iteration
- *   (S^T G S = R^T R with R_jj^2 = eta_j) and the FP64 Cholesky factor of S^T S.
+ *   Sec. 3.1).  Each step's term is formed during the filter from its definition: S^T G S (with
+ *   the stored G s_j), S^T S and S^T r in FP64, both Cholesky-factored in FP64 (on a side stream
+ *   that overlaps the truncation; cakf_filter returns after it has finished).
  *   nll_out: one double (host).
  */
 int cakf_nll(cakf_ctx* ctx, double* nll_out);
