@@ -323,7 +323,7 @@ def main():
                 "avg_ms_parts": dict(zip(["tridiagonalisation", "divide_conquer", "back_transform"],
                                          [p / max(1, prof["eig_calls"]) for p in eig_parts]))},
         "phase_ms": {"filter": st["filter_ms"], "smooth": st["smooth_ms"]},
-        "phase_ms_per_pass": dict(zip(["filter_cg", "filter_finalize", "filter_truncate", "smooth_gram",
+        "phase_ms_per_pass": dict(zip(["filter_cg", "filter_finalize", "filter_truncate", "smooth_products",
                                        "smooth_combine", "smooth_truncate", "nll", "reserved"],
                                       [p / max(1, args.steps) for p in phases])),
         "clocks": clocks,
