@@ -797,13 +797,46 @@ __global__ void k_scatter_add_rows(const T* __restrict__ In, int ldi, const int*
   if (i < m && c < cols) Out[(size_t)c * ldo + idx[i]] += alpha * In[(size_t)c * ldi + i];
 }
 
+// sum_c A[i, c]^2 for row i of a column-major block.  FP32 factors: four compensated (Kahan) FP32
+// sums combined in FP64 -- relative error about 2^-24 whatever the column count, at FP32-pipe speed
+// (an FP64 accumulation chain per row is bound by GB300's narrow FP64 pipe); FP64 factors: FP64.
+template <class T>
+__device__ __forceinline__ double row_sumsq(const T* __restrict__ A, int lda, int i, int cols) {
+  double acc = 0.0;
+  if constexpr (sizeof(T) == 4) {
+    float s[4] = {0.f, 0.f, 0.f, 0.f}, e[4] = {0.f, 0.f, 0.f, 0.f};
+    int c = 0;
+    for (; c + 3 < cols; c += 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float v = A[(size_t)(c + u) * lda + i];
+        const float y = fmaf(v, v, -e[u]);
+        const float t = s[u] + y;
+        e[u] = (t - s[u]) - y;
+        s[u] = t;
+      }
+    }
+    for (; c < cols; ++c) {
+      const float v = A[(size_t)c * lda + i];
+      const float y = fmaf(v, v, -e[0]);
+      const float t = s[0] + y;
+      e[0] = (t - s[0]) - y;
+      s[0] = t;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc += double(s[u]) - double(e[u]);
+  } else {
+    for (int c = 0; c < cols; ++c) { const double v = double(A[(size_t)c * lda + i]); acc += v * v; }
+  }
+  return acc;
+}
+
 // rs[i] = sum_c A[i, c]^2 (+ beta * rs[i])
 template <class T>
 __global__ void k_rowsumsq(const T* __restrict__ A, int lda, int n, int cols, double beta, double* __restrict__ rs) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double acc = 0.0;
-  for (int c = 0; c < cols; ++c) { double v = double(A[(size_t)c * lda + i]); acc += v * v; }
+  const double acc = row_sumsq(A, lda, i, cols);
   rs[i] = acc + (beta != 0.0 ? beta * rs[i] : 0.0);
 }
 
@@ -823,8 +856,7 @@ __global__ void k_filter_out(const double* __restrict__ mpred, const T* __restri
                              double* __restrict__ mout, double* __restrict__ vout, double* __restrict__ rs_pw) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double acc = 0.0;
-  for (int c = 0; c < ic; ++c) { double v = double(PVv[(size_t)c * ld + i]); acc += v * v; }
+  const double acc = ic > 0 ? row_sumsq(PVv, ld, i, ic) : 0.0;
   double pw = ic >= 0 ? double(PVv[(size_t)ic * ld + i]) : 0.0;
   mout[i] = mpred[i] + pw;
   vout[i] = sf2 - a2 * rs_plus[i] - acc;
@@ -845,8 +877,7 @@ __global__ void k_smooth_out(const double* __restrict__ mk, const double* __rest
                              int ld, int cw, int n, double* __restrict__ ms, double* __restrict__ vs) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double acc = 0.0;
-  for (int c = 0; c < cw; ++c) { double v = double(Y[(size_t)c * ld + i]); acc += v * v; }
+  const double acc = row_sumsq(Y, ld, i, cw);
   ms[i] = mk[i] + double(Y[(size_t)cw * ld + i]);
   vs[i] = vk[i] - acc;
 }
