@@ -264,12 +264,18 @@ def main():
                                                   # XU-pipe issue peak is twice that (see profiles/)
     peak_note = f"derived: {nsm} SMs x {{}} x median SM clock {clk_mhz:.0f} MHz"
     kernels = {}
+    # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
+    # each kernel as it is now, on the shapes of this workload (summaries under profiles/):
+    # k_tridiag at N = 576, k_gram_matvec_f2 at m = 8,192 (a launch of the first step, without the
+    # M^T s blocks), k_gram_tc (split FP16) at 65,536 x 8,192 x 65.  Only the sphere-65k split-FP16 configuration has them; other runs report null.
+    ncu_traffic = {"k_tridiag": 2705664.0, "k_gram_matvec": 197376.0, "k_gram_tc": 8160000.0} \
+        if (args.config == "sphere-65k" and args.precision == "fp16x3") else {}
     # FP64 tridiagonalisation (the eigensolver's dominant part): (4/3) N^3 flops per call
     tri_ms = eig_parts[0]
     if prof["eig_calls"] and tri_ms > 0:
         ach = eig_flops[0] / (tri_ms / 1e3) / 1e12
         kernels["k_tridiag"] = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
-                                "frac": ach / fp64_peak, "traffic": None,
+                                "frac": ach / fp64_peak, "traffic": ncu_traffic.get("k_tridiag"),
                                 "peak_source": peak_note.format("2 FP64 FMA/clk x 2"),
                                 "launches": prof["eig_calls"], "avg_ms": tri_ms / prof["eig_calls"],
                                 "ms_total": tri_ms,
@@ -280,7 +286,8 @@ def main():
         evals = prof["gram_block_evals"] / (gb_ms / 1e3) / 1e12
         tfl = prof["gram_block_flops"] / (gb_ms / 1e3) / 1e12
         ent = {"bound": "alu", "achieved": 2 * evals, "peak": mufu_peak, "unit": "TMUFU-op/s",
-               "frac": 2 * evals / mufu_peak, "traffic": None, "peak_source": peak_note.format("16 MUFU/clk"),
+               "frac": 2 * evals / mufu_peak, "traffic": ncu_traffic.get("k_gram_tc"),
+               "peak_source": peak_note.format("16 MUFU/clk"),
                "launches": prof["gram_block_launches"], "avg_ms": gb_ms / prof["gram_block_launches"],
                "ms_total": gb_ms, "tensor_tflops": tfl}
         if args.precision in ("bf16", "fp16x3"):
@@ -295,7 +302,8 @@ def main():
         mv_ms = prof["cg_matvec_ms"]
         evals = prof["cg_matvec_evals"] / (mv_ms / 1e3) / 1e12
         kernels["k_gram_matvec"] = {"bound": "alu", "achieved": 2 * evals, "peak": mufu_peak,
-                                    "unit": "TMUFU-op/s", "frac": 2 * evals / mufu_peak, "traffic": None,
+                                    "unit": "TMUFU-op/s", "frac": 2 * evals / mufu_peak,
+                                    "traffic": ncu_traffic.get("k_gram_matvec"),
                                     "peak_source": peak_note.format("16 MUFU/clk"),
                                     "launches_sampled": prof["cg_matvec_launches"],
                                     "avg_ms": mv_ms / prof["cg_matvec_launches"],
