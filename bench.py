@@ -267,7 +267,8 @@ def main():
     # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
     # each kernel as it is now, on the shapes of this workload (summaries under profiles/):
     # k_tridiag at N = 576, k_gram_matvec_f2 at m = 8,192 (a launch of the first step, without the
-    # M^T s blocks), k_gram_tc (split FP16) at 65,536 x 8,192 x 65.  Only the sphere-65k split-FP16 configuration has them; other runs report null.
+    # M^T s blocks), k_gram_tc (split FP16) at 65,536 x 8,192 x 65.  Only the sphere-65k split-FP16
+    # configuration has them; other runs report null.
     ncu_traffic = {"k_tridiag": 2705664.0, "k_gram_matvec": 197376.0, "k_gram_tc": 8160000.0} \
         if (args.config == "sphere-65k" and args.precision == "fp16x3") else {}
     # FP64 tridiagonalisation (the eigensolver's dominant part): (4/3) N^3 flops per call
