@@ -79,6 +79,11 @@ CASES = {
                                              kernel=synth.MATERN12, missing=(2, 5)),
     "m52-full-budget-trunc": lambda: synth.small(n=150, dim=2, m=20, T=5, budget_i=20, rank_r=30, seed=34,
                                                  kernel=synth.MATERN52),
+    # degenerate and ragged shapes: one state and one observation; one full 128-wide matvec tile
+    # plus a single-row tile; a single time step with truncation in it
+    "scalar-n1-m1": lambda: synth.small(n=1, m=1, T=5, budget_i=1, rank_r=0, seed=36),
+    "ragged-m129": lambda: synth.small(n=400, dim=2, m=129, T=3, budget_i=5, rank_r=12, seed=37),
+    "one-step-trunc": lambda: synth.small(n=100, dim=2, m=30, T=1, budget_i=6, rank_r=4, seed=38),
 }
 
 # Truncation Grams of order 512 (r + i = 448 + 64): the eigensolver's larger shared-memory
@@ -118,7 +123,8 @@ def test_fp64_replayed_actions(name):
     assert abs(got["nll"] - ref["nll"]) < 1e-10 * abs(ref["nll"])
 
 
-@pytest.mark.parametrize("name", ["grid2d-ragged-trunc", "sphere-m32-trunc", "missing-steps-m12"])
+@pytest.mark.parametrize("name", ["grid2d-ragged-trunc", "sphere-m32-trunc", "missing-steps-m12", "scalar-n1-m1",
+                                  "ragged-m129", "one-step-trunc"])
 def test_fp32_parity(name):
     w = CASES[name]()
     ref = run_oracle(w)
