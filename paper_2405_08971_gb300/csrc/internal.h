@@ -35,8 +35,6 @@ template <class T>
 void cg_combine(const T* part, int nsplit, const T* s, T sn2, const T* Mo, int ldm, int r, const T* t, T a2, int m,
                 T* g, const T* V, int ldv, int j, const T* r0, const T* v, T* dpart1, const int* active,
                 cudaStream_t st);
-template <class T>
-void gemv_t(const T* A, int lda, int rows, int cols, const T* x, T* t, const int* active, cudaStream_t st);
 // elements needed for dpart1 followed by dpart2 at m observations and an action budget
 size_t cg_dpart_elems(int m, int budget);
 template <class T>

@@ -50,7 +50,7 @@ __global__ void k_gather_coords(const C4<T>* __restrict__ X, const int* __restri
 // A lane owns MVS_R rows of the tile; each warp takes 32 of its columns (staged in shared memory)
 // and reduces a column's MVS_R * 32 products with one warp sum.
 // The first ngv blocks instead form the partials of t = Mo^T s (one warp per column of Mo and
-// chunk of GV_CHUNK rows, as k_gemv_t), which k_cg_combine needs next: one launch for both.
+// chunk of GV_CHUNK rows), which k_cg_combine needs next: one launch for both.
 constexpr int MVS_T = 128, MVS_R = MVS_T / 32, MVS_W = MVS_T / 32;
 constexpr int GV_CHUNK = 1024;
 template <int KER, class T>
@@ -256,8 +256,9 @@ k_gram_matvec_f2(const C4<float>* __restrict__ Xo, const float* __restrict__ s, 
 }
 
 // g = sum_p part[p] + sn2 * s - a2 * Mo t     (Mo: m x r col-major, ld = ldm).  t is summed from
-// the row-chunk partials of k_gemv_t (tz chunks) into shared memory first.  A block owns CB_ROWS
-// rows: lane = row, each of the CB_WARPS warps takes every CB_WARPS-th column of Mo (coalesced
+// the row-chunk partials of the matvec launch's Mo^T s blocks (tz chunks) into shared memory
+// first.  A block owns CB_ROWS rows: lane = row, each of the CB_WARPS warps takes every
+// CB_WARPS-th column of Mo (coalesced
 // 128-byte column segments, CB_UNROLL independent accumulators), and the warps' sums are added
 // in shared memory.  The block then forms its rows' share of the first dot pass of CG iteration j
 //   q < j: V[:, q] . g ;  j: s . g ;  j+1: s . r0 ;  j+2: g . v ;  j+3: s . s
@@ -335,24 +336,6 @@ k_cg_combine(const T* __restrict__ part, int nsplit, const T* __restrict__ s, T 
     pr = warp_sum(pr);
     if (lane == 0) dpart[(size_t)q * gridDim.x + blockIdx.x] = pr;
   }
-}
-
-// Partial transposed products: part[z][l] = sum_{i in row chunk z} A[i, l] x[i]  (A: rows x cols col-major).
-// One warp per (column, row chunk); the chunks are summed by the consumer (k_cg_combine).
-template <class T>
-__global__ void k_gemv_t(const T* __restrict__ A, int lda, int rows, int cols, const T* __restrict__ x,
-                         T* __restrict__ part, const int* __restrict__ active) {
-  if (active && !*active) return;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (warp >= cols) return;
-  const int z = blockIdx.y;
-  const int i0 = z * GV_CHUNK, i1 = min(rows, i0 + GV_CHUNK);
-  const T* a = A + (size_t)warp * lda;
-  T acc = T(0);
-#pragma unroll 8
-  for (int i = i0 + lane; i < i1; i += 32) acc = fma(a[i], x[i], acc);
-  acc = warp_sum(acc);
-  if (lane == 0) part[(size_t)z * cols + warp] = acc;
 }
 
 // Per-thread share of a block-wide dot product a . b over m entries (strided by blockDim.x).
@@ -1349,13 +1332,6 @@ void cg_combine(const T* part, int nsplit, const T* s, T sn2, const T* Mo, int l
       part, nsplit, s, sn2, Mo, ldm, r, t, tz, a2, m, g, V, ldv, j, r0, v, dpart1, active);
   note_launch();
 }
-// t must hold ceil(rows / 1024) * cols partials (summed by cg_combine)
-template <class T>
-void gemv_t(const T* A, int lda, int rows, int cols, const T* x, T* t, const int* active, cudaStream_t st) {
-  if (cols <= 0) return;
-  const int tz = std::max(1, (rows + GV_CHUNK - 1) / GV_CHUNK);
-  k_gemv_t<T><<<dim3(cdiv((size_t)cols * 32, 256), tz), 256, 0, st>>>(A, lda, rows, cols, x, t, active); note_launch();
-}
 size_t cg_dpart_elems(int m, int budget) {
   return (size_t)(budget + 4) * cdiv(std::max(m, 1), CB_ROWS) + (size_t)(budget + 1) * cdiv(std::max(m, 1), UP_THREADS);
 }
@@ -1614,7 +1590,6 @@ void check_finite(const double* x, size_t n, int* err, cudaStream_t st) {
                                          int, cudaStream_t);                                                     \
   template void cg_combine<T>(const T*, int, const T*, T, const T*, int, int, const T*, T, int, T*, const T*,     \
                               int, int, const T*, const T*, T*, const int*, cudaStream_t);                       \
-  template void gemv_t<T>(const T*, int, int, int, const T*, T*, const int*, cudaStream_t);                      \
   template void cg_upd1<T>(int, const T*, double*, T*, T*, int, const T*, const T*, int, T*,                    \
                            const int*, cudaStream_t);                                                            \
   template void cg_upd2<T>(int, const double*, const T*, T*, T*, int, T*, T*, T*, T*, int, double, double,       \
