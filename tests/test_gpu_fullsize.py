@@ -9,6 +9,9 @@ i = 64, r = 512), in the launch configuration bench.py times.
   properties that hold at any size: 0 < variance <= sigma_f^2, the smoother variance never above the
   filter variance of the same step, finite NLL.
 
+* Two steps of the largest configuration's shapes (n = 262,144, m = 16,384, i = 128, r = 256):
+  split FP16 against the device FP64 mode, and the same properties.
+
 Tolerances: FP64 mode 1e-9 (as on the small cases); FP32 and split FP16 1e-3 for means and
 variances (the accuracy target of the mixed-precision path), 1e-3 for the NLL.
 """
@@ -76,6 +79,26 @@ def test_three_steps_against_fp64_mode(fp64_T3, precision):
              ms=mean_err(got["ms"], ref["ms"]), vs=var_err(got["vs"], ref["vs"]),
              nll=abs(got["nll"] - ref["nll"]) / abs(ref["nll"]))
     print(precision, {k: f"{v:.2e}" for k, v in e.items()})
+    for k, v in e.items():
+        assert v < 1e-3, (k, v)
+    sf2 = float(np.exp(w.log_sf2))
+    for key in ("vf", "vs"):
+        assert np.all(got[key] > 0) and np.all(got[key] <= sf2 * (1 + 1e-6))
+    assert np.all(got["vs"][:-1] <= got["vf"][:-1] * (1 + 1e-5) + 1e-7)
+    assert np.isfinite(got["nll"])
+
+
+def test_sphere_262k_two_steps_against_fp64_mode():
+    """The largest configuration's shapes (512 x 512 sphere grid, n = 262,144, m = 16,384, i = 128,
+    r = 256) over two steps: the split-FP16 path against the device FP64 mode (1e-3), and the
+    properties that hold at any size.  (The dense oracle does not fit at this n.)"""
+    w = synth.sphere_262k(T=2)
+    ref = run_gpu(w, "fp64")
+    got = run_gpu(w, "fp16x3")
+    e = dict(mf=mean_err(got["mf"][1:], ref["mf"][1:]), vf=var_err(got["vf"], ref["vf"]),
+             ms=mean_err(got["ms"], ref["ms"]), vs=var_err(got["vs"], ref["vs"]),
+             nll=abs(got["nll"] - ref["nll"]) / abs(ref["nll"]))
+    print("262k fp16x3", {k: f"{v:.2e}" for k, v in e.items()})
     for k, v in e.items():
         assert v < 1e-3, (k, v)
     sf2 = float(np.exp(w.log_sf2))
