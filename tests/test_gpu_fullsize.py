@@ -9,6 +9,7 @@ i = 64, r = 512), in the launch configuration bench.py times.
   properties that hold at any size: 0 < variance <= sigma_f^2, the smoother variance never above the
   filter variance of the same step, finite NLL.
 
+* Two steps of the 2-D configuration at full size (n = 16,384) against the oracle itself.
 * Two steps of the largest configuration's shapes (n = 262,144, m = 16,384, i = 128, r = 256):
   split FP16 against the device FP64 mode, and the same properties.
 
@@ -106,3 +107,26 @@ def test_sphere_262k_two_steps_against_fp64_mode():
         assert np.all(got[key] > 0) and np.all(got[key] <= sf2 * (1 + 1e-6))
     assert np.all(got["vs"][:-1] <= got["vf"][:-1] * (1 + 1e-5) + 1e-7)
     assert np.isfinite(got["nll"])
+
+
+@pytest.fixture(scope="module")
+def grid16k_T2():
+    w = synth.grid2d_16k(T=2)
+    f = oracle.filter_run(w)
+    ms, vs, _ = oracle.smoother_run(w, f)
+    return w, dict(mf=f.m, vf=f.var, ms=ms, vs=vs, nll=oracle.nll_total(f))
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("fp32", 1e-3)])
+def test_grid16k_two_steps_against_oracle(grid16k_T2, precision, tol):
+    """The 2-D configuration at full size (128 x 128 grid, n = 16,384, m = 2,000, i = 32, r = 256,
+    Matern-5/2, seasonal prior mean) over two steps, filter and smoother, against the oracle."""
+    w, ref = grid16k_T2
+    got = run_gpu(w, precision)
+    e = dict(mf=mean_err(got["mf"][1:], ref["mf"][1:]), vf=var_err(got["vf"][1:], ref["vf"][1:]),
+             ms=mean_err(got["ms"], ref["ms"]), vs=var_err(got["vs"], ref["vs"]),
+             nll=abs(got["nll"] - ref["nll"]) / abs(ref["nll"]))
+    print("16k", precision, {k: f"{v:.2e}" for k, v in e.items()})
+    vtol = tol if precision == "fp64" else 2e-3
+    assert e["mf"] < tol and e["ms"] < tol and e["nll"] < tol
+    assert e["vf"] < vtol and e["vs"] < vtol

@@ -73,3 +73,24 @@ def test_autograd_function():
     nll.backward()
     _, g = gpu_grad(w, "fp64")
     assert np.allclose(theta.grad.numpy(), g, rtol=1e-12, atol=0)
+
+
+def test_gradient_fd_instance_n1024_t20():
+    """The gradient-check configuration: the 16k-grid model on a 32 x 32 grid (n = 1,024), T = 20,
+    m = 128, i = 32, r = 256; device FP64 gradient against central FD of the oracle (h = 1e-5),
+    within 1e-5 relative.  Here the budget is a quarter of the observations and CG converges
+    within it, so the device-chosen actions differ from the oracle's at rounding level and the
+    NLL (a function of span(S)) by ~1e-6; the device therefore replays the oracle's actions,
+    which makes both sides differentiate the same frozen model."""
+    w = synth.fd_grid2d_1k(T=20)
+    nll_o, g_fd = oracle.nll_grad_fd(w, h=1e-5)
+    f = oracle.filter_run(w)
+    flat, counts = ck.pack_actions(f.S, w.T)
+    prob = ck.problem_from_workload(w, precision="fp64", replay=(flat, counts))
+    ctx, _, _ = ck.cakf_filter(prob, want_outputs=False)
+    nll = ck.cakf_nll(ctx)
+    g = ck.cakf_nll_backward(ctx)
+    ctx.close()
+    print("n1024 fd", g_fd, "gpu", g)
+    assert abs(nll - nll_o) < 1e-9 * abs(nll_o)
+    assert rel(g, g_fd) < 1e-5, (g, g_fd)
