@@ -184,3 +184,35 @@ def test_pins_catch_planted_mistakes(monkeypatch):
     f = oracle.filter_run(w)
     ms, vs, _ = oracle.smoother_run(w, f)
     assert rel(vs, ref["vs"]) > 1e-3
+
+
+def test_smoother_kernel_products_follow_the_recursion():
+    """Alg. 3 needs P^-_k X with X = a [Ws ws]; its expensive part K X can be carried through the
+    smoother's own linear recursion: every column of [Ws ws] is a combination of earlier [Ws ws]
+    columns and of the filter's W_k = H^T V_k, so K [Ws ws] obeys the same recursion with K W_k in
+    place of W_k.  Checked here in FP64 against K applied directly, step by step (truncation
+    included), on the oracle's own filter run."""
+    w = synth.small(n=150, dim=2, m=30, T=6, budget_i=6, rank_r=14, seed=51)
+    model = oc.model_from(w)
+    f = oracle.filter_run(w)
+    a, T = model.a, w.T
+    Ws, ws = f.W[T], f.w[T]
+    KWs, Kws = model.K_times(Ws), model.K_times(ws)
+    for k in range(T - 1, 0, -1):
+        X = a * np.concatenate([Ws, ws[:, None]], axis=1)
+        KX = a * np.concatenate([KWs, Kws[:, None]], axis=1)            # recursion, no K evaluation
+        assert rel(KX, model.K_times(X)) < 1e-11
+        Mp = f.M_pred[k]
+        PmX = KX - Mp @ (Mp.T @ X)
+        Wk = f.W[k]
+        KWk, Kwk = model.K_times(Wk), model.K_times(f.w[k])            # the filter's stored products
+        Z = Wk.T @ PmX
+        Y2 = X - Wk @ Z
+        KY2 = KX - KWk @ Z
+        ws, Kws = f.w[k] + Y2[:, -1], Kwk + KY2[:, -1]
+        Wfull = np.concatenate([Wk, Y2[:, :-1]], axis=1)
+        KWfull = np.concatenate([KWk, KY2[:, :-1]], axis=1)
+        Ws, U, _, _ = oc.truncate(Wfull, w.rank_r)
+        KWs = KWfull if U is None else KWfull @ U
+        assert rel(KWs, model.K_times(Ws)) < 1e-11
+        assert rel(Kws, model.K_times(ws)) < 1e-11
