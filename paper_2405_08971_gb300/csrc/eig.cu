@@ -103,6 +103,13 @@ k_tridiag(double* __restrict__ A, int lda, int N, double* __restrict__ d, double
   const int G = gridDim.x, tid = threadIdx.x, TB = blockDim.x;
   const int warp = tid >> 5, lane = tid & 31, nw = TB >> 5;
   const int nslot = (N + G - 1) / G;   // column j lives in block j % G, slot j / G
+  // The block owning the last column writes the outputs (d, e, tau, reflectors): it publishes
+  // exchange words at every step.  Every other block leaves once it owns no column >= k + 2 (it
+  // would publish nothing more), so each block still reading step k's words publishes words for
+  // step k + 1 -- which is what keeps two exchange buffers safe: no block can publish step k + 2
+  // before every running block has consumed step k.
+  const int ob = (N - 1) % G;
+  const int maxcol = (int)blockIdx.x + G * ((N - 1 - (int)blockIdx.x) / G);
   if (N <= 2) {
     if (blockIdx.x == 0 && tid == 0) {
       d[0] = A[0];
@@ -151,10 +158,11 @@ k_tridiag(double* __restrict__ A, int lda, int N, double* __restrict__ d, double
       if (lane == 0) st_relaxed(Pbuf + j - 1, with_epoch(tk * acc, 0));
       if (j == 1) for (int t = lane; t < L; t += 32) st_relaxed(Cbuf + t, with_epoch(col[t], 0));
     }
-    if (blockIdx.x == 0 && tid == 0) d[0] = A[0];
+    if (blockIdx.x == ob && tid == 0) d[0] = A[0];
     __syncthreads();
   }
   for (int k = 0; k + 2 < N; ++k) {
+    if ((int)blockIdx.x != ob && maxcol < k + 2) return;
     const int L = N - k - 1;
     const double* Pk = Pbuf + (size_t)(k & 1) * N;
     double* Pn = Pbuf + (size_t)((k + 1) & 1) * N;
@@ -212,7 +220,7 @@ k_tridiag(double* __restrict__ A, int lda, int N, double* __restrict__ d, double
         double ta = 0.0, be = 0.0, sc = 0.0;
         if (next) house_scalars(c[1], sigma, ta, be, sc);
         bc[2] = ta; bc[3] = be; red[0] = sc;
-        if (blockIdx.x == 0) {
+        if (blockIdx.x == ob) {
           d[k + 1] = c[0];
           e[k] = bk;
           tau[k] = tk;
@@ -251,7 +259,7 @@ k_tridiag(double* __restrict__ A, int lda, int N, double* __restrict__ d, double
       }
     }
     // (5) store the reflector v_k below the subdiagonal of column k (for the back-transformation)
-    if (blockIdx.x == 0)
+    if (blockIdx.x == ob)
       for (int t = tid; t < L; t += TB) A[(size_t)k * lda + k + 1 + t] = v[t];
     tk = tn;
     bk = bn;
