@@ -56,7 +56,7 @@ enum { CAKF_MATERN12 = 0, CAKF_MATERN32 = 1, CAKF_MATERN52 = 2 };
 enum {
   CAKF_FP64 = 0,   /* all in FP64 (reference mode)                                          */
   CAKF_FP32 = 1,   /* plain FP32 SIMT kernels (factors, CG and tall-skinny GEMMs in FP32)    */
-  CAKF_TF32 = 2,   /* reserved (tcgen05 kind::tf32); rejected with CAKF_ERR_ARG in this build */
+  CAKF_TF32 = 2,   /* reserved (tcgen05 kind::tf32), not implemented: rejected with CAKF_ERR_ARG */
   CAKF_BF16 = 3,   /* Gram tiles x blocks on tcgen05 kind::f16 (bf16), FP32 accumulation    */
   CAKF_FP16X3 = 4  /* Gram tiles x blocks on tcgen05 kind::f16 with split FP16 operands:
                       x = hi + lo (both fp16, B scaled per column by a power of two), three

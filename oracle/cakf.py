@@ -31,7 +31,7 @@ Smoothing"):
 * Gradient: central finite differences of the NLL with the actions S_k and the
   truncation rotations U_k frozen (exact inference in a fixed modified model).
 
-Readings where the paper is ambiguous (each one is listed in the design doc):
+Readings taken where the paper is ambiguous, garbled or silent:
   R1 residual/action order in the iterative update: per iteration
      r = r0 - G v; s = r; alpha = s^T r; d = (I - V V^T G) s; eta = s^T G d;
      v += (alpha/eta) d; V <- (V, d/sqrt(eta)).

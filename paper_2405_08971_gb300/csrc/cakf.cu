@@ -1002,7 +1002,7 @@ int validate(const cakf_problem* p) {
   if (N > 0 && (!p->obs_idx || !p->y)) return fail(CAKF_ERR_ARG, "obs_idx / y is NULL");
   if (p->budget_i < 1 || p->budget_i > 1024) return fail(CAKF_ERR_ARG, "budget_i must be in 1..1024");
   if (p->precision < CAKF_FP64 || p->precision > CAKF_FP16X3) return fail(CAKF_ERR_ARG, "unknown precision");
-  if (p->precision == CAKF_TF32) return fail(CAKF_ERR_ARG, "CAKF_TF32 Gram tiles are not available in this build");
+  if (p->precision == CAKF_TF32) return fail(CAKF_ERR_ARG, "CAKF_TF32 Gram tiles are reserved and not implemented");
   const double hp[4] = {p->log_lx, p->log_lt, p->log_sf2, p->log_sn2};
   for (double h : hp)
     if (!std::isfinite(h) || std::fabs(h) > 80) return fail(CAKF_ERR_ARG, "hyperparameters must be finite");
