@@ -6,7 +6,11 @@
 * the butterfly reduce-scatter of the CG matvec (k_gram_matvec_f2): 32 lanes, each with 32
   per-column partial sums, exchange halves over offsets 16, 8, 4, 2, 1; lane l must end with the
   sum over lanes of column l;
-* the order-preserving integer key of a double used by the sorts (negative values mirrored).
+* the order-preserving integer key of a double used by the sorts (negative values mirrored);
+* the close-pole deflation of k_dc_prep (pair tests on the merged values, sequential scan only from
+  the first pair that fires) against the full sequential scan, on clustered poles with tiny z
+  components, and the grouped, register-carried rotation application of k_dc_rot against applying
+  the rotations one by one.
 """
 import struct
 
@@ -87,3 +91,104 @@ def test_butterfly_reduce_scatter():
         cur = new
         o >>= 1
     np.testing.assert_allclose(cur[:, 0], want, rtol=1e-12)
+
+
+# ---- divide & conquer deflation (k_dc_prep, k_dc_rot)
+def scan_full(D, Z, small, tol):
+    """Sequential close-pole scan over all entries (the definition)."""
+    D, Z = D.copy(), Z.copy()
+    stat = [1 if s else 0 for s in small]
+    rots, last = [], -1
+    for j in range(len(D)):
+        if stat[j]:
+            continue
+        if last >= 0:
+            zl, zj, dl, dj = Z[last], Z[j], D[last], D[j]
+            t2 = zl * zl + zj * zj
+            if abs(dj - dl) * abs(zl * zj) <= tol * t2:
+                t = np.sqrt(t2)
+                c, s = zj / t, -zl / t
+                rots.append((last, j, c, s))
+                D[last], D[j] = c * c * dl + s * s * dj, s * s * dl + c * c * dj
+                Z[last], Z[j] = 0.0, t
+                stat[last] = 2
+        last = j
+    return D, Z, stat, rots
+
+
+def scan_from_first_firing(D, Z, small, tol):
+    """The kernel's form: test consecutive candidate pairs on the merged values (in parallel),
+    then scan sequentially from the first pair that fires."""
+    cand = [j for j in range(len(D)) if not small[j]]
+    fires = [u for u in range(1, len(cand))
+             if abs(D[cand[u]] - D[cand[u - 1]]) * abs(Z[cand[u - 1]] * Z[cand[u]])
+             <= tol * (Z[cand[u - 1]] ** 2 + Z[cand[u]] ** 2)]
+    D, Z = D.copy(), Z.copy()
+    stat = [1 if s else 0 for s in small]
+    rots = []
+    if fires:
+        first = fires[0]
+        last = cand[first - 1]
+        for u in range(first, len(cand)):
+            j = cand[u]
+            zl, zj, dl, dj = Z[last], Z[j], D[last], D[j]
+            t2 = zl * zl + zj * zj
+            if abs(dj - dl) * abs(zl * zj) <= tol * t2:
+                t = np.sqrt(t2)
+                c, s = zj / t, -zl / t
+                rots.append((last, j, c, s))
+                D[last], D[j] = c * c * dl + s * s * dj, s * s * dl + c * c * dj
+                Z[last], Z[j] = 0.0, t
+                stat[last] = 2
+            last = j
+    return D, Z, stat, rots
+
+
+def apply_sequential(Q, rots):
+    Q = Q.copy()
+    for a, b, c, s in rots:
+        qa, qb = Q[:, a].copy(), Q[:, b].copy()
+        Q[:, a], Q[:, b] = c * qa + s * qb, -s * qa + c * qb
+    return Q
+
+
+def apply_grouped(Q, rots, RG=8):
+    """k_dc_rot per row: groups of RG rotations load their operands first; the a_q = b_{q-1}
+    chain is carried in a register."""
+    Q = Q.copy()
+    for row in range(Q.shape[0]):
+        carry, carry_col = 0.0, -1
+        for q0 in range(0, len(rots), RG):
+            grp = rots[q0:q0 + RG]
+            xa, xb = [], []
+            for u, (a, b, _, _) in enumerate(grp):
+                prev = carry_col if u == 0 else grp[u - 1][1]
+                xb.append(Q[row, b])
+                xa.append(0.0 if a == prev else Q[row, a])
+            for u, (a, b, c, s) in enumerate(grp):
+                prev = carry_col if u == 0 else grp[u - 1][1]
+                av = carry if a == prev else xa[u]
+                na, nb = c * av + s * xb[u], -s * av + c * xb[u]
+                Q[row, a], Q[row, b] = na, nb
+                carry, carry_col = nb, b
+    return Q
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_deflation_scan_and_rotation_application(seed):
+    rng = np.random.default_rng(100 + seed)
+    K = int(rng.integers(4, 60))
+    D = np.sort(rng.choice(np.round(rng.normal(size=K // 3 + 2), 1), K)
+                + 1e-15 * rng.normal(size=K))                 # clusters of near-equal poles
+    Z = rng.normal(size=K)
+    Z[rng.random(K) < 0.2] *= 1e-17                            # some tiny components
+    Z /= np.linalg.norm(Z)
+    rho, tol = 1.3, 8 * 2.22e-16 * 3.0
+    small = [rho * abs(z) <= tol for z in Z]
+    ref = scan_full(D, Z, small, tol)
+    got = scan_from_first_firing(D, Z, small, tol)
+    assert ref[2] == got[2] and len(ref[3]) == len(got[3])
+    np.testing.assert_array_equal(ref[0], got[0])
+    np.testing.assert_array_equal(ref[1], got[1])
+    Q = rng.normal(size=(K, K))
+    np.testing.assert_allclose(apply_grouped(Q, ref[3]), apply_sequential(Q, ref[3]), rtol=0, atol=1e-13)
