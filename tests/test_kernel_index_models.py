@@ -10,7 +10,9 @@
 * the close-pole deflation of k_dc_prep (pair tests on the merged values, sequential scan only from
   the first pair that fires) against the full sequential scan, on clustered poles with tiny z
   components, and the grouped, register-carried rotation application of k_dc_rot against applying
-  the rotations one by one.
+  the rotations one by one;
+* the merge product of k_dc_gemm, whose row tiles skip the kept columns supported on the other
+  child only, against the full product.
 """
 import struct
 
@@ -192,3 +194,43 @@ def test_deflation_scan_and_rotation_application(seed):
     np.testing.assert_array_equal(ref[1], got[1])
     Q = rng.normal(size=(K, K))
     np.testing.assert_allclose(apply_grouped(Q, ref[3]), apply_sequential(Q, ref[3]), rtol=0, atol=1e-13)
+
+
+# ---- divide & conquer merge product (k_dc_gemm with the support grouping of k_dc_prep)
+@pytest.mark.parametrize("seed", range(6))
+def test_merge_product_skips_only_zero_blocks(seed):
+    """The child eigenvector matrix of a merge is block diagonal; columns mixed by a deflation
+    rotation have both supports.  Kept columns are ordered child-1-only, mixed, child-2-only (gperm,
+    counts g1, g2); a 32-row tile inside child 1 sums over [0, g1 + g2), inside child 2 over
+    [g1, Kp), a straddling tile over all -- the same product as the full sum."""
+    rng = np.random.default_rng(200 + seed)
+    K = int(rng.integers(40, 130))
+    n1 = K // 2
+    Q = np.zeros((K, K))
+    Q[:n1, :n1] = rng.normal(size=(n1, n1))
+    Q[n1:, n1:] = rng.normal(size=(K - n1, K - n1))
+    typ = np.array([1] * n1 + [3] * (K - n1))
+    for _ in range(int(rng.integers(0, 6))):                  # a few mixing rotations
+        a, b = int(rng.integers(0, n1)), int(rng.integers(n1, K))
+        c, s = np.cos(0.3), np.sin(0.3)
+        qa, qb = Q[:, a].copy(), Q[:, b].copy()
+        Q[:, a], Q[:, b] = c * qa + s * qb, -s * qa + c * qb
+        typ[a] = typ[b] = 2
+    keep = np.sort(rng.choice(K, size=int(0.8 * K), replace=False))  # kept columns (pole order)
+    Kp = len(keep)
+    U = rng.normal(size=(Kp, Kp))
+    gperm = [q for t in (1, 2, 3) for q in range(Kp) if typ[keep[q]] == t]
+    g1 = sum(typ[keep[q]] == 1 for q in range(Kp))
+    g2 = sum(typ[keep[q]] == 2 for q in range(Kp))
+    full = Q[:, keep] @ U
+    out = np.zeros_like(full)
+    for r0 in range(0, K, 32):
+        rows = slice(r0, min(K, r0 + 32))
+        kb, ke = 0, Kp
+        if r0 + 32 <= n1:
+            ke = g1 + g2
+        elif r0 >= n1:
+            kb = g1
+        idx = gperm[kb:ke]
+        out[rows] = Q[rows][:, keep[idx]] @ U[idx]
+    np.testing.assert_allclose(out, full, rtol=1e-12, atol=1e-12 * np.abs(full).max())
