@@ -216,3 +216,38 @@ def test_smoother_kernel_products_follow_the_recursion():
         KWs = KWfull if U is None else KWfull @ U
         assert rel(KWs, model.K_times(Ws)) < 1e-11
         assert rel(Kws, model.K_times(ws)) < 1e-11
+
+
+def test_cg_policy_is_krylov_galerkin_and_rtol_stops_at_the_first_small_residual():
+    """With the CG policy (action = current residual) the actions span the Krylov space
+    K_j(G, r0), so the update's coefficient vector after j actions is the Galerkin solution of
+    G v = r0 on that space (the exact conjugate-gradient iterate) and the filter mean is
+    m^- + K(X, X_o) v_j; with cg_rtol the step stops at the first j whose residual norm is at most
+    cg_rtol ||r0|| (reading R2).  Reference: an orthonormal Krylov basis built with full
+    re-orthogonalisation and the projected solve (textbook CG recurrences lose orthogonality after
+    a dozen iterations here and would not be an FP64 reference)."""
+    w = synth.small(n=80, dim=2, m=24, T=1, budget_i=24, rank_r=0, seed=52)
+    model = oc.model_from(w)
+    obs = w.obs(1)
+    G = model.K_times(np.eye(len(obs)), rows=obs, cols=obs) + model.sn2 * np.eye(len(obs))
+    mp = model.a * model.m0()
+    r0 = w.yk(1) - mp[obs]
+    r0n = np.linalg.norm(r0)
+    Q = np.zeros((len(obs), 0))
+    q = r0 / r0n
+    xs, norms = [np.zeros_like(r0)], [r0n]
+    for _ in range(len(obs) - 4):
+        Q = np.concatenate([Q, q[:, None]], axis=1)
+        x = Q @ np.linalg.solve(Q.T @ G @ Q, Q.T @ r0)
+        xs.append(x)
+        norms.append(np.linalg.norm(r0 - G @ x))
+        z = G @ q
+        for _ in range(2):
+            z = z - Q @ (Q.T @ z)
+        q = z / np.linalg.norm(z)
+    for rtol in (1e-1, 1e-3):
+        j = next(k for k, nr in enumerate(norms) if nr <= rtol * r0n)
+        f = oracle.filter_run(w, cg_rtol=rtol)
+        assert f.iters[1] == j, (rtol, f.iters[1], j)
+        want = mp + model.K_times(xs[j], cols=obs)
+        assert rel(f.m[1], want) < 1e-9
