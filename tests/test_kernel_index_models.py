@@ -12,7 +12,9 @@
   components, and the grouped, register-carried rotation application of k_dc_rot against applying
   the rotations one by one;
 * the merge product of k_dc_gemm, whose row tiles skip the kept columns supported on the other
-  child only, against the full product.
+  child only, against the full product;
+* the stream-K partition of the tcgen05 Gram x block over (row tile, K slice) units: a tile is
+  shared by at most two CTAs, so its atomic accumulation onto zeros is order-independent.
 """
 import struct
 
@@ -234,3 +236,22 @@ def test_merge_product_skips_only_zero_blocks(seed):
         idx = gperm[kb:ke]
         out[rows] = Q[rows][:, keep[idx]] @ U[idx]
     np.testing.assert_allclose(out, full, rtol=1e-12, atol=1e-12 * np.abs(full).max())
+
+
+# ---- tcgen05 Gram x block: stream-K partition of (row tile, K slice) units (gram_tc launch)
+@pytest.mark.parametrize("ntiles,nk,slots", [(1, 2048, 152), (3, 7, 152), (512, 256, 152), (152, 1, 152),
+                                             (153, 5, 152), (2048, 33, 304), (600, 1, 152)])
+def test_stream_k_splits_a_tile_over_at_most_two_ctas(ntiles, nk, slots):
+    """grid = min(#tiles, resident slots); CTA b takes units [total b / grid, total (b+1) / grid).
+    Every range then holds at least one tile's worth of units, so a tile is shared by at most two
+    CTAs -- its two partial sums added with atomics onto zeros are order-independent."""
+    grid = min(ntiles, slots)
+    total = ntiles * nk
+    owners = [set() for _ in range(ntiles)]
+    for b in range(grid):
+        u0, u1 = total * b // grid, total * (b + 1) // grid
+        assert u1 - u0 >= nk
+        for u in range(u0, u1):
+            owners[u // nk].add(b)
+    assert max(len(o) for o in owners) <= 2
+    assert set().union(*owners) == set(range(grid))
