@@ -14,7 +14,9 @@
 * the merge product of k_dc_gemm, whose row tiles skip the kept columns supported on the other
   child only, against the full product;
 * the stream-K partition of the tcgen05 Gram x block over (row tile, K slice) units: a tile is
-  shared by at most two CTAs, so its atomic accumulation onto zeros is order-independent.
+  shared by at most two CTAs, so its atomic accumulation onto zeros is order-independent;
+* the split-FP16 operands (hi + lo parts, B columns scaled by a power of two, three exact products
+  per pair) against exact products: about 22 significant bits (one FP16 part alone: ~11).
 """
 import struct
 
@@ -255,3 +257,32 @@ def test_stream_k_splits_a_tile_over_at_most_two_ctas(ntiles, nk, slots):
             owners[u // nk].add(b)
     assert max(len(o) for o in owners) <= 2
     assert set().union(*owners) == set(range(grid))
+
+
+# ---- split-FP16 operands of the tcgen05 Gram x block (k_col_scale, k_pack_b, producers)
+def split16(x):
+    hi = x.astype(np.float16)
+    lo = (x - hi.astype(np.float32)).astype(np.float16)
+    return hi.astype(np.float32), lo.astype(np.float32)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_split_fp16_products_carry_about_22_bits(seed):
+    """Each kernel value k in (0, 1] and each B entry (column scaled by a power of two so that its
+    largest magnitude is in [0.5, 1)) is written as hi + lo FP16 parts; the three products
+    hi*hi + hi*lo + lo*hi are exact in FP32.  Against the exact product sum the error stays below
+    4 * 2^-22 of sum |k| |b| per output -- the split's ~22 significant bits."""
+    rng = np.random.default_rng(300 + seed)
+    rows, cols = 512, 8
+    k = np.exp(-rng.uniform(0, 8, size=rows)).astype(np.float32)            # correlations
+    B = (rng.normal(size=(rows, cols)) * 10.0 ** rng.uniform(-3, 3, size=cols)).astype(np.float32)
+    e = np.frexp(np.abs(B).max(axis=0))[1]
+    sc = np.ldexp(1.0, -e).astype(np.float32)                                 # k_col_scale
+    Bs = (B * sc).astype(np.float32)
+    kh, kl = split16(k)
+    bh, bl = split16(Bs)
+    approx = (kh[:, None].astype(np.float64) * bh + kh[:, None] * bl + kl[:, None] * bh).sum(axis=0)
+    approx = approx / sc                                                       # epilogue scale back
+    exact = (k.astype(np.float64)[:, None] * B.astype(np.float64)).sum(axis=0)
+    scale = (np.abs(k.astype(np.float64))[:, None] * np.abs(B.astype(np.float64))).sum(axis=0)
+    assert np.all(np.abs(approx - exact) <= 4 * 2.0 ** -22 * scale)
