@@ -16,7 +16,9 @@
 * the stream-K partition of the tcgen05 Gram x block over (row tile, K slice) units: a tile is
   shared by at most two CTAs, so its atomic accumulation onto zeros is order-independent;
 * the split-FP16 operands (hi + lo parts, B columns scaled by a power of two, three exact products
-  per pair) against exact products: about 22 significant bits (one FP16 part alone: ~11).
+  per pair) against exact products: about 22 significant bits (one FP16 part alone: ~11);
+* the compensated FP32 row sums of squares (row_sumsq) against exact sums, and the epoch tag of
+  the tridiagonalisation's exchange words (at most 3 ulps of change).
 """
 import struct
 
@@ -286,3 +288,43 @@ def test_split_fp16_products_carry_about_22_bits(seed):
     exact = (k.astype(np.float64)[:, None] * B.astype(np.float64)).sum(axis=0)
     scale = (np.abs(k.astype(np.float64))[:, None] * np.abs(B.astype(np.float64))).sum(axis=0)
     assert np.all(np.abs(approx - exact) <= 4 * 2.0 ** -22 * scale)
+
+
+# ---- compensated FP32 row sums of squares (row_sumsq) and the epoch tag of the exchange words
+def kahan4(v):
+    """row_sumsq for FP32 data: four compensated FP32 sums over interleaved columns, combined in FP64."""
+    s = np.zeros(4, dtype=np.float32)
+    e = np.zeros(4, dtype=np.float32)
+    n4 = len(v) - len(v) % 4
+    for c in range(0, n4, 4):
+        for u in range(4):
+            x = np.float32(v[c + u])
+            y = np.float32(np.float32(x * x) - e[u])     # the kernel fuses x*x - e in one fma
+            t = np.float32(s[u] + y)
+            e[u] = np.float32(np.float32(t - s[u]) - y)
+            s[u] = t
+    for c in range(n4, len(v)):
+        x = np.float32(v[c])
+        y = np.float32(np.float32(x * x) - e[0])
+        t = np.float32(s[0] + y)
+        e[0] = np.float32(np.float32(t - s[0]) - y)
+        s[0] = t
+    return float(np.sum(s.astype(np.float64) - e.astype(np.float64)))
+
+
+def test_compensated_row_sums_keep_fp32_accuracy():
+    rng = np.random.default_rng(5)
+    for cols in (3, 64, 511, 2048):
+        v = (rng.normal(size=cols) * np.exp(rng.normal(size=cols))).astype(np.float32)
+        exact = float(np.sum(v.astype(np.float64) ** 2))
+        assert abs(kahan4(v) - exact) <= 4 * 2.0 ** -24 * exact
+
+
+def test_epoch_tag_changes_a_word_by_at_most_three_ulps():
+    rng = np.random.default_rng(6)
+    x = rng.normal(size=1000) * 10.0 ** rng.integers(-200, 200, 1000)
+    bits = x.view(np.int64)
+    for ep in range(4):
+        tagged = ((bits & ~np.int64(3)) | np.int64(ep)).view(np.float64)
+        assert np.all(np.abs(tagged - x) <= 3 * np.spacing(np.abs(x)))
+        assert np.all((tagged.view(np.int64) & 3) == ep)
