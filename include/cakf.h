@@ -26,6 +26,10 @@
  *              stream).  Calls return once their results are in the output arrays.
  *   Errors     every call returns a cakf_status; nothing aborts or throws across the ABI.
  *              cakf_last_error() gives a message for the calling thread's last failure.
+ *              Device pointers must belong to the current device (CAKF_ERR_ARG otherwise).
+ *              cakf_smooth, cakf_nll, cakf_nll_backward and cakf_get_actions on a NULL context
+ *              (none created yet) or on one without a successful cakf_filter: CAKF_ERR_STATE.
+ *              A cakf_filter rejected by argument validation leaves its context untouched.
  *   Threads    a cakf_ctx may be used by one thread at a time.
  */
 #ifndef CAKF_H
@@ -208,8 +212,11 @@ int cakf_gram_matmul(int32_t kernel, double log_lx, double log_sf2, int32_t dim,
  * allocator, a pool sized at start-up) already holds almost all device memory; a caller in a
  * latency-bound loop, or one working inside a fixed memory plan, cannot accept either.  This
  * entry point performs no device allocation of its own: its scratch is one statically sized
- * device array of the library, CAKF_NOALLOC_SCRATCH_BYTES per device, reserved when the
- * library's module is loaded on that device.
+ * device array of the library, CAKF_NOALLOC_SCRATCH_BYTES per device.  The CUDA runtime loads the
+ * module that holds it lazily, so the array is reserved on a device by the first call of this
+ * entry point there (and kept until the process exits); make that first call during set-up,
+ * before a memory pool takes the rest of the device: if the reservation fails it returns
+ * CAKF_ERR_OOM.
  *
  * Limit: the scratch must hold 256 bytes + (nr + nc) coordinate records (32 bytes each for
  * CAKF_FP64, 16 otherwise, rounded up to 256) and, for CAKF_BF16, the packed operand
@@ -225,7 +232,10 @@ int cakf_gram_matmul(int32_t kernel, double log_lx, double log_sf2, int32_t dim,
  * Setup: the first call on a device looks up the scratch address (cudaGetSymbolAddress, with
  * that device current) and sets kernel attributes; make that first call before any stream
  * capture begins on the device.
- * Errors: as cakf_gram_matmul, with CAKF_ERR_ARG also for calls exceeding the scratch.
+ * Arrays: Xr, Xc, B and Out must be device memory of the current device (CAKF_ERR_ARG otherwise);
+ * their sizes cannot be checked here, so Xr must hold nr * dim and Xc nc * dim doubles.
+ * Errors: as cakf_gram_matmul, with CAKF_ERR_ARG also for calls exceeding the scratch and
+ * CAKF_ERR_OOM when the first call on a device cannot reserve the scratch.
  */
 #define CAKF_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
 int cakf_gram_matmul_noalloc(int32_t kernel, double log_lx, double log_sf2, int32_t dim, const double* Xr,

@@ -267,45 +267,84 @@ def cakf_get_stats(ctx: Context) -> dict:
     return out
 
 
+def _gram_args(name, Xr, Xc, B, out, dt):
+    """Shape, dtype and device checks shared by the two Gram x matrix wrappers (raise ValueError
+    before anything reaches the library): Xr (nr, dim) and Xc (nc, dim) float64 with 1 <= dim <= 3,
+    B (width, nc) and out (width, nr) of the precision's element type, all contiguous CUDA tensors
+    on the current device.  Returns (nr, nc, dim, width)."""
+    import torch
+    tensors = (("Xr", Xr, torch.float64), ("Xc", Xc, torch.float64), ("B", B, dt), ("out", out, dt))
+    for nm, t, want in tensors:
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"{name}: {nm} must be a torch tensor")
+        if t.dtype != want or not t.is_contiguous():
+            raise ValueError(f"{name}: {nm} must be a contiguous {want} tensor")
+    if Xr.dim() != 2 or Xc.dim() != 2 or B.dim() != 2 or out.dim() != 2:
+        raise ValueError(f"{name}: Xr, Xc, B and out must be 2-D")
+    nr, dim = Xr.shape
+    nc = Xc.shape[0]
+    width = B.shape[0]
+    if not 1 <= dim <= 3 or Xc.shape[1] != dim:
+        raise ValueError(f"{name}: Xr must be (nr, dim) and Xc (nc, dim) with the same dim in 1..3")
+    if nr < 1 or nc < 1 or width < 1:
+        raise ValueError(f"{name}: empty operand")
+    if tuple(B.shape) != (width, nc):
+        raise ValueError(f"{name}: B must have shape (width, nc) = ({width}, {nc})")
+    if tuple(out.shape) != (width, nr):
+        raise ValueError(f"{name}: out must have shape (width, nr) = ({width}, {nr})")
+    dev = Xr.device
+    if dev.type != "cuda":
+        raise ValueError(f"{name}: the operands must be CUDA tensors")
+    if dev.index != torch.cuda.current_device():
+        raise ValueError(f"{name}: the operands must be on the current CUDA device")
+    for nm, t, _ in tensors:
+        if t.device != dev:
+            raise ValueError(f"{name}: {nm} is on {t.device}, Xr on {dev}")
+    return nr, nc, dim, width
+
+
+def _stream_of(stream, dev):
+    """The caller's stream handle, or torch's current stream on dev (so that the call is ordered
+    after the work that produced its inputs)."""
+    if stream is not None:
+        return stream
+    import torch
+    return torch.cuda.current_stream(dev).cuda_stream
+
+
 def cakf_gram_matmul(kernel, log_lx, log_sf2, Xr, Xc, B, out=None, precision="fp32", stream=None):
     """Out = K(Xr, Xc) B on the device (torch CUDA tensors; B and Out column-major, i.e. stored as
-    (width, rows) row-major tensors).  Returns Out with shape (width, nr)."""
+    (width, rows) row-major tensors).  Xr, Xc are converted to contiguous float64 and B to the
+    precision's element type.  Runs on `stream` (a cudaStream_t handle), by default torch's current
+    stream.  Returns Out with shape (width, nr)."""
     import torch
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     dt = torch.float64 if prec == FP64 else torch.float32
     Xr = Xr.to(torch.float64).contiguous()
     Xc = Xc.to(torch.float64).contiguous()
     B = B.to(dt).contiguous()
-    width, nc = B.shape
-    nr = Xr.shape[0]
-    dim = Xr.shape[1] if Xr.dim() > 1 else 1
     if out is None:
-        out = torch.empty((width, nr), dtype=dt, device=Xr.device)
+        out = torch.empty((B.shape[0], Xr.shape[0]), dtype=dt, device=Xr.device)
+    nr, nc, dim, width = _gram_args("cakf_gram_matmul", Xr, Xc, B, out, dt)
     _check(lib().cakf_gram_matmul(int(kernel), float(log_lx), float(log_sf2), int(dim), Xr.data_ptr(), int(nr),
                                   Xc.data_ptr(), int(nc), B.data_ptr(), int(nc), int(width), out.data_ptr(), int(nr),
-                                  prec, stream))
+                                  prec, _stream_of(stream, Xr.device)))
     return out
 
 
 def cakf_gram_matmul_noalloc(kernel, log_lx, log_sf2, Xr, Xc, B, out, precision="fp32", stream=None):
     """cakf_gram_matmul into a caller-provided `out`, with no device allocation by the library or
-    by this binding: Xr, Xc must be contiguous float64 CUDA tensors, B and out contiguous CUDA
-    tensors of the precision's element type (float64 for fp64, float32 otherwise), B of shape
-    (width, nc) and out of shape (width, nr) (column-major blocks).  Returns out."""
+    by this binding: Xr, Xc must be contiguous float64 CUDA tensors of shapes (nr, dim), (nc, dim),
+    B and out contiguous CUDA tensors of the precision's element type (float64 for fp64, float32
+    otherwise) of shapes (width, nc) and (width, nr) (column-major blocks), all on the current
+    device.  Runs on `stream`, by default torch's current stream.  Returns out."""
     import torch
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     dt = torch.float64 if prec == FP64 else torch.float32
-    for name, t, want in (("Xr", Xr, torch.float64), ("Xc", Xc, torch.float64), ("B", B, dt), ("out", out, dt)):
-        if t.dtype != want or not t.is_contiguous():
-            raise ValueError(f"cakf_gram_matmul_noalloc: {name} must be a contiguous {want} tensor")
-    width, nc = B.shape
-    nr = Xr.shape[0]
-    dim = Xr.shape[1] if Xr.dim() > 1 else 1
-    if tuple(out.shape) != (width, nr):
-        raise ValueError("cakf_gram_matmul_noalloc: out must have shape (width, nr)")
+    nr, nc, dim, width = _gram_args("cakf_gram_matmul_noalloc", Xr, Xc, B, out, dt)
     _check(lib().cakf_gram_matmul_noalloc(int(kernel), float(log_lx), float(log_sf2), int(dim), Xr.data_ptr(),
                                           int(nr), Xc.data_ptr(), int(nc), B.data_ptr(), int(nc), int(width),
-                                          out.data_ptr(), int(nr), prec, stream))
+                                          out.data_ptr(), int(nr), prec, _stream_of(stream, Xr.device)))
     return out
 
 

@@ -29,12 +29,21 @@ int fail(int code, const std::string& msg) {
   return code;
 }
 
-bool is_device_ptr(const void* p) {
-  if (!p) return false;
+// Where a caller's pointer lives: host memory (pageable or pinned), device memory of the current
+// device, or device memory of another device (which the kernels here must not be given).
+enum PtrKind { kHost = 0, kDevice = 1, kOtherDevice = 2 };
+
+PtrKind ptr_kind(const void* p) {
+  if (!p) return kHost;
   cudaPointerAttributes at;
-  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) { cudaGetLastError(); return false; }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) { cudaGetLastError(); return kHost; }
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return kHost;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return kOtherDevice; }
+  return (at.type == cudaMemoryTypeManaged || at.device == dev) ? kDevice : kOtherDevice;
 }
+
+bool is_device_ptr(const void* p) { return ptr_kind(p) == kDevice; }
 
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
@@ -341,14 +350,18 @@ int plan_and_alloc(cakf_ctx* c, const cakf_problem* p) {
 
 int copy_in(void* dst, const void* src, size_t bytes, cudaStream_t st) {
   if (bytes == 0) return CAKF_OK;
-  cudaError_t ce = cudaMemcpyAsync(dst, src, bytes, is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+  const PtrKind kind = ptr_kind(src);
+  if (kind == kOtherDevice) return fail(CAKF_ERR_ARG, "an input array lives on another device than the current one");
+  cudaError_t ce = cudaMemcpyAsync(dst, src, bytes, kind == kDevice ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
   return ce == cudaSuccess ? CAKF_OK : fail(CAKF_ERR_CUDA, std::string("copy in: ") + cudaGetErrorString(ce));
 }
 
 int copy_out(double* dst, const double* src, size_t elems, cudaStream_t st) {
   if (!dst || elems == 0) return CAKF_OK;
+  const PtrKind kind = ptr_kind(dst);
+  if (kind == kOtherDevice) return fail(CAKF_ERR_ARG, "an output array lives on another device than the current one");
   cudaError_t ce = cudaMemcpyAsync(dst, src, elems * sizeof(double),
-                                   is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
+                                   kind == kDevice ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
   return ce == cudaSuccess ? CAKF_OK : fail(CAKF_ERR_CUDA, std::string("copy out: ") + cudaGetErrorString(ce));
 }
 
@@ -1168,11 +1181,13 @@ int cakf_filter(const cakf_problem* p, cakf_ctx** ctx_inout, double* mean_out, d
 }
 
 int cakf_smooth(cakf_ctx* c, double* mean_out, double* var_out, void* cuda_stream) {
-  if (!c) return fail(CAKF_ERR_ARG, "ctx is NULL");
+  if (!c) return fail(CAKF_ERR_STATE, "cakf_smooth: no context (cakf_filter creates it)");
   if (!c->filtered) return fail(CAKF_ERR_STATE, "cakf_smooth needs a successful cakf_filter on this context");
   cudaStream_t st = (cudaStream_t)cuda_stream;
   const size_t tot = (size_t)(c->T + 1) * c->n;
   int rc;
+  if (ptr_kind(mean_out) == kOtherDevice || ptr_kind(var_out) == kOtherDevice)
+    return fail(CAKF_ERR_ARG, "cakf_smooth: an output array lives on another device than the current one");
   double* ms = is_device_ptr(mean_out) ? mean_out : nullptr;
   double* vs = is_device_ptr(var_out) ? var_out : nullptr;
   if (!ms || !vs) {
@@ -1208,7 +1223,8 @@ int cakf_smooth(cakf_ctx* c, double* mean_out, double* var_out, void* cuda_strea
 }
 
 int cakf_nll(cakf_ctx* c, double* nll_out) {
-  if (!c || !nll_out) return fail(CAKF_ERR_ARG, "NULL argument");
+  if (!nll_out) return fail(CAKF_ERR_ARG, "cakf_nll: nll_out is NULL");
+  if (!c) return fail(CAKF_ERR_STATE, "cakf_nll: no context (cakf_filter creates it)");
   if (!c->filtered) return fail(CAKF_ERR_STATE, "cakf_nll needs a successful cakf_filter on this context");
   std::vector<double> v(c->T + 1);
   if (cudaMemcpy(v.data(), c->nll, (c->T + 1) * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
@@ -1220,7 +1236,8 @@ int cakf_nll(cakf_ctx* c, double* nll_out) {
 }
 
 int cakf_get_actions(cakf_ctx* c, double* actions_out, int32_t* counts_out) {
-  if (!c || !counts_out) return fail(CAKF_ERR_ARG, "NULL argument");
+  if (!counts_out) return fail(CAKF_ERR_ARG, "cakf_get_actions: counts_out is NULL");
+  if (!c) return fail(CAKF_ERR_STATE, "cakf_get_actions: no context (cakf_filter creates it)");
   if (!c->filtered) return fail(CAKF_ERR_STATE, "no filter run on this context");
   std::vector<int> cnt(c->T + 1);
   cudaMemcpy(cnt.data(), c->count, (c->T + 1) * sizeof(int), cudaMemcpyDeviceToHost);
@@ -1301,7 +1318,7 @@ extern "C" int cakf_gram_matmul(int32_t kernel, double log_lx, double log_sf2, i
     return fail(CAKF_ERR_ARG, "cakf_gram_matmul: invalid sizes or kernel");
   if (!Xr || !Xc || !B || !Out) return fail(CAKF_ERR_ARG, "cakf_gram_matmul: NULL pointer");
   if (!is_device_ptr(Xr) || !is_device_ptr(Xc) || !is_device_ptr(B) || !is_device_ptr(Out))
-    return fail(CAKF_ERR_ARG, "cakf_gram_matmul: all arrays must be device arrays");
+    return fail(CAKF_ERR_ARG, "cakf_gram_matmul: all arrays must be device arrays of the current device");
   if (precision != CAKF_FP64 && precision != CAKF_FP32 && precision != CAKF_BF16 && precision != CAKF_FP16X3)
     return fail(CAKF_ERR_ARG, "cakf_gram_matmul: precision must be FP64, FP32, BF16 or FP16X3");
   const bool tcp = precision == CAKF_BF16 || precision == CAKF_FP16X3;
@@ -1354,7 +1371,7 @@ extern "C" int cakf_gram_matmul(int32_t kernel, double log_lx, double log_sf2, i
 extern "C" int cakf_eig_topk(const double* A, int32_t N, int32_t keep, double* w_out, double* U_out, void* cuda_stream) {
   if (!A || !w_out || !U_out || N < 1 || keep < 1 || keep > N) return fail(CAKF_ERR_ARG, "cakf_eig_topk: invalid arguments");
   if (!is_device_ptr(A) || !is_device_ptr(w_out) || !is_device_ptr(U_out))
-    return fail(CAKF_ERR_ARG, "cakf_eig_topk: all arrays must be device arrays");
+    return fail(CAKF_ERR_ARG, "cakf_eig_topk: all arrays must be device arrays of the current device");
   cudaStream_t st = (cudaStream_t)cuda_stream;
   const size_t wb = eig_workspace_bytes(N);
   double* Aw = nullptr;
@@ -1382,7 +1399,8 @@ extern "C" int cakf_eig_topk(const double* A, int32_t N, int32_t keep, double* w
 }
 
 extern "C" int cakf_nll_backward(cakf_ctx* c, double* grad_out) {
-  if (!c || !grad_out) return fail(CAKF_ERR_ARG, "NULL argument");
+  if (!grad_out) return fail(CAKF_ERR_ARG, "cakf_nll_backward: grad_out is NULL");
+  if (!c) return fail(CAKF_ERR_STATE, "cakf_nll_backward: no context (cakf_filter creates it)");
   if (!c->filtered) return fail(CAKF_ERR_STATE, "cakf_nll_backward needs a successful cakf_filter on this context");
   cudaStream_t st = nullptr;
   int rc;

@@ -32,10 +32,16 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 double nu_scale_of(int kernel) { return kernel == 0 ? 1.0 : (kernel == 1 ? std::sqrt(3.0) : std::sqrt(5.0)); }
 
+// True when p is device (or managed) memory of the current device: the kernels launched here run
+// on the current device and must not be handed another device's allocation.
 bool on_device(const void* p) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) { cudaGetLastError(); return false; }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (at.type == cudaMemoryTypeManaged) return true;
+  if (at.type != cudaMemoryTypeDevice) return false;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return false; }
+  return at.device == dev;
 }
 
 int err(int code, const std::string& msg) { return set_last_error(code, msg.c_str()); }
@@ -50,11 +56,13 @@ int scratch_base(void** out) {
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_base[dev]) {
     void* p = nullptr;
+    // The first lookup on a device loads this module there, which reserves the static scratch:
+    // next to a full memory pool that can fail with cudaErrorMemoryAllocation.
     ce = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (ce != cudaSuccess || !p) {
       cudaGetLastError();
-      return err(CAKF_ERR_CUDA, std::string("cakf_gram_matmul_noalloc: cudaGetSymbolAddress failed: ") +
-                                    cudaGetErrorString(ce));
+      return err(ce == cudaErrorMemoryAllocation ? CAKF_ERR_OOM : CAKF_ERR_CUDA,
+                 std::string("cakf_gram_matmul_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(ce));
     }
     g_base[dev] = p;
   }
@@ -89,7 +97,7 @@ extern "C" int cakf_gram_matmul_noalloc(int32_t kernel, double log_lx, double lo
                                  " bytes of scratch but the static scratch holds " + std::to_string(kScratchBytes) +
                                  " bytes; use cakf_gram_matmul, or split the rows / columns into smaller calls");
   if (!on_device(Xr) || !on_device(Xc) || !on_device(B) || !on_device(Out))
-    return err(CAKF_ERR_ARG, "cakf_gram_matmul_noalloc: all arrays must be device arrays");
+    return err(CAKF_ERR_ARG, "cakf_gram_matmul_noalloc: all arrays must be device arrays of the current device");
 
   void* base = nullptr;
   int rc = scratch_base(&base);

@@ -69,4 +69,35 @@ def test_argument_validation_on_host(lib):
     assert ei.value.code == b.ERR_ARG
     with pytest.raises(b.CakfError) as ei:
         b.cakf_smooth(ctx)
-    assert ei.value.code == b.ERR_ARG   # no context yet
+    assert ei.value.code == b.ERR_STATE   # no filter has created a context yet
+    for call in (b.cakf_nll, b.cakf_nll_backward):
+        with pytest.raises(b.CakfError) as ei:
+            call(ctx)
+        assert ei.value.code == b.ERR_STATE
+
+
+def test_gram_wrappers_check_shapes_before_any_launch():
+    """The Gram x matrix wrappers reject operands whose shapes disagree (a shorter or narrower Xc
+    would make the library read past it) and operands off the current CUDA device, with ValueError,
+    before the library is called."""
+    torch = pytest.importorskip("torch")
+    from paper_2405_08971_gb300 import binding as b
+    f64, f32 = torch.float64, torch.float32
+    Xr = torch.zeros((10, 2), dtype=f64)
+    good = dict(Xc=torch.zeros((7, 2), dtype=f64), B=torch.zeros((3, 7), dtype=f32), out=torch.zeros((3, 10), dtype=f32))
+    bad = [dict(good, Xc=torch.zeros((6, 2), dtype=f64)),       # B has 7 rows per column
+           dict(good, Xc=torch.zeros((7, 1), dtype=f64)),       # narrower than Xr
+           dict(good, Xc=torch.zeros((7, 4), dtype=f64)),       # dim 4
+           dict(good, B=torch.zeros((3, 8), dtype=f32)),
+           dict(good, out=torch.zeros((3, 9), dtype=f32)),
+           dict(good, out=torch.zeros((4, 10), dtype=f32)),
+           dict(good, B=torch.zeros((3, 7), dtype=f64))]       # wrong element type for fp32
+    for case in bad:
+        with pytest.raises(ValueError):
+            b.cakf_gram_matmul_noalloc(1, 0.0, 0.0, Xr, case["Xc"], case["B"], case["out"], precision="fp32")
+        if case["B"].dtype == f32:   # cakf_gram_matmul converts B to the element type first
+            with pytest.raises(ValueError):
+                b.cakf_gram_matmul(1, 0.0, 0.0, Xr, case["Xc"], case["B"], out=case["out"], precision="fp32")
+    # well-formed host tensors are still refused: the library works on the current CUDA device
+    with pytest.raises(ValueError, match="CUDA"):
+        b.cakf_gram_matmul_noalloc(1, 0.0, 0.0, Xr, good["Xc"], good["B"], good["out"], precision="fp32")

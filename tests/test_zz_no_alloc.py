@@ -21,7 +21,7 @@ if not torch.cuda.is_available():
 import paper_2405_08971_gb300 as ck  # noqa: E402
 
 SCRATCH = 64 << 20
-TOL = {"fp64": 1e-13, "fp32": 1e-6, "bf16": 1e-6}
+TOL = {"fp64": 1e-13, "fp32": 1e-6, "bf16": 1e-6, "fp16x3": 1e-6}
 
 
 def inputs(nr, nc, width, dim, precision, seed):
@@ -43,6 +43,8 @@ def rel(a, b):
 CASES = [
     (1000, 777, 2, 2, 1, "fp64"), (513, 1000, 65, 1, 0, "fp32"), (300, 257, 17, 3, 2, "bf16"),
     (384, 300, 513, 2, 1, "bf16"), (4096, 32768, 513, 3, 1, "bf16"), (2000, 65536, 257, 2, 1, "bf16"),
+    # split FP16: two packed operand parts plus the per-column scales in the staging area
+    (700, 1000, 33, 2, 1, "fp16x3"), (4096, 32768, 257, 3, 1, "fp16x3"),
 ]
 
 
@@ -60,11 +62,13 @@ def test_noalloc_matches_allocating_entry_point(nr, nc, width, dim, kernel, prec
     assert e2 <= TOL[precision], e2
 
 
-def test_noalloc_rejects_calls_beyond_the_scratch():
-    """BF16 with nc = 65536 and width 513 needs the packed operand (64 MiB) plus coordinates."""
-    Xr, Xc, B, (out, _, _) = inputs(256, 65536, 513, 2, "bf16", seed=7)
+@pytest.mark.parametrize("nc,width,precision", [(65536, 513, "bf16"), (32768, 513, "fp16x3")])
+def test_noalloc_rejects_calls_beyond_the_scratch(nc, width, precision):
+    """BF16 with nc = 65536 and width 513 needs the packed operand (64 MiB) plus coordinates; split
+    FP16 needs twice the operand bytes, so nc = 32768 at width 513 is over the limit as well."""
+    Xr, Xc, B, (out, _, _) = inputs(256, nc, width, 2, precision, seed=7)
     with pytest.raises(ck.CakfError) as ei:
-        ck.cakf_gram_matmul_noalloc(1, 0.0, 0.0, Xr, Xc, B, out, precision="bf16")
+        ck.cakf_gram_matmul_noalloc(1, 0.0, 0.0, Xr, Xc, B, out, precision=precision)
     assert ei.value.code == ck.binding.ERR_ARG
     assert "bytes of scratch" in str(ei.value) and str(SCRATCH) in str(ei.value)
     assert torch.isnan(out).all()          # rejected before any device work
