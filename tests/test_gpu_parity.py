@@ -164,7 +164,7 @@ def test_state_errors():
     ctx = ck.Context()
     with pytest.raises(ck.CakfError) as ei:
         ck.cakf_nll(ctx)
-    assert ei.value.code == ck.binding.ERR_ARG
+    assert ei.value.code == ck.binding.ERR_STATE
     w = CASES["missing-steps-m12"]()
     prob = ck.problem_from_workload(w, precision="fp32")
     ctx, _, _ = ck.cakf_filter(prob, ctx)
