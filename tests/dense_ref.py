@@ -211,3 +211,79 @@ def dense_truncated(w, S_list, r):
         ws = ww[k] + B @ ws
         Om = rank_r(Ww[k] + B @ Om @ B.T)
     return dict(mf=np.array(mf), vf=np.array([np.diag(p) for p in Pf]), ms=np.array(ms), vs=np.array(vs))
+
+
+def _chol_sym(A):
+    """Cholesky factor L (A = L L^T) of a symmetric matrix without conjugation: analytic in the
+    entries of A, so it can carry a complex-step perturbation."""
+    n = A.shape[0]
+    L = np.zeros_like(A)
+    for j in range(n):
+        L[j, j] = np.sqrt(A[j, j] - np.sum(L[j, :j] * L[j, :j]))
+        for i in range(j + 1, n):
+            L[i, j] = (A[i, j] - np.sum(L[i, :j] * L[j, :j])) / L[j, j]
+    return L
+
+
+def frozen_truncated_nll(w, S_list, U_list, theta):
+    """NLL of the projected data in the modified model with frozen actions S_k and frozen
+    truncation rotations U_k, at log-hyperparameters theta = (log l_x, log l_t, log sf2, log sn2).
+
+    Written with factors and the batch form of the update (V_k = S_k L_k^-T with
+    L_k L_k^T = S_k^T G_k S_k, the G-orthonormalisation of the actions): M^-_k = a M+_{k-1},
+    [P^-W_k, P^-w_k] = K[:, o] [V_k v_k] - M^-_k (M^-_k[o]^T [V_k v_k]), M_k = (M^-_k, P^-W_k),
+    M+_k = M_k U_k (U_k None: no truncation).  Every operation is analytic in theta (no
+    conjugation, no absolute values, no eigendecomposition), so theta may be complex: the
+    complex-step derivative Im f(theta + i h e_p) / h is then the exact gradient."""
+    lx, lt, sf2, sn2 = (np.exp(theta[0]), np.exp(theta[1]), np.exp(theta[2]), np.exp(theta[3]))
+    a = np.exp(-w.dt / lt)
+    X = w.coords
+    d = np.sqrt(((X[:, None, :] - X[None, :, :]) ** 2).sum(-1))
+    u = d / lx
+    if w.kernel == 0:
+        K = sf2 * np.exp(-u)
+    elif w.kernel == 1:
+        K = sf2 * (1 + math.sqrt(3) * u) * np.exp(-math.sqrt(3) * u)
+    else:
+        K = sf2 * (1 + math.sqrt(5) * u + 5 * u * u / 3) * np.exp(-math.sqrt(5) * u)
+    n = w.n
+    m = _mu(w, 0).astype(complex)
+    Mp = np.zeros((n, 0), dtype=complex)
+    nll = 0.0 + 0.0j
+    for k in range(1, w.T + 1):
+        mpk = a * m + (_mu(w, k) - a * _mu(w, k - 1))
+        Mm = a * Mp
+        o = w.obs(k)
+        Sk = S_list[k]
+        if len(o) == 0 or Sk.shape[1] == 0:
+            m, Mk = mpk, Mm
+        else:
+            Mo = Mm[o]
+            G = K[np.ix_(o, o)] - Mo @ Mo.T + sn2 * np.eye(len(o))
+            r0 = w.yk(k) - mpk[o]
+            L = _chol_sym(Sk.T @ G @ Sk)
+            V = np.linalg.solve(L, Sk.T).T                     # S L^-T
+            yh = Sk.T @ r0
+            z = np.linalg.solve(L, yh)
+            v = V @ z
+            Ls = _chol_sym((Sk.T @ Sk).astype(complex))
+            j = Sk.shape[1]
+            nll += 0.5 * j * math.log(2 * math.pi) + np.sum(np.log(np.diag(L))) + 0.5 * z @ z \
+                - np.sum(np.log(np.diag(Ls)))
+            Vv = np.concatenate([V, v[:, None]], axis=1)
+            PVv = K[:, o] @ Vv - Mm @ (Mo.T @ Vv)
+            m = mpk + PVv[:, -1]
+            Mk = np.concatenate([Mm, PVv[:, :-1]], axis=1)
+        Mp = Mk if U_list[k] is None else Mk @ U_list[k]
+    return nll
+
+
+def frozen_truncated_nll_grad(w, S_list, U_list, h=1e-30):
+    """Exact gradient of frozen_truncated_nll by the complex step (no subtraction, no h error)."""
+    th = np.array([w.log_lx, w.log_lt, w.log_sf2, w.log_sn2], dtype=complex)
+    g = np.zeros(4)
+    for p in range(4):
+        t = th.copy()
+        t[p] += 1j * h
+        g[p] = frozen_truncated_nll(w, S_list, U_list, t).imag / h
+    return float(frozen_truncated_nll(w, S_list, U_list, th).real), g

@@ -153,6 +153,48 @@ def test_fd_gradient_matches_batch_analytic():
     assert np.allclose(g_fd, g_an, rtol=1e-6, atol=1e-6 * np.max(np.abs(g_an)))
 
 
+def test_fd_gradient_with_truncation_matches_complex_step():
+    """The oracle's truncated NLL with frozen actions and rotations (the U_replay path of
+    filter_run), pinned by an independent factor-form implementation of the same modified model
+    (batch update V = S L^-T, frozen M+_k = M_k U_k) differentiated by the complex step: its NLL
+    at the base point equals the oracle's and its exact gradient equals the oracle's central FD.
+    Truncation is active (rank 5 < 3 columns per step accumulated over 4 steps), so a rotation
+    replayed at the wrong step changes the function and fails the comparison."""
+    w = synth.small(n=30, dim=2, m=9, T=4, budget_i=3, rank_r=5, seasonal=True, seed=23)
+    f = oracle.filter_run(w)
+    assert sum(u is not None for u in f.U) >= 2
+    nll0, g_fd = oracle.nll_grad_fd(w, h=1e-5)
+    nll_ref, g_cs = dense_ref.frozen_truncated_nll_grad(w, f.S, f.U)
+    assert abs(nll0 - nll_ref) <= 1e-10 * abs(nll_ref)
+    assert np.allclose(g_fd, g_cs, rtol=1e-6, atol=1e-7 * np.max(np.abs(g_cs))), (g_fd, g_cs)
+    # the rotation of the next step replayed in place of this one (same shape) is a different
+    # model: its gradient moves visibly (the last step's rotation feeds no NLL term, so a later
+    # step's is taken for an earlier one)
+    shifted = list(f.U)
+    for k in range(1, w.T):
+        if f.U[k] is not None and f.U[k + 1] is not None and f.U[k].shape == f.U[k + 1].shape:
+            shifted[k] = f.U[k + 1]
+            break
+    assert any(shifted[k] is not f.U[k] for k in range(1, w.T + 1))
+    _, g_bad = dense_ref.frozen_truncated_nll_grad(w, f.S, shifted)
+    assert not np.allclose(g_bad, g_cs, rtol=1e-4)
+
+
+def test_breakdown_exit_stops_at_a_repeated_action():
+    """A replayed action that repeats an earlier one has d = (I - V V^T G) s = 0, so eta falls
+    below 1e-12 s^T G s: the update stops there (R2), keeps only the actions before it, and the
+    result equals the run given just those actions."""
+    w = synth.small(n=40, dim=2, m=12, T=2, budget_i=4, rank_r=0, seed=29)
+    base = oracle.filter_run(w)
+    s1, s2 = base.S[1][:, 0], base.S[1][:, 1]
+    rep = [None, np.stack([s1, s2, s1, base.S[1][:, 2]], axis=1), base.S[2]]
+    f = oracle.filter_run(w, S_replay=rep)
+    assert f.iters[1] == 2 and f.iters[2] == base.S[2].shape[1]
+    g = oracle.filter_run(w, S_replay=[None, np.stack([s1, s2], axis=1), base.S[2]])
+    assert np.array_equal(f.m, g.m) and np.array_equal(f.var, g.var)
+    assert f.nll[1] == g.nll[1]
+
+
 def test_matern_against_sklearn():
     sk = pytest.importorskip("sklearn.gaussian_process.kernels")
     rng = np.random.default_rng(0)
