@@ -51,7 +51,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32-compare", action="store_true",
                     help="skip the plain-FP32 comparison pass (one untimed + one timed pass at fp32)")
-    ap.add_argument("--cpu-sample-steps", type=int, default=1)
+    ap.add_argument("--cpu-row-frac", type=int, default=16,
+                    help="the CPU baseline's smoother kernel products are timed on 1/N of the rows and scaled")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the untimed FP64 pass that gives the accuracy of the timed precision")
     return ap.parse_args()
 
 
@@ -168,17 +171,59 @@ def job_value(ws, T, steps, ms_max):
 
 
 # --------------------------------------------------------------------------------------- CPU leg
-def oracle_sample(w, steps):
-    """Time the FP64 oracle on the first `steps` filter steps of the workload (host cores)."""
+def oracle_sample(w, row_frac=16):
+    """Time the FP64 oracle on one steady-state step pair of the workload (host cores).
+
+    Filter: the oracle's update (iterative version, CG actions) and Truncate on a prior factor of
+    the steady-state width r (random columns with decaying norms, the shapes the filter reaches
+    after r / i steps), measured in full.  Smoother: the oracle's step costs two products
+    K [Ws ws] of width r + i + 1 over all n x n kernel entries (P_k A^T X and P^-_k A^T X) plus
+    low-rank terms; the K products are timed on 1/row_frac of the rows and scaled by row_frac,
+    the low-rank terms in full.  Returns (seconds per time step, description)."""
     import oracle
-    import synth
-    sub = w.with_(T=steps, obs_ptr=w.obs_ptr[:steps + 1],
-                  prior_mean=None if w.prior_mean is None else w.prior_mean[:steps + 1])
+    model = oracle.model_from(w)
+    n, r, i = w.n, max(w.rank_r, 0), w.budget_i
+    rng = np.random.default_rng(0)
+    # a valid downdate factor of the steady-state width: the update of the prior by r noisy point
+    # values, K(X, X_s) (K_ss + sn2 I)^(-1/2), so that K - M M^T stays positive definite
+    pts = np.sort(rng.choice(n, r, replace=False))
+    Ks = model.K_times(np.eye(r), cols=pts)
+    lam, Q = np.linalg.eigh(Ks[pts] + model.sn2 * np.eye(r))
+    Mp = Ks @ (Q / np.sqrt(lam)[None, :])
+    obs = w.obs(1)
+    m_pred = np.zeros(n)
     t0 = time.perf_counter()
-    oracle.filter_run(sub)
-    dt = time.perf_counter() - t0
-    return dt, f"oracle filter over steps 1..{steps} of the same workload (n={w.n}, m={int(w.obs_ptr[1])}); " \
-               f"smoother steps excluded (each costs more than a filter step, so this overstates CPU steps/s)"
+    m_new, M_hat, *_ = oracle.update_iterative(model, m_pred, model.a * Mp, obs, w.yk(1), i)
+    var = model.sf2 - np.sum(M_hat * M_hat, axis=1)
+    oracle.truncate(M_hat, r)
+    t_f = time.perf_counter() - t0
+    c = M_hat.shape[1]
+    X = model.a * rng.standard_normal((n, c + 1)) / math.sqrt(n)
+    rows = np.arange(0, n, row_frac)
+    t0 = time.perf_counter()
+    for _ in range(2):                                    # P_k A^T X and P^-_k A^T X
+        model.K_times(X, rows=rows)
+    t_k = (time.perf_counter() - t0) * (n / rows.size)
+    t0 = time.perf_counter()
+    for M in (M_hat, model.a * Mp):
+        M @ (M.T @ X)
+    t_l = time.perf_counter() - t0
+    del var, m_new
+    desc = (f"one steady-state step pair of the oracle (n={n}, m={len(obs)}, i={i}, r={r}): filter update + "
+            f"Truncate measured in full ({t_f:.1f} s); smoother: the two n x n x {c + 1} kernel products timed on "
+            f"1/{row_frac} of the rows and scaled ({t_k:.1f} s), its low-rank products in full ({t_l:.1f} s)")
+    return t_f + t_k + t_l, desc
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                if ln.lower().startswith(("model name", "cpu part", "hardware")):
+                    return ln.split(":", 1)[1].strip() + f" ({os.cpu_count()} cores)"
+    except Exception:
+        pass
+    return f"{os.cpu_count()} cores"
 
 
 def cpu_cores():
@@ -189,6 +234,40 @@ def cpu_cores():
         return int(n)
     except Exception:
         return os.cpu_count()
+
+
+def run_untimed(ck, w, coords, obs_idx, y, mu, precision, like, stream):
+    """One untimed filter + smoother pass at `precision`; returns its four (T+1) x n outputs."""
+    import torch
+    prob = ck.make_problem(coords, w.kernel, w.log_lx, w.log_lt, w.log_sf2, w.log_sn2, w.T, w.dt, w.obs_ptr,
+                           obs_idx, y, w.budget_i, w.rank_r, precision=precision, prior_mean=mu)
+    outs = [torch.empty_like(o) for o in like]
+    ctx = ck.Context()
+    ck.cakf_filter(prob, ctx, outs[0], outs[1], stream=stream.cuda_stream)
+    ck.cakf_smooth(ctx, outs[2], outs[3], stream=stream.cuda_stream)
+    nll = ck.cakf_nll(ctx)
+    ctx.close()
+    torch.cuda.synchronize()
+    outs.append(nll)
+    return outs
+
+
+def accuracy(got, ref, against):
+    """Errors of one pass against a reference pass, per result, max over the steps 1..T (state 0 is
+    the prior): means normwise relative per step, variances elementwise relative."""
+    out = {"against": against}
+    for name, i, kind in (("filter_mean", 0, "m"), ("filter_var", 1, "v"), ("smoother_mean", 2, "m"),
+                          ("smoother_var", 3, "v")):
+        a, b = got[i][1:], ref[i][1:]
+        if kind == "m":
+            e = (a - b).norm(dim=1) / b.norm(dim=1).clamp_min(1e-300)
+        else:
+            e = ((a - b).abs() / b.abs().clamp_min(1e-300)).amax(dim=1)
+        out[name] = float(e.max())
+        out[name + "_worst_step"] = int(e.argmax()) + 1
+    if len(got) > 4 and len(ref) > 4:
+        out["nll"] = abs(got[4] - ref[4]) / abs(ref[4])
+    return out
 
 
 # --------------------------------------------------------------------------------------- main
@@ -259,10 +338,12 @@ def main():
     clk_mhz = clocks.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
     clk = clk_mhz * 1e6
     nsm = 152
-    fp64_peak = nsm * 2 * 2 * clk / 1e12          # 2 FP64 FMA per clock per SM
-    mufu_peak = nsm * 16 * clk / 1e12             # 16 MUFU results per clock per SM (T ops/s); ncu's
-                                                  # XU-pipe issue peak is twice that (see profiles/)
-    peak_note = f"derived: {nsm} SMs x {{}} x median SM clock {clk_mhz:.0f} MHz"
+    # MUFU (sqrt + exp2 pair) and FP64 FMA throughputs measured by the library's probe kernels on
+    # this device right after the timed region (MEASURED_PEAKS.json holds only copy and GEMM rates)
+    probe = ck.cakf_probe_peaks(stream.cuda_stream)
+    fp64_peak = probe["fp64_flops_per_s"] / 1e12
+    mufu_peak = probe["mufu_ops_per_s"] / 1e12
+    peak_note = "measured by cakf_probe_peaks ({})"
     kernels = {}
     # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
     # each kernel as it is now, on the shapes of this workload (summaries under profiles/):
@@ -277,7 +358,7 @@ def main():
         ach = eig_flops[0] / (tri_ms / 1e3) / 1e12
         kernels["k_tridiag"] = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
                                 "frac": ach / fp64_peak, "traffic": ncu_traffic.get("k_tridiag"),
-                                "peak_source": peak_note.format("2 FP64 FMA/clk x 2"),
+                                "peak_source": peak_note.format("FP64 FMA chains, 2 flops each"),
                                 "launches": prof["eig_calls"], "avg_ms": tri_ms / prof["eig_calls"],
                                 "ms_total": tri_ms,
                                 "note": "one cross-block exchange per Householder column (epoch-tagged words, no grid barrier): bound by its latency chain, not by FP64 throughput"}
@@ -288,7 +369,7 @@ def main():
         tfl = prof["gram_block_flops"] / (gb_ms / 1e3) / 1e12
         ent = {"bound": "alu", "achieved": 2 * evals, "peak": mufu_peak, "unit": "TMUFU-op/s",
                "frac": 2 * evals / mufu_peak, "traffic": ncu_traffic.get("k_gram_tc"),
-               "peak_source": peak_note.format("16 MUFU/clk"),
+               "peak_source": peak_note.format("sqrt.approx + ex2.approx chains"),
                "launches": prof["gram_block_launches"], "avg_ms": gb_ms / prof["gram_block_launches"],
                "ms_total": gb_ms, "tensor_tflops": tfl}
         if args.precision in ("bf16", "fp16x3"):
@@ -305,7 +386,7 @@ def main():
         kernels["k_gram_matvec"] = {"bound": "alu", "achieved": 2 * evals, "peak": mufu_peak,
                                     "unit": "TMUFU-op/s", "frac": 2 * evals / mufu_peak,
                                     "traffic": ncu_traffic.get("k_gram_matvec"),
-                                    "peak_source": peak_note.format("16 MUFU/clk"),
+                                    "peak_source": peak_note.format("sqrt.approx + ex2.approx chains"),
                                     "launches_sampled": prof["cg_matvec_launches"],
                                     "avg_ms": mv_ms / prof["cg_matvec_launches"],
                                     "ms_total": mv_ms * phases_launches_cg}
@@ -337,6 +418,9 @@ def main():
                                       [p / max(1, args.steps) for p in phases])),
         "clocks": clocks,
         "gpu_launches": launches,
+        "probed_peaks": {"mufu_tops": mufu_peak, "fp64_tflops": fp64_peak,
+                         "mufu_per_sm_per_clk": probe["mufu_ops_per_s"] / (nsm * clk),
+                         "fp64_fma_per_sm_per_clk": probe["fp64_flops_per_s"] / 2 / (nsm * clk)},
     }
 
     # ---- end to end through the C ABI with pinned host buffers (copies inside the timed region)
@@ -365,33 +449,50 @@ def main():
 
     # ---- CPU baseline: the FP64 oracle on a bounded sample (rank 0, N = 1 only)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        secs, sample = oracle_sample(w, args.cpu_sample_steps)
-        line["cpu_baseline"] = {"value": args.cpu_sample_steps / secs, "unit": "time steps/s",
-                                "cores": cpu_cores(), "kind": "oracle", "sample": sample}
+        secs, sample = oracle_sample(w, args.cpu_row_frac)
+        line["cpu_baseline"] = {"value": 1.0 / secs, "unit": "time steps/s", "cores": cpu_cores(), "kind": "oracle",
+                                "sample": sample, "cpu": cpu_model()}
+    nll_timed = ck.cakf_nll(ctx)
     ctx.close()
 
+    # ---- accuracy of the timed precision: the device FP64 mode on the same workload (one untimed
+    # pass; its parity with the oracle is pinned by the tests), errors per result and step
+    ref = None
+    if not args.no_accuracy and args.precision != "fp64":
+        got = [o.clone() for o in outs] + [nll_timed]
+        ref = run_untimed(ck, w, coords, obs_idx, y, mu, "fp64", outs, stream)
+        line["accuracy"] = accuracy(got, ref, "fp64 device mode")
+        del got
+
     # ---- the same workload through the plain FP32 path (SIMT Gram x block, FP32 factors), for the
-    # mixed-vs-FP32 comparison the metric names: one untimed and one timed pass, events on the stream
+    # mixed-vs-FP32 comparison the metric names: one untimed and three timed passes (median), events
+    # on the stream
     if not args.no_fp32_compare and args.precision != "fp32":
         prob32 = ck.make_problem(coords, w.kernel, w.log_lx, w.log_lt, w.log_sf2, w.log_sn2, T, w.dt, w.obs_ptr,
                                  obs_idx, y, w.budget_i, w.rank_r, precision="fp32", prior_mean=mu)
         ctx32 = ck.Context()
         ck.cakf_filter(prob32, ctx32, outs[0], outs[1], stream=stream.cuda_stream)
         ck.cakf_smooth(ctx32, outs[2], outs[3], stream=stream.cuda_stream)
-        barrier(ws)
-        torch.cuda.synchronize(dev)
-        f0 = torch.cuda.Event(enable_timing=True)
-        f1 = torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        ck.cakf_filter(prob32, ctx32, outs[0], outs[1], stream=stream.cuda_stream)
-        ck.cakf_smooth(ctx32, outs[2], outs[3], stream=stream.cuda_stream)
-        f1.record(stream)
-        torch.cuda.synchronize(dev)
-        ms32 = allmax(ws, f0.elapsed_time(f1))
-        ctx32.close()
+        times32 = []
+        for _ in range(3):
+            barrier(ws)
+            torch.cuda.synchronize(dev)
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            ck.cakf_filter(prob32, ctx32, outs[0], outs[1], stream=stream.cuda_stream)
+            ck.cakf_smooth(ctx32, outs[2], outs[3], stream=stream.cuda_stream)
+            f1.record(stream)
+            torch.cuda.synchronize(dev)
+            times32.append(allmax(ws, f0.elapsed_time(f1)))
+        ms32 = statistics.median(times32)
         v32 = ws * T / (ms32 / 1e3)
-        line["fp32_plain"] = {"value": v32, "unit": "time steps/s", "steps": 1, "ms_per_step": ms32,
+        line["fp32_plain"] = {"value": v32, "unit": "time steps/s", "timed_passes": len(times32),
+                              "ms_per_pass_median": ms32, "ms_per_pass_all": times32,
                               "mixed_over_fp32": value / v32}
+        if ref is not None:
+            line["fp32_plain"]["accuracy"] = accuracy(outs + [ck.cakf_nll(ctx32)], ref, "fp64 device mode")
+        ctx32.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -401,23 +502,22 @@ def run_reference(args, ws, rank):
     if rank != 0:
         return
     w, desc = workload(args.config, args.T, device=None)
-    steps = max(1, args.cpu_sample_steps)
-    for _ in range(max(0, min(args.warmup, 1))):
-        oracle_sample(w, steps)
+    if args.warmup > 0:                       # one untimed sample (page-in, BLAS thread start)
+        oracle_sample(w, args.cpu_row_frac)
     times = []
     sample = ""
     for _ in range(max(1, args.steps)):
-        secs, sample = oracle_sample(w, steps)
+        secs, sample = oracle_sample(w, args.cpu_row_frac)
         times.append(secs)
     tot = sum(times)
-    value = steps * len(times) / tot
+    value = len(times) / tot
     line = {"metric": "filter+smoother time steps/sec", "value": value, "unit": "time steps/s", "n_gpus": ws,
             "steps": len(times), "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
             "config": {"workload": desc, "precision": "fp64 oracle"},
             "cpu_baseline": {"value": value, "unit": "time steps/s", "cores": cpu_cores(), "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "cpu": cpu_model()},
             "e2e": {"value": value, "unit": "time steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

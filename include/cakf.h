@@ -60,11 +60,14 @@ enum { CAKF_MATERN12 = 0, CAKF_MATERN32 = 1, CAKF_MATERN52 = 2 };
 enum {
   CAKF_FP64 = 0,   /* all in FP64 (reference mode)                                          */
   CAKF_FP32 = 1,   /* plain FP32 SIMT kernels (factors, CG and tall-skinny GEMMs in FP32)    */
-  CAKF_TF32 = 2,   /* reserved (tcgen05 kind::tf32), not implemented: rejected with CAKF_ERR_ARG */
+  CAKF_TF32 = 2,   /* Gram tiles x blocks on tcgen05 kind::tf32 (operands rounded to TF32,
+                      11 significant bits), FP32 accumulation                                 */
   CAKF_BF16 = 3,   /* Gram tiles x blocks on tcgen05 kind::f16 (bf16), FP32 accumulation    */
-  CAKF_FP16X3 = 4  /* Gram tiles x blocks on tcgen05 kind::f16 with split FP16 operands:
+  CAKF_FP16X3 = 4, /* Gram tiles x blocks on tcgen05 kind::f16 with split FP16 operands:
                       x = hi + lo (both fp16, B scaled per column by a power of two), three
                       MMAs hi*hi + hi*lo + lo*hi, FP32 accumulation: FP32-class products      */
+  CAKF_TF32X3 = 5  /* Gram tiles x blocks on tcgen05 kind::tf32 with split TF32 operands
+                      (x = hi + lo, both tf32, no scaling), three MMAs: FP32-class products   */
 };
 
 typedef struct {
@@ -88,7 +91,8 @@ typedef struct {
   int32_t budget_i;           /* action budget per step (CG iterations), >= 1                 */
   int32_t rank_r;             /* truncation rank of the downdate factors; <= 0: no truncation */
   double cg_rtol;             /* stop a step's CG early when ||r|| <= cg_rtol ||r0||; 0 = never */
-  int32_t precision;          /* CAKF_FP64 | CAKF_FP32 | CAKF_BF16 | CAKF_FP16X3 (TF32: rejected) */
+  int32_t precision;          /* CAKF_FP64 | CAKF_FP32 | CAKF_TF32 | CAKF_BF16 | CAKF_FP16X3 |
+                                 CAKF_TF32X3                                                  */
   const double* replay_actions; /* NULL, or frozen actions: for each step k the m_k x i_k
                                  column-major block S_k, concatenated over k = 1..T (host)    */
   const int32_t* replay_counts; /* with replay_actions: T+1 entries, i_k for k = 0..T (host)  */
@@ -191,10 +195,10 @@ int cakf_get_actions(cakf_ctx* ctx, double* actions_out, int32_t* counts_out);
  *   B                 DEVICE, column-major nc x width (leading dimension ldb >= nc); double for
  *                     CAKF_FP64, float otherwise
  *   Out               DEVICE, column-major nr x width (ldo >= nr); same element type as B
- *   precision         CAKF_FP64 / CAKF_FP32: SIMT kernels; CAKF_BF16 / CAKF_FP16X3: tcgen05
- *                     tensor cores for columns 0..width-2 (bf16 operands, or fp16 hi + lo
- *                     parts for FP16X3; fp32 accumulation) and fp32 CUDA-core accumulation of
- *                     the last column (width >= 2 and <= 513 for these paths)
+ *   precision         CAKF_FP64 / CAKF_FP32: SIMT kernels; CAKF_BF16 / CAKF_FP16X3 / CAKF_TF32
+ *                     / CAKF_TF32X3: tcgen05 tensor cores for columns 0..width-2 (bf16, fp16 hi +
+ *                     lo, tf32, or tf32 hi + lo operands; fp32 accumulation) and fp32 CUDA-core
+ *                     accumulation of the last column (width >= 2 and <= 513 for these paths)
  * Scratch is allocated on the first call per thread and kept (grown when needed).
  * Errors: CAKF_ERR_ARG (sizes, NULL, host pointers), CAKF_ERR_OOM, CAKF_ERR_CUDA.
  */
@@ -220,7 +224,8 @@ int cakf_gram_matmul(int32_t kernel, double log_lx, double log_sf2, int32_t dim,
  *
  * Limit: the scratch must hold 256 bytes + (nr + nc) coordinate records (32 bytes each for
  * CAKF_FP64, 16 otherwise, rounded up to 256) and, for CAKF_BF16, the packed operand
- * (about 2 * nc * (width - 1) bytes plus 20 * nc; twice the operand bytes for CAKF_FP16X3).
+ * (about 2 * nc * (width - 1) bytes plus 20 * nc; twice the operand bytes for CAKF_FP16X3 and
+ * CAKF_TF32, four times for CAKF_TF32X3).
  * A call needing more returns CAKF_ERR_ARG with the required size in cakf_last_error, before
  * any device work; for example BF16 with nc = 32768, width = 513 fits, nc = 65536 needs
  * width <= 257 (FP16X3: nc = 32768 needs width <= 257).
@@ -243,6 +248,24 @@ int cakf_gram_matmul_noalloc(int32_t kernel, double log_lx, double log_sf2, int3
                              void* Out, int32_t ldo, int32_t precision, void* cuda_stream);
 
 /*
+ * cakf_factor_gemm -- the tall-skinny factor product of the filter and smoother on its own (the
+ * products M^- (M_o^T [V v]), M_hat U of Truncate (Sec. 3.2), M^T X and the rotations of Alg. 3),
+ * the same device code the filter and smoother run:
+ *     C = alpha op(A) B + beta C,   op(A) = A (trans_a = 0) or A^T (trans_a = 1).
+ *   A       DEVICE float, column-major: M x K (lda >= M) for trans_a = 0, K x M (lda >= K) for 1
+ *   B       DEVICE float, column-major K x N (ldb >= K)
+ *   C       DEVICE float, column-major M x N (ldc >= M), read when beta != 0
+ *   precision  CAKF_FP32: FP32 SIMT kernels; a tensor-core mode (CAKF_TF32, CAKF_BF16, CAKF_FP16X3,
+ *           CAKF_TF32X3): tcgen05 with split TF32 operands (hi + lo, three MMAs, FP32
+ *           accumulation) for the large products, as in those modes' filter and smoother.
+ * Allocates and frees its workspace on every call (verification and tools, not the hot loop).
+ * Errors: CAKF_ERR_ARG, CAKF_ERR_OOM, CAKF_ERR_CUDA, CAKF_ERR_TIMEOUT.
+ */
+int cakf_factor_gemm(int32_t trans_a, int32_t M, int32_t N, int32_t K, double alpha, const float* A, int32_t lda,
+                     const float* B, int32_t ldb, double beta, float* C, int32_t ldc, int32_t precision,
+                     void* cuda_stream);
+
+/*
  * cakf_eig_topk -- the FP64 symmetric eigensolver of Truncate (Sec. 3.2) on its own: the top
  * `keep` eigenpairs of the N x N symmetric matrix A (the Gram M^T M of a downdate factor in the
  * filter and smoother), the same device code the filter and smoother run.
@@ -254,6 +277,17 @@ int cakf_gram_matmul_noalloc(int32_t kernel, double log_lx, double log_sf2, int3
  * CAKF_ERR_NUMERIC (secular iteration without convergence or non-finite values).
  */
 int cakf_eig_topk(const double* A, int32_t N, int32_t keep, double* w_out, double* U_out, void* cuda_stream);
+
+/*
+ * cakf_probe_peaks -- measured throughputs for the roofline denominators of the kernels that are
+ * bound neither by HBM nor by the tensor cores (no counterpart in the paper: a measurement aid).
+ *   mufu_ops_per_s    special-function results per second of the sqrt.approx + ex2.approx pair
+ *                     that every kernel-matrix entry costs (both counted), over the whole device
+ *   fp64_flops_per_s  FP64 fused multiply-add throughput (2 flops each) over the whole device
+ * Plain kernels timed with CUDA events on cuda_stream after one warm-up launch each (a few ms);
+ * the current device.  Errors: CAKF_ERR_ARG (NULL outputs), CAKF_ERR_OOM, CAKF_ERR_CUDA.
+ */
+int cakf_probe_peaks(double* mufu_ops_per_s, double* fp64_flops_per_s, void* cuda_stream);
 
 /* cakf_get_stats -- timings and counters of the last filter / smooth calls (host output). */
 int cakf_get_stats(const cakf_ctx* ctx, cakf_stats* out);

@@ -18,8 +18,8 @@ LIB_PATH = os.path.join(HERE, "libcakf.so")
 ABI_VERSION = 1
 OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_NUMERIC, ERR_TIMEOUT, ERR_STATE = range(7)
 MATERN12, MATERN32, MATERN52 = 0, 1, 2
-FP64, FP32, TF32, BF16, FP16X3 = 0, 1, 2, 3, 4
-PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32": TF32, "bf16": BF16, "fp16x3": FP16X3}
+FP64, FP32, TF32, BF16, FP16X3, TF32X3 = 0, 1, 2, 3, 4, 5
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32": TF32, "bf16": BF16, "fp16x3": FP16X3, "tf32x3": TF32X3}
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_NUMERIC", 5: "ERR_TIMEOUT", 6: "ERR_STATE"}
 
 
@@ -76,6 +76,11 @@ def lib():
         L.cakf_eig_topk.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, vp]
         L.cakf_eig_topk.restype = C.c_int
         L.cakf_gram_matmul_noalloc.restype = C.c_int
+        L.cakf_factor_gemm.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_double, vp, C.c_int32, vp,
+                                       C.c_int32, C.c_double, vp, C.c_int32, C.c_int32, vp]
+        L.cakf_factor_gemm.restype = C.c_int
+        L.cakf_probe_peaks.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
+        L.cakf_probe_peaks.restype = C.c_int
         L.cakf_free.argtypes = [vp]
         L.cakf_free.restype = None
         L.cakf_last_error.restype = C.c_char_p
@@ -361,6 +366,39 @@ def cakf_eig_topk(A, keep, stream=None):
     U = torch.empty((keep, N), dtype=torch.float64, device=A.device)
     _check(lib().cakf_eig_topk(Ac.data_ptr(), int(N), int(keep), w.data_ptr(), U.data_ptr(), stream))
     return w, U
+
+
+def cakf_factor_gemm(A, B, C=None, trans_a=False, alpha=1.0, beta=0.0, precision="fp32", stream=None):
+    """C = alpha op(A) B + beta C on the device with the library's factor-product kernels.  A, B, C
+    are CUDA float32 tensors holding column-major matrices as transposed row-major tensors: A of
+    shape (K, M) for op(A) = A (M x K) or (M, K) for op(A) = A^T (A is K x M), B of shape (N, K),
+    C of shape (N, M).  Returns C."""
+    import torch
+    for nm, t in (("A", A), ("B", B)):
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float32 or not t.is_contiguous() or not t.is_cuda:
+            raise ValueError(f"cakf_factor_gemm: {nm} must be a contiguous CUDA float32 tensor")
+    if trans_a:
+        M, K = A.shape
+    else:
+        K, M = A.shape
+    N = B.shape[0]
+    if tuple(B.shape) != (N, K):
+        raise ValueError("cakf_factor_gemm: B must have shape (N, K)")
+    if C is None:
+        C = torch.zeros((N, M), dtype=torch.float32, device=A.device)
+    if tuple(C.shape) != (N, M) or C.dtype != torch.float32 or not C.is_contiguous():
+        raise ValueError("cakf_factor_gemm: C must be a contiguous float32 tensor of shape (N, M)")
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    _check(lib().cakf_factor_gemm(1 if trans_a else 0, M, N, K, float(alpha), A.data_ptr(), K if trans_a else M,
+                                  B.data_ptr(), K, float(beta), C.data_ptr(), M, prec, _stream_of(stream, A.device)))
+    return C
+
+
+def cakf_probe_peaks(stream=None) -> dict:
+    """Measured MUFU (sqrt + exp2 pair) and FP64 FMA throughputs of the current device."""
+    mufu, fp64 = C.c_double(), C.c_double()
+    _check(lib().cakf_probe_peaks(C.byref(mufu), C.byref(fp64), stream))
+    return {"mufu_ops_per_s": mufu.value, "fp64_flops_per_s": fp64.value}
 
 
 def cakf_set_profiling(ctx: Context, on: bool):

@@ -20,7 +20,6 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcakf.so")
 INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CUDA_LIB = "/usr/local/cuda/lib64"
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 
 
@@ -68,8 +67,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = LIB + ".tmp"
-    cmd = [cc, *ARCH, "-shared", "-cudart=static", "-o", tmp, *objs, "-L" + CUDA_LIB, "-lcublas",
-           "-Xlinker", "-rpath=" + CUDA_LIB]
+    cmd = [cc, *ARCH, "-shared", "-cudart=static", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

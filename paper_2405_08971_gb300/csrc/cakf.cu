@@ -10,6 +10,7 @@
 //   S[k]     m_k x i_k actions
 //   mf, vf   (T+1) x n filter means / variances (FP64)
 #include <cstring>
+#include <cstdlib>
 #include <cstdio>
 #include <string>
 #include <vector>
@@ -187,6 +188,18 @@ namespace {
 
 size_t elem_size(int precision) { return precision == CAKF_FP64 ? 8 : 4; }
 
+// Operand mode of the tensor-core Gram x block for a precision (gram_block_tc's kind), -1 for the
+// SIMT paths.
+int tc_kind_of(int precision) {
+  switch (precision) {
+    case CAKF_BF16: return 0;
+    case CAKF_FP16X3: return 1;
+    case CAKF_TF32: return 2;
+    case CAKF_TF32X3: return 3;
+    default: return -1;
+  }
+}
+
 // ------------------------------------------------------------------------------------ planning
 int plan_and_alloc(cakf_ctx* c, const cakf_problem* p) {
   const int T = p->T;
@@ -340,8 +353,8 @@ int plan_and_alloc(cakf_ctx* c, const cakf_problem* p) {
   c->off_U[1] = 0;
   for (int k = 1; k <= T; ++k) c->off_U[k + 1] = c->off_U[k] + (size_t)c->Urows[k] * (c->Urows[k] ? c->mcols[k] : 0);
   if ((rc = c->alloc(c->Upool, std::max<size_t>(c->off_U[T + 1], 1) * sizeof(double)))) return rc;
-  if (c->precision == CAKF_BF16 || c->precision == CAKF_FP16X3) {
-    c->Bpack_bytes = gram_tc_staging_bytes(std::max(c->n, c->mmax), (int)wfin, c->precision == CAKF_FP16X3 ? 1 : 0) + 4096;
+  if (tc_kind_of(c->precision) >= 0) {
+    c->Bpack_bytes = gram_tc_staging_bytes(std::max(c->n, c->mmax), (int)wfin, tc_kind_of(c->precision)) + 4096;
     if ((rc = c->alloc(c->Bpack, c->Bpack_bytes))) return rc;
   }
   if (!c->ev0) { cudaEventCreate(&c->ev0); cudaEventCreate(&c->ev1); }
@@ -502,7 +515,7 @@ struct Runner {
       // FP64 mode's 1e-9 agreement needs.  The FP32-based modes need it only when the budget is a
       // large share of the observations (4 i >= m): there CG can converge within the budget and
       // the later residuals, at FP32 rounding level, are no longer independent of the earlier ones.
-      const bool reorth = !rep && (sizeof(T) == 8 || 4 * ic >= m);
+      const bool reorth = !rep && (sizeof(T) == 8 || 4 * ic >= m || getenv("CAKF_EXP_REORTH"));
       // CG policy without re-orthogonalisation: k_cg_upd2 writes the next action (the updated
       // residual) itself, so the selection runs only for the first action
       const bool fused_select = !rep && !reorth;
@@ -1014,8 +1027,7 @@ int validate(const cakf_problem* p) {
   const int N = p->obs_ptr[p->T];
   if (N > 0 && (!p->obs_idx || !p->y)) return fail(CAKF_ERR_ARG, "obs_idx / y is NULL");
   if (p->budget_i < 1 || p->budget_i > 1024) return fail(CAKF_ERR_ARG, "budget_i must be in 1..1024");
-  if (p->precision < CAKF_FP64 || p->precision > CAKF_FP16X3) return fail(CAKF_ERR_ARG, "unknown precision");
-  if (p->precision == CAKF_TF32) return fail(CAKF_ERR_ARG, "CAKF_TF32 Gram tiles are reserved and not implemented");
+  if (p->precision < CAKF_FP64 || p->precision > CAKF_TF32X3) return fail(CAKF_ERR_ARG, "unknown precision");
   const double hp[4] = {p->log_lx, p->log_lt, p->log_sf2, p->log_sn2};
   for (double h : hp)
     if (!std::isfinite(h) || std::fabs(h) > 80) return fail(CAKF_ERR_ARG, "hyperparameters must be finite");
@@ -1104,13 +1116,14 @@ void collect_profile(cakf_ctx* c) {
 
 template <class T>
 Runner<T> make_runner(cakf_ctx* c, cudaStream_t st) {
-  // plain FP32 factor products: cuBLAS FP32; mixed mode: cuBLAS FP32 emulated on BF16 tensor cores
+  // plain FP32 factor products: own SIMT kernels; tensor-core modes: own split-TF32 tcgen05 kernels
   set_gemm_mode(c->precision == CAKF_FP64 ? 0 : (c->precision == CAKF_FP32 ? 1 : 2));
+  set_gemm_err(c->err);
   Runner<T> r;
   r.c = c;
   r.st = st;
-  r.tc = (c->precision == CAKF_BF16 || c->precision == CAKF_FP16X3);
-  r.tc_kind = (c->precision == CAKF_FP16X3) ? 1 : 0;
+  r.tc = tc_kind_of(c->precision) >= 0;
+  r.tc_kind = std::max(tc_kind_of(c->precision), 0);
   return r;
 }
 
@@ -1319,9 +1332,9 @@ extern "C" int cakf_gram_matmul(int32_t kernel, double log_lx, double log_sf2, i
   if (!Xr || !Xc || !B || !Out) return fail(CAKF_ERR_ARG, "cakf_gram_matmul: NULL pointer");
   if (!is_device_ptr(Xr) || !is_device_ptr(Xc) || !is_device_ptr(B) || !is_device_ptr(Out))
     return fail(CAKF_ERR_ARG, "cakf_gram_matmul: all arrays must be device arrays of the current device");
-  if (precision != CAKF_FP64 && precision != CAKF_FP32 && precision != CAKF_BF16 && precision != CAKF_FP16X3)
-    return fail(CAKF_ERR_ARG, "cakf_gram_matmul: precision must be FP64, FP32, BF16 or FP16X3");
-  const bool tcp = precision == CAKF_BF16 || precision == CAKF_FP16X3;
+  if (precision < CAKF_FP64 || precision > CAKF_TF32X3)
+    return fail(CAKF_ERR_ARG, "cakf_gram_matmul: unknown precision");
+  const bool tcp = tc_kind_of(precision) >= 0;
   if (tcp && (width < 2 || width > gram_tc_max_width()))
     return fail(CAKF_ERR_ARG, "cakf_gram_matmul: the tensor-core paths need 2 <= width <= 513");
   if (!std::isfinite(log_lx) || !std::isfinite(log_sf2)) return fail(CAKF_ERR_ARG, "non-finite hyperparameters");
@@ -1349,7 +1362,7 @@ extern "C" int cakf_gram_matmul(int32_t kernel, double log_lx, double log_sf2, i
     if (precision == CAKF_FP32) {
       gram_block_simt<float>(kernel, xr, nr, xc, nc, (const float*)B, ldb, width, (float)sf2, (float*)Out, ldo, st);
     } else {
-      const int kind = precision == CAKF_FP16X3 ? 1 : 0;
+      const int kind = tc_kind_of(precision);
       if ((rc = ensure(g_gs.stage, g_gs.stage_bytes, gram_tc_staging_bytes(nc, width, kind) + 4096))) return rc;
       const int ldp = (int)gram_tc_packed_ld(nc);
       int r2 = gram_tc_pack_b(kind, (const float*)B, ldb, nc, width, g_gs.stage, ldp, st);
@@ -1365,6 +1378,51 @@ extern "C" int cakf_gram_matmul(int32_t kernel, double log_lx, double log_sf2, i
   if (e == kErrTimeout) return fail(CAKF_ERR_TIMEOUT, "cakf_gram_matmul: a device-side wait exceeded its limit");
   if (e) return fail(CAKF_ERR_NUMERIC, "cakf_gram_matmul: numeric error");
   (void)es;
+  return CAKF_OK;
+}
+
+extern "C" int cakf_factor_gemm(int32_t trans_a, int32_t M, int32_t N, int32_t K, double alpha, const float* A,
+                                int32_t lda, const float* B, int32_t ldb, double beta, float* C, int32_t ldc,
+                                int32_t precision, void* cuda_stream) {
+  if ((trans_a != 0 && trans_a != 1) || M < 1 || N < 1 || K < 0 || ldb < K || ldc < M ||
+      lda < (trans_a ? K : M) || !A || !B || !C)
+    return fail(CAKF_ERR_ARG, "cakf_factor_gemm: invalid sizes or NULL pointer");
+  if (!is_device_ptr(A) || !is_device_ptr(B) || !is_device_ptr(C))
+    return fail(CAKF_ERR_ARG, "cakf_factor_gemm: all arrays must be device arrays of the current device");
+  if (precision != CAKF_FP32 && tc_kind_of(precision) < 0)
+    return fail(CAKF_ERR_ARG, "cakf_factor_gemm: precision must be CAKF_FP32 or a tensor-core mode");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const int mode = precision == CAKF_FP32 ? 1 : 2;
+  const size_t part_elems = std::max<size_t>(size_t(1) << 22, (size_t)M * N * 2);
+  double *part = nullptr, *c64 = nullptr;
+  int* err = nullptr;
+  auto release = [&]() { if (part) cudaFree(part); if (c64) cudaFree(c64); if (err) cudaFree(err); };
+  if (cudaMalloc(&part, part_elems * sizeof(double)) != cudaSuccess || cudaMalloc(&err, sizeof(int)) != cudaSuccess ||
+      (trans_a && cudaMalloc(&c64, (size_t)M * N * sizeof(double)) != cudaSuccess)) {
+    cudaGetLastError();
+    release();
+    return fail(CAKF_ERR_OOM, "cakf_factor_gemm: workspace allocation failed");
+  }
+  cudaMemsetAsync(err, 0, sizeof(int), st);
+  const int saved = gemm_mode();
+  set_gemm_mode(mode);
+  set_gemm_err(err);
+  if (trans_a) {
+    // C = alpha A^T B + beta C through the FP64-output product, converted back to FP32
+    convert_to_f64(C, ldc, M, N, c64, M, st);
+    gemm_tn<float>(A, lda, M, B, ldb, N, K, alpha, beta, c64, M, part, part_elems, st);
+    convert_from_f64<float>(c64, M, M, N, C, ldc, st);
+  } else {
+    gemm_nn<float, float>(M, N, K, (float)alpha, A, lda, B, ldb, (float)beta, C, ldc, st);
+  }
+  set_gemm_mode(saved);
+  cudaError_t ce = cudaStreamSynchronize(st);
+  int e = 0;
+  if (ce == cudaSuccess) cudaMemcpy(&e, err, sizeof(int), cudaMemcpyDeviceToHost);
+  release();
+  if (ce != cudaSuccess) return fail(CAKF_ERR_CUDA, std::string("cakf_factor_gemm: ") + cudaGetErrorString(ce));
+  if (e == kErrTimeout) return fail(CAKF_ERR_TIMEOUT, "cakf_factor_gemm: a device-side wait exceeded its limit");
+  if (e) return fail(CAKF_ERR_NUMERIC, "cakf_factor_gemm: numeric error");
   return CAKF_OK;
 }
 

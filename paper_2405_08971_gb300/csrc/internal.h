@@ -96,6 +96,7 @@ void check_finite(const double* x, size_t n, int* err, cudaStream_t st);
 void scale_f64(double* A, int ld, int rows, int cols, double s, cudaStream_t st);
 template <class T>
 void convert_from_f64(const double* In, int ldi, int rows, int cols, T* Out, int ldo, cudaStream_t st);
+void convert_to_f64(const float* In, int ldi, int rows, int cols, double* Out, int ldo, cudaStream_t st);
 
 // Record msg as the calling thread's cakf_last_error message; returns code.
 int set_last_error(int code, const char* msg);
@@ -104,13 +105,13 @@ int set_last_error(int code, const char* msg);
 constexpr int kErrNumeric = 1;
 constexpr int kErrTimeout = 2;
 
-// ---- cuBLAS GEMMs for the plain FP32 factor products (blas.cu) ----
-int blas_gemm_f32(int emulate_bf16x9, int transA, int M, int N, int K, float alpha, const float* A, int lda,
-                  const float* B, int ldb, float beta, float* C, int ldc, cudaStream_t st);
-// Global switch for the FP32 GEMM launchers: 0 = own SIMT kernels, 1 = cuBLAS FP32, 2 = cuBLAS
-// FP32 emulated on BF16 tensor cores.  Set by the orchestration per call (thread-local).
+// Switch for the FP32 GEMM launchers (gemm_nn / gemm_tn): 0 or 1 = own SIMT kernels (the plain
+// FP32 path), 2 = own tensor-core kernels with split TF32 operands for the large products (the
+// tensor-core modes).  Set by the orchestration per call (thread-local), with the device error
+// flag the tensor-core kernels raise when a bounded wait runs out.
 void set_gemm_mode(int mode);
 int gemm_mode();
+void set_gemm_err(int* err);
 
 // ---- FP64 symmetric eigensolver (eig.cu) ----
 // Workspace bytes needed for matrices up to order nmax.
@@ -128,6 +129,16 @@ int eig_sym_topk(double* A, int lda, int N, int nkeep, double* w, T* U, int ldu,
 // kind: 0 = BF16 operands (one MMA per slice), 1 = split BF16 (hi + lo parts, three MMAs).
 int gram_block_tc(int ker, int kind, const C4<float>* Xr, int nr, const C4<float>* Xc, int nc, const void* B, int ldb,
                   int width, float sf2, float* Out, int ldo, int* err, cudaStream_t st);
+// Tall-skinny FP32 products on the tensor cores with split TF32 operands (about 22 significant bits
+// per product, FP32 accumulation):
+//   gemm_tc_nn: C (M x N, float) = alpha A B + beta C, A M x K (lda), B K x N (ldb), column-major;
+//   gemm_tc_tn: C (na x nb, double) = alpha A^T B + beta C, A K x na, B K x nb, with the K range
+//               split over CTAs; part (part_bytes) holds the FP32 partial tiles, summed in FP64.
+// Return 0 on success (launch errors otherwise); a timed-out wait raises the device flag err.
+int gemm_tc_nn(int M, int N, int K, float alpha, const float* A, int lda, const float* B, int ldb, float beta,
+               float* C, int ldc, int* err, cudaStream_t st);
+int gemm_tc_tn(const float* A, int lda, int na, const float* B, int ldb, int nb, int K, double alpha, double beta,
+               double* C, int ldc, void* part, size_t part_bytes, int* err, cudaStream_t st);
 // Convert a column-major float block (rows x cols, ld) into the operand layout of gram_block_tc.
 int gram_tc_pack_b(int kind, const float* B, int ldb, int rows, int cols, void* Bp, int ldp, cudaStream_t st);
 size_t gram_tc_packed_ld(int rows);

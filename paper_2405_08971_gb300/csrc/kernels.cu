@@ -13,8 +13,10 @@ namespace cakf {
 
 static std::atomic<long long> g_launches{0};
 static thread_local int t_gemm_mode = 0;
+static thread_local int* t_gemm_err = nullptr;
 void set_gemm_mode(int mode) { t_gemm_mode = mode; }
 int gemm_mode() { return t_gemm_mode; }
+void set_gemm_err(int* err) { t_gemm_err = err; }
 long long launch_count() { return g_launches.load(); }
 void note_launch(long long k) { g_launches += k; }
 
@@ -1381,18 +1383,21 @@ __global__ void k_axpby_f32_f64(const float* __restrict__ X, int ldx, int rows, 
   *p = alpha * double(X[(size_t)c * ldx + i]) + (beta != 0.0 ? beta * *p : 0.0);
 }
 
+void convert_to_f64(const float* In, int ldi, int rows, int cols, double* Out, int ldo, cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return;
+  k_axpby_f32_f64<<<dim3(cdiv(rows, 256), cols), 256, 0, st>>>(In, ldi, rows, cols, 1.0, 0.0, Out, ldo); note_launch();
+}
+
 template <class T>
 void gemm_tn(const T* A, int lda, int na, const T* B, int ldb, int nb, int K, double alpha, double beta, double* C,
              int ldc, double* part, size_t part_elems, cudaStream_t st) {
   if (na <= 0 || nb <= 0) return;
-  if (sizeof(T) == 4 && t_gemm_mode > 0 && (double)na * nb * K > 2e7 && part_elems * 2 >= (size_t)na * nb) {
-    // FP32 product into the partial buffer (reinterpreted as floats), then scale into C (double)
-    float* tmp = reinterpret_cast<float*>(part);
-    if (blas_gemm_f32(t_gemm_mode == 2, 1, na, nb, K, 1.0f, (const float*)A, lda, (const float*)B, ldb, 0.0f, tmp, na,
-                      st) == 0) {
-      k_axpby_f32_f64<<<dim3(cdiv(na, 256), nb), 256, 0, st>>>(tmp, na, na, nb, alpha, beta, C, ldc); note_launch();
+  if (sizeof(T) == 4 && t_gemm_mode == 2 && (double)na * nb * K > 2e7 && K >= 64) {
+    // FP32 operands on the tensor cores (split TF32), FP32 partial tiles summed in FP64
+    if (gemm_tc_tn((const float*)A, lda, na, (const float*)B, ldb, nb, K, alpha, beta, C, ldc, part,
+                   part_elems * sizeof(double), t_gemm_err, st) == 0)
       return;
-    }
+    cudaGetLastError();
   }
   const size_t tile_elems = (size_t)na * nb;
   int gx = cdiv(na, TN_T), gy = cdiv(nb, TN_T);
@@ -1408,7 +1413,7 @@ void gemm_tn(const T* A, int lda, int na, const T* B, int ldb, int nb, int K, do
   k_reduce_splits<double><<<cdiv(tile_elems, 256), 256, 0, st>>>(part, nsplit, na, nb, alpha, beta, C, ldc); note_launch();
 }
 
-// FP32 copy of a small double coefficient block for the cuBLAS path (thread-local device scratch)
+// FP32 copy of a small double coefficient block for the tensor-core path (thread-local device scratch)
 static thread_local float* t_bscratch = nullptr;
 static thread_local size_t t_bscratch_elems = 0;
 static float* bscratch(size_t elems) {
@@ -1429,7 +1434,8 @@ void gemm_nn(int M, int N, int K, T alpha, const T* A, int lda, const TB* B, int
   if (K <= 0) {
     if (beta == T(1)) return;
   }
-  if (sizeof(T) == 4 && t_gemm_mode > 0 && K > 0 && (double)M * N * K > 2e7) {
+  if (sizeof(T) == 4 && t_gemm_mode == 2 && K >= 16 && M >= 4096 && (double)M * N * K > 2e7) {
+    // tall factor times a small coefficient block on the tensor cores (split TF32)
     const float* Bf = reinterpret_cast<const float*>(B);
     int ldbf = ldb;
     if (sizeof(TB) == 8) {
@@ -1442,9 +1448,10 @@ void gemm_nn(int M, int N, int K, T alpha, const T* A, int lda, const TB* B, int
         Bf = nullptr;
       }
     }
-    if (Bf && blas_gemm_f32(t_gemm_mode == 2, 0, M, N, K, (float)alpha, (const float*)A, lda, Bf, ldbf, (float)beta,
-                            (float*)C, ldc, st) == 0)
+    if (Bf && gemm_tc_nn(M, N, K, (float)alpha, (const float*)A, lda, Bf, ldbf, (float)beta, (float*)C, ldc,
+                         t_gemm_err, st) == 0)
       return;
+    cudaGetLastError();
   }
   k_gemm_nn<T, TB><<<dim3(cdiv(M, NN_BM), cdiv(N, NN_BN)), 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc); note_launch();
 }

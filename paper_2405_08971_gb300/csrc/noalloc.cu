@@ -6,7 +6,7 @@
 // Scratch layout inside g_noalloc_scratch (offsets 256-byte aligned):
 //   [0, 256)              device error flag (int), cleared on the call's stream before each use
 //   [256, 256 + coords)   (nr + nc) pre-scaled coordinate records, C4<double> or C4<float>
-//   [.., .. + staging)    tensor-core paths only: packed bf16 operand part(s), fp32 last column, padded
+//   [.., .. + staging)    tensor-core paths only: packed operand part(s), fp32 last column, padded
 //                         coordinates (layout of gram_tc_pack_b / gram_block_tc)
 // Every byte the kernels read from the coordinate and staging regions is written earlier on
 // the same stream by the same call, so only the error flag has to start at zero.
@@ -78,10 +78,11 @@ extern "C" int cakf_gram_matmul_noalloc(int32_t kernel, double log_lx, double lo
   if (kernel < 0 || kernel > 2 || dim < 1 || dim > 3 || nr < 1 || nc < 1 || width < 1 || ldb < nc || ldo < nr)
     return err(CAKF_ERR_ARG, "cakf_gram_matmul_noalloc: invalid sizes or kernel");
   if (!Xr || !Xc || !B || !Out) return err(CAKF_ERR_ARG, "cakf_gram_matmul_noalloc: NULL pointer");
-  if (precision != CAKF_FP64 && precision != CAKF_FP32 && precision != CAKF_BF16 && precision != CAKF_FP16X3)
-    return err(CAKF_ERR_ARG, "cakf_gram_matmul_noalloc: precision must be FP64, FP32, BF16 or FP16X3");
-  const bool tcp = precision == CAKF_BF16 || precision == CAKF_FP16X3;
-  const int kind = precision == CAKF_FP16X3 ? 1 : 0;
+  if (precision < CAKF_FP64 || precision > CAKF_TF32X3)
+    return err(CAKF_ERR_ARG, "cakf_gram_matmul_noalloc: unknown precision");
+  const int kind = precision == CAKF_BF16 ? 0 : precision == CAKF_FP16X3 ? 1 : precision == CAKF_TF32 ? 2
+                 : precision == CAKF_TF32X3 ? 3 : -1;
+  const bool tcp = kind >= 0;
   if (tcp && (width < 2 || width > gram_tc_max_width()))
     return err(CAKF_ERR_ARG, "cakf_gram_matmul_noalloc: the tensor-core paths need 2 <= width <= 513");
   if (!std::isfinite(log_lx) || !std::isfinite(log_sf2))

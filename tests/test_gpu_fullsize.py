@@ -5,7 +5,7 @@ i = 64, r = 512), in the launch configuration bench.py times.
   well under a minute): means (normwise), variances (elementwise) and the NLL term, for the FP64,
   FP32 and split-FP16 (x3) modes.
 * Three filter steps and the smoother pass of the FP32 and split-FP16 modes against the device FP64
-  mode, whose parity with the oracle is pinned at 1e-9 on the smaller cases of test_gpu_parity; the
+  mode, whose parity with the oracle is pinned at 1e-10 on the smaller cases of test_gpu_parity; the
   properties that hold at any size: 0 < variance <= sigma_f^2, the smoother variance never above the
   filter variance of the same step, finite NLL.
 
@@ -13,8 +13,8 @@ i = 64, r = 512), in the launch configuration bench.py times.
 * Two steps of the largest configuration's shapes (n = 262,144, m = 16,384, i = 128, r = 256):
   split FP16 against the device FP64 mode, and the same properties.
 
-Tolerances: FP64 mode 1e-9 (as on the small cases); FP32 and split FP16 1e-3 for means and
-variances (the accuracy target of the mixed-precision path), 1e-3 for the NLL.
+Tolerances: FP64 mode 1e-10 (as on the small cases); FP32 and split FP16 / TF32 1e-3 for means
+(normwise), variances (elementwise) and the NLL (the accuracy target of the mixed-precision path).
 """
 import numpy as np
 import pytest
@@ -55,7 +55,7 @@ def step1():
     return w, f
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("fp32", 1e-3), ("fp16x3", 1e-3)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-3), ("fp16x3", 1e-3), ("tf32x3", 1e-3)])
 def test_step1_against_oracle(step1, precision, tol):
     w, f = step1
     got = run_gpu(w, precision, smooth=False)
@@ -72,7 +72,7 @@ def fp64_T3():
     return w, run_gpu(w, "fp64")
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp16x3"])
+@pytest.mark.parametrize("precision", ["fp32", "fp16x3", "tf32x3"])
 def test_three_steps_against_fp64_mode(fp64_T3, precision):
     w, ref = fp64_T3
     got = run_gpu(w, precision)
@@ -117,7 +117,7 @@ def grid16k_T2():
     return w, dict(mf=f.m, vf=f.var, ms=ms, vs=vs, nll=oracle.nll_total(f))
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("fp32", 1e-3)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-3)])
 def test_grid16k_two_steps_against_oracle(grid16k_T2, precision, tol):
     """The 2-D configuration at full size (128 x 128 grid, n = 16,384, m = 2,000, i = 32, r = 256,
     Matern-5/2, seasonal prior mean) over two steps, filter and smoother, against the oracle."""
@@ -127,6 +127,5 @@ def test_grid16k_two_steps_against_oracle(grid16k_T2, precision, tol):
              ms=mean_err(got["ms"], ref["ms"]), vs=var_err(got["vs"], ref["vs"]),
              nll=abs(got["nll"] - ref["nll"]) / abs(ref["nll"]))
     print("16k", precision, {k: f"{v:.2e}" for k, v in e.items()})
-    vtol = tol if precision == "fp64" else 2e-3
-    assert e["mf"] < tol and e["ms"] < tol and e["nll"] < tol
-    assert e["vf"] < vtol and e["vs"] < vtol
+    for k, v in e.items():
+        assert v < tol, (k, v)

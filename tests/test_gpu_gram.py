@@ -17,6 +17,10 @@ persistent tensor-core grid splits tiles between CTAs.  Tolerances:
                term); what remains is the tensor core's own FP32 accumulation, which measures
                1e-6..2e-5 on these cases (the same order as the BF16 path's distance from its
                exactly-accumulated BF16 emulation).
+  TF32        kind::tf32, operands rounded to TF32 (round to nearest, 2^-11): within 2e-4 of the
+               exact product of the TF32-rounded operands, and within 5e-3 of the exact product.
+  TF32X3      tf32 hi + lo parts (no scaling), three kind::tf32 MMAs: within 1e-4 of the exact
+               product, as FP16X3.
 """
 import math
 
@@ -51,6 +55,13 @@ def case(nr, nc, width, dim, kernel, seed, lx=0.3, sf2=1.7):
     return Xr, Xc, B, ref, ref_bf16, math.log(lx), math.log(sf2)
 
 
+def tf32(a):
+    """FP32 -> TF32 round to nearest (ties away from zero) on the magnitude bits, as cvt.rna.tf32."""
+    bits = np.asarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    bits = ((bits + 0x1000) & 0xFFFFE000).astype(np.uint32)
+    return bits.view(np.float32).astype(np.float64)
+
+
 @pytest.mark.parametrize("nr,nc,width,dim,kernel", [
     (1000, 777, 2, 2, 1), (300, 257, 17, 3, 2), (513, 1000, 65, 1, 0), (257, 640, 257, 3, 1),
     (384, 300, 513, 2, 1), (130, 70, 100, 3, 2),
@@ -80,10 +91,30 @@ def test_gram_matmul_all_precisions(nr, nc, width, dim, kernel):
     print(f"   fp16x3 {ex3[:-1].max():.1e} last-col {ex3[-1]:.1e}")
     assert ex3[:-1].max() < 1e-4, ex3[:-1].max()
     assert ex3[-1] < 2e-5, ex3[-1]
+    C = oracle.kernel_matrix(Xr, Xc, kernel, math.exp(llx), 1.0)
+    ref_tf32 = math.exp(lsf2) * (tf32(C) @ tf32(B).T).T
+    outtf = ck.cakf_gram_matmul(kernel, llx, lsf2, tXr, tXc, torch.as_tensor(B, device=d), precision="tf32")
+    got = outtf.cpu().double().numpy()
+    etf, emt = colwise_rel(got, ref), colwise_rel(got[:-1], ref_tf32[:-1])
+    outt3 = ck.cakf_gram_matmul(kernel, llx, lsf2, tXr, tXc, torch.as_tensor(B, device=d), precision="tf32x3")
+    et3 = colwise_rel(outt3.cpu().double().numpy(), ref)
+    print(f"   tf32 {etf[:-1].max():.1e} (vs tf32-rounded operands {emt.max():.1e}) tf32x3 {et3[:-1].max():.1e} "
+          f"last-col {etf[-1]:.1e} {et3[-1]:.1e}")
+    assert emt.max() < 2e-4, emt.max()
+    assert etf[:-1].max() < 5e-3, etf[:-1].max()
+    assert et3[:-1].max() < 1e-4, et3[:-1].max()
+    assert etf[-1] < 2e-5 and et3[-1] < 2e-5
 
 
 def test_gram_matmul_rejects_host_pointers():
+    """Host tensors are refused by the binding (ValueError) and, passed straight to the C ABI, by
+    the library (CAKF_ERR_ARG) before any launch."""
     Xr = torch.zeros((4, 2), dtype=torch.float64)
-    with pytest.raises(ck.CakfError) as ei:
-        ck.cakf_gram_matmul(1, 0.0, 0.0, Xr, Xr, torch.zeros((3, 4), dtype=torch.float32), precision="fp32")
-    assert ei.value.code == ck.binding.ERR_ARG
+    B = torch.zeros((3, 4), dtype=torch.float32)
+    out = torch.zeros((3, 4), dtype=torch.float32)
+    with pytest.raises(ValueError):
+        ck.cakf_gram_matmul(1, 0.0, 0.0, Xr, Xr, B, out=out, precision="fp32")
+    for fn in (ck.lib().cakf_gram_matmul, ck.lib().cakf_gram_matmul_noalloc):
+        rc = fn(1, 0.0, 0.0, 2, Xr.data_ptr(), 4, Xr.data_ptr(), 4, B.data_ptr(), 4, 3, out.data_ptr(), 4,
+                ck.FP32, None)
+        assert rc == ck.binding.ERR_ARG

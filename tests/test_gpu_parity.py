@@ -1,15 +1,15 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle on identical seeded inputs.
 
 Tolerances (written per quantity):
-  FP64 mode: means (per-step normwise) and variances (elementwise) within 1e-9 relative when the
-             CG actions are chosen on the device, 1e-10 when the oracle's actions are replayed.
-             NLL within 1e-9 (computed on the device from its definition: FP64 Cholesky factors of
-             S^T G S and S^T S, as in the oracle).
+  FP64 mode: means (per-step normwise), variances (elementwise) and the NLL within 1e-10 relative,
+             with the CG actions chosen on the device and with the oracle's actions replayed (the
+             NLL is computed on the device from its definition: FP64 Cholesky factors of S^T G S
+             and S^T S, as in the oracle).
   FP32 mode: the CG actions are chosen from FP32 residuals, so the projected subspace itself moves
-             by ~1e-6; bounds of 1e-3 (means) and 2e-3 (variances) hold with a wide margin.
-  FP16X3 mode: the Gram x block products carry each operand as two FP16 parts (22 significant
-             bits, FP32 accumulation; the mean column stays FP32), the rest is the FP32 path: the
-             FP32 bounds (1e-3 means, 2e-3 variances, 1e-3 NLL).
+             by ~1e-6; 1e-3 relative on means (normwise), variances (elementwise) and the NLL.
+  FP16X3 / TF32X3 modes: the Gram x block products carry each operand as two FP16 (TF32) parts
+             (22 significant bits, FP32 accumulation; the mean column stays FP32) and the factor
+             products are split-TF32 tensor-core GEMMs; the FP32 bounds (1e-3).
   (Plain BF16 rounds each operand to 2^-8 relative; variances near observed points, where the
   posterior variance is a small difference of O(sf2) terms, then lose 1e-2..4e-1 relative on
   these ill-conditioned cases, so that mode is checked at the kernel level in test_gpu_gram.)
@@ -108,7 +108,7 @@ def test_fp64_parity(name):
     print(name, {k: f"{v:.2e}" for k, v in e.items()})
     assert np.array_equal(got["counts"][1:], ref["f"].iters[1:])
     for k, v in e.items():
-        assert v < 1e-9, (k, v)
+        assert v < 1e-10, (k, v)
 
 
 @pytest.mark.parametrize("name", ["grid2d-ragged-trunc", "sphere-m32-trunc", "large-rank-trunc"])
@@ -133,9 +133,8 @@ def test_fp32_parity(name):
              ms=mean_err(got["ms"], ref["ms"]), vs=var_err(got["vs"], ref["vs"]),
              nll=abs(got["nll"] - ref["nll"]) / abs(ref["nll"]))
     print(name, "fp32", {k: f"{v:.2e}" for k, v in e.items()})
-    assert e["mf"] < 1e-3 and e["ms"] < 1e-3
-    assert e["vf"] < 2e-3 and e["vs"] < 2e-3
-    assert e["nll"] < 1e-3
+    for k, v in e.items():
+        assert v < 1e-3, (k, v)
 
 
 def test_device_buffers_and_context_reuse():
@@ -175,15 +174,33 @@ def test_state_errors():
     ctx.close()
 
 
-@pytest.mark.parametrize("name", ["grid2d-ragged-trunc", "sphere-m32-trunc", "missing-steps-m12"])
-def test_fp16x3_parity(name):
+@pytest.mark.parametrize("precision", ["fp16x3", "tf32x3"])
+@pytest.mark.parametrize("name", ["grid2d-ragged-trunc", "sphere-m32-trunc", "missing-steps-m12", "ragged-m129"])
+def test_split_tensor_core_parity(name, precision):
     w = CASES[name]()
     ref = run_oracle(w)
-    got = run_gpu(w, "fp16x3")
+    got = run_gpu(w, precision)
     e = dict(mf=mean_err(got["mf"], ref["mf"]), vf=var_err(got["vf"], ref["vf"]),
              ms=mean_err(got["ms"], ref["ms"]), vs=var_err(got["vs"], ref["vs"]),
              nll=abs(got["nll"] - ref["nll"]) / abs(ref["nll"]))
-    print(name, "fp16x3", {k: f"{v:.2e}" for k, v in e.items()})
-    assert e["mf"] < 1e-3 and e["ms"] < 1e-3
-    assert e["vf"] < 2e-3 and e["vs"] < 2e-3
-    assert e["nll"] < 1e-3
+    print(name, precision, {k: f"{v:.2e}" for k, v in e.items()})
+    for k, v in e.items():
+        assert v < 1e-3, (k, v)
+
+
+@pytest.mark.parametrize("name", ["grid2d-ragged-trunc", "sphere-m32-trunc"])
+def test_single_pass_tensor_core_modes_run(name):
+    """BF16 and TF32 (one MMA per product, 8 resp. 11 significant bits) are the fast, less accurate
+    modes: on these ill-conditioned cases they are checked for finite outputs within the prior
+    variance and a mean error below 5e-2 (their kernel-level accuracy is pinned in test_gpu_gram)."""
+    w = CASES[name]()
+    ref = run_oracle(w)
+    sf2 = float(np.exp(w.log_sf2))
+    for precision in ("bf16", "tf32"):
+        got = run_gpu(w, precision)
+        e = mean_err(got["mf"], ref["mf"])
+        print(name, precision, f"mean {e:.2e} var {var_err(got['vf'], ref['vf']):.2e}")
+        for key in ("mf", "vf", "ms", "vs"):
+            assert np.all(np.isfinite(got[key]))
+        assert np.all(got["vf"] <= sf2 * (1 + 1e-5))
+        assert e < 5e-2
