@@ -42,7 +42,7 @@
 extern "C" {
 #endif
 
-#define CAKF_ABI_VERSION 1
+#define CAKF_ABI_VERSION 2
 
 typedef enum {
   CAKF_OK = 0,
@@ -68,6 +68,19 @@ enum {
                       MMAs hi*hi + hi*lo + lo*hi, FP32 accumulation: FP32-class products      */
   CAKF_TF32X3 = 5  /* Gram tiles x blocks on tcgen05 kind::tf32 with split TF32 operands
                       (x = hi + lo, both tf32, no scaling), three MMAs: FP32-class products   */
+};
+
+/* Where the per-step factors the smoother and the gradient pass read (M+_k, [P^-W_k P^-w_k],
+   K(X, X_o)[V_k v_k], [V_k v_k]) are kept between cakf_filter and cakf_smooth (memory O(n r) per
+   step, Sec. 3.2). */
+enum {
+  CAKF_STORE_FP32 = 0,   /* all steps resident in the working precision (FP64 in CAKF_FP64 mode)   */
+  CAKF_STORE_BF16 = 1,   /* all steps kept as BF16 copies (half the bytes; the smoother reads them
+                            back rounded to 8 significant bits); FP32-based precisions only        */
+  CAKF_RECOMPUTE = 2     /* only M+_k and its eigenvalues every checkpoint_every steps (and the
+                            actions of every step) are kept; the smoother and the gradient pass
+                            re-run the filter over each segment with the stored actions, which
+                            reproduces the first pass's factors exactly                           */
 };
 
 typedef struct {
@@ -96,6 +109,9 @@ typedef struct {
   const double* replay_actions; /* NULL, or frozen actions: for each step k the m_k x i_k
                                  column-major block S_k, concatenated over k = 1..T (host)    */
   const int32_t* replay_counts; /* with replay_actions: T+1 entries, i_k for k = 0..T (host)  */
+  int32_t factor_storage;     /* CAKF_STORE_FP32 | CAKF_STORE_BF16 | CAKF_RECOMPUTE              */
+  int32_t checkpoint_every;   /* segment length of CAKF_STORE_BF16 / CAKF_RECOMPUTE (the steps
+                                 restored at a time; 0 = 20); ignored for CAKF_STORE_FP32     */
 } cakf_problem;
 
 typedef struct cakf_ctx cakf_ctx;   /* library-owned state; holds the stored factors */
@@ -123,7 +139,9 @@ typedef struct {
          evaluations; low-rank correction)
      [4] smoother combine and outputs (Z, P X, ws)
      [5] smoother truncation (Gram identities, FP64 eig, rotation)
-     [6] NLL term per step (side stream: overlaps [2])        [7] reserved               */
+     [6] NLL term per step (side stream: overlaps [2])
+     [7] restoring stored factors for the smoother / gradient pass (recomputation of filter
+         segments, or BF16 unpacking); zero with CAKF_STORE_FP32                              */
   double phase_ms[8];
   /* summed device time of the eigensolver's parts (profiling on): [0] tridiagonalisation,
      [1] divide & conquer, [2] back-transformation and conversion of the kept vectors      */

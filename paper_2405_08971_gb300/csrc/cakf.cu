@@ -10,7 +10,6 @@
 //   S[k]     m_k x i_k actions
 //   mf, vf   (T+1) x n filter means / variances (FP64)
 #include <cstring>
-#include <cstdlib>
 #include <cstdio>
 #include <string>
 #include <vector>
@@ -129,6 +128,14 @@ struct cakf_ctx {
   size_t gsmall_elems = 0;
   double* ms_dev = nullptr;   // smoother outputs when the caller passes host arrays
   double* vs_dev = nullptr;
+  // factor storage between the filter and the smoother / gradient pass: seg_c = 0 keeps every step
+  // resident; otherwise the pools are rings of seg_c steps (M: seg_c + 1 slots) and the steps
+  // [res_a, res_b] are resident; RECOMPUTE keeps M+ and lam at every segment start, STORE_BF16
+  // keeps BF16 copies of every step's factors
+  int storage = CAKF_STORE_FP32, ckpt_req = 0, seg_c = 0, res_a = 1, res_b = 0;
+  void* ckptM = nullptr;
+  double* ckpt_lam = nullptr;
+  void *Mh = nullptr, *PVh = nullptr, *KVh = nullptr, *Vh = nullptr;
   // state
   bool filtered = false;
   long long launch_base = 0;
@@ -245,6 +252,13 @@ int plan_and_alloc(cakf_ctx* c, const cakf_problem* p) {
 
   const size_t es = elem_size(c->precision);
   const size_t ldn = c->ldn;
+  c->storage = p->factor_storage;
+  c->ckpt_req = p->checkpoint_every;
+  c->seg_c = 0;
+  if (c->storage != CAKF_STORE_FP32) {
+    const int seg = p->checkpoint_every > 0 ? p->checkpoint_every : 20;
+    c->seg_c = seg < T ? seg : 0;   // a segment as long as the series keeps every step resident
+  }
   // per-step pools
   c->off_M.assign(T + 2, 0);
   c->off_PV.assign(T + 2, 0);
@@ -267,10 +281,28 @@ int plan_and_alloc(cakf_ctx* c, const cakf_problem* p) {
   if (c->has_mu && (rc = c->alloc(c->mu, (size_t)(T + 1) * n * sizeof(double)))) return rc;
   if ((rc = c->alloc(c->mf, (size_t)(T + 1) * n * sizeof(double)))) return rc;
   if ((rc = c->alloc(c->vf, (size_t)(T + 1) * n * sizeof(double)))) return rc;
-  if ((rc = c->alloc(c->Mpool, c->off_M[T + 1] * es))) return rc;
-  if ((rc = c->alloc(c->PVpool, c->off_PV[T + 1] * es))) return rc;
-  if ((rc = c->alloc(c->KVpool, c->off_PV[T + 1] * es))) return rc;
-  if ((rc = c->alloc(c->Vpool, c->off_V[T + 1] * es))) return rc;
+  if (c->seg_c == 0) {
+    if ((rc = c->alloc(c->Mpool, c->off_M[T + 1] * es))) return rc;
+    if ((rc = c->alloc(c->PVpool, c->off_PV[T + 1] * es))) return rc;
+    if ((rc = c->alloc(c->KVpool, c->off_PV[T + 1] * es))) return rc;
+    if ((rc = c->alloc(c->Vpool, c->off_V[T + 1] * es))) return rc;
+  } else {
+    const size_t sc = c->seg_c, rmx = std::max(c->rmax, 1), ip = c->imax + 1;
+    if ((rc = c->alloc(c->Mpool, (sc + 1) * ldn * rmx * es))) return rc;
+    if ((rc = c->alloc(c->PVpool, sc * ldn * ip * es))) return rc;
+    if ((rc = c->alloc(c->KVpool, sc * ldn * ip * es))) return rc;
+    if ((rc = c->alloc(c->Vpool, sc * (size_t)std::max(c->mmax, 1) * ip * es))) return rc;
+    if (c->storage == CAKF_RECOMPUTE) {
+      const size_t nck = (size_t)(T - 1) / sc + 1;
+      if ((rc = c->alloc(c->ckptM, nck * ldn * rmx * es))) return rc;
+      if ((rc = c->alloc(c->ckpt_lam, nck * rmx * sizeof(double)))) return rc;
+    } else {
+      if ((rc = c->alloc(c->Mh, c->off_M[T + 1] * 2))) return rc;
+      if ((rc = c->alloc(c->PVh, c->off_PV[T + 1] * 2))) return rc;
+      if ((rc = c->alloc(c->KVh, c->off_PV[T + 1] * 2))) return rc;
+      if ((rc = c->alloc(c->Vh, c->off_V[T + 1] * 2))) return rc;
+    }
+  }
   if ((rc = c->alloc(c->Spool, c->off_S[T + 1] * es))) return rc;
   if (c->replay) {
     c->off_rep.assign(T + 2, 0);
@@ -309,7 +341,7 @@ int plan_and_alloc(cakf_ctx* c, const cakf_problem* p) {
   if ((rc = c->alloc(c->dots, (B + 8) * sizeof(double)))) return rc;
   if ((rc = c->alloc(c->dots2, (B + 8) * sizeof(double)))) return rc;
   if ((rc = c->alloc(c->dpart, cg_dpart_elems((int)mm, B) * sizeof(double)))) return rc;
-  c->part64_elems = std::max<size_t>(size_t(1) << 22, NE * NE * 4);
+  c->part64_elems = std::max<size_t>(size_t(1) << 24, NE * NE * 4);   // partial tiles of the split-K products
   if ((rc = c->alloc(c->part64, c->part64_elems * sizeof(double)))) return rc;
   if ((rc = c->alloc(c->gram, NE * NE * sizeof(double)))) return rc;
   c->small_elems = 8 * (NE * (size_t)wmax + NE * NE) + 64;
@@ -387,8 +419,9 @@ struct Runner {
   int tc_kind;  // 0 BF16, 1 split FP16 (three MMAs per slice)
 
   // phase timers (profiling on): begin returns the start event, end records the pair
+  bool quiet = false;   // no phase timers (recomputation inside the smoother or gradient pass)
   cudaEvent_t ph_begin() {
-    if (!c->profiling) return nullptr;
+    if (!c->profiling || quiet) return nullptr;
     cudaEvent_t e = c->ev();
     cudaEventRecord(e, st);
     return e;
@@ -400,10 +433,94 @@ struct Runner {
     c->prof_phase.push_back({id, {e0, e1}});
   }
 
-  T* Mk(int k) { return (T*)c->Mpool + c->off_M[k]; }
-  T* PV(int k) { return (T*)c->PVpool + c->off_PV[k]; }
-  T* KV(int k) { return (T*)c->KVpool + c->off_PV[k]; }
-  T* Vk(int k) { return (T*)c->Vpool + c->off_V[k]; }
+  // per-step factors: exact offsets when every step is resident, ring slots otherwise
+  T* Mk(int k) {
+    return c->seg_c ? (T*)c->Mpool + (size_t)(k % (c->seg_c + 1)) * c->ldn * std::max(c->rmax, 1)
+                    : (T*)c->Mpool + c->off_M[k];
+  }
+  T* PV(int k) {
+    return c->seg_c ? (T*)c->PVpool + (size_t)(k % c->seg_c) * c->ldn * (c->imax + 1) : (T*)c->PVpool + c->off_PV[k];
+  }
+  T* KV(int k) {
+    return c->seg_c ? (T*)c->KVpool + (size_t)(k % c->seg_c) * c->ldn * (c->imax + 1) : (T*)c->KVpool + c->off_PV[k];
+  }
+  T* Vk(int k) {
+    return c->seg_c ? (T*)c->Vpool + (size_t)(k % c->seg_c) * std::max(c->mmax, 1) * (c->imax + 1)
+                    : (T*)c->Vpool + c->off_V[k];
+  }
+
+  // ---------------------------------------------------------------- factor storage
+  // M+_k and its eigenvalues at the start of a RECOMPUTE segment (k = a - 1, a multiple of seg_c)
+  void save_checkpoint(int k) {
+    const size_t j = (size_t)k / c->seg_c, rmx = std::max(c->rmax, 1);
+    const int cols = c->mcols[k];
+    if (cols > 0) {
+      cudaMemcpyAsync((T*)c->ckptM + j * c->ldn * rmx, Mk(k), (size_t)c->ldn * cols * sizeof(T),
+                      cudaMemcpyDeviceToDevice, st);
+      cudaMemcpyAsync(c->ckpt_lam + j * rmx, c->lam, cols * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    }
+  }
+  // BF16 copies of step k's factors (STORE_BF16)
+  void pack_history(int k) {
+    if (sizeof(T) != 4) return;
+    const int ldn = c->ldn, ic = c->icap[k];
+    if (k == 1) pack_one(0);
+    pack_one(k);
+    if (mk(k) > 0 && ic > 0) {
+      to_bf16((const float*)PV(k), ldn, c->n, ic + 1, (uint16_t*)c->PVh + c->off_PV[k], ldn, st);
+      to_bf16((const float*)KV(k), ldn, c->n, ic + 1, (uint16_t*)c->KVh + c->off_PV[k], ldn, st);
+      to_bf16((const float*)Vk(k), mk(k), mk(k), ic + 1, (uint16_t*)c->Vh + c->off_V[k], mk(k), st);
+    }
+  }
+  void pack_one(int k) {
+    if (c->mcols[k] > 0)
+      to_bf16((const float*)Mk(k), c->ldn, c->n, c->mcols[k], (uint16_t*)c->Mh + c->off_M[k], c->ldn, st);
+  }
+  // Make the factors of filter step k (1..T) and M+_{k-1} resident in the rings: the segment of
+  // seg_c steps holding k is recomputed from its checkpoint with the stored actions (RECOMPUTE)
+  // or unpacked from the BF16 copies (STORE_BF16).
+  int restore(int k) {
+    if (!c->seg_c || (k >= c->res_a && k <= c->res_b)) return CAKF_OK;
+    const int sc = c->seg_c;
+    const int a0 = ((k - 1) / sc) * sc + 1, b0 = std::min(c->T, a0 + sc - 1);
+    cudaEvent_t ph7 = ph_begin();
+    const bool q = quiet;
+    quiet = true;
+    if (c->storage == CAKF_RECOMPUTE) {
+      const size_t j = (size_t)(a0 - 1) / sc, rmx = std::max(c->rmax, 1);
+      const int cols = c->mcols[a0 - 1];
+      if (cols > 0) {
+        cudaMemcpyAsync(Mk(a0 - 1), (T*)c->ckptM + j * c->ldn * rmx, (size_t)c->ldn * cols * sizeof(T),
+                        cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(c->lam, c->ckpt_lam + j * rmx, cols * sizeof(double), cudaMemcpyDeviceToDevice, st);
+        rowsumsq<T>(Mk(a0 - 1), c->ldn, c->n, cols, 0.0, c->rs_plus, st);
+      } else {
+        cudaMemsetAsync(c->rs_plus, 0, c->n * sizeof(double), st);
+      }
+      for (int kk = a0; kk <= b0; ++kk) {
+        int rc = filter_step(kk, true, nullptr);
+        if (rc) { quiet = q; return rc; }
+      }
+    } else if (sizeof(T) == 4) {
+      const int ldn = c->ldn;
+      for (int kk = a0 - 1; kk <= b0; ++kk)
+        if (c->mcols[kk] > 0)
+          from_bf16((const uint16_t*)c->Mh + c->off_M[kk], ldn, c->n, c->mcols[kk], (float*)Mk(kk), ldn, st);
+      for (int kk = a0; kk <= b0; ++kk) {
+        const int ic = c->icap[kk];
+        if (mk(kk) == 0 || ic == 0) continue;
+        from_bf16((const uint16_t*)c->PVh + c->off_PV[kk], ldn, c->n, ic + 1, (float*)PV(kk), ldn, st);
+        from_bf16((const uint16_t*)c->KVh + c->off_PV[kk], ldn, c->n, ic + 1, (float*)KV(kk), ldn, st);
+        from_bf16((const uint16_t*)c->Vh + c->off_V[kk], mk(kk), mk(kk), ic + 1, (float*)Vk(kk), mk(kk), st);
+      }
+    }
+    quiet = q;
+    ph_end(7, ph7);
+    c->res_a = a0;
+    c->res_b = b0;
+    cudaError_t ce = cudaGetLastError();
+    return ce == cudaSuccess ? CAKF_OK : fail(CAKF_ERR_CUDA, std::string("restoring factors: ") + cudaGetErrorString(ce));
+  }
   T* Sk(int k) { return (T*)c->Spool + c->off_S[k]; }
   int mk(int k) { return c->obs_ptr[k] - c->obs_ptr[k - 1]; }
   const int* obs(int k) { return c->obs + c->obs_ptr[k - 1]; }
@@ -439,8 +556,7 @@ struct Runner {
 
   // ---------------------------------------------------------------- filter (Alg. 1)
   int filter() {
-    const int n = c->n, T_ = c->T, ldn = c->ldn;
-    const double a = c->a, a2 = a * a;
+    const int n = c->n, T_ = c->T;
     cudaMemsetAsync(c->err, 0, sizeof(int), st);
     cudaMemsetAsync(c->rs_plus, 0, n * sizeof(double), st);
     cudaMemsetAsync(c->nll, 0, (T_ + 1) * sizeof(double), st);
@@ -454,15 +570,42 @@ struct Runner {
       cudaMemcpyAsync(c->vf, sfv.data(), n * sizeof(double), cudaMemcpyHostToDevice, st);
       cudaStreamSynchronize(st);
     }
-    const int B = std::max(c->budget, c->imax);
-    const double bd_tol = (sizeof(T) == 8) ? 1e-12 : 1e-6;
     bool nll_pending = false;   // an NLL term is in flight on the side stream
+    c->res_a = 1;
+    c->res_b = 0;
     for (int k = 1; k <= T_; ++k) {
-      const int m = mk(k), ic = c->icap[k], rp = c->mcols[k - 1];
       if (nll_pending) {
         cudaStreamWaitEvent(st, c->ev_join, 0);
         nll_pending = false;
       }
+      if (c->seg_c && c->storage == CAKF_RECOMPUTE && (k - 1) % c->seg_c == 0) save_checkpoint(k - 1);
+      int rc = filter_step(k, false, &nll_pending);
+      if (rc) return rc;
+      if (c->seg_c && c->storage == CAKF_STORE_BF16) pack_history(k);
+      cudaError_t ce = cudaGetLastError();
+      if (ce != cudaSuccess) return fail(CAKF_ERR_CUDA, std::string("filter step: ") + cudaGetErrorString(ce));
+    }
+    if (nll_pending) cudaStreamWaitEvent(st, c->ev_join, 0);
+    if (c->seg_c) {   // the ring holds the last segment
+      c->res_a = T_ >= 1 ? ((T_ - 1) / c->seg_c) * c->seg_c + 1 : 1;
+      c->res_b = T_;
+    } else {
+      c->res_a = 1;
+      c->res_b = T_;
+    }
+    return CAKF_OK;
+  }
+
+  // One filter step k (Alg. 1: predict, iterative update, finalize, Truncate).  With recompute the
+  // step is re-run from the actions stored by the first pass (replayed from the action pool, no
+  // NLL term, no phase timers): the same kernels on the same inputs give the same factors.
+  int filter_step(int k, bool recompute, bool* nll_pending) {
+    const int n = c->n, ldn = c->ldn;
+    const double a = c->a, a2 = a * a;
+    const int B = std::max(c->budget, c->imax);
+    const double bd_tol = (sizeof(T) == 8) ? 1e-12 : 1e-6;
+    {
+      const int m = mk(k), ic = c->icap[k], rp = c->mcols[k - 1];
       const double* mprev = c->mf + (size_t)(k - 1) * n;
       double* mout = c->mf + (size_t)k * n;
       double* vout = c->vf + (size_t)k * n;
@@ -474,7 +617,7 @@ struct Runner {
         scale_copy<T>(Mk(k - 1), ldn, n, rp, T(a), Mk(k), ldn, st);
         if (rp > 0) rowsumsq<T>(Mk(k), ldn, n, rp, 0.0, c->rs_plus, st);
         scale_f64(c->lam, rp, rp, 1, a2, st);   // lam_k = a^2 lam_{k-1}
-        continue;
+        return CAKF_OK;
       }
       const int* ob = obs(k);
       C4<T>* Xo = (C4<T>*)c->Xo;
@@ -500,7 +643,7 @@ struct Runner {
       // rtol threshold needs ||r0||^2: read back once per step only when requested
       double rtol2 = 0.0;
       int use_rtol = 0;
-      if (c->cg_rtol > 0 && !c->replay) {
+      if (c->cg_rtol > 0 && !c->replay && !recompute) {
         double r0sq = 0;
         cudaMemcpyAsync(&r0sq, c->r0sq, sizeof(double), cudaMemcpyDeviceToHost, st);
         cudaStreamSynchronize(st);
@@ -508,25 +651,27 @@ struct Runner {
         use_rtol = 1;
       }
       const int nsplit = gram_matvec_slots(m);
-      const double* rep = c->replay ? c->rep + c->off_rep[k] : nullptr;
+      const double* rep = (c->replay && !recompute) ? c->rep + c->off_rep[k] : nullptr;
       T* Qa = (T*)c->Qa;       // orthonormal basis of the previous actions (CG policy only)
       // Re-orthogonalising each action against the previous ones leaves span(S) -- and so every
       // output -- unchanged; it keeps S^T S well conditioned for the NLL's FP64 Cholesky, which the
       // FP64 mode's 1e-9 agreement needs.  The FP32-based modes need it only when the budget is a
       // large share of the observations (4 i >= m): there CG can converge within the budget and
       // the later residuals, at FP32 rounding level, are no longer independent of the earlier ones.
-      const bool reorth = !rep && (sizeof(T) == 8 || 4 * ic >= m || getenv("CAKF_EXP_REORTH"));
+      // (a recomputed step takes every action from its stored column: no selection, no reorth)
+      const bool reorth = !rep && !recompute && (sizeof(T) == 8 || 4 * ic >= m);
       // CG policy without re-orthogonalisation: k_cg_upd2 writes the next action (the updated
       // residual) itself, so the selection runs only for the first action
-      const bool fused_select = !rep && !reorth;
+      const bool fused_select = !rep && !reorth && !recompute;
       T* dpart1 = (T*)c->dpart;
       T* dpart2 = dpart1 + (size_t)(B + 4) * ((m + 31) / 32);
       for (int j = 0; j < ic; ++j) {
         T* g = GSk + (size_t)j * m;
-        if (!fused_select || j == 0) cg_select<T>(j, r, rep, m, s, Sk(k), m, c->active, st);
+        if (recompute) cg_select<T>(j, Sk(k) + (size_t)j * m, nullptr, m, s, Sk(k), m, c->active, st);
+        else if (!fused_select || j == 0) cg_select<T>(j, r, rep, m, s, Sk(k), m, c->active, st);
         if (reorth) cg_reorth<T>(Qa, m, j, s, m, c->dots2, Sk(k), m, c->active, st);
         cudaEvent_t e0 = nullptr, e1 = nullptr;
-        bool prof = c->profiling && (j % 8 == 0);
+        bool prof = c->profiling && !recompute && (j % 8 == 0);
         if (prof) { e0 = c->ev(); e1 = c->ev(); cudaEventRecord(e0, st); }
         gram_matvec<T>(c->kernel, Xo, s, m, T(c->sf2), (T*)c->part, Mo, m, rp, (T*)c->tv, c->active, st);
         if (prof) {
@@ -559,7 +704,7 @@ struct Runner {
       // NLL term from its definition: S^T G S (with the stored G s_j), S^T S and S^T r0, FP64 Cholesky.
       // It reads only this step's actions, G S and r0, so it runs on the side stream while the
       // truncation below runs here; the next step waits for it before the CG reuses those buffers.
-      {
+      if (!recompute) {
         cudaEventRecord(c->ev_fork, st);
         cudaStreamWaitEvent(c->st_nll, c->ev_fork, 0);
         cudaStream_t s2 = c->st_nll;
@@ -582,7 +727,7 @@ struct Runner {
           c->prof_phase.push_back({6, {ph6, e1}});
         }
         cudaEventRecord(c->ev_join, s2);
-        nll_pending = true;
+        *nll_pending = true;
       }
       // Truncate (Sec. 3.2)
       cudaEvent_t ph2 = ph_begin();
@@ -592,7 +737,6 @@ struct Runner {
       cudaError_t ce = cudaGetLastError();
       if (ce != cudaSuccess) return fail(CAKF_ERR_CUDA, std::string("filter step: ") + cudaGetErrorString(ce));
     }
-    if (nll_pending) cudaStreamWaitEvent(st, c->ev_join, 0);
     return CAKF_OK;
   }
 
@@ -677,6 +821,7 @@ struct Runner {
     T* wn = (T*)c->wsB;
     double* Gw = c->Gws;
     double* Gn = c->Gws2;
+    if (int rc = restore(T_)) return rc;
     // Ws_T = H^T V_T, ws_T = H^T v_T
     int cw = c->icap[T_];
     cudaMemsetAsync(ws, 0, ldn * sizeof(T), st);
@@ -698,6 +843,8 @@ struct Runner {
     if (cw > 0) cudaMemcpyAsync(KW, KV(T_), (size_t)ldn * (cw + 1) * sizeof(T), cudaMemcpyDeviceToDevice, st);
     else cudaMemsetAsync(KW, 0, (size_t)ldn * sizeof(T), st);
     for (int k = T_ - 1; k >= 0; --k) {
+      if (k >= 1)
+        if (int rc = restore(k)) return rc;
       // X = A^T [Ws ws] = a [Ws ws]
       cudaEvent_t ph3 = ph_begin();
       build_x<T>(Ws, ldn, cw, ws, T(a), n, Xs, ldn, st);
@@ -844,6 +991,7 @@ struct Runner {
     cudaMemsetAsync(dm, 0, (size_t)NP * n * sizeof(double), st);
     const size_t estride = (size_t)ldn * (c->imax + 1);
     for (int k = 1; k <= T_; ++k) {
+      if (int rc = restore(k)) return rc;
       const int m = mk(k), icap = c->icap[k], rp = c->mcols[k - 1];
       const int ic = (m > 0 && icap > 0) ? cnt[k] : 0;
       const double* mprev = c->mf + (size_t)(k - 1) * n;
@@ -1033,6 +1181,11 @@ int validate(const cakf_problem* p) {
     if (!std::isfinite(h) || std::fabs(h) > 80) return fail(CAKF_ERR_ARG, "hyperparameters must be finite");
   if (!(p->dt > 0) || !std::isfinite(p->dt)) return fail(CAKF_ERR_ARG, "dt must be > 0");
   if (!(p->cg_rtol >= 0)) return fail(CAKF_ERR_ARG, "cg_rtol must be >= 0");
+  if (p->factor_storage < CAKF_STORE_FP32 || p->factor_storage > CAKF_RECOMPUTE)
+    return fail(CAKF_ERR_ARG, "unknown factor_storage");
+  if (p->factor_storage == CAKF_STORE_BF16 && p->precision == CAKF_FP64)
+    return fail(CAKF_ERR_ARG, "CAKF_STORE_BF16 needs an FP32-based precision");
+  if (p->checkpoint_every < 0) return fail(CAKF_ERR_ARG, "checkpoint_every must be >= 0");
   if (p->replay_actions && !p->replay_counts) return fail(CAKF_ERR_ARG, "replay_actions without replay_counts");
   if (p->replay_counts) {
     for (int k = 1; k <= p->T; ++k) {
@@ -1063,7 +1216,8 @@ int validate(const cakf_problem* p) {
 
 bool same_shape(const cakf_ctx* c, const cakf_problem* p) {
   if (c->n != p->n || c->T != p->T || c->budget != p->budget_i || c->rank_r != p->rank_r ||
-      c->precision != p->precision || c->has_mu != (p->prior_mean != nullptr) || c->replay != (p->replay_actions != nullptr))
+      c->precision != p->precision || c->has_mu != (p->prior_mean != nullptr) || c->replay != (p->replay_actions != nullptr) ||
+      c->storage != p->factor_storage || c->ckpt_req != p->checkpoint_every)
     return false;
   for (int k = 0; k <= p->T; ++k)
     if (c->obs_ptr[k] != p->obs_ptr[k]) return false;

@@ -1060,7 +1060,9 @@ int gemm_tc_launch(int transA, int Mr, int N, int K, float alpha, const float* A
   if (force_split || base_units < slots) {
     const size_t per_chunk = (size_t)N * P.Mpad;
     const int cap = part ? (int)std::min<size_t>(4096, part_floats / std::max<size_t>(per_chunk, 1)) : 1;
-    const int want = std::max(1, (slots + base_units - 1) / base_units);
+    // enough chunks to fill the GPU, and at most 64 slices (1,024 K values) per chunk so that the
+    // FP32 accumulation chains in TMEM stay short; the chunks are summed in FP64
+    const int want = std::max((slots + base_units - 1) / base_units, (P.nk + 63) / 64);
     kchunks = std::max(1, std::min({want, cap, std::max(1, P.nk / 4)}));
     if (force_split && cap < 1) return 11;
   }

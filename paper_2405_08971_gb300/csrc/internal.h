@@ -97,6 +97,8 @@ void scale_f64(double* A, int ld, int rows, int cols, double s, cudaStream_t st)
 template <class T>
 void convert_from_f64(const double* In, int ldi, int rows, int cols, T* Out, int ldo, cudaStream_t st);
 void convert_to_f64(const float* In, int ldi, int rows, int cols, double* Out, int ldo, cudaStream_t st);
+void to_bf16(const float* In, int ldi, int rows, int cols, uint16_t* Out, int ldo, cudaStream_t st);
+void from_bf16(const uint16_t* In, int ldi, int rows, int cols, float* Out, int ldo, cudaStream_t st);
 
 // Record msg as the calling thread's cakf_last_error message; returns code.
 int set_last_error(int code, const char* msg);

@@ -5,6 +5,7 @@
 //   - the CG / Gram-Schmidt bookkeeping of the iterative update step
 //   - gathers, scatters and row epilogues of the filter and smoother.
 #include "common.cuh"
+#include <cuda_bf16.h>
 #include "internal.h"
 
 #include <atomic>
@@ -1381,6 +1382,31 @@ __global__ void k_axpby_f32_f64(const float* __restrict__ X, int ldx, int rows, 
   if (i >= rows || c >= cols) return;
   double* p = C + (size_t)c * ldc + i;
   *p = alpha * double(X[(size_t)c * ldx + i]) + (beta != 0.0 ? beta * *p : 0.0);
+}
+
+// FP32 <-> BF16 (round to nearest even) copies of column-major blocks, for the BF16 factor store
+__global__ void k_to_bf16(const float* __restrict__ In, int ldi, int rows, int cols, uint16_t* __restrict__ Out,
+                          int ldo) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.y;
+  if (i >= rows || c >= cols) return;
+  const __nv_bfloat16 b = __float2bfloat16_rn(In[(size_t)c * ldi + i]);
+  Out[(size_t)c * ldo + i] = *reinterpret_cast<const uint16_t*>(&b);
+}
+__global__ void k_from_bf16(const uint16_t* __restrict__ In, int ldi, int rows, int cols, float* __restrict__ Out,
+                            int ldo) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.y;
+  if (i >= rows || c >= cols) return;
+  Out[(size_t)c * ldo + i] = __uint_as_float((uint32_t)In[(size_t)c * ldi + i] << 16);
+}
+void to_bf16(const float* In, int ldi, int rows, int cols, uint16_t* Out, int ldo, cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return;
+  k_to_bf16<<<dim3(cdiv(rows, 256), cols), 256, 0, st>>>(In, ldi, rows, cols, Out, ldo); note_launch();
+}
+void from_bf16(const uint16_t* In, int ldi, int rows, int cols, float* Out, int ldo, cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return;
+  k_from_bf16<<<dim3(cdiv(rows, 256), cols), 256, 0, st>>>(In, ldi, rows, cols, Out, ldo); note_launch();
 }
 
 void convert_to_f64(const float* In, int ldi, int rows, int cols, double* Out, int ldo, cudaStream_t st) {
