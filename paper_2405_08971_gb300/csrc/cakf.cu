@@ -586,9 +586,12 @@ struct Runner {
       if (ce != cudaSuccess) return fail(CAKF_ERR_CUDA, std::string("filter step: ") + cudaGetErrorString(ce));
     }
     if (nll_pending) cudaStreamWaitEvent(st, c->ev_join, 0);
-    if (c->seg_c) {   // the ring holds the last segment
+    if (c->seg_c && c->storage == CAKF_RECOMPUTE) {   // the ring holds the last segment
       c->res_a = T_ >= 1 ? ((T_ - 1) / c->seg_c) * c->seg_c + 1 : 1;
       c->res_b = T_;
+    } else if (c->seg_c) {   // BF16 store: every segment is read back from the BF16 copies
+      c->res_a = 1;
+      c->res_b = 0;
     } else {
       c->res_a = 1;
       c->res_b = T_;
