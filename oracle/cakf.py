@@ -20,6 +20,10 @@ Smoothing"):
   the small Gram M^T M, same eigenvectors up to the map u -> M u).
 * Smoother: Alg. 3 (CAKS), the inverse-free RTS recursion in downdate form
   (Prop. "Inverse-free RTS smoother").
+* Block policies: the batch update (Alg. 2, "CAKF Update Step"): the actions S are chosen once
+  per step, Ghat = S^T (H P^- H^T + R) S, W = H^T S lsqrt(Ghat^+), w = H^T S Ghat^+ S^T (y - H m^-),
+  with coordinate actions (unit vectors at a space-filling subset of the observations) or given
+  actions (e.g. Gaussian sketches drawn by the caller) -- the policy appendix.
 * NLL: not in the paper (named as future work at the end of the conclusion).
   Defined here as the negative log density of the projected data S_k^T y_k
   under the modified observation model (eq. proj-observation), in Euclidean-
@@ -44,6 +48,10 @@ Readings taken where the paper is ambiguous, garbled or silent:
      P_k = K - M_k M_k^T) and the predicted P^-_k = K - a^2 M+_{k-1} M+_{k-1}^T.
   R7 smoother loop k = T-1 .. 0 with w_0 = 0, W_0 empty.
   R9 Matern kernels in the Rasmussen-Williams form, output scale = variance.
+  R18 coordinate policy: the space-filling subset is read as i observations evenly spaced through
+     the step's observation list (sorted grid indices, i.e. raster order of the grid): positions
+     floor((q + 1/2) m_k / i), q = 0..i-1; the left square root of Ghat^+ is L^-T with
+     L L^T = Ghat (Cholesky; Ghat is positive definite for distinct coordinates and noise > 0).
 """
 from __future__ import annotations
 
@@ -204,6 +212,42 @@ def update_iterative(model: Model, m_pred, M_pred, obs, y, budget, cg_rtol=0.0, 
     return m_new, M_hat, w, W, S, V, G, r0
 
 
+def coordinate_actions(m: int, i: int) -> np.ndarray:
+    """Coordinate policy (policy appendix, reading R18): m x i unit vectors at observation positions
+    floor((q + 1/2) m / i), q = 0..i-1 (i <= m)."""
+    i = min(i, m)
+    S = np.zeros((m, i))
+    for q in range(i):
+        S[int((q + 0.5) * m / i), q] = 1.0
+    return S
+
+
+def update_batch(model: Model, m_pred, M_pred, obs, y, S):
+    """CAKF update step, batch version (Alg. 2) with the actions S (m x i) chosen up front.
+
+    Ghat = S^T G S with G = H P^- H^T + sigma_n^2 I (dense here), W = H^T S L^-T (L L^T = Ghat),
+    w = H^T S Ghat^-1 S^T r0.  Returns the same tuple as update_iterative."""
+    n = model.n
+    mo = len(obs)
+    Ko = model.K_times(np.eye(mo), rows=obs, cols=obs)
+    Mo = M_pred[obs]
+    G = Ko - Mo @ Mo.T + model.sn2 * np.eye(mo)
+    r0 = y - m_pred[obs]
+    Gh = S.T @ G @ S
+    L = np.linalg.cholesky(Gh)
+    V = np.linalg.solve(L, S.T).T                     # S L^-T: lsqrt of Ghat^+ applied to S
+    v = S @ np.linalg.solve(Gh, S.T @ r0)
+    Vv = np.concatenate([V, v[:, None]], axis=1)
+    PVv = model.K_times(Vv, cols=obs) - M_pred @ (Mo.T @ Vv)
+    m_new = m_pred + PVv[:, -1]
+    M_hat = np.concatenate([M_pred, PVv[:, :-1]], axis=1)
+    w = np.zeros(n)
+    w[obs] = v
+    W = np.zeros((n, V.shape[1]))
+    W[obs] = V
+    return m_new, M_hat, w, W, S, V, G, r0
+
+
 def _nll_step(G, S, r0):
     """Per-step NLL of the projected data (definition in the module docstring)."""
     j = S.shape[1]
@@ -219,8 +263,11 @@ def _nll_step(G, S, r0):
 
 
 def filter_run(w, model: Optional[Model] = None, budget=None, rank_r=None, cg_rtol=0.0,
-               S_replay=None, U_replay=None, keep_G=False) -> FilterResult:
-    """Alg. 1 (CAKF) over steps k = 1..T of a `synth.Workload`."""
+               S_replay=None, U_replay=None, keep_G=False, policy="cg", S_given=None) -> FilterResult:
+    """Alg. 1 (CAKF) over steps k = 1..T of a `synth.Workload`.
+
+    policy "cg": iterative update with CG actions (or S_replay); "coordinate": batch update (Alg. 2)
+    with coordinate actions; "given": batch update with the actions S_given[k] (m_k x i_k)."""
     model = model or model_from(w)
     budget = w.budget_i if budget is None else budget
     rank_r = w.rank_r if rank_r is None else rank_r
@@ -242,9 +289,13 @@ def filter_run(w, model: Optional[Model] = None, budget=None, rank_r=None, cg_rt
             m_new, M_hat = m_pred, M_pred
             wk, Wk, S, G, r0 = np.zeros(n), np.zeros((n, 0)), np.zeros((0, 0)), None, None
         else:
-            Srep = None if S_replay is None else S_replay[k]
-            m_new, M_hat, wk, Wk, S, V, G, r0 = update_iterative(
-                model, m_pred, M_pred, obs, w.yk(k), budget, cg_rtol, Srep)
+            if policy == "cg":
+                Srep = None if S_replay is None else S_replay[k]
+                m_new, M_hat, wk, Wk, S, V, G, r0 = update_iterative(
+                    model, m_pred, M_pred, obs, w.yk(k), budget, cg_rtol, Srep)
+            else:
+                Sb = coordinate_actions(len(obs), budget) if policy == "coordinate" else S_given[k]
+                m_new, M_hat, wk, Wk, S, V, G, r0 = update_batch(model, m_pred, M_pred, obs, w.yk(k), Sb)
             res.nll[k] = _nll_step(G, S, r0)
         m[k] = m_new
         var[k] = model.sf2 - np.sum(M_hat * M_hat, axis=1)

@@ -238,3 +238,16 @@ def small(n=200, dim=2, m=40, T=6, budget_i=8, rank_r=0, kernel=MATERN32, lx=0.3
         coords = rng.uniform(0, 1, size=(n, dim))
     return make(f"small-n{n}", coords, kernel, lx, lt, sf2, sn2, T, dt, m, budget_i=budget_i,
                 rank_r=rank_r, seed=seed, seasonal=seasonal, missing=missing, **kw)
+
+
+def gaussian_actions(w: Workload, seed: int = 0, budget_i: Optional[int] = None) -> list:
+    """Randomized actions of the policy appendix: for each step k an m_k x i_k matrix of i.i.d.
+    standard normal entries (i_k = min(budget, m_k)); entry [0] is an empty placeholder.  The
+    draws are inputs of the method, made here once and passed to both the oracle and the device."""
+    rng = np.random.default_rng(seed)
+    i = w.budget_i if budget_i is None else budget_i
+    out = [np.zeros((0, 0))]
+    for k in range(1, w.T + 1):
+        m = int(w.obs_ptr[k] - w.obs_ptr[k - 1])
+        out.append(rng.standard_normal((m, min(i, m))) if m else np.zeros((0, 0)))
+    return out

@@ -195,6 +195,45 @@ def test_breakdown_exit_stops_at_a_repeated_action():
     assert f.nll[1] == g.nll[1]
 
 
+def test_coordinate_policy_is_exact_conditioning_on_the_chosen_points():
+    """Batch update (Alg. 2) with coordinate actions: conditioning on the chosen subset of each
+    step's observations exactly, so without truncation it equals the dense Kalman filter / RTS
+    smoother run on the data of those points only (means, variances, NLL terms); with i = m it is the
+    full Kalman filter."""
+    w = synth.small(n=60, dim=2, m=14, T=4, budget_i=5, rank_r=0, seasonal=True, seed=51)
+    f = oracle.filter_run(w, policy="coordinate")
+    ms, vs, _ = oracle.smoother_run(w, f)
+    # the workload restricted to the coordinates the policy picks
+    idx, ys, ptr = [], [], [0]
+    for k in range(1, w.T + 1):
+        o, yk = w.obs(k), w.yk(k)
+        pos = np.nonzero(oracle.coordinate_actions(len(o), w.budget_i).sum(axis=1))[0]
+        idx.append(o[pos]); ys.append(yk[pos]); ptr.append(ptr[-1] + len(pos))
+    sub = w.with_(obs_idx=np.concatenate(idx).astype(np.int32), y=np.concatenate(ys),
+                  obs_ptr=np.array(ptr, dtype=np.int32))
+    ref = dense_ref.kf_rts(sub)
+    for got, exp in ((f.m, ref["mf"]), (f.var, ref["vf"]), (ms, ref["ms"]), (vs, ref["vs"])):
+        assert rel(got, exp) < 1e-9
+    assert np.allclose(f.nll, ref["nll"], rtol=1e-9, atol=1e-12)
+    full = oracle.filter_run(w.with_(budget_i=w.n), policy="coordinate")
+    kf = dense_ref.kf_rts(w)
+    assert rel(full.m, kf["mf"]) < 1e-9 and rel(full.var, kf["vf"]) < 1e-9
+
+
+def test_batch_update_equals_iterative_update_with_the_same_actions():
+    """Alg. 2 and the iterative update give the same filter (and NLL) for the same actions (the
+    paper's proposition on their equivalence): Gaussian actions drawn once, truncation active."""
+    w = synth.small(n=70, dim=2, m=16, T=5, budget_i=6, rank_r=10, seed=52)
+    S = synth.gaussian_actions(w, seed=7)
+    fb = oracle.filter_run(w, policy="given", S_given=S)
+    fi = oracle.filter_run(w, S_replay=S)
+    assert rel(fb.m, fi.m) < 1e-9 and rel(fb.var, fi.var) < 1e-9
+    assert np.allclose(fb.nll, fi.nll, rtol=1e-9, atol=1e-12)
+    mb, vb, _ = oracle.smoother_run(w, fb)
+    mi, vi, _ = oracle.smoother_run(w, fi)
+    assert rel(mb, mi) < 1e-9 and rel(vb, vi) < 1e-9
+
+
 def test_matern_against_sklearn():
     sk = pytest.importorskip("sklearn.gaussian_process.kernels")
     rng = np.random.default_rng(0)
