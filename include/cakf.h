@@ -70,6 +70,17 @@ enum {
                       (x = hi + lo, both tf32, no scaling), three MMAs: FP32-class products   */
 };
 
+/* How the actions S_k of a step are chosen (Sec. 3.3 and the policy appendix). */
+enum {
+  CAKF_POLICY_CG = 0,          /* iterative update, the action of iteration j is the current residual
+                                  (or replay_actions[j] when given)                               */
+  CAKF_POLICY_COORDINATE = 1,  /* batch update (Alg. 2) with unit-vector actions at min(i, m_k)
+                                  observations evenly spaced through the step's observation list
+                                  (positions floor((q + 1/2) m_k / i)); i <= 160                 */
+  CAKF_POLICY_BATCH = 2        /* batch update (Alg. 2) with the actions given in replay_actions
+                                  (e.g. Gaussian sketches drawn by the caller); i_k <= 160       */
+};
+
 /* Where the per-step factors the smoother and the gradient pass read (M+_k, [P^-W_k P^-w_k],
    K(X, X_o)[V_k v_k], [V_k v_k]) are kept between cakf_filter and cakf_smooth (memory O(n r) per
    step, Sec. 3.2). */
@@ -112,6 +123,7 @@ typedef struct {
   int32_t factor_storage;     /* CAKF_STORE_FP32 | CAKF_STORE_BF16 | CAKF_RECOMPUTE              */
   int32_t checkpoint_every;   /* segment length of CAKF_STORE_BF16 / CAKF_RECOMPUTE (the steps
                                  restored at a time; 0 = 20); ignored for CAKF_STORE_FP32     */
+  int32_t policy;             /* CAKF_POLICY_CG | CAKF_POLICY_COORDINATE | CAKF_POLICY_BATCH     */
 } cakf_problem;
 
 typedef struct cakf_ctx cakf_ctx;   /* library-owned state; holds the stored factors */

@@ -20,6 +20,8 @@ OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_NUMERIC, ERR_TIMEOUT, ERR_STATE = range(7)
 MATERN12, MATERN32, MATERN52 = 0, 1, 2
 STORE_FP32, STORE_BF16, RECOMPUTE = 0, 1, 2
 STORAGE = {"fp32": STORE_FP32, "bf16": STORE_BF16, "recompute": RECOMPUTE}
+POLICY_CG, POLICY_COORDINATE, POLICY_BATCH = 0, 1, 2
+POLICIES = {"cg": POLICY_CG, "coordinate": POLICY_COORDINATE, "batch": POLICY_BATCH}
 FP64, FP32, TF32, BF16, FP16X3, TF32X3 = 0, 1, 2, 3, 4, 5
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32": TF32, "bf16": BF16, "fp16x3": FP16X3, "tf32x3": TF32X3}
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_NUMERIC", 5: "ERR_TIMEOUT", 6: "ERR_STATE"}
@@ -33,7 +35,7 @@ class cakf_problem(C.Structure):
         ("obs_idx", C.c_void_p), ("y", C.c_void_p), ("prior_mean", C.c_void_p), ("budget_i", C.c_int32),
         ("rank_r", C.c_int32), ("cg_rtol", C.c_double), ("precision", C.c_int32),
         ("replay_actions", C.c_void_p), ("replay_counts", C.c_void_p), ("factor_storage", C.c_int32),
-        ("checkpoint_every", C.c_int32),
+        ("checkpoint_every", C.c_int32), ("policy", C.c_int32),
     ]
 
 
@@ -137,7 +139,7 @@ class Context:
 
 def make_problem(coords, kernel, log_lx, log_lt, log_sf2, log_sn2, T, dt, obs_ptr, obs_idx, y, budget_i, rank_r,
                  precision="fp32", prior_mean=None, cg_rtol=0.0, replay_actions=None, replay_counts=None,
-                 factor_storage="fp32", checkpoint_every=0):
+                 factor_storage="fp32", checkpoint_every=0, policy="cg"):
     """Build a cakf_problem; returns (struct, keepalive list)."""
     keep = []
     p = cakf_problem()
@@ -165,6 +167,7 @@ def make_problem(coords, kernel, log_lx, log_lt, log_sf2, log_sn2, T, dt, obs_pt
     p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     p.factor_storage = STORAGE[factor_storage] if isinstance(factor_storage, str) else int(factor_storage)
     p.checkpoint_every = int(checkpoint_every)
+    p.policy = POLICIES[policy] if isinstance(policy, str) else int(policy)
     if replay_actions is not None:
         ra = np.ascontiguousarray(replay_actions, dtype=np.float64)
         rc = np.ascontiguousarray(replay_counts, dtype=np.int32)
@@ -174,7 +177,7 @@ def make_problem(coords, kernel, log_lx, log_lt, log_sf2, log_sn2, T, dt, obs_pt
 
 
 def problem_from_workload(w, precision="fp32", cg_rtol=0.0, replay=None, budget_i=None, rank_r=None,
-                          factor_storage="fp32", checkpoint_every=0, **hp):
+                          factor_storage="fp32", checkpoint_every=0, policy="cg", **hp):
     """cakf_problem of a `synth.Workload`-like object (any object with the same fields)."""
     ra = rc = None
     if replay is not None:
@@ -184,7 +187,7 @@ def problem_from_workload(w, precision="fp32", cg_rtol=0.0, replay=None, budget_
                         w.obs_idx, w.y, w.budget_i if budget_i is None else budget_i,
                         w.rank_r if rank_r is None else rank_r, precision=precision, prior_mean=w.prior_mean,
                         cg_rtol=cg_rtol, replay_actions=ra, replay_counts=rc, factor_storage=factor_storage,
-                        checkpoint_every=checkpoint_every)
+                        checkpoint_every=checkpoint_every, policy=policy)
 
 
 def _out(arr, shape):

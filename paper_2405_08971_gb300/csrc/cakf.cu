@@ -133,6 +133,9 @@ struct cakf_ctx {
   // [res_a, res_b] are resident; RECOMPUTE keeps M+ and lam at every segment start, STORE_BF16
   // keeps BF16 copies of every step's factors
   int storage = CAKF_STORE_FP32, ckpt_req = 0, seg_c = 0, res_a = 1, res_b = 0;
+  int policy = CAKF_POLICY_CG;
+  void* GSb = nullptr;     // batch policies: G [S r0] (m x (i + 1))
+  double* Lb = nullptr;    // batch policies: Cholesky factor of S^T G S and z = L^-1 S^T r0
   void* ckptM = nullptr;
   double* ckpt_lam = nullptr;
   void *Mh = nullptr, *PVh = nullptr, *KVh = nullptr, *Vh = nullptr;
@@ -254,6 +257,7 @@ int plan_and_alloc(cakf_ctx* c, const cakf_problem* p) {
   const size_t ldn = c->ldn;
   c->storage = p->factor_storage;
   c->ckpt_req = p->checkpoint_every;
+  c->policy = p->policy;
   c->seg_c = 0;
   if (c->storage != CAKF_STORE_FP32) {
     const int seg = p->checkpoint_every > 0 ? p->checkpoint_every : 20;
@@ -304,6 +308,11 @@ int plan_and_alloc(cakf_ctx* c, const cakf_problem* p) {
     }
   }
   if ((rc = c->alloc(c->Spool, c->off_S[T + 1] * es))) return rc;
+  if (c->policy != CAKF_POLICY_CG) {
+    const size_t ib = std::max(c->imax, 1);
+    if ((rc = c->alloc(c->GSb, (size_t)std::max(c->mmax, 1) * (ib + 1) * es))) return rc;
+    if ((rc = c->alloc(c->Lb, (2 * ib * ib + 2 * ib + 16) * sizeof(double)))) return rc;
+  }
   if (c->replay) {
     c->off_rep.assign(T + 2, 0);
     for (int k = 0; k <= T; ++k) {
@@ -643,6 +652,9 @@ struct Runner {
         int one = 1;
         cudaMemcpyAsync(c->active, &one, sizeof(int), cudaMemcpyHostToDevice, st);
       }
+      if (c->policy != CAKF_POLICY_CG) {
+        if (int rcb = batch_update(k, m, ic, rp, Xo, Mo, V, GSk, recompute)) return rcb;
+      } else {
       // rtol threshold needs ||r0||^2: read back once per step only when requested
       double rtol2 = 0.0;
       int use_rtol = 0;
@@ -688,6 +700,7 @@ struct Runner {
         T* snext = (fused_select && j + 1 < ic) ? Sk(k) + (size_t)(j + 1) * m : nullptr;
         cg_upd2<T>(j, c->dots, dpart2, V, GV, m, r, vcol, s, reorth ? Qa : nullptr, m, bd_tol, rtol2, use_rtol,
                    c->active, c->eta + (size_t)k * B, c->alpha + (size_t)k * B, c->count + k, snext, st);
+      }
       }
       ph_end(0, ph0);
       // finalize: [P^- W, P^- w] = K(X, X_o) [V v] - a^2 M+ (M+_o^T [V v])
@@ -740,6 +753,42 @@ struct Runner {
       cudaError_t ce = cudaGetLastError();
       if (ce != cudaSuccess) return fail(CAKF_ERR_CUDA, std::string("filter step: ") + cudaGetErrorString(ce));
     }
+    return CAKF_OK;
+  }
+
+  // Batch update (Alg. 2) of step k: the ic actions S are fixed up front (coordinate actions, or
+  // the given ones; a recomputed step reuses the stored ones), G [S r0] = K(X_o, X_o)[S r0] + sn2 S -
+  // a^2 M_o (M_o^T S) with the Gram x block product (tensor cores in those modes), S^T G S = L L^T
+  // and z = L^-1 S^T r0 in FP64, then [V v] = [S L^-T, S L^-T z].  G S is kept for the NLL term.
+  int batch_update(int k, int m, int ic, int rp, const C4<T>* Xo, const T* Mo, T* V, T* GSk, bool recompute) {
+    const double a2 = c->a * c->a;
+    T* S = Sk(k);
+    if (!recompute) {
+      if (c->policy == CAKF_POLICY_COORDINATE) coord_actions<T>(m, ic, S, st);
+      else convert_from_f64<T>(c->rep + c->off_rep[k], m, m, ic, S, m, st);
+    }
+    T* Bsr = (T*)c->Xobs;
+    cudaMemcpyAsync(Bsr, S, (size_t)m * ic * sizeof(T), cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(Bsr + (size_t)ic * m, c->r0v, (size_t)m * sizeof(T), cudaMemcpyDeviceToDevice, st);
+    T* GSb = (T*)c->GSb;
+    if (int rcg = gram_block(Xo, m, Xo, m, Bsr, m, ic + 1, GSb, m)) return rcg;
+    if (rp > 0) {
+      double* t = c->small;
+      gemm_tn<T>(Mo, m, rp, S, m, ic, m, 1.0, 0.0, t, rp, c->part64, c->part64_elems, st);
+      gemm_nn<T, double>(m, ic, rp, T(-a2), Mo, m, t, rp, T(1), GSb, m, st);
+    }
+    axpy_block<T>(T(c->sn2), S, m, m, ic, GSb, m, st);
+    cudaMemcpyAsync(GSk, GSb, (size_t)m * ic * sizeof(T), cudaMemcpyDeviceToDevice, st);
+    const size_t ii = (size_t)ic * ic;
+    double* Gh = c->Lb;
+    double* L = Gh + ii;
+    double* yh = L + ii;
+    double* z = yh + ic;
+    gemm_tn<T>(S, m, ic, GSb, m, ic, m, 1.0, 0.0, Gh, ic, c->part64, c->part64_elems, st);
+    gemm_tn<T>(S, m, ic, (const T*)c->r0v, m, 1, m, 1.0, 0.0, yh, ic, c->part64, c->part64_elems, st);
+    if (batch_chol(Gh, ic, yh, L, z, c->err, st)) return fail(CAKF_ERR_ARG, "too many actions for the batch update");
+    batch_v<T>(S, m, ic, L, z, V, st);
+    cudaMemcpyAsync(c->count + k, &ic, sizeof(int), cudaMemcpyHostToDevice, st);
     return CAKF_OK;
   }
 
@@ -1189,11 +1238,20 @@ int validate(const cakf_problem* p) {
   if (p->factor_storage == CAKF_STORE_BF16 && p->precision == CAKF_FP64)
     return fail(CAKF_ERR_ARG, "CAKF_STORE_BF16 needs an FP32-based precision");
   if (p->checkpoint_every < 0) return fail(CAKF_ERR_ARG, "checkpoint_every must be >= 0");
+  if (p->policy < CAKF_POLICY_CG || p->policy > CAKF_POLICY_BATCH) return fail(CAKF_ERR_ARG, "unknown policy");
+  if (p->policy == CAKF_POLICY_BATCH && !p->replay_actions)
+    return fail(CAKF_ERR_ARG, "CAKF_POLICY_BATCH takes its actions from replay_actions");
+  if (p->policy == CAKF_POLICY_COORDINATE && p->replay_actions)
+    return fail(CAKF_ERR_ARG, "CAKF_POLICY_COORDINATE chooses its own actions (replay_actions must be NULL)");
+  if (p->policy == CAKF_POLICY_COORDINATE && p->budget_i > kBatchMaxActions)
+    return fail(CAKF_ERR_ARG, "the batch policies take at most 160 actions per step");
   if (p->replay_actions && !p->replay_counts) return fail(CAKF_ERR_ARG, "replay_actions without replay_counts");
   if (p->replay_counts) {
     for (int k = 1; k <= p->T; ++k) {
       int c = p->replay_counts[k], mk = p->obs_ptr[k] - p->obs_ptr[k - 1];
       if (c < 0 || c > mk || c > 1024) return fail(CAKF_ERR_ARG, "replay_counts out of range");
+      if (p->policy == CAKF_POLICY_BATCH && c > kBatchMaxActions)
+        return fail(CAKF_ERR_ARG, "the batch policies take at most 160 actions per step");
     }
   }
   // observation indices: range and distinctness per step (checked on a host copy)
@@ -1220,7 +1278,7 @@ int validate(const cakf_problem* p) {
 bool same_shape(const cakf_ctx* c, const cakf_problem* p) {
   if (c->n != p->n || c->T != p->T || c->budget != p->budget_i || c->rank_r != p->rank_r ||
       c->precision != p->precision || c->has_mu != (p->prior_mean != nullptr) || c->replay != (p->replay_actions != nullptr) ||
-      c->storage != p->factor_storage || c->ckpt_req != p->checkpoint_every)
+      c->storage != p->factor_storage || c->ckpt_req != p->checkpoint_every || c->policy != p->policy)
     return false;
   for (int k = 0; k <= p->T; ++k)
     if (c->obs_ptr[k] != p->obs_ptr[k]) return false;

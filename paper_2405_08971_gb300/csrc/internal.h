@@ -100,6 +100,14 @@ void convert_to_f64(const float* In, int ldi, int rows, int cols, double* Out, i
 void to_bf16(const float* In, int ldi, int rows, int cols, uint16_t* Out, int ldo, cudaStream_t st);
 void from_bf16(const uint16_t* In, int ldi, int rows, int cols, float* Out, int ldo, cudaStream_t st);
 
+// Batch update (Alg. 2): coordinate actions, Cholesky of the projected Gram with z = L^-1 S^T r0,
+// and [V v] = [S L^-T, S L^-T z].  At most kBatchMaxActions actions per step.
+constexpr int kBatchMaxActions = 160;
+template <class T> void coord_actions(int m, int i, T* S, cudaStream_t st);
+int batch_chol(const double* Gh, int i, const double* yh, double* L, double* z, int* err, cudaStream_t st);
+template <class T>
+void batch_v(const T* S, int m, int i, const double* L, const double* z, T* Vv, cudaStream_t st);
+
 // Record msg as the calling thread's cakf_last_error message; returns code.
 int set_last_error(int code, const char* msg);
 

@@ -1586,6 +1586,110 @@ void nll_def(const int* count, double* Gh, double* SS, int ld, const double* yh,
   k_nll_def<<<1, 256, 0, st>>>(count, Gh, SS, ld, yh, z, nll_k, err); note_launch();
 }
 
+// ------------------------------------------------------------------------------------------
+// Batch update (Alg. 2) helpers: the actions S are fixed up front, Ghat = S^T G S = L L^T,
+// W = H^T S L^-T, w = H^T S Ghat^-1 S^T r0.
+
+// Coordinate actions (reading R18 of the oracle): S = 0 except S[floor((q + 1/2) m / i), q] = 1.
+template <class T>
+__global__ void k_coord_actions(int m, int i, T* __restrict__ S) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= i) return;
+  const int row = (int)(((double)q + 0.5) * (double)m / (double)i);
+  S[(size_t)q * m + min(row, m - 1)] = T(1);
+}
+
+// Cholesky Ghat = L L^T (FP64, i x i, lower triangle of Ghat read symmetrised; L in shared memory,
+// written to Lout with ld i) and z = L^-1 yh.  One block.  A non-positive or non-finite pivot
+// raises the numeric error flag (the step's projected Gram must be positive definite).
+constexpr int BCH_THREADS = 256;
+__global__ void __launch_bounds__(BCH_THREADS)
+k_batch_chol(const double* __restrict__ Gh, int i, const double* __restrict__ yh, double* __restrict__ Lout,
+             double* __restrict__ z, int* __restrict__ err) {
+  extern __shared__ double bsm[];
+  double* L = bsm;                  // i x i, column-major
+  double* zz = bsm + (size_t)i * i;
+  __shared__ double piv;
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  for (int e = threadIdx.x; e < i * i; e += blockDim.x) {
+    const int r = e % i, c = e / i;
+    L[e] = r >= c ? 0.5 * (Gh[(size_t)c * i + r] + Gh[(size_t)r * i + c]) : 0.0;
+  }
+  for (int q = threadIdx.x; q < i; q += blockDim.x) zz[q] = yh[q];
+  __syncthreads();
+  for (int p = 0; p < i; ++p) {
+    if (threadIdx.x == 0) {
+      double d = L[(size_t)p * i + p];
+      if (!(d > 0.0) || !isfinite(d)) { bad = 1; d = 1.0; }
+      piv = sqrt(d);
+      L[(size_t)p * i + p] = piv;
+      zz[p] /= piv;
+    }
+    __syncthreads();
+    const double ip = 1.0 / piv, zp = zz[p];
+    for (int q = p + 1 + threadIdx.x; q < i; q += blockDim.x) {
+      const double lq = L[(size_t)p * i + q] * ip;
+      L[(size_t)p * i + q] = lq;
+      zz[q] -= lq * zp;
+    }
+    __syncthreads();
+    // trailing update of the lower triangle: column c, rows q >= c
+    const int w = i - p - 1;
+    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+      const int c = p + 1 + e / w, q = p + 1 + e % w;
+      if (q >= c) L[(size_t)c * i + q] -= L[(size_t)p * i + q] * L[(size_t)p * i + c];
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < i * i; e += blockDim.x) Lout[e] = L[e];
+  for (int q = threadIdx.x; q < i; q += blockDim.x) z[q] = zz[q];
+  if (threadIdx.x == 0 && bad) atomicExch(err, kErrNumeric);
+}
+
+// V = S L^-T (row by row: x L^T = s, forward substitution in FP64) into columns 0..i-1 of Vv, and
+// v = V z into column i.  One thread per row of S.
+template <class T>
+__global__ void k_batch_v(const T* __restrict__ S, int m, int i, const double* __restrict__ L,
+                          const double* __restrict__ z, T* __restrict__ Vv) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= m) return;
+  double x[160];
+  double v = 0.0;
+  for (int j = 0; j < i; ++j) {
+    double acc = (double)S[(size_t)j * m + row];
+    for (int l = 0; l < j; ++l) acc = fma(-x[l], L[(size_t)l * i + j], acc);
+    x[j] = acc / L[(size_t)j * i + j];
+    Vv[(size_t)j * m + row] = T(x[j]);
+    v = fma(x[j], z[j], v);
+  }
+  Vv[(size_t)i * m + row] = T(v);
+}
+
+template <class T>
+void coord_actions(int m, int i, T* S, cudaStream_t st) {
+  if (m <= 0 || i <= 0) return;
+  cudaMemsetAsync(S, 0, (size_t)m * i * sizeof(T), st);
+  k_coord_actions<T><<<cdiv(i, 128), 128, 0, st>>>(m, i, S); note_launch();
+}
+int batch_chol(const double* Gh, int i, const double* yh, double* L, double* z, int* err, cudaStream_t st) {
+  if (i <= 0) return 0;
+  if (i > kBatchMaxActions) return 1;
+  const size_t smem = ((size_t)i * i + i) * sizeof(double);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_batch_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_batch_chol<<<1, BCH_THREADS, smem, st>>>(Gh, i, yh, L, z, err); note_launch();
+  return 0;
+}
+template <class T>
+void batch_v(const T* S, int m, int i, const double* L, const double* z, T* Vv, cudaStream_t st) {
+  if (m <= 0 || i <= 0) return;
+  k_batch_v<T><<<cdiv(m, 128), 128, 0, st>>>(S, m, i, L, z, Vv); note_launch();
+}
+template void coord_actions<float>(int, int, float*, cudaStream_t);
+template void coord_actions<double>(int, int, double*, cudaStream_t);
+template void batch_v<float>(const float*, int, int, const double*, const double*, float*, cudaStream_t);
+template void batch_v<double>(const double*, int, int, const double*, const double*, double*, cudaStream_t);
+
 void set_diag(double* G, int ld, const double* lam, double scale, int r, cudaStream_t st) {
   if (r <= 0) return;
   k_set_diag<<<cdiv(r, 256), 256, 0, st>>>(G, ld, lam, scale, r); note_launch();
