@@ -319,6 +319,40 @@ int cakf_eig_topk(const double* A, int32_t N, int32_t keep, double* w_out, doubl
  */
 int cakf_probe_peaks(double* mufu_ops_per_s, double* fp64_flops_per_s, void* cuda_stream);
 
+/*
+ * cakf_get_diagnostics -- per-step records of the last filter (and smoother) run on ctx, for
+ * monitoring the approximation (the paper's update stops at the budget; these tell how far each
+ * step got).  Each output is NULL or an array of T+1 entries (host); entry 0 is the prior (zeros).
+ *   actions           i_k, the actions used (below the budget when the iteration broke down: an
+ *                     action whose G-orthogonal part vanished, R2)
+ *   rel_residual      |r_k| / |r0_k| of the step's final residual r = r0 - G v (the CG recursion's
+ *                     residual; for the batch policies r0 - G S Ghat^-1 S^T r0)
+ *   min_eta           the smallest eta_j = d_j^T G d_j of the step (the pivots of S^T G S)
+ *   dropped_filter    trace(M^T M) minus the kept eigenvalues at the filter's truncation of step k
+ *                     (the mass N N^T of Sec. 3.2 that is discarded); 0 without truncation
+ *   dropped_smoother  the same for the smoother's truncation of Ws at step k (after cakf_smooth)
+ * Errors: CAKF_ERR_STATE (no successful cakf_filter), CAKF_ERR_CUDA.
+ */
+int cakf_get_diagnostics(const cakf_ctx* ctx, int32_t* actions, double* rel_residual, double* min_eta,
+                         double* dropped_filter, double* dropped_smoother);
+
+/*
+ * cakf_set_wait_limit -- iteration limit of every bounded device-side wait (the tensor-core
+ * kernels' mbarrier waits, the tridiagonalisation's exchange polling) for the calls that follow,
+ * process-wide; 0 restores each kernel's default (seconds of waiting).  A wait that runs out makes
+ * its kernel stop cleanly and the call return CAKF_ERR_TIMEOUT; the context stays usable.  Meant
+ * for tests of that path.  No counterpart in the paper.  Errors: CAKF_ERR_ARG (negative).
+ */
+int cakf_set_wait_limit(int64_t iterations);
+
+/*
+ * cakf_set_device_memory_limit -- cap (bytes) on the device memory one context may hold; a
+ * cakf_filter that would exceed it returns CAKF_ERR_OOM before allocating.  0 = no cap (default).
+ * Process-wide.  No counterpart in the paper (a resource guard, and the way tests reach the
+ * out-of-memory path without exhausting the device).
+ */
+int cakf_set_device_memory_limit(uint64_t bytes);
+
 /* cakf_get_stats -- timings and counters of the last filter / smooth calls (host output). */
 int cakf_get_stats(const cakf_ctx* ctx, cakf_stats* out);
 

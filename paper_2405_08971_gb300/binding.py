@@ -86,6 +86,12 @@ def lib():
         L.cakf_factor_gemm.restype = C.c_int
         L.cakf_probe_peaks.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
         L.cakf_probe_peaks.restype = C.c_int
+        L.cakf_get_diagnostics.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.cakf_get_diagnostics.restype = C.c_int
+        L.cakf_set_wait_limit.argtypes = [C.c_int64]
+        L.cakf_set_wait_limit.restype = C.c_int
+        L.cakf_set_device_memory_limit.argtypes = [C.c_uint64]
+        L.cakf_set_device_memory_limit.restype = C.c_int
         L.cakf_free.argtypes = [vp]
         L.cakf_free.restype = None
         L.cakf_last_error.restype = C.c_char_p
@@ -410,6 +416,25 @@ def cakf_probe_peaks(stream=None) -> dict:
     mufu, fp64 = C.c_double(), C.c_double()
     _check(lib().cakf_probe_peaks(C.byref(mufu), C.byref(fp64), stream))
     return {"mufu_ops_per_s": mufu.value, "fp64_flops_per_s": fp64.value}
+
+
+def cakf_get_diagnostics(ctx: Context) -> dict:
+    """Per-step records of the last run: actions used, relative final residual, smallest eta,
+    discarded truncation mass of the filter and of the smoother (arrays of T+1 entries)."""
+    T = ctx.T if ctx.T is not None else 0
+    acts = np.zeros(T + 1, dtype=np.int32)
+    arrs = [np.zeros(T + 1) for _ in range(4)]
+    _check(lib().cakf_get_diagnostics(ctx.handle, acts.ctypes.data, *[a.ctypes.data for a in arrs]))
+    return {"actions": acts, "rel_residual": arrs[0], "min_eta": arrs[1], "dropped_filter": arrs[2],
+            "dropped_smoother": arrs[3]}
+
+
+def cakf_set_wait_limit(iterations: int):
+    _check(lib().cakf_set_wait_limit(int(iterations)))
+
+
+def cakf_set_device_memory_limit(nbytes: int):
+    _check(lib().cakf_set_device_memory_limit(int(nbytes)))
 
 
 def cakf_set_profiling(ctx: Context, on: bool):

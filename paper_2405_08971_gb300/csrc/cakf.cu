@@ -9,6 +9,7 @@
 //   Vv[k]    m_k x (i_k + 1): [V_k, v_k] -- G-orthonormal directions and solution coefficients
 //   S[k]     m_k x i_k actions
 //   mf, vf   (T+1) x n filter means / variances (FP64)
+#include <atomic>
 #include <cstring>
 #include <cstdio>
 #include <string>
@@ -23,6 +24,7 @@ using namespace cakf;
 namespace {
 
 thread_local std::string g_err;
+std::atomic<unsigned long long> g_mem_limit{0};   // cap on a context's device bytes (0 = none)
 
 int fail(int code, const std::string& msg) {
   g_err = msg;
@@ -85,7 +87,10 @@ struct cakf_ctx {
   int* count = nullptr;    // T+1
   int* err = nullptr;      // device error flag
   int* active = nullptr;
-  double* r0sq = nullptr;
+  double* r0sq = nullptr;     // (T+1) |r0|^2 per step
+  double* rfin = nullptr;     // (T+1) |r|^2 of the final residual per step
+  double* dropped_f = nullptr;   // (T+1) discarded eigenvalue mass of the filter truncation per step
+  double* dropped_s = nullptr;   // (T+1) the same for the smoother truncation
   // workspace
   double *mpred = nullptr, *rs_plus = nullptr, *rs_pw = nullptr, *lam = nullptr, *lam2 = nullptr;
   void *Xo = nullptr, *Mo = nullptr, *rv = nullptr, *r0v = nullptr, *sv = nullptr, *gv = nullptr, *GV = nullptr,
@@ -172,6 +177,11 @@ struct cakf_ctx {
   template <class P> int alloc(P*& out, size_t bytes) {
     void* p = nullptr;
     bytes = std::max<size_t>(bytes, 16);
+    const unsigned long long cap = g_mem_limit.load();
+    if (cap && dev_bytes + bytes > cap) {
+      out = nullptr;
+      return fail(CAKF_ERR_OOM, "device memory limit of " + std::to_string(cap) + " bytes reached (cakf_set_device_memory_limit)");
+    }
     cudaError_t ce = cudaMalloc(&p, bytes);
     if (ce != cudaSuccess) {
       cudaGetLastError();
@@ -328,7 +338,10 @@ int plan_and_alloc(cakf_ctx* c, const cakf_problem* p) {
   if ((rc = c->alloc(c->count, (T + 1) * sizeof(int)))) return rc;
   if ((rc = c->alloc(c->err, 16))) return rc;
   if ((rc = c->alloc(c->active, 16))) return rc;
-  if ((rc = c->alloc(c->r0sq, 16))) return rc;
+  if ((rc = c->alloc(c->r0sq, (T + 1) * sizeof(double)))) return rc;
+  if ((rc = c->alloc(c->rfin, (T + 1) * sizeof(double)))) return rc;
+  if ((rc = c->alloc(c->dropped_f, (T + 1) * sizeof(double)))) return rc;
+  if ((rc = c->alloc(c->dropped_s, (T + 1) * sizeof(double)))) return rc;
   if ((rc = c->alloc(c->mpred, n * sizeof(double)))) return rc;
   if ((rc = c->alloc(c->rs_plus, n * sizeof(double)))) return rc;
   if ((rc = c->alloc(c->rs_pw, n * sizeof(double)))) return rc;
@@ -570,6 +583,9 @@ struct Runner {
     cudaMemsetAsync(c->rs_plus, 0, n * sizeof(double), st);
     cudaMemsetAsync(c->nll, 0, (T_ + 1) * sizeof(double), st);
     cudaMemsetAsync(c->count, 0, (T_ + 1) * sizeof(int), st);
+    cudaMemsetAsync(c->r0sq, 0, (T_ + 1) * sizeof(double), st);
+    cudaMemsetAsync(c->rfin, 0, (T_ + 1) * sizeof(double), st);
+    cudaMemsetAsync(c->dropped_f, 0, (T_ + 1) * sizeof(double), st);
     cudaMemsetAsync(c->Spool, 0, c->off_S[T_ + 1] * sizeof(T), st);
     // state 0: prior
     if (c->has_mu) cudaMemcpyAsync(c->mf, c->mu, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
@@ -643,8 +659,9 @@ struct Runner {
       cudaEvent_t ph0 = ph_begin();
       gather_coords<T>(X(), ob, m, Xo, st);
       gather_rows<T>(Mk(k - 1), ldn, ob, m, rp, Mo, m, st);
-      cudaMemsetAsync(c->r0sq, 0, sizeof(double), st);
-      cg_init<T>(c->y + c->obs_ptr[k - 1], c->mpred, ob, m, r, (T*)c->r0v, vcol, c->r0sq, st);
+      cudaMemsetAsync(c->r0sq + k, 0, sizeof(double), st);
+      cudaMemsetAsync(c->rfin + k, 0, sizeof(double), st);
+      cg_init<T>(c->y + c->obs_ptr[k - 1], c->mpred, ob, m, r, (T*)c->r0v, vcol, c->r0sq + k, st);
       cudaMemsetAsync(V, 0, (size_t)m * ic * sizeof(T), st);
       cudaMemsetAsync(GV, 0, (size_t)m * std::max(ic, 1) * sizeof(T), st);
       cudaMemsetAsync(GSk, 0, (size_t)m * std::max(ic, 1) * sizeof(T), st);
@@ -660,7 +677,7 @@ struct Runner {
       int use_rtol = 0;
       if (c->cg_rtol > 0 && !c->replay && !recompute) {
         double r0sq = 0;
-        cudaMemcpyAsync(&r0sq, c->r0sq, sizeof(double), cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(&r0sq, c->r0sq + k, sizeof(double), cudaMemcpyDeviceToHost, st);
         cudaStreamSynchronize(st);
         rtol2 = c->cg_rtol * c->cg_rtol * r0sq;
         use_rtol = 1;
@@ -701,6 +718,7 @@ struct Runner {
         cg_upd2<T>(j, c->dots, dpart2, V, GV, m, r, vcol, s, reorth ? Qa : nullptr, m, bd_tol, rtol2, use_rtol,
                    c->active, c->eta + (size_t)k * B, c->alpha + (size_t)k * B, c->count + k, snext, st);
       }
+      sqnorm_acc<T>(r, m, c->rfin + k, st);   // the final (updated) residual
       }
       ph_end(0, ph0);
       // finalize: [P^- W, P^- w] = K(X, X_o) [V v] - a^2 M+ (M+_o^T [V v])
@@ -786,8 +804,11 @@ struct Runner {
     double* z = yh + ic;
     gemm_tn<T>(S, m, ic, GSb, m, ic, m, 1.0, 0.0, Gh, ic, c->part64, c->part64_elems, st);
     gemm_tn<T>(S, m, ic, (const T*)c->r0v, m, 1, m, 1.0, 0.0, yh, ic, c->part64, c->part64_elems, st);
-    if (batch_chol(Gh, ic, yh, L, z, c->err, st)) return fail(CAKF_ERR_ARG, "too many actions for the batch update");
+    const int B = std::max(c->budget, c->imax);
+    if (batch_chol(Gh, ic, yh, L, z, c->eta + (size_t)k * B, c->err, st))
+      return fail(CAKF_ERR_ARG, "too many actions for the batch update");
     batch_v<T>(S, m, ic, L, z, V, st);
+    batch_resid<T>(GSb, m, ic, L, z, (const T*)c->r0v, c->rfin + k, st);
     cudaMemcpyAsync(c->count + k, &ic, sizeof(int), cudaMemcpyHostToDevice, st);
     return CAKF_OK;
   }
@@ -814,8 +835,10 @@ struct Runner {
       put_block_sym(G, N, 0, rp, Bm, rp, rp, ic, 1.0, st);
     }
     gemm_tn<T>(PVk, ldn, ic, PVk, ldn, ic, n, 1.0, 0.0, G + (size_t)rp * N + rp, N, c->part64, c->part64_elems, st);
+    trace_into(G, N, N, c->dropped_f + k, st);   // discarded mass = trace - kept eigenvalues
     int rc = eig(G, N, keep);
     if (rc) return rc;
+    sub_sum(c->wv, keep, c->dropped_f + k, st);
     // M+_k = a M+_{k-1} U[0:rp, :] + P^- W U[rp:N, :]
     T* U = (T*)c->UT;
     if (rp > 0) gemm_nn<T, T>(n, keep, rp, T(a), Mk(k - 1), ldn, U, N, T(0), Mk(k), ldn, st);
@@ -866,6 +889,7 @@ struct Runner {
     const double a = c->a, a2 = a * a;
     cudaMemcpyAsync(ms + (size_t)T_ * n, c->mf + (size_t)T_ * n, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
     cudaMemcpyAsync(vs + (size_t)T_ * n, c->vf + (size_t)T_ * n, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    cudaMemsetAsync(c->dropped_s, 0, (T_ + 1) * sizeof(double), st);
     if (T_ == 0) return CAKF_OK;
     T* Ws = (T*)c->WsA;
     T* Wn = (T*)c->WsB;
@@ -974,8 +998,10 @@ struct Runner {
       }
       if (c->rank_r > 0) {
         const int keep = std::min(c->rank_r, N);
+        trace_into(G, N, N, c->dropped_s + k, st);
         int rc = eig(G, N, keep);
         if (rc) return rc;
+        sub_sum(c->wv, keep, c->dropped_s + k, st);
         T* U = (T*)c->UT;
         // Ws_new = X[:, :cw] U[ic:, :] + scatter_obs( V_k (U[:ic, :] - Z[:, :cw] U[ic:, :]) )
         if (cw > 0) gemm_nn<T, T>(n, keep, cw, T(1), Xs, ldn, U + ic, N, T(0), Wn, ldn, st);
@@ -1121,6 +1147,7 @@ struct Runner {
       T* r0 = (T*)c->r0v;
       predict_mean(mprev, c->has_mu ? c->mu + (size_t)k * n : nullptr, c->has_mu ? c->mu + (size_t)(k - 1) * n : nullptr,
                    a, n, c->mpred, st);
+      cudaMemsetAsync(c->r0sq, 0, sizeof(double), st);   // element 0 (no data at state 0): scratch
       cg_init<T>(c->y + c->obs_ptr[k - 1], c->mpred, ob, m, (T*)c->rv, r0, (T*)c->sv, c->r0sq, st);
       gemm_tn<T>(S, m, ic, r0, m, 1, m, 1.0, 0.0, yh, ic, c->part64, c->part64_elems, st);
       T* dmo = (T*)c->dmo;
@@ -1254,6 +1281,14 @@ int validate(const cakf_problem* p) {
         return fail(CAKF_ERR_ARG, "the batch policies take at most 160 actions per step");
     }
   }
+  // host inputs are checked for non-finite values here (device inputs surface as CAKF_ERR_NUMERIC
+  // through the outputs' finiteness check)
+  if (ptr_kind(p->coords) == kHost)
+    for (size_t q = 0; q < (size_t)p->n * p->dim; ++q)
+      if (!std::isfinite(p->coords[q])) return fail(CAKF_ERR_ARG, "non-finite coordinate");
+  if (N > 0 && ptr_kind(p->y) == kHost)
+    for (int q = 0; q < N; ++q)
+      if (!std::isfinite(p->y[q])) return fail(CAKF_ERR_ARG, "non-finite observation");
   // observation indices: range and distinctness per step (checked on a host copy)
   if (N > 0) {
     std::vector<int> idx(N);
@@ -1486,6 +1521,46 @@ int cakf_get_actions(cakf_ctx* c, double* actions_out, int32_t* counts_out) {
     }
     off += cnt_el;
   }
+  return CAKF_OK;
+}
+
+int cakf_get_diagnostics(const cakf_ctx* c, int32_t* actions, double* rel_residual, double* min_eta,
+                         double* dropped_filter, double* dropped_smoother) {
+  if (!c) return fail(CAKF_ERR_STATE, "cakf_get_diagnostics: no context (cakf_filter creates it)");
+  if (!c->filtered) return fail(CAKF_ERR_STATE, "cakf_get_diagnostics: no filter run on this context");
+  const int T = c->T, B = std::max(c->budget, c->imax);
+  std::vector<int> cnt(T + 1);
+  std::vector<double> r0(T + 1), rf(T + 1), eta((size_t)(T + 1) * B), df(T + 1), ds(T + 1);
+  if (cudaMemcpy(cnt.data(), c->count, (T + 1) * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(r0.data(), c->r0sq, (T + 1) * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(rf.data(), c->rfin, (T + 1) * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(eta.data(), c->eta, eta.size() * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(df.data(), c->dropped_f, (T + 1) * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(ds.data(), c->dropped_s, (T + 1) * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(CAKF_ERR_CUDA, "cakf_get_diagnostics: reading the per-step records");
+  for (int k = 0; k <= T; ++k) {
+    const int ik = k == 0 ? 0 : cnt[k];
+    if (actions) actions[k] = ik;
+    if (rel_residual) rel_residual[k] = (ik > 0 && r0[k] > 0) ? std::sqrt(rf[k] / r0[k]) : 0.0;
+    if (min_eta) {
+      double mn = ik > 0 ? eta[(size_t)k * B] : 0.0;
+      for (int j = 1; j < ik; ++j) mn = std::min(mn, eta[(size_t)k * B + j]);
+      min_eta[k] = mn;
+    }
+    if (dropped_filter) dropped_filter[k] = df[k];
+    if (dropped_smoother) dropped_smoother[k] = ds[k];
+  }
+  return CAKF_OK;
+}
+
+int cakf_set_wait_limit(int64_t iterations) {
+  if (iterations < 0) return fail(CAKF_ERR_ARG, "cakf_set_wait_limit: negative limit");
+  cakf::set_wait_limit((long long)iterations);
+  return CAKF_OK;
+}
+
+int cakf_set_device_memory_limit(uint64_t bytes) {
+  g_mem_limit.store(bytes);
   return CAKF_OK;
 }
 

@@ -92,7 +92,8 @@ __device__ __forceinline__ double warp0_sum(const double* red) {
 
 __global__ void __launch_bounds__(TD_THREADS)
 k_tridiag(double* __restrict__ A, int lda, int N, double* __restrict__ d, double* __restrict__ e,
-          double* __restrict__ tau, double* __restrict__ Pbuf, double* __restrict__ Cbuf, int* err) {
+          double* __restrict__ tau, double* __restrict__ Pbuf, double* __restrict__ Cbuf, int* err,
+          long long poll_limit) {
   extern __shared__ double sm[];
   // sm[0, N) and sm[N, 2N): v_k and v_{k+1}, swapped every step
   double* w = sm + 2 * N;           // w_k
@@ -184,7 +185,7 @@ k_tridiag(double* __restrict__ A, int lda, int N, double* __restrict__ d, double
         pt = ld_relaxed(Pk + t);
         ct = ld_relaxed(Ck + t);
         if (epoch_of(pt) == ek && epoch_of(ct) == ek) break;
-        if (++spins > kPollLimit) { atomicExch(err, kErrTimeout); ok = false; break; }
+        if (++spins > poll_limit) { atomicExch(err, kErrTimeout); ok = false; break; }
         if ((spins & 255) == 0 && ld_relaxed_int(err)) { ok = false; break; }
       }
       c[t] = ct;
@@ -1111,7 +1112,8 @@ int eig_sym_topk(double* A, int lda, int N, int nkeep, double* w, T* U, int ldu,
       G = std::max(1, occ * nsm);     // fewer blocks own more columns each
       if (occ == 0) { cudaGetLastError(); return 1000 + (int)cudaErrorCooperativeLaunchTooLarge; }
     }
-    void* args[] = {&A, &lda, &N, &d, &e, &tau, &P, &Cb, &err};
+    long long poll_limit = wait_limit(kPollLimit);
+    void* args[] = {&A, &lda, &N, &d, &e, &tau, &P, &Cb, &err, &poll_limit};
     cudaError_t ce = cudaLaunchCooperativeKernel((void*)k_tridiag, dim3(G), dim3(TD_THREADS), args, smem, st);
     note_launch();
     if (ce != cudaSuccess) return 1000 + (int)ce;

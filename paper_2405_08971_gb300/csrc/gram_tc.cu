@@ -85,8 +85,8 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
 }
 // Bounded wait for the completion of the phase with the given parity.  Returns false on timeout
 // or when another role of this CTA already aborted.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
-  for (long long it = 0; it < WAIT_LIMIT; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, long long limit) {
+  for (long long it = 0; it < limit; ++it) {
     uint32_t ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -215,6 +215,7 @@ struct TcParams {
   int stages;
   int tmem_cols;
   uint32_t b_stage_bytes;
+  long long wait_limit;    // iteration limit of every mbarrier wait
 };
 
 // Uniform vote over the producer warps (named barrier 1): true iff every producer passes true.
@@ -265,7 +266,8 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmapB, const TcParams P) {
   uint64_t* empty = bars + 3 * S;
   uint64_t* done = bars + 4 * S;           // MMA -> epilogue: a tile's accumulator is complete
   uint64_t* tfree = bars + 4 * S + 1;      // epilogue -> MMA: the accumulator has been read out
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 4 * S + 2);
+  uint64_t* fin = bars + 4 * S + 2;        // MMA issuer: all its MMAs have completed (exit)
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 4 * S + 3);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
   float* mean_part = reinterpret_cast<float*>(tmem_holder + 4);     // [2][8][BM]
 
@@ -283,6 +285,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmapB, const TcParams P) {
     }
     mbar_init(smem_u32(done), 1);
     mbar_init(smem_u32(tfree), NPROD_WARPS);
+    mbar_init(smem_u32(fin), 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -332,7 +335,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmapB, const TcParams P) {
         const uint32_t n = (uint32_t)(it / S);
         // fullC completes only after the TMA warp saw empty[s] (the MMAs of this stage's previous
         // use are done) and its copies landed, so it also releases the A stage to the producers.
-        ok = mbar_wait(smem_u32(&fullC[s]), n & 1, abort_flag);
+        ok = mbar_wait(smem_u32(&fullC[s]), n & 1, abort_flag, P.wait_limit);
         ok = __all_sync(0xffffffffu, ok);
         if (!ok) break;
         constexpr int NPAIR = M::CPT / 2;
@@ -402,7 +405,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmapB, const TcParams P) {
         if (split) atomicAdd(dst, m);
         else *dst = m;
       }
-      ok = mbar_wait(smem_u32(done), tcount & 1, abort_flag);
+      ok = mbar_wait(smem_u32(done), tcount & 1, abort_flag, P.wait_limit);
       ok = __all_sync(0xffffffffu, ok);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if (ok) {
@@ -451,7 +454,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmapB, const TcParams P) {
         const int s = (int)(it % S);
         const uint32_t n = (uint32_t)(it / S);
         const int kt = (int)(u % P.nk);
-        if (!mbar_wait(smem_u32(&empty[s]), (n & 1) ^ 1, abort_flag)) break;
+        if (!mbar_wait(smem_u32(&empty[s]), (n & 1) ^ 1, abort_flag, P.wait_limit)) break;
         const uint32_t cb = smem_u32(&fullC[s]);
         mbar_expect_tx(cb, M::C_STAGE + M::W_STAGE);
         bulk_load(smem_u32(C_base + (size_t)s * M::C_STAGE), P.Xc + (size_t)kt * M::BK, M::C_STAGE, cb);
@@ -486,7 +489,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmapB, const TcParams P) {
         const long long tend = (u / P.nk + 1) * P.nk;
         const long long uend = u1 < tend ? u1 : tend;
         if (tcount > 0) {   // the epilogue of the previous tile must have read the accumulator out
-          ok = mbar_wait(smem_u32(tfree), (tcount - 1) & 1, abort_flag);
+          ok = mbar_wait(smem_u32(tfree), (tcount - 1) & 1, abort_flag, P.wait_limit);
           if (!ok) break;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         }
@@ -495,7 +498,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmapB, const TcParams P) {
           const long long it = u - u0;
           const int s = (int)(it % S);
           const uint32_t n = (uint32_t)(it / S);
-          ok = mbar_wait(smem_u32(&fullA[s]), n & 1, abort_flag) && mbar_wait(smem_u32(&fullB[s]), n & 1, abort_flag);
+          ok = mbar_wait(smem_u32(&fullA[s]), n & 1, abort_flag, P.wait_limit) && mbar_wait(smem_u32(&fullB[s]), n & 1, abort_flag, P.wait_limit);
           if (!ok) break;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t a0 = smem_u32(A_base + (size_t)s * M::NPART * M::A_TILE);
@@ -523,6 +526,9 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmapB, const TcParams P) {
         mma_commit(smem_u32(done));
         ++tcount;
       }
+      // every MMA issued above has completed before TMEM is released (also after an abort)
+      mma_commit(smem_u32(fin));
+      mbar_drain(smem_u32(fin), 0);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -563,6 +569,7 @@ struct GemmParams {
   int* err;
   int stages, tmem_cols;
   uint32_t b_stage_bytes;
+  long long wait_limit;
 };
 
 template <int MD>
@@ -622,7 +629,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gemm_tc(const GemmParams P) {
       for (int ks = ks0; ks < ks1; ++ks, ++it) {
         const int s = (int)(it % S);
         const uint32_t n = (uint32_t)(it / S);
-        ok = mbar_wait(smem_u32(&empty[s]), (n & 1) ^ 1, abort_flag);
+        ok = mbar_wait(smem_u32(&empty[s]), (n & 1) ^ 1, abort_flag, P.wait_limit);
         ok = __all_sync(0xffffffffu, ok);
         if (!ok) break;
         const int k0 = ks * M::BK;
@@ -685,7 +692,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gemm_tc(const GemmParams P) {
       ok = producers_all(ok && !*abort_flag);
       if (!ok) break;
       // ---- epilogue of the unit
-      ok = mbar_wait(smem_u32(done), tcount & 1, abort_flag);
+      ok = mbar_wait(smem_u32(done), tcount & 1, abort_flag, P.wait_limit);
       ok = __all_sync(0xffffffffu, ok);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if (ok) {
@@ -739,14 +746,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gemm_tc(const GemmParams P) {
         const int kc = u / (P.ntiles * P.nchunks);
         const int ks0 = kc * P.kslices, ks1 = min(P.nk, ks0 + P.kslices);
         if (tcount > 0) {
-          ok = mbar_wait(smem_u32(tfree), (tcount - 1) & 1, abort_flag);
+          ok = mbar_wait(smem_u32(tfree), (tcount - 1) & 1, abort_flag, P.wait_limit);
           if (!ok) break;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         }
         for (int ks = ks0; ks < ks1; ++ks, ++it) {
           const int s = (int)(it % S);
           const uint32_t n = (uint32_t)(it / S);
-          ok = mbar_wait(smem_u32(&fullA[s]), n & 1, abort_flag);
+          ok = mbar_wait(smem_u32(&fullA[s]), n & 1, abort_flag, P.wait_limit);
           if (!ok) break;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t a0 = smem_u32(A_base + (size_t)s * M::NPART * M::A_TILE);
@@ -985,6 +992,7 @@ int launch(int ker, const C4<float>* Xr, int nr, int nc, const void* Bp, int ldp
   P.nk = ldp / M::BK; P.ntiles = (nr + BM - 1) / BM; P.npad = L.npad;
   P.nbox = L.nbox; P.boxh = L.boxh; P.wtc = wtc; P.sf2 = sf2; P.Out = Out; P.ldo = ldo; P.err = err;
   P.stages = L.stages; P.tmem_cols = L.tmem_cols; P.b_stage_bytes = L.b_stage_bytes;
+  P.wait_limit = wait_limit(WAIT_LIMIT);
 
   const void* fn = kernel_for<MD>(ker);
   cudaError_t ce = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
@@ -1076,6 +1084,7 @@ int gemm_tc_launch(int transA, int Mr, int N, int K, float alpha, const float* A
   P.part = split ? part : nullptr;
   P.err = err;
   P.stages = L.stages; P.tmem_cols = L.tmem_cols; P.b_stage_bytes = L.b_stage_bytes;
+  P.wait_limit = wait_limit(WAIT_LIMIT);
   const int units = P.ntiles * P.nchunks * P.kchunks;
   const int grid = std::min(units, slots);
   void* args[] = {&P};

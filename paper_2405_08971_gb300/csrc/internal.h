@@ -104,7 +104,14 @@ void from_bf16(const uint16_t* In, int ldi, int rows, int cols, float* Out, int 
 // and [V v] = [S L^-T, S L^-T z].  At most kBatchMaxActions actions per step.
 constexpr int kBatchMaxActions = 160;
 template <class T> void coord_actions(int m, int i, T* S, cudaStream_t st);
-int batch_chol(const double* Gh, int i, const double* yh, double* L, double* z, int* err, cudaStream_t st);
+int batch_chol(const double* Gh, int i, const double* yh, double* L, double* z, double* eta, int* err,
+               cudaStream_t st);
+// Per-step diagnostics: *out += |x|^2; *out = trace(G); *out -= sum(w[0..keep)); *out += |r0 - GS L^-T z|^2
+template <class T> void sqnorm_acc(const T* x, int m, double* out, cudaStream_t st);
+void trace_into(const double* G, int N, int ld, double* out, cudaStream_t st);
+void sub_sum(const double* w, int keep, double* out, cudaStream_t st);
+template <class T>
+void batch_resid(const T* GS, int m, int i, const double* L, const double* z, const T* r0, double* out, cudaStream_t st);
 template <class T>
 void batch_v(const T* S, int m, int i, const double* L, const double* z, T* Vv, cudaStream_t st);
 
@@ -122,6 +129,10 @@ constexpr int kErrTimeout = 2;
 void set_gemm_mode(int mode);
 int gemm_mode();
 void set_gemm_err(int* err);
+// Bounded device waits: the iteration limit to pass to a kernel (dflt unless cakf_set_wait_limit
+// set another).
+void set_wait_limit(long long it);
+long long wait_limit(long long dflt);
 
 // ---- FP64 symmetric eigensolver (eig.cu) ----
 // Workspace bytes needed for matrices up to order nmax.

@@ -18,6 +18,15 @@ static thread_local int* t_gemm_err = nullptr;
 void set_gemm_mode(int mode) { t_gemm_mode = mode; }
 int gemm_mode() { return t_gemm_mode; }
 void set_gemm_err(int* err) { t_gemm_err = err; }
+
+// Iteration limits of the bounded device-side waits (0 = the defaults of each kernel); a
+// diagnostic setting for tests of the timeout path.
+static std::atomic<long long> g_wait_limit{0};
+void set_wait_limit(long long it) { g_wait_limit.store(it < 0 ? 0 : it); }
+long long wait_limit(long long dflt) {
+  const long long v = g_wait_limit.load();
+  return v > 0 ? v : dflt;
+}
 long long launch_count() { return g_launches.load(); }
 void note_launch(long long k) { g_launches += k; }
 
@@ -1605,7 +1614,7 @@ __global__ void k_coord_actions(int m, int i, T* __restrict__ S) {
 constexpr int BCH_THREADS = 256;
 __global__ void __launch_bounds__(BCH_THREADS)
 k_batch_chol(const double* __restrict__ Gh, int i, const double* __restrict__ yh, double* __restrict__ Lout,
-             double* __restrict__ z, int* __restrict__ err) {
+             double* __restrict__ z, double* __restrict__ eta, int* __restrict__ err) {
   extern __shared__ double bsm[];
   double* L = bsm;                  // i x i, column-major
   double* zz = bsm + (size_t)i * i;
@@ -1621,6 +1630,7 @@ k_batch_chol(const double* __restrict__ Gh, int i, const double* __restrict__ yh
   for (int p = 0; p < i; ++p) {
     if (threadIdx.x == 0) {
       double d = L[(size_t)p * i + p];
+      if (eta) eta[p] = d;            // the pivot: eta_j of the iterative form (S^T G S = U^-T diag(eta) U^-1)
       if (!(d > 0.0) || !isfinite(d)) { bad = 1; d = 1.0; }
       piv = sqrt(d);
       L[(size_t)p * i + p] = piv;
@@ -1672,12 +1682,13 @@ void coord_actions(int m, int i, T* S, cudaStream_t st) {
   cudaMemsetAsync(S, 0, (size_t)m * i * sizeof(T), st);
   k_coord_actions<T><<<cdiv(i, 128), 128, 0, st>>>(m, i, S); note_launch();
 }
-int batch_chol(const double* Gh, int i, const double* yh, double* L, double* z, int* err, cudaStream_t st) {
+int batch_chol(const double* Gh, int i, const double* yh, double* L, double* z, double* eta, int* err,
+               cudaStream_t st) {
   if (i <= 0) return 0;
   if (i > kBatchMaxActions) return 1;
   const size_t smem = ((size_t)i * i + i) * sizeof(double);
   if (smem > 48 * 1024) cudaFuncSetAttribute(k_batch_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_batch_chol<<<1, BCH_THREADS, smem, st>>>(Gh, i, yh, L, z, err); note_launch();
+  k_batch_chol<<<1, BCH_THREADS, smem, st>>>(Gh, i, yh, L, z, eta, err); note_launch();
   return 0;
 }
 template <class T>
@@ -1689,6 +1700,71 @@ template void coord_actions<float>(int, int, float*, cudaStream_t);
 template void coord_actions<double>(int, int, double*, cudaStream_t);
 template void batch_v<float>(const float*, int, int, const double*, const double*, float*, cudaStream_t);
 template void batch_v<double>(const double*, int, int, const double*, const double*, double*, cudaStream_t);
+
+// ------------------------------------------------------------------------------------------
+// Per-step diagnostics: the squared norm of a vector (the final residual of a step's update), the
+// trace of the truncation Gram before the eigensolver and the discarded mass after it.
+template <class T>
+__global__ void k_sqnorm(const T* __restrict__ x, int m, double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const double v = i < m ? (double)x[i] : 0.0;
+  const double s = block_sum(v * v);
+  if (threadIdx.x == 0) atomicAdd(out, s);
+}
+__global__ void k_trace(const double* __restrict__ G, int N, int ld, double* __restrict__ out) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) acc += G[(size_t)i * ld + i];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) *out = acc;
+}
+__global__ void k_sub_sum(const double* __restrict__ w, int keep, double* __restrict__ out) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < keep; i += blockDim.x) acc += w[i];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) *out -= acc;
+}
+// r_final = r0 - (G S) L^-T z for the batch update: squared norm accumulated into out
+template <class T>
+__global__ void k_batch_resid(const T* __restrict__ GS, int m, int i, const double* __restrict__ L,
+                              const double* __restrict__ z, const T* __restrict__ r0, double* __restrict__ out) {
+  extern __shared__ double yc[];   // L^-T z, by back substitution (thread 0), shared by the block
+  if (threadIdx.x == 0) {
+    for (int j = i - 1; j >= 0; --j) {
+      double acc = z[j];
+      for (int l = j + 1; l < i; ++l) acc = fma(-L[(size_t)j * i + l], yc[l], acc);
+      yc[j] = acc / L[(size_t)j * i + j];
+    }
+  }
+  __syncthreads();
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  double r = 0.0;
+  if (row < m) {
+    r = (double)r0[row];
+    for (int j = 0; j < i; ++j) r = fma(-(double)GS[(size_t)j * m + row], yc[j], r);
+  }
+  const double s = block_sum(r * r);
+  if (threadIdx.x == 0) atomicAdd(out, s);
+}
+template <class T> void sqnorm_acc(const T* x, int m, double* out, cudaStream_t st) {
+  if (m <= 0) return;
+  k_sqnorm<T><<<cdiv(m, 256), 256, 0, st>>>(x, m, out); note_launch();
+}
+void trace_into(const double* G, int N, int ld, double* out, cudaStream_t st) {
+  k_trace<<<1, 256, 0, st>>>(G, N, ld, out); note_launch();
+}
+void sub_sum(const double* w, int keep, double* out, cudaStream_t st) {
+  k_sub_sum<<<1, 256, 0, st>>>(w, keep, out); note_launch();
+}
+template <class T>
+void batch_resid(const T* GS, int m, int i, const double* L, const double* z, const T* r0, double* out, cudaStream_t st) {
+  if (m <= 0 || i <= 0) return;
+  k_batch_resid<T><<<cdiv(m, 256), 256, i * sizeof(double), st>>>(GS, m, i, L, z, r0, out); note_launch();
+}
+template void sqnorm_acc<float>(const float*, int, double*, cudaStream_t);
+template void sqnorm_acc<double>(const double*, int, double*, cudaStream_t);
+template void batch_resid<float>(const float*, int, int, const double*, const double*, const float*, double*, cudaStream_t);
+template void batch_resid<double>(const double*, int, int, const double*, const double*, const double*, double*,
+                                  cudaStream_t);
 
 void set_diag(double* G, int ld, const double* lam, double scale, int r, cudaStream_t st) {
   if (r <= 0) return;
