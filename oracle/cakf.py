@@ -24,6 +24,12 @@ Smoothing"):
   per step, Ghat = S^T (H P^- H^T + R) S, W = H^T S lsqrt(Ghat^+), w = H^T S Ghat^+ S^T (y - H m^-),
   with coordinate actions (unit vectors at a space-filling subset of the observations) or given
   actions (e.g. Gaussian sketches drawn by the caller) -- the policy appendix.
+* Posterior sampler: the CAKF/CAKS sampler algorithm of the appendix (Matheron's rule in the
+  modified model, inverse-free smoother form): given a prior draw x_0, dynamics noise q_{k-1} and
+  observation noise eps_k, x^-_k = A x_{k-1} + b + q, w_k = H^T V_k V_k^T (y_k - H x^-_k - eps_k),
+  x_k = x^-_k + P^-_k w_k, then ws_k = w_k + (I - W_k W_k^T P^-_k) A^T ws_{k+1} and
+  x^s_k = x_k + P_k A^T ws_{k+1}.  The projected noise S^T eps has the law the algorithm draws
+  (N(0, S^T R S)), so the draw is made in observation space.
 * NLL: not in the paper (named as future work at the end of the conclusion).
   Defined here as the negative log density of the projected data S_k^T y_k
   under the modified observation model (eq. proj-observation), in Euclidean-
@@ -353,6 +359,54 @@ def smoother_run(w, filt: FilterResult, model: Optional[Model] = None, rank_r=No
         else:
             Ws, Us[k], _, _ = truncate(Wfull, rank_r)
     return ms, vs, Us
+
+
+# ----------------------------------------------------------------------------- posterior sampler
+def sample_run(w, filt: FilterResult, x0, q, eps, model: Optional[Model] = None):
+    """The CAKF/CAKS sampler (appendix algorithm) for S draws at once, with the filter's actions,
+    factors and G-orthonormal directions V_k = W_k[obs] of `filt`.
+
+    x0 (n, S) initial draw; q[k] (n, S) dynamics noise of the transition into step k; eps[k] (m_k, S)
+    observation noise.  Per step: x^-_k = a x_{k-1} + b_{k-1} + q[k];
+    w_k = H^T V_k V_k^T (y_k - H x^-_k - eps_k)  (= W_k lsqrt(Ghat)^T (S^T y - S^T H x^- - S^T eps));
+    x_k = x^-_k + P^-_k w_k.  Smoother: ws_T = w_T; for k = T-1..0:
+    x^s_k = x_k + P_k (a ws_{k+1}); ws_k = w_k + a ws_{k+1} - W_k W_k^T P^-_k (a ws_{k+1}).
+    Returns (filter draws (T+1, n, S), smoother draws (T+1, n, S))."""
+    model = model or model_from(w)
+    T, n, a = w.T, model.n, model.a
+    S = x0.shape[1]
+    xf = np.zeros((T + 1, n, S))
+    wk_all = [np.zeros((n, S))]
+    xf[0] = x0
+    for k in range(1, T + 1):
+        xp = a * xf[k - 1] + model.b(k)[:, None] + q[k]
+        obs = w.obs(k)
+        Mp = filt.M_pred[k]
+        if len(obs) == 0 or filt.W[k].shape[1] == 0:
+            xf[k] = xp
+            wk_all.append(np.zeros((n, S)))
+            continue
+        V = filt.W[k][obs]
+        c = V.T @ (w.yk(k)[:, None] - xp[obs] - eps[k])
+        wk = np.zeros((n, S))
+        wk[obs] = V @ c
+        Pw = model.K_times(wk) - Mp @ (Mp.T @ wk)                  # P^-_k w_k
+        xf[k] = xp + Pw
+        wk_all.append(wk)
+    xs = np.zeros_like(xf)
+    xs[T] = xf[T]
+    ws = wk_all[T]
+    for k in range(T - 1, -1, -1):
+        t = a * ws
+        Mh = filt.M_hat[k]
+        xs[k] = xf[k] + model.K_times(t) - Mh @ (Mh.T @ t)       # x_k + P_k A^T ws_{k+1}
+        if k == 0:
+            break
+        Mp = filt.M_pred[k]
+        Pt = model.K_times(t) - Mp @ (Mp.T @ t)                   # P^-_k A^T ws_{k+1}
+        Wk = filt.W[k]
+        ws = wk_all[k] + t - Wk @ (Wk.T @ Pt)
+    return xf, xs
 
 
 # ----------------------------------------------------------------------------- NLL and gradient

@@ -251,3 +251,31 @@ def gaussian_actions(w: Workload, seed: int = 0, budget_i: Optional[int] = None)
         m = int(w.obs_ptr[k] - w.obs_ptr[k - 1])
         out.append(rng.standard_normal((m, min(i, m))) if m else np.zeros((0, 0)))
     return out
+
+
+def sampler_inputs(w: Workload, n_samples: int, seed: int = 0, n_features: int = 1024):
+    """Random inputs of the posterior sampler (the sampling algorithm of the paper's appendix), drawn
+    once and passed to both the oracle and the device: an approximate prior sample of the initial
+    state x0 ~ N(mu_0, K) and of the OU dynamics noise q_{k-1} ~ N(0, (1 - a^2) K) by random Fourier
+    features (as the paper suggests), and observation noise eps_k ~ N(0, sn2 I).
+
+    Returns (x0, q, eps): x0 (n, S); q[k] (n, S) for k = 1..T (q[0] unused); eps[k] (m_k, S)."""
+    rng = np.random.default_rng(seed)
+    nu = NU[w.kernel]
+    lx, lt, sf2, sn2 = (math.exp(w.log_lx), math.exp(w.log_lt), math.exp(w.log_sf2), math.exp(w.log_sn2))
+    d = w.coords.shape[1]
+    z = rng.standard_normal((n_features, d))
+    g = rng.chisquare(2 * nu, size=n_features)
+    omega = z / lx * np.sqrt(2 * nu / g)[:, None]
+    phase = rng.uniform(0, 2 * np.pi, size=n_features)
+    feats = np.cos(w.coords @ omega.T + phase) * math.sqrt(2.0 * sf2 / n_features)   # (n, F)
+    a = math.exp(-w.dt / lt)
+    mu0 = np.zeros(w.n) if w.prior_mean is None else w.prior_mean[0]
+    x0 = mu0[:, None] + feats @ rng.standard_normal((n_features, n_samples))
+    q = [np.zeros((w.n, n_samples))]
+    eps = [np.zeros((0, n_samples))]
+    for k in range(1, w.T + 1):
+        q.append(math.sqrt(1 - a * a) * (feats @ rng.standard_normal((n_features, n_samples))))
+        m = int(w.obs_ptr[k] - w.obs_ptr[k - 1])
+        eps.append(rng.standard_normal((m, n_samples)) * math.sqrt(sn2))
+    return x0, q, eps

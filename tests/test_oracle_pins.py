@@ -234,6 +234,47 @@ def test_batch_update_equals_iterative_update_with_the_same_actions():
     assert rel(mb, mi) < 1e-9 and rel(vb, vi) < 1e-9
 
 
+def test_sampler_without_noise_returns_the_posterior_means():
+    """The sampler's recursions with the prior mean as initial draw and no dynamics or observation
+    noise are the filter's and the smoother's mean recursions (Matheron's rule at zero noise)."""
+    w = synth.small(n=60, dim=2, m=15, T=5, budget_i=4, rank_r=7, seasonal=True, seed=53)
+    f = oracle.filter_run(w)
+    ms, _, _ = oracle.smoother_run(w, f)
+    x0 = w.prior_mean[0][:, None].copy()
+    q = [np.zeros((w.n, 1))] * (w.T + 1)
+    eps = [np.zeros((int(w.obs_ptr[k] - w.obs_ptr[k - 1]) if k else 0, 1)) for k in range(w.T + 1)]
+    xf, xs = oracle.sample_run(w, f, x0, q, eps)
+    assert rel(xf[:, :, 0], f.m) < 1e-12
+    assert rel(xs[:, :, 0], ms) < 1e-11
+
+
+def test_sampler_at_full_budget_is_exact_matheron():
+    """At full budget without truncation the modified model is the original one, so each draw is
+    Matheron's rule for the space-time GP: x_prior + C(x, z) (C(z, z) + sn2 I)^-1 (y - x_prior[z] - eps),
+    with the prior trajectory x_prior built from the same x0 and dynamics noise; the filter draw of
+    step k conditions on the data of steps 1..k only."""
+    w = synth.small(n=30, dim=2, m=8, T=4, budget_i=8, rank_r=0, seasonal=True, seed=54)
+    f = oracle.filter_run(w)
+    x0, q, eps = synth.sampler_inputs(w, 3, seed=9)
+    xf, xs = oracle.sample_run(w, f, x0, q, eps)
+    m = oracle.model_from(w)
+    xp = [x0]
+    for k in range(1, w.T + 1):
+        xp.append(m.a * xp[-1] + m.b(k)[:, None] + q[k])
+    K = oracle.kernel_matrix(w.coords, w.coords, w.kernel, m.lx, m.sf2)
+    for upto in range(1, w.T + 1):
+        steps = np.concatenate([np.full(len(w.obs(k)), k) for k in range(1, upto + 1)])
+        idx = np.concatenate([w.obs(k) for k in range(1, upto + 1)])
+        Czz = (m.a ** np.abs(steps[:, None] - steps[None, :])) * K[np.ix_(idx, idx)] + m.sn2 * np.eye(idx.size)
+        d = np.concatenate([w.yk(k)[:, None] - xp[k][w.obs(k)] - eps[k] for k in range(1, upto + 1)])
+        sol = np.linalg.solve(Czz, d)
+        kk = range(0, upto + 1) if upto == w.T else [upto]
+        for k in kk:
+            exact = xp[k] + ((m.a ** np.abs(k - steps))[None, :] * K[:, idx]) @ sol
+            got = xs[k] if upto == w.T else xf[k]
+            assert rel(got, exact) < 1e-9, (upto, k)
+
+
 def test_matern_against_sklearn():
     sk = pytest.importorskip("sklearn.gaussian_process.kernels")
     rng = np.random.default_rng(0)
