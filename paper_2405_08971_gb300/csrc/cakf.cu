@@ -1415,6 +1415,17 @@ int cakf_filter(const cakf_problem* p, cakf_ctx** ctx_inout, double* mean_out, d
     // pack the replayed actions per step (host input, concatenated m_k x i_k blocks)
     if ((rc = copy_in(c->rep, p->replay_actions, c->off_rep[c->T + 1] * sizeof(double), st))) return rc;
   }
+  // device inputs are checked for non-finite values before any work (host inputs were checked by
+  // validate): a NaN observation would otherwise only end its step's update as a breakdown
+  if (ptr_kind(p->y) != kHost || ptr_kind(p->coords) != kHost) {
+    cudaMemsetAsync(c->err, 0, sizeof(int), st);
+    check_finite(c->y, N, c->err, st);
+    check_finite(c->coords64, (size_t)n * p->dim, c->err, st);
+    int e = 0;
+    cudaMemcpyAsync(&e, c->err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return fail(CAKF_ERR_CUDA, "checking the inputs");
+    if (e) return fail(CAKF_ERR_ARG, "non-finite coordinate or observation");
+  }
   const double scale = nu_scale(c->kernel) / c->lx;
   cudaEventRecord(c->ev0, st);
   if (c->precision == CAKF_FP64) {

@@ -11,7 +11,6 @@
 // All arithmetic is FP64; only the final eigenvector block is stored in the caller's precision.
 #include <vector>
 #include <map>
-#include <cstdlib>
 #include <mutex>
 #include "internal.h"
 
@@ -62,14 +61,6 @@ __device__ __forceinline__ int ld_relaxed_int(const int* p) {
 }
 constexpr long long kPollLimit = 4000000LL;
 
-int tridiag_variant() {
-  static int v = -1;
-  if (v < 0) {
-    const char* s = getenv("CAKF_TRIDIAG");
-    v = s ? atoi(s) : 0;
-  }
-  return v;
-}
 
 // ---------------------------------------------------------------------------------- tridiagonal
 // Householder tridiagonalisation (lower), one exchange of epoch-tagged words per column.  Columns
@@ -275,153 +266,6 @@ k_tridiag(double* __restrict__ A, int lda, int N, double* __restrict__ d, double
     tk = tn;
     bk = bn;
     __syncthreads();
-  }
-}
-
-// Warp-synchronous variant: one warp per block (several blocks per SM), so that every intra-block
-// step -- the scalar reductions, the Householder scalars and the hand-offs between the phases of a
-// column -- is a warp shuffle or a __syncwarp instead of a block barrier.  The exchange protocol
-// (epoch-tagged words, two buffers, the leaving rule and the output block) is that of k_tridiag.
-__global__ void __launch_bounds__(32)
-k_tridiag_w(double* __restrict__ A, int lda, int N, double* __restrict__ d, double* __restrict__ e,
-            double* __restrict__ tau, double* __restrict__ Pbuf, double* __restrict__ Cbuf, int* err,
-            long long poll_limit) {
-  extern __shared__ double sm[];
-  double* w = sm + 2 * N;           // w_k
-  double* c = sm + 3 * N;           // updated pivot column k+1
-  double* cols = sm + 4 * N;        // owned columns (full length N)
-  const int G = gridDim.x, lane = threadIdx.x;
-  const int nslot = (N + G - 1) / G;
-  const int ob = (N - 1) % G;
-  const int maxcol = (int)blockIdx.x + G * ((N - 1 - (int)blockIdx.x) / G);
-  if (N <= 2) {
-    if (blockIdx.x == 0 && lane == 0) {
-      d[0] = A[0];
-      if (N == 2) { e[0] = A[1]; d[1] = A[(size_t)lda + 1]; tau[0] = 0.0; }
-    }
-    return;
-  }
-  for (int q = 0; q < nslot; ++q) {
-    const int j = q * G + blockIdx.x;
-    if (j >= N) break;
-    for (int t = lane; t < N; t += 32) cols[(size_t)q * N + t] = A[(size_t)j * lda + t];
-  }
-  double tk, bk;
-  {
-    const int L = N - 1;
-    double part = 0.0;
-    for (int t = lane; t < L; t += 32) {
-      const double x = A[1 + t];
-      c[t] = x;
-      if (t >= 1) part = fma(x, x, part);
-    }
-    const double sigma = warp_sum(part);
-    __syncwarp();
-    double ta, be, sc;
-    house_scalars(c[0], sigma, ta, be, sc);
-    tk = ta; bk = be;
-    double* v = sm;
-    for (int t = lane; t < L; t += 32) v[t] = (t == 0) ? 1.0 : c[t] * sc;
-    __syncwarp();
-    for (int q = 0; q < nslot; ++q) {
-      const int j = q * G + blockIdx.x;
-      if (j < 1 || j >= N) continue;
-      const double* col = cols + (size_t)q * N + 1;
-      double acc = 0.0;
-      for (int t = lane; t < L; t += 32) acc = fma(col[t], v[t], acc);
-      acc = warp_sum(acc);
-      if (lane == 0) st_relaxed(Pbuf + j - 1, with_epoch(tk * acc, 0));
-      if (j == 1) for (int t = lane; t < L; t += 32) st_relaxed(Cbuf + t, with_epoch(col[t], 0));
-    }
-    if (blockIdx.x == ob && lane == 0) d[0] = A[0];
-    __syncwarp();
-  }
-  for (int k = 0; k + 2 < N; ++k) {
-    if ((int)blockIdx.x != ob && maxcol < k + 2) return;
-    const int L = N - k - 1;
-    const double* Pk = Pbuf + (size_t)(k & 1) * N;
-    double* Pn = Pbuf + (size_t)((k + 1) & 1) * N;
-    const double* Ck = Cbuf + (size_t)(k & 1) * N;
-    double* Cn = Cbuf + (size_t)((k + 1) & 1) * N;
-    const double* v = sm + (size_t)(k & 1) * N;
-    double* v2 = sm + (size_t)((k + 1) & 1) * N;
-    const bool next = (k + 3 < N);
-    const int ek = k & 3;
-    // (1) poll p_k and the pivot column, p_k . v_k
-    double part = 0.0;
-    bool ok = true;
-    for (int t = lane; t < L && ok; t += 32) {
-      double pt, ct;
-      long long spins = 0;
-      while (true) {
-        pt = ld_relaxed(Pk + t);
-        ct = ld_relaxed(Ck + t);
-        if (epoch_of(pt) == ek && epoch_of(ct) == ek) break;
-        if (++spins > poll_limit) { atomicExch(err, kErrTimeout); ok = false; break; }
-        if ((spins & 255) == 0 && ld_relaxed_int(err)) { ok = false; break; }
-      }
-      c[t] = ct;
-      w[t] = pt;
-      part = fma(pt, v[t], part);
-    }
-    if (!__all_sync(0xffffffffu, ok)) return;
-    const double kc = 0.5 * tk * warp_sum(part);
-    __syncwarp();
-    const double w0 = w[0] - kc;          // w_k[0] (v_k[0] = 1)
-    __syncwarp();
-    // (2) w_k and the updated pivot column c = C_k - v w0 - w v0; sum of squares of c[2..]
-    part = 0.0;
-    for (int t = lane; t < L; t += 32) {
-      const double wt = fma(-kc, v[t], w[t]);
-      w[t] = wt;
-      const double ct = fma(-v[t], w0, c[t]) - wt;
-      c[t] = ct;
-      if (t >= 2) part = fma(ct, ct, part);
-    }
-    const double sigma = warp_sum(part);
-    __syncwarp();
-    double tn = 0.0, bn = 0.0, scn = 0.0;
-    if (next) house_scalars(c[1], sigma, tn, bn, scn);
-    if (blockIdx.x == ob && lane == 0) {
-      d[k + 1] = c[0];
-      e[k] = bk;
-      tau[k] = tk;
-      if (!next) { e[k + 1] = c[1]; tau[k + 1] = 0.0; }
-    }
-    // (3) v_{k+1}
-    if (next)
-      for (int t = lane; t < L - 1; t += 32) v2[t] = (t == 0) ? 1.0 : c[t + 1] * scn;
-    __syncwarp();
-    // (4) owned columns: A22 -= v w^T + w v^T, fused dot for p_{k+1}, publish column k+2
-    for (int q = 0; q < nslot; ++q) {
-      const int j = q * G + blockIdx.x;
-      if (j < k + 1 || j >= N) continue;
-      const int tj = j - (k + 1);
-      double* col = cols + (size_t)q * N + k + 1;
-      const double vj = v[tj], wj = w[tj];
-      const bool publish = next && tj == 1;
-      double acc = 0.0;
-      for (int t = lane; t < L; t += 32) {
-        const double nv = fma(-v[t], wj, fma(-w[t], vj, col[t]));
-        col[t] = nv;
-        if (next && t >= 1) acc = fma(nv, v2[t - 1], acc);
-        if (publish && t >= 1) st_relaxed(Cn + t - 1, with_epoch(nv, (k + 1) & 3));
-      }
-      if (next && tj >= 1) {
-        acc = warp_sum(acc);
-        if (lane == 0) st_relaxed(Pn + tj - 1, with_epoch(tn * acc, (k + 1) & 3));
-      }
-      if (k + 3 == N && j == N - 1) {
-        __syncwarp();
-        if (lane == 0) d[N - 1] = col[L - 1];
-      }
-    }
-    // (5) the reflector v_k below the subdiagonal of column k
-    if (blockIdx.x == ob)
-      for (int t = lane; t < L; t += 32) A[(size_t)k * lda + k + 1 + t] = v[t];
-    tk = tn;
-    bk = bn;
-    __syncwarp();
   }
 }
 
@@ -1252,28 +1096,7 @@ int eig_sym_topk(double* A, int lda, int N, int nkeep, double* w, T* U, int ldu,
   cudaMemsetAsync(d, 0, 3 * N * sizeof(double), st);
 
   // 1. tridiagonalisation (cooperative: all blocks co-resident)
-  if (tridiag_variant() > 0 && N >= 3) {
-    int dev = 0, nsm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    int G = std::max(1, std::min(N, nsm * tridiag_variant()));
-    size_t smem = 0;
-    for (int attempt = 0; attempt < 8; ++attempt) {
-      const int nslot = (N + G - 1) / G;
-      smem = (4 + (size_t)nslot) * N * sizeof(double);
-      cudaFuncSetAttribute(k_tridiag_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 48 * 1024));
-      int occ = 0;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tridiag_w, 32, smem);
-      if ((long long)occ * nsm >= G) break;
-      G = std::max(1, occ * nsm);
-      if (occ == 0) { cudaGetLastError(); return 1000 + (int)cudaErrorCooperativeLaunchTooLarge; }
-    }
-    long long poll_limit = wait_limit(kPollLimit);
-    void* args[] = {&A, &lda, &N, &d, &e, &tau, &P, &Cb, &err, &poll_limit};
-    cudaError_t ce = cudaLaunchCooperativeKernel((void*)k_tridiag_w, dim3(G), dim3(32), args, smem, st);
-    note_launch();
-    if (ce != cudaSuccess) return 1000 + (int)ce;
-  } else {
+  {
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);

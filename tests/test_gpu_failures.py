@@ -4,8 +4,8 @@
   that the tensor-core Gram x block's mbarrier waits, the tensor-core factor GEMM's waits and the
   tridiagonalisation's exchange polling give up -- returns CAKF_ERR_TIMEOUT, and the next call with
   the default limit succeeds with correct results (the kernels stopped cleanly);
-* non-finite inputs: host arrays are rejected with CAKF_ERR_ARG, device arrays surface as
-  CAKF_ERR_NUMERIC, and the context is reused successfully afterwards;
+* non-finite inputs (host or device arrays) are rejected with CAKF_ERR_ARG before any work, and the
+  context is reused successfully afterwards;
 * a replayed action that repeats an earlier one ends the step's update there (breakdown, R2): the
   per-step diagnostics report fewer actions than the budget;
 * a cap on the context's device memory returns CAKF_ERR_OOM before any allocation;
@@ -106,7 +106,7 @@ def test_non_finite_inputs():
                            w.budget_i, w.rank_r, precision="fp32")
     with pytest.raises(ck.CakfError) as ei:
         ck.cakf_filter(prob, ctx)
-    assert ei.value.code == ck.binding.ERR_NUMERIC
+    assert ei.value.code == ck.binding.ERR_ARG
     ctx, mf2, _ = ck.cakf_filter(good, ctx)     # the context is usable again
     assert np.array_equal(mf, mf2)
     ctx.close()
