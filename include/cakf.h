@@ -320,6 +320,25 @@ int cakf_eig_topk(const double* A, int32_t N, int32_t keep, double* w_out, doubl
 int cakf_probe_peaks(double* mufu_ops_per_s, double* fp64_flops_per_s, void* cuda_stream);
 
 /*
+ * cakf_sample -- draws from the computation-aware posterior of the last cakf_filter (the CAKF/CAKS
+ * sampler algorithm of the appendix: Matheron's rule in the modified model, with the smoother in
+ * inverse-free form).  The filter's stored factors are reused: no kernel values are evaluated.
+ * The random inputs are the caller's (e.g. random-Fourier-feature draws):
+ *   x0    n x S  initial draw x_0 ~ N(mu_0, K), column s at x0[s * n]           (host or device)
+ *   q     (T+1) x S x n dynamics noise q_{k-1} ~ N(0, (1 - a^2) K) of the transition into step
+ *         k at q[(k * S + s) * n]; slot k = 0 is not read                          (host or device)
+ *   eps   observation noise eps_k ~ N(0, sn2 I): for step k the m_k x S block (column-major) at
+ *         eps[obs_ptr[k-1] * S]                                                    (host or device)
+ * Outputs (T+1) x S x n, layout of q, host or device, either may be NULL:
+ *   filter_out    x_k = x^-_k + P^-_k H^T V_k V_k^T (y_k - H x^-_k - eps_k), x^-_k = a x_{k-1} + b + q
+ *   smoother_out  x^s_k = x_k + P_k a ws_{k+1}, ws_k = w_k + (I - W_k W_k^T P^-_k) a ws_{k+1}
+ * With x0 = mu_0 and no noise the draws are the filter and smoother means.  1 <= S <= 1024.
+ * Allocates its workspace per call.  Errors: CAKF_ERR_STATE, CAKF_ERR_ARG, CAKF_ERR_OOM, CAKF_ERR_CUDA.
+ */
+int cakf_sample(cakf_ctx* ctx, int32_t n_samples, const double* x0, const double* q, const double* eps,
+                double* filter_out, double* smoother_out, void* cuda_stream);
+
+/*
  * cakf_get_diagnostics -- per-step records of the last filter (and smoother) run on ctx, for
  * monitoring the approximation (the paper's update stops at the budget; these tell how far each
  * step got).  Each output is NULL or an array of T+1 entries (host); entry 0 is the prior (zeros).

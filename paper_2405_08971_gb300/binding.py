@@ -86,6 +86,8 @@ def lib():
         L.cakf_factor_gemm.restype = C.c_int
         L.cakf_probe_peaks.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
         L.cakf_probe_peaks.restype = C.c_int
+        L.cakf_sample.argtypes = [vp, C.c_int32, vp, vp, vp, vp, vp, vp]
+        L.cakf_sample.restype = C.c_int
         L.cakf_get_diagnostics.argtypes = [vp, vp, vp, vp, vp, vp]
         L.cakf_get_diagnostics.restype = C.c_int
         L.cakf_set_wait_limit.argtypes = [C.c_int64]
@@ -416,6 +418,24 @@ def cakf_probe_peaks(stream=None) -> dict:
     mufu, fp64 = C.c_double(), C.c_double()
     _check(lib().cakf_probe_peaks(C.byref(mufu), C.byref(fp64), stream))
     return {"mufu_ops_per_s": mufu.value, "fp64_flops_per_s": fp64.value}
+
+
+def cakf_sample(ctx: Context, x0, q, eps, obs_ptr, stream=None):
+    """Posterior draws with the context's filter factors.  x0: (n, S); q: list of T+1 arrays (n, S)
+    (entry 0 unused); eps: list of T+1 arrays (m_k, S) (entry 0 unused).  Returns (filter draws,
+    smoother draws), each (T+1, n, S) numpy arrays."""
+    n, T = ctx.n, ctx.T
+    x0 = np.asarray(x0, dtype=np.float64)
+    S = x0.shape[1]
+    x0c = np.ascontiguousarray(x0.T)                                        # (S, n): column s at s*n
+    qc = np.ascontiguousarray(np.stack([np.zeros((S, n))] + [np.asarray(q[k]).T for k in range(1, T + 1)]))
+    ec = np.ascontiguousarray(np.concatenate([np.asarray(eps[k], dtype=np.float64).T.ravel()
+                                              for k in range(1, T + 1)] or [np.zeros(0)]))
+    fo = np.empty((T + 1, S, n))
+    so = np.empty((T + 1, S, n))
+    _check(lib().cakf_sample(ctx.handle, S, x0c.ctypes.data, qc.ctypes.data, ec.ctypes.data, fo.ctypes.data,
+                             so.ctypes.data, stream))
+    return fo.transpose(0, 2, 1), so.transpose(0, 2, 1)
 
 
 def cakf_get_diagnostics(ctx: Context) -> dict:

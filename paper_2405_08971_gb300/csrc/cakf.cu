@@ -1048,6 +1048,103 @@ struct Runner {
     return CAKF_OK;
   }
 
+  // ---------------------------------------------------------------- posterior sampler
+  // The CAKF/CAKS sampler (appendix algorithm) for S draws, with the filter's stored factors: no
+  // kernel values are evaluated.  Filter: x^-_k = a x_{k-1} + b + q_k, c_k = V_k^T (y_k - x^-_k[obs]
+  // - eps_k), x_k = x^-_k + [P^-W]_k c_k.  Smoother: t = a ws_{k+1}, with K t carried by the same
+  // recursion the smoother uses (K ws_T = K(X, X_o) V_T c_T, K ws_k = K t + K(X, X_o) V_k (c_k - z)):
+  // P^- t = K t - a^2 M+_{k-1}(M+_{k-1}^T t), z = V_k^T (P^- t)[obs], x^s_k = x_k + P^- t - [P^-W]_k z,
+  // ws_k = t + H^T V_k (c_k - z).  xf (T+1) x S x n holds the filter draws (x0 in slot 0); q and eps
+  // are device arrays laid out like the outputs / like y with S columns per step.
+  int sample(int S, double* xf, double* xs, const double* q, const double* eps, T* work, size_t work_elems,
+             double* small, size_t small_elems) {
+    const int n = c->n, T_ = c->T, ldn = c->ldn;
+    const double a = c->a, a2 = a * a;
+    const size_t blk = (size_t)n * S;
+    // work layout (precision T): tmp (ldn x S), t (ldn x S), Kt (ldn x S), ws (ldn x S), Kws (ldn x S),
+    // gathered rows (mmax x S) x 2
+    const size_t lS = (size_t)ldn * S, mS = (size_t)std::max(c->mmax, 1) * S;
+    if (work_elems < 5 * lS + 2 * mS) return fail(CAKF_ERR_ARG, "sampler workspace too small");
+    T* tmp = work;
+    T* t = tmp + lS;
+    T* Kt = t + lS;
+    T* ws = Kt + lS;
+    T* Kws = ws + lS;
+    T* dm = Kws + lS;
+    T* dm2 = dm + mS;
+    const size_t ii = (size_t)std::max(c->imax, 1) * S;
+    double* cc = small;                       // c_k for every step: (T+1) x imax x S
+    double* u = cc + (size_t)(T_ + 1) * ii;   // rmax x S
+    double* z = u + (size_t)std::max(c->rmax, 1) * S;
+    double* e = z + ii;
+    if ((size_t)(e + ii - small) > small_elems) return fail(CAKF_ERR_ARG, "sampler scratch too small");
+    cudaMemsetAsync(cc, 0, (size_t)(T_ + 1) * ii * sizeof(double), st);
+    // ---- filter draws
+    for (int k = 1; k <= T_; ++k) {
+      if (int rc = restore(k)) return rc;
+      double* xk = xf + (size_t)k * blk;
+      samp_predict(xf + (size_t)(k - 1) * blk, q + (size_t)k * blk, c->has_mu ? c->mu + (size_t)k * n : nullptr,
+                   c->has_mu ? c->mu + (size_t)(k - 1) * n : nullptr, a, n, S, xk, st);
+      const int m = mk(k), ic = c->icap[k];
+      if (m == 0 || ic == 0) continue;
+      samp_resid<T>(c->y + c->obs_ptr[k - 1], xk, obs(k), eps + (size_t)c->obs_ptr[k - 1] * S, m, n, S, dm, st);
+      double* ck = cc + (size_t)k * ii;
+      gemm_tn<T>(Vk(k), m, ic, dm, m, S, m, 1.0, 0.0, ck, ic, c->part64, c->part64_elems, st);
+      gemm_nn<T, double>(n, S, ic, T(1), PV(k), ldn, ck, ic, T(0), tmp, ldn, st);
+      samp_add<T>(xk, tmp, ldn, 1.0, n, S, xk, st);
+    }
+    // ---- smoother draws
+    cudaMemcpyAsync(xs + (size_t)T_ * blk, xf + (size_t)T_ * blk, blk * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    cudaMemsetAsync(ws, 0, lS * sizeof(T), st);
+    cudaMemsetAsync(Kws, 0, lS * sizeof(T), st);
+    if (T_ >= 1 && mk(T_) > 0 && c->icap[T_] > 0) {
+      const int m = mk(T_), ic = c->icap[T_];
+      if (int rc = restore(T_)) return rc;
+      const double* cT = cc + (size_t)T_ * ii;
+      gemm_nn<T, double>(m, S, ic, T(1), Vk(T_), m, cT, ic, T(0), dm, m, st);
+      scatter_add_rows<T>(dm, m, obs(T_), m, S, T(1), ws, ldn, st);
+      gemm_nn<T, double>(n, S, ic, T(1), KV(T_), ldn, cT, ic, T(0), Kws, ldn, st);
+    }
+    for (int k = T_ - 1; k >= 0; --k) {
+      if (k >= 1)
+        if (int rc = restore(k)) return rc;
+      scale_copy<T>(ws, ldn, n, S, T(a), t, ldn, st);
+      scale_copy<T>(Kws, ldn, n, S, T(a), Kt, ldn, st);
+      // P^- t into Kt (in place)
+      const int rp = (k >= 1) ? c->mcols[k - 1] : 0;
+      if (rp > 0) {
+        gemm_tn<T>(Mk(k - 1), ldn, rp, t, ldn, S, n, 1.0, 0.0, u, rp, c->part64, c->part64_elems, st);
+        gemm_nn<T, double>(n, S, rp, T(-a2), Mk(k - 1), ldn, u, rp, T(1), Kt, ldn, st);
+      }
+      const int m = (k >= 1) ? mk(k) : 0, ic = (k >= 1) ? c->icap[k] : 0;
+      double* xsk = xs + (size_t)k * blk;
+      if (m == 0 || ic == 0) {
+        samp_add<T>(xf + (size_t)k * blk, Kt, ldn, 1.0, n, S, xsk, st);
+        if (k == 0) break;
+        // no update at k: ws_k = t; K ws_k = K t (before the low-rank part)
+        cudaMemcpyAsync(ws, t, lS * sizeof(T), cudaMemcpyDeviceToDevice, st);
+        scale_copy<T>(Kws, ldn, n, S, T(a), Kws, ldn, st);
+        continue;
+      }
+      // z = V_k^T (P^- t)[obs];  x^s_k = x_k + P^- t - [P^-W]_k z
+      gather_rows<T>(Kt, ldn, obs(k), m, S, dm2, m, st);
+      gemm_tn<T>(Vk(k), m, ic, dm2, m, S, m, 1.0, 0.0, z, ic, c->part64, c->part64_elems, st);
+      gemm_nn<T, double>(n, S, ic, T(-1), PV(k), ldn, z, ic, T(1), Kt, ldn, st);
+      samp_add<T>(xf + (size_t)k * blk, Kt, ldn, 1.0, n, S, xsk, st);
+      // e = c_k - z;  ws_k = t + H^T V_k e;  K ws_k = a K ws_{k+1} + K(X, X_o) V_k e
+      const double* ck = cc + (size_t)k * ii;
+      copy_block(ck, ic, ic, S, e, ic);
+      axpy_f64(-1.0, z, e, (size_t)ic * S);
+      cudaMemcpyAsync(ws, t, lS * sizeof(T), cudaMemcpyDeviceToDevice, st);
+      gemm_nn<T, double>(m, S, ic, T(1), Vk(k), m, e, ic, T(0), dm, m, st);
+      scatter_add_rows<T>(dm, m, obs(k), m, S, T(1), ws, ldn, st);
+      scale_copy<T>(Kws, ldn, n, S, T(a), Kws, ldn, st);
+      gemm_nn<T, double>(n, S, ic, T(1), KV(k), ldn, e, ic, T(1), Kws, ldn, st);
+    }
+    cudaError_t ce = cudaGetLastError();
+    return ce == cudaSuccess ? CAKF_OK : fail(CAKF_ERR_CUDA, std::string("sampler: ") + cudaGetErrorString(ce));
+  }
+
   // ---------------------------------------------------------------- NLL gradient (tangent pass)
   // Forward-mode derivatives of the filter with the actions S_k and truncation rotations U_k of the
   // last filter run held fixed, for the four log-hyperparameters at once (p = 0: log l_x,
@@ -1533,6 +1630,56 @@ int cakf_get_actions(cakf_ctx* c, double* actions_out, int32_t* counts_out) {
     off += cnt_el;
   }
   return CAKF_OK;
+}
+
+int cakf_sample(cakf_ctx* c, int32_t n_samples, const double* x0, const double* q, const double* eps,
+                double* filter_out, double* smoother_out, void* cuda_stream) {
+  if (!c) return fail(CAKF_ERR_STATE, "cakf_sample: no context (cakf_filter creates it)");
+  if (!c->filtered) return fail(CAKF_ERR_STATE, "cakf_sample needs a successful cakf_filter on this context");
+  if (n_samples < 1 || n_samples > 1024 || !x0 || !q || !eps)
+    return fail(CAKF_ERR_ARG, "cakf_sample: 1 <= n_samples <= 1024 and x0, q, eps must be given");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const int S = n_samples, n = c->n, T = c->T;
+  const size_t blk = (size_t)n * S, tot = (size_t)(T + 1) * blk, Ne = (size_t)c->obs_ptr[T] * S;
+  const size_t es = elem_size(c->precision);
+  const size_t lS = (size_t)c->ldn * S, mS = (size_t)std::max(c->mmax, 1) * S;
+  const size_t work_elems = 5 * lS + 2 * mS;
+  const size_t ii = (size_t)std::max(c->imax, 1) * S;
+  const size_t small_elems = (size_t)(T + 2) * ii + (size_t)std::max(c->rmax, 1) * S + 2 * ii + 64;
+  double *xf = nullptr, *xs = nullptr, *qd = nullptr, *ed = nullptr, *small = nullptr;
+  void* work = nullptr;
+  auto release = [&]() {
+    for (void* p : {(void*)xf, (void*)xs, (void*)qd, (void*)ed, (void*)small, work}) if (p) cudaFree(p);
+  };
+  if (cudaMalloc(&xf, tot * 8) != cudaSuccess || cudaMalloc(&xs, tot * 8) != cudaSuccess ||
+      cudaMalloc(&qd, tot * 8) != cudaSuccess || cudaMalloc(&ed, std::max<size_t>(Ne, 1) * 8) != cudaSuccess ||
+      cudaMalloc(&small, small_elems * 8) != cudaSuccess || cudaMalloc(&work, work_elems * es) != cudaSuccess) {
+    cudaGetLastError();
+    release();
+    return fail(CAKF_ERR_OOM, "cakf_sample: workspace allocation failed");
+  }
+  int rc;
+  if ((rc = copy_in(xf, x0, blk * 8, st)) || (rc = copy_in(qd, q, tot * 8, st)) || (rc = copy_in(ed, eps, Ne * 8, st))) {
+    release();
+    return rc;
+  }
+  cudaMemsetAsync(c->err, 0, sizeof(int), st);
+  if (c->precision == CAKF_FP64) {
+    Runner<double> r = make_runner<double>(c, st);
+    rc = r.sample(S, xf, xs, qd, ed, (double*)work, work_elems, small, small_elems);
+  } else {
+    Runner<float> r = make_runner<float>(c, st);
+    rc = r.sample(S, xf, xs, qd, ed, (float*)work, work_elems, small, small_elems);
+  }
+  if (!rc) rc = sync_and_check(c, st, "cakf_sample");
+  if (!rc && filter_out) rc = copy_out(filter_out, xf, tot, st);
+  if (!rc && smoother_out) rc = copy_out(smoother_out, xs, tot, st);
+  if (!rc) {
+    cudaError_t ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) rc = fail(CAKF_ERR_CUDA, cudaGetErrorString(ce));
+  }
+  release();
+  return rc;
 }
 
 int cakf_get_diagnostics(const cakf_ctx* c, int32_t* actions, double* rel_residual, double* min_eta,

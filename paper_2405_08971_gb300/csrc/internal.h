@@ -115,6 +115,16 @@ void batch_resid(const T* GS, int m, int i, const double* L, const double* z, co
 template <class T>
 void batch_v(const T* S, int m, int i, const double* L, const double* z, T* Vv, cudaStream_t st);
 
+// Posterior sampler helpers (S draws as columns): xp = a xprev + b + q; d = y - xp[obs] - eps;
+// x = xa + alpha t.
+void samp_predict(const double* xprev, const double* q, const double* mu_k, const double* mu_km1, double a, int n,
+                  int S, double* xp, cudaStream_t st);
+template <class T>
+void samp_resid(const double* y, const double* xp, const int* obs, const double* eps, int m, int n, int S, T* d,
+                cudaStream_t st);
+template <class T>
+void samp_add(const double* xa, const T* t, int ldt, double alpha, int n, int S, double* x, cudaStream_t st);
+
 // Record msg as the calling thread's cakf_last_error message; returns code.
 int set_last_error(int code, const char* msg);
 

@@ -1766,6 +1766,56 @@ template void batch_resid<float>(const float*, int, int, const double*, const do
 template void batch_resid<double>(const double*, int, int, const double*, const double*, const double*, double*,
                                   cudaStream_t);
 
+// ------------------------------------------------------------------------------------------
+// Posterior sampler (the CAKF/CAKS sampler algorithm): S draws as the columns of n x S blocks.
+// xp = a xprev + (mu_k - a mu_{k-1}) + q   (FP64; mu pointers may be null)
+__global__ void k_samp_predict(const double* __restrict__ xprev, const double* __restrict__ q,
+                               const double* __restrict__ mu_k, const double* __restrict__ mu_km1, double a, int n,
+                               int S, double* __restrict__ xp) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = blockIdx.y;
+  if (j >= n || s >= S) return;
+  const double b = mu_k ? mu_k[j] - a * mu_km1[j] : 0.0;
+  xp[(size_t)s * n + j] = fma(a, xprev[(size_t)s * n + j], b + q[(size_t)s * n + j]);
+}
+// d = y - xp[obs] - eps  (m x S, precision T)
+template <class T>
+__global__ void k_samp_resid(const double* __restrict__ y, const double* __restrict__ xp, const int* __restrict__ obs,
+                             const double* __restrict__ eps, int m, int n, int S, T* __restrict__ d) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = blockIdx.y;
+  if (i >= m || s >= S) return;
+  d[(size_t)s * m + i] = T(y[i] - xp[(size_t)s * n + obs[i]] - eps[(size_t)s * m + i]);
+}
+// x = xa + alpha * t  (x, xa FP64 n x S with ld n; t precision T with ld ldt)
+template <class T>
+__global__ void k_samp_add(const double* __restrict__ xa, const T* __restrict__ t, int ldt, double alpha, int n, int S,
+                           double* __restrict__ x) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = blockIdx.y;
+  if (j >= n || s >= S) return;
+  x[(size_t)s * n + j] = fma(alpha, (double)t[(size_t)s * ldt + j], xa[(size_t)s * n + j]);
+}
+void samp_predict(const double* xprev, const double* q, const double* mu_k, const double* mu_km1, double a, int n,
+                  int S, double* xp, cudaStream_t st) {
+  k_samp_predict<<<dim3(cdiv(n, 256), S), 256, 0, st>>>(xprev, q, mu_k, mu_km1, a, n, S, xp); note_launch();
+}
+template <class T>
+void samp_resid(const double* y, const double* xp, const int* obs, const double* eps, int m, int n, int S, T* d,
+                cudaStream_t st) {
+  if (m <= 0) return;
+  k_samp_resid<T><<<dim3(cdiv(m, 256), S), 256, 0, st>>>(y, xp, obs, eps, m, n, S, d); note_launch();
+}
+template <class T>
+void samp_add(const double* xa, const T* t, int ldt, double alpha, int n, int S, double* x, cudaStream_t st) {
+  k_samp_add<T><<<dim3(cdiv(n, 256), S), 256, 0, st>>>(xa, t, ldt, alpha, n, S, x); note_launch();
+}
+template void samp_resid<float>(const double*, const double*, const int*, const double*, int, int, int, float*, cudaStream_t);
+template void samp_resid<double>(const double*, const double*, const int*, const double*, int, int, int, double*,
+                                 cudaStream_t);
+template void samp_add<float>(const double*, const float*, int, double, int, int, double*, cudaStream_t);
+template void samp_add<double>(const double*, const double*, int, double, int, int, double*, cudaStream_t);
+
 void set_diag(double* G, int ld, const double* lam, double scale, int r, cudaStream_t st) {
   if (r <= 0) return;
   k_set_diag<<<cdiv(r, 256), 256, 0, st>>>(G, ld, lam, scale, r); note_launch();
