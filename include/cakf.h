@@ -124,6 +124,11 @@ typedef struct {
   int32_t checkpoint_every;   /* segment length of CAKF_STORE_BF16 / CAKF_RECOMPUTE (the steps
                                  restored at a time; 0 = 20); ignored for CAKF_STORE_FP32     */
   int32_t policy;             /* CAKF_POLICY_CG | CAKF_POLICY_COORDINATE | CAKF_POLICY_BATCH     */
+  int32_t freeze_truncation;  /* 1: instead of eigendecomposing, the filter truncates with the
+                                 rotations U_k of the previous cakf_filter on the same context
+                                 (same sizes; with replay_actions this evaluates the frozen
+                                 modified model of cakf_nll_backward at other hyperparameters, for
+                                 finite-difference checks); 0: normal                          */
 } cakf_problem;
 
 typedef struct cakf_ctx cakf_ctx;   /* library-owned state; holds the stored factors */
@@ -175,7 +180,8 @@ typedef struct {
  * The context keeps per-step factors for cakf_smooth / cakf_nll / cakf_nll_backward.
  * Errors: CAKF_ERR_ARG (sizes, indices out of range, abi_version), CAKF_ERR_OOM,
  *         CAKF_ERR_NUMERIC (non-finite result or non-positive-definite action Gram),
- *         CAKF_ERR_CUDA, CAKF_ERR_TIMEOUT.
+ *         CAKF_ERR_CUDA, CAKF_ERR_TIMEOUT, CAKF_ERR_STATE (freeze_truncation without a previous
+ *         successful run of the same sizes on the context).
  */
 int cakf_filter(const cakf_problem* p, cakf_ctx** ctx_inout, double* mean_out, double* var_out,
                 void* cuda_stream);
@@ -288,7 +294,7 @@ int cakf_gram_matmul_noalloc(int32_t kernel, double log_lx, double log_sf2, int3
  *   precision  CAKF_FP32: FP32 SIMT kernels; a tensor-core mode (CAKF_TF32, CAKF_BF16, CAKF_FP16X3,
  *           CAKF_TF32X3): tcgen05 with split TF32 operands (hi + lo, three MMAs, FP32
  *           accumulation) for the large products, as in those modes' filter and smoother.
- * Allocates and frees its workspace on every call (verification and tools, not the hot loop).
+ * Its workspace is allocated on the first call per thread and kept (grown when needed).
  * Errors: CAKF_ERR_ARG, CAKF_ERR_OOM, CAKF_ERR_CUDA, CAKF_ERR_TIMEOUT.
  */
 int cakf_factor_gemm(int32_t trans_a, int32_t M, int32_t N, int32_t K, double alpha, const float* A, int32_t lda,

@@ -35,7 +35,7 @@ class cakf_problem(C.Structure):
         ("obs_idx", C.c_void_p), ("y", C.c_void_p), ("prior_mean", C.c_void_p), ("budget_i", C.c_int32),
         ("rank_r", C.c_int32), ("cg_rtol", C.c_double), ("precision", C.c_int32),
         ("replay_actions", C.c_void_p), ("replay_counts", C.c_void_p), ("factor_storage", C.c_int32),
-        ("checkpoint_every", C.c_int32), ("policy", C.c_int32),
+        ("checkpoint_every", C.c_int32), ("policy", C.c_int32), ("freeze_truncation", C.c_int32),
     ]
 
 
@@ -147,7 +147,7 @@ class Context:
 
 def make_problem(coords, kernel, log_lx, log_lt, log_sf2, log_sn2, T, dt, obs_ptr, obs_idx, y, budget_i, rank_r,
                  precision="fp32", prior_mean=None, cg_rtol=0.0, replay_actions=None, replay_counts=None,
-                 factor_storage="fp32", checkpoint_every=0, policy="cg"):
+                 factor_storage="fp32", checkpoint_every=0, policy="cg", freeze_truncation=False):
     """Build a cakf_problem; returns (struct, keepalive list)."""
     keep = []
     p = cakf_problem()
@@ -176,6 +176,7 @@ def make_problem(coords, kernel, log_lx, log_lt, log_sf2, log_sn2, T, dt, obs_pt
     p.factor_storage = STORAGE[factor_storage] if isinstance(factor_storage, str) else int(factor_storage)
     p.checkpoint_every = int(checkpoint_every)
     p.policy = POLICIES[policy] if isinstance(policy, str) else int(policy)
+    p.freeze_truncation = 1 if freeze_truncation else 0
     if replay_actions is not None:
         ra = np.ascontiguousarray(replay_actions, dtype=np.float64)
         rc = np.ascontiguousarray(replay_counts, dtype=np.int32)
@@ -185,7 +186,8 @@ def make_problem(coords, kernel, log_lx, log_lt, log_sf2, log_sn2, T, dt, obs_pt
 
 
 def problem_from_workload(w, precision="fp32", cg_rtol=0.0, replay=None, budget_i=None, rank_r=None,
-                          factor_storage="fp32", checkpoint_every=0, policy="cg", **hp):
+                          factor_storage="fp32", checkpoint_every=0, policy="cg", freeze_truncation=False,
+                          **hp):
     """cakf_problem of a `synth.Workload`-like object (any object with the same fields)."""
     ra = rc = None
     if replay is not None:
@@ -195,7 +197,7 @@ def problem_from_workload(w, precision="fp32", cg_rtol=0.0, replay=None, budget_
                         w.obs_idx, w.y, w.budget_i if budget_i is None else budget_i,
                         w.rank_r if rank_r is None else rank_r, precision=precision, prior_mean=w.prior_mean,
                         cg_rtol=cg_rtol, replay_actions=ra, replay_counts=rc, factor_storage=factor_storage,
-                        checkpoint_every=checkpoint_every, policy=policy)
+                        checkpoint_every=checkpoint_every, policy=policy, freeze_truncation=freeze_truncation)
 
 
 def _out(arr, shape):

@@ -139,6 +139,7 @@ struct cakf_ctx {
   // keeps BF16 copies of every step's factors
   int storage = CAKF_STORE_FP32, ckpt_req = 0, seg_c = 0, res_a = 1, res_b = 0;
   int policy = CAKF_POLICY_CG;
+  bool freeze = false;     // truncate with the stored rotations of the previous run
   void* GSb = nullptr;     // batch policies: G [S r0] (m x (i + 1))
   double* Lb = nullptr;    // batch policies: Cholesky factor of S^T G S and z = L^-1 S^T r0
   void* ckptM = nullptr;
@@ -826,6 +827,15 @@ struct Runner {
     }
     const int N = rp + ic;
     const int keep = std::min(c->rank_r, N);
+    T* U = (T*)c->UT;
+    if (c->freeze) {
+      // the rotation of the previous run at this step (the frozen modified model)
+      convert_from_f64<T>(c->Upool + c->off_U[k], N, N, keep, U, N, st);
+      if (rp > 0) gemm_nn<T, T>(n, keep, rp, T(a), Mk(k - 1), ldn, U, N, T(0), Mk(k), ldn, st);
+      gemm_nn<T, T>(n, keep, ic, T(1), PVk, ldn, U + rp, N, rp > 0 ? T(1) : T(0), Mk(k), ldn, st);
+      rowsumsq<T>(Mk(k), ldn, n, keep, 0.0, c->rs_plus, st);
+      return CAKF_OK;
+    }
     double* G = c->gram;
     cudaMemsetAsync(G, 0, (size_t)N * N * sizeof(double), st);
     set_diag(G, N, c->lam, a2, rp, st);
@@ -840,7 +850,6 @@ struct Runner {
     if (rc) return rc;
     sub_sum(c->wv, keep, c->dropped_f + k, st);
     // M+_k = a M+_{k-1} U[0:rp, :] + P^- W U[rp:N, :]
-    T* U = (T*)c->UT;
     if (rp > 0) gemm_nn<T, T>(n, keep, rp, T(a), Mk(k - 1), ldn, U, N, T(0), Mk(k), ldn, st);
     gemm_nn<T, T>(n, keep, ic, T(1), PVk, ldn, U + rp, N, rp > 0 ? T(1) : T(0), Mk(k), ldn, st);
     cudaMemcpyAsync(c->lam, c->wv, keep * sizeof(double), cudaMemcpyDeviceToDevice, st);
@@ -1486,6 +1495,9 @@ int cakf_filter(const cakf_problem* p, cakf_ctx** ctx_inout, double* mean_out, d
   cudaStream_t st = (cudaStream_t)cuda_stream;
   cakf_ctx* c = *ctx_inout;
   bool fresh = false;
+  if (p->freeze_truncation && (!c || !c->filtered || !same_shape(c, p) || c->rank_r <= 0))
+    return fail(CAKF_ERR_STATE, "freeze_truncation needs a previous successful cakf_filter of the same sizes "
+                                "(with truncation) on this context");
   if (c && !same_shape(c, p)) { c->release(); c->filtered = false; fresh = true; }
   if (!c) { c = new cakf_ctx(); *ctx_inout = c; fresh = true; }
   c->n = p->n; c->dim = p->dim; c->kernel = p->kernel; c->T = p->T; c->budget = p->budget_i; c->rank_r = p->rank_r;
@@ -1493,6 +1505,7 @@ int cakf_filter(const cakf_problem* p, cakf_ctx** ctx_inout, double* mean_out, d
   c->sn2 = std::exp(p->log_sn2); c->dt = p->dt; c->a = std::exp(-p->dt / c->lt); c->cg_rtol = p->cg_rtol;
   c->has_mu = p->prior_mean != nullptr;
   c->replay = p->replay_actions != nullptr;
+  c->freeze = p->freeze_truncation != 0;
   if (c->replay) c->replay_counts.assign(p->replay_counts, p->replay_counts + p->T + 1);
   c->filtered = false;
   if (fresh || c->bufs.empty()) {
@@ -1841,16 +1854,19 @@ extern "C" int cakf_factor_gemm(int32_t trans_a, int32_t M, int32_t N, int32_t K
     return fail(CAKF_ERR_ARG, "cakf_factor_gemm: precision must be CAKF_FP32 or a tensor-core mode");
   cudaStream_t st = (cudaStream_t)cuda_stream;
   const int mode = precision == CAKF_FP32 ? 1 : 2;
-  const size_t part_elems = std::max<size_t>(size_t(1) << 22, (size_t)M * N * 2);
-  double *part = nullptr, *c64 = nullptr;
-  int* err = nullptr;
-  auto release = [&]() { if (part) cudaFree(part); if (c64) cudaFree(c64); if (err) cudaFree(err); };
-  if (cudaMalloc(&part, part_elems * sizeof(double)) != cudaSuccess || cudaMalloc(&err, sizeof(int)) != cudaSuccess ||
-      (trans_a && cudaMalloc(&c64, (size_t)M * N * sizeof(double)) != cudaSuccess)) {
+  const size_t part_elems = std::max<size_t>(size_t(1) << 24, (size_t)M * N * 2);
+  // workspace kept per thread (grown when needed), like cakf_gram_matmul's scratch
+  static thread_local GramScratch ws;
+  int rc;
+  if ((rc = ensure(ws.stage, ws.stage_bytes, part_elems * sizeof(double) + (size_t)M * N * sizeof(double) + 256)))
+    return rc;
+  if (!ws.err && cudaMalloc(&ws.err, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
-    release();
     return fail(CAKF_ERR_OOM, "cakf_factor_gemm: workspace allocation failed");
   }
+  double* part = reinterpret_cast<double*>(ws.stage);
+  double* c64 = part + part_elems;
+  int* err = ws.err;
   cudaMemsetAsync(err, 0, sizeof(int), st);
   const int saved = gemm_mode();
   set_gemm_mode(mode);
@@ -1867,7 +1883,6 @@ extern "C" int cakf_factor_gemm(int32_t trans_a, int32_t M, int32_t N, int32_t K
   cudaError_t ce = cudaStreamSynchronize(st);
   int e = 0;
   if (ce == cudaSuccess) cudaMemcpy(&e, err, sizeof(int), cudaMemcpyDeviceToHost);
-  release();
   if (ce != cudaSuccess) return fail(CAKF_ERR_CUDA, std::string("cakf_factor_gemm: ") + cudaGetErrorString(ce));
   if (e == kErrTimeout) return fail(CAKF_ERR_TIMEOUT, "cakf_factor_gemm: a device-side wait exceeded its limit");
   if (e) return fail(CAKF_ERR_NUMERIC, "cakf_factor_gemm: numeric error");

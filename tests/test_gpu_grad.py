@@ -94,3 +94,54 @@ def test_gradient_fd_instance_n1024_t20():
     print("n1024 fd", g_fd, "gpu", g)
     assert abs(nll - nll_o) < 1e-9 * abs(nll_o)
     assert rel(g, g_fd) < 1e-5, (g, g_fd)
+
+
+def test_gradient_c4_configuration_against_frozen_fd():
+    """The gradient configuration at full size (128 x 128 grid, n = 16,384, T = 200, m = 2,000,
+    i = 32, r = 256): the device FP64 gradient against central differences (h = 1e-4 in log space)
+    of the device FP64 NLL of the same frozen modified model (the base run's actions replayed and
+    its truncation rotations reused through freeze_truncation), within 1e-5 relative; and the FP32
+    gradient of the same frozen actions against the FP64 one (reported, 1e-3)."""
+    w = synth.grid2d_16k(T=200)
+    prob = ck.problem_from_workload(w, precision="fp64")
+    ctx, _, _ = ck.cakf_filter(prob, want_outputs=False)
+    g64 = ck.cakf_nll_backward(ctx)
+    S, _ = ck.cakf_get_actions(ctx, w.obs_ptr)
+    rep = ck.pack_actions(S, w.T)
+    theta0 = np.array([w.log_lx, w.log_lt, w.log_sf2, w.log_sn2])
+    names = ["log_lx", "log_lt", "log_sf2", "log_sn2"]
+    h, g_fd = 1e-4, np.zeros(4)
+    for p in range(4):
+        vals = []
+        for sgn in (1, -1):
+            th = theta0.copy()
+            th[p] += sgn * h
+            pr = ck.problem_from_workload(w, precision="fp64", replay=rep, freeze_truncation=True,
+                                          **{nm: float(v) for nm, v in zip(names, th)})
+            ctx, _, _ = ck.cakf_filter(pr, ctx, want_outputs=False)
+            vals.append(ck.cakf_nll(ctx))
+        g_fd[p] = (vals[0] - vals[1]) / (2 * h)
+    ctx.close()
+    e = rel(g64, g_fd)
+    print("c4 fp64 gradient", g64, "frozen fd", g_fd, f"rel {e:.2e}")
+    assert e < 1e-5, (g64, g_fd)
+    prob32 = ck.problem_from_workload(w, precision="fp32", replay=rep)
+    ctx32, _, _ = ck.cakf_filter(prob32, want_outputs=False)
+    g32 = ck.cakf_nll_backward(ctx32)
+    ctx32.close()
+    print("c4 fp32 gradient", g32, f"rel to fp64 {rel(g32, g64):.2e}")
+    assert rel(g32, g64) < 1e-3
+
+
+def test_adam_fit_decreases_the_nll():
+    """Ten Adam steps through the autograd Function on the n = 1,024, T = 20 instance, from both
+    lengthscales doubled: the NLL decreases and the lengthscales move toward the generating ones."""
+    from paper_2405_08971_gb300.autograd import workload_data
+    from paper_2405_08971_gb300.fit import fit_adam
+    w = synth.fd_grid2d_1k(T=20)
+    theta0 = [w.log_lx + np.log(2.0), w.log_lt + np.log(2.0), w.log_sf2, w.log_sn2]
+    theta, trace = fit_adam(workload_data(w), theta0, steps=10, lr=0.05, precision="fp32")
+    nlls = [t[1] for t in trace]
+    print("adam nll trace", [f"{v:.2f}" for v in nlls])
+    assert nlls[-1] < nlls[0]
+    assert abs(theta[0] - w.log_lx) < abs(theta0[0] - w.log_lx)
