@@ -409,6 +409,66 @@ def sample_run(w, filt: FilterResult, x0, q, eps, model: Optional[Model] = None)
     return xf, xs
 
 
+# ----------------------------------------------------------------------------- temporal interpolation
+def interpolate_run(w, filt: FilterResult, smooth_W, smooth_w, tq, mu_q=None, model: Optional[Model] = None):
+    """Filter and smoother marginals at query times between the steps (the interpolation corollary of
+    the appendix, in downdate form), for the OU prior A(t, s) = exp(-(t - s)/l_t) I.
+
+    For t_k <= t < t_{k+1} (t_k = k dt; k = T for t >= t_T): a_tau = A(t, t_k),
+      filter:   m(t) = a_tau m_k + b(t, t_k),  P(t) = K - a_tau^2 M_k M_k^T  (M_k the updated factor),
+      smoother: m^s(t) = m(t) + P(t) A(t_{k+1}, t)^T ws_{k+1},
+                P^s(t) = P(t) - P(t) A^T Ws_{k+1} (P(t) A^T Ws_{k+1})^T   (t < t_T; else = filter),
+    with b(t, t_k) = mu(t) - a_tau mu_k (mu_q[q] the prior mean at tq[q], or zero).  smooth_W[k],
+    smooth_w[k] are the smoother messages Ws_k, ws_k of Alg. 3 (smoother_messages).
+    Returns (filter means, filter variances, smoother means, smoother variances), each (len(tq), n)."""
+    model = model or model_from(w)
+    T, n = w.T, model.n
+    lt = -w.dt / math.log(model.a)
+    out = [np.zeros((len(tq), n)) for _ in range(4)]
+    for q, t in enumerate(tq):
+        k = min(int(math.floor(t / w.dt + 1e-12)), T)
+        tau = t - k * w.dt
+        at = math.exp(-tau / lt)
+        mu_t = np.zeros(n) if mu_q is None else mu_q[q]
+        mu_k = np.zeros(n) if model.mu is None else model.mu[k]
+        m = at * filt.m[k] + (mu_t - at * mu_k)
+        Mt = at * filt.M_hat[k]
+        v = model.sf2 - np.sum(Mt * Mt, axis=1)
+        out[0][q], out[1][q] = m, v
+        if k == T:
+            out[2][q], out[3][q] = m, v
+            continue
+        a2 = math.exp(-(w.dt - tau) / lt)
+        X = a2 * np.concatenate([smooth_W[k + 1], smooth_w[k + 1][:, None]], axis=1)
+        PX = model.K_times(X) - Mt @ (Mt.T @ X)
+        out[2][q] = m + PX[:, -1]
+        E = PX[:, :-1]
+        out[3][q] = v - np.sum(E * E, axis=1)
+    return out
+
+
+def smoother_messages(w, filt: FilterResult, model: Optional[Model] = None, rank_r=None):
+    """The smoother messages (Ws_k, ws_k), k = 1..T, of Alg. 3 with its truncation (the factors the
+    smoother carries from step k + 1 to step k); entry k holds the message after step k's update."""
+    model = model or model_from(w)
+    rank_r = w.rank_r if rank_r is None else rank_r
+    T, n, a = w.T, model.n, model.a
+    Wm = [None] * (T + 1)
+    wm = [None] * (T + 1)
+    ws, Ws = filt.w[T], filt.W[T]
+    Wm[T], wm[T] = Ws, ws
+    for k in range(T - 1, 0, -1):
+        X = a * np.concatenate([Ws, ws[:, None]], axis=1)
+        Mp = filt.M_pred[k]
+        PmX = model.K_times(X) - Mp @ (Mp.T @ X)
+        Wk = filt.W[k]
+        Y2 = X - Wk @ (Wk.T @ PmX)
+        ws = filt.w[k] + Y2[:, -1]
+        Ws, _, _, _ = truncate(np.concatenate([Wk, Y2[:, :-1]], axis=1), rank_r)
+        Wm[k], wm[k] = Ws, ws
+    return Wm, wm
+
+
 # ----------------------------------------------------------------------------- NLL and gradient
 def nll_terms(filt: FilterResult) -> np.ndarray:
     return filt.nll.copy()

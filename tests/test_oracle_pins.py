@@ -275,6 +275,44 @@ def test_sampler_at_full_budget_is_exact_matheron():
             assert rel(got, exact) < 1e-9, (upto, k)
 
 
+def test_interpolation_at_full_budget_is_the_exact_gp_posterior():
+    """Filter and smoother marginals at times between the steps (interpolation corollary) equal the
+    exact space-time GP posterior at those times when the budget is full and nothing is truncated:
+    the filter conditions on the data up to the last step before t, the smoother on all data.  The
+    seasonal prior mean is evaluated at the query times.  At the step times themselves the
+    interpolation returns the filter and smoother outputs."""
+    w = synth.small(n=30, dim=2, m=8, T=4, budget_i=8, rank_r=0, seasonal=True, seed=55)
+    f = oracle.filter_run(w)
+    Wm, wm = oracle.smoother_messages(w, f)
+    m = oracle.model_from(w)
+    tq = np.array([0.03, 0.1, 0.17, 0.25, 0.31, 0.399, 0.4, 0.47])
+    mu_q = np.stack([0.5 * np.sin(2 * np.pi * t / 5.0) * np.cos(2 * np.pi * w.coords[:, 0]) for t in tq])
+    mf, vf, ms, vs = oracle.interpolate_run(w, f, Wm, wm, tq, mu_q=mu_q)
+    K = oracle.kernel_matrix(w.coords, w.coords, w.kernel, m.lx, m.sf2)
+    lt = math.exp(w.log_lt)
+    for q, t in enumerate(tq):
+        k = min(int(np.floor(t / w.dt + 1e-12)), w.T)
+        for upto, gm, gv in ((k, mf[q], vf[q]), (w.T, ms[q], vs[q])):
+            if upto == 0:
+                exp_m, exp_v = mu_q[q], np.diag(K)
+            else:
+                st = np.concatenate([np.full(len(w.obs(j)), j) for j in range(1, upto + 1)])
+                ix = np.concatenate([w.obs(j) for j in range(1, upto + 1)])
+                Czz = np.exp(-np.abs(st[:, None] - st[None, :]) * w.dt / lt) * K[np.ix_(ix, ix)] \
+                    + m.sn2 * np.eye(ix.size)
+                Ctz = np.exp(-np.abs(t - st * w.dt) / lt)[None, :] * K[:, ix]
+                resid = np.concatenate([w.yk(j) - w.prior_mean[j][w.obs(j)] for j in range(1, upto + 1)])
+                exp_m = mu_q[q] + Ctz @ np.linalg.solve(Czz, resid)
+                exp_v = np.diag(K) - np.einsum("ij,ji->i", Ctz, np.linalg.solve(Czz, Ctz.T))
+            assert rel(gm, exp_m) < 1e-9, (t, upto)
+            assert rel(gv, exp_v) < 1e-9, (t, upto)
+    # at the step times the interpolation is the filter / smoother output
+    ms_o, vs_o, _ = oracle.smoother_run(w, f)
+    tk = np.arange(w.T + 1) * w.dt
+    o = oracle.interpolate_run(w, f, Wm, wm, tk, mu_q=w.prior_mean)
+    assert rel(o[0], f.m) < 1e-13 and rel(o[2], ms_o) < 1e-13 and rel(o[3], vs_o) < 1e-13
+
+
 def test_matern_against_sklearn():
     sk = pytest.importorskip("sklearn.gaussian_process.kernels")
     rng = np.random.default_rng(0)
