@@ -326,6 +326,24 @@ int cakf_eig_topk(const double* A, int32_t N, int32_t keep, double* w_out, doubl
 int cakf_probe_peaks(double* mufu_ops_per_s, double* fp64_flops_per_s, void* cuda_stream);
 
 /*
+ * cakf_interpolate -- filter and smoother marginals at query times between (or after) the steps
+ * (the temporal-interpolation corollary of the appendix in downdate form), for the OU prior:
+ * for t_k <= t < t_{k+1} (t_k = k dt; k = T for t >= t_T), with A(t, s) = exp(-(t - s) / l_t),
+ *   filter    m(t) = A(t, t_k) m_k + mu(t) - A(t, t_k) mu_k,  P(t) = K - A(t, t_k)^2 M_k M_k^T,
+ *   smoother  m^s(t) = m(t) + P(t) A(t_{k+1}, t) ws_{k+1},
+ *             P^s(t) = P(t) - P(t) A Ws_{k+1} (P(t) A Ws_{k+1})^T   (the filter's for t >= t_T),
+ * with the smoother messages (Ws, ws) of Alg. 3.  Runs one smoother pass (the products come from
+ * the stored factors and the smoother's K-recursion: no kernel evaluations).
+ *   nq      number of query times, >= 1;  tq  nq times >= 0 (host)
+ *   mu_q    NULL, or nq x n prior mean at the query times (required when the problem has a prior
+ *           mean), host or device
+ *   fmean, fvar, smean, svar   nq x n outputs (host or device, each may be NULL)
+ * Errors: CAKF_ERR_STATE (no successful cakf_filter), CAKF_ERR_ARG, CAKF_ERR_OOM, CAKF_ERR_CUDA.
+ */
+int cakf_interpolate(cakf_ctx* ctx, int32_t nq, const double* tq, const double* mu_q, double* fmean, double* fvar,
+                     double* smean, double* svar, void* cuda_stream);
+
+/*
  * cakf_sample -- draws from the computation-aware posterior of the last cakf_filter (the CAKF/CAKS
  * sampler algorithm of the appendix: Matheron's rule in the modified model, with the smoother in
  * inverse-free form).  The filter's stored factors are reused: no kernel values are evaluated.

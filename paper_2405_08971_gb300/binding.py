@@ -86,6 +86,8 @@ def lib():
         L.cakf_factor_gemm.restype = C.c_int
         L.cakf_probe_peaks.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
         L.cakf_probe_peaks.restype = C.c_int
+        L.cakf_interpolate.argtypes = [vp, C.c_int32, vp, vp, vp, vp, vp, vp, vp]
+        L.cakf_interpolate.restype = C.c_int
         L.cakf_sample.argtypes = [vp, C.c_int32, vp, vp, vp, vp, vp, vp]
         L.cakf_sample.restype = C.c_int
         L.cakf_get_diagnostics.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -420,6 +422,18 @@ def cakf_probe_peaks(stream=None) -> dict:
     mufu, fp64 = C.c_double(), C.c_double()
     _check(lib().cakf_probe_peaks(C.byref(mufu), C.byref(fp64), stream))
     return {"mufu_ops_per_s": mufu.value, "fp64_flops_per_s": fp64.value}
+
+
+def cakf_interpolate(ctx: Context, tq, mu_q=None, stream=None):
+    """Filter and smoother marginals at the query times tq (host): returns (filter means, filter
+    variances, smoother means, smoother variances), each (len(tq), n)."""
+    tq = np.ascontiguousarray(tq, dtype=np.float64)
+    nq, n = tq.size, ctx.n
+    outs = [np.empty((nq, n)) for _ in range(4)]
+    mq = None if mu_q is None else np.ascontiguousarray(mu_q, dtype=np.float64)
+    _check(lib().cakf_interpolate(ctx.handle, nq, tq.ctypes.data, None if mq is None else mq.ctypes.data,
+                                  *[o.ctypes.data for o in outs], stream))
+    return tuple(outs)
 
 
 def cakf_sample(ctx: Context, x0, q, eps, obs_ptr, stream=None):

@@ -10,6 +10,7 @@
 //   S[k]     m_k x i_k actions
 //   mf, vf   (T+1) x n filter means / variances (FP64)
 #include <atomic>
+#include <type_traits>
 #include <cstring>
 #include <cstdio>
 #include <string>
@@ -443,6 +444,15 @@ struct Runner {
 
   // phase timers (profiling on): begin returns the start event, end records the pair
   bool quiet = false;   // no phase timers (recomputation inside the smoother or gradient pass)
+  // temporal interpolation queries (cakf_interpolate): per step k the query indices with
+  // t_k <= t < t_{k+1}; outputs nq x n (device, FP64); mu_q nq x n or null
+  struct Queries {
+    std::vector<std::vector<int>> at_k;
+    std::vector<double> tq;
+    const double* mu_q = nullptr;
+    double *fm = nullptr, *fv = nullptr, *sm = nullptr, *sv = nullptr;
+  };
+  const Queries* qs = nullptr;
   cudaEvent_t ph_begin() {
     if (!c->profiling || quiet) return nullptr;
     cudaEvent_t e = c->ev();
@@ -927,9 +937,11 @@ struct Runner {
     T* KWn = (T*)c->KWb;
     if (cw > 0) cudaMemcpyAsync(KW, KV(T_), (size_t)ldn * (cw + 1) * sizeof(T), cudaMemcpyDeviceToDevice, st);
     else cudaMemsetAsync(KW, 0, (size_t)ldn * sizeof(T), st);
+    if (qs) interp_at(T_, cw, Ws, ws, KW);
     for (int k = T_ - 1; k >= 0; --k) {
       if (k >= 1)
         if (int rc = restore(k)) return rc;
+      if (qs) interp_at(k, cw, Ws, ws, KW);
       // X = A^T [Ws ws] = a [Ws ws]
       cudaEvent_t ph3 = ph_begin();
       build_x<T>(Ws, ldn, cw, ws, T(a), n, Xs, ldn, st);
@@ -1055,6 +1067,53 @@ struct Runner {
       if (ce != cudaSuccess) return fail(CAKF_ERR_CUDA, std::string("smoother step: ") + cudaGetErrorString(ce));
     }
     return CAKF_OK;
+  }
+
+  // ---------------------------------------------------------------- temporal interpolation
+  // Queries t_k <= t < t_{k+1} (the interpolation corollary in downdate form, OU prior): with
+  // at = A(t, t_k), a2 = A(t_{k+1}, t), M_k = (a M+_{k-1}, [P^-W]_k) the updated factor,
+  //   filter   m(t) = at m_k + b(t, t_k), var(t) = sf2 - at^2 (sf2 - var_k),
+  //   smoother Y = P(t) a2 [Ws ws]_{k+1} = a2 (K[Ws ws] - at^2 M_k (M_k^T [Ws ws])) with K[Ws ws]
+  //            carried by the smoother's recursion, m^s(t) = m(t) + Y[:, cw],
+  //            var^s(t) = var(t) - rowsumsq(Y[:, :cw]);  at k = T the smoother output is the filter's.
+  void interp_at(int k, int cw, const T* Ws, const T* ws, const T* KW) {
+    const std::vector<int>& ids = qs->at_k[k];
+    if (ids.empty()) return;
+    const int n = c->n, ldn = c->ldn;
+    const double dt = c->dt, lt = c->lt;
+    T* Xs = (T*)c->Xs;
+    T* Y = (T*)c->Y;
+    const int rp = k >= 1 ? c->mcols[k - 1] : 0;
+    const int ic = (k >= 1 && mk(k) > 0) ? c->icap[k] : 0;
+    if (k < c->T) build_x<T>(Ws, ldn, cw, ws, T(1), n, Xs, ldn, st);   // [Ws ws] of step k + 1
+    double* u1 = c->small;
+    double* u2 = u1 + (size_t)std::max(rp, 1) * (cw + 1);
+    for (int q : ids) {
+      const double tau = qs->tq[q] - k * dt;
+      const double at = std::exp(-tau / lt);
+      double* fm = qs->fm + (size_t)q * n;
+      double* fv = qs->fv + (size_t)q * n;
+      interp_filter(c->mf + (size_t)k * n, c->vf + (size_t)k * n, qs->mu_q ? qs->mu_q + (size_t)q * n : nullptr,
+                    c->has_mu ? c->mu + (size_t)k * n : nullptr, at, c->sf2, n, fm, fv, st);
+      double* sm = qs->sm + (size_t)q * n;
+      double* sv = qs->sv + (size_t)q * n;
+      if (k == c->T) {
+        cudaMemcpyAsync(sm, fm, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(sv, fv, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+        continue;
+      }
+      const double ar = std::exp(-(dt - tau) / lt);     // A(t_{k+1}, t)
+      scale_copy<T>(KW, ldn, n, cw + 1, T(ar), Y, ldn, st);
+      if (rp > 0) {
+        gemm_tn<T>(Mk(k - 1), ldn, rp, Xs, ldn, cw + 1, n, 1.0, 0.0, u1, rp, c->part64, c->part64_elems, st);
+        gemm_nn<T, double>(n, cw + 1, rp, T(-ar * at * at * c->a * c->a), Mk(k - 1), ldn, u1, rp, T(1), Y, ldn, st);
+      }
+      if (ic > 0) {
+        gemm_tn<T>(PV(k), ldn, ic, Xs, ldn, cw + 1, n, 1.0, 0.0, u2, ic, c->part64, c->part64_elems, st);
+        gemm_nn<T, double>(n, cw + 1, ic, T(-ar * at * at), PV(k), ldn, u2, ic, T(1), Y, ldn, st);
+      }
+      smooth_out<T>(fm, fv, Y, ldn, cw, n, sm, sv, st);
+    }
   }
 
   // ---------------------------------------------------------------- posterior sampler
@@ -1643,6 +1702,75 @@ int cakf_get_actions(cakf_ctx* c, double* actions_out, int32_t* counts_out) {
     off += cnt_el;
   }
   return CAKF_OK;
+}
+
+int cakf_interpolate(cakf_ctx* c, int32_t nq, const double* tq, const double* mu_q, double* fmean, double* fvar,
+                     double* smean, double* svar, void* cuda_stream) {
+  if (!c) return fail(CAKF_ERR_STATE, "cakf_interpolate: no context (cakf_filter creates it)");
+  if (!c->filtered) return fail(CAKF_ERR_STATE, "cakf_interpolate needs a successful cakf_filter on this context");
+  if (nq < 1 || !tq) return fail(CAKF_ERR_ARG, "cakf_interpolate: nq >= 1 query times are needed");
+  if (ptr_kind(tq) != kHost) return fail(CAKF_ERR_ARG, "cakf_interpolate: tq must be a host array");
+  if (c->has_mu && !mu_q) return fail(CAKF_ERR_ARG, "cakf_interpolate: the problem has a prior mean, so mu_q is needed");
+  const int n = c->n, T = c->T;
+  const size_t tot = (size_t)nq * n;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  double* buf = nullptr;
+  double* mq = nullptr;
+  if (cudaMalloc(&buf, 4 * tot * sizeof(double)) != cudaSuccess ||
+      (mu_q && cudaMalloc(&mq, tot * sizeof(double)) != cudaSuccess)) {
+    cudaGetLastError();
+    if (buf) cudaFree(buf);
+    return fail(CAKF_ERR_OOM, "cakf_interpolate: workspace allocation failed");
+  }
+  int rc = mu_q ? copy_in(mq, mu_q, tot * sizeof(double), st) : CAKF_OK;
+  double* ms = nullptr;
+  double* vs = nullptr;
+  if (!rc && !c->ms_dev) {
+    if ((rc = c->alloc(c->ms_dev, (size_t)(T + 1) * n * sizeof(double))) == CAKF_OK)
+      rc = c->alloc(c->vs_dev, (size_t)(T + 1) * n * sizeof(double));
+  }
+  if (!rc) {
+    ms = c->ms_dev;
+    vs = c->vs_dev;
+    cudaMemsetAsync(c->err, 0, sizeof(int), st);
+    auto run = [&](auto* runner) {
+      using R = std::remove_pointer_t<decltype(runner)>;
+      typename R::Queries Q;
+      Q.at_k.assign(T + 1, {});
+      Q.tq.assign(tq, tq + nq);
+      for (int q = 0; q < nq; ++q) {
+        const double t = tq[q];
+        int k = (int)std::floor(t / c->dt + 1e-12);
+        k = std::max(0, std::min(k, T));
+        Q.at_k[k].push_back(q);
+      }
+      Q.mu_q = mq;
+      Q.fm = buf; Q.fv = buf + tot; Q.sm = buf + 2 * tot; Q.sv = buf + 3 * tot;
+      runner->qs = &Q;
+      return runner->smooth(ms, vs);
+    };
+    for (int q = 0; q < nq && !rc; ++q)
+      if (!(tq[q] >= 0.0) || !std::isfinite(tq[q])) rc = fail(CAKF_ERR_ARG, "cakf_interpolate: query times must be >= 0");
+    if (!rc) {
+      if (c->precision == CAKF_FP64) {
+        Runner<double> r = make_runner<double>(c, st);
+        rc = run(&r);
+      } else {
+        Runner<float> r = make_runner<float>(c, st);
+        rc = run(&r);
+      }
+    }
+  }
+  if (!rc) rc = sync_and_check(c, st, "cakf_interpolate");
+  double* outs[4] = {fmean, fvar, smean, svar};
+  for (int j = 0; j < 4 && !rc; ++j) rc = copy_out(outs[j], buf + j * tot, tot, st);
+  if (!rc) {
+    cudaError_t ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) rc = fail(CAKF_ERR_CUDA, cudaGetErrorString(ce));
+  }
+  cudaFree(buf);
+  if (mq) cudaFree(mq);
+  return rc;
 }
 
 int cakf_sample(cakf_ctx* c, int32_t n_samples, const double* x0, const double* q, const double* eps,

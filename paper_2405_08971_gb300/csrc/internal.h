@@ -125,6 +125,10 @@ void samp_resid(const double* y, const double* xp, const int* obs, const double*
 template <class T>
 void samp_add(const double* xa, const T* t, int ldt, double alpha, int n, int S, double* x, cudaStream_t st);
 
+// Temporal interpolation: filter mean and variance at t_k + tau from step k's (at = A(t, t_k)).
+void interp_filter(const double* mk, const double* vk, const double* mu_t, const double* mu_k, double at, double sf2,
+                   int n, double* m, double* v, cudaStream_t st);
+
 // Record msg as the calling thread's cakf_last_error message; returns code.
 int set_last_error(int code, const char* msg);
 

@@ -1816,6 +1816,22 @@ template void samp_resid<double>(const double*, const double*, const int*, const
 template void samp_add<float>(const double*, const float*, int, double, int, int, double*, cudaStream_t);
 template void samp_add<double>(const double*, const double*, int, double, int, int, double*, cudaStream_t);
 
+// Filter marginal at a query time t_k + tau (the interpolation corollary, OU prior): m(t) = at m_k +
+// mu(t) - at mu_k, var(t) = sf2 - at^2 (sf2 - var_k).
+__global__ void k_interp_filter(const double* __restrict__ mk, const double* __restrict__ vk,
+                                const double* __restrict__ mu_t, const double* __restrict__ mu_k, double at,
+                                double sf2, int n, double* __restrict__ m, double* __restrict__ v) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const double b = mu_t ? mu_t[j] - (mu_k ? at * mu_k[j] : 0.0) : 0.0;
+  m[j] = fma(at, mk[j], b);
+  v[j] = sf2 - at * at * (sf2 - vk[j]);
+}
+void interp_filter(const double* mk, const double* vk, const double* mu_t, const double* mu_k, double at, double sf2,
+                   int n, double* m, double* v, cudaStream_t st) {
+  k_interp_filter<<<cdiv(n, 256), 256, 0, st>>>(mk, vk, mu_t, mu_k, at, sf2, n, m, v); note_launch();
+}
+
 void set_diag(double* G, int ld, const double* lam, double scale, int r, cudaStream_t st) {
   if (r <= 0) return;
   k_set_diag<<<cdiv(r, 256), 256, 0, st>>>(G, ld, lam, scale, r); note_launch();
