@@ -545,7 +545,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmapB, const TcParams P) {
 // tensor cores with split TF32 operands (MD_TF32X3: hi = tf32(x), lo = tf32(x - hi), three MMAs,
 // about 22 significant bits per product, FP32 accumulation in TMEM).  op(A) = A (NN: A is M x K,
 // column-major, M the long dimension) or A^T (TN: A is K x M, column-major, K the long dimension).
-// B is K x N column-major.  The work is a list of units (128-row tile, N chunk <= 512 columns,
+// B is K x N column-major.  The work is a list of units (128-row tile, N chunk <= 256 columns,
 // K chunk); a persistent grid takes them round-robin.  Per K slice (16 values of K) the 16
 // producer warps load the A and B tiles from global memory (coalesced), split them into hi / lo
 // TF32 parts and write the swizzled K-major operand layout; one thread issues the MMAs; the
@@ -571,6 +571,51 @@ struct GemmParams {
   uint32_t b_stage_bytes;
   long long wait_limit;
 };
+
+// Operand rows of B per producer thread and slice: a chunk has at most 256 columns (npad <= 256),
+// 128 rows per pass of the 512 producer threads.
+constexpr int GEMM_BROWS = 2;
+constexpr int GEMM_MAX_CHUNK = 128 * GEMM_BROWS;
+
+// Global loads of one 16-wide K slice: A (128 rows) and B (npad operand rows) for this thread,
+// zero outside the matrices.  Thread mapping: A of a TN product and B as (row tid / 4, quad tid % 4
+// of 4 consecutive K values, one 16-byte load when aligned); A of an NN product as (row tid % 128,
+// quad tid / 128), the lanes of a warp on consecutive rows.
+__device__ __forceinline__ void load_slice(const GemmParams& P, int ks, int row0, int col0, int tid, float av[4],
+                                           float bv[GEMM_BROWS][4]) {
+  const int k0 = ks * 16;
+  if (P.transA) {
+    const int r = tid >> 2, kq = tid & 3;
+    const int row = row0 + r, k = k0 + kq * 4;
+    const float* src = P.A + (size_t)row * P.lda + k;
+    if (row < P.M && P.vecA && k + 3 < P.K) {
+      const float4 q = *reinterpret_cast<const float4*>(src);
+      av[0] = q.x; av[1] = q.y; av[2] = q.z; av[3] = q.w;
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) av[e] = (row < P.M && k + e < P.K) ? src[e] : 0.f;
+    }
+  } else {
+    const int r = tid & 127, kq = tid >> 7;
+    const int row = row0 + r, k = k0 + kq * 4;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) av[e] = (row < P.M && k + e < P.K) ? P.A[(size_t)(k + e) * P.lda + row] : 0.f;
+  }
+#pragma unroll
+  for (int b = 0; b < GEMM_BROWS; ++b) {
+    const int jr = (tid >> 2) + 128 * b, kq = tid & 3, k = k0 + kq * 4;
+    const int col = col0 + jr;
+    const bool valid = jr < P.cw && col < P.N;
+    const float* src = P.B + (size_t)col * P.ldb + k;
+    if (valid && P.vecB && k + 3 < P.K) {
+      const float4 q = *reinterpret_cast<const float4*>(src);
+      bv[b][0] = q.x; bv[b][1] = q.y; bv[b][2] = q.z; bv[b][3] = q.w;
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) bv[b][e] = (valid && k + e < P.K) ? src[e] : 0.f;
+    }
+  }
+}
 
 template <int MD>
 __global__ void __launch_bounds__(NTHREADS, 1) k_gemm_tc(const GemmParams P) {
@@ -626,65 +671,48 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gemm_tc(const GemmParams P) {
       const int kc = u / (P.ntiles * P.nchunks);
       const int row0 = t * BM, col0 = nc * P.cw;
       const int ks0 = kc * P.kslices, ks1 = min(P.nk, ks0 + P.kslices);
+      // the global loads of slice ks + 1 are issued before slice ks is converted and stored, so
+      // their latency overlaps the conversion, the stores and the wait for the next free stage
+      float av[4], bv[GEMM_BROWS][4];
+      load_slice(P, ks0, row0, col0, tid, av, bv);
       for (int ks = ks0; ks < ks1; ++ks, ++it) {
         const int s = (int)(it % S);
         const uint32_t n = (uint32_t)(it / S);
+        float an[4], bn[GEMM_BROWS][4];
+        if (ks + 1 < ks1) load_slice(P, ks + 1, row0, col0, tid, an, bn);
         ok = mbar_wait(smem_u32(&empty[s]), (n & 1) ^ 1, abort_flag, P.wait_limit);
         ok = __all_sync(0xffffffffu, ok);
         if (!ok) break;
-        const int k0 = ks * M::BK;
         uint8_t* ast = A_base + (size_t)s * M::NPART * M::A_TILE;
         uint8_t* bst = B_base + (size_t)s * P.b_stage_bytes;
-        // A tile: 128 rows x 16 K values; thread -> (row r, quad kq of 4 consecutive K values)
         {
-          float v[4];
-          int r, kq;
-          if (P.transA) {
-            r = tid >> 2; kq = tid & 3;
-            const int row = row0 + r, k = k0 + kq * 4;
-            const float* src = P.A + (size_t)row * P.lda + k;
-            if (row < P.M && P.vecA && k + 3 < P.K) {
-              const float4 q = *reinterpret_cast<const float4*>(src);
-              v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
-            } else {
-#pragma unroll
-              for (int e = 0; e < 4; ++e) v[e] = (row < P.M && k + e < P.K) ? src[e] : 0.f;
-            }
-          } else {
-            r = tid & 127; kq = tid >> 7;
-            const int row = row0 + r, k = k0 + kq * 4;
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-              v[e] = (row < P.M && k + e < P.K) ? P.A[(size_t)(k + e) * P.lda + row] : 0.f;
-          }
+          const int r = P.transA ? (tid >> 2) : (tid & 127);
+          const int kq = P.transA ? (tid & 3) : (tid >> 7);
           uint32_t h[4], l[4];
 #pragma unroll
-          for (int e = 0; e < 4; ++e) { h[e] = tf32_rna(v[e]); l[e] = tf32_rna(v[e] - __uint_as_float(h[e])); }
+          for (int e = 0; e < 4; ++e) { h[e] = tf32_rna(av[e]); l[e] = tf32_rna(av[e] - __uint_as_float(h[e])); }
           const uint32_t o = sw_off<MD>(r, kq * 16);
           *reinterpret_cast<uint4*>(ast + o) = make_uint4(h[0], h[1], h[2], h[3]);
           *reinterpret_cast<uint4*>(ast + M::A_TILE + o) = make_uint4(l[0], l[1], l[2], l[3]);
         }
-        // B tile: npad operand rows (columns of B) x 16 K values, same thread mapping as TN A
-        for (int jr = tid >> 2; jr < P.npad; jr += 128) {
-          const int kq = tid & 3, k = k0 + kq * 4;
-          const int col = col0 + jr;
-          const bool valid = jr < P.cw && col < P.N;
-          const float* src = P.B + (size_t)col * P.ldb + k;
-          float v[4];
-          if (valid && P.vecB && k + 3 < P.K) {
-            const float4 q = *reinterpret_cast<const float4*>(src);
-            v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
-          } else {
 #pragma unroll
-            for (int e = 0; e < 4; ++e) v[e] = (valid && k + e < P.K) ? src[e] : 0.f;
-          }
+        for (int b = 0; b < GEMM_BROWS; ++b) {
+          const int jr = (tid >> 2) + 128 * b;
+          if (jr >= P.npad) break;
+          const int kq = tid & 3;
           uint32_t h[4], l[4];
 #pragma unroll
-          for (int e = 0; e < 4; ++e) { h[e] = tf32_rna(v[e]); l[e] = tf32_rna(v[e] - __uint_as_float(h[e])); }
+          for (int e = 0; e < 4; ++e) { h[e] = tf32_rna(bv[b][e]); l[e] = tf32_rna(bv[b][e] - __uint_as_float(h[e])); }
           const uint32_t o = sw_off<MD>(jr, kq * 16);
           *reinterpret_cast<uint4*>(bst + o) = make_uint4(h[0], h[1], h[2], h[3]);
           *reinterpret_cast<uint4*>(bst + (size_t)P.npad * M::ROWB + o) = make_uint4(l[0], l[1], l[2], l[3]);
         }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) av[e] = an[e];
+#pragma unroll
+        for (int b = 0; b < GEMM_BROWS; ++b)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) bv[b][e] = bn[b][e];
         fence_proxy_async();
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&fullA[s]));
@@ -1048,7 +1076,7 @@ int gemm_tc_launch(int transA, int Mr, int N, int K, float alpha, const float* A
   GemmParams P{};
   P.A = A; P.lda = lda; P.transA = transA; P.B = B; P.ldb = ldb; P.M = Mr; P.N = N; P.K = K;
   P.ntiles = (Mr + BM - 1) / BM;
-  P.nchunks = (N + 511) / 512;
+  P.nchunks = (N + GEMM_MAX_CHUNK - 1) / GEMM_MAX_CHUNK;
   P.cw = (N + P.nchunks - 1) / P.nchunks;
   P.npad = round_up(P.cw, 16);
   P.nk = (K + M::BK - 1) / M::BK;

@@ -633,48 +633,56 @@ k_gram_block_simt(const C4<T>* __restrict__ Xr, int nr, const C4<T>* __restrict_
 }
 
 // ------------------------------------------------------------------------------------------
-// Split-K transposed product: part[z][a + b*lda_out] = sum_{t in chunk z} A[t, a] B[t, b]
-// (A: K x na, B: K x nb column-major).  Partials in double; k_reduce_splits sums them.
-constexpr int TN_T = 32;
+// Split-K transposed product: part[z][a + b*na] = sum_{t in chunk z} A[t, a] B[t, b]
+// (A: K x na, B: K x nb column-major), 64 x 64 output tiles, 4 x 4 per thread, K staged 32 at a time
+// (rows of A and B are contiguous along K: each warp reads 32 consecutive K values of 8 columns).
+// Accumulation in the working precision, partials in double; k_reduce_splits sums them.
+constexpr int TN_T = 64, TN_K = 32;
 template <class T>
 __global__ void __launch_bounds__(256)
 k_gemm_tn_part(const T* __restrict__ A, int lda, int na, const T* __restrict__ B, int ldb, int nb,
                int K, int chunk, double* __restrict__ part) {
-  __shared__ T As[TN_T][TN_T + 1];
-  __shared__ T Bs[TN_T][TN_T + 1];
+  __shared__ T As[TN_K][TN_T + 1];
+  __shared__ T Bs[TN_K][TN_T + 1];
   const int a0 = blockIdx.x * TN_T, b0 = blockIdx.y * TN_T;
   const int k_begin = blockIdx.z * chunk, k_end = min(K, k_begin + chunk);
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  float accf[2][2] = {{0, 0}, {0, 0}};
-  double accd[2][2] = {{0, 0}, {0, 0}};
-  for (int k0 = k_begin; k0 < k_end; k0 += TN_T) {
-    for (int e = threadIdx.x; e < TN_T * TN_T; e += 256) {
-      int kk = e % TN_T, cc = e / TN_T;
-      int t = k0 + kk;
-      As[kk][cc] = (t < k_end && a0 + cc < na) ? A[(size_t)(a0 + cc) * lda + t] : T(0);
-      Bs[kk][cc] = (t < k_end && b0 + cc < nb) ? B[(size_t)(b0 + cc) * ldb + t] : T(0);
+  T acc[4][4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[p][q] = T(0);
+  const int kk_ld = threadIdx.x & 31, cc_ld = threadIdx.x >> 5;   // 32 K values x 8 columns per pass
+  for (int k0 = k_begin; k0 < k_end; k0 += TN_K) {
+    const int t = k0 + kk_ld;
+#pragma unroll
+    for (int pass = 0; pass < TN_T / 8; ++pass) {
+      const int cc = cc_ld + 8 * pass;
+      As[kk_ld][cc] = (t < k_end && a0 + cc < na) ? A[(size_t)(a0 + cc) * lda + t] : T(0);
+      Bs[kk_ld][cc] = (t < k_end && b0 + cc < nb) ? B[(size_t)(b0 + cc) * ldb + t] : T(0);
     }
     __syncthreads();
 #pragma unroll 8
-    for (int kk = 0; kk < TN_T; ++kk) {
+    for (int kk = 0; kk < TN_K; ++kk) {
+      T aa[4], bb[4];
 #pragma unroll
-      for (int p = 0; p < 2; ++p)
+      for (int p = 0; p < 4; ++p) aa[p] = As[kk][ty + 16 * p];
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          if (sizeof(T) == 4) accf[p][q] = fmaf(float(As[kk][ty + 16 * p]), float(Bs[kk][tx + 16 * q]), accf[p][q]);
-          else accd[p][q] = fma(double(As[kk][ty + 16 * p]), double(Bs[kk][tx + 16 * q]), accd[p][q]);
-        }
+      for (int q = 0; q < 4; ++q) bb[q] = Bs[kk][tx + 16 * q];
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = fma(aa[p], bb[q], acc[p][q]);
     }
     __syncthreads();
   }
   const size_t stride = (size_t)na * nb;
 #pragma unroll
-  for (int p = 0; p < 2; ++p)
+  for (int p = 0; p < 4; ++p)
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      int a = a0 + ty + 16 * p, b = b0 + tx + 16 * q;
-      if (a < na && b < nb)
-        part[blockIdx.z * stride + (size_t)b * na + a] = (sizeof(T) == 4) ? double(accf[p][q]) : accd[p][q];
+    for (int q = 0; q < 4; ++q) {
+      const int a = a0 + ty + 16 * p, b = b0 + tx + 16 * q;
+      if (a < na && b < nb) part[blockIdx.z * stride + (size_t)b * na + a] = double(acc[p][q]);
     }
 }
 
@@ -1436,14 +1444,14 @@ void gemm_tn(const T* A, int lda, int na, const T* B, int ldb, int nb, int K, do
   }
   const size_t tile_elems = (size_t)na * nb;
   int gx = cdiv(na, TN_T), gy = cdiv(nb, TN_T);
-  int want = std::max(1, (int)(2 * 152 / std::max(1, gx * gy)));
+  int want = std::max(1, (int)(4 * 152 / std::max(1, gx * gy)));
   int chunk_min = 256;
   int nsplit = std::max(1, std::min(want, (K + chunk_min - 1) / chunk_min));
   nsplit = std::max(1, std::min<int>(nsplit, (int)(part_elems / tile_elems)));
   int chunk = (K + nsplit - 1) / nsplit;
-  chunk = ((chunk + TN_T - 1) / TN_T) * TN_T;
+  chunk = ((chunk + TN_K - 1) / TN_K) * TN_K;
   nsplit = std::max(1, (K + chunk - 1) / chunk);
-  if (K <= 0) { nsplit = 1; chunk = TN_T; }
+  if (K <= 0) { nsplit = 1; chunk = TN_K; }
   k_gemm_tn_part<T><<<dim3(gx, gy, nsplit), 256, 0, st>>>(A, lda, na, B, ldb, nb, std::max(K, 0), chunk, part); note_launch();
   k_reduce_splits<double><<<cdiv(tile_elems, 256), 256, 0, st>>>(part, nsplit, na, nb, alpha, beta, C, ldc); note_launch();
 }

@@ -34,7 +34,7 @@ def fit_adam(data: dict, theta0, steps: int = 50, lr: float = 0.05, precision: s
         nll = cakf_neg_log_likelihood(theta, data, precision=precision)
         nll.backward()
         opt.step()
-        rec = (it, float(nll), [float(v) for v in theta.detach()], time.perf_counter() - t0)
+        rec = (it, float(nll.detach()), [float(v) for v in theta.detach()], time.perf_counter() - t0)
         trace.append(rec)
         if log:
             log(rec)

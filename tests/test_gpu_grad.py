@@ -103,11 +103,13 @@ def test_gradient_c4_configuration_against_frozen_fd():
     its truncation rotations reused through freeze_truncation), within 1e-5 relative; and the FP32
     gradient of the same frozen actions against the FP64 one (reported, 1e-3)."""
     w = synth.grid2d_16k(T=200)
-    prob = ck.problem_from_workload(w, precision="fp64")
-    ctx, _, _ = ck.cakf_filter(prob, want_outputs=False)
-    g64 = ck.cakf_nll_backward(ctx)
+    ctx, _, _ = ck.cakf_filter(ck.problem_from_workload(w, precision="fp64"), want_outputs=False)
     S, _ = ck.cakf_get_actions(ctx, w.obs_ptr)
     rep = ck.pack_actions(S, w.T)
+    ctx.close()
+    # the base of the frozen model: the same actions replayed (its rotations are then reused)
+    ctx, _, _ = ck.cakf_filter(ck.problem_from_workload(w, precision="fp64", replay=rep), want_outputs=False)
+    g64 = ck.cakf_nll_backward(ctx)
     theta0 = np.array([w.log_lx, w.log_lt, w.log_sf2, w.log_sn2])
     names = ["log_lx", "log_lt", "log_sf2", "log_sn2"]
     h, g_fd = 1e-4, np.zeros(4)
