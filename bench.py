@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-DTYPE_NAME = {"fp16x3": "fp16x3", "bf16": "bf16", "fp32": "f32", "fp64": "f64"}
+DTYPE_NAME = {"fp16x3": "fp16x3", "tf32x3": "tf32x3", "tf32": "tf32", "bf16": "bf16", "fp32": "f32", "fp64": "f64"}
 
 
 def parse():
@@ -384,7 +384,7 @@ def main():
                                 "peak_source": peak_note.format("FP64 FMA chains, 2 flops each"),
                                 "launches": prof["eig_calls"], "avg_ms": tri_ms / prof["eig_calls"],
                                 "ms_total": tri_ms,
-                                "note": "one cross-block exchange per Householder column (epoch-tagged words, no grid barrier): bound by its latency chain, not by FP64 throughput"}
+                                "note": "one cross-block exchange per Householder column (epoch-tagged word pairs, no grid barrier): bound by its latency chain, not by FP64 throughput"}
     # tensor-core / SIMT Gram x block (filter finalize): kernel entries on MUFU (sqrt + exp2 each)
     if prof["gram_block_launches"]:
         gb_ms = prof["gram_block_ms"]
@@ -395,12 +395,18 @@ def main():
                "peak_source": peak_note.format("sqrt.approx + ex2.approx chains"),
                "launches": prof["gram_block_launches"], "avg_ms": gb_ms / prof["gram_block_launches"],
                "ms_total": gb_ms, "tensor_tflops": tfl}
-        if args.precision in ("bf16", "fp16x3"):
+        tc_modes = ("bf16", "fp16x3", "tf32", "tf32x3")
+        if args.precision in tc_modes:
             tpk = float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops")))
-            mmas = 3 if args.precision == "fp16x3" else 1
+            # TF32 MMAs: the measured BF16 rate times the nominal TF32 / BF16 dense ratio (1.1 / 2.25)
+            tf32 = args.precision in ("tf32", "tf32x3")
+            if tf32:
+                tpk *= 1.1 / 2.25
+            mmas = 3 if args.precision in ("fp16x3", "tf32x3") else 1
             ent["tensor_frac"] = mmas * tfl / tpk
-            ent["tensor_peak_source"] = f"{pk_src} bf16_tflops_sustained; {mmas} MMA(s) per algorithmic flop"
-        kernels["k_gram_tc" if args.precision in ("bf16", "fp16x3") else "k_gram_block_simt"] = ent
+            ent["tensor_peak_source"] = (f"{pk_src} bf16_tflops_sustained" + (" x 1.1/2.25 (nominal TF32/BF16)" if tf32 else "")
+                                         + f"; {mmas} MMA(s) per algorithmic flop")
+        kernels["k_gram_tc" if args.precision in tc_modes else "k_gram_block_simt"] = ent
     # CG Gram matvec (sampled every 8th iteration): m (m + 1) / 2 unique kernel entries per launch
     # (the symmetric Gram is evaluated once per entry pair), 2 MUFU operations each
     if prof["cg_matvec_launches"]:

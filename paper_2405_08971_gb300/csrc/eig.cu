@@ -36,23 +36,27 @@ __device__ __forceinline__ double nr_rcp(double x) {
   return r;
 }
 
-// Per-step exchange without a grid barrier: every FP64 word a block publishes for step k carries the
-// step's epoch (k mod 4) in its two lowest mantissa bits (a relative change below 7e-16), and the
-// consumers poll the words themselves until all carry the epoch they wait for.  Each 8-byte word
-// is written and read as one access, so a reader sees either the old or the new word; the data
-// dependence of the recursion (no block can publish step k + 2 before every block has published
-// step k + 1, which needs step k consumed) makes two buffers enough.
+// Per-step exchange without a grid barrier: every word a block publishes for step k carries the
+// step's epoch (k mod 4) in its two lowest mantissa bits, and the consumers poll the words themselves
+// until all carry the epoch they wait for.  A value x travels as the pair (hi, lo): hi is x with its
+// two lowest mantissa bits replaced by the epoch, lo is the exact remainder x - hi (same binade,
+// at most 3 ulp) tagged the same way.  Re-tagging lo moves it by at most 3 ulp(lo) <= 9 * 2^-52 ulp(x),
+// so hi + lo rounds back to x exactly: the exchange is lossless (subnormal x, far below any Gram
+// entry here, could lose its last 2 bits).  Each 8-byte word is written and read as one access, so a
+// reader sees either the old or the new word; the data dependence of the recursion (no block can
+// publish step k + 2 before every block has published step k + 1, which needs step k consumed) makes
+// two buffers enough.
 __device__ __forceinline__ double with_epoch(double x, int ep) {
   return __longlong_as_double((__double_as_longlong(x) & ~3LL) | (long long)ep);
 }
 __device__ __forceinline__ int epoch_of(double x) { return (int)(__double_as_longlong(x) & 3LL); }
-__device__ __forceinline__ double ld_relaxed(const double* p) {
-  double v;
-  asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
-  return v;
+__device__ __forceinline__ void publish_pair(double* p, double x, int ep) {
+  const double hi = with_epoch(x, ep);
+  const double lo = with_epoch(x - hi, ep);
+  asm volatile("st.relaxed.gpu.global.v2.f64 [%0], {%1, %2};" ::"l"(p), "d"(hi), "d"(lo) : "memory");
 }
-__device__ __forceinline__ void st_relaxed(double* p, double v) {
-  asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+__device__ __forceinline__ void ld_pair(const double* p, double& hi, double& lo) {
+  asm volatile("ld.relaxed.gpu.global.v2.f64 {%0, %1}, [%2];" : "=d"(hi), "=d"(lo) : "l"(p) : "memory");
 }
 __device__ __forceinline__ int ld_relaxed_int(const int* p) {
   int v;
@@ -73,14 +77,15 @@ constexpr long long kPollLimit = 4000000LL;
 // subdiagonal (v_k[0] = 1).  Block reductions go through shared memory and one warp (the FP64 pipe
 // is narrow on this GPU, so a shuffle tree in every warp would cost more than the data it sums).
 constexpr int TD_THREADS = 128;
+constexpr int TD_BATCH = 8;     // exchange entries a thread polls with their loads in flight together
 
 // Householder scalars for x (x[0] = alpha, sum of the squares of x[1..] = sigma): H x = beta e_1,
 // H = I - tau v v^T with v[0] = 1 and v[t] = x[t] * scal.
 __device__ __forceinline__ void house_scalars(double alpha, double sigma, double& tau, double& beta, double& scal) {
   if (sigma == 0.0) { tau = 0.0; beta = alpha; scal = 0.0; return; }
   beta = -copysign(sqrt(alpha * alpha + sigma), alpha);
-  tau = (beta - alpha) / beta;
-  scal = 1.0 / (alpha - beta);
+  tau = (beta - alpha) * nr_rcp(beta);
+  scal = nr_rcp(alpha - beta);
 }
 
 // Sum of red[0 .. blockDim.x) by warp 0 (called by warp 0 only); the result is in every lane.
@@ -157,8 +162,8 @@ k_tridiag(double* __restrict__ A, int lda, int N, double* __restrict__ d, double
       double acc = 0.0;
       for (int t = lane; t < L; t += 32) acc = fma(col[t], v[t], acc);
       acc = warp_sum(acc);
-      if (lane == 0) st_relaxed(Pbuf + j - 1, with_epoch(tk * acc, 0));
-      if (j == 1) for (int t = lane; t < L; t += 32) st_relaxed(Cbuf + t, with_epoch(col[t], 0));
+      if (lane == 0) publish_pair(Pbuf + 2 * (j - 1), tk * acc, 0);
+      if (j == 1) for (int t = lane; t < L; t += 32) publish_pair(Cbuf + 2 * t, col[t], 0);
     }
     if (blockIdx.x == ob && tid == 0) d[0] = A[0];
     __syncthreads();
@@ -166,32 +171,54 @@ k_tridiag(double* __restrict__ A, int lda, int N, double* __restrict__ d, double
   for (int k = 0; k + 2 < N; ++k) {
     if ((int)blockIdx.x != ob && maxcol < k + 2) return;
     const int L = N - k - 1;
-    const double* Pk = Pbuf + (size_t)(k & 1) * N;
-    double* Pn = Pbuf + (size_t)((k + 1) & 1) * N;
-    const double* Ck = Cbuf + (size_t)(k & 1) * N;
-    double* Cn = Cbuf + (size_t)((k + 1) & 1) * N;
+    const double* Pk = Pbuf + (size_t)(k & 1) * 2 * N;
+    double* Pn = Pbuf + (size_t)((k + 1) & 1) * 2 * N;
+    const double* Ck = Cbuf + (size_t)(k & 1) * 2 * N;
+    double* Cn = Cbuf + (size_t)((k + 1) & 1) * 2 * N;
     const double* v = sm + (size_t)(k & 1) * N;
     double* v2 = sm + (size_t)((k + 1) & 1) * N;
     const bool next = (k + 3 < N);      // a reflector for column k+1 exists
     // (1) p_k . v_k; the pivot column C_k is fetched in the same pass (into c).  Each thread polls
-    // its entries of P_k and C_k until they carry epoch k mod 4 (bounded; a timeout or another
-    // block's error ends the kernel).
+    // its entries of P_k and C_k, up to TD_BATCH of them with their loads in flight together, until
+    // all carry epoch k mod 4 (bounded; a timeout or another block's error ends the kernel).
     const int ek = k & 3;
     double part = 0.0;
     bool ok = true;
-    for (int t = tid; t < L && ok; t += TB) {
-      double pt, ct;
+    for (int t0 = tid; t0 < L && ok; t0 += TB * TD_BATCH) {
+      double ph[TD_BATCH], pl[TD_BATCH], ch[TD_BATCH], cl[TD_BATCH];
+      unsigned pend = 0;
+#pragma unroll
+      for (int u = 0; u < TD_BATCH; ++u)
+        if (t0 + u * TB < L) pend |= 1u << u;
       long long spins = 0;
-      while (true) {
-        pt = ld_relaxed(Pk + t);
-        ct = ld_relaxed(Ck + t);
-        if (epoch_of(pt) == ek && epoch_of(ct) == ek) break;
+      while (pend) {
+#pragma unroll
+        for (int u = 0; u < TD_BATCH; ++u)
+          if ((pend >> u) & 1u) {
+            const int t = t0 + u * TB;
+            ld_pair(Pk + 2 * t, ph[u], pl[u]);
+            ld_pair(Ck + 2 * t, ch[u], cl[u]);
+          }
+#pragma unroll
+        for (int u = 0; u < TD_BATCH; ++u)
+          if (((pend >> u) & 1u) && epoch_of(ph[u]) == ek && epoch_of(pl[u]) == ek && epoch_of(ch[u]) == ek &&
+              epoch_of(cl[u]) == ek)
+            pend &= ~(1u << u);
+        if (!pend) break;
         if (++spins > poll_limit) { atomicExch(err, kErrTimeout); ok = false; break; }
         if ((spins & 255) == 0 && ld_relaxed_int(err)) { ok = false; break; }
       }
-      c[t] = ct;
-      w[t] = pt;
-      part = fma(pt, v[t], part);
+      if (!ok) break;
+#pragma unroll
+      for (int u = 0; u < TD_BATCH; ++u) {
+        const int t = t0 + u * TB;
+        if (t < L) {
+          const double pt = ph[u] + pl[u], ct = ch[u] + cl[u];
+          c[t] = ct;
+          w[t] = pt;
+          part = fma(pt, v[t], part);
+        }
+      }
     }
     red[tid] = part;
     if (!__syncthreads_and(ok)) return;
@@ -249,11 +276,11 @@ k_tridiag(double* __restrict__ A, int lda, int N, double* __restrict__ d, double
         const double nv = fma(-v[t], wj, fma(-w[t], vj, col[t]));
         col[t] = nv;
         if (next && t >= 1) acc = fma(nv, v2[t - 1], acc);
-        if (publish && t >= 1) st_relaxed(Cn + t - 1, with_epoch(nv, (k + 1) & 3));
+        if (publish && t >= 1) publish_pair(Cn + 2 * (t - 1), nv, (k + 1) & 3);
       }
       if (next && tj >= 1) {
         acc = warp_sum(acc);
-        if (lane == 0) st_relaxed(Pn + tj - 1, with_epoch(tn * acc, (k + 1) & 3));
+        if (lane == 0) publish_pair(Pn + 2 * (tj - 1), tn * acc, (k + 1) & 3);
       }
       if (k + 3 == N && j == N - 1) {                  // last diagonal entry (written by lane L-1)
         __syncwarp();
@@ -1038,7 +1065,7 @@ size_t eig_workspace_bytes(int nmax) {
   size_t N = std::max(nmax, 1);
   size_t b = 0;
   b += align_up(3 * N * sizeof(double));          // d, e, tau
-  b += 2 * align_up(2 * N * sizeof(double));      // P, C (double buffered)
+  b += 2 * align_up(4 * N * sizeof(double));      // P, C (double buffered (hi, lo) pairs)
   b += 3 * align_up(N * N * sizeof(double));      // Q, Qtmp, Delta
   b += 10 * align_up(N * sizeof(double));         // lam, lamk, lamtmp, Dw, Zw, Dk, Zk, Dd, rho, spare
   b += align_up(4 * N * sizeof(double));          // rot
@@ -1061,8 +1088,8 @@ int eig_sym_topk(double* A, int lda, int N, int nkeep, double* w, T* U, int ldu,
   double* d = (double*)take(3 * N * sizeof(double));
   double* e = d + N;
   double* tau = e + N;
-  double* P = (double*)take(2 * N * sizeof(double));
-  double* Cb = (double*)take(2 * N * sizeof(double));
+  double* P = (double*)take(4 * N * sizeof(double));
+  double* Cb = (double*)take(4 * N * sizeof(double));
   DcWork W;
   W.Q = (double*)take((size_t)N * N * sizeof(double));
   W.Qtmp = (double*)take((size_t)N * N * sizeof(double));
@@ -1090,8 +1117,8 @@ int eig_sym_topk(double* A, int lda, int N, int nkeep, double* w, T* U, int ldu,
 
   // exchange buffers of the tridiagonalisation: every byte 0x03, i.e. words with epoch 3, which
   // no consumer waits for before the buffer has been rewritten
-  cudaMemsetAsync(P, 0x03, 2 * N * sizeof(double), st);
-  cudaMemsetAsync(Cb, 0x03, 2 * N * sizeof(double), st);
+  cudaMemsetAsync(P, 0x03, 4 * N * sizeof(double), st);
+  cudaMemsetAsync(Cb, 0x03, 4 * N * sizeof(double), st);
   cudaMemsetAsync(W.Q, 0, (size_t)N * N * sizeof(double), st);
   cudaMemsetAsync(d, 0, 3 * N * sizeof(double), st);
 
