@@ -11,7 +11,10 @@ Smoothing"):
   separable Gauss-Markov processes"): A = A^t (x) I, Q = Q^t (x) K.  With an
   Ornstein-Uhlenbeck temporal factor (D'=1) this is A = a I, Q = (1-a^2) K,
   a = exp(-dt/l_t), and the stationary prior covariance Sigma_k = K for all k.
-  A known prior mean mu_k enters as b_{k-1} = mu_k - a mu_{k-1}.
+  A known prior mean mu_k enters as b_{k-1} = mu_k - a mu_{k-1}.  With a
+  Matern-3/2 temporal factor (D'=2; the remark after the lemma: Matern(p + 1/2)
+  kernels have a state-space form) the state is (f, df/dt) at every grid point,
+  A^t = expm(F dt), Sigma = P^t_inf (x) K and Q^t = P^t_inf - A^t P^t_inf A^t^T.
 * Filter: Alg. 1 (CAKF) with the iterative update step (appendix algorithm
   "CAKF Update Step (Iterative Version)"), CG policy = the current residual
   (Sec. 3.3).  Predict / update in downdate form (Prop. "Downdate-form Kalman
@@ -54,6 +57,10 @@ Readings taken where the paper is ambiguous, garbled or silent:
      P_k = K - M_k M_k^T) and the predicted P^-_k = K - a^2 M+_{k-1} M+_{k-1}^T.
   R7 smoother loop k = T-1 .. 0 with w_0 = 0, W_0 empty.
   R9 Matern kernels in the Rasmussen-Williams form, output scale = variance.
+  R20 Matern-3/2 temporal factor: the state stacks the positions above the velocities; the
+     temporal factor has unit variance (sigma_f^2 stays in K); a prior mean mu_k of the
+     positions enters as the state mean (mu_k, 0) -- the model is the zero-mean Matern process
+     of the deviation f - mu, so b_{k-1} = (mu_k, 0) - A (mu_{k-1}, 0); H observes positions.
   R18 coordinate policy: the space-filling subset is read as i observations evenly spaced through
      the step's observation list (sorted grid indices, i.e. raster order of the grid): positions
      floor((q + 1/2) m_k / i), q = 0..i-1; the left square root of Ghat^+ is L^-T with
@@ -94,18 +101,43 @@ def kernel_matrix(Xa: np.ndarray, Xb: np.ndarray, kernel: int, lx: float, sf2: f
 
 @dataclasses.dataclass
 class Model:
-    """Separable OU x Matern state-space model on a fixed grid (appendix lemma on STSGMPs)."""
+    """Separable state-space model on a fixed grid (appendix lemma on STSGMPs): A = A^t (x) I_n,
+    Q = Q^t (x) K, stationary prior covariance Sigma = P^t_inf (x) K.
+
+    temporal 0: Ornstein-Uhlenbeck factor (D' = 1): A^t = a = exp(-dt/l_t), P^t_inf = 1.
+    temporal 1: Matern-3/2 factor (D' = 2, state (f, df/dt) stacked as [positions; velocities]):
+      the SDE dx = F x dt + L dW with F = [[0, 1], [-lam^2, -2 lam]], lam = sqrt(3)/l_t, whose
+      stationary covariance is P^t_inf = diag(1, lam^2) (unit temporal variance; sigma_f^2 sits in K);
+      A^t = expm(F dt) and Q^t = P^t_inf - A^t P^t_inf A^t^T (Lemma: Sigma_{k+1} = A Sigma_k A^T + Q).
+    """
     X: np.ndarray
     kernel: int
     lx: float
     sf2: float
     a: float
     sn2: float
-    mu: Optional[np.ndarray]   # (T+1, n) prior mean or None
+    mu: Optional[np.ndarray]   # (T+1, n) prior mean of the positions, or None
+    temporal: int = 0
+    At: Optional[np.ndarray] = None     # (D', D') temporal transition over one step
+    Pinf: Optional[np.ndarray] = None   # (D', D') stationary temporal covariance
+
+    def __post_init__(self):
+        if self.At is None:
+            self.At = np.array([[self.a]])
+            self.Pinf = np.array([[1.0]])
 
     @property
     def n(self):
         return self.X.shape[0]
+
+    @property
+    def dprime(self):
+        return self.At.shape[0]
+
+    @property
+    def D(self):
+        """State dimension n D'."""
+        return self.n * self.dprime
 
     def K_times(self, B: np.ndarray, rows: Optional[np.ndarray] = None,
                 cols: Optional[np.ndarray] = None) -> np.ndarray:
@@ -120,14 +152,63 @@ class Model:
             out[lo:hi] = kernel_matrix(Xr[lo:hi], Xc, self.kernel, self.lx, self.sf2) @ B2
         return out.reshape((Xr.shape[0],) + B.shape[1:])
 
+    def _blocks(self, B):
+        n = self.n
+        return [B[q * n:(q + 1) * n] for q in range(self.dprime)]
+
+    def _kron_times(self, C: np.ndarray, B: np.ndarray) -> np.ndarray:
+        """(C (x) I_n) B for a D' x D' matrix C and a D-row B."""
+        Bq = self._blocks(B)
+        return np.concatenate([sum(C[p, q] * Bq[q] for q in range(self.dprime)) for p in range(self.dprime)],
+                              axis=0)
+
+    def A_times(self, B: np.ndarray) -> np.ndarray:
+        return self._kron_times(self.At, B)
+
+    def AT_times(self, B: np.ndarray) -> np.ndarray:
+        return self._kron_times(self.At.T, B)
+
+    def sigma_times(self, B: np.ndarray) -> np.ndarray:
+        """Sigma B = (P^t_inf (x) K) B."""
+        KB = [self.K_times(Bq) for Bq in self._blocks(B)]
+        return np.concatenate([sum(self.Pinf[p, q] * KB[q] for q in range(self.dprime)) for p in range(self.dprime)],
+                              axis=0)
+
+    def sigma_Ht_times(self, V: np.ndarray, obs: np.ndarray) -> np.ndarray:
+        """Sigma H^T V with H selecting the positions obs: blocks P^t_inf[p, 0] K(X, X_obs) V."""
+        KV = self.K_times(V, cols=obs)
+        return np.concatenate([self.Pinf[p, 0] * KV for p in range(self.dprime)], axis=0)
+
+    def H_sigma_Ht(self, obs: np.ndarray) -> np.ndarray:
+        """H Sigma H^T = P^t_inf[0, 0] K(X_obs, X_obs)."""
+        return self.Pinf[0, 0] * self.K_times(np.eye(len(obs)), rows=obs, cols=obs)
+
+    def prior_var(self) -> np.ndarray:
+        """diag(Sigma) (D)."""
+        return np.concatenate([np.full(self.n, self.Pinf[p, p] * self.sf2) for p in range(self.dprime)])
+
+    def _mean_state(self, k: int) -> np.ndarray:
+        """Prior mean of the state at step k: the position mean mu_k, zero velocities (reading R20)."""
+        out = np.zeros(self.D)
+        if self.mu is not None:
+            out[:self.n] = self.mu[k]
+        return out
+
     def b(self, k: int) -> np.ndarray:
         """Dynamics offset b_{k-1} so that the prior mean at step k is mu_k."""
-        if self.mu is None:
-            return np.zeros(self.n)
-        return self.mu[k] - self.a * self.mu[k - 1]
+        return self._mean_state(k) - self.A_times(self._mean_state(k - 1))
 
     def m0(self) -> np.ndarray:
-        return np.zeros(self.n) if self.mu is None else self.mu[0].copy()
+        return self._mean_state(0)
+
+
+def matern32_temporal(lt: float, dt: float):
+    """(A^t, P^t_inf) of the Matern-3/2 temporal factor over a step dt.  F + lam I is nilpotent
+    ((F + lam I)^2 = 0), so expm(F dt) = exp(-lam dt) (I + dt (F + lam I))."""
+    lam = math.sqrt(3.0) / lt
+    F = np.array([[0.0, 1.0], [-lam * lam, -2.0 * lam]])
+    At = math.exp(-lam * dt) * (np.eye(2) + dt * (F + lam * np.eye(2)))
+    return At, np.diag([1.0, lam * lam])
 
 
 def model_from(w, log_lx=None, log_lt=None, log_sf2=None, log_sn2=None) -> Model:
@@ -136,8 +217,14 @@ def model_from(w, log_lx=None, log_lt=None, log_sf2=None, log_sn2=None) -> Model
     lt = math.exp(w.log_lt if log_lt is None else log_lt)
     sf2 = math.exp(w.log_sf2 if log_sf2 is None else log_sf2)
     sn2 = math.exp(w.log_sn2 if log_sn2 is None else log_sn2)
+    temporal = int(getattr(w, "temporal", 0))
+    At = Pinf = None
+    if temporal == 1:
+        At, Pinf = matern32_temporal(lt, w.dt)
+    elif temporal != 0:
+        raise ValueError(f"unknown temporal factor {temporal}")
     return Model(X=np.asarray(w.coords, dtype=np.float64), kernel=w.kernel, lx=lx, sf2=sf2,
-                 a=math.exp(-w.dt / lt), sn2=sn2, mu=w.prior_mean)
+                 a=math.exp(-w.dt / lt), sn2=sn2, mu=w.prior_mean, temporal=temporal, At=At, Pinf=Pinf)
 
 
 # ----------------------------------------------------------------------------- truncation
@@ -158,12 +245,12 @@ def truncate(M: np.ndarray, r: int):
 # ----------------------------------------------------------------------------- filter
 @dataclasses.dataclass
 class FilterResult:
-    m: np.ndarray                 # (T+1, n) filter means
-    var: np.ndarray               # (T+1, n) filter marginal variances (pre-truncation)
-    M_hat: List[np.ndarray]       # updated factor per step (untruncated); [0] is n x 0
-    M_pred: List[np.ndarray]      # predictive factor a M+_{k-1} per step; [0] is n x 0
-    w: List[np.ndarray]           # filter message w_k = H^T v (dense n-vector); [0] zeros
-    W: List[np.ndarray]           # filter message W_k = H^T V (dense n x j); [0] empty
+    m: np.ndarray                 # (T+1, D) filter means (D = n D' state dimension)
+    var: np.ndarray               # (T+1, D) filter marginal variances (pre-truncation)
+    M_hat: List[np.ndarray]       # updated factor per step (untruncated); [0] is D x 0
+    M_pred: List[np.ndarray]      # predictive factor A M+_{k-1} per step; [0] is D x 0
+    w: List[np.ndarray]           # filter message w_k = H^T v (dense D-vector); [0] zeros
+    W: List[np.ndarray]           # filter message W_k = H^T V (dense D x j); [0] empty
     S: List[np.ndarray]           # actions per step (m_k x j)
     U: List[Optional[np.ndarray]] # truncation rotations per step (None: not truncated)
     nll: np.ndarray               # (T+1,) per-step NLL terms, [0] = 0
@@ -179,11 +266,10 @@ def update_iterative(model: Model, m_pred, M_pred, obs, y, budget, cg_rtol=0.0, 
     Forms G = H P^- H^T + sigma_n^2 I densely (m x m; this is the oracle) and
     runs the G-orthogonalised projected update with CG actions s = current
     residual.  Returns (m, M_hat, w, W, S, V, G, r0)."""
-    n = model.n
-    Xo = obs
+    D = model.D
     mo = len(obs)
-    Ko = model.K_times(np.eye(mo), rows=Xo, cols=Xo)
-    Mo = M_pred[obs]
+    Ko = model.H_sigma_Ht(obs)
+    Mo = M_pred[obs]                                  # H M^-: the positions come first in the state
     G = Ko - Mo @ Mo.T + model.sn2 * np.eye(mo)
     r0 = y - m_pred[obs]
     v = np.zeros(mo)
@@ -206,14 +292,14 @@ def update_iterative(model: Model, m_pred, M_pred, obs, y, budget, cg_rtol=0.0, 
         V = np.concatenate([V, (d / math.sqrt(eta))[:, None]], axis=1)
         S.append(s)
     S = np.stack(S, axis=1) if S else np.zeros((mo, 0))
-    # w = H^T v, W = H^T V; P^- [W w] = K(X, X_o) [V v] - M^- (M_o^T [V v])
+    # w = H^T v, W = H^T V; P^- [W w] = Sigma H^T [V v] - M^- (M_o^T [V v])
     Vv = np.concatenate([V, v[:, None]], axis=1)
-    PVv = model.K_times(Vv, cols=Xo) - M_pred @ (Mo.T @ Vv)
+    PVv = model.sigma_Ht_times(Vv, obs) - M_pred @ (Mo.T @ Vv)
     m_new = m_pred + PVv[:, -1]
     M_hat = np.concatenate([M_pred, PVv[:, :-1]], axis=1)
-    w = np.zeros(n)
+    w = np.zeros(D)
     w[obs] = v
-    W = np.zeros((n, V.shape[1]))
+    W = np.zeros((D, V.shape[1]))
     W[obs] = V
     return m_new, M_hat, w, W, S, V, G, r0
 
@@ -233,9 +319,9 @@ def update_batch(model: Model, m_pred, M_pred, obs, y, S):
 
     Ghat = S^T G S with G = H P^- H^T + sigma_n^2 I (dense here), W = H^T S L^-T (L L^T = Ghat),
     w = H^T S Ghat^-1 S^T r0.  Returns the same tuple as update_iterative."""
-    n = model.n
+    D = model.D
     mo = len(obs)
-    Ko = model.K_times(np.eye(mo), rows=obs, cols=obs)
+    Ko = model.H_sigma_Ht(obs)
     Mo = M_pred[obs]
     G = Ko - Mo @ Mo.T + model.sn2 * np.eye(mo)
     r0 = y - m_pred[obs]
@@ -244,12 +330,12 @@ def update_batch(model: Model, m_pred, M_pred, obs, y, S):
     V = np.linalg.solve(L, S.T).T                     # S L^-T: lsqrt of Ghat^+ applied to S
     v = S @ np.linalg.solve(Gh, S.T @ r0)
     Vv = np.concatenate([V, v[:, None]], axis=1)
-    PVv = model.K_times(Vv, cols=obs) - M_pred @ (Mo.T @ Vv)
+    PVv = model.sigma_Ht_times(Vv, obs) - M_pred @ (Mo.T @ Vv)
     m_new = m_pred + PVv[:, -1]
     M_hat = np.concatenate([M_pred, PVv[:, :-1]], axis=1)
-    w = np.zeros(n)
+    w = np.zeros(D)
     w[obs] = v
-    W = np.zeros((n, V.shape[1]))
+    W = np.zeros((D, V.shape[1]))
     W[obs] = V
     return m_new, M_hat, w, W, S, V, G, r0
 
@@ -277,23 +363,24 @@ def filter_run(w, model: Optional[Model] = None, budget=None, rank_r=None, cg_rt
     model = model or model_from(w)
     budget = w.budget_i if budget is None else budget
     rank_r = w.rank_r if rank_r is None else rank_r
-    n, T = model.n, w.T
-    m = np.zeros((T + 1, n))
-    var = np.zeros((T + 1, n))
+    D, T = model.D, w.T
+    pvar = model.prior_var()
+    m = np.zeros((T + 1, D))
+    var = np.zeros((T + 1, D))
     m[0] = model.m0()
-    var[0] = model.sf2
-    Mplus = np.zeros((n, 0))
-    res = FilterResult(m=m, var=var, M_hat=[Mplus], M_pred=[Mplus], w=[np.zeros(n)],
-                       W=[np.zeros((n, 0))], S=[np.zeros((0, 0))], U=[None], nll=np.zeros(T + 1),
+    var[0] = pvar
+    Mplus = np.zeros((D, 0))
+    res = FilterResult(m=m, var=var, M_hat=[Mplus], M_pred=[Mplus], w=[np.zeros(D)],
+                       W=[np.zeros((D, 0))], S=[np.zeros((0, 0))], U=[None], nll=np.zeros(T + 1),
                        iters=np.zeros(T + 1, dtype=np.int64), dropped=np.zeros(T + 1), G=[None], r0=[None])
     for k in range(1, T + 1):
         # predict (Alg. 1): m^- = A m + b, M^- = A M+
-        m_pred = model.a * m[k - 1] + model.b(k)
-        M_pred = model.a * Mplus
+        m_pred = model.A_times(m[k - 1]) + model.b(k)
+        M_pred = model.A_times(Mplus)
         obs = w.obs(k)
         if len(obs) == 0:   # IsMissing
             m_new, M_hat = m_pred, M_pred
-            wk, Wk, S, G, r0 = np.zeros(n), np.zeros((n, 0)), np.zeros((0, 0)), None, None
+            wk, Wk, S, G, r0 = np.zeros(D), np.zeros((D, 0)), np.zeros((0, 0)), None, None
         else:
             if policy == "cg":
                 Srep = None if S_replay is None else S_replay[k]
@@ -304,7 +391,7 @@ def filter_run(w, model: Optional[Model] = None, budget=None, rank_r=None, cg_rt
                 m_new, M_hat, wk, Wk, S, V, G, r0 = update_batch(model, m_pred, M_pred, obs, w.yk(k), Sb)
             res.nll[k] = _nll_step(G, S, r0)
         m[k] = m_new
-        var[k] = model.sf2 - np.sum(M_hat * M_hat, axis=1)
+        var[k] = pvar - np.sum(M_hat * M_hat, axis=1)
         if U_replay is not None:   # frozen truncation: None = the base run kept the factor
             U, lam_drop = U_replay[k], None
             Mplus = M_hat if U is None else M_hat @ U
@@ -330,25 +417,26 @@ def smoother_run(w, filt: FilterResult, model: Optional[Model] = None, rank_r=No
     Returns (means, variances, per-step smoother truncation rotations)."""
     model = model or model_from(w)
     rank_r = w.rank_r if rank_r is None else rank_r
-    T, n, a = w.T, model.n, model.a
-    ms = np.zeros((T + 1, n))
-    vs = np.zeros((T + 1, n))
+    T, D = w.T, model.D
+    ms = np.zeros((T + 1, D))
+    vs = np.zeros((T + 1, D))
     ms[T] = filt.m[T]
     vs[T] = filt.var[T]
     ws = filt.w[T]
     Ws = filt.W[T]
     Us: List[Optional[np.ndarray]] = [None] * (T + 1)
     for k in range(T - 1, -1, -1):
-        X = a * np.concatenate([Ws, ws[:, None]], axis=1)          # A^T [Ws ws]
+        X = model.AT_times(np.concatenate([Ws, ws[:, None]], axis=1))   # A^T [Ws ws]
         Mk = filt.M_hat[k]
-        PX = model.K_times(X) - Mk @ (Mk.T @ X)                      # P_k A^T [Ws ws]
+        SX = model.sigma_times(X)
+        PX = SX - Mk @ (Mk.T @ X)                                    # P_k A^T [Ws ws]
         ms[k] = filt.m[k] + PX[:, -1]
         E = PX[:, :-1]
         vs[k] = filt.var[k] - np.sum(E * E, axis=1)                 # M^s_k = (M_k, P_k A^T Ws)
         if k == 0:
             break
         Mp = filt.M_pred[k]
-        PmX = model.K_times(X) - Mp @ (Mp.T @ X)                     # P^-_k A^T [Ws ws]
+        PmX = SX - Mp @ (Mp.T @ X)                                   # P^-_k A^T [Ws ws]
         Wk = filt.W[k]
         Y2 = X - Wk @ (Wk.T @ PmX)                                   # (I - W W^T P^-) A^T [Ws ws]
         ws = filt.w[k] + Y2[:, -1]
@@ -373,6 +461,8 @@ def sample_run(w, filt: FilterResult, x0, q, eps, model: Optional[Model] = None)
     x^s_k = x_k + P_k (a ws_{k+1}); ws_k = w_k + a ws_{k+1} - W_k W_k^T P^-_k (a ws_{k+1}).
     Returns (filter draws (T+1, n, S), smoother draws (T+1, n, S))."""
     model = model or model_from(w)
+    if model.dprime != 1:
+        raise NotImplementedError("sample_run: Ornstein-Uhlenbeck temporal factor only")
     T, n, a = w.T, model.n, model.a
     S = x0.shape[1]
     xf = np.zeros((T + 1, n, S))
@@ -422,6 +512,8 @@ def interpolate_run(w, filt: FilterResult, smooth_W, smooth_w, tq, mu_q=None, mo
     smooth_w[k] are the smoother messages Ws_k, ws_k of Alg. 3 (smoother_messages).
     Returns (filter means, filter variances, smoother means, smoother variances), each (len(tq), n)."""
     model = model or model_from(w)
+    if model.dprime != 1:
+        raise NotImplementedError("interpolate_run: Ornstein-Uhlenbeck temporal factor only")
     T, n = w.T, model.n
     lt = -w.dt / math.log(model.a)
     out = [np.zeros((len(tq), n)) for _ in range(4)]
@@ -452,15 +544,15 @@ def smoother_messages(w, filt: FilterResult, model: Optional[Model] = None, rank
     smoother carries from step k + 1 to step k); entry k holds the message after step k's update."""
     model = model or model_from(w)
     rank_r = w.rank_r if rank_r is None else rank_r
-    T, n, a = w.T, model.n, model.a
+    T = w.T
     Wm = [None] * (T + 1)
     wm = [None] * (T + 1)
     ws, Ws = filt.w[T], filt.W[T]
     Wm[T], wm[T] = Ws, ws
     for k in range(T - 1, 0, -1):
-        X = a * np.concatenate([Ws, ws[:, None]], axis=1)
+        X = model.AT_times(np.concatenate([Ws, ws[:, None]], axis=1))
         Mp = filt.M_pred[k]
-        PmX = model.K_times(X) - Mp @ (Mp.T @ X)
+        PmX = model.sigma_times(X) - Mp @ (Mp.T @ X)
         Wk = filt.W[k]
         Y2 = X - Wk @ (Wk.T @ PmX)
         ws = filt.w[k] + Y2[:, -1]

@@ -12,8 +12,10 @@ step k = 1..T a set of m_k observed grid indices with i.i.d. Gaussian noise.
 
 Data are drawn from random Fourier features (RFF) of the Matern spectral
 density (a multivariate Student-t with 2*nu degrees of freedom, scale 1/l_x),
-with OU dynamics on the feature weights, so that the sample is (up to the
-feature count) a draw from the same separable prior.  The paper's ERA5 data are
+with OU dynamics on the feature weights (or, for the Matern-3/2 temporal
+factor, weight paths drawn from that kernel's covariance over the step times),
+so that the sample is (up to the feature count) a draw from the same separable
+prior.  The paper's ERA5 data are
 not available here; configs "sphere-*" stand in for them with the ERA5 grid
 shape (lat-lon grid mapped to the unit sphere, extrinsic Matern on chordal
 distance).
@@ -48,6 +50,7 @@ class Workload:
     rank_r: int                   # <= 0: no truncation
     prior_mean: Optional[np.ndarray] = None   # (T+1, n) float64 or None (zero mean)
     truth: Optional[np.ndarray] = None        # (T+1, n) latent sample when kept
+    temporal: int = 0                         # temporal factor: 0 Ornstein-Uhlenbeck, 1 Matern-3/2
 
     @property
     def n(self) -> int:
@@ -128,8 +131,11 @@ def seasonal_mean(coords: np.ndarray, T: int, dt: float) -> np.ndarray:
 
 
 def rff_draw(rng, coords, kernel, lx, lt, sf2, sn2, T, dt, obs_ptr, obs_idx,
-             n_features=1024, keep_truth=False, prior_mean=None, device=None):
-    """Observations y from an RFF prior sample with OU feature weights.
+             n_features=1024, keep_truth=False, prior_mean=None, device=None, temporal=0):
+    """Observations y from an RFF prior sample with OU feature weights (temporal = 0) or with
+    Matern-3/2 feature weights (temporal = 1: each weight's path over the step times t_k = k dt is
+    drawn from the closed-form temporal covariance (1 + sqrt(3) |t - t'| / l_t) exp(-sqrt(3) |t - t'| / l_t)
+    through its Cholesky factor).
 
     Returns (y, truth-or-None).  The bulk cos() evaluation runs through torch on
     `device` when given (data generation only; never timed).
@@ -140,11 +146,18 @@ def rff_draw(rng, coords, kernel, lx, lt, sf2, sn2, T, dt, obs_ptr, obs_idx,
     g = rng.chisquare(2 * nu, size=n_features)
     omega = z / lx * np.sqrt(2 * nu / g)[:, None]
     phase = rng.uniform(0, 2 * np.pi, size=n_features)
-    a = math.exp(-dt / lt)
-    w = np.empty((T + 1, n_features))
-    w[0] = rng.standard_normal(n_features)
-    for k in range(1, T + 1):
-        w[k] = a * w[k - 1] + math.sqrt(1 - a * a) * rng.standard_normal(n_features)
+    if temporal == 1:
+        tt = np.arange(T + 1) * dt
+        u = math.sqrt(3.0) * np.abs(tt[:, None] - tt[None, :]) / lt
+        Ct = (1.0 + u) * np.exp(-u)
+        Lt = np.linalg.cholesky(Ct + 1e-12 * np.eye(T + 1))
+        w = Lt @ rng.standard_normal((T + 1, n_features))
+    else:
+        a = math.exp(-dt / lt)
+        w = np.empty((T + 1, n_features))
+        w[0] = rng.standard_normal(n_features)
+        for k in range(1, T + 1):
+            w[k] = a * w[k - 1] + math.sqrt(1 - a * a) * rng.standard_normal(n_features)
     scale = math.sqrt(2.0 * sf2 / n_features)
     noise = rng.standard_normal(obs_idx.size) * math.sqrt(sn2)
 
@@ -179,7 +192,7 @@ def rff_draw(rng, coords, kernel, lx, lt, sf2, sn2, T, dt, obs_ptr, obs_idx,
 
 def make(name, coords, kernel, lx, lt, sf2, sn2, T, dt, m, budget_i, rank_r, seed,
          stations=False, seasonal=False, missing=(), n_features=1024, keep_truth=False,
-         device=None) -> Workload:
+         device=None, temporal=0) -> Workload:
     rng = np.random.default_rng(seed)
     n = coords.shape[0]
     if stations:
@@ -188,10 +201,11 @@ def make(name, coords, kernel, lx, lt, sf2, sn2, T, dt, m, budget_i, rank_r, see
         ptr, idx = obs_uniform(rng, n, m, T, missing=missing)
     pm = seasonal_mean(coords, T, dt) if seasonal else None
     y, truth = rff_draw(rng, coords, kernel, lx, lt, sf2, sn2, T, dt, ptr, idx,
-                        n_features=n_features, keep_truth=keep_truth, prior_mean=pm, device=device)
+                        n_features=n_features, keep_truth=keep_truth, prior_mean=pm, device=device,
+                        temporal=temporal)
     return Workload(name=name, coords=coords, kernel=kernel, log_lx=math.log(lx), log_lt=math.log(lt),
                     log_sf2=math.log(sf2), log_sn2=math.log(sn2), T=T, dt=dt, obs_ptr=ptr, obs_idx=idx,
-                    y=y, budget_i=budget_i, rank_r=rank_r, prior_mean=pm, truth=truth)
+                    y=y, budget_i=budget_i, rank_r=rank_r, prior_mean=pm, truth=truth, temporal=temporal)
 
 
 # ----------------------------------------------------------------------------- named configs

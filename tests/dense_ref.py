@@ -4,7 +4,9 @@ None of this code is shared with `oracle/`: every routine is written from its
 textbook / paper definition with dense matrices.
 
 * `kf_rts`: the Kalman filter (Thm. "Kalman filter") and the RTS smoother
-  (Thm. "RTS smoother") with dense covariances and an explicit smoother gain.
+  (Thm. "RTS smoother") with dense covariances and an explicit smoother gain, on the dense
+  state-space matrices A = A^t (x) I, Q, Sigma; for the Matern-3/2 temporal factor A^t and P^t_inf
+  come from scipy's matrix exponential and Lyapunov solver (`_temporal`), not from the oracle.
 * `batch_gp`: the iteratively approximated batch GP posterior (Def.
   "Iteratively approximated batch GP regression") with block-diagonal actions
   (Prop. "Connecting batch spatio-temporal GP regression and filtering and
@@ -53,17 +55,63 @@ def _mu(w, k):
     return np.zeros(w.n) if w.prior_mean is None else w.prior_mean[k]
 
 
-def kf_rts(w):
-    """Dense Kalman filter + RTS smoother; returns dict of means/vars (T+1, n) and per-step NLL."""
+def _temporal(w):
+    """Temporal factor (A^t, P^t_inf) of a workload, from library routines: the OU factor
+    (a = exp(-dt/l_t), 1); for the Matern-3/2 factor the matrix exponential of the SDE drift
+    F = [[0, 1], [-lam^2, -2 lam]] (scipy expm) and the stationary covariance from the continuous
+    Lyapunov equation F P + P F^T + L q L^T = 0 with the Matern-3/2 spectral density q = 4 lam^3."""
+    lx, lt, sf2, sn2, a = _params(w)
+    if getattr(w, "temporal", 0) == 0:
+        return np.array([[a]]), np.array([[1.0]])
+    import scipy.linalg as sl
+    lam = math.sqrt(3.0) / lt
+    F = np.array([[0.0, 1.0], [-lam * lam, -2.0 * lam]])
+    Pinf = sl.solve_continuous_lyapunov(F, -np.array([[0.0, 0.0], [0.0, 4.0 * lam ** 3]]))
+    return sl.expm(F * w.dt), Pinf
+
+
+def _tcorr(w, lag):
+    """Temporal correlation between steps lag apart (closed form): a^|lag| for the OU factor,
+    (1 + lam tau) exp(-lam tau), tau = |lag| dt, lam = sqrt(3)/l_t for the Matern-3/2 factor."""
+    lx, lt, sf2, sn2, a = _params(w)
+    lag = np.abs(lag)
+    if getattr(w, "temporal", 0) == 0:
+        return a ** lag
+    u = math.sqrt(3.0) * lag * w.dt / lt
+    return (1.0 + u) * np.exp(-u)
+
+
+def _lgssm(w):
+    """Dense (A, Q, Sigma, state prior means) of the state-space model: A = A^t (x) I,
+    Sigma = P^t_inf (x) K, Q = Sigma - A Sigma A^T; the state mean stacks the prior mean of the
+    positions above zero velocities."""
     lx, lt, sf2, sn2, a = _params(w)
     K = _kern(w.coords, w.coords, w.kernel, lx, sf2)
-    n, T = w.n, w.T
-    m, P = _mu(w, 0).copy(), K.copy()
+    At, Pinf = _temporal(w)
+    dp = At.shape[0]
+    A = np.kron(At, np.eye(w.n))
+    Sig = np.kron(Pinf, K)
+    Q = Sig - A @ Sig @ A.T
+
+    def mu(k):
+        out = np.zeros(dp * w.n)
+        out[:w.n] = _mu(w, k)
+        return out
+    return A, Q, Sig, mu
+
+
+def kf_rts(w):
+    """Dense Kalman filter + RTS smoother over the whole state (D = n D'); returns dict of
+    means/vars (T+1, D) and per-step NLL."""
+    lx, lt, sf2, sn2, a = _params(w)
+    A, Q, Sig, mu = _lgssm(w)
+    T = w.T
+    m, P = mu(0), Sig.copy()
     mf, Pf, mp, Pp = [m], [P], [None], [None]
     nll = np.zeros(T + 1)
     for k in range(1, T + 1):
-        mpk = a * m + (_mu(w, k) - a * _mu(w, k - 1))
-        Ppk = a * a * P + (1 - a * a) * K
+        mpk = A @ m + (mu(k) - A @ mu(k - 1))
+        Ppk = A @ P @ A.T + Q
         o = w.obs(k)
         if len(o):
             G = Ppk[np.ix_(o, o)] + sn2 * np.eye(len(o))
@@ -79,7 +127,7 @@ def kf_rts(w):
     ms, Ps = [None] * (T + 1), [None] * (T + 1)
     ms[T], Ps[T] = mf[T], Pf[T]
     for k in range(T - 1, -1, -1):
-        J = a * np.linalg.solve(Pp[k + 1].T, Pf[k].T).T          # P_k A^T (P^-_{k+1})^{-1}
+        J = np.linalg.solve(Pp[k + 1].T, (Pf[k] @ A.T).T).T      # P_k A^T (P^-_{k+1})^{-1}
         ms[k] = mf[k] + J @ (ms[k + 1] - mp[k + 1])
         Ps[k] = Pf[k] + J @ (Ps[k + 1] - Pp[k + 1]) @ J.T
     return dict(mf=np.array(mf), vf=np.array([np.diag(p) for p in Pf]),
@@ -93,16 +141,16 @@ def _spacetime(w, upto=None):
     T = w.T if upto is None else upto
     steps = np.concatenate([np.full(len(w.obs(k)), k) for k in range(1, T + 1)]) if T > 0 else np.zeros(0, int)
     idx = np.concatenate([w.obs(k) for k in range(1, T + 1)]) if T > 0 else np.zeros(0, int)
-    return K, steps.astype(int), idx.astype(int), a, sn2
+    return K, steps.astype(int), idx.astype(int), sn2
 
 
 def batch_gp(w, S_list, upto=None, k_eval=None):
     """Iteratively approximated batch GP posterior marginals at all grid points of step k_eval,
     using data of steps 1..upto and block-diagonal actions S = diag(S_1, ..., S_upto)."""
-    K, st, ix, a, sn2 = _spacetime(w, upto)
+    K, st, ix, sn2 = _spacetime(w, upto)
     T = w.T if upto is None else upto
     N = ix.size
-    Kzz = (a ** np.abs(st[:, None] - st[None, :])) * K[np.ix_(ix, ix)]
+    Kzz = _tcorr(w, st[:, None] - st[None, :]) * K[np.ix_(ix, ix)]
     Ky = Kzz + sn2 * np.eye(N)
     cols = sum(S_list[k].shape[1] for k in range(1, T + 1))
     S = np.zeros((N, cols))
@@ -115,7 +163,7 @@ def batch_gp(w, S_list, upto=None, k_eval=None):
     ybar = np.concatenate([w.yk(k) - _mu(w, k)[w.obs(k)] for k in range(1, T + 1)])
     C = S @ np.linalg.solve(S.T @ Ky @ S, S.T)
     kk = T if k_eval is None else k_eval
-    Kxz = (a ** np.abs(kk - st))[None, :] * K[:, ix]
+    Kxz = _tcorr(w, kk - st)[None, :] * K[:, ix]
     mean = _mu(w, kk) + Kxz @ (C @ ybar)
     var = np.diag(K) - np.einsum("ij,jk,ik->i", Kxz, C, Kxz)
     Gh = S.T @ Ky @ S
@@ -128,7 +176,8 @@ def batch_gp(w, S_list, upto=None, k_eval=None):
 def batch_nll_grad(w, S_list):
     """Analytic d NLL / d(log l_x, log l_t, log sf2, log sn2) of the projected batch NLL, frozen S."""
     lx, lt, sf2, sn2, a = _params(w)
-    K, st, ix, a, sn2 = _spacetime(w)
+    assert getattr(w, "temporal", 0) == 0, "batch_nll_grad: OU temporal factor"
+    K, st, ix, sn2 = _spacetime(w)
     N = ix.size
     dk = np.abs(st[:, None] - st[None, :])
     At = a ** dk
@@ -160,33 +209,33 @@ def batch_nll_grad(w, S_list):
 
 
 def dense_truncated(w, S_list, r):
-    """Outer-product (dense covariance) CAKF + CAKS with truncation on the n x n downdates.
+    """Outer-product (dense covariance) CAKF + CAKS with truncation on the D x D downdates.
 
-    Filter: P^-_k = a^2 P~_{k-1} + (1-a^2) K; update with the given actions S_k;
-    truncation P~_k = K - best_rank_r(K - P_k).  Smoother (Alg. 3 in outer-product
-    form): Omega_k = W_k W_k^T + B Omega~_{k+1} B^T with B = (I - W W^T P^-_k) a and
-    Omega~ = best_rank_r(Omega); mean m^s_k = m_k + P_k a ws_{k+1};
-    cov P^s_k = P_k - a^2 P_k Omega~_{k+1} P_k."""
+    Filter: P^-_k = A P~_{k-1} A^T + Q; update with the given actions S_k;
+    truncation P~_k = Sigma - best_rank_r(Sigma - P_k).  Smoother (Alg. 3 in outer-product
+    form): Omega_k = W_k W_k^T + B Omega~_{k+1} B^T with B = (I - W W^T P^-_k) A^T and
+    Omega~ = best_rank_r(Omega); mean m^s_k = m_k + P_k A^T ws_{k+1};
+    cov P^s_k = P_k - P_k A^T Omega~_{k+1} A P_k."""
     lx, lt, sf2, sn2, a = _params(w)
-    K = _kern(w.coords, w.coords, w.kernel, lx, sf2)
-    n, T = w.n, w.T
+    A, Q, Sig, mu = _lgssm(w)
+    D, T = Sig.shape[0], w.T
 
-    def rank_r(D):
+    def rank_r(Dm):
         if r <= 0:
-            return D
-        lam, U = np.linalg.eigh(D)
+            return Dm
+        lam, U = np.linalg.eigh(Dm)
         o = np.argsort(lam)[::-1][:r]
         return (U[:, o] * lam[o]) @ U[:, o].T
 
-    m, Pt = _mu(w, 0).copy(), K.copy()
-    mf, Pf, Pm, Ww, ww = [m], [K.copy()], [K.copy()], [np.zeros((n, n))], [np.zeros(n)]
+    m, Pt = mu(0), Sig.copy()
+    mf, Pf, Pm, Ww, ww = [m], [Sig.copy()], [Sig.copy()], [np.zeros((D, D))], [np.zeros(D)]
     for k in range(1, T + 1):
-        mpk = a * m + (_mu(w, k) - a * _mu(w, k - 1))
-        Ppk = a * a * Pt + (1 - a * a) * K
+        mpk = A @ m + (mu(k) - A @ mu(k - 1))
+        Ppk = A @ Pt @ A.T + Q
         o = w.obs(k)
         Sk = S_list[k]
         if len(o) and Sk.shape[1]:
-            H = np.zeros((len(o), n))
+            H = np.zeros((len(o), D))
             H[np.arange(len(o)), o] = 1.0
             Hs = Sk.T @ H
             Gh = Hs @ Ppk @ Hs.T + sn2 * Sk.T @ Sk
@@ -196,18 +245,18 @@ def dense_truncated(w, S_list, r):
             m = mpk + Ppk @ wk
             P = Ppk - Ppk @ WW @ Ppk
         else:
-            wk, WW, m, P = np.zeros(n), np.zeros((n, n)), mpk, Ppk
+            wk, WW, m, P = np.zeros(D), np.zeros((D, D)), mpk, Ppk
         mf.append(m); Pf.append(P); Pm.append(Ppk); Ww.append(WW); ww.append(wk)
-        Pt = K - rank_r(K - P)
+        Pt = Sig - rank_r(Sig - P)
     ms, vs = [None] * (T + 1), [None] * (T + 1)
     ms[T], vs[T] = mf[T], np.diag(Pf[T])
     ws, Om = ww[T], Ww[T]
     for k in range(T - 1, -1, -1):
-        ms[k] = mf[k] + a * Pf[k] @ ws
-        vs[k] = np.diag(Pf[k] - a * a * Pf[k] @ Om @ Pf[k])
+        ms[k] = mf[k] + Pf[k] @ A.T @ ws
+        vs[k] = np.diag(Pf[k] - Pf[k] @ A.T @ Om @ A @ Pf[k])
         if k == 0:
             break
-        B = a * (np.eye(n) - Ww[k] @ Pm[k])
+        B = (np.eye(D) - Ww[k] @ Pm[k]) @ A.T
         ws = ww[k] + B @ ws
         Om = rank_r(Ww[k] + B @ Om @ B.T)
     return dict(mf=np.array(mf), vf=np.array([np.diag(p) for p in Pf]), ms=np.array(ms), vs=np.array(vs))
