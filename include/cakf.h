@@ -42,7 +42,7 @@
 extern "C" {
 #endif
 
-#define CAKF_ABI_VERSION 2
+#define CAKF_ABI_VERSION 3
 
 typedef enum {
   CAKF_OK = 0,
@@ -55,6 +55,23 @@ typedef enum {
 } cakf_status;
 
 enum { CAKF_MATERN12 = 0, CAKF_MATERN32 = 1, CAKF_MATERN52 = 2 };
+
+/* Temporal factor of the space-time separable prior (the appendix lemma on space-time separable
+   Gauss-Markov processes: A = A^t (x) I_n, Q = Q^t (x) K, stationary covariance P^t_inf (x) K). */
+enum {
+  CAKF_TEMPORAL_OU = 0,        /* Ornstein-Uhlenbeck, D' = 1: A^t = exp(-dt / l_t), P^t_inf = 1;
+                                  the state is the n grid values                               */
+  CAKF_TEMPORAL_MATERN32 = 1   /* Matern-3/2, D' = 2 (the remark after that lemma: Matern(p + 1/2)
+                                  kernels have an exact state-space form): the state holds the
+                                  grid values f and their time derivatives (D = 2n);
+                                  lam = sqrt(3) / l_t, A^t = expm(F dt) with
+                                  F = [[0, 1], [-lam^2, -2 lam]], P^t_inf = diag(1, lam^2).  The
+                                  outputs (means, variances) are those of f; a prior mean mu_k
+                                  applies to f (zero for the derivatives).  Supported by
+                                  cakf_filter / cakf_smooth / cakf_nll with CAKF_STORE_FP32;
+                                  cakf_nll_backward, cakf_sample, cakf_interpolate and
+                                  freeze_truncation return CAKF_ERR_ARG                        */
+};
 
 /* Arithmetic of the kernel-Gram x block products (everything else follows in parentheses). */
 enum {
@@ -96,12 +113,12 @@ enum {
 
 typedef struct {
   int32_t abi_version;        /* must equal CAKF_ABI_VERSION                                  */
-  int32_t n;                  /* grid points = state dimension D (OU prior: D' = 1)           */
+  int32_t n;                  /* grid points; the state dimension is D = n D' (temporal)       */
   int32_t dim;                /* coordinate dimension, 1..3                                   */
   const double* coords;       /* n*dim, row-major, host or device; sphere grids pass xyz       */
   int32_t kernel;             /* CAKF_MATERN12 | CAKF_MATERN32 | CAKF_MATERN52                */
   double log_lx;              /* log spatial lengthscale                                      */
-  double log_lt;              /* log OU temporal lengthscale                                  */
+  double log_lt;              /* log temporal lengthscale (OU or Matern-3/2, see temporal)     */
   double log_sf2;             /* log output variance sigma_f^2                                */
   double log_sn2;             /* log observation-noise variance sigma_n^2                     */
   int32_t T;                  /* number of steps with data; states are k = 0..T              */
@@ -129,6 +146,7 @@ typedef struct {
                                  (same sizes; with replay_actions this evaluates the frozen
                                  modified model of cakf_nll_backward at other hyperparameters, for
                                  finite-difference checks); 0: normal                          */
+  int32_t temporal;           /* CAKF_TEMPORAL_OU | CAKF_TEMPORAL_MATERN32                      */
 } cakf_problem;
 
 typedef struct cakf_ctx cakf_ctx;   /* library-owned state; holds the stored factors */

@@ -15,9 +15,10 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libcakf.so")
 
-ABI_VERSION = 2
+ABI_VERSION = 3
 OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_NUMERIC, ERR_TIMEOUT, ERR_STATE = range(7)
 MATERN12, MATERN32, MATERN52 = 0, 1, 2
+TEMPORAL = {"ou": 0, "matern32": 1}
 STORE_FP32, STORE_BF16, RECOMPUTE = 0, 1, 2
 STORAGE = {"fp32": STORE_FP32, "bf16": STORE_BF16, "recompute": RECOMPUTE}
 POLICY_CG, POLICY_COORDINATE, POLICY_BATCH = 0, 1, 2
@@ -36,6 +37,7 @@ class cakf_problem(C.Structure):
         ("rank_r", C.c_int32), ("cg_rtol", C.c_double), ("precision", C.c_int32),
         ("replay_actions", C.c_void_p), ("replay_counts", C.c_void_p), ("factor_storage", C.c_int32),
         ("checkpoint_every", C.c_int32), ("policy", C.c_int32), ("freeze_truncation", C.c_int32),
+        ("temporal", C.c_int32),
     ]
 
 
@@ -149,8 +151,9 @@ class Context:
 
 def make_problem(coords, kernel, log_lx, log_lt, log_sf2, log_sn2, T, dt, obs_ptr, obs_idx, y, budget_i, rank_r,
                  precision="fp32", prior_mean=None, cg_rtol=0.0, replay_actions=None, replay_counts=None,
-                 factor_storage="fp32", checkpoint_every=0, policy="cg", freeze_truncation=False):
-    """Build a cakf_problem; returns (struct, keepalive list)."""
+                 factor_storage="fp32", checkpoint_every=0, policy="cg", freeze_truncation=False, temporal=0):
+    """Build a cakf_problem; returns (struct, keepalive list).  temporal: 0 / "ou" (Ornstein-Uhlenbeck)
+    or 1 / "matern32" (Matern-3/2 temporal factor, state of values and time derivatives)."""
     keep = []
     p = cakf_problem()
     p.abi_version = ABI_VERSION
@@ -179,6 +182,7 @@ def make_problem(coords, kernel, log_lx, log_lt, log_sf2, log_sn2, T, dt, obs_pt
     p.checkpoint_every = int(checkpoint_every)
     p.policy = POLICIES[policy] if isinstance(policy, str) else int(policy)
     p.freeze_truncation = 1 if freeze_truncation else 0
+    p.temporal = TEMPORAL[temporal] if isinstance(temporal, str) else int(temporal)
     if replay_actions is not None:
         ra = np.ascontiguousarray(replay_actions, dtype=np.float64)
         rc = np.ascontiguousarray(replay_counts, dtype=np.int32)
@@ -189,7 +193,7 @@ def make_problem(coords, kernel, log_lx, log_lt, log_sf2, log_sn2, T, dt, obs_pt
 
 def problem_from_workload(w, precision="fp32", cg_rtol=0.0, replay=None, budget_i=None, rank_r=None,
                           factor_storage="fp32", checkpoint_every=0, policy="cg", freeze_truncation=False,
-                          **hp):
+                          temporal=None, **hp):
     """cakf_problem of a `synth.Workload`-like object (any object with the same fields)."""
     ra = rc = None
     if replay is not None:
@@ -199,7 +203,8 @@ def problem_from_workload(w, precision="fp32", cg_rtol=0.0, replay=None, budget_
                         w.obs_idx, w.y, w.budget_i if budget_i is None else budget_i,
                         w.rank_r if rank_r is None else rank_r, precision=precision, prior_mean=w.prior_mean,
                         cg_rtol=cg_rtol, replay_actions=ra, replay_counts=rc, factor_storage=factor_storage,
-                        checkpoint_every=checkpoint_every, policy=policy, freeze_truncation=freeze_truncation)
+                        checkpoint_every=checkpoint_every, policy=policy, freeze_truncation=freeze_truncation,
+                        temporal=getattr(w, "temporal", 0) if temporal is None else temporal)
 
 
 def _out(arr, shape):

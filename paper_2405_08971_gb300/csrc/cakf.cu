@@ -61,11 +61,21 @@ struct cakf_ctx {
   // problem
   int n = 0, dim = 0, kernel = 1, T = 0, budget = 0, rank_r = 0, precision = 1;
   double lx = 1, lt = 1, sf2 = 1, sn2 = 1, dt = 1, a = 1, cg_rtol = 0;
+  // temporal factor: dprime = 1 (OU: the factors are propagated lazily by the scalar a) or 2
+  // (Matern-3/2: two row blocks of ldn rows, positions then velocities; the prediction M^- =
+  // (A^t (x) I) M+ is applied in place, after which the step runs with the scalar 1).  At and
+  // Pt are A^t and P^t_inf, row-major.
+  int dprime = 1;
+  double At[4] = {1, 0, 0, 1}, Pt[4] = {1, 0, 0, 1};
+  // the scalar the lazily propagated factors carry (a for OU, 1 once the two-block prediction has
+  // been applied)
+  double a_lazy() const { return dprime == 2 ? 1.0 : a; }
   bool has_mu = false, replay = false;
   std::vector<int> obs_ptr, icap, mcols, replay_counts;
-  // sizes
-  int ldn = 0, mmax = 0, rmax = 0, imax = 0, nmax_eig = 0, cwmax = 0;
-  std::vector<size_t> off_M, off_PV, off_V, off_S;
+  // sizes: ldn rows per block, ldf = dprime * ldn rows of a factor column, mstride = the stride
+  // of the per-step state means in mf (n for OU, ldf for the two-block state)
+  int ldn = 0, ldf = 0, mstride = 0, mmax = 0, rmax = 0, imax = 0, nmax_eig = 0, cwmax = 0;
+  std::vector<size_t> off_M, off_PV, off_KV, off_V, off_S;
   // device memory
   std::vector<DevBuf> bufs;
   size_t dev_bytes = 0;
@@ -119,6 +129,7 @@ struct cakf_ctx {
   void *KWa = nullptr, *KWb = nullptr;   // smoother: K [Ws, ws] (ldn x (cw + 1)), double buffered
   void *WsA = nullptr, *WsB = nullptr, *wsA = nullptr, *wsB = nullptr, *Xs = nullptr, *Y = nullptr, *Xobs = nullptr,
        *Fb = nullptr;
+  void* KX = nullptr;   // two-block smoother: K A^T [Ws ws] (ldf x (cw + 1))
   double* Gws = nullptr;
   double* Gws2 = nullptr;
   // tensor-core operand staging (bf16 / tf32 paths)
@@ -242,6 +253,8 @@ int plan_and_alloc(cakf_ctx* c, const cakf_problem* p) {
   c->rmax = 0;
   for (int k = 0; k <= T; ++k) { c->imax = std::max(c->imax, c->icap[k]); c->rmax = std::max(c->rmax, c->mcols[k]); }
   c->ldn = round_up(std::max(c->n, 1), 128);
+  c->ldf = c->dprime * c->ldn;
+  c->mstride = c->dprime == 1 ? c->n : c->ldf;
   // smoother width bound: rank (after truncation) or the untruncated accumulation
   int cw = 0, cwmax = 0;
   for (int k = T; k >= 1; --k) {
@@ -266,7 +279,7 @@ int plan_and_alloc(cakf_ctx* c, const cakf_problem* p) {
   const int wmax = std::max(c->cwmax, cwfull) + 1;   // width of the smoother Gram x block
 
   const size_t es = elem_size(c->precision);
-  const size_t ldn = c->ldn;
+  const size_t ldn = c->ldn, ldf = c->ldf;
   c->storage = p->factor_storage;
   c->ckpt_req = p->checkpoint_every;
   c->policy = p->policy;
@@ -278,12 +291,14 @@ int plan_and_alloc(cakf_ctx* c, const cakf_problem* p) {
   // per-step pools
   c->off_M.assign(T + 2, 0);
   c->off_PV.assign(T + 2, 0);
+  c->off_KV.assign(T + 2, 0);
   c->off_V.assign(T + 2, 0);
   c->off_S.assign(T + 2, 0);
   for (int k = 0; k <= T; ++k) {
     int mk = (k == 0) ? 0 : c->obs_ptr[k] - c->obs_ptr[k - 1];
-    c->off_M[k + 1] = c->off_M[k] + ldn * c->mcols[k];
-    c->off_PV[k + 1] = c->off_PV[k] + (c->icap[k] ? ldn * (c->icap[k] + 1) : 0);
+    c->off_M[k + 1] = c->off_M[k] + ldf * c->mcols[k];
+    c->off_PV[k + 1] = c->off_PV[k] + (c->icap[k] ? ldf * (c->icap[k] + 1) : 0);
+    c->off_KV[k + 1] = c->off_KV[k] + (c->icap[k] ? ldn * (c->icap[k] + 1) : 0);
     c->off_V[k + 1] = c->off_V[k] + (size_t)mk * (c->icap[k] + 1);
     c->off_S[k + 1] = c->off_S[k] + (size_t)mk * c->icap[k];
   }
@@ -295,12 +310,12 @@ int plan_and_alloc(cakf_ctx* c, const cakf_problem* p) {
   if ((rc = c->alloc(c->obs, std::max<size_t>(Ntot, 1) * sizeof(int)))) return rc;
   if ((rc = c->alloc(c->y, std::max<size_t>(Ntot, 1) * sizeof(double)))) return rc;
   if (c->has_mu && (rc = c->alloc(c->mu, (size_t)(T + 1) * n * sizeof(double)))) return rc;
-  if ((rc = c->alloc(c->mf, (size_t)(T + 1) * n * sizeof(double)))) return rc;
+  if ((rc = c->alloc(c->mf, (size_t)(T + 1) * c->mstride * sizeof(double)))) return rc;
   if ((rc = c->alloc(c->vf, (size_t)(T + 1) * n * sizeof(double)))) return rc;
   if (c->seg_c == 0) {
     if ((rc = c->alloc(c->Mpool, c->off_M[T + 1] * es))) return rc;
     if ((rc = c->alloc(c->PVpool, c->off_PV[T + 1] * es))) return rc;
-    if ((rc = c->alloc(c->KVpool, c->off_PV[T + 1] * es))) return rc;
+    if ((rc = c->alloc(c->KVpool, c->off_KV[T + 1] * es))) return rc;
     if ((rc = c->alloc(c->Vpool, c->off_V[T + 1] * es))) return rc;
   } else {
     const size_t sc = c->seg_c, rmx = std::max(c->rmax, 1), ip = c->imax + 1;
@@ -344,7 +359,7 @@ int plan_and_alloc(cakf_ctx* c, const cakf_problem* p) {
   if ((rc = c->alloc(c->rfin, (T + 1) * sizeof(double)))) return rc;
   if ((rc = c->alloc(c->dropped_f, (T + 1) * sizeof(double)))) return rc;
   if ((rc = c->alloc(c->dropped_s, (T + 1) * sizeof(double)))) return rc;
-  if ((rc = c->alloc(c->mpred, n * sizeof(double)))) return rc;
+  if ((rc = c->alloc(c->mpred, c->mstride * sizeof(double)))) return rc;
   if ((rc = c->alloc(c->rs_plus, n * sizeof(double)))) return rc;
   if ((rc = c->alloc(c->rs_pw, n * sizeof(double)))) return rc;
   const size_t NE = c->nmax_eig;
@@ -385,15 +400,16 @@ int plan_and_alloc(cakf_ctx* c, const cakf_problem* p) {
   c->eigw_bytes = eig_workspace_bytes((int)NE);
   if ((rc = c->alloc(c->eigw, c->eigw_bytes))) return rc;
   const size_t wsw = std::max(c->cwmax, cwfull);
-  if ((rc = c->alloc(c->WsA, ldn * std::max<size_t>(wsw, 1) * es))) return rc;
-  if ((rc = c->alloc(c->WsB, ldn * std::max<size_t>(wsw, 1) * es))) return rc;
-  if ((rc = c->alloc(c->wsA, ldn * es))) return rc;
-  if ((rc = c->alloc(c->wsB, ldn * es))) return rc;
-  if ((rc = c->alloc(c->KWa, ldn * (wsw + 1) * es))) return rc;
-  if ((rc = c->alloc(c->KWb, ldn * (wsw + 1) * es))) return rc;
+  if ((rc = c->alloc(c->WsA, ldf * std::max<size_t>(wsw, 1) * es))) return rc;
+  if ((rc = c->alloc(c->WsB, ldf * std::max<size_t>(wsw, 1) * es))) return rc;
+  if ((rc = c->alloc(c->wsA, ldf * es))) return rc;
+  if ((rc = c->alloc(c->wsB, ldf * es))) return rc;
+  if ((rc = c->alloc(c->KWa, ldf * (wsw + 1) * es))) return rc;
+  if ((rc = c->alloc(c->KWb, ldf * (wsw + 1) * es))) return rc;
   const size_t wfin = std::max<size_t>(wmax, c->imax + 1);
-  if ((rc = c->alloc(c->Xs, ldn * wfin * es))) return rc;
-  if ((rc = c->alloc(c->Y, ldn * wfin * es))) return rc;
+  if ((rc = c->alloc(c->Xs, ldf * wfin * es))) return rc;
+  if ((rc = c->alloc(c->Y, ldf * wfin * es))) return rc;
+  if (c->dprime == 2 && (rc = c->alloc(c->KX, ldf * wfin * es))) return rc;
   if ((rc = c->alloc(c->Xobs, mm * wfin * es))) return rc;
   if ((rc = c->alloc(c->Fb, mm * std::max<size_t>(NE, 1) * es))) return rc;
   if ((rc = c->alloc(c->Gws, NE * NE * sizeof(double)))) return rc;
@@ -475,7 +491,7 @@ struct Runner {
     return c->seg_c ? (T*)c->PVpool + (size_t)(k % c->seg_c) * c->ldn * (c->imax + 1) : (T*)c->PVpool + c->off_PV[k];
   }
   T* KV(int k) {
-    return c->seg_c ? (T*)c->KVpool + (size_t)(k % c->seg_c) * c->ldn * (c->imax + 1) : (T*)c->KVpool + c->off_PV[k];
+    return c->seg_c ? (T*)c->KVpool + (size_t)(k % c->seg_c) * c->ldn * (c->imax + 1) : (T*)c->KVpool + c->off_KV[k];
   }
   T* Vk(int k) {
     return c->seg_c ? (T*)c->Vpool + (size_t)(k % c->seg_c) * std::max(c->mmax, 1) * (c->imax + 1)
@@ -598,7 +614,8 @@ struct Runner {
     cudaMemsetAsync(c->rfin, 0, (T_ + 1) * sizeof(double), st);
     cudaMemsetAsync(c->dropped_f, 0, (T_ + 1) * sizeof(double), st);
     cudaMemsetAsync(c->Spool, 0, c->off_S[T_ + 1] * sizeof(T), st);
-    // state 0: prior
+    // state 0: prior (the two-block state starts with zero velocities)
+    if (c->dprime == 2) cudaMemsetAsync(c->mf, 0, (size_t)(T_ + 1) * c->mstride * sizeof(double), st);
     if (c->has_mu) cudaMemcpyAsync(c->mf, c->mu, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
     else cudaMemsetAsync(c->mf, 0, n * sizeof(double), st);
     {
@@ -639,22 +656,37 @@ struct Runner {
   // step is re-run from the actions stored by the first pass (replayed from the action pool, no
   // NLL term, no phase timers): the same kernels on the same inputs give the same factors.
   int filter_step(int k, bool recompute, bool* nll_pending) {
-    const int n = c->n, ldn = c->ldn;
-    const double a = c->a, a2 = a * a;
+    const int n = c->n, ldn = c->ldn, ldf = c->ldf;
+    const bool two = c->dprime == 2;
+    const int rows = two ? ldf : n;    // factor rows the products run over
+    const double a = c->a_lazy(), a2 = a * a;
     const int B = std::max(c->budget, c->imax);
     const double bd_tol = (sizeof(T) == 8) ? 1e-12 : 1e-6;
     {
       const int m = mk(k), ic = c->icap[k], rp = c->mcols[k - 1];
-      const double* mprev = c->mf + (size_t)(k - 1) * n;
-      double* mout = c->mf + (size_t)k * n;
+      const double* mprev = c->mf + (size_t)(k - 1) * c->mstride;
+      double* mout = c->mf + (size_t)k * c->mstride;
       double* vout = c->vf + (size_t)k * n;
-      predict_mean(mprev, c->has_mu ? c->mu + (size_t)k * n : nullptr,
-                   c->has_mu ? c->mu + (size_t)(k - 1) * n : nullptr, a, n, c->mpred, st);
+      if (two) {
+        // predict the two-block state: m^- = A m + b, and M^- = (A^t (x) I) M+_{k-1} in place (the
+        // slot of M+_{k-1} holds M^-_k from here on, which is what the smoother reads); the
+        // positions' part of rowsumsq(M^-) enters the variances
+        predict_mean2(mprev, c->has_mu ? c->mu + (size_t)k * n : nullptr,
+                      c->has_mu ? c->mu + (size_t)(k - 1) * n : nullptr, c->At, n, ldn, c->mpred, st);
+        if (rp > 0) {
+          mix2<T>(Mk(k - 1), ldf, Mk(k - 1), ldf, ldn, rp, c->At, st);
+          rowsumsq<T>(Mk(k - 1), ldf, n, rp, 0.0, c->rs_plus, st);
+        }
+      } else {
+        predict_mean(mprev, c->has_mu ? c->mu + (size_t)k * n : nullptr,
+                     c->has_mu ? c->mu + (size_t)(k - 1) * n : nullptr, a, n, c->mpred, st);
+      }
       if (m == 0 || ic == 0) {
         // no data at this step: m = m^-, M = M^- = a M+_{k-1}; no truncation needed (c_k = c_{k-1})
         filter_out<T>(c->mpred, (const T*)nullptr, ldn, -1, c->sf2, a2, c->rs_plus, n, mout, vout, nullptr, st);
-        scale_copy<T>(Mk(k - 1), ldn, n, rp, T(a), Mk(k), ldn, st);
-        if (rp > 0) rowsumsq<T>(Mk(k), ldn, n, rp, 0.0, c->rs_plus, st);
+        if (two) cudaMemcpyAsync(mout + ldn, c->mpred + ldn, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+        scale_copy<T>(Mk(k - 1), ldf, rows, rp, T(a), Mk(k), ldf, st);
+        if (rp > 0 && !two) rowsumsq<T>(Mk(k), ldn, n, rp, 0.0, c->rs_plus, st);
         scale_f64(c->lam, rp, rp, 1, a2, st);   // lam_k = a^2 lam_{k-1}
         return CAKF_OK;
       }
@@ -669,7 +701,7 @@ struct Runner {
       T* GSk = (T*)c->GS;      // G s_j of every iteration (column j), for the NLL
       cudaEvent_t ph0 = ph_begin();
       gather_coords<T>(X(), ob, m, Xo, st);
-      gather_rows<T>(Mk(k - 1), ldn, ob, m, rp, Mo, m, st);
+      gather_rows<T>(Mk(k - 1), ldf, ob, m, rp, Mo, m, st);   // H M^-: the position rows
       cudaMemsetAsync(c->r0sq + k, 0, sizeof(double), st);
       cudaMemsetAsync(c->rfin + k, 0, sizeof(double), st);
       cg_init<T>(c->y + c->obs_ptr[k - 1], c->mpred, ob, m, r, (T*)c->r0v, vcol, c->r0sq + k, st);
@@ -738,13 +770,22 @@ struct Runner {
       // K(X, X_o)[V v] is kept (the smoother propagates K [Ws, ws] from it); P^- [W w] = that minus
       // the low-rank part
       if (int rcg = gram_block(X(), n, Xo, m, V, m, ic + 1, KV(k), ldn)) return rcg;
-      cudaMemcpyAsync(PVk, KV(k), (size_t)ldn * (ic + 1) * sizeof(T), cudaMemcpyDeviceToDevice, st);
+      if (two) {
+        // Sigma H^T [V v] = (P^t_inf[:, 0] (x) K(X, X_o)) [V v]: P^t_inf[1][0] = 0 for the stationary
+        // Matern-3/2 factor, so the velocity rows start at zero
+        cudaMemsetAsync(PVk, 0, (size_t)ldf * (ic + 1) * sizeof(T), st);
+        cudaMemcpy2DAsync(PVk, ldf * sizeof(T), KV(k), ldn * sizeof(T), n * sizeof(T), ic + 1,
+                          cudaMemcpyDeviceToDevice, st);
+      } else {
+        cudaMemcpyAsync(PVk, KV(k), (size_t)ldn * (ic + 1) * sizeof(T), cudaMemcpyDeviceToDevice, st);
+      }
       if (rp > 0) {
         double* t2 = c->small;
         gemm_tn<T>(Mo, m, rp, V, m, ic + 1, m, 1.0, 0.0, t2, rp, c->part64, c->part64_elems, st);
-        gemm_nn<T, double>(n, ic + 1, rp, T(-a2), Mk(k - 1), ldn, t2, rp, T(1), PVk, ldn, st);
+        gemm_nn<T, double>(rows, ic + 1, rp, T(-a2), Mk(k - 1), ldf, t2, rp, T(1), PVk, ldf, st);
       }
-      filter_out<T>(c->mpred, PVk, ldn, ic, c->sf2, a2, c->rs_plus, n, mout, vout, c->rs_pw, st);
+      filter_out<T>(c->mpred, PVk, ldf, ic, c->sf2, a2, c->rs_plus, n, mout, vout, c->rs_pw, st);
+      if (two) add_vec<T>(c->mpred + ldn, PVk + (size_t)ic * ldf + ldn, n, mout + ldn, st);
       ph_end(1, ph1);
       // NLL term from its definition: S^T G S (with the stored G s_j), S^T S and S^T r0, FP64 Cholesky.
       // It reads only this step's actions, G S and r0, so it runs on the side stream while the
@@ -790,7 +831,7 @@ struct Runner {
   // a^2 M_o (M_o^T S) with the Gram x block product (tensor cores in those modes), S^T G S = L L^T
   // and z = L^-1 S^T r0 in FP64, then [V v] = [S L^-T, S L^-T z].  G S is kept for the NLL term.
   int batch_update(int k, int m, int ic, int rp, const C4<T>* Xo, const T* Mo, T* V, T* GSk, bool recompute) {
-    const double a2 = c->a * c->a;
+    const double a2 = c->a_lazy() * c->a_lazy();
     T* S = Sk(k);
     if (!recompute) {
       if (c->policy == CAKF_POLICY_COORDINATE) coord_actions<T>(m, ic, S, st);
@@ -825,16 +866,19 @@ struct Runner {
   }
 
   int truncate_filter(int k, int rp, int ic) {
-    const int n = c->n, ldn = c->ldn;
-    const double a = c->a, a2 = a * a;
+    const int n = c->n, ldn = c->ldn, ldf = c->ldf;
+    const bool two = c->dprime == 2;
+    const int rows = two ? ldf : n;
+    const double a = c->a_lazy(), a2 = a * a;
     T* PVk = PV(k);
     if (c->rank_r <= 0) {
       // M+_k = M_k = (a M+_{k-1}, P^- W_k)
-      scale_copy<T>(Mk(k - 1), ldn, n, rp, T(a), Mk(k), ldn, st);
-      scale_copy<T>(PVk, ldn, n, ic, T(1), Mk(k) + (size_t)rp * ldn, ldn, st);
-      rowsumsq<T>(Mk(k), ldn, n, rp + ic, 0.0, c->rs_plus, st);
+      scale_copy<T>(Mk(k - 1), ldf, rows, rp, T(a), Mk(k), ldf, st);
+      scale_copy<T>(PVk, ldf, rows, ic, T(1), Mk(k) + (size_t)rp * ldf, ldf, st);
+      if (!two) rowsumsq<T>(Mk(k), ldn, n, rp + ic, 0.0, c->rs_plus, st);
       return CAKF_OK;
     }
+    if (two) return truncate_filter2(k, rp, ic);
     const int N = rp + ic;
     const int keep = std::min(c->rank_r, N);
     T* U = (T*)c->UT;
@@ -865,6 +909,35 @@ struct Runner {
     cudaMemcpyAsync(c->lam, c->wv, keep * sizeof(double), cudaMemcpyDeviceToDevice, st);
     cudaMemcpyAsync(c->Upool + c->off_U[k], c->U64, (size_t)N * keep * sizeof(double), cudaMemcpyDeviceToDevice, st);
     rowsumsq<T>(Mk(k), ldn, n, keep, 0.0, c->rs_plus, st);
+    return CAKF_OK;
+  }
+
+  // Truncate for the two-block state: the columns of M^-_k = (A^t (x) I) M+_{k-1} are not
+  // orthogonal, so the whole Gram of M_k = (M^-_k, P^- W_k) is formed over its ldf rows (three
+  // products: M^-T M^-, M^-T P^-W, (P^-W)^T P^-W), eigendecomposed in FP64 and rotated.
+  int truncate_filter2(int k, int rp, int ic) {
+    const int ldf = c->ldf;
+    T* PVk = PV(k);
+    const int N = rp + ic;
+    const int keep = std::min(c->rank_r, N);
+    T* U = (T*)c->UT;
+    double* G = c->gram;
+    cudaMemsetAsync(G, 0, (size_t)N * N * sizeof(double), st);
+    if (rp > 0) {
+      gemm_tn<T>(Mk(k - 1), ldf, rp, Mk(k - 1), ldf, rp, ldf, 1.0, 0.0, G, N, c->part64, c->part64_elems, st);
+      double* Bm = c->small;
+      gemm_tn<T>(Mk(k - 1), ldf, rp, PVk, ldf, ic, ldf, 1.0, 0.0, Bm, rp, c->part64, c->part64_elems, st);
+      put_block_sym(G, N, 0, rp, Bm, rp, rp, ic, 1.0, st);
+    }
+    gemm_tn<T>(PVk, ldf, ic, PVk, ldf, ic, ldf, 1.0, 0.0, G + (size_t)rp * N + rp, N, c->part64, c->part64_elems, st);
+    trace_into(G, N, N, c->dropped_f + k, st);   // discarded mass = trace - kept eigenvalues
+    int rc = eig(G, N, keep);
+    if (rc) return rc;
+    sub_sum(c->wv, keep, c->dropped_f + k, st);
+    if (rp > 0) gemm_nn<T, T>(ldf, keep, rp, T(1), Mk(k - 1), ldf, U, N, T(0), Mk(k), ldf, st);
+    gemm_nn<T, T>(ldf, keep, ic, T(1), PVk, ldf, U + rp, N, rp > 0 ? T(1) : T(0), Mk(k), ldf, st);
+    cudaMemcpyAsync(c->lam, c->wv, keep * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(c->Upool + c->off_U[k], c->U64, (size_t)N * keep * sizeof(double), cudaMemcpyDeviceToDevice, st);
     return CAKF_OK;
   }
 
@@ -902,8 +975,134 @@ struct Runner {
     gemm_nn<T, double>(n, 1, ic, T(-1), KVk, ldn, Z + (size_t)cw * ic, ic, T(1), out, ldn, st);
   }
 
+  // ---------------------------------------------------------------- smoother, two-block state
+  // Alg. 3 for the Matern-3/2 temporal factor.  As in the OU smoother, KW = (I_2 (x) K) [Ws ws] is
+  // carried through the recursion from the filter's K(X, X_o)[V v] blocks, so for X = A^T [Ws ws]
+  //   K X = (A^t^T (x) I) KW   and   Sigma X = (P^t_inf A^t^T (x) I) KW
+  // need no kernel evaluations.  W_k = H^T V_k lives in the position rows.  The Gram of the new
+  // Ws (whose predicted part has no orthogonal columns here) is formed from its ldf rows.
+  int smooth2(double* ms, double* vs) {
+    const int n = c->n, T_ = c->T, ldn = c->ldn, ldf = c->ldf;
+    cudaMemcpyAsync(ms + (size_t)T_ * n, c->mf + (size_t)T_ * c->mstride, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(vs + (size_t)T_ * n, c->vf + (size_t)T_ * n, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    cudaMemsetAsync(c->dropped_s, 0, (T_ + 1) * sizeof(double), st);
+    if (T_ == 0) return CAKF_OK;
+    const double AT[4] = {c->At[0], c->At[2], c->At[1], c->At[3]};   // (A^t)^T, row-major
+    const double PAT[4] = {c->Pt[0] * AT[0] + c->Pt[1] * AT[2], c->Pt[0] * AT[1] + c->Pt[1] * AT[3],
+                           c->Pt[2] * AT[0] + c->Pt[3] * AT[2], c->Pt[2] * AT[1] + c->Pt[3] * AT[3]};
+    T* Ws = (T*)c->WsA;
+    T* Wn = (T*)c->WsB;
+    T* ws = (T*)c->wsA;
+    T* wn = (T*)c->wsB;
+    T* KW = (T*)c->KWa;
+    T* KWn = (T*)c->KWb;
+    T* Xs = (T*)c->Xs;
+    T* Y = (T*)c->Y;
+    T* KX = (T*)c->KX;
+    const size_t es = sizeof(T);
+    int cw = c->icap[T_];
+    cudaMemsetAsync(ws, 0, ldf * es, st);
+    cudaMemsetAsync(KW, 0, (size_t)ldf * (cw + 1) * es, st);
+    if (cw > 0) {
+      const int m = mk(T_);
+      cudaMemsetAsync(Ws, 0, (size_t)ldf * cw * es, st);
+      scatter_add_rows<T>(Vk(T_), m, obs(T_), m, cw, T(1), Ws, ldf, st);
+      scatter_add_rows<T>(Vk(T_) + (size_t)cw * m, m, obs(T_), m, 1, T(1), ws, ldf, st);
+      cudaMemcpy2DAsync(KW, ldf * es, KV(T_), ldn * es, n * es, cw + 1, cudaMemcpyDeviceToDevice, st);
+    }
+    for (int k = T_ - 1; k >= 0; --k) {
+      cudaEvent_t ph3 = ph_begin();
+      // X = A^T [Ws ws];  K X and Y = Sigma X from KW
+      mix2<T>(Ws, ldf, Xs, ldf, ldn, cw, AT, st);
+      mix2<T>(ws, ldf, Xs + (size_t)cw * ldf, ldf, ldn, 1, AT, st);
+      mix2<T>(KW, ldf, KX, ldf, ldn, cw + 1, AT, st);
+      mix2<T>(KW, ldf, Y, ldf, ldn, cw + 1, PAT, st);
+      // Y = P^-_k X = Sigma X - M^-_k (M^-_k^T X)  (the slot of M+_{k-1} holds M^-_k)
+      const int rp = (k >= 1) ? c->mcols[k - 1] : 0;
+      if (rp > 0) {
+        double* t = c->small;
+        gemm_tn<T>(Mk(k - 1), ldf, rp, Xs, ldf, cw + 1, ldf, 1.0, 0.0, t, rp, c->part64, c->part64_elems, st);
+        gemm_nn<T, double>(ldf, cw + 1, rp, T(-1), Mk(k - 1), ldf, t, rp, T(1), Y, ldf, st);
+      }
+      ph_end(3, ph3);
+      cudaEvent_t ph4 = ph_begin();
+      const int ic = (k >= 1) ? c->icap[k] : 0;
+      const int m = (k >= 1) ? mk(k) : 0;
+      double* Z = c->small;                       // ic x (cw + 1)
+      if (ic > 0) {
+        // Z = W_k^T P^- X = V_k^T Y[obs];  Y <- P_k X = Y - (P^- W_k) Z
+        T* Xo = (T*)c->Xobs;
+        gather_rows<T>(Y, ldf, obs(k), m, cw + 1, Xo, m, st);
+        gemm_tn<T>(Vk(k), m, ic, Xo, m, cw + 1, m, 1.0, 0.0, Z, ic, c->part64, c->part64_elems, st);
+        gemm_nn<T, double>(ldf, cw + 1, ic, T(-1), PV(k), ldf, Z, ic, T(1), Y, ldf, st);
+      }
+      smooth_out<T>(c->mf + (size_t)k * c->mstride, c->vf + (size_t)k * n, Y, ldf, cw, n, ms + (size_t)k * n,
+                    vs + (size_t)k * n, st);
+      if (k == 0) break;
+      if (ic == 0) {
+        // no update at k: [Ws ws]_k = A^T [Ws ws]_{k+1}, K [Ws ws]_k = K X
+        cudaMemcpyAsync(wn, Xs + (size_t)cw * ldf, ldf * es, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(Wn, Xs, (size_t)ldf * cw * es, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(KWn, KX, (size_t)ldf * (cw + 1) * es, cudaMemcpyDeviceToDevice, st);
+        std::swap(Ws, Wn); std::swap(ws, wn); std::swap(KW, KWn);
+        ph_end(4, ph4);
+        continue;
+      }
+      T* Vkk = Vk(k);
+      const T* KVk = KV(k);
+      // ws_k = w_k + X[:, cw] - W_k Z[:, cw]
+      cudaMemcpyAsync(wn, Xs + (size_t)cw * ldf, ldf * es, cudaMemcpyDeviceToDevice, st);
+      T* vz = (T*)c->Fb;
+      gemm_nn<T, double>(m, 1, ic, T(1), Vkk, m, Z + (size_t)cw * ic, ic, T(0), vz, m, st);
+      ws_obs<T>(obs(k), m, Vkk + (size_t)ic * m, vz, wn, st);
+      ph_end(4, ph4);
+      cudaEvent_t ph5 = ph_begin();
+      // Ws_full = [W_k, X[:, :cw] - W_k Z[:, :cw]] and K Ws_full = [K W_k, K X[:, :cw] - K W_k Z[:, :cw]],
+      // with K ws_k = K w_k + K X[:, cw] - K W_k Z[:, cw] in column N
+      const int N = ic + cw;
+      cudaMemsetAsync(Wn, 0, (size_t)ldf * N * es, st);
+      scatter_add_rows<T>(Vkk, m, obs(k), m, ic, T(1), Wn, ldf, st);
+      cudaMemsetAsync(KWn, 0, (size_t)ldf * ic * es, st);
+      cudaMemcpy2DAsync(KWn, ldf * es, KVk, ldn * es, n * es, ic, cudaMemcpyDeviceToDevice, st);
+      cudaMemcpyAsync(KWn + (size_t)ic * ldf, KX, (size_t)ldf * (cw + 1) * es, cudaMemcpyDeviceToDevice, st);
+      if (cw > 0) {
+        cudaMemcpyAsync(Wn + (size_t)ic * ldf, Xs, (size_t)ldf * cw * es, cudaMemcpyDeviceToDevice, st);
+        T* F = (T*)c->Fb;
+        gemm_nn<T, double>(m, cw, ic, T(1), Vkk, m, Z, ic, T(0), F, m, st);
+        scatter_add_rows<T>(F, m, obs(k), m, cw, T(-1), Wn + (size_t)ic * ldf, ldf, st);
+      }
+      axpy_block<T>(T(1), KVk + (size_t)ic * ldn, ldn, n, 1, KWn + (size_t)N * ldf, ldf, st);
+      gemm_nn<T, double>(n, cw + 1, ic, T(-1), KVk, ldn, Z, ic, T(1), KWn + (size_t)ic * ldf, ldf, st);
+      if (c->rank_r > 0) {
+        const int keep = std::min(c->rank_r, N);
+        double* G = c->gram;
+        gemm_tn<T>(Wn, ldf, N, Wn, ldf, N, ldf, 1.0, 0.0, G, N, c->part64, c->part64_elems, st);
+        trace_into(G, N, N, c->dropped_s + k, st);
+        int rc = eig(G, N, keep);
+        if (rc) return rc;
+        sub_sum(c->wv, keep, c->dropped_s + k, st);
+        T* U = (T*)c->UT;
+        // Ws = Ws_full U, K Ws = (K Ws_full) U  (into the buffers of step k + 1, no longer needed)
+        gemm_nn<T, T>(ldf, keep, N, T(1), Wn, ldf, U, N, T(0), Ws, ldf, st);
+        gemm_nn<T, T>(ldf, keep, N, T(1), KWn, ldf, U, N, T(0), KW, ldf, st);
+        cudaMemcpyAsync(KW + (size_t)keep * ldf, KWn + (size_t)N * ldf, ldf * es, cudaMemcpyDeviceToDevice, st);
+        cw = keep;
+      } else {
+        std::swap(Ws, Wn);
+        std::swap(KW, KWn);
+        cw = N;
+      }
+      std::swap(ws, wn);
+      ph_end(5, ph5);
+      cudaError_t ce = cudaGetLastError();
+      if (ce != cudaSuccess) return fail(CAKF_ERR_CUDA, std::string("smoother step: ") + cudaGetErrorString(ce));
+    }
+    return CAKF_OK;
+  }
+
   // ---------------------------------------------------------------- smoother (Alg. 3)
   int smooth(double* ms, double* vs) {
+    if (c->dprime == 2) return smooth2(ms, vs);
     const int n = c->n, T_ = c->T, ldn = c->ldn;
     const double a = c->a, a2 = a * a;
     cudaMemcpyAsync(ms + (size_t)T_ * n, c->mf + (size_t)T_ * n, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
@@ -1431,6 +1630,12 @@ int validate(const cakf_problem* p) {
     return fail(CAKF_ERR_ARG, "CAKF_STORE_BF16 needs an FP32-based precision");
   if (p->checkpoint_every < 0) return fail(CAKF_ERR_ARG, "checkpoint_every must be >= 0");
   if (p->policy < CAKF_POLICY_CG || p->policy > CAKF_POLICY_BATCH) return fail(CAKF_ERR_ARG, "unknown policy");
+  if (p->temporal != CAKF_TEMPORAL_OU && p->temporal != CAKF_TEMPORAL_MATERN32)
+    return fail(CAKF_ERR_ARG, "unknown temporal factor");
+  if (p->temporal == CAKF_TEMPORAL_MATERN32 && p->factor_storage != CAKF_STORE_FP32)
+    return fail(CAKF_ERR_ARG, "the Matern-3/2 temporal factor keeps its factors resident (CAKF_STORE_FP32)");
+  if (p->temporal == CAKF_TEMPORAL_MATERN32 && p->freeze_truncation)
+    return fail(CAKF_ERR_ARG, "freeze_truncation is not available with the Matern-3/2 temporal factor");
   if (p->policy == CAKF_POLICY_BATCH && !p->replay_actions)
     return fail(CAKF_ERR_ARG, "CAKF_POLICY_BATCH takes its actions from replay_actions");
   if (p->policy == CAKF_POLICY_COORDINATE && p->replay_actions)
@@ -1478,7 +1683,8 @@ int validate(const cakf_problem* p) {
 bool same_shape(const cakf_ctx* c, const cakf_problem* p) {
   if (c->n != p->n || c->T != p->T || c->budget != p->budget_i || c->rank_r != p->rank_r ||
       c->precision != p->precision || c->has_mu != (p->prior_mean != nullptr) || c->replay != (p->replay_actions != nullptr) ||
-      c->storage != p->factor_storage || c->ckpt_req != p->checkpoint_every || c->policy != p->policy)
+      c->storage != p->factor_storage || c->ckpt_req != p->checkpoint_every || c->policy != p->policy ||
+      c->dprime != (p->temporal == CAKF_TEMPORAL_MATERN32 ? 2 : 1))
     return false;
   for (int k = 0; k <= p->T; ++k)
     if (c->obs_ptr[k] != p->obs_ptr[k]) return false;
@@ -1562,6 +1768,16 @@ int cakf_filter(const cakf_problem* p, cakf_ctx** ctx_inout, double* mean_out, d
   c->n = p->n; c->dim = p->dim; c->kernel = p->kernel; c->T = p->T; c->budget = p->budget_i; c->rank_r = p->rank_r;
   c->precision = p->precision; c->lx = std::exp(p->log_lx); c->lt = std::exp(p->log_lt); c->sf2 = std::exp(p->log_sf2);
   c->sn2 = std::exp(p->log_sn2); c->dt = p->dt; c->a = std::exp(-p->dt / c->lt); c->cg_rtol = p->cg_rtol;
+  c->dprime = p->temporal == CAKF_TEMPORAL_MATERN32 ? 2 : 1;
+  if (c->dprime == 2) {
+    // A^t = expm(F dt) = exp(-lam dt) (I + dt (F + lam I)) (F + lam I is nilpotent),
+    // P^t_inf = diag(1, lam^2), F = [[0, 1], [-lam^2, -2 lam]], lam = sqrt(3) / l_t
+    const double lam = std::sqrt(3.0) / c->lt, e = std::exp(-lam * p->dt), h = p->dt;
+    const double At[4] = {e * (1.0 + lam * h), e * h, -e * lam * lam * h, e * (1.0 - lam * h)};
+    const double Pt[4] = {1.0, 0.0, 0.0, lam * lam};
+    std::memcpy(c->At, At, sizeof(At));
+    std::memcpy(c->Pt, Pt, sizeof(Pt));
+  }
   c->has_mu = p->prior_mean != nullptr;
   c->replay = p->replay_actions != nullptr;
   c->freeze = p->freeze_truncation != 0;
@@ -1608,14 +1824,24 @@ int cakf_filter(const cakf_problem* p, cakf_ctx** ctx_inout, double* mean_out, d
   }
   cudaEventRecord(c->ev1, st);
   if (rc) return rc;
-  check_finite(c->mf, (size_t)(c->T + 1) * n, c->err, st);
+  check_finite(c->mf, (size_t)(c->T + 1) * c->mstride, c->err, st);
   check_finite(c->vf, (size_t)(c->T + 1) * n, c->err, st);
   if ((rc = sync_and_check(c, st, "cakf_filter"))) return rc;
   float ms = 0;
   cudaEventElapsedTime(&ms, c->ev0, c->ev1);
   c->stats.filter_ms = ms;
   if (c->profiling) collect_profile(c);
-  if ((rc = copy_out(mean_out, c->mf, (size_t)(c->T + 1) * n, st))) return rc;
+  if (c->mstride == n) {
+    if ((rc = copy_out(mean_out, c->mf, (size_t)(c->T + 1) * n, st))) return rc;
+  } else if (mean_out) {
+    // the positions of the two-block state means
+    const PtrKind kind = ptr_kind(mean_out);
+    if (kind == kOtherDevice) return fail(CAKF_ERR_ARG, "an output array lives on another device than the current one");
+    cudaError_t ce = cudaMemcpy2DAsync(mean_out, n * sizeof(double), c->mf, c->mstride * sizeof(double),
+                                       n * sizeof(double), c->T + 1,
+                                       kind == kDevice ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
+    if (ce != cudaSuccess) return fail(CAKF_ERR_CUDA, std::string("copy out: ") + cudaGetErrorString(ce));
+  }
   if ((rc = copy_out(var_out, c->vf, (size_t)(c->T + 1) * n, st))) return rc;
   cudaError_t ce = cudaStreamSynchronize(st);
   if (ce != cudaSuccess) return fail(CAKF_ERR_CUDA, cudaGetErrorString(ce));
@@ -1708,6 +1934,7 @@ int cakf_interpolate(cakf_ctx* c, int32_t nq, const double* tq, const double* mu
                      double* smean, double* svar, void* cuda_stream) {
   if (!c) return fail(CAKF_ERR_STATE, "cakf_interpolate: no context (cakf_filter creates it)");
   if (!c->filtered) return fail(CAKF_ERR_STATE, "cakf_interpolate needs a successful cakf_filter on this context");
+  if (c->dprime != 1) return fail(CAKF_ERR_ARG, "cakf_interpolate: Ornstein-Uhlenbeck temporal factor only");
   if (nq < 1 || !tq) return fail(CAKF_ERR_ARG, "cakf_interpolate: nq >= 1 query times are needed");
   if (ptr_kind(tq) != kHost) return fail(CAKF_ERR_ARG, "cakf_interpolate: tq must be a host array");
   if (c->has_mu && !mu_q) return fail(CAKF_ERR_ARG, "cakf_interpolate: the problem has a prior mean, so mu_q is needed");
@@ -1777,6 +2004,7 @@ int cakf_sample(cakf_ctx* c, int32_t n_samples, const double* x0, const double* 
                 double* filter_out, double* smoother_out, void* cuda_stream) {
   if (!c) return fail(CAKF_ERR_STATE, "cakf_sample: no context (cakf_filter creates it)");
   if (!c->filtered) return fail(CAKF_ERR_STATE, "cakf_sample needs a successful cakf_filter on this context");
+  if (c->dprime != 1) return fail(CAKF_ERR_ARG, "cakf_sample: Ornstein-Uhlenbeck temporal factor only");
   if (n_samples < 1 || n_samples > 1024 || !x0 || !q || !eps)
     return fail(CAKF_ERR_ARG, "cakf_sample: 1 <= n_samples <= 1024 and x0, q, eps must be given");
   cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -2051,6 +2279,7 @@ extern "C" int cakf_nll_backward(cakf_ctx* c, double* grad_out) {
   if (!grad_out) return fail(CAKF_ERR_ARG, "cakf_nll_backward: grad_out is NULL");
   if (!c) return fail(CAKF_ERR_STATE, "cakf_nll_backward: no context (cakf_filter creates it)");
   if (!c->filtered) return fail(CAKF_ERR_STATE, "cakf_nll_backward needs a successful cakf_filter on this context");
+  if (c->dprime != 1) return fail(CAKF_ERR_ARG, "cakf_nll_backward: Ornstein-Uhlenbeck temporal factor only");
   cudaStream_t st = nullptr;
   int rc;
   const size_t es = elem_size(c->precision);

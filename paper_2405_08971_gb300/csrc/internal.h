@@ -68,6 +68,14 @@ void predict_mean(const double* mprev, const double* mu_k, const double* mu_km1,
 template <class T>
 void filter_out(const double* mpred, const T* PVv, int ld, int ic, double sf2, double a2, const double* rs_plus, int n,
                 double* mout, double* vout, double* rs_pw, cudaStream_t st);
+// Two-block state of the Matern-3/2 temporal factor (rows [0, half) positions, [half, 2 half)
+// velocities): Out = (C (x) I) In with C row-major 2 x 2 (In == Out allowed); the mean prediction
+// m^- = A (m - (mu_{k-1}, 0)) + (mu_k, 0); out = a + b.
+template <class T>
+void mix2(const T* In, int ldi, T* Out, int ldo, int half, int cols, const double C[4], cudaStream_t st);
+void predict_mean2(const double* mprev, const double* mu_k, const double* mu_km1, const double A[4], int n, int half,
+                   double* mpred, cudaStream_t st);
+template <class T> void add_vec(const double* a, const T* b, int n, double* out, cudaStream_t st);
 template <class T> void scale_copy(const T* In, int ldi, int n, int cols, T alpha, T* Out, int ldo, cudaStream_t st);
 template <class T>
 void smooth_out(const double* mk, const double* vk, const T* Y, int ld, int cw, int n, double* ms, double* vs,

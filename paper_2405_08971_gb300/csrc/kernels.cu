@@ -373,61 +373,101 @@ template <class T> __device__ __forceinline__ double dot_part(const T* __restric
   }
 }
 
+// Sum of the per-block partials part[q * nblk + b] over b for q in [0, nq), in a fixed order, into
+// out[q] (shared memory) -- and, if dots != null, into dots[q] in FP64.  Each warp takes UP_QB values
+// of q at a time so that their loads are in flight together.
+constexpr int UP_QB = 4;
+template <class T>
+__device__ __forceinline__ void sum_partials(const T* __restrict__ part, int nblk, int nq, T* out, double* dots) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int q0 = warp * UP_QB; q0 < nq; q0 += nw * UP_QB) {
+    T acc[UP_QB];
+#pragma unroll
+    for (int u = 0; u < UP_QB; ++u) acc[u] = T(0);
+    for (int b = lane; b < nblk; b += 32)
+#pragma unroll
+      for (int u = 0; u < UP_QB; ++u)
+        if (q0 + u < nq) acc[u] += part[(size_t)(q0 + u) * nblk + b];
+#pragma unroll
+    for (int u = 0; u < UP_QB; ++u) {
+      const T t = warp_sum(acc[u]);
+      if (lane == 0 && q0 + u < nq) {
+        out[q0 + u] = t;
+        if (dots) dots[q0 + u] = double(t);
+      }
+    }
+  }
+}
+
+// Row block of the CG update kernels: UP_ROWS rows, UP_SPLIT threads per row, each summing every
+// UP_SPLIT-th term of a row's sum over the previous directions (the loads of a warp stay coalesced:
+// its 32 threads take 32 consecutive rows of one column).
+constexpr int UP_THREADS = 256, UP_ROWS = 64, UP_SPLIT = UP_THREADS / UP_ROWS;
+
 // First G-orthogonalisation pass of CG iteration j.  The first-pass dots are summed from the
 // combine blocks' partials (FP64, fixed order; block 0 also stores all j + 4 of them in dots1):
 // c = V^T G s, then d = s - V c, G d = g - GV c, parked unnormalised in column j of V and GV.
 // The block then forms its rows' share of the second-pass dots (q < j: V[:, q] . G d; j: d . G d)
 // into dpart2[q * gridDim.x + block].
-constexpr int UP_THREADS = 256;
 template <class T>
 __global__ void __launch_bounds__(UP_THREADS)
 k_cg_upd1(int j, const T* __restrict__ dpart1, int nblk1, double* __restrict__ dots1, T* __restrict__ V,
           T* __restrict__ GV, int ldv, const T* __restrict__ s, const T* __restrict__ g, int m,
           T* __restrict__ dpart2, const int* __restrict__ active) {
   if (!*active) return;
-  __shared__ T c[1024];
-  __shared__ T sd[UP_THREADS], sgd[UP_THREADS];
+  __shared__ T c[1024 + 4];
+  __shared__ T sd[UP_SPLIT][UP_ROWS], sgd[UP_SPLIT][UP_ROWS];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  const int nq = (blockIdx.x == 0) ? j + 4 : j;
-  for (int q = warp; q < nq; q += nw) {
-    T acc = T(0);
-    for (int b = lane; b < nblk1; b += 32) acc += dpart1[(size_t)q * nblk1 + b];
-    acc = warp_sum(acc);
-    if (lane == 0) {
-      if (q < j) c[q] = acc;
-      if (blockIdx.x == 0) dots1[q] = double(acc);
-    }
-  }
+  sum_partials(dpart1, nblk1, (blockIdx.x == 0) ? j + 4 : j, c, blockIdx.x == 0 ? dots1 : nullptr);
   __syncthreads();
-  const int row0 = blockIdx.x * blockDim.x;
-  const int i = row0 + threadIdx.x;
+  const int rl = threadIdx.x % UP_ROWS, sp = threadIdx.x / UP_ROWS;
+  const int row0 = blockIdx.x * UP_ROWS;
+  const int i = row0 + rl;
   T d = T(0), gd = T(0);
   if (i < m) {
-    d = s[i];
-    gd = g[i];
-#pragma unroll 8
-    for (int q = 0; q < j; ++q) {
+#pragma unroll 4
+    for (int q = sp; q < j; q += UP_SPLIT) {
       const T cq = c[q];
       d = fma(-V[(size_t)q * ldv + i], cq, d);
       gd = fma(-GV[(size_t)q * ldv + i], cq, gd);
     }
-    V[(size_t)j * ldv + i] = d;
-    GV[(size_t)j * ldv + i] = gd;
   }
-  sd[threadIdx.x] = d;
-  sgd[threadIdx.x] = gd;
+  sd[sp][rl] = d;
+  sgd[sp][rl] = gd;
   __syncthreads();
-  const int nrow = min((int)blockDim.x, m - row0);
-  for (int q = warp; q <= j; q += nw) {
-    T acc = T(0);
-    if (q < j) {
-      const T* vq = V + (size_t)q * ldv + row0;
-      for (int t = lane; t < nrow; t += 32) acc = fma(vq[t], sgd[t], acc);
-    } else {
-      for (int t = lane; t < nrow; t += 32) acc = fma(sd[t], sgd[t], acc);
+  if (sp == 0) {
+    d = T(0); gd = T(0);
+    if (i < m) {
+      d = s[i];
+      gd = g[i];
+#pragma unroll
+      for (int u = 0; u < UP_SPLIT; ++u) { d += sd[u][rl]; gd += sgd[u][rl]; }
+      V[(size_t)j * ldv + i] = d;
+      GV[(size_t)j * ldv + i] = gd;
     }
-    acc = warp_sum(acc);
-    if (lane == 0) dpart2[(size_t)q * gridDim.x + blockIdx.x] = acc;
+    sd[0][rl] = d;
+    sgd[0][rl] = gd;
+  }
+  __syncthreads();
+  const int nrow = min(UP_ROWS, m - row0);
+  for (int q0 = warp * UP_QB; q0 <= j; q0 += nw * UP_QB) {
+    T acc[UP_QB];
+#pragma unroll
+    for (int u = 0; u < UP_QB; ++u) acc[u] = T(0);
+    for (int t = lane; t < nrow; t += 32) {
+      const T gt = sgd[0][t];
+#pragma unroll
+      for (int u = 0; u < UP_QB; ++u) {
+        const int q = q0 + u;
+        if (q < j) acc[u] = fma(V[(size_t)q * ldv + row0 + t], gt, acc[u]);
+        else if (q == j) acc[u] = fma(sd[0][t], gt, acc[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < UP_QB; ++u) {
+      const T t = warp_sum(acc[u]);
+      if (lane == 0 && q0 + u <= j) dpart2[(size_t)(q0 + u) * gridDim.x + blockIdx.x] = t;
+    }
   }
 }
 
@@ -446,27 +486,18 @@ k_cg_upd2(int j, const double* __restrict__ dots1, const T* __restrict__ dpart2,
           double* __restrict__ eta_out, double* __restrict__ alpha_out, int* __restrict__ count,
           T* __restrict__ Snext) {
   if (!*active) return;
-  __shared__ T c[1024];
-  __shared__ double cd[1025];
+  __shared__ T c[1024 + 4];
   __shared__ double sh[3];
   __shared__ T shc[3];             // 1 / sqrt(eta), alpha / eta, 1 / |s| (formed once, in FP64)
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int q = warp; q <= j; q += nw) {
-    T acc = T(0);
-    for (int b = lane; b < nblk2; b += 32) acc += dpart2[(size_t)q * nblk2 + b];
-    acc = warp_sum(acc);
-    if (lane == 0) {
-      cd[q] = double(acc);
-      if (q < j) c[q] = acc;
-    }
-  }
+  __shared__ T sd[UP_SPLIT][UP_ROWS], sgd[UP_SPLIT][UP_ROWS];
+  sum_partials(dpart2, nblk2, j + 1, c, nullptr);
   __syncthreads();
   double ccp = 0.0;
-  for (int q = threadIdx.x; q < j; q += blockDim.x) ccp = fma(cd[q], cd[q], ccp);
+  for (int q = threadIdx.x; q < j; q += blockDim.x) ccp = fma(double(c[q]), double(c[q]), ccp);
   const double cc = block_sum(ccp);
   if (threadIdx.x == 0) {
     const double sg = dots1[j];
-    const double eta = cd[j] - cc;
+    const double eta = double(c[j]) - cc;
     const double alpha = dots1[j + 1] - dots1[j + 2];
     int stop = !(eta > bd_tol * sg) || !isfinite(eta) || !isfinite(alpha);
     if (use_rtol && dots1[j + 3] <= rtol2_r0sq) stop = 1;
@@ -479,21 +510,31 @@ k_cg_upd2(int j, const double* __restrict__ dots1, const T* __restrict__ dpart2,
   }
   __syncthreads();
   const double eta = sh[0], alpha = sh[1];
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int rl = threadIdx.x % UP_ROWS, sp = threadIdx.x / UP_ROWS;
+  const int i = blockIdx.x * UP_ROWS + rl;
   if (sh[2] != 0.0) {
     // breakdown / converged: this direction is not used; clear the parked column
-    if (i < m) { V[(size_t)j * ldv + i] = T(0); GV[(size_t)j * ldv + i] = T(0); }
+    if (sp == 0 && i < m) { V[(size_t)j * ldv + i] = T(0); GV[(size_t)j * ldv + i] = T(0); }
     if (blockIdx.x == 0 && threadIdx.x == 0) *active = 0;
     return;
   }
+  T d = T(0), gd = T(0);
   if (i < m) {
-    T d = V[(size_t)j * ldv + i], gd = GV[(size_t)j * ldv + i];
-#pragma unroll 8
-    for (int q = 0; q < j; ++q) {
+#pragma unroll 4
+    for (int q = sp; q < j; q += UP_SPLIT) {
       const T cq = c[q];
       d = fma(-V[(size_t)q * ldv + i], cq, d);
       gd = fma(-GV[(size_t)q * ldv + i], cq, gd);
     }
+  }
+  sd[sp][rl] = d;
+  sgd[sp][rl] = gd;
+  __syncthreads();
+  if (sp == 0 && i < m) {
+    d = V[(size_t)j * ldv + i];
+    gd = GV[(size_t)j * ldv + i];
+#pragma unroll
+    for (int u = 0; u < UP_SPLIT; ++u) { d += sd[u][rl]; gd += sgd[u][rl]; }
     const T inv = shc[0];
     const T coef = shc[1];
     V[(size_t)j * ldv + i] = d * inv;
@@ -850,6 +891,39 @@ __global__ void k_predict_mean(const double* __restrict__ mprev, const double* _
   if (i >= n) return;
   double b = mu_k ? (mu_k[i] - a * mu_km1[i]) : 0.0;
   mpred[i] = a * mprev[i] + b;
+}
+
+// Two-block state (Matern-3/2 temporal factor: positions in rows [0, half), velocities in rows
+// [half, 2 half)): Out = (C (x) I) In for a 2 x 2 matrix C = [[c00, c01], [c10, c11]], i.e.
+//   Out[i] = c00 In[i] + c01 In[half + i],  Out[half + i] = c10 In[i] + c11 In[half + i]
+// per column.  In == Out is allowed: each thread reads its pair before writing it.
+template <class T>
+__global__ void k_mix2(const T* In, int ldi, T* Out, int ldo, int half, int cols, T c00, T c01, T c10, T c11) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.y;
+  if (i >= half || c >= cols) return;
+  const T x = In[(size_t)c * ldi + i], v = In[(size_t)c * ldi + half + i];
+  Out[(size_t)c * ldo + i] = fma(c00, x, c01 * v);
+  Out[(size_t)c * ldo + half + i] = fma(c10, x, c11 * v);
+}
+
+// Mean prediction of the two-block state with the prior mean (mu_k, 0) of the positions:
+//   m^- = A (m - (mu_{k-1}, 0)) + (mu_k, 0)   (mu may be null: zero mean)
+__global__ void k_predict_mean2(const double* __restrict__ mprev, const double* __restrict__ mu_k,
+                                const double* __restrict__ mu_km1, double a00, double a01, double a10, double a11,
+                                int n, int half, double* __restrict__ mpred) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double x = mprev[i] - (mu_km1 ? mu_km1[i] : 0.0), v = mprev[half + i];
+  mpred[i] = fma(a00, x, a01 * v) + (mu_k ? mu_k[i] : 0.0);
+  mpred[half + i] = fma(a10, x, a11 * v);
+}
+
+// out[i] = a[i] + b[i] (FP64 plus working precision), i < n
+template <class T>
+__global__ void k_add_vec(const double* __restrict__ a, const T* __restrict__ b, int n, double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = a[i] + double(b[i]);
 }
 
 // Filter outputs of step k:  m_k = m_pred + (P^- w);  var_k = sf2 - a^2 rs_plus - rowsumsq(P^- W)
@@ -1353,22 +1427,22 @@ void cg_combine(const T* part, int nsplit, const T* s, T sn2, const T* Mo, int l
   note_launch();
 }
 size_t cg_dpart_elems(int m, int budget) {
-  return (size_t)(budget + 4) * cdiv(std::max(m, 1), CB_ROWS) + (size_t)(budget + 1) * cdiv(std::max(m, 1), UP_THREADS);
+  return (size_t)(budget + 4) * cdiv(std::max(m, 1), CB_ROWS) + (size_t)(budget + 1) * cdiv(std::max(m, 1), UP_ROWS);
 }
 template <class T>
 void cg_upd1(int j, const T* dpart1, double* dots1, T* V, T* GV, int ldv, const T* s, const T* g, int m,
              T* dpart2, const int* active, cudaStream_t st) {
-  k_cg_upd1<T><<<cdiv(m, UP_THREADS), UP_THREADS, 0, st>>>(j, dpart1, (int)cdiv(m, CB_ROWS), dots1, V, GV, ldv, s, g, m,
-                                                           dpart2, active);
+  k_cg_upd1<T><<<cdiv(m, UP_ROWS), UP_THREADS, 0, st>>>(j, dpart1, (int)cdiv(m, CB_ROWS), dots1, V, GV, ldv, s, g, m,
+                                                        dpart2, active);
   note_launch();
 }
 template <class T>
 void cg_upd2(int j, const double* dots1, const T* dpart2, T* V, T* GV, int ldv, T* r, T* v, T* s, T* Q,
              int m, double bd_tol, double rtol2_r0sq, int use_rtol, int* active, double* eta, double* alpha,
              int* count, T* Snext, cudaStream_t st) {
-  k_cg_upd2<T><<<cdiv(m, UP_THREADS), UP_THREADS, 0, st>>>(j, dots1, dpart2, (int)cdiv(m, UP_THREADS), V, GV, ldv, r, v,
-                                                           s, Q, m, bd_tol, rtol2_r0sq, use_rtol, active, eta, alpha,
-                                                           count, Snext);
+  k_cg_upd2<T><<<cdiv(m, UP_ROWS), UP_THREADS, 0, st>>>(j, dots1, dpart2, (int)cdiv(m, UP_ROWS), V, GV, ldv, r, v,
+                                                        s, Q, m, bd_tol, rtol2_r0sq, use_rtol, active, eta, alpha,
+                                                        count, Snext);
   note_launch();
 }
 template <class T>
@@ -1522,6 +1596,22 @@ void rowsumsq(const T* A, int lda, int n, int cols, double beta, double* rs, cud
 void predict_mean(const double* mprev, const double* mu_k, const double* mu_km1, double a, int n, double* mpred,
                   cudaStream_t st) {
   k_predict_mean<<<cdiv(n, 256), 256, 0, st>>>(mprev, mu_k, mu_km1, a, n, mpred); note_launch();
+}
+template <class T>
+void mix2(const T* In, int ldi, T* Out, int ldo, int half, int cols, const double C[4], cudaStream_t st) {
+  if (half <= 0 || cols <= 0) return;
+  k_mix2<T><<<dim3(cdiv(half, 256), cols), 256, 0, st>>>(In, ldi, Out, ldo, half, cols, T(C[0]), T(C[1]), T(C[2]),
+                                                         T(C[3])); note_launch();
+}
+void predict_mean2(const double* mprev, const double* mu_k, const double* mu_km1, const double A[4], int n, int half,
+                   double* mpred, cudaStream_t st) {
+  k_predict_mean2<<<cdiv(n, 256), 256, 0, st>>>(mprev, mu_k, mu_km1, A[0], A[1], A[2], A[3], n, half, mpred);
+  note_launch();
+}
+template <class T>
+void add_vec(const double* a, const T* b, int n, double* out, cudaStream_t st) {
+  if (n <= 0) return;
+  k_add_vec<T><<<cdiv(n, 256), 256, 0, st>>>(a, b, n, out); note_launch();
 }
 template <class T>
 void filter_out(const double* mpred, const T* PVv, int ld, int ic, double sf2, double a2, const double* rs_plus, int n,
@@ -1896,7 +1986,9 @@ void check_finite(const double* x, size_t n, int* err, cudaStream_t st) {
   template void smooth_out<T>(const double*, const double*, const T*, int, int, int, double*, double*,           \
                               cudaStream_t);                                                                     \
   template void ws_obs<T>(const int*, int, const T*, const T*, T*, cudaStream_t);                                \
-  template void build_x<T>(const T*, int, int, const T*, T, int, T*, int, cudaStream_t);
+  template void build_x<T>(const T*, int, int, const T*, T, int, T*, int, cudaStream_t);                        \
+  template void mix2<T>(const T*, int, T*, int, int, int, const double*, cudaStream_t);                          \
+  template void add_vec<T>(const double*, const T*, int, double*, cudaStream_t);
 
 INST(float)
 INST(double)
