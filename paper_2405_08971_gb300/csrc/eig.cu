@@ -37,26 +37,27 @@ __device__ __forceinline__ double nr_rcp(double x) {
 }
 
 // Per-step exchange without a grid barrier: every word a block publishes for step k carries the
-// step's epoch (k mod 4) in its two lowest mantissa bits, and the consumers poll the words themselves
-// until all carry the epoch they wait for.  A value x travels as the pair (hi, lo): hi is x with its
-// two lowest mantissa bits replaced by the epoch, lo is the exact remainder x - hi (same binade,
-// at most 3 ulp) tagged the same way.  Re-tagging lo moves it by at most 3 ulp(lo) <= 9 * 2^-52 ulp(x),
-// so hi + lo rounds back to x exactly: the exchange is lossless (subnormal x, far below any Gram
-// entry here, could lose its last 2 bits).  Each 8-byte word is written and read as one access, so a
-// reader sees either the old or the new word; the data dependence of the recursion (no block can
-// publish step k + 2 before every block has published step k + 1, which needs step k consumed) makes
-// two buffers enough.
-__device__ __forceinline__ double with_epoch(double x, int ep) {
-  return __longlong_as_double((__double_as_longlong(x) & ~3LL) | (long long)ep);
-}
-__device__ __forceinline__ int epoch_of(double x) { return (int)(__double_as_longlong(x) & 3LL); }
+// step's epoch (k mod 4), and the consumers poll the words themselves until all carry the epoch they
+// wait for.  A value x travels as a pair of 8-byte words: hi is the bit pattern of x with its two
+// lowest bits replaced by the epoch, lo holds those two original bits in bits 0-1 and the epoch in
+// bits 2-3.  The reader accepts the pair when both epochs match and rebuilds x bit for bit from hi
+// and lo with integer operations (no FP64 arithmetic, nothing lost).  Each 8-byte word is written
+// and read as one access, so a reader sees either the old or the new word; the data dependence of
+// the recursion (no block can publish step k + 2 before every block has published step k + 1, which
+// needs step k consumed) makes two buffers enough.
+__device__ __forceinline__ int epoch_hi(long long h) { return (int)(h & 3LL); }
+__device__ __forceinline__ int epoch_lo(long long l) { return (int)((l >> 2) & 3LL); }
 __device__ __forceinline__ void publish_pair(double* p, double x, int ep) {
-  const double hi = with_epoch(x, ep);
-  const double lo = with_epoch(x - hi, ep);
-  asm volatile("st.relaxed.gpu.global.v2.f64 [%0], {%1, %2};" ::"l"(p), "d"(hi), "d"(lo) : "memory");
+  const long long b = __double_as_longlong(x);
+  const long long hi = (b & ~3LL) | (long long)ep;
+  const long long lo = (b & 3LL) | ((long long)ep << 2);
+  asm volatile("st.relaxed.gpu.global.v2.b64 [%0], {%1, %2};" ::"l"(p), "l"(hi), "l"(lo) : "memory");
 }
-__device__ __forceinline__ void ld_pair(const double* p, double& hi, double& lo) {
-  asm volatile("ld.relaxed.gpu.global.v2.f64 {%0, %1}, [%2];" : "=d"(hi), "=d"(lo) : "l"(p) : "memory");
+__device__ __forceinline__ void ld_pair(const double* p, long long& hi, long long& lo) {
+  asm volatile("ld.relaxed.gpu.global.v2.b64 {%0, %1}, [%2];" : "=l"(hi), "=l"(lo) : "l"(p) : "memory");
+}
+__device__ __forceinline__ double pair_value(long long hi, long long lo) {
+  return __longlong_as_double((hi & ~3LL) | (lo & 3LL));
 }
 __device__ __forceinline__ int ld_relaxed_int(const int* p) {
   int v;
@@ -76,8 +77,9 @@ constexpr long long kPollLimit = 4000000LL;
 // p_{k+1} and publish the next pivot column.  Reflector v_k is stored in column k below the
 // subdiagonal (v_k[0] = 1).  Block reductions go through shared memory and one warp (the FP64 pipe
 // is narrow on this GPU, so a shuffle tree in every warp would cost more than the data it sums).
-constexpr int TD_THREADS = 128;
-constexpr int TD_BATCH = 8;     // exchange entries a thread polls with their loads in flight together
+constexpr int TD_THREADS = 160;      // warp 0: reductions and Householder scalars; warps 1-4: columns
+constexpr int TD_MAX_SLOTS = 64;     // owned columns per block
+constexpr int TD_BATCH = 5;     // exchange entries a thread polls with their loads in flight together
 
 // Householder scalars for x (x[0] = alpha, sum of the squares of x[1..] = sigma): H x = beta e_1,
 // H = I - tau v v^T with v[0] = 1 and v[t] = x[t] * scal.
@@ -107,6 +109,7 @@ k_tridiag(double* __restrict__ A, int lda, int N, double* __restrict__ d, double
   double* cols = sm + 4 * N;        // owned columns (full length N), resident for the whole reduction
   __shared__ double red[TD_THREADS];
   __shared__ double bc[4];          // broadcast scalars
+  __shared__ double colS[TD_MAX_SLOTS], colF[TD_MAX_SLOTS];   // owner warps' parts of p_{k+1}
   const int G = gridDim.x, tid = threadIdx.x, TB = blockDim.x;
   const int warp = tid >> 5, lane = tid & 31, nw = TB >> 5;
   const int nslot = (N + G - 1) / G;   // column j lives in block j % G, slot j / G
@@ -185,7 +188,7 @@ k_tridiag(double* __restrict__ A, int lda, int N, double* __restrict__ d, double
     double part = 0.0;
     bool ok = true;
     for (int t0 = tid; t0 < L && ok; t0 += TB * TD_BATCH) {
-      double ph[TD_BATCH], pl[TD_BATCH], ch[TD_BATCH], cl[TD_BATCH];
+      long long ph[TD_BATCH], pl[TD_BATCH], ch[TD_BATCH], cl[TD_BATCH];
       unsigned pend = 0;
 #pragma unroll
       for (int u = 0; u < TD_BATCH; ++u)
@@ -201,8 +204,8 @@ k_tridiag(double* __restrict__ A, int lda, int N, double* __restrict__ d, double
           }
 #pragma unroll
         for (int u = 0; u < TD_BATCH; ++u)
-          if (((pend >> u) & 1u) && epoch_of(ph[u]) == ek && epoch_of(pl[u]) == ek && epoch_of(ch[u]) == ek &&
-              epoch_of(cl[u]) == ek)
+          if (((pend >> u) & 1u) && epoch_hi(ph[u]) == ek && epoch_lo(pl[u]) == ek && epoch_hi(ch[u]) == ek &&
+              epoch_lo(cl[u]) == ek)
             pend &= ~(1u << u);
         if (!pend) break;
         if (++spins > poll_limit) { atomicExch(err, kErrTimeout); ok = false; break; }
@@ -213,7 +216,7 @@ k_tridiag(double* __restrict__ A, int lda, int N, double* __restrict__ d, double
       for (int u = 0; u < TD_BATCH; ++u) {
         const int t = t0 + u * TB;
         if (t < L) {
-          const double pt = ph[u] + pl[u], ct = ch[u] + cl[u];
+          const double pt = pair_value(ph[u], pl[u]), ct = pair_value(ch[u], cl[u]);
           c[t] = ct;
           w[t] = pt;
           part = fma(pt, v[t], part);
@@ -243,12 +246,17 @@ k_tridiag(double* __restrict__ A, int lda, int N, double* __restrict__ d, double
     }
     red[tid] = part;
     __syncthreads();
+    // (3) warp 0 sums sigma and forms the Householder scalars of column k+1 while the owner warps
+    // update their columns, A22 -= v w^T + w v^T (rows k+1..), publish the next pivot column
+    // (column k+2) as it is formed, and sum their parts of p_{k+1} = tau_{k+1} A22 v_{k+1}:
+    // nv[1] + scn * sum_{t >= 2} nv[t] c[t]  (v_{k+1}[0] = 1, v_{k+1}[t-1] = c[t] scn), finished
+    // once scn is known.
     if (warp == 0) {
       const double sigma = warp0_sum(red);
       if (lane == 0) {
         double ta = 0.0, be = 0.0, sc = 0.0;
         if (next) house_scalars(c[1], sigma, ta, be, sc);
-        bc[2] = ta; bc[3] = be; red[0] = sc;
+        bc[2] = ta; bc[3] = be; bc[0] = sc;
         if (blockIdx.x == ob) {
           d[k + 1] = c[0];
           e[k] = bk;
@@ -256,37 +264,51 @@ k_tridiag(double* __restrict__ A, int lda, int N, double* __restrict__ d, double
           if (!next) { e[k + 1] = c[1]; tau[k + 1] = 0.0; }
         }
       }
+    } else {
+      for (int q = warp - 1; q < nslot; q += nw - 1) {
+        const int j = q * G + blockIdx.x;
+        if (j < k + 1 || j >= N) continue;
+        const int tj = j - (k + 1);
+        double* col = cols + (size_t)q * N + k + 1;
+        const double vj = v[tj], wj = w[tj];
+        const bool publish = next && tj == 1;       // column k+2 becomes the next pivot column
+        double a0 = 0.0, a1 = 0.0, first = 0.0;
+        for (int t = lane; t < L; t += 64) {
+          const double nv = fma(-v[t], wj, fma(-w[t], vj, col[t]));
+          col[t] = nv;
+          if (publish && t >= 1) publish_pair(Cn + 2 * (t - 1), nv, (k + 1) & 3);
+          if (t >= 2) a0 = fma(nv, c[t], a0);
+          else if (t == 1) first = nv;
+          const int t2 = t + 32;
+          if (t2 < L) {
+            const double nv2 = fma(-v[t2], wj, fma(-w[t2], vj, col[t2]));
+            col[t2] = nv2;
+            if (publish) publish_pair(Cn + 2 * (t2 - 1), nv2, (k + 1) & 3);
+            a1 = fma(nv2, c[t2], a1);
+          }
+        }
+        const double S = warp_sum(a0 + a1);
+        const double F = warp_sum(first);
+        if (lane == 0) { colS[q] = S; colF[q] = F; }
+        if (k + 3 == N && j == N - 1) {                  // last diagonal entry (written by lane L-1)
+          __syncwarp();
+          if (lane == 0) d[N - 1] = col[L - 1];
+        }
+      }
     }
     __syncthreads();
-    const double tn = bc[2], bn = bc[3], scn = red[0];
-    // (3) v_{k+1}
+    const double tn = bc[2], bn = bc[3], scn = bc[0];
+    // (4) the owners publish their entries of p_{k+1} (lane 0 reads back its own colS, colF);
+    // every thread writes v_{k+1}
+    if (warp > 0 && lane == 0 && next) {
+      for (int q = warp - 1; q < nslot; q += nw - 1) {
+        const int j = q * G + blockIdx.x;
+        if (j < k + 2 || j >= N) continue;
+        publish_pair(Pn + 2 * (j - k - 2), tn * fma(scn, colS[q], colF[q]), (k + 1) & 3);
+      }
+    }
     if (next)
       for (int t = tid; t < L - 1; t += TB) v2[t] = (t == 0) ? 1.0 : c[t + 1] * scn;
-    __syncthreads();
-    // (4) owned columns: A22 -= v w^T + w v^T (rows k+1..), fused dot for p_{k+1}, publish column k+2
-    for (int q = warp; q < nslot; q += nw) {
-      const int j = q * G + blockIdx.x;
-      if (j < k + 1 || j >= N) continue;
-      const int tj = j - (k + 1);
-      double* col = cols + (size_t)q * N + k + 1;
-      const double vj = v[tj], wj = w[tj];
-      const bool publish = next && tj == 1;       // column k+2 becomes the next pivot column
-      double acc = 0.0;
-      for (int t = lane; t < L; t += 32) {
-        const double nv = fma(-v[t], wj, fma(-w[t], vj, col[t]));
-        col[t] = nv;
-        if (next && t >= 1) acc = fma(nv, v2[t - 1], acc);
-        if (publish && t >= 1) publish_pair(Cn + 2 * (t - 1), nv, (k + 1) & 3);
-      }
-      if (next && tj >= 1) {
-        acc = warp_sum(acc);
-        if (lane == 0) publish_pair(Pn + 2 * (tj - 1), tn * acc, (k + 1) & 3);
-      }
-      if (k + 3 == N && j == N - 1) {                  // last diagonal entry (written by lane L-1)
-        __syncwarp();
-        if (lane == 0) d[N - 1] = col[L - 1];
-      }
-    }
     // (5) store the reflector v_k below the subdiagonal of column k (for the back-transformation)
     if (blockIdx.x == ob)
       for (int t = tid; t < L; t += TB) A[(size_t)k * lda + k + 1 + t] = v[t];
@@ -1115,10 +1137,10 @@ int eig_sym_topk(double* A, int lda, int N, int nkeep, double* w, T* U, int ldu,
   W.gcnt = (int*)take(2 * N * sizeof(int));
   W.mergeof = nullptr;
 
-  // exchange buffers of the tridiagonalisation: every byte 0x03, i.e. words with epoch 3, which
-  // no consumer waits for before the buffer has been rewritten
-  cudaMemsetAsync(P, 0x03, 4 * N * sizeof(double), st);
-  cudaMemsetAsync(Cb, 0x03, 4 * N * sizeof(double), st);
+  // exchange buffers of the tridiagonalisation: every byte 0x0f, i.e. pairs whose both words carry
+  // epoch 3, which no consumer waits for before the buffer has been rewritten
+  cudaMemsetAsync(P, 0x0f, 4 * N * sizeof(double), st);
+  cudaMemsetAsync(Cb, 0x0f, 4 * N * sizeof(double), st);
   cudaMemsetAsync(W.Q, 0, (size_t)N * N * sizeof(double), st);
   cudaMemsetAsync(d, 0, 3 * N * sizeof(double), st);
 
@@ -1140,6 +1162,7 @@ int eig_sym_topk(double* A, int lda, int N, int nkeep, double* w, T* U, int ldu,
       G = std::max(1, occ * nsm);     // fewer blocks own more columns each
       if (occ == 0) { cudaGetLastError(); return 1000 + (int)cudaErrorCooperativeLaunchTooLarge; }
     }
+    if ((N + G - 1) / G > TD_MAX_SLOTS) return 1000 + (int)cudaErrorInvalidValue;
     long long poll_limit = wait_limit(kPollLimit);
     void* args[] = {&A, &lda, &N, &d, &e, &tau, &P, &Cb, &err, &poll_limit};
     cudaError_t ce = cudaLaunchCooperativeKernel((void*)k_tridiag, dim3(G), dim3(TD_THREADS), args, smem, st);
