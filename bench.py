@@ -46,6 +46,12 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp16x3", choices=list(DTYPE_NAME))
     ap.add_argument("--config", default="sphere-65k")
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16", "recompute"],
+                    help="factor storage between the filter and the smoother (cakf_problem.factor_storage)")
+    ap.add_argument("--checkpoint-every", type=int, default=0,
+                    help="segment length of the bf16 / recompute storage (0: the library default, 20)")
+    ap.add_argument("--grad", action="store_true",
+                    help="after the timed passes, time one cakf_nll_backward (NLL gradient) on the last filter")
     ap.add_argument("--T", type=int, default=None, help="override the number of time steps")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -229,6 +235,11 @@ def cpu_model():
 
 
 def cpu_cores():
+    # an explicit BLAS / OpenMP thread limit in the environment (e.g. a single-thread timing) wins
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        v = os.environ.get(var)
+        if v and v.isdigit():
+            return min(int(v), os.cpu_count() or int(v))
     try:
         import threadpoolctl
         info = threadpoolctl.threadpool_info()
@@ -313,7 +324,8 @@ def main():
     y = torch.as_tensor(w.y, device=dev)
     mu = None if w.prior_mean is None else torch.as_tensor(w.prior_mean, device=dev)
     prob = ck.make_problem(coords, w.kernel, w.log_lx, w.log_lt, w.log_sf2, w.log_sn2, T, w.dt, w.obs_ptr,
-                           obs_idx, y, w.budget_i, w.rank_r, precision=args.precision, prior_mean=mu)
+                           obs_idx, y, w.budget_i, w.rank_r, precision=args.precision, prior_mean=mu,
+                           factor_storage=args.storage, checkpoint_every=args.checkpoint_every)
     shape = (T + 1, n)
     outs = [torch.empty(shape, dtype=torch.float64, device=dev) for _ in range(4)]
     ctx = ck.Context()
@@ -429,7 +441,7 @@ def main():
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": DTYPE_NAME[args.precision], "data": "synthetic (seeded RFF prior sample; ERA5-shaped grid)",
         "config": {"workload": desc, "n": n, "m_per_step": int(w.obs_ptr[1] - w.obs_ptr[0]), "T": T,
-                   "i": w.budget_i, "r": w.rank_r, "precision": args.precision,
+                   "i": w.budget_i, "r": w.rank_r, "precision": args.precision, "factor_storage": args.storage,
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "l2": "working set larger than L2 (stored factors ~%.0f GB)" % (
                        (n * (w.rank_r + w.budget_i) * T * (8 if args.precision == 'fp64' else 4)) / 1e9)},
@@ -475,6 +487,20 @@ def main():
         d2h = 4 * (T + 1) * n * 8
         line["e2e"] = {"value": ws * T * args.steps / te, "unit": "time steps/s", "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": d2h}
+
+    # ---- NLL gradient on the last filter run (untimed by the steps/s figure; cakf_nll_backward runs on
+    # the legacy default stream, timed with events there)
+    if args.grad:
+        torch.cuda.synchronize(dev)
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        legacy = torch.cuda.default_stream(dev)
+        g0.record(legacy)
+        grad = ck.cakf_nll_backward(ctx)
+        g1.record(legacy)
+        torch.cuda.synchronize(dev)
+        line["grad"] = {"ms": g0.elapsed_time(g1), "value": [float(x) for x in grad],
+                        "wrt": ["log_lx", "log_lt", "log_sf2", "log_sn2"], "nll": ck.cakf_nll(ctx)}
 
     # ---- CPU baseline: the FP64 oracle on a bounded sample (rank 0, N = 1 only)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

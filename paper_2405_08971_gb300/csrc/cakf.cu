@@ -800,11 +800,20 @@ struct Runner {
         double* Gh = SS + (size_t)ic * ic;
         double* yh = Gh + (size_t)ic * ic;
         double* zs = yh + ic;
+        // The term depends on the actions only through their span.  The CG policy evaluates it on
+        // the G-orthonormal directions V_k (same span, with G V_k kept by the iteration): when CG
+        // converges within the budget the late residual actions are numerically dependent, and
+        // S^T G S formed from working-precision G s products is no longer positive definite, while
+        // V^T V and V^T G V stay well conditioned.  Given actions (batch policies) are used as they
+        // are.
+        const bool cg = c->policy == CAKF_POLICY_CG;
+        const T* Sa = cg ? (const T*)V : Sk(k);
+        const T* GSa = cg ? (const T*)GV : GSk;
         const int mode = gemm_mode();
         set_gemm_mode(0);   // own kernels only: the library GEMM handle belongs to the main stream
-        gemm_tn<T>(Sk(k), m, ic, Sk(k), m, ic, m, 1.0, 0.0, SS, ic, c->part_nll, c->part_nll_elems, s2);
-        gemm_tn<T>(Sk(k), m, ic, GSk, m, ic, m, 1.0, 0.0, Gh, ic, c->part_nll, c->part_nll_elems, s2);
-        gemm_tn<T>(Sk(k), m, ic, (const T*)c->r0v, m, 1, m, 1.0, 0.0, yh, ic, c->part_nll, c->part_nll_elems, s2);
+        gemm_tn<T>(Sa, m, ic, Sa, m, ic, m, 1.0, 0.0, SS, ic, c->part_nll, c->part_nll_elems, s2);
+        gemm_tn<T>(Sa, m, ic, GSa, m, ic, m, 1.0, 0.0, Gh, ic, c->part_nll, c->part_nll_elems, s2);
+        gemm_tn<T>(Sa, m, ic, (const T*)c->r0v, m, 1, m, 1.0, 0.0, yh, ic, c->part_nll, c->part_nll_elems, s2);
         set_gemm_mode(mode);
         nll_def(c->count + k, Gh, SS, ic, yh, zs, c->nll + k, c->err, s2);
         if (ph6) {
@@ -1415,7 +1424,8 @@ struct Runner {
   // ---------------------------------------------------------------- NLL gradient (tangent pass)
   // Forward-mode derivatives of the filter with the actions S_k and truncation rotations U_k of the
   // last filter run held fixed, for the four log-hyperparameters at once (p = 0: log l_x,
-  // 1: log l_t, 2: log sf2, 3: log sn2).  Per step, with Gh = S^T G S = R^T R:
+  // 1: log l_t, 2: log sf2, 3: log sn2).  Per step, with S the basis V_k of span(S_k) (below) and
+  // Gh = S^T G S = R^T R:
   //   dGh_p = S^T dK_oo S - sym(...) + dsn2 S^T S,  dyh_p = -S^T dm^-_p[obs],
   //   dNLL_p = 1/2 tr(Gh^-1 dGh_p) + beta^T dyh_p - 1/2 beta^T dGh_p beta,
   //   d(P^-W)_p = dP^-_{:,obs} V - (P^-W) Phi(R^-T dGh_p R^-1),
@@ -1450,7 +1460,12 @@ struct Runner {
       const int* ob = obs(k);
       C4<T>* Xo = (C4<T>*)c->Xo;
       gather_coords<T>(X(), ob, m, Xo, st);
-      T* S = Sk(k);
+      // The derivatives depend on the actions only through span(S_k), so the products below use
+      // the stored G-orthonormal directions V_k as the basis of that span: with B = V_k the
+      // Cholesky factor of B^T G B is R = R_S R_S0^-1 at every theta, and H^T B R^-1 = H^T S_k R_S^-1,
+      // the same W as with S_k itself, while B^T G B stays well conditioned where CG converged
+      // within the budget (the NLL term uses the same basis).
+      T* S = Vk(k);
       T* V = Vk(k);                       // m x (icap + 1): V (ic valid columns), zero columns, v
       T* PVk = PV(k);                     // n x (icap + 1): P^- W, P^- w
       T* Mo = (T*)c->Mo;
@@ -1696,13 +1711,24 @@ bool same_shape(const cakf_ctx* c, const cakf_problem* p) {
 
 double nu_scale(int kernel) { return kernel == 0 ? 1.0 : (kernel == 1 ? std::sqrt(3.0) : std::sqrt(5.0)); }
 
+const char* numeric_error_text(int e) {
+  switch (e) {
+    case kErrNllChol: return "a step's projected Gram S^T G S (or S^T S) is not positive definite in the NLL term";
+    case kErrBatchChol: return "the batch update's projected Gram S^T G S is not positive definite";
+    case kErrSecular: return "a secular equation of the truncation eigensolver did not converge";
+    case kErrNonFinite: return "non-finite value in the outputs";
+    case kErrGradChol: return "a step's projected Gram is not positive definite in the gradient pass";
+    default: return "non-finite value or non-positive-definite action Gram";
+  }
+}
+
 int sync_and_check(cakf_ctx* c, cudaStream_t st, const char* what) {
   cudaError_t ce = cudaStreamSynchronize(st);
   if (ce != cudaSuccess) return fail(CAKF_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(ce));
   int e = 0;
   cudaMemcpy(&e, c->err, sizeof(int), cudaMemcpyDeviceToHost);
   if (e == kErrTimeout) return fail(CAKF_ERR_TIMEOUT, std::string(what) + ": a device-side wait exceeded its limit");
-  if (e != 0) return fail(CAKF_ERR_NUMERIC, std::string(what) + ": non-finite value or non-positive-definite action Gram");
+  if (e != 0) return fail(CAKF_ERR_NUMERIC, std::string(what) + ": " + numeric_error_text(e));
   return CAKF_OK;
 }
 

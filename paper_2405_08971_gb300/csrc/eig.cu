@@ -739,7 +739,7 @@ __global__ void k_dc_secular(const MergeDesc* __restrict__ merges, const int* __
     conv = fabs(nt - tau) <= 2.0 * kEps * fmax(fabs(nt), fabs(tau)) ||
            (thi - tlo) <= 4.0 * kEps * fmax(fabs(tlo), fabs(thi));
     tau = nt;
-    if (it == 199 && !conv && lane == 0) atomicExch(err, kErrNumeric);
+    if (it == 199 && !conv && lane == 0) atomicExch(err, kErrSecular);
   }
   for (int j = lane; j < Kp; j += LANES) delta[j] = (Dk[j] - Dorg) - tau;
   if (lane == 0) W.lamk[lo + i] = Dorg + tau;
@@ -974,15 +974,50 @@ k_backtransform(const double* __restrict__ A, int lda, const double* __restrict_
       Vs[(size_t)a * N + row] = (a < nb && row >= k0 + a + 1) ? A[(size_t)(k0 + a) * lda + row] : 0.0;
     }
     __syncthreads();
-    // Y = V^T Z: RB * CB dots, one warp per dot (round robin)
-    for (int p = warp; p < RB * CB; p += nw) {
-      const int a = p / CB, c = p - a * CB;
-      const double* va = Vs + (size_t)a * N;
-      const double* zc = Z + (size_t)c * N;
-      double acc = 0.0;
-      for (int row = r0 + lane; row < N; row += 32) acc = fma(va[row], zc[row], acc);
-      acc = warp_sum(acc);
-      if (lane == 0) Y[a][c] = acc;
+    // Y = V^T Z: warp w takes reflectors 2w, 2w + 1 for all CB columns, 2 * CB = 8 partial dots
+    // per lane, summed over the warp by a transposing butterfly (each exchange halves the values a
+    // lane holds; 9 adds per lane instead of 5 per dot)
+    {
+      static_assert(RB == 16 && CB == 4, "the butterfly assumes 16 reflectors over 8 warps and 4 columns");
+      const int a0 = 2 * warp;
+      double acc[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc[u] = 0.0;
+      const double* va0 = Vs + (size_t)a0 * N;
+      const double* va1 = va0 + N;
+      for (int row = r0 + lane; row < N; row += 32) {
+        const double x0 = va0[row], x1 = va1[row];
+#pragma unroll
+        for (int c = 0; c < CB; ++c) {
+          const double z = Z[(size_t)c * N + row];
+          acc[c] = fma(x0, z, acc[c]);
+          acc[CB + c] = fma(x1, z, acc[CB + c]);
+        }
+      }
+      const bool b16 = lane & 16, b8 = lane & 8, b4 = lane & 4;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const double send = b16 ? acc[u] : acc[u + 4];
+        const double keep = b16 ? acc[u + 4] : acc[u];
+        acc[u] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const double send = b8 ? acc[u] : acc[u + 2];
+        const double keep = b8 ? acc[u + 2] : acc[u];
+        acc[u] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+      }
+      {
+        const double send = b4 ? acc[0] : acc[1];
+        const double keep = b4 ? acc[1] : acc[0];
+        acc[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+      }
+      acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 2);
+      acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 1);
+      if ((lane & 3) == 0) {
+        const int idx = (b16 ? 4 : 0) + (b8 ? 2 : 0) + (b4 ? 1 : 0);   // = 4 * (a - a0) + c
+        Y[a0 + (idx >> 2)][idx & 3] = acc[0];
+      }
     }
     __syncthreads();
     // Yt = T Y (T upper triangular), then Z -= V Yt

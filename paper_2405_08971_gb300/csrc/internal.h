@@ -141,8 +141,13 @@ void interp_filter(const double* mk, const double* vk, const double* mu_t, const
 int set_last_error(int code, const char* msg);
 
 // Device error-flag values (the flag is an int in device memory, 0 = ok)
-constexpr int kErrNumeric = 1;
+constexpr int kErrNumeric = 1;     // a numeric failure without a more specific code
 constexpr int kErrTimeout = 2;
+constexpr int kErrNllChol = 3;     // S^T G S or S^T S of a step not positive definite (NLL term)
+constexpr int kErrBatchChol = 4;   // the batch update's S^T G S not positive definite
+constexpr int kErrSecular = 5;     // a secular equation of the eigensolver did not converge
+constexpr int kErrNonFinite = 6;   // a non-finite output
+constexpr int kErrGradChol = 7;    // the gradient pass's S^T G S not positive definite
 
 // Switch for the FP32 GEMM launchers (gemm_nn / gemm_tn): 0 or 1 = own SIMT kernels (the plain
 // FP32 path), 2 = own tensor-core kernels with split TF32 operands for the large products (the

@@ -1013,7 +1013,7 @@ __global__ void k_nll_step(const double* __restrict__ eta, const double* __restr
       acc -= log(SS[(size_t)q * ic + q]);
     }
     *nll_k = acc;
-    if (s_bad || !isfinite(acc)) atomicExch(err, 1);
+    if (s_bad || !isfinite(acc)) atomicExch(err, kErrNllChol);
   }
 }
 
@@ -1120,7 +1120,7 @@ __global__ void k_grad_small(int ic, int np, const double* __restrict__ Gh, cons
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0 && bad) atomicExch(err, kErrNumeric);
+  if (threadIdx.x == 0 && bad) atomicExch(err, kErrGradChol);
 }
 
 // out[i, p] = in[idx[i] + p * ld]   (gather rows of a double block into precision T)
@@ -1231,7 +1231,7 @@ __global__ void k_nll_def(const int* __restrict__ count, double* __restrict__ Gh
     }
     const double val = 0.5 * j * 1.8378770664093453 + ld1 + 0.5 * quad - ld2;
     *nll_k = val;
-    if (!ok1 || !ok2 || !isfinite(val)) atomicExch(err, kErrNumeric);
+    if (!ok1 || !ok2 || !isfinite(val)) atomicExch(err, kErrNllChol);
   }
 }
 
@@ -1312,7 +1312,7 @@ k_nll_def_smem(const int* __restrict__ count, const double* __restrict__ Gh, con
     for (int w2 = 0; w2 < nw; ++w2) ldiff += red[w2];
     const double val = 0.5 * j * 1.8378770664093453 + ldiff + 0.5 * quad;
     *nll_k = val;
-    if (bad || !isfinite(val)) atomicExch(err, kErrNumeric);
+    if (bad || !isfinite(val)) atomicExch(err, kErrNllChol);
   }
 }
 
@@ -1334,7 +1334,7 @@ __global__ void k_put_block_sym(double* __restrict__ G, int ld, int row0, int co
 
 __global__ void k_check_finite(const double* __restrict__ x, size_t n, int* __restrict__ err) {
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n && !isfinite(x[i])) atomicExch(err, 1);
+  if (i < n && !isfinite(x[i])) atomicExch(err, kErrNonFinite);
 }
 
 
@@ -1752,7 +1752,7 @@ k_batch_chol(const double* __restrict__ Gh, int i, const double* __restrict__ yh
   }
   for (int e = threadIdx.x; e < i * i; e += blockDim.x) Lout[e] = L[e];
   for (int q = threadIdx.x; q < i; q += blockDim.x) z[q] = zz[q];
-  if (threadIdx.x == 0 && bad) atomicExch(err, kErrNumeric);
+  if (threadIdx.x == 0 && bad) atomicExch(err, kErrBatchChol);
 }
 
 // V = S L^-T (row by row: x L^T = s, forward substitution in FP64) into columns 0..i-1 of Vv, and
