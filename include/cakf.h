@@ -333,6 +333,16 @@ int cakf_factor_gemm(int32_t trans_a, int32_t M, int32_t N, int32_t K, double al
 int cakf_eig_topk(const double* A, int32_t N, int32_t keep, double* w_out, double* U_out, void* cuda_stream);
 
 /*
+ * cakf_eig_topk_mixed -- cakf_eig_topk as the FP32-based precision modes run it inside Truncate
+ * (Sec. 3.2): the tridiagonalisation, divide and conquer and eigenvalues in FP64, the final product
+ * of the Householder reflectors with the tridiagonal's eigenvectors in double-FP32 arithmetic
+ * (pairs of FP32 numbers, about 48 significant bits; roughly 1e-14 relative error in U), because
+ * those modes round U to FP32 right after.  Same arguments, layout, ownership and errors as
+ * cakf_eig_topk.
+ */
+int cakf_eig_topk_mixed(const double* A, int32_t N, int32_t keep, double* w_out, double* U_out, void* cuda_stream);
+
+/*
  * cakf_probe_peaks -- measured throughputs for the roofline denominators of the kernels that are
  * bound neither by HBM nor by the tensor cores (no counterpart in the paper: a measurement aid).
  *   mufu_ops_per_s    special-function results per second of the sqrt.approx + ex2.approx pair

@@ -82,6 +82,8 @@ def lib():
         L.cakf_gram_matmul_noalloc.argtypes = L.cakf_gram_matmul.argtypes
         L.cakf_eig_topk.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, vp]
         L.cakf_eig_topk.restype = C.c_int
+        L.cakf_eig_topk_mixed.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, vp]
+        L.cakf_eig_topk_mixed.restype = C.c_int
         L.cakf_gram_matmul_noalloc.restype = C.c_int
         L.cakf_factor_gemm.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_double, vp, C.c_int32, vp,
                                        C.c_int32, C.c_double, vp, C.c_int32, C.c_int32, vp]
@@ -381,18 +383,22 @@ def cakf_gram_matmul_noalloc(kernel, log_lx, log_sf2, Xr, Xc, B, out, precision=
     return out
 
 
-def cakf_eig_topk(A, keep, stream=None):
+def cakf_eig_topk(A, keep, stream=None, mixed=False):
     """Top `keep` eigenpairs of the symmetric CUDA float64 tensor A (N x N) through the library's
     FP64 eigensolver.  Returns (w, U): w descending (keep,), U with shape (keep, N) (column-major
-    N x keep, i.e. row q of U is the q-th eigenvector)."""
+    N x keep, i.e. row q of U is the q-th eigenvector).  mixed=True calls cakf_eig_topk_mixed (the
+    eigenvector assembly in double-FP32, as the FP32-based modes run it)."""
     import torch
     if A.dtype != torch.float64 or not A.is_cuda:
         raise ValueError("cakf_eig_topk: A must be a CUDA float64 tensor")
     N = A.shape[0]
+    if A.dim() != 2 or A.shape[1] != N or not 1 <= int(keep) <= N:
+        raise ValueError("cakf_eig_topk: A must be square and 1 <= keep <= N")
     Ac = A.t().contiguous()          # column-major copy (A is symmetric: same values)
     w = torch.empty(keep, dtype=torch.float64, device=A.device)
     U = torch.empty((keep, N), dtype=torch.float64, device=A.device)
-    _check(lib().cakf_eig_topk(Ac.data_ptr(), int(N), int(keep), w.data_ptr(), U.data_ptr(), stream))
+    fn = lib().cakf_eig_topk_mixed if mixed else lib().cakf_eig_topk
+    _check(fn(Ac.data_ptr(), int(N), int(keep), w.data_ptr(), U.data_ptr(), _stream_of(stream, A.device)))
     return w, U
 
 

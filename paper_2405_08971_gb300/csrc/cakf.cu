@@ -954,8 +954,9 @@ struct Runner {
   int eig(double* G, int N, int keep) {
     cudaEvent_t e0 = nullptr, e1 = nullptr, mk[2] = {nullptr, nullptr};
     if (c->profiling) { e0 = c->ev(); e1 = c->ev(); mk[0] = c->ev(); mk[1] = c->ev(); cudaEventRecord(e0, st); }
+    // U feeds FP32 products in the FP32-based modes: its final assembly runs in double-FP32 there
     int rc = eig_sym_topk<double>(G, N, N, keep, c->wv, c->U64, N, c->eigw, c->eigw_bytes, c->err, st,
-                                  c->profiling ? mk : nullptr);
+                                  c->profiling ? mk : nullptr, sizeof(T) == 4 ? kAssemblyFF : kAssemblyFP64);
     if (rc) {
       cudaGetLastError();
       std::string why = rc >= 1000 ? cudaGetErrorString((cudaError_t)(rc - 1000)) : std::to_string(rc);
@@ -2271,7 +2272,8 @@ extern "C" int cakf_factor_gemm(int32_t trans_a, int32_t M, int32_t N, int32_t K
   return CAKF_OK;
 }
 
-extern "C" int cakf_eig_topk(const double* A, int32_t N, int32_t keep, double* w_out, double* U_out, void* cuda_stream) {
+static int eig_topk_entry(const double* A, int32_t N, int32_t keep, double* w_out, double* U_out, void* cuda_stream,
+                          int assembly) {
   if (!A || !w_out || !U_out || N < 1 || keep < 1 || keep > N) return fail(CAKF_ERR_ARG, "cakf_eig_topk: invalid arguments");
   if (!is_device_ptr(A) || !is_device_ptr(w_out) || !is_device_ptr(U_out))
     return fail(CAKF_ERR_ARG, "cakf_eig_topk: all arrays must be device arrays of the current device");
@@ -2289,7 +2291,7 @@ extern "C" int cakf_eig_topk(const double* A, int32_t N, int32_t keep, double* w
   }
   cudaMemsetAsync(err, 0, sizeof(int), st);
   cudaMemcpyAsync(Aw, A, (size_t)N * N * sizeof(double), cudaMemcpyDeviceToDevice, st);
-  int rc = eig_sym_topk<double>(Aw, N, N, keep, w_out, U_out, N, work, wb, err, st);
+  int rc = eig_sym_topk<double>(Aw, N, N, keep, w_out, U_out, N, work, wb, err, st, nullptr, assembly);
   cudaError_t ce = cudaStreamSynchronize(st);
   int e = 0;
   if (ce == cudaSuccess) cudaMemcpy(&e, err, sizeof(int), cudaMemcpyDeviceToHost);
@@ -2299,6 +2301,15 @@ extern "C" int cakf_eig_topk(const double* A, int32_t N, int32_t keep, double* w
   if (e == kErrTimeout) return fail(CAKF_ERR_TIMEOUT, "cakf_eig_topk: a device-side wait exceeded its limit");
   if (e) return fail(CAKF_ERR_NUMERIC, "cakf_eig_topk: numeric error");
   return CAKF_OK;
+}
+
+extern "C" int cakf_eig_topk(const double* A, int32_t N, int32_t keep, double* w_out, double* U_out, void* cuda_stream) {
+  return eig_topk_entry(A, N, keep, w_out, U_out, cuda_stream, kAssemblyFP64);
+}
+
+extern "C" int cakf_eig_topk_mixed(const double* A, int32_t N, int32_t keep, double* w_out, double* U_out,
+                                   void* cuda_stream) {
+  return eig_topk_entry(A, N, keep, w_out, U_out, cuda_stream, kAssemblyFF);
 }
 
 extern "C" int cakf_nll_backward(cakf_ctx* c, double* grad_out) {

@@ -22,6 +22,14 @@ __device__ __forceinline__ float approx_exp_neg(float s) {   // exp(-s) via ex2.
   return r;
 }
 
+// ---- programmatic dependent launch.  A kernel started by launch_pdl may become resident while the
+// kernel before it in the stream is still running; pdl_wait() returns once that kernel has completed
+// and its writes are visible, so every such kernel calls it before it touches memory, and then
+// pdl_trigger() so that the next kernel's launch overlaps this one.  (Without the launch attribute
+// both are no-ops.)
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Matern correlation times sf2 of the scaled distance^2 (Rasmussen-Williams forms):
 //   nu=1/2: e^-s,  nu=3/2: (1+s) e^-s,  nu=5/2: (1 + s + s^2/3) e^-s.
 template <int KER> __device__ __forceinline__ float kval(float s2, float sf2) {

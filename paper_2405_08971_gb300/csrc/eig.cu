@@ -902,6 +902,43 @@ k_dc_copy(const MergeDesc* __restrict__ merges, int N, DcWork W) {
   }
 }
 
+// ---- double-FP32 arithmetic (pairs hi + lo of FP32 numbers).  The _rn intrinsics keep the compiler
+// from contracting the error-free transformations into FMAs.
+__device__ __forceinline__ float2 ff_from_double(double x) {
+  const float h = __double2float_rn(x);
+  return make_float2(h, __double2float_rn(x - (double)h));
+}
+// (s, c) <- (s, c) + (s2, c2): two_sum of the leading terms (Knuth), errors into the compensation
+__device__ __forceinline__ void ff_acc_add(float& s, float& c, float s2, float c2) {
+  const float t = __fadd_rn(s, s2);
+  const float bb = __fsub_rn(t, s);
+  const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(s2, bb));
+  s = t;
+  c = __fadd_rn(__fadd_rn(c, c2), e);
+}
+// (s, c) <- (s, c) + a b: the product of the leading parts exactly (its error by FMA), the cross
+// terms into its error, the lo * lo term (2^-48 relative) dropped
+__device__ __forceinline__ void ff_fma_acc(float& s, float& c, float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float pe = __fmaf_rn(a.x, b.x, -p);
+  pe = __fmaf_rn(a.x, b.y, pe);
+  pe = __fmaf_rn(a.y, b.x, pe);
+  ff_acc_add(s, c, p, pe);
+}
+// normalised pair of s + c (two_sum, valid for any magnitudes)
+__device__ __forceinline__ float2 ff_norm(float s, float c) {
+  const float h = __fadd_rn(s, c);
+  const float bb = __fsub_rn(h, s);
+  const float l = __fadd_rn(__fsub_rn(s, __fsub_rn(h, bb)), __fsub_rn(c, bb));
+  return make_float2(h, l);
+}
+// z - (s + c)
+__device__ __forceinline__ float2 ff_sub(float2 z, float s, float c) {
+  float hs = z.x, cs = z.y;
+  ff_acc_add(hs, cs, -s, -c);
+  return ff_norm(hs, cs);
+}
+
 // Back-transformation of the top columns through the reflectors, RB reflectors at a time in the
 // compact WY form: H_k0 H_k0+1 ... H_k0+RB-1 = I - V T V^T (V the RB reflectors, T upper
 // triangular).  A block owns CB output columns; per group it stages V in shared memory once for
@@ -913,7 +950,7 @@ constexpr int CB = 4;
 // The RB (RB - 1) / 2 reflector dots are spread over the warps.
 __global__ void __launch_bounds__(256)
 k_bt_tmat(const double* __restrict__ A, int lda, const double* __restrict__ tau, int N,
-          double* __restrict__ Tm) {
+          double* __restrict__ Tm, float2* __restrict__ Vff, float2* __restrict__ Tff) {
   const int g = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const int nref = N - 2;
   const int k0 = g * RB, nb = min(RB, nref - k0);
@@ -946,6 +983,16 @@ k_bt_tmat(const double* __restrict__ A, int lda, const double* __restrict__ tau,
     __syncthreads();
   }
   for (int e = threadIdx.x; e < RB * RB; e += blockDim.x) Tm[(size_t)g * RB * RB + e] = Ts[e / RB][e % RB];
+  if (Vff) {
+    // the group's reflectors (zero outside their support) and T as double-FP32 pairs, for
+    // k_backtransform_ff: converted once here instead of in every block of the back-transform
+    for (int e = threadIdx.x; e < RB * RB; e += blockDim.x) Tff[(size_t)g * RB * RB + e] = ff_from_double(Ts[e / RB][e % RB]);
+    for (int e = threadIdx.x; e < RB * N; e += blockDim.x) {
+      const int a = e / N, row = e - a * N;
+      const double x = (a < nb && row >= k0 + a + 1) ? A[(size_t)(k0 + a) * lda + row] : 0.0;
+      Vff[((size_t)g * RB + a) * N + row] = ff_from_double(x);
+    }
+  }
 }
 
 // One block per CB output columns (descending eigenvalue order: column c holds Q[:, N-1-c]).
@@ -1045,6 +1092,149 @@ k_backtransform(const double* __restrict__ A, int lda, const double* __restrict_
   if (threadIdx.x < ncol) w[c0 + threadIdx.x] = lam[N - 1 - (c0 + threadIdx.x)];
 }
 
+// The same back-transformation in double-FP32 arithmetic, for callers that round U to FP32: every
+// value is an unevaluated pair hi + lo of FP32 numbers (about 48 significant bits), products are
+// formed exactly by FMA and sums carry their rounding errors in a compensation term (the Dot2 scheme
+// of Ogita, Rump and Oishi), so each dot product is as accurate as if computed in twice FP32's
+// precision.  It runs on the FP32 pipe (64 lanes per SM per clock against FP64's 1.67 FMA), so it
+// is several times faster than the FP64 kernel; its error in U (about 1e-14 relative) stays far
+// below the FP32 rounding that the FP32-based modes apply to U next.  Same grouping as
+// k_backtransform (RB reflectors in compact WY form per group, CB output columns per block); the
+// next group's reflectors are copied into the other half of a double buffer (cp.async) while the
+// current group is applied, and in Z -= V Yt each thread owns rows and updates all CB columns of a
+// row together (CB independent accumulations sharing the V loads).
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(sdst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int PENDING> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(PENDING) : "memory");
+}
+
+__global__ void __launch_bounds__(256)
+k_backtransform_ff(const float2* __restrict__ Vff, const float2* __restrict__ Tff, int N,
+                   const double* __restrict__ Q, const double* __restrict__ lam, int nkeep,
+                   double* __restrict__ w, double* __restrict__ U, int ldu) {
+  extern __shared__ float2 bsf[];
+  // bsf: two buffers of RB x N (the reflectors of a group), then Z
+  float2* Z = bsf + (size_t)2 * RB * N;            // CB x N, the columns being transformed
+  __shared__ float2 Y[RB][CB], Yt[RB][CB];
+  const int c0 = blockIdx.x * CB;
+  const int ncol = min(CB, nkeep - c0);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nref = N - 2, ng = (nref + RB - 1) / RB;
+  // rows [g RB + 1, N) of the RB reflectors of group g into buffer b (the rest of the group's
+  // column range is zero and never read)
+  auto stage = [&](int g, int b) {
+    const int r0 = g * RB + 1, L = N - r0;
+    float2* dst = bsf + (size_t)b * RB * N;
+    for (int e = threadIdx.x; e < RB * L; e += blockDim.x) {
+      const int a = e / L, row = r0 + (e - a * L);
+      cp_async8(dst + (size_t)a * N + row, Vff + ((size_t)g * RB + a) * N + row);
+    }
+    cp_async_commit();
+  };
+  stage(ng - 1, (ng - 1) & 1);
+  for (int e = threadIdx.x; e < CB * N; e += blockDim.x) {
+    const int c = e / N, t = e - c * N;
+    Z[e] = (c < ncol) ? ff_from_double(Q[(size_t)(N - 1 - (c0 + c)) * N + t]) : make_float2(0.f, 0.f);
+  }
+  for (int g = ng - 1; g >= 0; --g) {
+    const int k0 = g * RB, r0 = k0 + 1;
+    const float2* Vs = bsf + (size_t)(g & 1) * RB * N;
+    if (g > 0) {
+      stage(g - 1, (g - 1) & 1);   // its buffer was last read in the previous iteration (synced below)
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    // Y = V^T Z: warp w takes reflectors 2w, 2w + 1 for all CB columns; the 8 (sum, compensation)
+    // pairs of a lane are combined over the warp by a transposing butterfly
+    {
+      static_assert(RB == 16 && CB == 4, "the butterfly assumes 16 reflectors over 8 warps and 4 columns");
+      const int a0 = 2 * warp;
+      float sa[8], ca[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) { sa[u] = 0.f; ca[u] = 0.f; }
+      const float2* va0 = Vs + (size_t)a0 * N;
+      const float2* va1 = va0 + N;
+      for (int row = r0 + lane; row < N; row += 32) {
+        const float2 x0 = va0[row], x1 = va1[row];
+#pragma unroll
+        for (int c = 0; c < CB; ++c) {
+          const float2 z = Z[(size_t)c * N + row];
+          ff_fma_acc(sa[c], ca[c], x0, z);
+          ff_fma_acc(sa[CB + c], ca[CB + c], x1, z);
+        }
+      }
+      const bool b16 = lane & 16, b8 = lane & 8, b4 = lane & 4;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float ss = b16 ? sa[u] : sa[u + 4], cs = b16 ? ca[u] : ca[u + 4];
+        const float sk = b16 ? sa[u + 4] : sa[u], ck = b16 ? ca[u + 4] : ca[u];
+        sa[u] = sk; ca[u] = ck;
+        ff_acc_add(sa[u], ca[u], __shfl_xor_sync(0xffffffffu, ss, 16), __shfl_xor_sync(0xffffffffu, cs, 16));
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const float ss = b8 ? sa[u] : sa[u + 2], cs = b8 ? ca[u] : ca[u + 2];
+        const float sk = b8 ? sa[u + 2] : sa[u], ck = b8 ? ca[u + 2] : ca[u];
+        sa[u] = sk; ca[u] = ck;
+        ff_acc_add(sa[u], ca[u], __shfl_xor_sync(0xffffffffu, ss, 8), __shfl_xor_sync(0xffffffffu, cs, 8));
+      }
+      {
+        const float ss = b4 ? sa[0] : sa[1], cs = b4 ? ca[0] : ca[1];
+        const float sk = b4 ? sa[1] : sa[0], ck = b4 ? ca[1] : ca[0];
+        sa[0] = sk; ca[0] = ck;
+        ff_acc_add(sa[0], ca[0], __shfl_xor_sync(0xffffffffu, ss, 4), __shfl_xor_sync(0xffffffffu, cs, 4));
+      }
+      ff_acc_add(sa[0], ca[0], __shfl_xor_sync(0xffffffffu, sa[0], 2), __shfl_xor_sync(0xffffffffu, ca[0], 2));
+      ff_acc_add(sa[0], ca[0], __shfl_xor_sync(0xffffffffu, sa[0], 1), __shfl_xor_sync(0xffffffffu, ca[0], 1));
+      if ((lane & 3) == 0) {
+        const int idx = (b16 ? 4 : 0) + (b8 ? 2 : 0) + (b4 ? 1 : 0);   // = 4 * (a - a0) + c
+        Y[a0 + (idx >> 2)][idx & 3] = ff_norm(sa[0], ca[0]);
+      }
+    }
+    __syncthreads();
+    // Yt = T Y (T upper triangular), then Z -= V Yt
+    if (threadIdx.x < RB * CB) {
+      const int i = threadIdx.x / CB, c = threadIdx.x - i * CB;
+      const float2* Tg = Tff + (size_t)g * RB * RB + i * RB;
+      float sacc = 0.f, cacc = 0.f;
+      for (int j = i; j < RB; ++j) ff_fma_acc(sacc, cacc, Tg[j], Y[j][c]);
+      Yt[i][c] = ff_norm(sacc, cacc);
+    }
+    __syncthreads();
+    for (int row = r0 + threadIdx.x; row < N; row += blockDim.x) {
+      float sacc[CB], cacc[CB];
+#pragma unroll
+      for (int c = 0; c < CB; ++c) { sacc[c] = 0.f; cacc[c] = 0.f; }
+#pragma unroll
+      for (int a = 0; a < RB; ++a) {
+        const float2 v = Vs[(size_t)a * N + row];
+#pragma unroll
+        for (int c = 0; c < CB; ++c) ff_fma_acc(sacc[c], cacc[c], v, Yt[a][c]);
+      }
+#pragma unroll
+      for (int c = 0; c < CB; ++c) {
+        float2& z = Z[(size_t)c * N + row];
+        z = ff_sub(z, sacc[c], cacc[c]);
+      }
+    }
+    __syncthreads();   // every thread is done with Vs before it is refilled two groups later
+  }
+  for (int e = threadIdx.x; e < ncol * N; e += blockDim.x) {
+    const int c = e / N, t = e - c * N;
+    const float2 z = Z[e];
+    U[(size_t)(c0 + c) * ldu + t] = (double)z.x + (double)z.y;   // exact: 48 bits fit in FP64
+  }
+  if (threadIdx.x < ncol) w[c0 + threadIdx.x] = lam[N - 1 - (c0 + threadIdx.x)];
+}
+
 // ------------------------------------------------------------------------------------ host side
 struct Plan {
   std::vector<MergeDesc> merges;      // all levels, deepest first
@@ -1127,6 +1317,8 @@ size_t eig_workspace_bytes(int nmax) {
   b += 10 * align_up(N * sizeof(double));         // lam, lamk, lamtmp, Dw, Zw, Dk, Zk, Dd, rho, spare
   b += align_up(4 * N * sizeof(double));          // rot
   b += align_up((N / RB + 2) * RB * RB * sizeof(double));   // back-transform T blocks
+  b += align_up((N / RB + 2) * RB * RB * sizeof(float2));   // T blocks as double-FP32 pairs
+  b += align_up((N / RB + 2) * RB * N * sizeof(float2));    // reflector groups as double-FP32 pairs
   b += 7 * align_up(N * sizeof(int));             // colk, cold, perm, Kp, nrot, gperm, spare
   b += align_up(2 * N * sizeof(int));             // gcnt
   return b + 4096;
@@ -1134,7 +1326,7 @@ size_t eig_workspace_bytes(int nmax) {
 
 template <class T>
 int eig_sym_topk(double* A, int lda, int N, int nkeep, double* w, T* U, int ldu, void* work, size_t work_bytes,
-                 int* err, cudaStream_t st, cudaEvent_t* marks) {
+                 int* err, cudaStream_t st, cudaEvent_t* marks, int assembly) {
   if (N <= 0 || nkeep <= 0) return 0;
   if (nkeep > N) nkeep = N;
   if (work_bytes < eig_workspace_bytes(N)) return 1;
@@ -1163,6 +1355,8 @@ int eig_sym_topk(double* A, int lda, int N, int nkeep, double* w, T* U, int ldu,
   W.z2 = (double*)take(N * sizeof(double));
   W.rot = (double*)take(4 * N * sizeof(double));
   W.Tm = (double*)take(((size_t)N / RB + 2) * RB * RB * sizeof(double));
+  float2* Tff = (float2*)take(((size_t)N / RB + 2) * RB * RB * sizeof(float2));
+  float2* Vff = (float2*)take(((size_t)N / RB + 2) * RB * (size_t)N * sizeof(float2));
   W.colk = (int*)take(N * sizeof(int));
   W.cold = (int*)take(N * sizeof(int));
   W.perm = (int*)take(N * sizeof(int));
@@ -1238,8 +1432,18 @@ int eig_sym_topk(double* A, int lda, int N, int nkeep, double* w, T* U, int ldu,
   // 3. back-transformation of the top nkeep columns (descending eigenvalues)
   {
     const int ng = std::max(1, (N - 2 + RB - 1) / RB);
+    if constexpr (sizeof(T) == sizeof(double)) {
+      // (larger orders than the double-buffered staging fits in shared memory take the FP64 kernel)
+      if (assembly == kAssemblyFF && N >= 3 && (size_t)(2 * RB + CB) * N * sizeof(float2) <= 227 * 1024) {
+        k_bt_tmat<<<ng, 256, 0, st>>>(A, lda, tau, N, W.Tm, Vff, Tff); note_launch();
+        const size_t smem = (size_t)(2 * RB + CB) * N * sizeof(float2);
+        if (smem > 40 * 1024) cudaFuncSetAttribute(k_backtransform_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_backtransform_ff<<<(nkeep + CB - 1) / CB, 256, smem, st>>>(Vff, Tff, N, W.Q, W.lam, nkeep, w, U, ldu); note_launch();
+        return cudaGetLastError() == cudaSuccess ? 0 : 4;
+      }
+    }
     if (N >= 3) {
-      k_bt_tmat<<<ng, 256, 0, st>>>(A, lda, tau, N, W.Tm); note_launch();
+      k_bt_tmat<<<ng, 256, 0, st>>>(A, lda, tau, N, W.Tm, nullptr, nullptr); note_launch();
     }
     const size_t smem = (size_t)(RB + CB) * N * sizeof(double);
     if (smem > 40 * 1024) cudaFuncSetAttribute(k_backtransform<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1249,8 +1453,8 @@ int eig_sym_topk(double* A, int lda, int N, int nkeep, double* w, T* U, int ldu,
 }
 
 template int eig_sym_topk<float>(double*, int, int, int, double*, float*, int, void*, size_t, int*, cudaStream_t,
-                                  cudaEvent_t*);
+                                  cudaEvent_t*, int);
 template int eig_sym_topk<double>(double*, int, int, int, double*, double*, int, void*, size_t, int*, cudaStream_t,
-                                   cudaEvent_t*);
+                                   cudaEvent_t*, int);
 
 }  // namespace cakf

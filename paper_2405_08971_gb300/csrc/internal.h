@@ -12,6 +12,26 @@ namespace cakf {
 long long launch_count();
 void note_launch(long long k = 1);
 
+// Launch of a kernel that begins with pdl_wait(); pdl_trigger(); with programmatic stream
+// serialisation, so that its launch overlaps the previous kernel in the stream (the chains of short
+// dependent kernels of the CG loop and the eigensolver).  Counts the launch.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  note_launch();
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 template <class T> void prep_coords(const double* X, int n, int dim, double scale, C4<T>* out, cudaStream_t st);
 template <class T> void gather_coords(const C4<T>* X, const int* idx, int m, C4<T>* out, cudaStream_t st);
 template <class T>
@@ -168,9 +188,14 @@ size_t eig_workspace_bytes(int nmax);
 // overwritten).  w: nkeep eigenvalues, descending (device).  U: N x nkeep eigenvectors
 // (column-major, ld = ldu) in precision T.  err: device flag raised on timeout / non-finite.
 // marks: NULL, or two events recorded after the tridiagonalisation and after divide & conquer.
+// assembly: kAssemblyFP64, or kAssemblyFF for callers that round U to FP32 -- the final product of
+// the Householder reflectors with the tridiagonal's eigenvectors then runs in double-FP32
+// arithmetic (about 1e-14 relative in U) on the FP32 pipe; the tridiagonalisation, the divide and
+// conquer and the eigenvalues stay FP64.  (T = double only.)
+constexpr int kAssemblyFP64 = 0, kAssemblyFF = 1;
 template <class T>
 int eig_sym_topk(double* A, int lda, int N, int nkeep, double* w, T* U, int ldu, void* work, size_t work_bytes,
-                 int* err, cudaStream_t st, cudaEvent_t* marks = nullptr);
+                 int* err, cudaStream_t st, cudaEvent_t* marks = nullptr, int assembly = kAssemblyFP64);
 
 // ---- tensor-core Gram x block (gram_tc.cu) ----
 // Out[nr x width] (FP32, column-major, ld = ldo) = sf2 K(Xr, Xc) B with B packed by gram_tc_pack_b.

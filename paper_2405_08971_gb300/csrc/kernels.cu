@@ -70,6 +70,8 @@ __global__ void __launch_bounds__(MVS_W * 32)
 k_gram_matvec(const C4<T>* __restrict__ Xo, const T* __restrict__ s, int m, int nb, T sf2, T* __restrict__ part,
               const T* __restrict__ Mo, int ldm, int rp, int ngv, T* __restrict__ tpart,
               const int* __restrict__ active) {
+  pdl_wait();
+  pdl_trigger();
   if (active && !*active) return;
   __shared__ C4<T> xs[MVS_T];
   __shared__ T ss[MVS_T];
@@ -165,6 +167,8 @@ __global__ void __launch_bounds__(MVS_W * 32)
 k_gram_matvec_f2(const C4<float>* __restrict__ Xo, const float* __restrict__ s, int m, int nb, float sf2,
                  float* __restrict__ part, const float* __restrict__ Mo, int ldm, int rp, int ngv,
                  float* __restrict__ tpart, const int* __restrict__ active) {
+  pdl_wait();
+  pdl_trigger();
   if (active && !*active) return;
   __shared__ uint64_t xs2[MVS_T][4];
   __shared__ float racc[MVS_W][MVS_T];
@@ -283,14 +287,27 @@ k_cg_combine(const T* __restrict__ part, int nsplit, const T* __restrict__ s, T 
              const T* __restrict__ Mo, int ldm, int r, const T* __restrict__ tpart, int tz, T a2,
              int m, T* __restrict__ g, const T* __restrict__ V, int ldv, int j, const T* __restrict__ r0,
              const T* __restrict__ v, T* __restrict__ dpart, const int* __restrict__ active) {
+  pdl_wait();
+  pdl_trigger();
   if (!*active) return;
   extern __shared__ unsigned char sm_raw[];
   T* t = reinterpret_cast<T*>(sm_raw);                 // r coefficients
   __shared__ T red[CB_WARPS][CB_ROWS], redk[CB_WARPS][CB_ROWS];
   __shared__ T gsh[CB_ROWS];
+  // Every loop below loads a batch of independent values before it uses any of them, so a thread
+  // waits for one L2 round trip per batch rather than one per value (the summation order is the
+  // same as one value at a time).
   for (int l = threadIdx.x; l < r; l += blockDim.x) {
     T acc = T(0);
-    for (int z = 0; z < tz; ++z) acc += tpart[(size_t)z * r + l];
+    int z = 0;
+    for (; z + 8 <= tz; z += 8) {
+      T x[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) x[u] = tpart[(size_t)(z + u) * r + l];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc += x[u];
+    }
+    for (; z < tz; ++z) acc += tpart[(size_t)z * r + l];
     t[l] = acc;
   }
   __syncthreads();
@@ -302,6 +319,18 @@ k_cg_combine(const T* __restrict__ part, int nsplit, const T* __restrict__ s, T 
   for (int u = 0; u < CB_UNROLL; ++u) acc[u] = T(0);
   if (valid) {
     int l = warp;
+    constexpr int CB_BATCH = 4;   // groups of CB_UNROLL columns loaded together
+    for (; l + (CB_BATCH * CB_UNROLL - 1) * CB_WARPS < r; l += CB_BATCH * CB_UNROLL * CB_WARPS) {
+      T x[CB_BATCH][CB_UNROLL];
+#pragma unroll
+      for (int b = 0; b < CB_BATCH; ++b)
+#pragma unroll
+        for (int u = 0; u < CB_UNROLL; ++u) x[b][u] = Mo[(size_t)(l + (b * CB_UNROLL + u) * CB_WARPS) * ldm + i];
+#pragma unroll
+      for (int b = 0; b < CB_BATCH; ++b)
+#pragma unroll
+        for (int u = 0; u < CB_UNROLL; ++u) acc[u] = fma(x[b][u], t[l + (b * CB_UNROLL + u) * CB_WARPS], acc[u]);
+    }
     for (; l + (CB_UNROLL - 1) * CB_WARPS < r; l += CB_UNROLL * CB_WARPS) {
 #pragma unroll
       for (int u = 0; u < CB_UNROLL; ++u) {
@@ -317,8 +346,17 @@ k_cg_combine(const T* __restrict__ part, int nsplit, const T* __restrict__ s, T 
   red[warp][lane] = lr;
   // the Gram partials: warp w sums slots w, w + CB_WARPS, ...
   T kw = T(0);
-  if (valid)
-    for (int p = warp; p < nsplit; p += CB_WARPS) kw += part[(size_t)p * m + i];
+  if (valid) {
+    int p = warp;
+    for (; p + 7 * CB_WARPS < nsplit; p += 8 * CB_WARPS) {
+      T x[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) x[u] = part[(size_t)(p + u * CB_WARPS) * m + i];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) kw += x[u];
+    }
+    for (; p < nsplit; p += CB_WARPS) kw += part[(size_t)p * m + i];
+  }
   redk[warp][lane] = kw;
   __syncthreads();
   if (warp == 0) {
@@ -336,17 +374,29 @@ k_cg_combine(const T* __restrict__ part, int nsplit, const T* __restrict__ s, T 
   __syncthreads();
   const T gi = gsh[lane];
   const T si = valid ? s[i] : T(0);
-  for (int q = warp; q < j + 4; q += CB_WARPS) {
-    T pr = T(0);
-    if (valid) {
-      if (q < j) pr = V[(size_t)q * ldv + i] * gi;
-      else if (q == j) pr = si * gi;
-      else if (q == j + 1) pr = si * r0[i];
-      else if (q == j + 2) pr = gi * v[i];
-      else pr = si * si;
+  constexpr int CB_QB = 8;   // dots per warp whose loads are in flight together
+  for (int q0 = warp; q0 < j + 4; q0 += CB_QB * CB_WARPS) {
+    T pr[CB_QB];
+#pragma unroll
+    for (int u = 0; u < CB_QB; ++u) {
+      const int q = q0 + u * CB_WARPS;
+      T x = T(0);
+      if (valid && q < j + 4) {
+        if (q < j) x = V[(size_t)q * ldv + i] * gi;
+        else if (q == j) x = si * gi;
+        else if (q == j + 1) x = si * r0[i];
+        else if (q == j + 2) x = gi * v[i];
+        else x = si * si;
+      }
+      pr[u] = x;
     }
-    pr = warp_sum(pr);
-    if (lane == 0) dpart[(size_t)q * gridDim.x + blockIdx.x] = pr;
+#pragma unroll
+    for (int u = 0; u < CB_QB; ++u) {
+      const int q = q0 + u * CB_WARPS;
+      if (q >= j + 4) break;   // uniform across the warp
+      const T tot = warp_sum(pr[u]);
+      if (lane == 0) dpart[(size_t)q * gridDim.x + blockIdx.x] = tot;
+    }
   }
 }
 
@@ -380,14 +430,26 @@ constexpr int UP_QB = 4;
 template <class T>
 __device__ __forceinline__ void sum_partials(const T* __restrict__ part, int nblk, int nq, T* out, double* dots) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  constexpr int BB = 8;   // partials per lane and value whose loads are in flight together
   for (int q0 = warp * UP_QB; q0 < nq; q0 += nw * UP_QB) {
     T acc[UP_QB];
 #pragma unroll
     for (int u = 0; u < UP_QB; ++u) acc[u] = T(0);
-    for (int b = lane; b < nblk; b += 32)
+    for (int b0 = lane; b0 < nblk; b0 += 32 * BB) {
+      T x[UP_QB][BB];
 #pragma unroll
       for (int u = 0; u < UP_QB; ++u)
-        if (q0 + u < nq) acc[u] += part[(size_t)(q0 + u) * nblk + b];
+#pragma unroll
+        for (int e = 0; e < BB; ++e) {
+          const int b = b0 + 32 * e;
+          x[u][e] = (q0 + u < nq && b < nblk) ? part[(size_t)(q0 + u) * nblk + b] : T(0);
+        }
+#pragma unroll
+      for (int u = 0; u < UP_QB; ++u)
+#pragma unroll
+        for (int e = 0; e < BB; ++e)
+          if (b0 + 32 * e < nblk) acc[u] += x[u][e];
+    }
 #pragma unroll
     for (int u = 0; u < UP_QB; ++u) {
       const T t = warp_sum(acc[u]);
@@ -403,6 +465,8 @@ __device__ __forceinline__ void sum_partials(const T* __restrict__ part, int nbl
 // UP_SPLIT-th term of a row's sum over the previous directions (the loads of a warp stay coalesced:
 // its 32 threads take 32 consecutive rows of one column).
 constexpr int UP_THREADS = 256, UP_ROWS = 64, UP_SPLIT = UP_THREADS / UP_ROWS;
+static_assert(UP_ROWS % 32 == 0, "rows per lane");
+constexpr int UP_VB = 8;   // previous directions per thread whose V, GV loads are in flight together
 
 // First G-orthogonalisation pass of CG iteration j.  The first-pass dots are summed from the
 // combine blocks' partials (FP64, fixed order; block 0 also stores all j + 4 of them in dots1):
@@ -414,6 +478,8 @@ __global__ void __launch_bounds__(UP_THREADS)
 k_cg_upd1(int j, const T* __restrict__ dpart1, int nblk1, double* __restrict__ dots1, T* __restrict__ V,
           T* __restrict__ GV, int ldv, const T* __restrict__ s, const T* __restrict__ g, int m,
           T* __restrict__ dpart2, const int* __restrict__ active) {
+  pdl_wait();
+  pdl_trigger();
   if (!*active) return;
   __shared__ T c[1024 + 4];
   __shared__ T sd[UP_SPLIT][UP_ROWS], sgd[UP_SPLIT][UP_ROWS];
@@ -425,11 +491,23 @@ k_cg_upd1(int j, const T* __restrict__ dpart1, int nblk1, double* __restrict__ d
   const int i = row0 + rl;
   T d = T(0), gd = T(0);
   if (i < m) {
-#pragma unroll 4
-    for (int q = sp; q < j; q += UP_SPLIT) {
-      const T cq = c[q];
-      d = fma(-V[(size_t)q * ldv + i], cq, d);
-      gd = fma(-GV[(size_t)q * ldv + i], cq, gd);
+    for (int q0 = sp; q0 < j; q0 += UP_SPLIT * UP_VB) {
+      T xv[UP_VB], xg[UP_VB];
+#pragma unroll
+      for (int e = 0; e < UP_VB; ++e) {
+        const int q = q0 + UP_SPLIT * e;
+        xv[e] = q < j ? V[(size_t)q * ldv + i] : T(0);
+        xg[e] = q < j ? GV[(size_t)q * ldv + i] : T(0);
+      }
+#pragma unroll
+      for (int e = 0; e < UP_VB; ++e) {
+        const int q = q0 + UP_SPLIT * e;
+        if (q < j) {
+          const T cq = c[q];
+          d = fma(-xv[e], cq, d);
+          gd = fma(-xg[e], cq, gd);
+        }
+      }
     }
   }
   sd[sp][rl] = d;
@@ -450,16 +528,28 @@ k_cg_upd1(int j, const T* __restrict__ dpart1, int nblk1, double* __restrict__ d
   }
   __syncthreads();
   const int nrow = min(UP_ROWS, m - row0);
+  constexpr int RT = UP_ROWS / 32;   // rows per lane
   for (int q0 = warp * UP_QB; q0 <= j; q0 += nw * UP_QB) {
     T acc[UP_QB];
 #pragma unroll
     for (int u = 0; u < UP_QB; ++u) acc[u] = T(0);
-    for (int t = lane; t < nrow; t += 32) {
+    T x[UP_QB][RT];
+#pragma unroll
+    for (int u = 0; u < UP_QB; ++u)
+#pragma unroll
+      for (int e = 0; e < RT; ++e) {
+        const int t = lane + 32 * e, q = q0 + u;
+        x[u][e] = (t < nrow && q < j) ? V[(size_t)q * ldv + row0 + t] : T(0);
+      }
+#pragma unroll
+    for (int e = 0; e < RT; ++e) {
+      const int t = lane + 32 * e;
+      if (t >= nrow) continue;
       const T gt = sgd[0][t];
 #pragma unroll
       for (int u = 0; u < UP_QB; ++u) {
         const int q = q0 + u;
-        if (q < j) acc[u] = fma(V[(size_t)q * ldv + row0 + t], gt, acc[u]);
+        if (q < j) acc[u] = fma(x[u][e], gt, acc[u]);
         else if (q == j) acc[u] = fma(sd[0][t], gt, acc[u]);
       }
     }
@@ -485,6 +575,8 @@ k_cg_upd2(int j, const double* __restrict__ dots1, const T* __restrict__ dpart2,
           double bd_tol, double rtol2_r0sq, int use_rtol, int* __restrict__ active,
           double* __restrict__ eta_out, double* __restrict__ alpha_out, int* __restrict__ count,
           T* __restrict__ Snext) {
+  pdl_wait();
+  pdl_trigger();
   if (!*active) return;
   __shared__ T c[1024 + 4];
   __shared__ double sh[3];
@@ -520,11 +612,23 @@ k_cg_upd2(int j, const double* __restrict__ dots1, const T* __restrict__ dpart2,
   }
   T d = T(0), gd = T(0);
   if (i < m) {
-#pragma unroll 4
-    for (int q = sp; q < j; q += UP_SPLIT) {
-      const T cq = c[q];
-      d = fma(-V[(size_t)q * ldv + i], cq, d);
-      gd = fma(-GV[(size_t)q * ldv + i], cq, gd);
+    for (int q0 = sp; q0 < j; q0 += UP_SPLIT * UP_VB) {
+      T xv[UP_VB], xg[UP_VB];
+#pragma unroll
+      for (int e = 0; e < UP_VB; ++e) {
+        const int q = q0 + UP_SPLIT * e;
+        xv[e] = q < j ? V[(size_t)q * ldv + i] : T(0);
+        xg[e] = q < j ? GV[(size_t)q * ldv + i] : T(0);
+      }
+#pragma unroll
+      for (int e = 0; e < UP_VB; ++e) {
+        const int q = q0 + UP_SPLIT * e;
+        if (q < j) {
+          const T cq = c[q];
+          d = fma(-xv[e], cq, d);
+          gd = fma(-xg[e], cq, gd);
+        }
+      }
     }
   }
   sd[sp][rl] = d;
@@ -556,6 +660,8 @@ k_cg_upd2(int j, const double* __restrict__ dots1, const T* __restrict__ dpart2,
 template <class T>
 __global__ void k_cg_qdots(const T* __restrict__ Q, int ldq, int j, const T* __restrict__ s, int m,
                            double* __restrict__ qd, const int* __restrict__ active) {
+  pdl_wait();
+  pdl_trigger();
   if (!*active) return;
   const int l = blockIdx.x;
   const T* a = Q + (size_t)l * ldq;
@@ -567,6 +673,8 @@ __global__ void k_cg_qdots(const T* __restrict__ Q, int ldq, int j, const T* __r
 template <class T>
 __global__ void k_cg_qorth(const T* __restrict__ Q, int ldq, int j, const double* __restrict__ qd, T* __restrict__ s,
                            int m, T* __restrict__ S, int lds, const int* __restrict__ active) {
+  pdl_wait();
+  pdl_trigger();
   if (!*active) return;
   __shared__ T c[1024];
   for (int q = threadIdx.x; q < j; q += blockDim.x) c[q] = T(qd[q]);
@@ -583,6 +691,8 @@ __global__ void k_cg_qorth(const T* __restrict__ Q, int ldq, int j, const double
 template <class T>
 __global__ void k_cg_select(int j, const T* __restrict__ r, const double* __restrict__ rep, int m,
                             T* __restrict__ s, T* __restrict__ S, int lds, const int* __restrict__ active) {
+  pdl_wait();
+  pdl_trigger();
   if (!*active) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m) return;
@@ -1378,18 +1488,17 @@ void gram_matvec(int ker, const C4<T>* Xo, const T* s, int m, T sf2, T* part, co
   const int grid = ngv + nb * (nb + 1) / 2;
   if constexpr (sizeof(T) == 4) {
     switch (ker) {
-      case 0: k_gram_matvec_f2<0><<<grid, MVS_W * 32, 0, st>>>(Xo, s, m, nb, sf2, part, Mo, ldm, rp, ngv, tpart, active); break;
-      case 1: k_gram_matvec_f2<1><<<grid, MVS_W * 32, 0, st>>>(Xo, s, m, nb, sf2, part, Mo, ldm, rp, ngv, tpart, active); break;
-      default: k_gram_matvec_f2<2><<<grid, MVS_W * 32, 0, st>>>(Xo, s, m, nb, sf2, part, Mo, ldm, rp, ngv, tpart, active); break;
+      case 0: launch_pdl(k_gram_matvec_f2<0>, dim3(grid), dim3(MVS_W * 32), 0, st, Xo, s, m, nb, sf2, part, Mo, ldm, rp, ngv, tpart, active); break;
+      case 1: launch_pdl(k_gram_matvec_f2<1>, dim3(grid), dim3(MVS_W * 32), 0, st, Xo, s, m, nb, sf2, part, Mo, ldm, rp, ngv, tpart, active); break;
+      default: launch_pdl(k_gram_matvec_f2<2>, dim3(grid), dim3(MVS_W * 32), 0, st, Xo, s, m, nb, sf2, part, Mo, ldm, rp, ngv, tpart, active); break;
     }
   } else {
     switch (ker) {
-      case 0: k_gram_matvec<0, T><<<grid, MVS_W * 32, 0, st>>>(Xo, s, m, nb, sf2, part, Mo, ldm, rp, ngv, tpart, active); break;
-      case 1: k_gram_matvec<1, T><<<grid, MVS_W * 32, 0, st>>>(Xo, s, m, nb, sf2, part, Mo, ldm, rp, ngv, tpart, active); break;
-      default: k_gram_matvec<2, T><<<grid, MVS_W * 32, 0, st>>>(Xo, s, m, nb, sf2, part, Mo, ldm, rp, ngv, tpart, active); break;
+      case 0: launch_pdl(k_gram_matvec<0, T>, dim3(grid), dim3(MVS_W * 32), 0, st, Xo, s, m, nb, sf2, part, Mo, ldm, rp, ngv, tpart, active); break;
+      case 1: launch_pdl(k_gram_matvec<1, T>, dim3(grid), dim3(MVS_W * 32), 0, st, Xo, s, m, nb, sf2, part, Mo, ldm, rp, ngv, tpart, active); break;
+      default: launch_pdl(k_gram_matvec<2, T>, dim3(grid), dim3(MVS_W * 32), 0, st, Xo, s, m, nb, sf2, part, Mo, ldm, rp, ngv, tpart, active); break;
     }
   }
-  note_launch();
 }
 
 template <class T>
@@ -1422,9 +1531,8 @@ void cg_combine(const T* part, int nsplit, const T* s, T sn2, const T* Mo, int l
                 T* g, const T* V, int ldv, int j, const T* r0, const T* v, T* dpart1, const int* active,
                 cudaStream_t st) {
   const int tz = std::max(1, (m + GV_CHUNK - 1) / GV_CHUNK);
-  k_cg_combine<T><<<cdiv(m, CB_ROWS), CB_WARPS * 32, std::max(r, 1) * sizeof(T), st>>>(
+  launch_pdl(k_cg_combine<T>, dim3(cdiv(m, CB_ROWS)), dim3(CB_WARPS * 32), std::max(r, 1) * sizeof(T), st, 
       part, nsplit, s, sn2, Mo, ldm, r, t, tz, a2, m, g, V, ldv, j, r0, v, dpart1, active);
-  note_launch();
 }
 size_t cg_dpart_elems(int m, int budget) {
   return (size_t)(budget + 4) * cdiv(std::max(m, 1), CB_ROWS) + (size_t)(budget + 1) * cdiv(std::max(m, 1), UP_ROWS);
@@ -1432,33 +1540,30 @@ size_t cg_dpart_elems(int m, int budget) {
 template <class T>
 void cg_upd1(int j, const T* dpart1, double* dots1, T* V, T* GV, int ldv, const T* s, const T* g, int m,
              T* dpart2, const int* active, cudaStream_t st) {
-  k_cg_upd1<T><<<cdiv(m, UP_ROWS), UP_THREADS, 0, st>>>(j, dpart1, (int)cdiv(m, CB_ROWS), dots1, V, GV, ldv, s, g, m,
+  launch_pdl(k_cg_upd1<T>, dim3(cdiv(m, UP_ROWS)), dim3(UP_THREADS), 0, st, j, dpart1, (int)cdiv(m, CB_ROWS), dots1, V, GV, ldv, s, g, m,
                                                         dpart2, active);
-  note_launch();
 }
 template <class T>
 void cg_upd2(int j, const double* dots1, const T* dpart2, T* V, T* GV, int ldv, T* r, T* v, T* s, T* Q,
              int m, double bd_tol, double rtol2_r0sq, int use_rtol, int* active, double* eta, double* alpha,
              int* count, T* Snext, cudaStream_t st) {
-  k_cg_upd2<T><<<cdiv(m, UP_ROWS), UP_THREADS, 0, st>>>(j, dots1, dpart2, (int)cdiv(m, UP_ROWS), V, GV, ldv, r, v,
+  launch_pdl(k_cg_upd2<T>, dim3(cdiv(m, UP_ROWS)), dim3(UP_THREADS), 0, st, j, dots1, dpart2, (int)cdiv(m, UP_ROWS), V, GV, ldv, r, v,
                                                         s, Q, m, bd_tol, rtol2_r0sq, use_rtol, active, eta, alpha,
                                                         count, Snext);
-  note_launch();
 }
 template <class T>
 void cg_reorth(const T* Q, int ldq, int j, T* s, int m, double* qd, T* S, int lds, const int* active, cudaStream_t st) {
   // two classical Gram-Schmidt passes against the previous (orthonormal) action basis
   for (int pass = 0; pass < 2; ++pass) {
     if (j > 0) {
-      k_cg_qdots<T><<<j, 256, 0, st>>>(Q, ldq, j, s, m, qd, active); note_launch();
+      launch_pdl(k_cg_qdots<T>, dim3(j), dim3(256), 0, st, Q, ldq, j, s, m, qd, active);
     }
-    k_cg_qorth<T><<<cdiv(m, 256), 256, 0, st>>>(Q, ldq, j, qd, s, m, pass == 1 ? S : nullptr, lds, active);
-    note_launch();
+    launch_pdl(k_cg_qorth<T>, dim3(cdiv(m, 256)), dim3(256), 0, st, Q, ldq, j, qd, s, m, pass == 1 ? S : nullptr, lds, active);
   }
 }
 template <class T>
 void cg_select(int j, const T* r, const double* rep, int m, T* s, T* S, int lds, const int* active, cudaStream_t st) {
-  k_cg_select<T><<<cdiv(m, 256), 256, 0, st>>>(j, r, rep, m, s, S, lds, active); note_launch();
+  launch_pdl(k_cg_select<T>, dim3(cdiv(m, 256)), dim3(256), 0, st, j, r, rep, m, s, S, lds, active);
 }
 template <class T>
 void cg_init(const double* y, const double* mpred, const int* obs, int m, T* r, T* r0, T* v, double* r0sq,
