@@ -709,29 +709,32 @@ __global__ void k_dc_secular(const MergeDesc* __restrict__ merges, const int* __
     // residual test: f is as small as rounding of its terms allows (psi < 0 < phi term-wise)
     if (fabs(f) <= 8.0 * kEps * (1.0 - psi + phi)) break;
     if (f > 0.0) thi = tau; else tlo = tau;
+    // The model step is a guess (the bracket and the residual test decide convergence), so its
+    // quotients are taken as products with Newton reciprocals (about 1 ulp; an FP64 division has a
+    // much longer dependency chain on this GPU).
     const double Dl = (Dk[i] - Dorg) - tau;
     const double sl = Dl * Dl * dpsi;
     double nt = NAN;
     if (i < Kp - 1) {
       const double Dr = (Dk[i + 1] - Dorg) - tau;
       const double sr = Dr * Dr * dphi;
-      const double c = f - sl / Dl - sr / Dr;
+      const double c = f - sl * nr_rcp(Dl) - sr * nr_rcp(Dr);
       const double A2 = c, B2 = -(c * (Dl + Dr) + sl + sr), C2 = c * Dl * Dr + sl * Dr + sr * Dl;
       double c1 = NAN, c2 = NAN;
-      if (A2 == 0.0) { if (B2 != 0.0) c1 = -C2 / B2; }
+      if (A2 == 0.0) { if (B2 != 0.0) c1 = -C2 * nr_rcp(B2); }
       else {
         double disc = B2 * B2 - 4.0 * A2 * C2;
         if (disc < 0.0) disc = 0.0;
         const double q = -0.5 * (B2 + copysign(sqrt(disc), B2));
-        c1 = q / A2;
-        if (q != 0.0) c2 = C2 / q;
+        c1 = q * nr_rcp(A2);
+        if (q != 0.0) c2 = C2 * nr_rcp(q);
       }
       if (isfinite(c1) && tau + c1 > tlo && tau + c1 < thi) nt = tau + c1;
       else if (isfinite(c2) && tau + c2 > tlo && tau + c2 < thi) nt = tau + c2;
     } else {
-      const double c = f - sl / Dl;
+      const double c = f - sl * nr_rcp(Dl);
       if (c != 0.0) {
-        const double t2 = tau + Dl + sl / c;
+        const double t2 = tau + Dl + sl * nr_rcp(c);
         if (isfinite(t2) && t2 > tlo && t2 < thi) nt = t2;
       }
     }
@@ -1096,7 +1099,7 @@ k_backtransform(const double* __restrict__ A, int lda, const double* __restrict_
 // value is an unevaluated pair hi + lo of FP32 numbers (about 48 significant bits), products are
 // formed exactly by FMA and sums carry their rounding errors in a compensation term (the Dot2 scheme
 // of Ogita, Rump and Oishi), so each dot product is as accurate as if computed in twice FP32's
-// precision.  It runs on the FP32 pipe (64 lanes per SM per clock against FP64's 1.67 FMA), so it
+// precision.  It runs on the FP32 pipe (128 lanes per SM per clock against FP64's 1.67 FMA), so it
 // is several times faster than the FP64 kernel; its error in U (about 1e-14 relative) stays far
 // below the FP32 rounding that the FP32-based modes apply to U next.  Same grouping as
 // k_backtransform (RB reflectors in compact WY form per group, CB output columns per block); the
@@ -1200,29 +1203,47 @@ k_backtransform_ff(const float2* __restrict__ Vff, const float2* __restrict__ Tf
       }
     }
     __syncthreads();
-    // Yt = T Y (T upper triangular), then Z -= V Yt
-    if (threadIdx.x < RB * CB) {
-      const int i = threadIdx.x / CB, c = threadIdx.x - i * CB;
+    // Yt = T Y (T upper triangular): output (i, c) by the 4 threads of a quad, each summing every
+    // fourth term, combined by two shuffles
+    {
+      const int o = threadIdx.x >> 2, part = threadIdx.x & 3;   // 64 outputs x 4 parts = 256 threads
+      const int i = o / CB, c = o - i * CB;
       const float2* Tg = Tff + (size_t)g * RB * RB + i * RB;
       float sacc = 0.f, cacc = 0.f;
-      for (int j = i; j < RB; ++j) ff_fma_acc(sacc, cacc, Tg[j], Y[j][c]);
-      Yt[i][c] = ff_norm(sacc, cacc);
+      for (int j = i + part; j < RB; j += 4) ff_fma_acc(sacc, cacc, Tg[j], Y[j][c]);
+      ff_acc_add(sacc, cacc, __shfl_xor_sync(0xffffffffu, sacc, 1), __shfl_xor_sync(0xffffffffu, cacc, 1));
+      ff_acc_add(sacc, cacc, __shfl_xor_sync(0xffffffffu, sacc, 2), __shfl_xor_sync(0xffffffffu, cacc, 2));
+      if (part == 0) Yt[i][c] = ff_norm(sacc, cacc);
     }
     __syncthreads();
-    for (int row = r0 + threadIdx.x; row < N; row += blockDim.x) {
-      float sacc[CB], cacc[CB];
+    // Z -= V Yt: two rows per thread at a time, CB columns each (2 CB independent accumulations)
+    for (int row = r0 + threadIdx.x; row < N; row += 2 * blockDim.x) {
+      const int row2 = row + blockDim.x;
+      const bool two = row2 < N;
+      float sacc[2][CB], cacc[2][CB];
 #pragma unroll
-      for (int c = 0; c < CB; ++c) { sacc[c] = 0.f; cacc[c] = 0.f; }
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int c = 0; c < CB; ++c) { sacc[h][c] = 0.f; cacc[h][c] = 0.f; }
 #pragma unroll
       for (int a = 0; a < RB; ++a) {
-        const float2 v = Vs[(size_t)a * N + row];
+        const float2 v0 = Vs[(size_t)a * N + row];
+        const float2 v1 = two ? Vs[(size_t)a * N + row2] : make_float2(0.f, 0.f);
 #pragma unroll
-        for (int c = 0; c < CB; ++c) ff_fma_acc(sacc[c], cacc[c], v, Yt[a][c]);
+        for (int c = 0; c < CB; ++c) {
+          const float2 y = Yt[a][c];
+          ff_fma_acc(sacc[0][c], cacc[0][c], v0, y);
+          ff_fma_acc(sacc[1][c], cacc[1][c], v1, y);
+        }
       }
 #pragma unroll
       for (int c = 0; c < CB; ++c) {
         float2& z = Z[(size_t)c * N + row];
-        z = ff_sub(z, sacc[c], cacc[c]);
+        z = ff_sub(z, sacc[0][c], cacc[0][c]);
+        if (two) {
+          float2& z2 = Z[(size_t)c * N + row2];
+          z2 = ff_sub(z2, sacc[1][c], cacc[1][c]);
+        }
       }
     }
     __syncthreads();   // every thread is done with Vs before it is refilled two groups later

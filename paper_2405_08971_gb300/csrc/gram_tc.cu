@@ -570,11 +570,13 @@ struct GemmParams {
   int stages, tmem_cols;
   uint32_t b_stage_bytes;
   long long wait_limit;
+  const uint8_t* Bpre;             // non-null: B already split and swizzled per (N chunk, K slice)
 };
 
 // Operand rows of B per producer thread and slice: a chunk has at most 256 columns (npad <= 256),
 // 128 rows per pass of the 512 producer threads.
 constexpr int GEMM_BROWS = 2;
+constexpr int GEMM_PF = 3;   // slices of A in flight per producer thread
 constexpr int GEMM_MAX_CHUNK = 128 * GEMM_BROWS;
 
 // Global loads of one 16-wide K slice: A (128 rows) and B (npad operand rows) for this thread,
@@ -582,9 +584,10 @@ constexpr int GEMM_MAX_CHUNK = 128 * GEMM_BROWS;
 // of 4 consecutive K values, one 16-byte load when aligned); A of an NN product as (row tid % 128,
 // quad tid / 128), the lanes of a warp on consecutive rows.
 __device__ __forceinline__ void load_slice(const GemmParams& P, int ks, int row0, int col0, int tid, float av[4],
-                                           float bv[GEMM_BROWS][4]) {
+                                           float bv[GEMM_BROWS][4], bool with_b, bool with_a = true) {
   const int k0 = ks * 16;
-  if (P.transA) {
+  if (!with_a) {
+  } else if (P.transA) {
     const int r = tid >> 2, kq = tid & 3;
     const int row = row0 + r, k = k0 + kq * 4;
     const float* src = P.A + (size_t)row * P.lda + k;
@@ -601,6 +604,7 @@ __device__ __forceinline__ void load_slice(const GemmParams& P, int ks, int row0
 #pragma unroll
     for (int e = 0; e < 4; ++e) av[e] = (row < P.M && k + e < P.K) ? P.A[(size_t)(k + e) * P.lda + row] : 0.f;
   }
+  if (!with_b) return;
 #pragma unroll
   for (int b = 0; b < GEMM_BROWS; ++b) {
     const int jr = (tid >> 2) + 128 * b, kq = tid & 3, k = k0 + kq * 4;
@@ -632,15 +636,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gemm_tc(const GemmParams P) {
   uint64_t* done = bars + 2 * S;           // MMA -> epilogue: a unit's accumulator is complete
   uint64_t* tfree = bars + 2 * S + 1;      // epilogue -> MMA: the accumulator has been read out
   uint64_t* fin = bars + 2 * S + 2;        // MMA issuer: all its MMAs have completed (exit)
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * S + 3);
+  uint64_t* fullB = bars + 2 * S + 3;      // bulk copy -> MMA: the stage's pre-split B slice landed
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 3 * S + 3);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int units = P.ntiles * P.nchunks * P.kchunks;
+  const bool preB = P.Bpre != nullptr;
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(smem_u32(&fullA[s]), NPROD_WARPS);
       mbar_init(smem_u32(&empty[s]), 1);
+      mbar_init(smem_u32(&fullB[s]), 1);
     }
     mbar_init(smem_u32(done), 1);
     mbar_init(smem_u32(tfree), NPROD_WARPS);
@@ -660,7 +667,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gemm_tc(const GemmParams P) {
 
   if (warp < NPROD_WARPS) {
     // ------------------------------------------------------------ operand producers + epilogue
+    // With a pre-split B, thread 0 also copies each stage's B slice (one bulk copy onto fullB[s])
+    // once the stage is free; the producers then load and split A only.
     const int tid = threadIdx.x;                    // 0 .. 511
+    long long issued = 0;                           // B copies issued by thread 0
     const int lg = warp & 3, qt = warp >> 2;        // epilogue: TMEM lane group, column-chunk phase
     long long it = 0;                               // slices produced so far (stage counter)
     int tcount = 0;
@@ -671,51 +681,68 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gemm_tc(const GemmParams P) {
       const int kc = u / (P.ntiles * P.nchunks);
       const int row0 = t * BM, col0 = nc * P.cw;
       const int ks0 = kc * P.kslices, ks1 = min(P.nk, ks0 + P.kslices);
-      // the global loads of slice ks + 1 are issued before slice ks is converted and stored, so
-      // their latency overlaps the conversion, the stores and the wait for the next free stage
-      float av[4], bv[GEMM_BROWS][4];
-      load_slice(P, ks0, row0, col0, tid, av, bv);
-      for (int ks = ks0; ks < ks1; ++ks, ++it) {
-        const int s = (int)(it % S);
-        const uint32_t n = (uint32_t)(it / S);
-        float an[4], bn[GEMM_BROWS][4];
-        if (ks + 1 < ks1) load_slice(P, ks + 1, row0, col0, tid, an, bn);
-        ok = mbar_wait(smem_u32(&empty[s]), (n & 1) ^ 1, abort_flag, P.wait_limit);
-        ok = __all_sync(0xffffffffu, ok);
-        if (!ok) break;
-        uint8_t* ast = A_base + (size_t)s * M::NPART * M::A_TILE;
-        uint8_t* bst = B_base + (size_t)s * P.b_stage_bytes;
-        {
-          const int r = P.transA ? (tid >> 2) : (tid & 127);
-          const int kq = P.transA ? (tid & 3) : (tid >> 7);
-          uint32_t h[4], l[4];
+      // A is loaded GEMM_PF slices ahead (a ring of registers indexed statically: the loop over
+      // the slices is unrolled GEMM_PF times), B one slice ahead when the producers split it, so
+      // that the loads' latency overlaps the conversion, the stores and the waits for free stages
+      float ar[GEMM_PF][4], bv[GEMM_BROWS][4];
+      load_slice(P, ks0, row0, col0, tid, ar[0], bv, !preB);
 #pragma unroll
-          for (int e = 0; e < 4; ++e) { h[e] = tf32_rna(av[e]); l[e] = tf32_rna(av[e] - __uint_as_float(h[e])); }
-          const uint32_t o = sw_off<MD>(r, kq * 16);
-          *reinterpret_cast<uint4*>(ast + o) = make_uint4(h[0], h[1], h[2], h[3]);
-          *reinterpret_cast<uint4*>(ast + M::A_TILE + o) = make_uint4(l[0], l[1], l[2], l[3]);
+      for (int q = 1; q < GEMM_PF; ++q)
+        if (ks0 + q < ks1) load_slice(P, ks0 + q, row0, col0, tid, ar[q], bv, false);
+      for (int kb = ks0; kb < ks1 && ok; kb += GEMM_PF) {
+#pragma unroll
+        for (int j = 0; j < GEMM_PF; ++j) {
+          const int ks = kb + j;
+          if (ks >= ks1) break;
+          const int s = (int)(it % S);
+          const uint32_t n = (uint32_t)(it / S);
+          float bn[GEMM_BROWS][4];
+          if (!preB && ks + 1 < ks1) load_slice(P, ks + 1, row0, col0, tid, ar[j], bn, true, false);
+          ok = mbar_wait(smem_u32(&empty[s]), (n & 1) ^ 1, abort_flag, P.wait_limit);
+          ok = __all_sync(0xffffffffu, ok);
+          if (!ok) break;
+          uint8_t* ast = A_base + (size_t)s * M::NPART * M::A_TILE;
+          uint8_t* bst = B_base + (size_t)s * P.b_stage_bytes;
+          if (preB && tid == 0) {
+            mbar_expect_tx(smem_u32(&fullB[s]), P.b_stage_bytes);
+            bulk_load(smem_u32(bst), P.Bpre + ((size_t)nc * P.nk + ks) * P.b_stage_bytes, P.b_stage_bytes,
+                      smem_u32(&fullB[s]));
+            ++issued;
+          }
+          {
+            const int r = P.transA ? (tid >> 2) : (tid & 127);
+            const int kq = P.transA ? (tid & 3) : (tid >> 7);
+            uint32_t h[4], l[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) { h[e] = tf32_rna(ar[j][e]); l[e] = tf32_rna(ar[j][e] - __uint_as_float(h[e])); }
+            const uint32_t o = sw_off<MD>(r, kq * 16);
+            *reinterpret_cast<uint4*>(ast + o) = make_uint4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<uint4*>(ast + M::A_TILE + o) = make_uint4(l[0], l[1], l[2], l[3]);
+          }
+          if (ks + GEMM_PF < ks1) load_slice(P, ks + GEMM_PF, row0, col0, tid, ar[j], bn, false);
+#pragma unroll
+          for (int b = 0; b < GEMM_BROWS; ++b) {
+            const int jr = (tid >> 2) + 128 * b;
+            if (preB || jr >= P.npad) break;
+            const int kq = tid & 3;
+            uint32_t h[4], l[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) { h[e] = tf32_rna(bv[b][e]); l[e] = tf32_rna(bv[b][e] - __uint_as_float(h[e])); }
+            const uint32_t o = sw_off<MD>(jr, kq * 16);
+            *reinterpret_cast<uint4*>(bst + o) = make_uint4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<uint4*>(bst + (size_t)P.npad * M::ROWB + o) = make_uint4(l[0], l[1], l[2], l[3]);
+          }
+          if (!preB) {
+#pragma unroll
+            for (int b = 0; b < GEMM_BROWS; ++b)
+#pragma unroll
+              for (int e = 0; e < 4; ++e) bv[b][e] = bn[b][e];
+          }
+          fence_proxy_async();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_u32(&fullA[s]));
+          ++it;
         }
-#pragma unroll
-        for (int b = 0; b < GEMM_BROWS; ++b) {
-          const int jr = (tid >> 2) + 128 * b;
-          if (jr >= P.npad) break;
-          const int kq = tid & 3;
-          uint32_t h[4], l[4];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) { h[e] = tf32_rna(bv[b][e]); l[e] = tf32_rna(bv[b][e] - __uint_as_float(h[e])); }
-          const uint32_t o = sw_off<MD>(jr, kq * 16);
-          *reinterpret_cast<uint4*>(bst + o) = make_uint4(h[0], h[1], h[2], h[3]);
-          *reinterpret_cast<uint4*>(bst + (size_t)P.npad * M::ROWB + o) = make_uint4(l[0], l[1], l[2], l[3]);
-        }
-#pragma unroll
-        for (int e = 0; e < 4; ++e) av[e] = an[e];
-#pragma unroll
-        for (int b = 0; b < GEMM_BROWS; ++b)
-#pragma unroll
-          for (int e = 0; e < 4; ++e) bv[b][e] = bn[b][e];
-        fence_proxy_async();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&fullA[s]));
       }
       ok = producers_all(ok && !*abort_flag);
       if (!ok) break;
@@ -764,6 +791,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gemm_tc(const GemmParams P) {
       ++tcount;
       ok = producers_all(ok);
     }
+    if (preB && tid == 0) {
+      // copy q went to stage q % S in phase q / S; after an abort the ones still in flight land
+      // before the CTA exits (each has already completed in a run without abort)
+      for (long long q = issued > S ? issued - S : 0; q < issued; ++q)
+        mbar_drain(smem_u32(&fullB[(int)(q % S)]), (uint32_t)((q / S) & 1));
+    }
   } else if (warp == MMA_WARP) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
@@ -782,6 +815,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gemm_tc(const GemmParams P) {
           const int s = (int)(it % S);
           const uint32_t n = (uint32_t)(it / S);
           ok = mbar_wait(smem_u32(&fullA[s]), n & 1, abort_flag, P.wait_limit);
+          if (ok && preB) ok = mbar_wait(smem_u32(&fullB[s]), n & 1, abort_flag, P.wait_limit);
           if (!ok) break;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t a0 = smem_u32(A_base + (size_t)s * M::NPART * M::A_TILE);
@@ -817,6 +851,32 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gemm_tc(const GemmParams P) {
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(P.tmem_cols) : "memory");
+  }
+}
+
+// B of an NN product split into TF32 hi / lo parts once, in the swizzled stage layout k_gemm_tc's
+// producers would write (same rounding, same zero padding): one b_stage_bytes block per (N chunk,
+// K slice), hi part then lo part, so that the GEMM copies each stage's B with one bulk copy.
+__global__ void __launch_bounds__(256)
+k_gemm_prep_b(const float* __restrict__ B, int ldb, int K, int N, int cw, int npad, int nk, uint32_t b_stage_bytes,
+              uint8_t* __restrict__ out) {
+  using M = Mode<MD_TF32X3>;
+  const int nc = blockIdx.x / nk, ks = blockIdx.x - nc * nk;
+  uint8_t* bst = out + (size_t)blockIdx.x * b_stage_bytes;
+  for (int idx = threadIdx.x; idx < npad * 4; idx += blockDim.x) {
+    const int jr = idx >> 2, kq = idx & 3;
+    const int col = nc * cw + jr, k = ks * 16 + kq * 4;
+    const bool valid = jr < cw && col < N;
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float b = (valid && k + e < K) ? B[(size_t)col * ldb + k + e] : 0.f;
+      h[e] = tf32_rna(b);
+      l[e] = tf32_rna(b - __uint_as_float(h[e]));
+    }
+    const uint32_t o = sw_off<MD_TF32X3>(jr, kq * 16);
+    *reinterpret_cast<uint4*>(bst + o) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(bst + (size_t)npad * M::ROWB + o) = make_uint4(l[0], l[1], l[2], l[3]);
   }
 }
 
@@ -1069,6 +1129,20 @@ GemmLayout gemm_layout(int npad) {
 
 // Launch k_gemm_tc; C_f32 receives alpha op(A) B + beta C directly when the K range is not split,
 // otherwise part (part_floats capacity) takes the per-chunk partial sums and the caller reduces.
+// Device scratch for the pre-split B of NN products (per host thread, grown on demand; a few MB).
+thread_local uint8_t* t_bpre = nullptr;
+thread_local size_t t_bpre_bytes = 0;
+uint8_t* bpre_scratch(size_t bytes) {
+  if (bytes > t_bpre_bytes) {
+    if (t_bpre) cudaFree(t_bpre);
+    t_bpre = nullptr;
+    t_bpre_bytes = 0;
+    if (cudaMalloc(&t_bpre, bytes) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    t_bpre_bytes = bytes;
+  }
+  return t_bpre;
+}
+
 int gemm_tc_launch(int transA, int Mr, int N, int K, float alpha, const float* A, int lda, const float* B, int ldb,
                    float beta, float* C_f32, int ldc, bool force_split, float* part, size_t part_floats,
                    int* kchunks_out, int* Mpad_out, int* err, cudaStream_t st) {
@@ -1113,6 +1187,16 @@ int gemm_tc_launch(int transA, int Mr, int N, int K, float alpha, const float* A
   P.err = err;
   P.stages = L.stages; P.tmem_cols = L.tmem_cols; P.b_stage_bytes = L.b_stage_bytes;
   P.wait_limit = wait_limit(WAIT_LIMIT);
+  P.Bpre = nullptr;
+  if (!transA && P.ntiles >= 64) {
+    // B (K x N, small) is read by every row tile: split it once and copy it per stage in bulk
+    const size_t bytes = (size_t)P.nchunks * P.nk * P.b_stage_bytes;
+    if (uint8_t* bp = bpre_scratch(bytes)) {
+      k_gemm_prep_b<<<P.nchunks * P.nk, 256, 0, st>>>(B, ldb, K, N, P.cw, P.npad, P.nk, P.b_stage_bytes, bp);
+      note_launch();
+      P.Bpre = bp;
+    }
+  }
   const int units = P.ntiles * P.nchunks * P.kchunks;
   const int grid = std::min(units, slots);
   void* args[] = {&P};

@@ -4,7 +4,9 @@ These are the products of the downdate factors in the filter's finalize and Trun
 the smoother (Alg. 3): a tall factor times a small coefficient block (NN: n x K times K x N) and the
 projection of one tall block onto another (TN: n x M transposed times n x N), with n up to the
 65,536-state workload's size.  Shapes are ragged (rows not a multiple of the 128-row tile, K not a
-multiple of the 16-wide slice, N above the 512-column accumulator so that it is split into chunks).
+multiple of the 16-wide slice, N above the 256-column chunk so that it is split into chunks).  NN
+products with at least 64 row tiles take B pre-split into its stage layout (one bulk copy per
+stage); the others split B in the producers.
 
 Tolerance, per output column normwise relative to the exact product of the FP32 inputs:
   FP32 SIMT            1e-5 (FP32 accumulation over K up to 65,536 terms)
@@ -39,7 +41,7 @@ def factors(rows, cols, rng, decay=6.0):
 
 @pytest.mark.parametrize("precision", ["fp32", "tf32x3"])
 @pytest.mark.parametrize("M,K,N", [(5000, 576, 512), (65536, 576, 512), (4097, 512, 577), (300000 // 7, 64, 65),
-                                   (2000, 17, 33)])
+                                   (2000, 17, 33), (20000, 100, 300)])
 def test_nn_tall_times_small(precision, M, K, N):
     rng = np.random.default_rng(M + K + N)
     A = factors(M, K, rng)                                    # column-major M x K = row-major (K, M)^T
