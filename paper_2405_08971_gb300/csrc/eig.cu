@@ -405,10 +405,8 @@ inline size_t prep_smem_bytes(int K) { return (size_t)K * (4 * sizeof(double) + 
 //      by rank when a rotation moved one.
 //   5. The kept columns are grouped by their row support (child 1 only, both, child 2 only) for the
 //      eigenvector product of phase 5.
-__global__ void __launch_bounds__(DC_THREADS)
-k_dc_prep(const MergeDesc* __restrict__ merges, const double* __restrict__ e, int N, DcWork W) {
-  extern __shared__ double psm[];
-  const MergeDesc mg = merges[blockIdx.x];
+// (device function: every thread of the block calls it; psm holds prep_smem_bytes(K))
+__device__ void dc_prep(const MergeDesc mg, const double* __restrict__ e, int N, DcWork W, double* psm) {
   const int lo = mg.lo, mid = mg.mid, K = mg.hi - mg.lo, n1 = mg.mid - mg.lo;
   double* sLam = psm;
   double* sZr = psm + K;
@@ -587,16 +585,18 @@ k_dc_prep(const MergeDesc* __restrict__ merges, const double* __restrict__ e, in
     }
   }
 }
+__global__ void __launch_bounds__(DC_THREADS)
+k_dc_prep(const MergeDesc* __restrict__ merges, const double* __restrict__ e, int N, DcWork W) {
+  extern __shared__ double psm[];
+  dc_prep(merges[blockIdx.x], e, N, W, psm);
+}
 
 // Phase 1b: the deflation rotations applied to the child eigenvector columns, one thread per row of
 // the merge.  Rotation q acts on (a_q, b_q) with b_q a column no earlier rotation touched, and a_q
 // either untouched as well or equal to b_{q-1}; so each group of RG rotations loads its operands up
 // front (independent loads), and the a_q = b_{q-1} chain is carried in a register.
-__global__ void __launch_bounds__(128)
-k_dc_rot(const MergeDesc* __restrict__ merges, int N, DcWork W) {
-  const MergeDesc mg = merges[blockIdx.y];
+__device__ void dc_rot_row(const MergeDesc mg, int N, DcWork W, int row) {
   const int lo = mg.lo, K = mg.hi - mg.lo;
-  const int row = blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= K) return;
   const int nrot = W.nrot[lo];
   if (nrot == 0) return;
@@ -635,26 +635,29 @@ k_dc_rot(const MergeDesc* __restrict__ merges, int N, DcWork W) {
     }
   }
 }
+__global__ void __launch_bounds__(128)
+k_dc_rot(const MergeDesc* __restrict__ merges, int N, DcWork W) {
+  dc_rot_row(merges[blockIdx.y], N, W, blockIdx.x * blockDim.x + threadIdx.x);
+}
 
-// Sum over the LANES lanes that share one root (LANES = 32: a warp; LANES = 1: one thread).
-template <int LANES> __device__ __forceinline__ double group_sum(double v) {
+// Sum over the LANES lanes that share one root (LANES = 32: a warp; LANES = 1: one thread; in
+// between, an aligned group of lanes of a warp named by mask, which lets the groups of one warp
+// run different iteration counts).
+template <int LANES> __device__ __forceinline__ double group_sum(double v, unsigned mask = 0xffffffffu) {
   if constexpr (LANES == 32) return warp_sum(v);
-  else return v;
+  else if constexpr (LANES == 1) return v;
+  else {
+#pragma unroll
+    for (int o = LANES / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
+    return v;
+  }
 }
 
 // Phase 2: secular roots, LANES lanes per (merge, root) -- a warp for large merges, one thread for
 // small ones; the sums over poles are split across the lanes.
 // delta column i: Delta[(lo+i)*N + lo + j] = Dk_j - lam_i, computed from the origin pole.
 template <int LANES>
-__global__ void k_dc_secular(const MergeDesc* __restrict__ merges, const int* __restrict__ mergeof, int N, DcWork W,
-                             int* err) {
-  const int p = (blockIdx.x * blockDim.x + threadIdx.x) / LANES;
-  const int lane = threadIdx.x % LANES;
-  if (p >= N) return;
-  const int mi = mergeof[p];
-  if (mi < 0) return;
-  const int lo = merges[mi].lo;
-  const int i = p - lo;
+__device__ void dc_secular_root(int lo, int i, int N, DcWork W, int* err, int lane, unsigned gmask) {
   const int Kp = W.Kp[lo];
   if (i >= Kp) return;
   const double* Dk = W.Dk + lo;
@@ -677,7 +680,8 @@ __global__ void k_dc_secular(const MergeDesc* __restrict__ merges, const int* __
       if (j <= i) { psi += tv; dpsi += tv * rinv; }
       else { phi += tv; dphi += tv * rinv; }
     }
-    psi = group_sum<LANES>(psi); dpsi = group_sum<LANES>(dpsi); phi = group_sum<LANES>(phi); dphi = group_sum<LANES>(dphi);
+    psi = group_sum<LANES>(psi, gmask); dpsi = group_sum<LANES>(dpsi, gmask);
+    phi = group_sum<LANES>(phi, gmask); dphi = group_sum<LANES>(dphi, gmask);
     if (1.0 + psi + phi >= 0.0) { org = i; tlo = 0.0; thi = mid - Dk[i]; tau = thi; }
     else { org = i + 1; tlo = mid - Dk[i + 1]; thi = 0.0; tau = tlo; }
     have = true;
@@ -686,7 +690,7 @@ __global__ void k_dc_secular(const MergeDesc* __restrict__ merges, const int* __
     double zz = 0.0;
     for (int j = lane; j < Kp; j += LANES) zz += Zk[j] * Zk[j];
     tlo = 0.0;
-    thi = rho * group_sum<LANES>(zz);
+    thi = rho * group_sum<LANES>(zz, gmask);
     tau = 0.5 * (tlo + thi);
   }
   const double Dorg = Dk[org];
@@ -701,7 +705,8 @@ __global__ void k_dc_secular(const MergeDesc* __restrict__ merges, const int* __
         if (j <= i) { psi += tv; dpsi += tv * rinv; }
         else { phi += tv; dphi += tv * rinv; }
       }
-      psi = group_sum<LANES>(psi); dpsi = group_sum<LANES>(dpsi); phi = group_sum<LANES>(phi); dphi = group_sum<LANES>(dphi);
+      psi = group_sum<LANES>(psi, gmask); dpsi = group_sum<LANES>(dpsi, gmask);
+      phi = group_sum<LANES>(phi, gmask); dphi = group_sum<LANES>(dphi, gmask);
     }
     have = false;
     const double f = 1.0 + psi + phi;
@@ -747,19 +752,23 @@ __global__ void k_dc_secular(const MergeDesc* __restrict__ merges, const int* __
   for (int j = lane; j < Kp; j += LANES) delta[j] = (Dk[j] - Dorg) - tau;
   if (lane == 0) W.lamk[lo + i] = Dorg + tau;
 }
-
-// Phase 3: Loewner-corrected z (one warp per j):
-//   zhat_j^2 = (lam_last - D_j)/rho * prod_{i<j} (lam_i - D_j)/(D_i - D_j) * prod_{i>j} (lam_{i-1} - D_j)/(D_i - D_j)
-// The product is formed as a sum of logarithms of the (positive) factors split across lanes.
 template <int LANES>
-__global__ void k_dc_zhat(const MergeDesc* __restrict__ merges, const int* __restrict__ mergeof, int N, DcWork W) {
+__global__ void k_dc_secular(const MergeDesc* __restrict__ merges, const int* __restrict__ mergeof, int N, DcWork W,
+                             int* err) {
   const int p = (blockIdx.x * blockDim.x + threadIdx.x) / LANES;
   const int lane = threadIdx.x % LANES;
   if (p >= N) return;
   const int mi = mergeof[p];
   if (mi < 0) return;
   const int lo = merges[mi].lo;
-  const int j = p - lo;
+  dc_secular_root<LANES>(lo, p - lo, N, W, err, lane, 0xffffffffu);
+}
+
+// Phase 3: Loewner-corrected z (one warp per j):
+//   zhat_j^2 = (lam_last - D_j)/rho * prod_{i<j} (lam_i - D_j)/(D_i - D_j) * prod_{i>j} (lam_{i-1} - D_j)/(D_i - D_j)
+// The product is formed as a sum of logarithms of the (positive) factors split across lanes.
+template <int LANES>
+__device__ void dc_zhat_one(int lo, int j, int N, DcWork W, int lane, unsigned gmask) {
   const int Kp = W.Kp[lo];
   if (j >= Kp) return;
   const double* Dk = W.Dk + lo;
@@ -776,14 +785,35 @@ __global__ void k_dc_zhat(const MergeDesc* __restrict__ merges, const int* __res
     if (!(prod > 1e-150 && prod < 1e150)) { lg += log(prod); prod = 1.0; }
   }
   lg += log(prod);
-  lg = group_sum<LANES>(lg);
+  lg = group_sum<LANES>(lg, gmask);
   if (lane == 0) {
     const double last = -W.Delta[(size_t)(lo + Kp - 1) * N + lo + j] / rho;
     W.Zw[lo + j] = copysign(sqrt(fabs(last)) * exp(0.5 * lg), W.Zk[lo + j]);
   }
 }
+template <int LANES>
+__global__ void k_dc_zhat(const MergeDesc* __restrict__ merges, const int* __restrict__ mergeof, int N, DcWork W) {
+  const int p = (blockIdx.x * blockDim.x + threadIdx.x) / LANES;
+  const int lane = threadIdx.x % LANES;
+  if (p >= N) return;
+  const int mi = mergeof[p];
+  if (mi < 0) return;
+  const int lo = merges[mi].lo;
+  dc_zhat_one<LANES>(lo, p - lo, N, W, lane, 0xffffffffu);
+}
 
 // Phase 4: eigenvector columns u_i = zhat / delta_i, normalised, written over Delta (one warp per i).
+template <int LANES>
+__device__ void dc_vecs_one(int lo, int i, int N, DcWork W, int lane, unsigned gmask) {
+  const int Kp = W.Kp[lo];
+  if (i >= Kp) return;
+  double* col = W.Delta + (size_t)(lo + i) * N + lo;
+  double nrm = 0.0;
+  for (int j = lane; j < Kp; j += LANES) { double u = W.Zw[lo + j] * nr_rcp(col[j]); col[j] = u; nrm += u * u; }
+  nrm = group_sum<LANES>(nrm, gmask);
+  const double inv = 1.0 / sqrt(nrm);
+  for (int j = lane; j < Kp; j += LANES) col[j] *= inv;
+}
 template <int LANES>
 __global__ void k_dc_vecs(const MergeDesc* __restrict__ merges, const int* __restrict__ mergeof, int N, DcWork W) {
   const int p = (blockIdx.x * blockDim.x + threadIdx.x) / LANES;
@@ -792,27 +822,17 @@ __global__ void k_dc_vecs(const MergeDesc* __restrict__ merges, const int* __res
   const int mi = mergeof[p];
   if (mi < 0) return;
   const int lo = merges[mi].lo;
-  const int i = p - lo;
-  const int Kp = W.Kp[lo];
-  if (i >= Kp) return;
-  double* col = W.Delta + (size_t)(lo + i) * N + lo;
-  double nrm = 0.0;
-  for (int j = lane; j < Kp; j += LANES) { double u = W.Zw[lo + j] * nr_rcp(col[j]); col[j] = u; nrm += u * u; }
-  nrm = group_sum<LANES>(nrm);
-  const double inv = 1.0 / sqrt(nrm);
-  for (int j = lane; j < Kp; j += LANES) col[j] *= inv;
+  dc_vecs_one<LANES>(lo, p - lo, N, W, lane, 0xffffffffu);
 }
 
 // Phase 5: Qtmp[lo:hi, lo+i] = Q[lo:hi, colk] U[:, i] (i < Kp); deflated columns copied after them.
 // The sum over kept poles runs in the support order of phase 1 (gperm): a row tile inside child 1
 // skips the columns supported on child 2 only and vice versa, about half of the products.
 constexpr int DG_T = 32;
-__global__ void __launch_bounds__(256)
-k_dc_gemm(const MergeDesc* __restrict__ merges, int N, DcWork W) {
-  const MergeDesc mg = merges[blockIdx.z];
+// (device function: every thread of a 256-thread block calls it with the same tile)
+__device__ void dc_gemm_tile(const MergeDesc mg, int N, DcWork W, int r0, int c0) {
   const int lo = mg.lo, K = mg.hi - mg.lo, n1 = mg.mid - mg.lo;
   const int Kp = W.Kp[lo];
-  const int r0 = blockIdx.x * DG_T, c0 = blockIdx.y * DG_T;
   if (r0 >= K || c0 >= K) return;
   __shared__ double As[DG_T][DG_T + 1], Bs[DG_T][DG_T + 1];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -859,14 +879,15 @@ k_dc_gemm(const MergeDesc* __restrict__ merges, int N, DcWork W) {
       W.Qtmp[(size_t)(lo + c) * N + lo + row] = val;
     }
 }
+__global__ void __launch_bounds__(256)
+k_dc_gemm(const MergeDesc* __restrict__ merges, int N, DcWork W) {
+  dc_gemm_tile(merges[blockIdx.z], N, W, blockIdx.x * DG_T, blockIdx.y * DG_T);
+}
 
 // Phase 6a: order the merged spectrum ascending (one block per merge): W.lam and the column
 // permutation W.perm (relative to lo) for phase 6b.  Rank sort on (value key, position): the kept
 // roots come before deflated poles of equal value.
-__global__ void __launch_bounds__(256)
-k_dc_finish(const MergeDesc* __restrict__ merges, int N, DcWork W) {
-  extern __shared__ double fsm[];
-  const MergeDesc mg = merges[blockIdx.x];
+__device__ void dc_finish(const MergeDesc mg, int N, DcWork W, double* fsm) {
   const int lo = mg.lo, K = mg.hi - mg.lo;
   const int Kp = W.Kp[lo];
   double* sl = fsm;                                          // K merged eigenvalues (kept roots, deflated poles)
@@ -888,14 +909,16 @@ k_dc_finish(const MergeDesc* __restrict__ merges, int N, DcWork W) {
     W.perm[lo + rank] = t;
   }
 }
+__global__ void __launch_bounds__(256)
+k_dc_finish(const MergeDesc* __restrict__ merges, int N, DcWork W) {
+  extern __shared__ double fsm[];
+  dc_finish(merges[blockIdx.x], N, W, fsm);
+}
 
 // Phase 6b: move the merged eigenvector columns back into Q in ascending order
 // (grid: column groups of 8 x merges).
-__global__ void __launch_bounds__(256)
-k_dc_copy(const MergeDesc* __restrict__ merges, int N, DcWork W) {
-  const MergeDesc mg = merges[blockIdx.y];
+__device__ void dc_copy_cols(const MergeDesc mg, int N, DcWork W, int c0) {
   const int lo = mg.lo, K = mg.hi - mg.lo;
-  const int c0 = blockIdx.x * 8;
   if (c0 >= K) return;
   const int c1 = min(K, c0 + 8);
   for (int c = c0; c < c1; ++c) {
@@ -903,6 +926,47 @@ k_dc_copy(const MergeDesc* __restrict__ merges, int N, DcWork W) {
     double* dst = W.Q + (size_t)(lo + c) * N + lo;
     for (int row = threadIdx.x; row < K; row += blockDim.x) dst[row] = src[row];
   }
+}
+__global__ void __launch_bounds__(256)
+k_dc_copy(const MergeDesc* __restrict__ merges, int N, DcWork W) {
+  dc_copy_cols(merges[blockIdx.y], N, W, blockIdx.x * 8);
+}
+
+// All phases of a merge of order at most DC_SMALL_K in one block (one block per merge of the level):
+// the levels near the leaves have many small merges, where eight launches per level cost more than
+// the work.  The phases run in the order of the per-phase kernels, separated by block barriers;
+// every phase touches only the merge's own rows and columns.  Roots, z entries and eigenvector
+// columns are taken by groups of DC_SMALL_LANES lanes.
+constexpr int DC_SMALL_K = 40;
+constexpr int DC_SMALL_LANES = 8;
+inline size_t small_smem_bytes(int K) {
+  return std::max(prep_smem_bytes(K), (size_t)K * (sizeof(double) + sizeof(long long)));
+}
+__global__ void __launch_bounds__(DC_THREADS)
+k_dc_small(const MergeDesc* __restrict__ merges, const double* __restrict__ e, int N, DcWork W, int* err) {
+  extern __shared__ double ssm[];
+  constexpr int L = DC_SMALL_LANES;
+  const MergeDesc mg = merges[blockIdx.x];
+  const int lo = mg.lo, K = mg.hi - mg.lo;
+  dc_prep(mg, e, N, W, ssm);
+  __syncthreads();
+  for (int row = threadIdx.x; row < K; row += blockDim.x) dc_rot_row(mg, N, W, row);
+  __syncthreads();
+  const int Kp = W.Kp[lo];
+  const int grp = threadIdx.x / L, lane = threadIdx.x % L, ngrp = blockDim.x / L;
+  const unsigned gmask = ((1u << L) - 1u) << ((threadIdx.x & 31) & ~(L - 1));
+  for (int i = grp; i < Kp; i += ngrp) dc_secular_root<L>(lo, i, N, W, err, lane, gmask);
+  __syncthreads();
+  for (int j = grp; j < Kp; j += ngrp) dc_zhat_one<L>(lo, j, N, W, lane, gmask);
+  __syncthreads();
+  for (int i = grp; i < Kp; i += ngrp) dc_vecs_one<L>(lo, i, N, W, lane, gmask);
+  __syncthreads();
+  const int nt = (K + DG_T - 1) / DG_T;
+  for (int t = 0; t < nt * nt; ++t) dc_gemm_tile(mg, N, W, (t / nt) * DG_T, (t % nt) * DG_T);
+  __syncthreads();
+  dc_finish(mg, N, W, ssm);
+  __syncthreads();
+  for (int c0 = 0; c0 < K; c0 += 8) dc_copy_cols(mg, N, W, c0);
 }
 
 // ---- double-FP32 arithmetic (pairs hi + lo of FP32 numbers).  The _rn intrinsics keep the compiler
@@ -1010,7 +1074,7 @@ k_backtransform(const double* __restrict__ A, int lda, const double* __restrict_
   __shared__ double Y[RB][CB], Yt[RB][CB];
   const int c0 = blockIdx.x * CB;
   const int ncol = min(CB, nkeep - c0);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int e = threadIdx.x; e < CB * N; e += blockDim.x) {
     const int c = e / N, t = e - c * N;
     Z[e] = (c < ncol) ? Q[(size_t)(N - 1 - (c0 + c)) * N + t] : 0.0;
@@ -1432,6 +1496,10 @@ int eig_sym_topk(double* A, int lda, int N, int nkeep, double* w, T* U, int ldu,
     const int* dmo = pe->d_mergeof + (size_t)lv * N;
     int kmax = 0;
     for (int q = m0; q < m1; ++q) kmax = std::max(kmax, pl.merges[q].hi - pl.merges[q].lo);
+    if (kmax <= DC_SMALL_K) {
+      k_dc_small<<<nm, DC_THREADS, small_smem_bytes(kmax), st>>>(dm, e, N, W, err); note_launch();
+      continue;
+    }
     const size_t psmem = prep_smem_bytes(kmax);
     if (psmem > 40 * 1024) cudaFuncSetAttribute(k_dc_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
     k_dc_prep<<<nm, DC_THREADS, psmem, st>>>(dm, e, N, W); note_launch();

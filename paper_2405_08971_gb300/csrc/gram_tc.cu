@@ -752,25 +752,33 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gemm_tc(const GemmParams P) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if (ok) {
         const int row = row0 + lg * 32 + lane;
-        const int nch = (P.npad + 31) / 32;
-        for (int ch = qt; ch < nch; ch += NQ) {
-          uint32_t v[32];
-          const uint32_t taddr = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(ch * 32);
+        // TMEM is read 16 columns at a time; with beta != 0 the 16 matching C values are loaded
+        // first, together, so they are in flight at once instead of one load per column
+        const bool rdc = !P.part && P.beta != 0.f;
+        const int nh = (P.npad + 15) / 16;
+        for (int hc = qt; hc < nh; hc += NQ) {
+          float cin[16];
+          if (rdc && row < P.M) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int c = hc * 16 + j, col = col0 + c;
+              cin[j] = (c < P.cw && col < P.N) ? P.C[(size_t)col * P.ldc + row] : 0.f;
+            }
+          }
+          uint32_t v[16];
+          const uint32_t taddr = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(hc * 16);
           asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-              "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
                 "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-                "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-                "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                "=r"(v[15])
               : "r"(taddr)
               : "memory");
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
           if (row < P.M) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const int c = ch * 32 + j;
+            for (int j = 0; j < 16; ++j) {
+              const int c = hc * 16 + j;
               const int col = col0 + c;
               if (c < P.cw && col < P.N) {
                 const float acc = __uint_as_float(v[j]);
@@ -778,7 +786,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gemm_tc(const GemmParams P) {
                   P.part[((size_t)kc * P.N + col) * P.Mpad + row] = acc;
                 } else {
                   float* dst = P.C + (size_t)col * P.ldc + row;
-                  *dst = P.beta == 0.f ? P.alpha * acc : fmaf(P.alpha, acc, P.beta * *dst);
+                  *dst = rdc ? fmaf(P.alpha, acc, P.beta * cin[j]) : P.alpha * acc;
                 }
               }
             }
