@@ -163,7 +163,7 @@ k_gram_matvec(const C4<T>* __restrict__ Xo, const T* __restrict__ s, int m, int 
 // reduce-scatter (31 shuffles) instead of one warp sum per column.  Same tiles, slots and Mo^T s
 // blocks as k_gram_matvec.
 template <int KER>
-__global__ void __launch_bounds__(MVS_W * 32)
+__global__ void __launch_bounds__(MVS_W * 32, 7)   // 7 blocks per SM (72 registers): 24.3 -> 23.9 us
 k_gram_matvec_f2(const C4<float>* __restrict__ Xo, const float* __restrict__ s, int m, int nb, float sf2,
                  float* __restrict__ part, const float* __restrict__ Mo, int ldm, int rp, int ngv,
                  float* __restrict__ tpart, const int* __restrict__ active) {
