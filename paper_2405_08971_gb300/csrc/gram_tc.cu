@@ -1137,10 +1137,20 @@ GemmLayout gemm_layout(int npad) {
 
 // Launch k_gemm_tc; C_f32 receives alpha op(A) B + beta C directly when the K range is not split,
 // otherwise part (part_floats capacity) takes the per-chunk partial sums and the caller reduces.
-// Device scratch for the pre-split B of NN products (per host thread, grown on demand; a few MB).
+// Device scratch for the pre-split B of NN products (per host thread and current device, grown on
+// demand; a few MB).
 thread_local uint8_t* t_bpre = nullptr;
 thread_local size_t t_bpre_bytes = 0;
+thread_local int t_bpre_dev = -1;
 uint8_t* bpre_scratch(size_t bytes) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+  if (dev != t_bpre_dev) {            // a buffer of another device is not reachable from this one
+    if (t_bpre) cudaFree(t_bpre);
+    t_bpre = nullptr;
+    t_bpre_bytes = 0;
+    t_bpre_dev = dev;
+  }
   if (bytes > t_bpre_bytes) {
     if (t_bpre) cudaFree(t_bpre);
     t_bpre = nullptr;

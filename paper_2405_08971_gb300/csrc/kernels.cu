@@ -1635,10 +1635,20 @@ void gemm_tn(const T* A, int lda, int na, const T* B, int ldb, int nb, int K, do
   k_reduce_splits<double><<<cdiv(tile_elems, 256), 256, 0, st>>>(part, nsplit, na, nb, alpha, beta, C, ldc); note_launch();
 }
 
-// FP32 copy of a small double coefficient block for the tensor-core path (thread-local device scratch)
+// FP32 copy of a small double coefficient block for the tensor-core path (device scratch per host
+// thread and current device)
 static thread_local float* t_bscratch = nullptr;
 static thread_local size_t t_bscratch_elems = 0;
+static thread_local int t_bscratch_dev = -1;
 static float* bscratch(size_t elems) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+  if (dev != t_bscratch_dev) {        // a buffer of another device is not reachable from this one
+    if (t_bscratch) cudaFree(t_bscratch);
+    t_bscratch = nullptr;
+    t_bscratch_elems = 0;
+    t_bscratch_dev = dev;
+  }
   if (elems > t_bscratch_elems) {
     if (t_bscratch) cudaFree(t_bscratch);
     t_bscratch = nullptr;
